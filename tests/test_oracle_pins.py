@@ -1,0 +1,375 @@
+"""Pins of the FP64 CPU oracle against things other than itself.
+
+Each test ties one part of the oracle to mathematics or to a value fixed
+outside it: a dense matrix written from the footnote's definition of M, the
+closed-form eigenvalues of a circulant operator, a dense pseudo-inverse,
+textbook B-spline values, the rock-salt Madelung constant through an
+independent Ewald sum, Ewald forces, momentum conservation (Sec. II.A),
+energy conservation of V_work (Eq. E_nostra, Sec. III.C), time
+reversibility (Sec. III.C) and the SHAKE identity (Eqs. SHAKEy, SHAKEPhiFinal).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2505_20418_gb300 import synth
+from tests.ewald import ewald
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def madelung():
+    with open(os.path.join(GOLDEN, "madelung_nacl.txt")) as f:
+        return float([l for l in f if not l.startswith("#")][0])
+
+
+def dense_M(N):
+    """M from the footnote: -6 on the diagonal, +1 for each of the six
+    periodic neighbours in (i, j, k), flat index n = i + jN + kN^2."""
+    n = N ** 3
+    A = np.zeros((n, n))
+    for k in range(N):
+        for j in range(N):
+            for i in range(N):
+                a = i + j * N + k * N * N
+                A[a, a] += -6.0
+                for di, dj, dk in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+                    b = (i + di) % N + ((j + dj) % N) * N + ((k + dk) % N) * N * N
+                    A[a, b] += 1.0
+    return A
+
+
+def flat(v):
+    return v.ravel()  # [k, j, i] C-order -> n = i + jN + kN^2
+
+
+@pytest.mark.parametrize("N", [3, 4, 5])
+def test_apply_M_matches_dense_footnote(N):
+    A = dense_M(N)
+    rng = np.random.default_rng(N)
+    x = rng.normal(size=(N, N, N))
+    np.testing.assert_allclose(flat(O.apply_M(x)), A @ flat(x), rtol=0, atol=1e-13)
+    assert np.allclose(A, A.T)  # symmetric, as the footnote recalls
+
+
+def test_plane_waves_are_eigenvectors():
+    N = 6
+    lam = O.M_eigenvalues(N)
+    k, j, i = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    for kz, ky, kx in ((0, 0, 1), (1, 2, 3), (5, 0, 2)):
+        wave = np.cos(2 * np.pi * (kx * i + ky * j + kz * k) / N)
+        np.testing.assert_allclose(O.apply_M(wave), lam[kz, ky, kx] * wave, atol=1e-12)
+    assert lam[0, 0, 0] == 0.0 and lam.max() <= 0 and math.isclose(lam.min(), -12.0)
+
+
+@pytest.mark.parametrize("N", [4, 6])
+def test_exact_solve_is_pseudo_inverse(N):
+    A = dense_M(N)
+    rng = np.random.default_rng(1)
+    b = rng.normal(size=(N, N, N))
+    b -= b.mean()
+    ref = np.linalg.lstsq(A, flat(b), rcond=None)[0]
+    np.testing.assert_allclose(flat(O.solve_exact(b)), ref, atol=1e-11)
+
+
+@pytest.mark.parametrize("solver", ["cg", "mg"])
+def test_iterative_solvers_vs_dense_lstsq(solver):
+    """P8: N = 8, dense 512 x 512 M solved by lstsq vs the oracle's PLCG and MG."""
+    N = 8
+    A = dense_M(N)
+    rng = np.random.default_rng(2)
+    b = rng.normal(size=(N, N, N))
+    b -= b.mean()
+    ref = np.linalg.lstsq(A, flat(b), rcond=None)[0]
+    y, info = O.solve(b, np.zeros_like(b), 1e-12, solver)
+    assert info.converged and info.resid < 1e-12
+    np.testing.assert_allclose(flat(y - y.mean()), ref - ref.mean(), atol=1e-11)
+    assert np.max(np.abs(A @ flat(y) - flat(b))) < 1e-12
+
+
+def test_plcg_warm_start_no_work():
+    N = 8
+    rng = np.random.default_rng(3)
+    b = rng.normal(size=(N, N, N))
+    b -= b.mean()
+    y = O.solve_exact(b)
+    _, info = O.plcg(b, y, 1e-10)
+    assert info.iters == 0
+
+
+def test_mg_transfer_operators():
+    """Full weighting is 1/8 of the transpose of trilinear prolongation, both
+    preserve constants, and one V-cycle contracts the error strongly."""
+    rng = np.random.default_rng(4)
+    u = rng.normal(size=(8, 8, 8))
+    v = rng.normal(size=(4, 4, 4))
+    lhs = np.sum(O.restrict_fw(u) * v)
+    rhs = np.sum(u * O.prolong_trilinear(v)) / 8.0
+    assert abs(lhs - rhs) < 1e-12
+    np.testing.assert_allclose(O.restrict_fw(np.full((8, 8, 8), 3.0)), 3.0)
+    np.testing.assert_allclose(O.prolong_trilinear(np.full((4, 4, 4), 2.0)), 2.0)
+    # prolongation of a linear-in-x coarse field is linear where no wrap occurs
+    ramp = np.broadcast_to(np.arange(4.0)[None, None, :], (4, 4, 4))
+    fine = O.prolong_trilinear(ramp)
+    np.testing.assert_allclose(fine[0, 0, :7], np.arange(7) / 2.0)
+    # V-cycle convergence factor on a random zero-mean rhs
+    N = 32
+    b = rng.normal(size=(N, N, N))
+    b -= b.mean()
+    x = np.zeros_like(b)
+    r0 = O.inf_norm(b)
+    x = O.vcycle(x, b, 1e-12)
+    r1 = O.inf_norm(b - O.apply_M(x))
+    x = O.vcycle(x, b, 1e-12)
+    r2 = O.inf_norm(b - O.apply_M(x))
+    assert r1 / r0 < 0.2 and r2 / r1 < 0.2
+
+
+def test_rbgs_is_gauss_seidel():
+    """A red half-sweep sets each red point so that its residual vanishes."""
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=(6, 6, 6))
+    b = rng.normal(size=(6, 6, 6))
+    red = O.red_mask(6)
+    nb = O.apply_M(x) + 6 * x
+    xr = np.where(red, (nb - b) / 6.0, x)
+    r = b - O.apply_M(xr)
+    assert np.max(np.abs(r[red])) < 1e-12
+    xs = O.rbgs_sweep(x, b)
+    r = b - O.apply_M(xs)
+    assert np.max(np.abs(r[~red])) < 1e-12      # black points are exact after the sweep
+
+
+def test_bspline_textbook_values():
+    # cubic B-spline at integer and half-integer offsets
+    np.testing.assert_allclose(O.bspline(np.array([-1.0, 0.0, 1.0, 2.0]), 4), [1 / 6, 2 / 3, 1 / 6, 0.0])
+    np.testing.assert_allclose(O.bspline(np.array([-1.5, -0.5, 0.5, 1.5]), 4), [1 / 48, 23 / 48, 23 / 48, 1 / 48])
+    np.testing.assert_allclose(O.bspline(np.array([0.25, -0.75]), 2), [0.75, 0.25])
+    # partition of unity and reproduction of linear functions, random offsets
+    rng = np.random.default_rng(6)
+    pos = rng.uniform(0, 10, size=(50, 3))
+    for P in (2, 4):
+        nodes, dist = O.support(pos, 10.0, 10, P)
+        w = O.bspline(dist, P)
+        np.testing.assert_allclose(w.sum(-1), 1.0, atol=1e-14)
+        np.testing.assert_allclose((w * dist).sum(-1), 0.0, atol=1e-14)
+    # derivative is the derivative
+    d = np.linspace(-2.2, 2.2, 41)
+    for P in (2, 4):
+        fd = (O.bspline(d + 1e-6, P) - O.bspline(d - 1e-6, P)) / 2e-6
+        ok = np.abs(np.abs(d) - np.round(np.abs(d))) > 1e-3
+        np.testing.assert_allclose(O.bspline_deriv(d, P)[ok], fd[ok], atol=1e-6)
+
+
+@pytest.mark.parametrize("P", [2, 4])
+def test_spread_conserves_charge_and_dipole(P):
+    rng = np.random.default_rng(7)
+    L, N = 10.0, 20
+    pos = rng.uniform(3.0, 7.0, size=(12, 3))      # away from the periodic seam
+    Q = rng.normal(size=12)
+    q = O.spread(pos, Q, L, N, P)
+    assert abs(q.sum() - Q.sum()) < 1e-12
+    h = L / N
+    k, j, i = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    for c, idx in enumerate((i, j, k)):
+        assert abs((q * idx * h).sum() - (Q * pos[:, c]).sum()) < 1e-11
+    # an ion on a node with P = 2 puts all of its charge on that node
+    q1 = O.spread(np.array([[2.0, 3.0, 4.5]]), np.array([1.0]), L, N, 2)
+    assert q1[9, 6, 4] == 1.0 and abs(q1).sum() == 1.0
+
+
+def test_madelung_from_ewald_and_grid():
+    """P3: an independent Ewald sum gives the rock-salt Madelung energy; the
+    grid energy (self-energy removed, App. A) converges to it as h^2."""
+    Mad = madelung()
+    L, n = 12.6, 4
+    d = L / n
+    pos, types = synth.rocksalt(n, L, 0.0, np.random.default_rng(0))
+    Q = np.where(types == 0, 1.0, -1.0)
+    E, F = ewald(pos, Q, L)
+    ref = -Mad * (len(Q) / 2) * O.K_E / d
+    assert abs(E * O.K_E - ref) < 1e-9 * abs(ref)
+    assert np.abs(F).max() < 1e-12
+    E1, _ = ewald(pos[:1], np.array([1.0]), L)     # one charge + background
+    errs = []
+    for N in (16, 32, 64):
+        p = O.Params(L=L, N=N, dt=1.0, tol=1e-12)
+        phi, q = O.exact_potential(pos, types, p)
+        Vd = O.discrete_energy(q, phi)
+        q1 = O.spread(pos[:1], np.array([1.0]), L, N, 4)
+        q1 -= q1.mean()
+        Es = O.discrete_energy(q1, -(4 * np.pi / p.h) * O.solve_exact(q1))
+        est = Vd - len(Q) * (Es - E1 * O.K_E)
+        errs.append(abs(est - ref))
+        # on the perfect lattice aligned with the grid the field force vanishes
+        assert np.abs(O.gather_forces(pos, Q, phi, L, N, 4)).max() < 1e-12
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.0   # O(h^2)
+    assert errs[2] < 0.005 * abs(ref)
+
+
+@pytest.mark.parametrize("P", [2, 4])
+def test_forces_converge_to_ewald(P):
+    """P4: random 8-ion box; grid forces approach Ewald forces as h shrinks."""
+    L = 10.0
+    pos, types = synth.random_neutral(8, L, 7, min_dist=2.0)
+    Q = np.where(types == 0, 1.0, -1.0)
+    _, Fe = ewald(pos, Q, L)
+    Fe *= O.K_E
+    errs = []
+    for N in (16, 32, 64):
+        p = O.Params(L=L, N=N, dt=1.0, tol=1e-12, P=P)
+        phi, _ = O.exact_potential(pos, types, p)
+        F = O.gather_forces(pos, Q, phi, L, N, P)
+        errs.append(np.abs(F - Fe).max() / np.abs(Fe).max())
+        # P5: momentum conservation of Eq. F_nostra
+        assert np.abs(F.sum(0)).max() < 1e-12 * np.abs(F).sum()
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 0.005
+
+
+def test_tilde_force_breaks_momentum():
+    """Eq. F_Benoit does not conserve momentum, Eq. F_nostra does (Sec. II.A)."""
+    L, N = 10.0, 16
+    pos, types = synth.random_neutral(8, L, 11, min_dist=2.0)
+    Q = np.where(types == 0, 1.0, -1.0)
+    p = O.Params(L=L, N=N, dt=1.0, tol=1e-12)
+    phi, _ = O.exact_potential(pos, types, p)
+    F = O.gather_forces(pos, Q, phi, L, N, 4)
+    Ft = O.gather_forces_tilde(pos, Q, phi, L, N, 4)
+    assert np.abs(F.sum(0)).max() < 1e-12
+    assert np.abs(Ft.sum(0)).max() > 1e-6
+    # F~ is exactly minus the gradient of the discrete energy 1/2 phi^T q,
+    # self-energy included (that is where its noise comes from)
+    eps = 1e-5
+    for a, c in ((0, 0), (3, 2), (5, 1)):
+        e = []
+        for sgn in (1, -1):
+            pp = pos.copy(); pp[a, c] += sgn * eps
+            ph, q = O.exact_potential(pp, types, p)
+            e.append(O.discrete_energy(q, ph))
+        fd = -(e[0] - e[1]) / (2 * eps)
+        assert abs(fd - Ft[a, c]) < 1e-5 * max(1.0, abs(Ft[a, c]))
+
+
+def test_tf_force_is_minus_gradient():
+    tf = synth.tosi_fumi_nacl()
+    L = 12.0
+    pos, types = synth.random_neutral(6, L, 3, min_dist=2.2)
+    F, V = O.tf_forces(pos, types, L, tf, 6.0)
+    assert np.abs(F.sum(0)).max() < 1e-10
+    eps = 1e-6
+    for a in range(3):
+        for c in range(3):
+            pp = pos.copy(); pp[a, c] += eps
+            pm = pos.copy(); pm[a, c] -= eps
+            fd = -(O.tf_forces(pp, types, L, tf, 6.0)[1] - O.tf_forces(pm, types, L, tf, 6.0)[1]) / (2 * eps)
+            assert abs(fd - F[a, c]) < 1e-6 * max(1.0, abs(F[a, c]))
+    np.testing.assert_allclose(O.tf_forces_on([0, 4], pos, types, L, tf, 6.0), F[[0, 4]], atol=1e-12)
+
+
+def test_tf_pair_energy_at_contact():
+    """With the dispersion terms removed, the pair energy at r = s is A."""
+    tf = synth.tosi_fumi_nacl()
+    t0 = synth.TosiFumi(A=tf.A, B=tf.B, s=tf.s, C=(0.0,) * 3, D=(0.0,) * 3)
+    pos = np.array([[1.0, 1.0, 1.0], [1.0 + tf.s[1], 1.0, 1.0]])
+    _, V = O.tf_forces(pos, np.array([0, 1], dtype=np.int32), 20.0, t0, 1e9)
+    assert abs(V - tf.A[1]) < 1e-14
+
+
+def _short_run(n_steps, tol=1e-10, solver="cg", reverse=False):
+    w = synth.workload("nacl64")
+    pos, vel, types = synth.make_state(w)
+    tf = synth.tosi_fumi_nacl()
+    p = O.Params(L=w.L, N=w.N, dt=w.dt, tol=tol, rc=w.rc, solver=solver)
+    rec = []
+    st = O.run(pos, vel, types, p, tf, n_steps, rec)
+    return w, p, tf, rec
+
+
+def test_nve_work_energy_conserved():
+    """P6: with V_work the total energy is conserved far better than its parts
+    fluctuate (the paper reports Delta E / Delta V_work = 2.2e-5 at h = 0.172)."""
+    w, p, tf, rec = _short_run(60)
+    E = np.array([O.energies(s, p)["e_tot"] for s in rec])
+    Vw = np.array([s.V_work for s in rec])
+    KE = np.array([O.kinetic(s, p) for s in rec])
+    assert E.std() / Vw.std() < 2e-4
+    assert E.std() / KE.std() < 2e-3
+    assert all(s.resid < p.tol for s in rec)
+
+
+def test_shake_identity_and_constraint():
+    """P2/P9: after each step the constraint (h/4pi) M phi + q = 0 holds to the
+    solver tolerance, and phi equals the exact discrete potential."""
+    w, p, tf, rec = _short_run(5, tol=1e-12)
+    for s in rec[1:]:
+        Q = np.where(s.types == 0, 1.0, -1.0)
+        q = O.spread(s.pos, Q, p.L, p.N, p.P)
+        sig = (p.h / (4 * np.pi)) * O.apply_M(s.phi) + q
+        assert O.inf_norm(sig) < 2e-12
+        ex, _ = O.exact_potential(s.pos, s.types, p)
+        assert O.inf_norm(s.phi - s.phi.mean() - ex) < 1e-9
+
+
+def test_static_system_needs_no_solver_work():
+    """With ions at rest on the lattice the Verlet proposal phi_p = 2 phi^k -
+    phi^{k-1} already satisfies the constraint, so SHAKE needs 0 iterations."""
+    L, n = 12.6, 4
+    pos, types = synth.rocksalt(n, L, 0.0, np.random.default_rng(0))
+    tf = synth.TosiFumi(A=(0.0,) * 3, B=1.0, s=(0.0,) * 3, C=(0.0,) * 3, D=(0.0,) * 3)
+    p = O.Params(L=L, N=16, dt=1.0, tol=1e-10, rc=6.3)
+    st = O.init(pos, np.zeros_like(pos), types, p, tf)
+    for _ in range(3):
+        st = O.step(st, p, tf)
+        assert st.iters == 0
+
+
+def test_maze_start_beats_static_start():
+    """Sec. III.A.1 / App. B: warm-started SHAKE needs fewer iterations than a
+    direct Poisson solve started from the previous potential."""
+    w, p, tf, rec = _short_run(12, solver="cg")
+    maze_it, static_it = [], []
+    for prev, cur in zip(rec[5:-1], rec[6:]):
+        maze_it.append(cur.iters)
+        Q = np.where(cur.types == 0, 1.0, -1.0)
+        q = O.spread(cur.pos, Q, p.L, p.N, p.P)
+        # direct Poisson M phi = -4 pi q / h from phi^k, same residual units (e)
+        b = q
+        y0 = -(p.h / (4 * np.pi)) * prev.phi
+        _, info = O.plcg(b, y0, p.tol)
+        static_it.append(info.iters)
+    assert np.mean(maze_it) < np.mean(static_it)
+
+
+def test_time_reversibility():
+    """Sec. III.C: run forward, flip the velocities and the phi history, run
+    back; the positions return (tight tolerance)."""
+    w = synth.workload("nacl64")
+    pos, vel, types = synth.make_state(w)
+    tf = synth.tosi_fumi_nacl()
+    p = O.Params(L=w.L, N=w.N, dt=w.dt, tol=1e-12, rc=w.rc)
+    st = O.init(pos, vel, types, p, tf)
+    start = st.pos.copy()
+    for _ in range(20):
+        st = O.step(st, p, tf)
+    st.vel = -st.vel
+    st.phi, st.phi_prev = st.phi_prev, st.phi
+    st.y = np.zeros_like(st.y)
+    for _ in range(20):
+        st = O.step(st, p, tf)
+    d = st.pos - start
+    d -= p.L * np.round(d / p.L)
+    rmsd = np.sqrt((d * d).sum(1)).sum() / (len(d) * p.L)
+    assert rmsd < 1e-8
+
+
+def test_cg_and_mg_agree_on_trajectory():
+    """The two constraint solvers (App. B and Sec. III.A) give the same
+    trajectory to the force tolerance when the constraint is tight."""
+    _, p1, _, r1 = _short_run(10, tol=1e-13, solver="cg")
+    _, p2, _, r2 = _short_run(10, tol=1e-13, solver="mg")
+    for a, b in zip(r1, r2):
+        assert np.abs(a.F - b.F).max() < 1e-10 * np.abs(a.F).max()
