@@ -1,0 +1,309 @@
+"""Benchmark of the GB300 Poisson MaZe step (one JSON line on rank 0).
+
+A step is one full MaZe MD step (S1-S9) of one synthetic molten-NaCl box.
+Default workload: 1000 ions (500 Na+, 500 Cl-), L = 31.5 Angstrom, 32^3 grid,
+1200 K, dt = 1 fs, constraint tolerance 1e-10, cubic B-spline assignment,
+warm-started CG constraint solve, FP64. Inputs are resident in HBM when the
+timed region starts; L2 is flushed (256 MiB write) between timed steps,
+outside the per-step CUDA events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs an independent replica box (weak scaling, no
+collective on the data path); value = steps of all ranks / max rank time.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2505_20418_gb300 import synth  # noqa: E402
+
+METRIC = "MaZe steps/s, solve GB/s vs HBM peak, p50/p99 step latency at stated force error"
+KERNELS_PER_STEP_CELLS = 6    # ion update, 3 cell-list kernels, solve, forces
+KERNELS_PER_STEP_NOCELLS = 3
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d["hbm_gbs"], "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            except Exception:
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def solve_bytes_per_launch(ng, iters, confirms=1):
+    """Algorithmic DRAM bytes of one solve launch (FP64, 8 B per value):
+    S4 pass 56 B/pt (read phi^k, phi^{k-1}, q, y; write phi_p, sigma_p, r),
+    64 B/pt per CG iteration (read r, p, write p; read p, y, r, write y, r),
+    24 B/pt per true-residual check (read y, sigma_p, write r),
+    32 B/pt correction (read phi_p, y, write phi, y)."""
+    return ng * (56 + 64 * iters + 24 * confirms + 32)
+
+
+def run_cpu_baseline(w, budget_s=15.0):
+    """The FP64 oracle as it stands, on a bounded sample of the same workload."""
+    import oracle as O
+    pos, vel, types = synth.make_state(w)
+    tf = synth.tosi_fumi_nacl()
+    p = O.Params(L=w.L, N=w.N, dt=w.dt, tol=w.tol, rc=w.rc, P=w.order)
+    st = O.init(pos, vel, types, p, tf)
+    n = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        st = O.step(st, p, tf)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} MD steps of the same {w.n_ions}-ion {w.N}^3 box from its initial state, "
+                      f"numpy FP64, single thread ({dt:.1f} s)"}
+
+
+def bench_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import oracle as O
+    pos, vel, types = synth.make_state(w)
+    tf = synth.tosi_fumi_nacl()
+    p = O.Params(L=w.L, N=w.N, dt=w.dt, tol=w.tol, rc=w.rc, P=w.order)
+    st = O.init(pos, vel, types, p, tf)
+    for _ in range(args.warmup):
+        st = O.step(st, p, tf)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        st = O.step(st, p, tf)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    val = args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(w, args),
+            "p50_us": 1e6 * float(np.percentile(times, 50)), "p99_us": 1e6 * float(np.percentile(times, 99)),
+            "cpu_baseline": {"value": val, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} timed MD steps after {args.warmup} warm-up steps of the "
+                                       f"{w.n_ions}-ion {w.N}^3 box, numpy FP64, one host thread"},
+            "e2e": {"value": val, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(w, args):
+    return {"workload": f"molten NaCl {w.n_ions} ions, L={w.L} A, {w.N}^3 grid, {w.T:.0f} K, dt={w.dt} fs, "
+                        f"tol={w.tol:g}, P={w.order}, r_cut={w.rc} A",
+            "n_ions": w.n_ions, "grid": w.N, "solver": args.solver, "precision": "fp64",
+            "l2": "flushed between timed steps (256 MiB write outside the step events)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="nacl1000", choices=["nacl64", "nacl1000", "nacl512000"])
+    ap.add_argument("--solver", default="cg", choices=["cg"])
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    w = synth.workload(args.workload)
+    if args.impl == "reference":
+        return bench_reference(args, w)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2505_20418_gb300 import maze as M
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    M.load()
+
+    # every rank advances its own replica (independent seed)
+    w.seed = w.seed + rank
+    pos, vel, types = synth.make_state(w)
+    tf = synth.tosi_fumi_nacl()
+    stream = torch.cuda.Stream(device=dev)
+    sim = M.MazeSim(pos, vel, types, w.L, w.N, tf, r_cut=w.rc, dt=w.dt, tol=w.tol, order=w.order,
+                    stream=stream.cuda_stream)
+    sim.set_timing(True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    s0 = sim.stats()
+    for _ in range(args.warmup):
+        sim.step_async(1)
+    torch.cuda.synchronize()
+    s1 = sim.stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    solve_ms = []
+    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    it_before = s1["total_iters"]
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            ev[k][0].record(stream)
+            sim.step_async(1)
+            ev[k][1].record(stream)
+        solve_ms.append(sim.timing()[2])     # synchronises: reads the in-graph phase events
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+        dist.barrier()
+    clk = clocks.stop()
+    s2 = sim.stats()
+    if s2["status"] != 0:
+        raise RuntimeError(f"step failed: {s2}")
+    iters = (s2["total_iters"] - it_before) / args.steps
+
+    # force error at the stated tolerance: GPU forces vs the oracle's exact
+    # discrete solution on the GPU's final positions (rank 0, not timed)
+    ferr = None
+    if rank == 0:
+        import oracle as O
+        x = sim.get(M.MAZE_POS)
+        F = sim.get(M.MAZE_FORCE)
+        p = O.Params(L=w.L, N=w.N, dt=w.dt, tol=w.tol, rc=w.rc, P=w.order)
+        phi_ex, _ = O.exact_potential(x, types, p)
+        Q = np.where(types == 0, 1.0, -1.0)
+        Fo = O.gather_forces(x, Q, phi_ex, w.L, w.N, w.order) + O.tf_forces(x, types, w.L, tf, w.rc)[0]
+        nrm = np.linalg.norm(Fo, axis=1)
+        ferr = float((np.linalg.norm(F - Fo, axis=1) / np.maximum(nrm, np.sqrt((nrm ** 2).mean()))).max())
+
+    # end to end through the C ABI with host buffers: per step upload the ion
+    # state from pinned host memory, run the step, read back positions + stats
+    e2e = None
+    if not args.no_e2e:
+        hp = torch.empty((w.n_ions, 3), dtype=torch.float64).pin_memory()
+        hv = torch.empty((w.n_ions, 3), dtype=torch.float64).pin_memory()
+        hp.copy_(torch.from_numpy(sim.get(M.MAZE_POS)))
+        hv.copy_(torch.from_numpy(sim.get(M.MAZE_VEL)))
+        hpn, hvn = hp.numpy(), hv.numpy()
+        n_e2e = min(args.steps, 100)
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            sim.set(M.MAZE_POS, hpn)
+            sim.set(M.MAZE_VEL, hvn)
+            sim.step(1)
+            M.maze_get(sim.h, M.MAZE_POS, hpn)
+            M.maze_get(sim.h, M.MAZE_VEL, hvn)
+            sim.stats()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * n_e2e / e2e_s, "unit": "steps/s",
+               "h2d_bytes_per_step": 2 * 24 * w.n_ions,
+               "d2h_bytes_per_step": 2 * 24 * w.n_ions + 104}
+
+    if rank == 0:
+        ng = w.N ** 3
+        bytes_launch = solve_bytes_per_launch(ng, iters)
+        mean_solve_s = statistics.mean(solve_ms) / 1e3
+        achieved = bytes_launch / mean_solve_s / 1e9
+        peak, peak_kind = peaks()
+        cpu = None if args.no_cpu else run_cpu_baseline(w)
+        kps = KERNELS_PER_STEP_CELLS if int(np.floor(w.L / w.rc)) >= 3 else KERNELS_PER_STEP_NOCELLS
+        line = {
+            "metric": METRIC, "value": world * args.steps / total_s, "unit": "steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(w, args),
+            "p50_us": 1e3 * float(np.percentile(step_ms, 50)), "p99_us": 1e3 * float(np.percentile(step_ms, 99)),
+            "iters_per_step": iters, "force_error": ferr,
+            "solve_gbs": achieved, "solve_us": 1e6 * mean_solve_s,
+            "roofline": {"kernel": "k_cg_solve", "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None,
+                         "algorithmic_bytes_per_launch": bytes_launch},
+            "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": kps * args.steps, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,222 @@
+/*
+ * maze.h - C ABI of the GB300 Poisson MaZe hot path (arxiv 2505.20418).
+ *
+ * Poisson MaZe treats the grid values of the electrostatic potential phi as
+ * zero-mass auxiliary degrees of freedom and enforces the discretised Poisson
+ * equation M phi = -4 pi q / h (Sec. II, Eq. linearproblem) as a SHAKE
+ * constraint sigma = (h/4pi) M phi + q = 0 (Eq. Constraints) at every MD step.
+ * One step (Sec. II, Fig. algorithm; Sec. III velocity Verlet):
+ *
+ *   S1 v += dt F / 2m, r += dt v (wrapped)        velocity Verlet, first half
+ *   S3 q_n = sum_a Q_a W(r_a - r_n)               charge assignment, Sec. II.A
+ *   S4 phi_p = 2 phi^k - phi^{k-1},
+ *      sigma_p = (h/4pi) M phi_p + q              Eq. SHAKE
+ *   S5 solve M y = sigma_p from the previous y    Eq. SHAKEy, App. B / Sec. III.A
+ *   S6 phi^{k+1} = phi_p - (4pi/h) y              Eq. SHAKEPhiFinal
+ *   S7 F_a = -k_e Q_a sum_n W(r_a - r_n) D phi_n  Eq. F_nostra
+ *   S8 Tosi-Fumi pair forces within r_cut         Sec. III
+ *   S9 v += dt F / 2m; KE, V_work, 1/2 phi.q      Eq. E_nostra, Eq. energy_discr
+ *
+ * Units: Angstrom, fs, amu, elementary charge e, eV. Energies and forces carry
+ * k_e = e^2 / (4 pi eps0) = 14.3996454784 eV Angstrom (the paper writes
+ * Gaussian units). Grid index n = i + j N + k N^2, x fastest (footnote to
+ * Eq. linearproblem).
+ *
+ * Conventions
+ *  - Every call returns a maze_status; nothing throws across the ABI.
+ *  - A context owns all of its device memory (allocated in maze_create, freed
+ *    in maze_destroy). Host pointers passed in are read only during the call.
+ *  - Work is issued on the context's CUDA stream. Calls that return data to
+ *    the host (maze_get, maze_get_stats, maze_solve, maze_step) synchronise
+ *    that stream before returning.
+ *  - After a failed maze_step see maze_step for what the context holds.
+ *  - The library needs a CUDA device of compute capability 10.3 (sm_103a);
+ *    maze_create fails with MAZE_ERR_CUDA when none is present.
+ *  - maze_last_error returns a message for the last failing call on the
+ *    calling thread (never NULL; empty when there is none).
+ */
+#ifndef MAZE_H
+#define MAZE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MAZE_OK = 0,
+  MAZE_ERR_INVALID = 1,        /* bad argument or configuration */
+  MAZE_ERR_OOM = 2,            /* device allocation failed */
+  MAZE_ERR_NOT_CONVERGED = 3,  /* constraint solve hit max_iter */
+  MAZE_ERR_NONFINITE = 4,      /* NaN or Inf in a residual or energy */
+  MAZE_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up */
+  MAZE_ERR_CUDA = 6            /* CUDA runtime error (message in maze_last_error) */
+} maze_status;
+
+enum { MAZE_SOLVER_CG = 0, MAZE_SOLVER_MG = 1 };
+enum { MAZE_FP64 = 0, MAZE_MIXED = 1 };
+
+/* Physical constants used by the library (CODATA 2018). */
+#define MAZE_KE_EV_ANGSTROM 14.399645478425668  /* e^2/(4 pi eps0) in eV*Angstrom */
+#define MAZE_ACC_UNIT 9.648533212331002e-3      /* 1 eV/(amu*Angstrom) in Angstrom/fs^2 */
+
+/*
+ * Run configuration; everything is host memory and is copied by maze_create.
+ *
+ * n_ions      number of ions N_p (>= 2)
+ * grid_N      grid points per box edge N (even, 8 <= N <= 1024)
+ * box_L       cubic box edge L in Angstrom; grid spacing h = L / N
+ * pos, vel    [n_ions * 3] x,y,z per ion (Angstrom, Angstrom/fs); pos may lie
+ *             outside [0, L) and is wrapped
+ * type        [n_ions] species index, 0 or 1
+ * charge,mass per species (e, amu); the system must be neutral:
+ *             |sum_a Q_a| <= 1e-9 * sum_a |Q_a|
+ * tf_*        Tosi-Fumi pair energy A exp(B (s - r)) - C/r^6 - D/r^8 (Sec. III)
+ *             for pair kinds 0 = (0,0), 1 = (0,1), 2 = (1,1); eV and Angstrom
+ * r_cut       pair cutoff (Angstrom), 0 < r_cut <= L/2; the pair energy is
+ *             shifted to zero at r_cut, forces are truncated
+ * dt          time step (fs)
+ * tol         constraint tolerance: the solve stops when
+ *             max_n |(M y - sigma_p)_n| < tol (Eq. res_poisson_maze), in e
+ * max_iter    iteration cap of one solve (CG iterations or V-cycles)
+ * solver      MAZE_SOLVER_CG (Jacobi-PLCG, App. B) or MAZE_SOLVER_MG (V-cycle,
+ *             Sec. III.A)
+ * mg_pre/post red-black Gauss-Seidel sweeps before/after the coarse correction
+ * order_P     assignment order: 2 (linear B-spline over the 8 nearest points)
+ *             or 4 (cubic B-spline over 4^3 points), Sec. II.A
+ * precision   MAZE_FP64, or MAZE_MIXED (FP32 grid arithmetic, FP64 reductions)
+ * cuda_stream cudaStream_t to issue work on; NULL makes the context create
+ *             and own a non-blocking stream
+ */
+typedef struct {
+  int32_t n_ions;
+  int32_t grid_N;
+  double box_L;
+  const double* pos;
+  const double* vel;
+  const int32_t* type;
+  double charge[2];
+  double mass[2];
+  double tf_A[3];
+  double tf_B;
+  double tf_s[3];
+  double tf_C[3];
+  double tf_D[3];
+  double r_cut;
+  double dt;
+  double tol;
+  int32_t max_iter;
+  int32_t solver;
+  int32_t mg_pre;
+  int32_t mg_post;
+  int32_t order_P;
+  int32_t precision;
+  void* cuda_stream;
+} maze_config;
+
+/* Per-step record, filled on the device at the end of every step. */
+typedef struct {
+  int64_t step;        /* completed MD steps since maze_create */
+  int32_t iters;       /* iterations of the last constraint solve */
+  int32_t status;      /* maze_status of the last step */
+  double resid;        /* max_n |(M y - sigma_p)_n| at exit of the last solve */
+  double ke;           /* kinetic energy, eV */
+  double v_tf;         /* Tosi-Fumi energy, eV */
+  double v_work;       /* work electrostatic energy V_work (Eq. E_nostra), eV */
+  double v_disc;       /* discrete energy 1/2 k_e phi^T q (Eq. energy_discr), eV */
+  double e_tot;        /* ke + v_tf + v_work */
+  double momentum[3];  /* sum_a m_a v_a, amu Angstrom / fs */
+  int64_t total_iters; /* solver iterations summed over all steps */
+} maze_stats;
+
+/* Quantities for maze_get / maze_set (layouts in doubles). */
+enum {
+  MAZE_POS = 0,       /* [n_ions*3], x,y,z per ion, in [0, L) */
+  MAZE_VEL = 1,       /* [n_ions*3] */
+  MAZE_FORCE = 2,     /* [n_ions*3] total force F_el + F_tf, eV/Angstrom (get only) */
+  MAZE_FORCE_EL = 3,  /* [n_ions*3] electrostatic force (Eq. F_nostra) (get only) */
+  MAZE_PHI = 4,       /* [N^3] phi^k, e/Angstrom (Gaussian units) */
+  MAZE_PHI_PREV = 5,  /* [N^3] phi^{k-1} */
+  MAZE_Y = 6,         /* [N^3] last SHAKE solution y (warm start of the next solve) */
+  MAZE_CHARGE = 7,    /* [N^3] q on the grid from the last spread, e (get only) */
+  MAZE_SIGMA = 8      /* [N^3] sigma_p of the last solve, e (get only) */
+};
+
+typedef struct maze_ctx maze_ctx;
+
+/* Create a context: validate cfg, allocate device state, upload the ions and
+ * do step 0: spread the charges, solve the constraint from phi = 0 (a zero-mean
+ * phi^0) with an iteration cap of max(max_iter, 20000), set phi^{-1} = phi^0
+ * and y = 0, and compute F^0 and the energies.
+ * On success *out owns the context; on failure *out is NULL. */
+maze_status maze_create(const maze_config* cfg, maze_ctx** out);
+
+/* S3 alone: spread the charges of the current positions onto the grid. */
+maze_status maze_spread(maze_ctx* ctx);
+
+/* S4-S6 alone, on the charges of the last maze_spread: build sigma_p, solve
+ * M y = sigma_p from the stored y, correct phi and rotate phi^{k-1} <- phi^k,
+ * phi^k <- phi^{k+1}. Returns the iteration count and the final residual
+ * max_n |(M y - sigma_p)_n|. Synchronises. MAZE_ERR_NOT_CONVERGED when
+ * max_iter was reached (the state is still updated with the last iterate). */
+maze_status maze_solve(maze_ctx* ctx, int32_t* iters, double* resid_inf);
+
+/* S7 + S8 alone: forces F_el (Eq. F_nostra) and Tosi-Fumi forces on the
+ * current positions from the current phi^k, plus V_TF and 1/2 phi.q. */
+maze_status maze_gather(maze_ctx* ctx);
+
+/* S1..S9 repeated nsteps times (nsteps >= 0). Synchronises and reports the
+ * first failing step's status. A step whose solve reaches max_iter still
+ * completes with the last iterate (MAZE_ERR_NOT_CONVERGED) and no later step
+ * of the call runs; after MAZE_ERR_TIMEOUT or MAZE_ERR_NONFINITE the context
+ * state is undefined and it should be destroyed. */
+maze_status maze_step(maze_ctx* ctx, int32_t nsteps);
+
+/* As maze_step, but only enqueues the steps on the context's stream and
+ * returns without synchronising; device-side failures surface in the next
+ * maze_get_stats (field status) or maze_step. */
+maze_status maze_step_async(maze_ctx* ctx, int32_t nsteps);
+
+/* Copy a quantity (MAZE_POS ...) to host memory of the documented size. */
+maze_status maze_get(maze_ctx* ctx, int32_t what, double* host_out);
+
+/* Overwrite a quantity (MAZE_POS, MAZE_VEL, MAZE_PHI, MAZE_PHI_PREV, MAZE_Y)
+ * from host memory. Setting MAZE_POS wraps the positions into [0, L); the
+ * forces are not recomputed (call maze_gather). */
+maze_status maze_set(maze_ctx* ctx, int32_t what, const double* host_in);
+
+/* Copy the per-step record to *out. Synchronises. */
+maze_status maze_get_stats(maze_ctx* ctx, maze_stats* out);
+
+/* Checkpoint: the full dynamical state (step, V_work, positions, velocities,
+ * forces, phi^k, phi^{k-1}, y) as an opaque blob. With blob == NULL,
+ * maze_get_state stores the needed size in *n. Restoring a blob from a
+ * context of the same configuration resumes bit-identically. */
+maze_status maze_get_state(maze_ctx* ctx, void* blob, size_t* n);
+maze_status maze_set_state(maze_ctx* ctx, const void* blob, size_t n);
+
+/* Free everything the context owns. NULL-safe. */
+void maze_destroy(maze_ctx* ctx);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* maze_last_error(void);
+
+/* Device timing of the phases of the most recent maze_step / maze_step_async
+ * step, in milliseconds, measured with CUDA events on the context's stream:
+ * out[0] half kick + drift + spread, out[1] cell list, out[2] constraint
+ * solve (S4-S6), out[3] forces + second half kick. maze_set_timing(ctx, 1)
+ * makes every step record these events (a small cost); maze_get_timing
+ * synchronises and fails with MAZE_ERR_INVALID while timing is off. */
+maze_status maze_set_timing(maze_ctx* ctx, int32_t on);
+maze_status maze_get_timing(maze_ctx* ctx, double* out4);
+
+/* Library version string, e.g. "maze-gb300 0.1". */
+const char* maze_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MAZE_H */

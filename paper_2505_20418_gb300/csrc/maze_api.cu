@@ -1,0 +1,727 @@
+// C ABI of libmaze: context lifetime, configuration checks, the order of the
+// kernels in one MaZe step, CUDA-graph replay of the step, host transfers and
+// checkpoints. See include/maze.h for the contract of each entry point.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "maze_internal.cuh"
+
+using namespace maze;
+
+namespace {
+
+thread_local std::string g_err;
+
+maze_status fail(maze_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) {                                                                  \
+      return fail(e_ == cudaErrorMemoryAllocation ? MAZE_ERR_OOM : MAZE_ERR_CUDA,             \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+    }                                                                                         \
+  } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr uint64_t kBlobMagic = 0x4d415a4530314250ull;  // "MAZE01BP"
+
+}  // namespace
+
+struct maze_ctx {
+  maze_config cfg;
+  int n = 0, N = 0, P = 4;
+  size_t ng = 0;
+  double L = 0, h = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  // ions, SoA [3][n]
+  double *pos = nullptr, *vel = nullptr, *force = nullptr, *force_el = nullptr;
+  int* type = nullptr;
+  float4* pos32 = nullptr;
+  // grid
+  unsigned long long* qfix = nullptr;
+  double* qd = nullptr;
+  double* phi[3] = {nullptr, nullptr, nullptr};
+  int ik = 0;  // phi^k is phi[ik], phi^{k-1} phi[(ik+1)%3], scratch phi[(ik+2)%3]
+  double *sigma = nullptr, *y = nullptr, *r = nullptr, *p = nullptr, *Mp = nullptr;
+  double* spart = nullptr;
+  unsigned* bar = nullptr;
+  int sblocks = 0;
+  // cells
+  int nc = 0, ncell = 0;
+  int *cell_of = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cursor = nullptr, *cell_ions = nullptr;
+  // force reductions
+  double* fpart = nullptr;
+  unsigned* ticket = nullptr;
+  int fblocks = 0;
+  maze_stats* rec = nullptr;       // device
+  maze_stats* rec_host = nullptr;  // pinned
+  cudaGraphExec_t graph[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  bool graphs_tried[2] = {false, false}, graphs_ok[2] = {false, false};
+  int timing = 0;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int max_iter_init = 20000;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+template <typename T>
+maze_status dalloc(maze_ctx* c, T** p, size_t count) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, count * sizeof(T) + 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MAZE_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  c->allocs.push_back(v);
+  *p = static_cast<T*>(v);
+  return MAZE_OK;
+}
+
+maze_status validate(const maze_config* c) {
+  if (!c) return fail(MAZE_ERR_INVALID, "config is NULL");
+  if (c->n_ions < 2) return fail(MAZE_ERR_INVALID, "n_ions must be >= 2");
+  if (c->grid_N < 8 || c->grid_N > 1024 || c->grid_N % 2)
+    return fail(MAZE_ERR_INVALID, "grid_N must be even and in [8, 1024]");
+  if (!(c->box_L > 0) || !isfinite(c->box_L)) return fail(MAZE_ERR_INVALID, "box_L must be > 0");
+  if (!(c->r_cut > 0) || c->r_cut > 0.5 * c->box_L * (1 + 1e-12))
+    return fail(MAZE_ERR_INVALID, "r_cut must be in (0, L/2]");
+  if (!(c->dt > 0)) return fail(MAZE_ERR_INVALID, "dt must be > 0");
+  if (!(c->tol > 0)) return fail(MAZE_ERR_INVALID, "tol must be > 0");
+  if (c->max_iter < 1) return fail(MAZE_ERR_INVALID, "max_iter must be >= 1");
+  if (c->solver != MAZE_SOLVER_CG) return fail(MAZE_ERR_INVALID, "solver: only MAZE_SOLVER_CG is available in this build");
+  if (c->order_P != 2 && c->order_P != 4) return fail(MAZE_ERR_INVALID, "order_P must be 2 or 4");
+  if (c->precision != MAZE_FP64) return fail(MAZE_ERR_INVALID, "precision: only MAZE_FP64 is available in this build");
+  if (!c->pos || !c->vel || !c->type) return fail(MAZE_ERR_INVALID, "pos, vel and type must be non-NULL");
+  if (!(c->mass[0] > 0) || !(c->mass[1] > 0)) return fail(MAZE_ERR_INVALID, "masses must be > 0");
+  double qsum = 0, qabs = 0;
+  for (int i = 0; i < c->n_ions; ++i) {
+    const int t = c->type[i];
+    if (t != 0 && t != 1) return fail(MAZE_ERR_INVALID, "type must be 0 or 1");
+    qsum += c->charge[t];
+    qabs += fabs(c->charge[t]);
+    for (int d = 0; d < 3; ++d)
+      if (!isfinite(c->pos[3 * i + d]) || !isfinite(c->vel[3 * i + d]))
+        return fail(MAZE_ERR_INVALID, "non-finite position or velocity");
+  }
+  if (fabs(qsum) > 1e-9 * qabs) return fail(MAZE_ERR_INVALID, "the system must be charge neutral");
+  return MAZE_OK;
+}
+
+double wrap_host(double x, double L) {
+  x -= L * floor(x / L);
+  if (x >= L) x -= L;
+  return x;
+}
+
+// --- argument blocks for the current rotation ------------------------------
+
+IonArgs ion_args(maze_ctx* c, int do_move, int do_spread) {
+  IonArgs a;
+  a.n = c->n;
+  a.L = c->L;
+  a.h = c->h;
+  a.N = c->N;
+  a.P = c->P;
+  a.pos = c->pos;
+  a.vel = c->vel;
+  a.force = c->force;
+  a.type = c->type;
+  a.pos32 = c->pos32;
+  a.qfix = do_spread ? c->qfix : nullptr;
+  a.cell_of = c->cell_of;
+  a.cell_count = c->cell_count;
+  a.nc = c->nc;
+  a.charge0 = c->cfg.charge[0];
+  a.charge1 = c->cfg.charge[1];
+  a.kick0 = 0.5 * c->cfg.dt * MAZE_ACC_UNIT / c->cfg.mass[0];
+  a.kick1 = 0.5 * c->cfg.dt * MAZE_ACC_UNIT / c->cfg.mass[1];
+  a.dt = c->cfg.dt;
+  a.do_move = do_move;
+  a.rec = c->rec;
+  return a;
+}
+
+CellArgs cell_args(maze_ctx* c) {
+  CellArgs a;
+  a.n = c->n;
+  a.ncell = c->ncell;
+  a.cell_of = c->cell_of;
+  a.cell_count = c->cell_count;
+  a.cell_start = c->cell_start;
+  a.cursor = c->cursor;
+  a.cell_ions = c->cell_ions;
+  a.rec = c->rec;
+  return a;
+}
+
+ForceArgs force_args(maze_ctx* c, const double* phi, int do_kick, int count_step) {
+  ForceArgs a;
+  const maze_config& g = c->cfg;
+  a.n = c->n;
+  a.L = c->L;
+  a.h = c->h;
+  a.N = c->N;
+  a.P = c->P;
+  a.pos = c->pos;
+  a.vel = c->vel;
+  a.force = c->force;
+  a.force_el = c->force_el;
+  a.pos32 = c->pos32;
+  a.type = c->type;
+  a.phi = phi;
+  a.nc = c->nc;
+  a.cell_start = c->cell_start;
+  a.cell_ions = c->cell_ions;
+  a.cell_of = c->cell_of;
+  a.charge0 = g.charge[0];
+  a.charge1 = g.charge[1];
+  a.mass0 = g.mass[0];
+  a.mass1 = g.mass[1];
+  a.kick0 = 0.5 * g.dt * MAZE_ACC_UNIT / g.mass[0];
+  a.kick1 = 0.5 * g.dt * MAZE_ACC_UNIT / g.mass[1];
+  a.dt = g.dt;
+  a.ke_coef = 0.5 / MAZE_ACC_UNIT;
+  const double rc = g.r_cut;
+  for (int k = 0; k < 3; ++k) {
+    a.A[k] = g.tf_A[k];
+    a.s[k] = g.tf_s[k];
+    a.C[k] = g.tf_C[k];
+    a.D[k] = g.tf_D[k];
+    a.Vc[k] = g.tf_A[k] * exp(g.tf_B * (g.tf_s[k] - rc)) - g.tf_C[k] / pow(rc, 6) - g.tf_D[k] / pow(rc, 8);
+  }
+  a.B = g.tf_B;
+  a.rc2 = rc * rc;
+  const double rcf = rc + 1e-3 + 1e-6 * c->L;
+  a.rc2_filter = (float)(rcf * rcf);
+  a.Lf = (float)c->L;
+  a.do_kick = do_kick;
+  a.count_step = count_step;
+  a.part = c->fpart;
+  a.ticket = c->ticket;
+  a.rec = c->rec;
+  return a;
+}
+
+SolveArgs solve_args(maze_ctx* c, int zero_phi, double* q_out) {
+  SolveArgs a;
+  a.N = c->N;
+  a.n = (int)c->ng;
+  a.phi_k = c->phi[c->ik];
+  a.phi_km1 = c->phi[(c->ik + 1) % 3];
+  a.phi_out = c->phi[(c->ik + 2) % 3];
+  a.qfix = c->qfix;
+  a.q_out = q_out;
+  a.sigma = c->sigma;
+  a.y = c->y;
+  a.r = c->r;
+  a.p = c->p;
+  a.Mp = c->Mp;
+  a.part = c->spart;
+  a.bar = c->bar;
+  a.rec = c->rec;
+  a.c_sig = c->h / (4.0 * kPi);
+  a.c_phi = 4.0 * kPi / c->h;
+  a.tol = c->cfg.tol;
+  a.max_iter = zero_phi ? c->max_iter_init : c->cfg.max_iter;
+  a.zero_phi = zero_phi;
+  return a;
+}
+
+// --- sequences ------------------------------------------------------------
+
+maze_status enqueue_solve(maze_ctx* c, int zero_phi, double* q_out) {
+  CK(cudaMemsetAsync(c->bar, 0, sizeof(unsigned), c->stream));
+  CK(launch_cg_solve(solve_args(c, zero_phi, q_out), c->sblocks, c->stream));
+  return MAZE_OK;
+}
+
+maze_status enqueue_cells(maze_ctx* c) {
+  if (c->nc >= 3) CK(launch_cells(cell_args(c), c->stream));
+  return MAZE_OK;
+}
+
+// One MaZe step for the current rotation (does not rotate). With timing on,
+// events bracket the four phases.
+maze_status enqueue_step(maze_ctx* c, int timed) {
+  if (timed) CK(cudaEventRecord(c->ev[0], c->stream));
+  CK(launch_ion_update(ion_args(c, 1, 1), c->stream));
+  if (timed) CK(cudaEventRecord(c->ev[1], c->stream));
+  maze_status s = enqueue_cells(c);
+  if (s != MAZE_OK) return s;
+  if (timed) CK(cudaEventRecord(c->ev[2], c->stream));
+  s = enqueue_solve(c, 0, nullptr);
+  if (s != MAZE_OK) return s;
+  if (timed) CK(cudaEventRecord(c->ev[3], c->stream));
+  CK(launch_forces(force_args(c, c->phi[(c->ik + 2) % 3], 1, 1), c->fblocks, c->stream));
+  if (timed) CK(cudaEventRecord(c->ev[4], c->stream));
+  return MAZE_OK;
+}
+
+void rotate(maze_ctx* c, int steps) { c->ik = (c->ik + 2 * (steps % 3)) % 3; }
+
+// Capture one step per rotation state (phi^k in phi[0], phi[1], phi[2]);
+// on any capture failure fall back to direct launches.
+maze_status build_graphs(maze_ctx* c, int timed) {
+  c->graphs_tried[timed] = true;
+  const int ik0 = c->ik;
+  for (int g = 0; g < 3; ++g) {
+    c->ik = g;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      c->ik = ik0;
+      return MAZE_OK;
+    }
+    maze_status s = enqueue_step(c, timed);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    if (s != MAZE_OK || e != cudaSuccess || !graph) {
+      cudaGetLastError();
+      if (graph) cudaGraphDestroy(graph);
+      c->ik = ik0;
+      return MAZE_OK;
+    }
+    e = cudaGraphInstantiate(&c->graph[timed][g], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->graph[timed][g] = nullptr;
+      c->ik = ik0;
+      return MAZE_OK;
+    }
+  }
+  c->ik = ik0;
+  c->graphs_ok[timed] = true;
+  return MAZE_OK;
+}
+
+maze_status clear_status(maze_ctx* c) {
+  CK(cudaMemsetAsync(&c->rec->status, 0, sizeof(int32_t), c->stream));
+  return MAZE_OK;
+}
+
+maze_status read_stats(maze_ctx* c) {
+  CK(cudaMemcpyAsync(c->rec_host, c->rec, sizeof(maze_stats), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return MAZE_OK;
+}
+
+maze_status status_message(maze_ctx* c) {
+  const int s = c->rec_host->status;
+  if (s == MAZE_OK) return MAZE_OK;
+  char buf[160];
+  if (s == MAZE_ERR_NOT_CONVERGED)
+    snprintf(buf, sizeof buf, "constraint solve not converged: residual %.3e after %d iterations",
+             c->rec_host->resid, c->rec_host->iters);
+  else if (s == MAZE_ERR_TIMEOUT)
+    snprintf(buf, sizeof buf, "a device-side wait timed out; the context must be destroyed");
+  else if (s == MAZE_ERR_NONFINITE)
+    snprintf(buf, sizeof buf, "non-finite residual or energy");
+  else
+    snprintf(buf, sizeof buf, "device status %d", s);
+  return fail((maze_status)s, buf);
+}
+
+void free_ctx(maze_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (int t = 0; t < 2; ++t)
+    for (int g = 0; g < 3; ++g)
+      if (c->graph[t][g]) cudaGraphExecDestroy(c->graph[t][g]);
+  for (int k = 0; k < 5; ++k)
+    if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->rec_host) cudaFreeHost(c->rec_host);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* maze_last_error(void) { return g_err.c_str(); }
+
+const char* maze_version(void) { return "maze-gb300 0.1"; }
+
+maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
+  if (!out) return fail(MAZE_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  maze_status s = validate(cfg);
+  if (s != MAZE_OK) return s;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, dev));
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(MAZE_ERR_CUDA, "libmaze is built for sm_103a (GB300); this device is sm_" +
+                                   std::to_string(prop.major) + std::to_string(prop.minor));
+  int coop = 0;
+  CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return fail(MAZE_ERR_CUDA, "device does not support cooperative launch");
+
+  maze_ctx* c = new maze_ctx();
+  c->cfg = *cfg;
+  c->cfg.pos = c->cfg.vel = nullptr;
+  c->cfg.type = nullptr;
+  c->n = cfg->n_ions;
+  c->N = cfg->grid_N;
+  c->P = cfg->order_P;
+  c->ng = (size_t)c->N * c->N * c->N;
+  c->L = cfg->box_L;
+  c->h = cfg->box_L / cfg->grid_N;
+  if (cfg->cuda_stream) {
+    c->stream = (cudaStream_t)cfg->cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return fail(MAZE_ERR_CUDA, "cudaStreamCreate failed");
+    }
+    c->own_stream = true;
+  }
+  const int n = c->n;
+  const size_t ng = c->ng;
+  c->nc = (int)floor(c->L / cfg->r_cut);
+  if (c->nc < 3) c->nc = 0;
+  c->ncell = c->nc * c->nc * c->nc;
+  c->sblocks = solve_blocks((int)ng);
+  c->fblocks = force_blocks(n);
+#define AL(p, cnt)                          \
+  do {                                      \
+    maze_status s_ = dalloc(c, &(p), (cnt)); \
+    if (s_ != MAZE_OK) {                    \
+      free_ctx(c);                          \
+      return s_;                            \
+    }                                       \
+  } while (0)
+  AL(c->pos, 3 * (size_t)n);
+  AL(c->vel, 3 * (size_t)n);
+  AL(c->force, 3 * (size_t)n);
+  AL(c->force_el, 3 * (size_t)n);
+  AL(c->type, (size_t)n);
+  AL(c->pos32, (size_t)n);
+  AL(c->qfix, ng);
+  AL(c->qd, ng);
+  for (int g = 0; g < 3; ++g) AL(c->phi[g], ng);
+  AL(c->sigma, ng);
+  AL(c->y, ng);
+  AL(c->r, ng);
+  AL(c->p, ng);
+  AL(c->Mp, ng);
+  AL(c->spart, 2 * (size_t)c->sblocks * 4);
+  AL(c->bar, 4);
+  AL(c->cell_of, (size_t)n);
+  if (c->nc >= 3) {
+    AL(c->cell_count, (size_t)c->ncell);
+    AL(c->cell_start, (size_t)c->ncell + 1);
+    AL(c->cursor, (size_t)c->ncell);
+    AL(c->cell_ions, (size_t)n);
+  }
+  AL(c->fpart, (size_t)c->fblocks * 8);
+  AL(c->ticket, 4);
+  AL(c->rec, 1);
+#undef AL
+  if (cudaMallocHost(&c->rec_host, sizeof(maze_stats)) != cudaSuccess) {
+    free_ctx(c);
+    return fail(MAZE_ERR_OOM, "cudaMallocHost failed");
+  }
+  // upload (AoS host -> SoA device)
+  std::vector<double> tmp(3 * (size_t)n);
+  for (int d = 0; d < 3; ++d)
+    for (int i = 0; i < n; ++i) tmp[(size_t)d * n + i] = wrap_host(cfg->pos[3 * i + d], c->L);
+  cudaStream_t st = c->stream;
+#define CKC(call)                                                          \
+  do {                                                                     \
+    cudaError_t e_ = (call);                                               \
+    if (e_ != cudaSuccess) {                                               \
+      free_ctx(c);                                                         \
+      return fail(MAZE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    }                                                                      \
+  } while (0)
+  CKC(cudaMemcpyAsync(c->pos, tmp.data(), tmp.size() * 8, cudaMemcpyHostToDevice, st));
+  CKC(cudaStreamSynchronize(st));
+  for (int d = 0; d < 3; ++d)
+    for (int i = 0; i < n; ++i) tmp[(size_t)d * n + i] = cfg->vel[3 * i + d];
+  CKC(cudaMemcpyAsync(c->vel, tmp.data(), tmp.size() * 8, cudaMemcpyHostToDevice, st));
+  CKC(cudaMemcpyAsync(c->type, cfg->type, (size_t)n * 4, cudaMemcpyHostToDevice, st));
+  CKC(cudaMemsetAsync(c->force, 0, 3 * (size_t)n * 8, st));
+  CKC(cudaMemsetAsync(c->force_el, 0, 3 * (size_t)n * 8, st));
+  CKC(cudaMemsetAsync(c->qfix, 0, ng * 8, st));
+  CKC(cudaMemsetAsync(c->y, 0, ng * 8, st));
+  CKC(cudaMemsetAsync(c->phi[0], 0, ng * 8, st));
+  CKC(cudaMemsetAsync(c->phi[1], 0, ng * 8, st));
+  CKC(cudaMemsetAsync(c->phi[2], 0, ng * 8, st));
+  CKC(cudaMemsetAsync(c->rec, 0, sizeof(maze_stats), st));
+  CKC(cudaMemsetAsync(c->ticket, 0, 4, st));
+  if (c->nc >= 3) CKC(cudaMemsetAsync(c->cell_count, 0, (size_t)c->ncell * 4, st));
+  CKC(cudaStreamSynchronize(st));
+#undef CKC
+  // step 0: spread, solve M y = q from zero, phi^0 = -(4pi/h)(y - mean y),
+  // phi^{-1} = phi^0, y = 0, forces F^0 and energies
+  c->ik = 1;  // solve writes phi[(ik+2)%3] = phi[0]
+  s = MAZE_OK;
+  auto run = [&]() -> maze_status {
+    CK(launch_ion_update(ion_args(c, 0, 1), st));
+    maze_status r = enqueue_cells(c);
+    if (r != MAZE_OK) return r;
+    r = enqueue_solve(c, 1, c->qd);
+    if (r != MAZE_OK) return r;
+    c->ik = 0;
+    CK(cudaMemcpyAsync(c->phi[1], c->phi[0], ng * 8, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemsetAsync(c->y, 0, ng * 8, st));
+    CK(launch_forces(force_args(c, c->phi[0], 0, 0), c->fblocks, st));
+    r = read_stats(c);
+    if (r != MAZE_OK) return r;
+    return status_message(c);
+  };
+  s = run();
+  if (s != MAZE_OK) {
+    std::string keep = g_err;
+    free_ctx(c);
+    g_err = keep;
+    return s;
+  }
+  *out = c;
+  return MAZE_OK;
+}
+
+void maze_destroy(maze_ctx* ctx) { free_ctx(ctx); }
+
+maze_status maze_spread(maze_ctx* c) {
+  if (!c) return fail(MAZE_ERR_INVALID, "ctx is NULL");
+  maze_status s = clear_status(c);
+  if (s != MAZE_OK) return s;
+  CK(cudaMemsetAsync(c->qfix, 0, c->ng * 8, c->stream));
+  CK(launch_ion_update(ion_args(c, 0, 1), c->stream));
+  s = enqueue_cells(c);
+  if (s != MAZE_OK) return s;
+  CK(launch_q_to_double(c->qfix, c->qd, (int)c->ng, c->stream));
+  return MAZE_OK;
+}
+
+maze_status maze_solve(maze_ctx* c, int32_t* iters, double* resid) {
+  if (!c) return fail(MAZE_ERR_INVALID, "ctx is NULL");
+  maze_status s = clear_status(c);
+  if (s != MAZE_OK) return s;
+  s = enqueue_solve(c, 0, c->qd);
+  if (s != MAZE_OK) return s;
+  rotate(c, 1);
+  s = read_stats(c);
+  if (s != MAZE_OK) return s;
+  if (iters) *iters = c->rec_host->iters;
+  if (resid) *resid = c->rec_host->resid;
+  return status_message(c);
+}
+
+maze_status maze_gather(maze_ctx* c) {
+  if (!c) return fail(MAZE_ERR_INVALID, "ctx is NULL");
+  maze_status s = clear_status(c);
+  if (s != MAZE_OK) return s;
+  CK(launch_ion_update(ion_args(c, 0, 0), c->stream));
+  s = enqueue_cells(c);
+  if (s != MAZE_OK) return s;
+  CK(launch_forces(force_args(c, c->phi[c->ik], 0, 0), c->fblocks, c->stream));
+  s = read_stats(c);
+  if (s != MAZE_OK) return s;
+  return status_message(c);
+}
+
+maze_status maze_step_async(maze_ctx* c, int32_t nsteps) {
+  if (!c) return fail(MAZE_ERR_INVALID, "ctx is NULL");
+  if (nsteps < 0) return fail(MAZE_ERR_INVALID, "nsteps must be >= 0");
+  const int t = c->timing;
+  if (!c->graphs_tried[t]) {
+    maze_status s = build_graphs(c, t);
+    if (s != MAZE_OK) return s;
+  }
+  for (int k = 0; k < nsteps; ++k) {
+    if (c->graphs_ok[t]) {
+      CK(cudaGraphLaunch(c->graph[t][c->ik], c->stream));
+    } else {
+      maze_status s = enqueue_step(c, t);
+      if (s != MAZE_OK) return s;
+    }
+    rotate(c, 1);
+  }
+  return MAZE_OK;
+}
+
+maze_status maze_step(maze_ctx* c, int32_t nsteps) {
+  if (!c) return fail(MAZE_ERR_INVALID, "ctx is NULL");
+  maze_status s = read_stats(c);
+  if (s != MAZE_OK) return s;
+  const int64_t before = c->rec_host->step;
+  s = clear_status(c);
+  if (s != MAZE_OK) return s;
+  const int ik0 = c->ik;
+  s = maze_step_async(c, nsteps);
+  if (s != MAZE_OK) return s;
+  s = read_stats(c);
+  if (s != MAZE_OK) return s;
+  if (c->rec_host->status != MAZE_OK) {
+    // later steps were skipped on the device: put the rotation where the
+    // last completed step left it
+    const int64_t done = c->rec_host->step - before;
+    c->ik = (int)((ik0 + 2 * (done % 3)) % 3);
+  }
+  return status_message(c);
+}
+
+maze_status maze_set_timing(maze_ctx* c, int32_t on) {
+  if (!c) return fail(MAZE_ERR_INVALID, "ctx is NULL");
+  if (on && !c->ev[0])
+    for (int k = 0; k < 5; ++k) CK(cudaEventCreate(&c->ev[k]));
+  c->timing = on ? 1 : 0;
+  return MAZE_OK;
+}
+
+maze_status maze_get_timing(maze_ctx* c, double* out) {
+  if (!c || !out) return fail(MAZE_ERR_INVALID, "NULL argument");
+  if (!c->timing) return fail(MAZE_ERR_INVALID, "timing is off (maze_set_timing)");
+  CK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < 4; ++k) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]));
+    out[k] = ms;
+  }
+  return MAZE_OK;
+}
+
+maze_status maze_get_stats(maze_ctx* c, maze_stats* out) {
+  if (!c || !out) return fail(MAZE_ERR_INVALID, "NULL argument");
+  maze_status s = read_stats(c);
+  if (s != MAZE_OK) return s;
+  *out = *c->rec_host;
+  return MAZE_OK;
+}
+
+maze_status maze_get(maze_ctx* c, int32_t what, double* out) {
+  if (!c || !out) return fail(MAZE_ERR_INVALID, "NULL argument");
+  const double* src = nullptr;
+  bool ion = false;
+  switch (what) {
+    case MAZE_POS: src = c->pos; ion = true; break;
+    case MAZE_VEL: src = c->vel; ion = true; break;
+    case MAZE_FORCE: src = c->force; ion = true; break;
+    case MAZE_FORCE_EL: src = c->force_el; ion = true; break;
+    case MAZE_PHI: src = c->phi[c->ik]; break;
+    case MAZE_PHI_PREV: src = c->phi[(c->ik + 1) % 3]; break;
+    case MAZE_Y: src = c->y; break;
+    case MAZE_CHARGE: src = c->qd; break;
+    case MAZE_SIGMA: src = c->sigma; break;
+    default: return fail(MAZE_ERR_INVALID, "unknown quantity");
+  }
+  if (ion) {
+    const int n = c->n;
+    std::vector<double> tmp(3 * (size_t)n);
+    CK(cudaMemcpyAsync(tmp.data(), src, tmp.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int d = 0; d < 3; ++d)
+      for (int i = 0; i < n; ++i) out[3 * i + d] = tmp[(size_t)d * n + i];
+  } else {
+    CK(cudaMemcpyAsync(out, src, c->ng * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return MAZE_OK;
+}
+
+maze_status maze_set(maze_ctx* c, int32_t what, const double* in) {
+  if (!c || !in) return fail(MAZE_ERR_INVALID, "NULL argument");
+  double* dst = nullptr;
+  bool ion = false;
+  switch (what) {
+    case MAZE_POS: dst = c->pos; ion = true; break;
+    case MAZE_VEL: dst = c->vel; ion = true; break;
+    case MAZE_PHI: dst = c->phi[c->ik]; break;
+    case MAZE_PHI_PREV: dst = c->phi[(c->ik + 1) % 3]; break;
+    case MAZE_Y: dst = c->y; break;
+    default: return fail(MAZE_ERR_INVALID, "quantity cannot be set");
+  }
+  if (ion) {
+    const int n = c->n;
+    std::vector<double> tmp(3 * (size_t)n);
+    for (int d = 0; d < 3; ++d)
+      for (int i = 0; i < n; ++i) {
+        const double v = in[3 * i + d];
+        if (!isfinite(v)) return fail(MAZE_ERR_INVALID, "non-finite input");
+        tmp[(size_t)d * n + i] = what == MAZE_POS ? wrap_host(v, c->L) : v;
+      }
+    CK(cudaMemcpyAsync(dst, tmp.data(), tmp.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  } else {
+    CK(cudaMemcpyAsync(dst, in, c->ng * 8, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return MAZE_OK;
+}
+
+// Blob layout: header (magic, n, N, step, total_iters) + V_work, then
+// pos, vel, force, force_el ([3][n] each), phi^k, phi^{k-1}, y ([N^3] each).
+maze_status maze_get_state(maze_ctx* c, void* blob, size_t* nbytes) {
+  if (!c || !nbytes) return fail(MAZE_ERR_INVALID, "NULL argument");
+  const size_t ion = 3 * (size_t)c->n * 8, grid = c->ng * 8;
+  const size_t need = 6 * 8 + 4 * ion + 3 * grid;
+  if (!blob) {
+    *nbytes = need;
+    return MAZE_OK;
+  }
+  if (*nbytes < need) return fail(MAZE_ERR_INVALID, "blob too small");
+  maze_status s = read_stats(c);
+  if (s != MAZE_OK) return s;
+  char* b = static_cast<char*>(blob);
+  uint64_t hdr[5] = {kBlobMagic, (uint64_t)c->n, (uint64_t)c->N, (uint64_t)c->rec_host->step,
+                     (uint64_t)c->rec_host->total_iters};
+  memcpy(b, hdr, sizeof hdr);
+  memcpy(b + 40, &c->rec_host->v_work, 8);
+  char* q = b + 48;
+  const double* ions[4] = {c->pos, c->vel, c->force, c->force_el};
+  for (int k = 0; k < 4; ++k, q += ion) CK(cudaMemcpyAsync(q, ions[k], ion, cudaMemcpyDeviceToHost, c->stream));
+  const double* grids[3] = {c->phi[c->ik], c->phi[(c->ik + 1) % 3], c->y};
+  for (int k = 0; k < 3; ++k, q += grid) CK(cudaMemcpyAsync(q, grids[k], grid, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *nbytes = need;
+  return MAZE_OK;
+}
+
+maze_status maze_set_state(maze_ctx* c, const void* blob, size_t nbytes) {
+  if (!c || !blob) return fail(MAZE_ERR_INVALID, "NULL argument");
+  const size_t ion = 3 * (size_t)c->n * 8, grid = c->ng * 8;
+  const size_t need = 6 * 8 + 4 * ion + 3 * grid;
+  if (nbytes != need) return fail(MAZE_ERR_INVALID, "blob size does not match this context");
+  const char* b = static_cast<const char*>(blob);
+  uint64_t hdr[5];
+  memcpy(hdr, b, sizeof hdr);
+  if (hdr[0] != kBlobMagic || hdr[1] != (uint64_t)c->n || hdr[2] != (uint64_t)c->N)
+    return fail(MAZE_ERR_INVALID, "blob does not belong to a context of this shape");
+  double vw;
+  memcpy(&vw, b + 40, 8);
+  c->ik = 0;
+  const char* q = b + 48;
+  double* ions[4] = {c->pos, c->vel, c->force, c->force_el};
+  for (int k = 0; k < 4; ++k, q += ion) CK(cudaMemcpyAsync(ions[k], q, ion, cudaMemcpyHostToDevice, c->stream));
+  double* grids[3] = {c->phi[0], c->phi[1], c->y};
+  for (int k = 0; k < 3; ++k, q += grid) CK(cudaMemcpyAsync(grids[k], q, grid, cudaMemcpyHostToDevice, c->stream));
+  maze_status s = read_stats(c);
+  if (s != MAZE_OK) return s;
+  maze_stats st = *c->rec_host;
+  st.step = (int64_t)hdr[3];
+  st.total_iters = (int64_t)hdr[4];
+  st.v_work = vw;
+  st.status = MAZE_OK;
+  *c->rec_host = st;
+  CK(cudaMemcpyAsync(c->rec, c->rec_host, sizeof(maze_stats), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return MAZE_OK;
+}
+
+}  // extern "C"

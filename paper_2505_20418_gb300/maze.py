@@ -1,0 +1,294 @@
+"""Thin ctypes binding of libmaze (include/maze.h).
+
+Argument marshalling only: every step of the MaZe path runs in the CUDA
+kernels of libmaze.so. The module-level functions carry the C names; the
+:class:`MazeSim` class wraps one context. Loading fails loudly when the
+library has not been built (``python -m paper_2505_20418_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmaze.so")
+
+MAZE_OK, MAZE_ERR_INVALID, MAZE_ERR_OOM, MAZE_ERR_NOT_CONVERGED = 0, 1, 2, 3
+MAZE_ERR_NONFINITE, MAZE_ERR_TIMEOUT, MAZE_ERR_CUDA = 4, 5, 6
+MAZE_SOLVER_CG, MAZE_SOLVER_MG = 0, 1
+MAZE_FP64, MAZE_MIXED = 0, 1
+MAZE_POS, MAZE_VEL, MAZE_FORCE, MAZE_FORCE_EL = 0, 1, 2, 3
+MAZE_PHI, MAZE_PHI_PREV, MAZE_Y, MAZE_CHARGE, MAZE_SIGMA = 4, 5, 6, 7, 8
+
+# every entry point declared in include/maze.h
+EXPORTS = ("maze_create", "maze_spread", "maze_solve", "maze_gather", "maze_step",
+           "maze_step_async", "maze_get", "maze_set", "maze_get_stats", "maze_get_state",
+           "maze_set_state", "maze_destroy", "maze_last_error", "maze_version",
+           "maze_set_timing", "maze_get_timing")
+
+_D = ctypes.c_double
+_I = ctypes.c_int32
+
+
+class MazeConfig(ctypes.Structure):
+    _fields_ = [
+        ("n_ions", _I), ("grid_N", _I), ("box_L", _D),
+        ("pos", ctypes.POINTER(_D)), ("vel", ctypes.POINTER(_D)), ("type", ctypes.POINTER(_I)),
+        ("charge", _D * 2), ("mass", _D * 2),
+        ("tf_A", _D * 3), ("tf_B", _D), ("tf_s", _D * 3), ("tf_C", _D * 3), ("tf_D", _D * 3),
+        ("r_cut", _D), ("dt", _D), ("tol", _D),
+        ("max_iter", _I), ("solver", _I), ("mg_pre", _I), ("mg_post", _I),
+        ("order_P", _I), ("precision", _I), ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class MazeStats(ctypes.Structure):
+    _fields_ = [
+        ("step", ctypes.c_int64), ("iters", _I), ("status", _I), ("resid", _D),
+        ("ke", _D), ("v_tf", _D), ("v_work", _D), ("v_disc", _D), ("e_tot", _D),
+        ("momentum", _D * 3), ("total_iters", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["momentum"] = list(self.momentum)
+        return d
+
+
+class MazeError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"maze status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libmaze.so (cached). Raises if it is missing: there is no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmaze.so not built at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    lib.maze_create.argtypes = [ctypes.POINTER(MazeConfig), ctypes.POINTER(P)]
+    lib.maze_spread.argtypes = [P]
+    lib.maze_solve.argtypes = [P, ctypes.POINTER(_I), ctypes.POINTER(_D)]
+    lib.maze_gather.argtypes = [P]
+    lib.maze_step.argtypes = [P, _I]
+    lib.maze_step_async.argtypes = [P, _I]
+    lib.maze_get.argtypes = [P, _I, ctypes.POINTER(_D)]
+    lib.maze_set.argtypes = [P, _I, ctypes.POINTER(_D)]
+    lib.maze_get_stats.argtypes = [P, ctypes.POINTER(MazeStats)]
+    lib.maze_get_state.argtypes = [P, P, ctypes.POINTER(ctypes.c_size_t)]
+    lib.maze_set_state.argtypes = [P, P, ctypes.c_size_t]
+    lib.maze_set_timing.argtypes = [P, _I]
+    lib.maze_get_timing.argtypes = [P, ctypes.POINTER(_D)]
+    lib.maze_destroy.argtypes = [P]
+    lib.maze_destroy.restype = None
+    lib.maze_last_error.restype = ctypes.c_char_p
+    lib.maze_version.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("maze_destroy", "maze_last_error", "maze_version"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != MAZE_OK:
+        raise MazeError(status, load().maze_last_error().decode())
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(_D))
+
+
+# ---- C-named functions -----------------------------------------------------
+
+def maze_create(cfg: MazeConfig):
+    h = ctypes.c_void_p()
+    _check(load().maze_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def maze_spread(h):
+    _check(load().maze_spread(h))
+
+
+def maze_solve(h):
+    it, res = _I(), _D()
+    st = load().maze_solve(h, ctypes.byref(it), ctypes.byref(res))
+    return st, it.value, res.value
+
+
+def maze_gather(h):
+    _check(load().maze_gather(h))
+
+
+def maze_step(h, nsteps: int):
+    return load().maze_step(h, int(nsteps))
+
+
+def maze_step_async(h, nsteps: int):
+    _check(load().maze_step_async(h, int(nsteps)))
+
+
+def maze_get(h, what: int, out: np.ndarray):
+    _check(load().maze_get(h, what, _dptr(out)))
+    return out
+
+
+def maze_set(h, what: int, arr: np.ndarray):
+    arr = np.ascontiguousarray(arr, dtype=np.float64)
+    _check(load().maze_set(h, what, _dptr(arr)))
+
+
+def maze_get_stats(h) -> MazeStats:
+    s = MazeStats()
+    _check(load().maze_get_stats(h, ctypes.byref(s)))
+    return s
+
+
+def maze_get_state(h) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(load().maze_get_state(h, None, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(load().maze_get_state(h, buf, ctypes.byref(n)))
+    return buf.raw
+
+
+def maze_set_state(h, blob: bytes):
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(load().maze_set_state(h, buf, len(blob)))
+
+
+def maze_set_timing(h, on: bool):
+    _check(load().maze_set_timing(h, int(bool(on))))
+
+
+def maze_get_timing(h):
+    """Phase times (ms) of the last step: spread, cells, solve, forces."""
+    out = np.zeros(4)
+    _check(load().maze_get_timing(h, _dptr(out)))
+    return out
+
+
+def maze_destroy(h):
+    load().maze_destroy(h)
+
+
+def maze_last_error() -> str:
+    return load().maze_last_error().decode()
+
+
+def maze_version() -> str:
+    return load().maze_version().decode()
+
+
+# ---- convenience wrapper ---------------------------------------------------
+
+def make_config(pos, vel, types, L, N, tf, *, r_cut, dt=1.0, tol=1e-10, max_iter=10000,
+                solver=MAZE_SOLVER_CG, order=4, precision=MAZE_FP64, charge=(1.0, -1.0),
+                mass=(22.98977, 35.453), mg_pre=2, mg_post=2, stream=None):
+    """Build a MazeConfig; the returned tuple keeps the host arrays alive."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    vel = np.ascontiguousarray(vel, dtype=np.float64)
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    c = MazeConfig()
+    c.n_ions = pos.shape[0]
+    c.grid_N = int(N)
+    c.box_L = float(L)
+    c.pos = _dptr(pos)
+    c.vel = _dptr(vel)
+    c.type = types.ctypes.data_as(ctypes.POINTER(_I))
+    c.charge[:] = list(charge)
+    c.mass[:] = list(mass)
+    c.tf_A[:] = list(tf.A)
+    c.tf_B = tf.B
+    c.tf_s[:] = list(tf.s)
+    c.tf_C[:] = list(tf.C)
+    c.tf_D[:] = list(tf.D)
+    c.r_cut = float(r_cut)
+    c.dt = float(dt)
+    c.tol = float(tol)
+    c.max_iter = int(max_iter)
+    c.solver = int(solver)
+    c.mg_pre = int(mg_pre)
+    c.mg_post = int(mg_post)
+    c.order_P = int(order)
+    c.precision = int(precision)
+    c.cuda_stream = stream
+    return c, (pos, vel, types)
+
+
+class MazeSim:
+    """One MaZe simulation context on the current CUDA device."""
+
+    def __init__(self, pos, vel, types, L, N, tf, **kw):
+        cfg, keep = make_config(pos, vel, types, L, N, tf, **kw)
+        self.n = cfg.n_ions
+        self.N = int(N)
+        self.h = maze_create(cfg)
+        del keep
+
+    def close(self):
+        if self.h:
+            maze_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ion(self):
+        return np.empty((self.n, 3))
+
+    def _grid(self):
+        return np.empty((self.N, self.N, self.N))
+
+    def get(self, what):
+        out = self._ion() if what <= MAZE_FORCE_EL else self._grid()
+        return maze_get(self.h, what, out)
+
+    def set(self, what, arr):
+        maze_set(self.h, what, arr)
+
+    def step(self, nsteps=1):
+        _check(maze_step(self.h, nsteps))
+
+    def step_async(self, nsteps=1):
+        maze_step_async(self.h, nsteps)
+
+    def spread(self):
+        maze_spread(self.h)
+
+    def solve(self, check=True):
+        st, it, res = maze_solve(self.h)
+        if check:
+            _check(st)
+        return it, res
+
+    def gather(self):
+        maze_gather(self.h)
+
+    def stats(self) -> dict:
+        return maze_get_stats(self.h).as_dict()
+
+    def set_timing(self, on=True):
+        maze_set_timing(self.h, on)
+
+    def timing(self):
+        return maze_get_timing(self.h)
+
+    def get_state(self) -> bytes:
+        return maze_get_state(self.h)
+
+    def set_state(self, blob: bytes):
+        maze_set_state(self.h, blob)
