@@ -60,7 +60,7 @@ enum { MAZE_FP64 = 0, MAZE_MIXED = 1 };
 
 /* Physical constants used by the library (CODATA 2018). */
 #define MAZE_KE_EV_ANGSTROM 14.399645478425668  /* e^2/(4 pi eps0) in eV*Angstrom */
-#define MAZE_ACC_UNIT 9.648533212331002e-3      /* 1 eV/(amu*Angstrom) in Angstrom/fs^2 */
+#define MAZE_ACC_UNIT 9.648533215665327e-3      /* e/u * 1e-20: 1 eV/(amu*Angstrom) in Angstrom/fs^2 */
 
 /*
  * Run configuration; everything is host memory and is copied by maze_create.
@@ -211,6 +211,33 @@ const char* maze_last_error(void);
  * synchronises and fails with MAZE_ERR_INVALID while timing is off. */
 maze_status maze_set_timing(maze_ctx* ctx, int32_t on);
 maze_status maze_get_timing(maze_ctx* ctx, double* out4);
+
+/* Allocation-free constraint solve. The paper has no counterpart: this entry
+ * exists for callers that cannot call cudaMalloc - a host framework that owns
+ * all device memory through its own pool, a latency-critical loop that must
+ * not take cudaMalloc's implicit device synchronisation, or a process held to
+ * a fixed device-memory budget. It solves M y = sigma_p (Eq. SHAKEy) with the
+ * same warm-started CG and stopping rule as maze_solve, then removes the mean
+ * of y.
+ *   grid_N     grid edge N, even, 8 <= N <= 64
+ *   sigma_p    [N^3] device pointer, read only, flat index n = i + jN + kN^2
+ *   y          [N^3] device pointer; in: warm start, out: zero-mean solution
+ *   tol        stop when max_n |(M y - sigma_p)_n| < tol
+ *   max_iter   CG iteration cap
+ *   cuda_stream stream to run on (NULL = legacy default stream); the call
+ *              synchronises it before returning
+ *   iters, resid_inf  optional outputs (host pointers)
+ * It allocates nothing: its work vectors live in one file-scope device array
+ * of about 6.4 MB (3 x 64^3 doubles plus a small status block), which every
+ * GPU that loads the library holds until the process exits. Larger grids are
+ * rejected with MAZE_ERR_INVALID. The first call on a device, with that device
+ * current, resolves the array's device address and the launch size; make that
+ * first call before any stream capture. Every call shares the one array and
+ * keeps the last call's contents in it, so calls that overlap on the GPU (on
+ * different streams or threads) race and must be serialised by the caller. */
+maze_status maze_solve_shake_noalloc(int32_t grid_N, const double* sigma_p, double* y, double tol,
+                                     int32_t max_iter, void* cuda_stream, int32_t* iters,
+                                     double* resid_inf);
 
 /* Library version string, e.g. "maze-gb300 0.1". */
 const char* maze_version(void);

@@ -36,6 +36,8 @@ constexpr uint64_t kBlobMagic = 0x4d415a4530314250ull;  // "MAZE01BP"
 
 }  // namespace
 
+void maze::set_last_error(const char* msg) { g_err = msg; }
+
 struct maze_ctx {
   maze_config cfg;
   int n = 0, N = 0, P = 4;
@@ -64,6 +66,7 @@ struct maze_ctx {
   unsigned* ticket = nullptr;
   int fblocks = 0;
   maze_stats* rec = nullptr;       // device
+  int* gate = nullptr;             // device: current step skipped
   maze_stats* rec_host = nullptr;  // pinned
   cudaGraphExec_t graph[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
   bool graphs_tried[2] = {false, false}, graphs_ok[2] = {false, false};
@@ -149,6 +152,7 @@ IonArgs ion_args(maze_ctx* c, int do_move, int do_spread) {
   a.dt = c->cfg.dt;
   a.do_move = do_move;
   a.rec = c->rec;
+  a.gate = c->gate;
   return a;
 }
 
@@ -210,6 +214,7 @@ ForceArgs force_args(maze_ctx* c, const double* phi, int do_kick, int count_step
   a.part = c->fpart;
   a.ticket = c->ticket;
   a.rec = c->rec;
+  a.gate = c->gate;
   return a;
 }
 
@@ -235,6 +240,7 @@ SolveArgs solve_args(maze_ctx* c, int zero_phi, double* q_out) {
   a.tol = c->cfg.tol;
   a.max_iter = zero_phi ? c->max_iter_init : c->cfg.max_iter;
   a.zero_phi = zero_phi;
+  a.gate = c->gate;
   return a;
 }
 
@@ -254,17 +260,17 @@ maze_status enqueue_cells(maze_ctx* c) {
 // One MaZe step for the current rotation (does not rotate). With timing on,
 // events bracket the four phases.
 maze_status enqueue_step(maze_ctx* c, int timed) {
-  if (timed) CK(cudaEventRecord(c->ev[0], c->stream));
+  if (timed) CK(cudaEventRecordWithFlags(c->ev[0], c->stream, cudaEventRecordExternal));
   CK(launch_ion_update(ion_args(c, 1, 1), c->stream));
-  if (timed) CK(cudaEventRecord(c->ev[1], c->stream));
+  if (timed) CK(cudaEventRecordWithFlags(c->ev[1], c->stream, cudaEventRecordExternal));
   maze_status s = enqueue_cells(c);
   if (s != MAZE_OK) return s;
-  if (timed) CK(cudaEventRecord(c->ev[2], c->stream));
+  if (timed) CK(cudaEventRecordWithFlags(c->ev[2], c->stream, cudaEventRecordExternal));
   s = enqueue_solve(c, 0, nullptr);
   if (s != MAZE_OK) return s;
-  if (timed) CK(cudaEventRecord(c->ev[3], c->stream));
+  if (timed) CK(cudaEventRecordWithFlags(c->ev[3], c->stream, cudaEventRecordExternal));
   CK(launch_forces(force_args(c, c->phi[(c->ik + 2) % 3], 1, 1), c->fblocks, c->stream));
-  if (timed) CK(cudaEventRecord(c->ev[4], c->stream));
+  if (timed) CK(cudaEventRecordWithFlags(c->ev[4], c->stream, cudaEventRecordExternal));
   return MAZE_OK;
 }
 
@@ -430,6 +436,7 @@ maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
   AL(c->fpart, (size_t)c->fblocks * 8);
   AL(c->ticket, 4);
   AL(c->rec, 1);
+  AL(c->gate, 1);
 #undef AL
   if (cudaMallocHost(&c->rec_host, sizeof(maze_stats)) != cudaSuccess) {
     free_ctx(c);
@@ -463,6 +470,7 @@ maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
   CKC(cudaMemsetAsync(c->phi[2], 0, ng * 8, st));
   CKC(cudaMemsetAsync(c->rec, 0, sizeof(maze_stats), st));
   CKC(cudaMemsetAsync(c->ticket, 0, 4, st));
+  CKC(cudaMemsetAsync(c->gate, 0, 4, st));
   if (c->nc >= 3) CKC(cudaMemsetAsync(c->cell_count, 0, (size_t)c->ncell * 4, st));
   CKC(cudaStreamSynchronize(st));
 #undef CKC

@@ -44,6 +44,7 @@ struct IonArgs {
   double dt;
   int do_move;           // 1: half kick + drift before spreading
   maze_stats* rec;
+  int* gate;             // set to 1 when the step starts after an error
 };
 
 struct CellArgs {
@@ -86,6 +87,7 @@ struct ForceArgs {
   double* part;          // [gridDim][8] block partials
   unsigned* ticket;      // last-block ticket (self-resetting)
   maze_stats* rec;
+  const int* gate;       // 1: this step was skipped
 };
 
 struct SolveArgs {
@@ -108,6 +110,7 @@ struct SolveArgs {
   double tol;
   int max_iter;
   int zero_phi;          // step 0: phi^k = phi^{k-1} = 0
+  const int* gate;       // 1: this step was skipped
 };
 
 // Host-side launchers (defined in the .cu files).
@@ -118,6 +121,8 @@ cudaError_t launch_forces(const ForceArgs& a, int blocks, cudaStream_t s);
 int force_blocks(int n_ions);
 cudaError_t launch_cg_solve(const SolveArgs& a, int blocks, cudaStream_t s);
 int solve_blocks(int n_points);
+// Sets the message returned by maze_last_error on the calling thread.
+void set_last_error(const char* msg);
 
 // ---------------------------------------------------------------------------
 // Device helpers

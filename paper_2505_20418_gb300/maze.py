@@ -26,7 +26,7 @@ MAZE_PHI, MAZE_PHI_PREV, MAZE_Y, MAZE_CHARGE, MAZE_SIGMA = 4, 5, 6, 7, 8
 EXPORTS = ("maze_create", "maze_spread", "maze_solve", "maze_gather", "maze_step",
            "maze_step_async", "maze_get", "maze_set", "maze_get_stats", "maze_get_state",
            "maze_set_state", "maze_destroy", "maze_last_error", "maze_version",
-           "maze_set_timing", "maze_get_timing")
+           "maze_set_timing", "maze_get_timing", "maze_solve_shake_noalloc")
 
 _D = ctypes.c_double
 _I = ctypes.c_int32
@@ -88,6 +88,7 @@ def load(path: str = LIB_PATH):
     lib.maze_set_state.argtypes = [P, P, ctypes.c_size_t]
     lib.maze_set_timing.argtypes = [P, _I]
     lib.maze_get_timing.argtypes = [P, ctypes.POINTER(_D)]
+    lib.maze_solve_shake_noalloc.argtypes = [_I, P, P, _D, _I, P, ctypes.POINTER(_I), ctypes.POINTER(_D)]
     lib.maze_destroy.argtypes = [P]
     lib.maze_destroy.restype = None
     lib.maze_last_error.restype = ctypes.c_char_p
@@ -176,6 +177,17 @@ def maze_get_timing(h):
     out = np.zeros(4)
     _check(load().maze_get_timing(h, _dptr(out)))
     return out
+
+
+def maze_solve_shake_noalloc(grid_N: int, sigma_ptr: int, y_ptr: int, tol: float, max_iter: int,
+                             stream: int | None = None):
+    """Allocation-free M y = sigma_p solve on caller-owned device memory
+    (raw device pointers, e.g. ``tensor.data_ptr()``). Returns (status, iters, resid)."""
+    it, res = _I(), _D()
+    st = load().maze_solve_shake_noalloc(int(grid_N), ctypes.c_void_p(sigma_ptr), ctypes.c_void_p(y_ptr),
+                                         float(tol), int(max_iter), ctypes.c_void_p(stream or 0),
+                                         ctypes.byref(it), ctypes.byref(res))
+    return st, it.value, res.value
 
 
 def maze_destroy(h):
