@@ -43,7 +43,10 @@ __device__ __forceinline__ double wrap_pos(double x, double L) {
 
 __global__ void k_ion_update(IonArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n || a.rec->status != MAZE_OK) return;
+  // the first kernel of a step decides, once, whether the step runs at all
+  const bool skip = a.rec->status != MAZE_OK;
+  if (i == 0) *a.gate = skip ? 1 : 0;
+  if (i >= a.n || skip) return;
   double x = a.pos[i], y = a.pos[a.n + i], z = a.pos[2 * a.n + i];
   const int t = a.type[i];
   if (a.do_move) {
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(ForceArgs a) {
   // a step whose solve hit max_iter still completes (forces, energies, step
   // count); any other error stops the step
   const int st0 = a.rec->status;
-  const bool live = i < a.n && (st0 == MAZE_OK || st0 == MAZE_ERR_NOT_CONVERGED);
+  const bool live = i < a.n && *a.gate == 0 && (st0 == MAZE_OK || st0 == MAZE_ERR_NOT_CONVERGED);
   // per-ion contributions to the block sums:
   // 0 KE, 1 V_TF (pairs counted twice), 2 1/2 phi.q, 3 dV_work, 4-6 momentum
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -338,7 +341,7 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(ForceArgs a) {
     if (threadIdx.x == 0) {
       maze_stats* r = a.rec;
       *a.ticket = 0;
-      if (r->status == MAZE_OK || r->status == MAZE_ERR_NOT_CONVERGED) {
+      if (*a.gate == 0 && (r->status == MAZE_OK || r->status == MAZE_ERR_NOT_CONVERGED)) {
         r->ke = tot[0];
         r->v_tf = tot[1];
         r->v_disc = tot[2];

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_cg_solve(SolveArgs a) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
   const size_t pbuf = (size_t)gridDim.x * 4;
-  if (a.rec->status != MAZE_OK) return;
+  if (*a.gate != 0 || a.rec->status != MAZE_OK) return;
 
   const bool sum3[3] = {false, true, false};     // (r.r, max|r|, sum y)
   const bool sum1[1] = {false};

@@ -47,9 +47,9 @@ def case(name):
         pos, vel, types = synth.make_state(w)
         return pos, vel, types, w.L, w.N, w.rc, 4
     if name == "tiny8_N8":         # minimum grid, 8 ions
-        pos, types = synth.random_neutral(8, 6.3, 5, min_dist=2.4)
+        pos, types = synth.random_neutral(8, 8.0, 5, min_dist=2.3)
         vel = synth.maxwell(types, 1200.0, np.random.default_rng(5))
-        return pos, vel, types, 6.3, 8, 3.15, 4
+        return pos, vel, types, 8.0, 8, 4.0, 4
     raise KeyError(name)
 
 
