@@ -32,8 +32,8 @@ sys.path.insert(0, ROOT)
 from paper_2505_20418_gb300 import synth  # noqa: E402
 
 METRIC = "MaZe steps/s, solve GB/s vs HBM peak, p50/p99 step latency at stated force error"
-KERNELS_PER_STEP_CELLS = 6    # ion update, 3 cell-list kernels, solve, forces
-KERNELS_PER_STEP_NOCELLS = 3
+KERNELS_PER_STEP_CELLS = 7    # move, spread, 3 cell-list kernels, solve, forces
+KERNELS_PER_STEP_NOCELLS = 4
 
 
 def peaks():
@@ -95,21 +95,39 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def solve_bytes_per_launch(ng, iters, confirms=1):
-    """Algorithmic DRAM bytes of one solve launch (FP64, 8 B per value):
-    S4 pass 56 B/pt (read phi^k, phi^{k-1}, q, y; write phi_p, sigma_p, r),
-    64 B/pt per CG iteration (read r, p, write p; read p, y, r, write y, r),
-    24 B/pt per true-residual check (read y, sigma_p, write r),
-    32 B/pt correction (read phi_p, y, write phi, y)."""
-    return ng * (56 + 64 * iters + 24 * confirms + 32)
+def mg_levels(N):
+    sizes = [N]
+    while sizes[-1] % 2 == 0 and sizes[-1] >= 8:
+        sizes.append(sizes[-1] // 2)
+    return sizes
 
 
-def run_cpu_baseline(w, budget_s=15.0):
+def solve_bytes_per_launch(N, iters, solver="cg", nu=(2, 2)):
+    """Algorithmic DRAM bytes of one solve launch (FP64, 8 B per value).
+
+    Common: S4 pass 56 B/pt (read phi^k, phi^{k-1}, q, y; write phi_p,
+    sigma_p, r) and the S6 correction 32 B/pt (read phi_p, y; write phi, y).
+    CG: 64 B/pt per iteration (read r, p, write p; read p, y, r, write y, r)
+    plus 24 B/pt for the true-residual confirmation.
+    MG, per V-cycle and level of n_l points: 32 B/pt per red-black sweep (x
+    read twice, b read, x written), residual 24 B/pt, full weighting 9 B/pt,
+    prolongation to black points 9 B/pt; coarsest solve 16 B/pt; residual
+    check on the finest level 16 B/pt."""
+    ng = N ** 3
+    base = ng * (56 + 32)
+    if solver == "cg":
+        return base + ng * (64 * iters + 24)
+    lv = mg_levels(N)
+    per_v = sum(n ** 3 * ((nu[0] + nu[1]) * 32 + 24 + 9 + 9) for n in lv[:-1]) + lv[-1] ** 3 * 16 + ng * 16
+    return base + per_v * iters
+
+
+def run_cpu_baseline(w, solver="mg", budget_s=15.0):
     """The FP64 oracle as it stands, on a bounded sample of the same workload."""
     import oracle as O
     pos, vel, types = synth.make_state(w)
     tf = synth.tosi_fumi_nacl()
-    p = O.Params(L=w.L, N=w.N, dt=w.dt, tol=w.tol, rc=w.rc, P=w.order)
+    p = O.Params(L=w.L, N=w.N, dt=w.dt, tol=w.tol, rc=w.rc, P=w.order, solver=solver)
     st = O.init(pos, vel, types, p, tf)
     n = 0
     t0 = time.perf_counter()
@@ -130,7 +148,7 @@ def bench_reference(args, w):
     import oracle as O
     pos, vel, types = synth.make_state(w)
     tf = synth.tosi_fumi_nacl()
-    p = O.Params(L=w.L, N=w.N, dt=w.dt, tol=w.tol, rc=w.rc, P=w.order)
+    p = O.Params(L=w.L, N=w.N, dt=w.dt, tol=w.tol, rc=w.rc, P=w.order, solver=args.solver)
     st = O.init(pos, vel, types, p, tf)
     for _ in range(args.warmup):
         st = O.step(st, p, tf)
@@ -167,7 +185,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="nacl1000", choices=["nacl64", "nacl1000", "nacl512000"])
-    ap.add_argument("--solver", default="cg", choices=["cg"])
+    ap.add_argument("--solver", default="mg", choices=["cg", "mg"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -194,8 +212,9 @@ def main():
     pos, vel, types = synth.make_state(w)
     tf = synth.tosi_fumi_nacl()
     stream = torch.cuda.Stream(device=dev)
+    solver = M.MAZE_SOLVER_MG if args.solver == "mg" else M.MAZE_SOLVER_CG
     sim = M.MazeSim(pos, vel, types, w.L, w.N, tf, r_cut=w.rc, dt=w.dt, tol=w.tol, order=w.order,
-                    stream=stream.cuda_stream)
+                    solver=solver, stream=stream.cuda_stream)
     sim.set_timing(True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     s0 = sim.stats()
@@ -282,11 +301,11 @@ def main():
 
     if rank == 0:
         ng = w.N ** 3
-        bytes_launch = solve_bytes_per_launch(ng, iters)
+        bytes_launch = solve_bytes_per_launch(w.N, iters, args.solver)
         mean_solve_s = statistics.mean(solve_ms) / 1e3 if solve_ms else float("nan")
         achieved = bytes_launch / mean_solve_s / 1e9
         peak, peak_kind = peaks()
-        cpu = None if args.no_cpu else run_cpu_baseline(w)
+        cpu = None if args.no_cpu else run_cpu_baseline(w, args.solver)
         kps = KERNELS_PER_STEP_CELLS if int(np.floor(w.L / w.rc)) >= 3 else KERNELS_PER_STEP_NOCELLS
         line = {
             "metric": METRIC, "value": world * args.steps / total_s, "unit": "steps/s",
@@ -296,7 +315,7 @@ def main():
             "p50_us": 1e3 * float(np.percentile(step_ms, 50)), "p99_us": 1e3 * float(np.percentile(step_ms, 99)),
             "iters_per_step": iters, "force_error": ferr,
             "solve_gbs": achieved, "solve_us": 1e6 * mean_solve_s,
-            "roofline": {"kernel": "k_cg_solve", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "roofline": {"kernel": "k_mg_solve" if args.solver == "mg" else "k_cg_solve", "bound": "hbm", "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None,
                          "algorithmic_bytes_per_launch": bytes_launch},

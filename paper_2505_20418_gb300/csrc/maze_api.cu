@@ -49,14 +49,20 @@ struct maze_ctx {
   double *pos = nullptr, *vel = nullptr, *force = nullptr, *force_el = nullptr;
   int* type = nullptr;
   float4* pos32 = nullptr;
+  double* wbuf = nullptr;   // [n][3][4] B-spline weights of the current positions
+  int4* wbase = nullptr;
   // grid
   unsigned long long* qfix = nullptr;
   double* qd = nullptr;
   double* phi[3] = {nullptr, nullptr, nullptr};
   int ik = 0;  // phi^k is phi[ik], phi^{k-1} phi[(ik+1)%3], scratch phi[(ik+2)%3]
-  double *sigma = nullptr, *y = nullptr, *r = nullptr, *p = nullptr, *Mp = nullptr;
-  double* spart = nullptr;
+  double *sigma = nullptr, *y = nullptr, *r = nullptr, *p = nullptr, *p1 = nullptr, *Mp = nullptr;
+  LLRec* recs = nullptr;
+  size_t recs_bytes = 0;
   unsigned* bar = nullptr;
+  // multigrid
+  MgArgs mg = {};
+  double *mg_x = nullptr, *mg_b = nullptr, *mg_r = nullptr, *mg_g = nullptr;
   int sblocks = 0;
   // cells
   int nc = 0, ncell = 0;
@@ -102,7 +108,10 @@ maze_status validate(const maze_config* c) {
   if (!(c->dt > 0)) return fail(MAZE_ERR_INVALID, "dt must be > 0");
   if (!(c->tol > 0)) return fail(MAZE_ERR_INVALID, "tol must be > 0");
   if (c->max_iter < 1) return fail(MAZE_ERR_INVALID, "max_iter must be >= 1");
-  if (c->solver != MAZE_SOLVER_CG) return fail(MAZE_ERR_INVALID, "solver: only MAZE_SOLVER_CG is available in this build");
+  if (c->solver != MAZE_SOLVER_CG && c->solver != MAZE_SOLVER_MG)
+    return fail(MAZE_ERR_INVALID, "solver must be MAZE_SOLVER_CG or MAZE_SOLVER_MG");
+  if (c->solver == MAZE_SOLVER_MG && (c->mg_pre < 1 || c->mg_post < 1 || c->mg_pre > 8 || c->mg_post > 8))
+    return fail(MAZE_ERR_INVALID, "mg_pre and mg_post must be in [1, 8]");
   if (c->order_P != 2 && c->order_P != 4) return fail(MAZE_ERR_INVALID, "order_P must be 2 or 4");
   if (c->precision != MAZE_FP64) return fail(MAZE_ERR_INVALID, "precision: only MAZE_FP64 is available in this build");
   if (!c->pos || !c->vel || !c->type) return fail(MAZE_ERR_INVALID, "pos, vel and type must be non-NULL");
@@ -134,6 +143,9 @@ IonArgs ion_args(maze_ctx* c, int do_move, int do_spread) {
   a.n = c->n;
   a.L = c->L;
   a.h = c->h;
+  a.inv_L = 1.0 / c->L;
+  a.inv_h = 1.0 / c->h;
+  a.cell_scale = c->nc / c->L;
   a.N = c->N;
   a.P = c->P;
   a.pos = c->pos;
@@ -153,6 +165,8 @@ IonArgs ion_args(maze_ctx* c, int do_move, int do_spread) {
   a.do_move = do_move;
   a.rec = c->rec;
   a.gate = c->gate;
+  a.wbuf = c->wbuf;
+  a.wbase = c->wbase;
   return a;
 }
 
@@ -175,6 +189,7 @@ ForceArgs force_args(maze_ctx* c, const double* phi, int do_kick, int count_step
   a.n = c->n;
   a.L = c->L;
   a.h = c->h;
+  a.inv_2h = 0.5 / c->h;
   a.N = c->N;
   a.P = c->P;
   a.pos = c->pos;
@@ -184,6 +199,8 @@ ForceArgs force_args(maze_ctx* c, const double* phi, int do_kick, int count_step
   a.pos32 = c->pos32;
   a.type = c->type;
   a.phi = phi;
+  a.wbuf = c->wbuf;
+  a.wbase = c->wbase;
   a.nc = c->nc;
   a.cell_start = c->cell_start;
   a.cell_ions = c->cell_ions;
@@ -209,6 +226,7 @@ ForceArgs force_args(maze_ctx* c, const double* phi, int do_kick, int count_step
   const double rcf = rc + 1e-3 + 1e-6 * c->L;
   a.rc2_filter = (float)(rcf * rcf);
   a.Lf = (float)c->L;
+  a.inv_Lf = (float)(1.0 / c->L);
   a.do_kick = do_kick;
   a.count_step = count_step;
   a.part = c->fpart;
@@ -231,12 +249,14 @@ SolveArgs solve_args(maze_ctx* c, int zero_phi, double* q_out) {
   a.y = c->y;
   a.r = c->r;
   a.p = c->p;
+  a.p1 = c->p1;
   a.Mp = c->Mp;
-  a.part = c->spart;
+  a.recs = c->recs;
   a.bar = c->bar;
   a.rec = c->rec;
   a.c_sig = c->h / (4.0 * kPi);
   a.c_phi = 4.0 * kPi / c->h;
+  a.inv_n = 1.0 / (double)c->ng;
   a.tol = c->cfg.tol;
   a.max_iter = zero_phi ? c->max_iter_init : c->cfg.max_iter;
   a.zero_phi = zero_phi;
@@ -247,9 +267,39 @@ SolveArgs solve_args(maze_ctx* c, int zero_phi, double* q_out) {
 // --- sequences ------------------------------------------------------------
 
 maze_status enqueue_solve(maze_ctx* c, int zero_phi, double* q_out) {
-  CK(cudaMemsetAsync(c->bar, 0, sizeof(unsigned), c->stream));
-  CK(launch_cg_solve(solve_args(c, zero_phi, q_out), c->sblocks, c->stream));
+  CK(cudaMemsetAsync(c->recs, 0, c->recs_bytes, c->stream));
+  if (c->cfg.solver == MAZE_SOLVER_MG) {
+    CK(cudaMemsetAsync(c->bar, 0, sizeof(unsigned), c->stream));
+    CK(launch_mg_solve(solve_args(c, zero_phi, q_out), c->mg, c->sblocks, c->stream));
+  } else {
+    CK(launch_cg_solve(solve_args(c, zero_phi, q_out), c->sblocks, c->stream));
+  }
   return MAZE_OK;
+}
+
+// Pseudo-inverse of the periodic h^2-scaled Laplacian on an Nc^3 grid as a
+// convolution kernel: g(d) = (1/Nc^3) sum_{k != 0} cos(2 pi k.d / Nc) / lambda(k),
+// lambda(k) = -6 + 2 cos(2 pi kx/Nc) + 2 cos(2 pi ky/Nc) + 2 cos(2 pi kz/Nc)
+// (the plane waves diagonalise the circulant M). g * b is the zero-mean
+// exact solution of M x = b - mean(b).
+std::vector<double> coarse_kernel(int Nc) {
+  const int n3 = Nc * Nc * Nc;
+  std::vector<double> c(Nc), g(n3, 0.0);
+  for (int t = 0; t < Nc; ++t) c[t] = cos(2.0 * kPi * t / Nc);
+  for (int dz = 0; dz < Nc; ++dz)
+    for (int dy = 0; dy < Nc; ++dy)
+      for (int dx = 0; dx < Nc; ++dx) {
+        double s = 0.0;
+        for (int kz = 0; kz < Nc; ++kz)
+          for (int ky = 0; ky < Nc; ++ky)
+            for (int kx = 0; kx < Nc; ++kx) {
+              if (!kx && !ky && !kz) continue;
+              const double lam = -6.0 + 2.0 * (c[kx] + c[ky] + c[kz]);
+              s += c[(kx * dx + ky * dy + kz * dz) % Nc] / lam;
+            }
+        g[dx + Nc * (dy + Nc * dz)] = s / n3;
+      }
+  return g;
 }
 
 maze_status enqueue_cells(maze_ctx* c) {
@@ -400,7 +450,7 @@ maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
   c->nc = (int)floor(c->L / cfg->r_cut);
   if (c->nc < 3) c->nc = 0;
   c->ncell = c->nc * c->nc * c->nc;
-  c->sblocks = solve_blocks((int)ng);
+  c->sblocks = cfg->solver == MAZE_SOLVER_MG ? mg_blocks((int)ng) : solve_blocks((int)ng);
   c->fblocks = force_blocks(n);
 #define AL(p, cnt)                          \
   do {                                      \
@@ -416,6 +466,8 @@ maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
   AL(c->force_el, 3 * (size_t)n);
   AL(c->type, (size_t)n);
   AL(c->pos32, (size_t)n);
+  AL(c->wbuf, 12 * (size_t)n);
+  AL(c->wbase, (size_t)n);
   AL(c->qfix, ng);
   AL(c->qd, ng);
   for (int g = 0; g < 3; ++g) AL(c->phi[g], ng);
@@ -423,9 +475,37 @@ maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
   AL(c->y, ng);
   AL(c->r, ng);
   AL(c->p, ng);
+  AL(c->p1, ng);
   AL(c->Mp, ng);
-  AL(c->spart, 2 * (size_t)c->sblocks * 4);
+  c->recs_bytes = 2 * (size_t)c->sblocks * 4 * 16;
+  AL(c->recs, 2 * (size_t)c->sblocks * 4);
   AL(c->bar, 4);
+  std::vector<double> gk;
+  if (cfg->solver == MAZE_SOLVER_MG) {
+    // hierarchy: halve while the edge is even and >= 8
+    MgArgs& g = c->mg;
+    g.L = 0;
+    size_t tot = 0;
+    for (int N = c->N;; N /= 2) {
+      g.Nl[g.L] = N;
+      g.off[g.L] = tot;
+      tot += (size_t)N * N * N;
+      ++g.L;
+      if (!(N % 2 == 0 && N >= 8) || g.L == kMaxLevels) break;
+    }
+    g.nu1 = cfg->mg_pre;
+    g.nu2 = cfg->mg_post;
+    AL(c->mg_x, tot);
+    AL(c->mg_b, tot);
+    AL(c->mg_r, tot);
+    const int Nc = g.Nl[g.L - 1];
+    gk = coarse_kernel(Nc);
+    AL(c->mg_g, gk.size());
+    g.x = c->mg_x;
+    g.b = c->mg_b;
+    g.r = c->mg_r;
+    g.gker = c->mg_g;
+  }
   AL(c->cell_of, (size_t)n);
   if (c->nc >= 3) {
     AL(c->cell_count, (size_t)c->ncell);
@@ -461,6 +541,7 @@ maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
     for (int i = 0; i < n; ++i) tmp[(size_t)d * n + i] = cfg->vel[3 * i + d];
   CKC(cudaMemcpyAsync(c->vel, tmp.data(), tmp.size() * 8, cudaMemcpyHostToDevice, st));
   CKC(cudaMemcpyAsync(c->type, cfg->type, (size_t)n * 4, cudaMemcpyHostToDevice, st));
+  if (!gk.empty()) CKC(cudaMemcpyAsync(c->mg_g, gk.data(), gk.size() * 8, cudaMemcpyHostToDevice, st));
   CKC(cudaMemsetAsync(c->force, 0, 3 * (size_t)n * 8, st));
   CKC(cudaMemsetAsync(c->force_el, 0, 3 * (size_t)n * 8, st));
   CKC(cudaMemsetAsync(c->qfix, 0, ng * 8, st));

@@ -19,9 +19,15 @@ constexpr double kQInv = 1.0 / 1125899906842624.0;
 
 // Spin limit of every device-side wait (about a second of polling).
 constexpr unsigned kSpinLimit = 1u << 22;
+// Largest cooperative grid the flag-carrying reduction supports.
+constexpr int kMaxReduceBlocks = 256;
 
 constexpr int kSolveThreads = 256;
 constexpr int kForceThreads = 256;   // 8 ions (one warp each) per block
+constexpr int kIonThreads = 128;
+constexpr int kSpreadThreads = 256;  // 8 ions (one warp each) per block
+
+struct LLRec;  // flag-carrying reduction record (defined below)
 
 // ---------------------------------------------------------------------------
 // Kernel argument blocks (plain device pointers).
@@ -29,6 +35,8 @@ constexpr int kForceThreads = 256;   // 8 ions (one warp each) per block
 struct IonArgs {
   int n;                 // ions
   double L, h;           // box edge, grid spacing
+  double inv_L, inv_h;   // 1/L, 1/h
+  double cell_scale;     // nc / L
   int N, P;              // grid edge, assignment order
   double* pos;           // [3][n] SoA
   double* vel;           // [3][n]
@@ -45,6 +53,8 @@ struct IonArgs {
   int do_move;           // 1: half kick + drift before spreading
   maze_stats* rec;
   int* gate;             // set to 1 when the step starts after an error
+  double* wbuf;          // [n][3][4] B-spline weights of the new positions
+  int4* wbase;           // [n] first support node per axis
 };
 
 struct CellArgs {
@@ -60,6 +70,7 @@ struct CellArgs {
 struct ForceArgs {
   int n;
   double L, h;
+  double inv_2h;         // 1 / (2h)
   int N, P;
   const double* pos;     // [3][n]
   double* vel;           // [3][n]
@@ -68,6 +79,8 @@ struct ForceArgs {
   const float4* pos32;
   const int* type;
   const double* phi;     // [N^3]
+  const double* wbuf;    // [n][3][4] weights written by k_ion_update
+  const int4* wbase;     // [n]
   int nc;                // cells per edge; < 3 means all pairs
   const int* cell_start;
   const int* cell_ions;
@@ -81,7 +94,7 @@ struct ForceArgs {
   double B;
   double rc2;            // r_cut^2
   float rc2_filter;      // (r_cut + margin)^2 for the FP32 pre-filter
-  float Lf;
+  float Lf, inv_Lf;
   int do_kick;           // 1: second half kick + V_work increment
   int count_step;        // 1: this completes an MD step
   double* part;          // [gridDim][8] block partials
@@ -100,27 +113,44 @@ struct SolveArgs {
   double* sigma;
   double* y;
   double* r;
-  double* p;
+  double* p;             // search direction, double-buffered with p1
+  double* p1;
   double* Mp;
-  double* part;          // [2][gridDim][4] double-buffered block partials
-  unsigned* bar;         // barrier counter, zero at launch
+  LLRec* recs;           // [2][gridDim][4] reduction records, zero at launch
+  unsigned* bar;         // grid barrier counter, zero at launch
   maze_stats* rec;
   double c_sig;          // h / 4pi
   double c_phi;          // 4pi / h
+  double inv_n;          // 1 / N^3
   double tol;
   int max_iter;
   int zero_phi;          // step 0: phi^k = phi^{k-1} = 0
   const int* gate;       // 1: this step was skipped
 };
 
+// Multigrid hierarchy (levels 0..L-1, level 0 is the SHAKE grid itself).
+constexpr int kMaxLevels = 10;
+struct MgArgs {
+  int L;
+  int Nl[kMaxLevels];
+  size_t off[kMaxLevels];  // offsets of each level in x, b, r (level 0 at 0)
+  double* x;               // corrections on levels >= 1 (level 0 uses y)
+  double* b;               // right-hand sides on levels >= 1 (level 0 uses sigma_p)
+  double* r;               // residuals, all levels
+  const double* gker;      // [Nc^3] pseudo-inverse kernel of the coarsest M
+  int nu1, nu2;
+};
+
 // Host-side launchers (defined in the .cu files).
-cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t s);
+cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t s);   // k_move, then k_spread if a.qfix
 cudaError_t launch_q_to_double(const unsigned long long* qfix, double* q, int n, cudaStream_t s);
 cudaError_t launch_cells(const CellArgs& a, cudaStream_t s);
 cudaError_t launch_forces(const ForceArgs& a, int blocks, cudaStream_t s);
 int force_blocks(int n_ions);
 cudaError_t launch_cg_solve(const SolveArgs& a, int blocks, cudaStream_t s);
 int solve_blocks(int n_points);
+cudaError_t launch_mg_solve(const SolveArgs& a, const MgArgs& g, int blocks, cudaStream_t s);
+int mg_blocks(int n_points);
 // Sets the message returned by maze_last_error on the calling thread.
 void set_last_error(const char* msg);
 
@@ -145,8 +175,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& epoch, maz
   if (threadIdx.x == 0) {
     epoch += 1;
     const unsigned target = epoch * gridDim.x;
-    __threadfence();
-    atomicAdd(bar, 1u);
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(bar), "r"(1u) : "memory");
     int ok = 1;
     unsigned spins = 0;
     while (ld_acquire_u32(bar) < target) {
@@ -156,11 +185,62 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& epoch, maz
         break;
       }
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Flag-carrying grid reduction. Each block publishes its partials as 16-byte
+// records {lo32, flag, hi32, flag}: each 8-byte half pairs half of the double
+// with the epoch number, so a reader that sees both flags equal to the epoch
+// holds the whole value (8-byte stores and loads are single-copy atomic).
+// One round of publish + poll replaces a barrier followed by a second trip to
+// read the partials. Records are double-buffered by epoch parity and must be
+// zero when the kernel starts. Release: __syncthreads,
+// then a gpu-scope release store of the record by the publishing thread;
+// acquire: gpu-scope acquire loads of the records, then __syncthreads.
+struct LLRec {
+  unsigned lo, f0, hi, f1;
+};
+
+// Release store: the block's earlier global writes (ordered before this
+// thread by __syncthreads) become visible no later than the record.
+__device__ __forceinline__ void ll_store(LLRec* r, double v, unsigned epoch) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  asm volatile("st.release.gpu.global.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(r), "r"((unsigned)b), "r"(epoch),
+               "r"((unsigned)(b >> 32)), "r"(epoch)
+               : "memory");
+}
+
+// Acquire load: once the flags match, the publisher's earlier writes are
+// visible to this thread (and, after __syncthreads, to its block).
+__device__ __forceinline__ bool ll_load(const LLRec* r, unsigned epoch, double& v) {
+  unsigned lo, f0, hi, f1;
+  asm volatile("ld.acquire.gpu.global.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(lo), "=r"(f0), "=r"(hi), "=r"(f1) : "l"(r)
+               : "memory");
+  if (f0 != epoch || f1 != epoch) return false;
+  v = __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+  return true;
+}
+
+// 1/d by Newton-Raphson on the mantissa: d = m 2^e with m in [1,2), an FP32
+// seed for 1/m, then two steps y <- y (2 - m y) (the error squares at each
+// step: ~2^-23 -> 2^-46 -> below FP64 rounding), and the exponent restored by
+// integer arithmetic. A handful of FP64 operations instead of the long FP64
+// division sequence; used for the scalar recurrences of the solvers. Zero,
+// denormal, infinite and NaN inputs take the ordinary division.
+__device__ __forceinline__ double recip_newton(double d) {
+  const long long b = __double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e == 0 || e == 2047) return 1.0 / d;
+  const double m = __longlong_as_double((b & (long long)0x800fffffffffffffULL) | (1023LL << 52));
+  double y = (double)(1.0f / (float)m);
+  y = y * (2.0 - m * y);
+  y = y * (2.0 - m * y);
+  const long long yb = __double_as_longlong(y) - ((long long)(e - 1023) << 52);
+  return __longlong_as_double(yb);
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -194,6 +274,211 @@ __device__ __forceinline__ Nbr neighbours(int n, int N) {
   b.zm = (k == 0) ? n + NN * (N - 1) : n - NN;
   b.zp = (k == N - 1) ? n - NN * (N - 1) : n + NN;
   return b;
+}
+
+// Identity post step of grid_reduce.
+struct NoPost {
+  __device__ double operator()(const double*) const { return 0.0; }
+};
+
+// ---------------------------------------------------------------------------
+// Exact sums of doubles on the integer pipe. GB300 issues FP64 at 1/64 of the
+// FP32 rate and a dependent FP64 add costs ~150 cycles, so a shuffle tree of
+// FP64 adds is slow. Instead every value is rounded to a 64-bit fixed-point
+// grid aligned to the largest exponent in the group (the value's 53-bit
+// significand shifted right by the exponent difference, round to nearest),
+// and the integers are summed exactly: each int64 is cut into four 16-bit
+// chunks and each chunk summed with __reduce_add_sync (32 lanes x 2^16 < 2^21),
+// then recombined modulo 2^64. The total is exact for the rounded inputs, so
+// the result is independent of summation order (bit-reproducible) and its
+// error is at most half an ulp of the largest input per input.
+
+__device__ __forceinline__ int dbl_exp(double v) { return (int)((__double_as_longlong(v) >> 52) & 0x7ff); }
+
+// v as an integer multiple of 2^(E - 1075); requires the exponent of v <= E.
+__device__ __forceinline__ long long dbl_to_fix(double v, int E) {
+  const long long b = __double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e == 0) return 0;  // zero and denormals (below 2^-1022) count as zero
+  const long long m = (b & 0xfffffffffffffLL) | (1LL << 52);
+  const int sh = E - e;
+  long long x;
+  if (sh <= 0) x = m;
+  else if (sh >= 62) x = 0;
+  else x = (m + (1LL << (sh - 1))) >> sh;
+  return b < 0 ? -x : x;
+}
+
+// S * 2^(E - 1075) as a double, built with integer operations only:
+// normalise |S| to a 53-bit significand (round half up) and set the exponent.
+__device__ __forceinline__ double fix_to_dbl(long long S, int E) {
+  if (S == 0) return 0.0;
+  const unsigned long long sign = S < 0 ? 0x8000000000000000ULL : 0ULL;
+  const unsigned long long u = S < 0 ? (unsigned long long)(-S) : (unsigned long long)S;
+  int sh = (64 - __clzll((long long)u)) - 53;
+  unsigned long long m;
+  if (sh > 0) {
+    m = (u + (1ULL << (sh - 1))) >> sh;
+    if (m >> 53) {
+      m >>= 1;
+      ++sh;
+    }
+  } else {
+    m = u << (-sh);
+  }
+  const int ed = sh + E;
+  if (ed <= 0) return 0.0;
+  if (ed >= 2047) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ULL));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)ed << 52) | (m & 0xfffffffffffffULL)));
+}
+
+__device__ __forceinline__ long long warp_isum(long long x) {
+  const unsigned long long u = (unsigned long long)x;
+  const unsigned c0 = __reduce_add_sync(0xffffffffu, (unsigned)(u & 0xffffu));
+  const unsigned c1 = __reduce_add_sync(0xffffffffu, (unsigned)((u >> 16) & 0xffffu));
+  const unsigned c2 = __reduce_add_sync(0xffffffffu, (unsigned)((u >> 32) & 0xffffu));
+  const unsigned c3 = __reduce_add_sync(0xffffffffu, (unsigned)(u >> 48));
+  return (long long)((unsigned long long)c0 + ((unsigned long long)c1 << 16) + ((unsigned long long)c2 << 32) +
+                     ((unsigned long long)c3 << 48));
+}
+
+// Max of non-negative doubles by integer max of their bit patterns (IEEE
+// ordering of non-negative values equals integer ordering).
+__device__ __forceinline__ unsigned long long warp_umax64(unsigned long long u) {
+  const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(u >> 32));
+  const unsigned lo = __reduce_max_sync(0xffffffffu, (unsigned)(u >> 32) == hi ? (unsigned)u : 0u);
+  return ((unsigned long long)hi << 32) | lo;
+}
+
+// Exact warp sum of doubles (every lane gets the result as fixed point S, E).
+__device__ __forceinline__ void warp_dsum_fix(double v, long long& S, int& E) {
+  E = (int)__reduce_max_sync(0xffffffffu, (unsigned)dbl_exp(v));
+  S = warp_isum(dbl_to_fix(v, E));
+}
+
+// Grid-wide reduction of K <= 4 values (sum, or max of non-negative values
+// where is_max[k]) over all blocks of a cooperative launch. ``v`` holds this
+// thread's contributions; on return every thread of every block holds the
+// identical totals in ``out``. Blocks publish their partials through the
+// flag-carrying records (``recs`` is [2][gridDim][4], zero at launch;
+// ``epoch`` counts rounds from 1). ``post`` runs once per block, in one lane,
+// on the totals; its result comes back in ``extra``. A poll that exceeds
+// kSpinLimit records MAZE_ERR_TIMEOUT and returns false.
+template <int K, typename Post = NoPost>
+__device__ __forceinline__ bool grid_reduce(const double (&v)[K], const bool (&is_max)[K], LLRec* recs, unsigned epoch,
+                                            maze_stats* rec, double (&out)[K], Post post = Post(),
+                                            double* extra = nullptr) {
+  __shared__ long long s_s[32][4];
+  __shared__ int s_e[32][4];
+  __shared__ double s_out[5];
+  __shared__ int s_ok;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // block stage 1: warp exponent maxima (sums) or bit maxima (maxima)
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (is_max[k]) {
+      const unsigned long long m = warp_umax64((unsigned long long)__double_as_longlong(fabs(v[k])));
+      if (lane == 0) s_s[warp][k] = (long long)m;
+    } else {
+      const int e = (int)__reduce_max_sync(0xffffffffu, (unsigned)dbl_exp(v[k]));
+      if (lane == 0) s_e[warp][k] = e;
+    }
+  }
+  __syncthreads();
+  // block stage 2: align every value to the block's largest exponent, sum exactly
+  int Eb[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (is_max[k]) continue;
+    int E = 0;
+    for (int u = 0; u < nw; ++u) E = max(E, s_e[u][k]);
+    Eb[k] = E;
+    const long long S = warp_isum(dbl_to_fix(v[k], E));
+    if (lane == 0) s_s[warp][k] = S;
+  }
+  __syncthreads();
+  LLRec* buf = recs + (size_t)(epoch & 1u) * gridDim.x * 4;
+  if (warp == 0) {
+    // publish the block partials (as doubles; one rounding of the exact sum)
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        double w;
+        if (is_max[k]) {
+          unsigned long long m = 0;
+          for (int u = 0; u < nw; ++u) m = max(m, (unsigned long long)s_s[u][k]);
+          w = __longlong_as_double((long long)m);
+        } else {
+          long long S = 0;
+          for (int u = 0; u < nw; ++u) S += s_s[u][k];
+          w = fix_to_dbl(S, Eb[k]);
+        }
+        ll_store(&buf[blockIdx.x * 4 + k], w, epoch);
+      }
+    }
+    // read every block's records; all of this lane's loads are in flight at once
+    constexpr int kMaxPer = kMaxReduceBlocks / 32;
+    double val[K][kMaxPer];
+    unsigned pending = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int j = 0; j < kMaxPer; ++j) {
+        val[k][j] = 0.0;
+        if (lane + 32 * j < (int)gridDim.x) pending |= 1u << (k * kMaxPer + j);
+      }
+    int ok = 1;
+    unsigned spins = 0;
+    while (pending) {
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int j = 0; j < kMaxPer; ++j) {
+          const unsigned bit = 1u << (k * kMaxPer + j);
+          if (pending & bit) {
+            if (ll_load(&buf[(lane + 32 * j) * 4 + k], epoch, val[k][j])) pending &= ~bit;
+          }
+        }
+      if (pending && ++spins > kSpinLimit) {
+        ok = 0;
+        break;
+      }
+    }
+    // combine the block partials exactly (same integer algorithm)
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double tot;
+      if (is_max[k]) {
+        unsigned long long m = 0;
+#pragma unroll
+        for (int j = 0; j < kMaxPer; ++j) m = max(m, (unsigned long long)__double_as_longlong(val[k][j]));
+        tot = __longlong_as_double((long long)warp_umax64(m));
+      } else {
+        int e = 0;
+#pragma unroll
+        for (int j = 0; j < kMaxPer; ++j) e = max(e, dbl_exp(val[k][j]));
+        const int E = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
+        long long x = 0;
+#pragma unroll
+        for (int j = 0; j < kMaxPer; ++j) x += dbl_to_fix(val[k][j], E);
+        tot = fix_to_dbl(warp_isum(x), E);
+      }
+      if (lane == 0) s_out[k] = tot;
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0) {
+      if (!ok) atomicCAS(&rec->status, MAZE_OK, MAZE_ERR_TIMEOUT);
+      s_ok = ok;
+      s_out[4] = post(s_out);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) out[k] = s_out[k];
+  if (extra) *extra = s_out[4];
+  const bool ok = s_ok != 0;
+  __syncthreads();
+  return ok;
 }
 
 #endif  // __CUDACC__

@@ -35,64 +35,79 @@ __device__ __forceinline__ int axis_weights(double u, int P, int N, double* w) {
 
 __device__ __forceinline__ int wrap_idx(int a, int N) { return a >= N ? a - N : a; }
 
-__device__ __forceinline__ double wrap_pos(double x, double L) {
-  x -= L * floor(x / L);
+__device__ __forceinline__ double wrap_pos(double x, double L, double inv_L) {
+  x -= L * floor(x * inv_L);
+  if (x < 0.0) x += L;
   if (x >= L) x -= L;
   return x;
 }
 
-__global__ void k_ion_update(IonArgs a) {
+// S1: one thread per ion for the Verlet half kick and drift, the FP32 copy,
+// the cell count and the B-spline weights of the new position (stored: the
+// spread and the gather of the same step reuse them).
+__global__ void __launch_bounds__(kIonThreads) k_move(IonArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   // the first kernel of a step decides, once, whether the step runs at all
   const bool skip = a.rec->status != MAZE_OK;
   if (i == 0) *a.gate = skip ? 1 : 0;
-  if (i >= a.n || skip) return;
-  double x = a.pos[i], y = a.pos[a.n + i], z = a.pos[2 * a.n + i];
-  const int t = a.type[i];
-  if (a.do_move) {
-    const double kick = t ? a.kick1 : a.kick0;
-    double vx = a.vel[i] + kick * a.force[i];
-    double vy = a.vel[a.n + i] + kick * a.force[a.n + i];
-    double vz = a.vel[2 * a.n + i] + kick * a.force[2 * a.n + i];
-    a.vel[i] = vx;
-    a.vel[a.n + i] = vy;
-    a.vel[2 * a.n + i] = vz;
-    x = wrap_pos(x + a.dt * vx, a.L);
-    y = wrap_pos(y + a.dt * vy, a.L);
-    z = wrap_pos(z + a.dt * vz, a.L);
-    a.pos[i] = x;
-    a.pos[a.n + i] = y;
-    a.pos[2 * a.n + i] = z;
-  }
-  const double Q = t ? a.charge1 : a.charge0;
-  a.pos32[i] = make_float4((float)x, (float)y, (float)z, (float)Q);
-  if (a.nc >= 3) {
-    const double cs = a.nc / a.L;
-    int cx = min((int)(x * cs), a.nc - 1), cy = min((int)(y * cs), a.nc - 1), cz = min((int)(z * cs), a.nc - 1);
-    const int c = cx + a.nc * (cy + a.nc * cz);
-    a.cell_of[i] = c;
-    atomicAdd(&a.cell_count[c], 1);
-  }
-  if (!a.qfix) return;
-  // S3: q_n += Q W(r - r_n) over the P^3 support, fixed-point atomics
-  double wx[4], wy[4], wz[4];
+  if (skip) return;
+  __shared__ double s_w[kIonThreads][12];
   const int N = a.N, P = a.P;
-  const int fx = axis_weights(x / a.h, P, N, wx);
-  const int fy = axis_weights(y / a.h, P, N, wy);
-  const int fz = axis_weights(z / a.h, P, N, wz);
-  for (int c = 0; c < P; ++c) {
-    const int iz = wrap_idx(fz + c, N);
-    const double qz = Q * wz[c];
-    for (int b = 0; b < P; ++b) {
-      const int iy = wrap_idx(fy + b, N);
-      const double qzy = qz * wy[b];
-      const size_t row = ((size_t)iz * N + iy) * N;
-      for (int aa = 0; aa < P; ++aa) {
-        const int ix = wrap_idx(fx + aa, N);
-        const long long v = __double2ll_rn(qzy * wx[aa] * kQScale);
-        atomicAdd(&a.qfix[row + ix], (unsigned long long)v);
-      }
+  if (i < a.n) {
+    double x = a.pos[i], y = a.pos[a.n + i], z = a.pos[2 * a.n + i];
+    const int t = a.type[i];
+    if (a.do_move) {
+      const double kick = t ? a.kick1 : a.kick0;
+      double vx = a.vel[i] + kick * a.force[i];
+      double vy = a.vel[a.n + i] + kick * a.force[a.n + i];
+      double vz = a.vel[2 * a.n + i] + kick * a.force[2 * a.n + i];
+      a.vel[i] = vx;
+      a.vel[a.n + i] = vy;
+      a.vel[2 * a.n + i] = vz;
+      x = wrap_pos(x + a.dt * vx, a.L, a.inv_L);
+      y = wrap_pos(y + a.dt * vy, a.L, a.inv_L);
+      z = wrap_pos(z + a.dt * vz, a.L, a.inv_L);
+      a.pos[i] = x;
+      a.pos[a.n + i] = y;
+      a.pos[2 * a.n + i] = z;
     }
+    const double Q = t ? a.charge1 : a.charge0;
+    a.pos32[i] = make_float4((float)x, (float)y, (float)z, (float)Q);
+    if (a.nc >= 3) {
+      const double cs = a.cell_scale;
+      int cx = min((int)(x * cs), a.nc - 1), cy = min((int)(y * cs), a.nc - 1), cz = min((int)(z * cs), a.nc - 1);
+      const int c = cx + a.nc * (cy + a.nc * cz);
+      a.cell_of[i] = c;
+      atomicAdd(&a.cell_count[c], 1);
+    }
+    double* w = s_w[threadIdx.x];
+    const int fx = axis_weights(x * a.inv_h, P, N, w);
+    const int fy = axis_weights(y * a.inv_h, P, N, w + 4);
+    const int fz = axis_weights(z * a.inv_h, P, N, w + 8);
+    if (P == 2) w[2] = w[3] = w[6] = w[7] = w[10] = w[11] = 0.0;
+    double* gw = a.wbuf + (size_t)i * 12;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) gw[k] = w[k];
+    a.wbase[i] = make_int4(fx, fy, fz, 0);
+  }
+}
+
+// S3: q_n += Q W(r - r_n), W = w_x w_y w_z over the P^3 support, one warp per
+// ion (lane l takes support points l, l+32, ...), fixed-point atomics.
+__global__ void __launch_bounds__(kSpreadThreads) k_spread(IonArgs a) {
+  if (*a.gate) return;
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (kSpreadThreads / 32) + (threadIdx.x >> 5);
+  if (i >= a.n) return;
+  const int N = a.N, P = a.P, P3 = P * P * P;
+  const double* w = a.wbuf + (size_t)i * 12;
+  const int4 b = a.wbase[i];
+  const double Q = a.type[i] ? a.charge1 : a.charge0;
+  for (int sidx = lane; sidx < P3; sidx += 32) {
+    const int ia = sidx % P, ib = (sidx / P) % P, ic = sidx / (P * P);
+    const double v = Q * w[8 + ic] * w[4 + ib] * w[ia];
+    const int ix = wrap_idx(b.x + ia, N), iy = wrap_idx(b.y + ib, N), iz = wrap_idx(b.z + ic, N);
+    atomicAdd(&a.qfix[((size_t)iz * N + iy) * N + ix], (unsigned long long)__double2ll_rn(v * kQScale));
   }
 }
 
@@ -102,8 +117,11 @@ __global__ void k_q_to_double(const unsigned long long* qfix, double* q, int n) 
 }
 
 cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t s) {
-  const int th = 128;
-  k_ion_update<<<(a.n + th - 1) / th, th, 0, s>>>(a);
+  k_move<<<(a.n + kIonThreads - 1) / kIonThreads, kIonThreads, 0, s>>>(a);
+  if (a.qfix) {
+    const int per = kSpreadThreads / 32;
+    k_spread<<<(a.n + per - 1) / per, kSpreadThreads, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -150,25 +168,46 @@ __global__ void k_cell_fill(CellArgs a) {
   a.cell_ions[slot] = i;
 }
 
-__global__ void k_cell_sort(CellArgs a) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per cell: each slot's rank among the cell's (distinct) ion indices
+// gives its sorted position. Cells larger than the shared buffer fall back to
+// an insertion sort by lane 0.
+constexpr int kSortWarps = 4;
+constexpr int kSortCap = 256;
+__global__ void __launch_bounds__(kSortWarps * 32) k_cell_sort(CellArgs a) {
+  __shared__ int s_ids[kSortWarps][kSortCap];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.x * kSortWarps + warp;
   if (c >= a.ncell) return;
-  const int lo = a.cell_start[c], hi = a.cell_start[c + 1];
-  for (int u = lo + 1; u < hi; ++u) {
-    const int v = a.cell_ions[u];
-    int w = u - 1;
-    while (w >= lo && a.cell_ions[w] > v) {
-      a.cell_ions[w + 1] = a.cell_ions[w];
-      --w;
-    }
-    a.cell_ions[w + 1] = v;
+  const int lo = a.cell_start[c], hi = a.cell_start[c + 1], m = hi - lo;
+  if (m <= 1) return;
+  if (m > kSortCap) {
+    if (lane == 0)
+      for (int u = lo + 1; u < hi; ++u) {
+        const int v = a.cell_ions[u];
+        int w = u - 1;
+        while (w >= lo && a.cell_ions[w] > v) {
+          a.cell_ions[w + 1] = a.cell_ions[w];
+          --w;
+        }
+        a.cell_ions[w + 1] = v;
+      }
+    return;
+  }
+  int* ids = s_ids[warp];
+  for (int u = lane; u < m; u += 32) ids[u] = a.cell_ions[lo + u];
+  __syncwarp();
+  for (int u = lane; u < m; u += 32) {
+    const int v = ids[u];
+    int rank = 0;
+    for (int k = 0; k < m; ++k) rank += ids[k] < v;
+    a.cell_ions[lo + rank] = v;
   }
 }
 
 cudaError_t launch_cells(const CellArgs& a, cudaStream_t s) {
   k_cell_scan<<<1, 1024, 0, s>>>(a);
   k_cell_fill<<<(a.n + 255) / 256, 256, 0, s>>>(a);
-  k_cell_sort<<<(a.ncell + 127) / 128, 128, 0, s>>>(a);
+  k_cell_sort<<<(a.ncell + kSortWarps - 1) / kSortWarps, kSortWarps * 32, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -176,14 +215,20 @@ cudaError_t launch_cells(const CellArgs& a, cudaStream_t s) {
 // S7-S9: one warp per ion.
 
 __device__ __forceinline__ void tf_pair(const ForceArgs& a, int kind, double r2, double& fr, double& V) {
-  // V = A exp(B (s - r)) - C r^-6 - D r^-8 - V(r_c);  fr = -(dV/dr) / r
-  const double r = sqrt(r2);
-  const double ir2 = 1.0 / r2;
+  // V = A exp(B (s - r)) - C r^-6 - D r^-8 - V(r_c);  fr = -(dV/dr) / r.
+  // 1/r by Newton-Raphson for the reciprocal square root, y <- y (3 - r2 y^2)/2,
+  // from an FP32 seed (two steps: ~2^-22 -> 2^-44 -> FP64 rounding), so no FP64
+  // square root or division is needed.
+  double ir = (double)rsqrtf((float)r2);
+  ir = ir * (1.5 - 0.5 * r2 * ir * ir);
+  ir = ir * (1.5 - 0.5 * r2 * ir * ir);
+  const double r = r2 * ir;
+  const double ir2 = ir * ir;
   const double ir6 = ir2 * ir2 * ir2;
   const double ir8 = ir6 * ir2;
   const double ex = a.A[kind] * exp(a.B * (a.s[kind] - r));
   V = ex - a.C[kind] * ir6 - a.D[kind] * ir8 - a.Vc[kind];
-  fr = (a.B * ex) / r - 6.0 * a.C[kind] * ir8 - 8.0 * a.D[kind] * ir8 * ir2;
+  fr = a.B * ex * ir - 6.0 * a.C[kind] * ir8 - 8.0 * a.D[kind] * ir8 * ir2;
 }
 
 __global__ void __launch_bounds__(kForceThreads) k_forces(ForceArgs a) {
@@ -197,24 +242,23 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(ForceArgs a) {
   // per-ion contributions to the block sums:
   // 0 KE, 1 V_TF (pairs counted twice), 2 1/2 phi.q, 3 dV_work, 4-6 momentum
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  __shared__ int s_queue[kForceThreads / 32][64];
   if (live) {
     const int n = a.n, N = a.N, P = a.P;
     const double x = a.pos[i], y = a.pos[n + i], z = a.pos[2 * n + i];
     const int t = a.type[i];
     const double Q = t ? a.charge1 : a.charge0;
-    // --- S7: Eq. F_nostra, F = -k_e Q sum_n W (phi_{n+e} - phi_{n-e}) / 2h
-    double w[3][4];
-    int first[3];
-    first[0] = axis_weights(x / a.h, P, N, w[0]);
-    first[1] = axis_weights(y / a.h, P, N, w[1]);
-    first[2] = axis_weights(z / a.h, P, N, w[2]);
+    // --- S7: Eq. F_nostra, F = -k_e Q sum_n W (phi_{n+e} - phi_{n-e}) / 2h,
+    // with the weights k_ion_update stored for this position
+    const double* w = a.wbuf + (size_t)i * 12;
+    const int4 first = a.wbase[i];
     const int P3 = P * P * P;
     double gx = 0, gy = 0, gz = 0, vd = 0;
     const size_t NN = (size_t)N * N;
     for (int sidx = lane; sidx < P3; sidx += 32) {
       const int ia = sidx % P, ib = (sidx / P) % P, ic = sidx / (P * P);
-      const int ix = wrap_idx(first[0] + ia, N), iy = wrap_idx(first[1] + ib, N), iz = wrap_idx(first[2] + ic, N);
-      const double wt = w[0][ia] * w[1][ib] * w[2][ic];
+      const int ix = wrap_idx(first.x + ia, N), iy = wrap_idx(first.y + ib, N), iz = wrap_idx(first.z + ic, N);
+      const double wt = w[ia] * w[4 + ib] * w[8 + ic];
       const size_t row = iz * NN + (size_t)iy * N;
       const double* ph = a.phi;
       const double px = ph[row + (ix == N - 1 ? 0 : ix + 1)] - ph[row + (ix == 0 ? N - 1 : ix - 1)];
@@ -231,22 +275,21 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(ForceArgs a) {
     gy = warp_sum(gy);
     gz = warp_sum(gz);
     vd = warp_sum(vd);
-    const double fe = -MAZE_KE_EV_ANGSTROM * Q / (2.0 * a.h);
+    const double fe = -MAZE_KE_EV_ANGSTROM * Q * a.inv_2h;
     const double Fex = fe * gx, Fey = fe * gy, Fez = fe * gz;
-    // --- S8: Tosi-Fumi pairs, minimum image, r < r_c. FP32 pre-filter with a
-    // margin, exact FP64 test and arithmetic for the survivors.
+    // --- S8: Tosi-Fumi pairs, minimum image, r < r_c. Candidates pass an
+    // FP32 pre-filter with a safety margin; survivors are queued per warp and
+    // evaluated 32 at a time in FP64 (exact cutoff test), so the FP64 pipe
+    // sees full warps instead of the ~10 % of lanes that pass the filter.
     const float4 pi32 = a.pos32[i];
     const float Lf = a.Lf;
+    int* q = s_queue[warp];
+    int qn = 0;
     double ftx = 0, fty = 0, ftz = 0, vtf = 0;
-    auto visit = [&](int j) {
-      if (j == i) return;
+    auto pair = [&](int j) {
       const float4 pj = a.pos32[j];
-      float dx = pj.x - pi32.x, dy = pj.y - pi32.y, dz = pj.z - pi32.z;
-      const float sx = rintf(dx / Lf), sy = rintf(dy / Lf), sz = rintf(dz / Lf);
-      dx -= sx * Lf;
-      dy -= sy * Lf;
-      dz -= sz * Lf;
-      if (dx * dx + dy * dy + dz * dz >= a.rc2_filter) return;
+      const float iL = a.inv_Lf;
+      const float sx = rintf((pj.x - pi32.x) * iL), sy = rintf((pj.y - pi32.y) * iL), sz = rintf((pj.z - pi32.z) * iL);
       const double ddx = (a.pos[j] - x) - (double)sx * a.L;
       const double ddy = (a.pos[n + j] - y) - (double)sy * a.L;
       const double ddz = (a.pos[2 * n + j] - z) - (double)sz * a.L;
@@ -258,6 +301,28 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(ForceArgs a) {
       fty -= fr * ddy;
       ftz -= fr * ddz;
       vtf += V;
+    };
+    auto offer = [&](int j, bool valid) {
+      bool pass = false;
+      if (valid && j != i) {
+        const float4 pj = a.pos32[j];
+        float dx = pj.x - pi32.x, dy = pj.y - pi32.y, dz = pj.z - pi32.z;
+        dx -= rintf(dx * a.inv_Lf) * Lf;
+        dy -= rintf(dy * a.inv_Lf) * Lf;
+        dz -= rintf(dz * a.inv_Lf) * Lf;
+        pass = dx * dx + dy * dy + dz * dz < a.rc2_filter;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, pass);
+      if (pass) q[qn + __popc(m & ((1u << lane) - 1u))] = j;
+      qn += __popc(m);
+      __syncwarp();
+      if (qn >= 32) {
+        pair(q[lane]);
+        __syncwarp();
+        if (lane < qn - 32) q[lane] = q[32 + lane];
+        __syncwarp();
+        qn -= 32;
+      }
     };
     if (a.nc >= 3) {
       const int nc = a.nc;
@@ -271,13 +336,17 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(ForceArgs a) {
             const int xx = (cx + dx + nc) % nc;
             const int cc = xx + nc * (yy + nc * zz);
             const int lo = a.cell_start[cc], hi = a.cell_start[cc + 1];
-            for (int u = lo + lane; u < hi; u += 32) visit(a.cell_ions[u]);
+            for (int u0 = lo; u0 < hi; u0 += 32) {
+              const int u = u0 + lane;
+              offer(u < hi ? a.cell_ions[u] : -1, u < hi);
+            }
           }
         }
       }
     } else {
-      for (int j = lane; j < n; j += 32) visit(j);
+      for (int j0 = 0; j0 < n; j0 += 32) offer(j0 + lane, j0 + lane < n);
     }
+    if (lane < qn) pair(q[lane]);
     ftx = warp_sum(ftx);
     fty = warp_sum(fty);
     ftz = warp_sum(ftz);

@@ -12,75 +12,29 @@
 // The stopping test is the paper's residual max_n |(M y - sigma_p)_n|
 // (Eq. res_poisson_maze) on the recursive residual, confirmed by one true
 // residual; a failed confirmation restarts CG from the true residual.
-// Grid-wide synchronisation uses a bounded barrier; every reduction sums the
-// block partials in the same fixed order in every block, so all blocks take
-// identical decisions and the result is bit-reproducible.
+// An iteration takes two grid rounds (flag-carrying reductions, see
+// grid_reduce): the direction update is fused into the stencil pass by
+// recomputing p_new at the six neighbours from r and a double-buffered p_old.
+// Every reduction combines the block partials in the same fixed order in
+// every block, so all blocks take identical decisions and the result is
+// bit-reproducible.
 #include <math.h>
 
 #include "maze_internal.cuh"
 
 namespace maze {
 
-namespace {
-
-// Block-level sums of up to 4 values, written as this block's partial.
-template <int K>
-__device__ __forceinline__ void block_partial(const double (&v)[K], const bool (&is_max)[K], double* part) {
-  __shared__ double s[kSolveThreads / 32][4];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double w[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) w[k] = is_max[k] ? warp_max(v[k]) : warp_sum(v[k]);
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < K; ++k) s[warp][k] = w[k];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      double acc = s[0][k];
-      for (int u = 1; u < kSolveThreads / 32; ++u) acc = is_max[k] ? fmax(acc, s[u][k]) : acc + s[u][k];
-      part[blockIdx.x * 4 + k] = acc;
-    }
-  }
-}
-
-// After the barrier: every block combines all partials in the same order.
-template <int K>
-__device__ __forceinline__ void grid_combine(const double* part, const bool (&is_max)[K], double (&out)[K]) {
-  __shared__ double s_out[4];
-  if (threadIdx.x < 32) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      double acc = is_max[k] ? 0.0 : 0.0;
-      for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
-        const double v = __ldcg(&part[b * 4 + k]);
-        acc = is_max[k] ? fmax(acc, v) : acc + v;
-      }
-      acc = is_max[k] ? warp_max(acc) : warp_sum(acc);
-      if (threadIdx.x == 0) s_out[k] = acc;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < K; ++k) out[k] = s_out[k];
-  __syncthreads();
-}
-
-}  // namespace
-
 __global__ void __launch_bounds__(kSolveThreads) k_cg_solve(SolveArgs a) {
-  unsigned epoch = 0;   // barrier count (thread 0)
-  int red = 0;          // reduction count: selects the partial buffer
+  unsigned epoch = 0;   // reduction rounds of this launch
   const int n = a.n, N = a.N;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
-  const size_t pbuf = (size_t)gridDim.x * 4;
   if (*a.gate != 0 || a.rec->status != MAZE_OK) return;
 
-  const bool sum3[3] = {false, true, false};     // (r.r, max|r|, sum y)
-  const bool sum1[1] = {false};
-  const bool sum2[2] = {false, true};
+  const bool m3[3] = {false, true, false};     // (r.r, max|r|, sum y)
+  const bool m1[1] = {false};
+  const bool m2[2] = {false, true};
+  double tot[3];
 
   // ---- S4 and the initial residual r0 = sigma_p - M y0
   {
@@ -111,12 +65,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_cg_solve(SolveArgs a) {
       ys += y[m];
     }
     const double v[3] = {rr, rmax, ys};
-    block_partial<3>(v, sum3, a.part + (red & 1) * pbuf);
+    if (!grid_reduce<3>(v, m3, a.recs, ++epoch, a.rec, tot)) return;
   }
-  if (!grid_barrier(a.bar, epoch, a.rec)) return;
-  double tot[3];
-  grid_combine<3>(a.part + (red & 1) * pbuf, sum3, tot);
-  ++red;
   double rho = tot[0], res = tot[1], ysum = tot[2];
   int it = 0;
   bool conv = res < a.tol;
@@ -124,84 +74,92 @@ __global__ void __launch_bounds__(kSolveThreads) k_cg_solve(SolveArgs a) {
   bool have_ysum = true;
   double beta = 0.0;
   bool finite = isfinite(res);
+  int cur = 0;          // p_old lives in p[cur], p_new goes to p[cur ^ 1]
 
   while (!conv && finite && it < a.max_iter) {
     have_ysum = false;
-    // phase A: p = r + beta p
-    for (int m = tid; m < n; m += stride) a.p[m] = fresh ? a.r[m] : a.r[m] + beta * a.p[m];
-    if (!grid_barrier(a.bar, epoch, a.rec)) return;
-    // phase B: Mp and p.Mp
+    // phase AB: p_new = r + beta p_old, here and at the six neighbours (from
+    // r and p_old, which no block writes in this phase), then Mp_new and the
+    // partial p_new.Mp_new. One grid round instead of a barrier between the
+    // direction update and the stencil.
+    double* pn = cur ? a.p : a.p1;
+    const double* po = cur ? a.p1 : a.p;
     {
       double pmp = 0;
-      const double* p = a.p;
+      const double* r = a.r;
       for (int m = tid; m < n; m += stride) {
         const Nbr b = neighbours(m, N);
-        const double pm = p[m];
-        const double mp = (p[b.xm] + p[b.xp]) + (p[b.ym] + p[b.yp]) + (p[b.zm] + p[b.zp]) - 6.0 * pm;
+        double c0, s6;
+        if (fresh) {
+          c0 = r[m];
+          s6 = (r[b.xm] + r[b.xp]) + (r[b.ym] + r[b.yp]) + (r[b.zm] + r[b.zp]);
+        } else {
+          c0 = r[m] + beta * po[m];
+          s6 = ((r[b.xm] + beta * po[b.xm]) + (r[b.xp] + beta * po[b.xp])) +
+               ((r[b.ym] + beta * po[b.ym]) + (r[b.yp] + beta * po[b.yp])) +
+               ((r[b.zm] + beta * po[b.zm]) + (r[b.zp] + beta * po[b.zp]));
+        }
+        const double mp = s6 - 6.0 * c0;
+        pn[m] = c0;
         a.Mp[m] = mp;
-        pmp += pm * mp;
+        pmp += c0 * mp;
       }
       const double v[1] = {pmp};
-      block_partial<1>(v, sum1, a.part + (red & 1) * pbuf);
-    }
-    if (!grid_barrier(a.bar, epoch, a.rec)) return;
-    double t1[1];
-    grid_combine<1>(a.part + (red & 1) * pbuf, sum1, t1);
-    ++red;
-    const double alpha = rho / t1[0];
-    // phase C: y += alpha p, r -= alpha Mp; r.r and max|r|
-    {
+      double t1[1], alpha;
+      const double rho_c = rho;
+      if (!grid_reduce<1>(v, m1, a.recs, ++epoch, a.rec, t1,
+                          [rho_c](const double* t) { return rho_c * recip_newton(t[0]); }, &alpha))
+        return;
+      // phase C: y += alpha p_new, r -= alpha Mp; r.r and max|r|
       double rr = 0, rmax = 0;
       for (int m = tid; m < n; m += stride) {
-        a.y[m] += alpha * a.p[m];
-        const double r = a.r[m] - alpha * a.Mp[m];
-        a.r[m] = r;
-        rr += r * r;
-        rmax = fmax(rmax, fabs(r));
+        a.y[m] += alpha * pn[m];
+        const double rv = a.r[m] - alpha * a.Mp[m];
+        a.r[m] = rv;
+        rr += rv * rv;
+        rmax = fmax(rmax, fabs(rv));
       }
-      const double v[2] = {rr, rmax};
-      block_partial<2>(v, sum2, a.part + (red & 1) * pbuf);
-    }
-    if (!grid_barrier(a.bar, epoch, a.rec)) return;
-    double t2[2];
-    grid_combine<2>(a.part + (red & 1) * pbuf, sum2, t2);
-    ++red;
-    ++it;
-    res = t2[1];
-    finite = isfinite(res) && isfinite(t2[0]);
-    if (!finite) break;
-    if (res < a.tol) {
-      // confirm with the true residual sigma_p - M y (also gives sum y)
-      double rr = 0, rmax = 0, ys = 0;
-      const double* y = a.y;
-      for (int m = tid; m < n; m += stride) {
-        const Nbr b = neighbours(m, N);
-        const double My = (y[b.xm] + y[b.xp]) + (y[b.ym] + y[b.yp]) + (y[b.zm] + y[b.zp]) - 6.0 * y[m];
-        const double r = a.sigma[m] - My;
-        a.r[m] = r;
-        rr += r * r;
-        rmax = fmax(rmax, fabs(r));
-        ys += y[m];
-      }
-      const double v[3] = {rr, rmax, ys};
-      block_partial<3>(v, sum3, a.part + (red & 1) * pbuf);
-      if (!grid_barrier(a.bar, epoch, a.rec)) return;
-      grid_combine<3>(a.part + (red & 1) * pbuf, sum3, tot);
-      ++red;
-      res = tot[1];
-      ysum = tot[2];
-      have_ysum = true;
+      const double v2[2] = {rr, rmax};
+      double t2[2], beta_new;
+      const double rho_old = rho;
+      if (!grid_reduce<2>(v2, m2, a.recs, ++epoch, a.rec, t2,
+                          [rho_old](const double* t) { return t[0] * recip_newton(rho_old); }, &beta_new))
+        return;
+      cur ^= 1;
+      ++it;
+      res = t2[1];
+      finite = isfinite(res) && isfinite(t2[0]);
+      if (!finite) break;
       if (res < a.tol) {
-        conv = true;
-        break;
+        // confirm with the true residual sigma_p - M y (also gives sum y)
+        double rr3 = 0, rmax3 = 0, ys = 0;
+        const double* y = a.y;
+        for (int m = tid; m < n; m += stride) {
+          const Nbr b = neighbours(m, N);
+          const double My = (y[b.xm] + y[b.xp]) + (y[b.ym] + y[b.yp]) + (y[b.zm] + y[b.zp]) - 6.0 * y[m];
+          const double rv = a.sigma[m] - My;
+          a.r[m] = rv;
+          rr3 += rv * rv;
+          rmax3 = fmax(rmax3, fabs(rv));
+          ys += y[m];
+        }
+        const double v3[3] = {rr3, rmax3, ys};
+        if (!grid_reduce<3>(v3, m3, a.recs, ++epoch, a.rec, tot)) return;
+        res = tot[1];
+        ysum = tot[2];
+        have_ysum = true;
+        if (res < a.tol) {
+          conv = true;
+          break;
+        }
+        rho = tot[0];
+        fresh = true;
+        continue;
       }
-      rho = tot[0];
-      fresh = true;
-      continue;
+      beta = beta_new;
+      rho = t2[0];
+      fresh = false;
     }
-    beta = t2[0] / rho;
-    rho = t2[0];
-    fresh = false;
   }
   if (!have_ysum) {
     // stopped at max_iter or on a non-finite value: true residual and sum y
@@ -210,21 +168,18 @@ __global__ void __launch_bounds__(kSolveThreads) k_cg_solve(SolveArgs a) {
     for (int m = tid; m < n; m += stride) {
       const Nbr b = neighbours(m, N);
       const double My = (y[b.xm] + y[b.xp]) + (y[b.ym] + y[b.yp]) + (y[b.zm] + y[b.zp]) - 6.0 * y[m];
-      const double r = a.sigma[m] - My;
-      rr += r * r;
-      rmax = fmax(rmax, fabs(r));
+      const double rv = a.sigma[m] - My;
+      rr += rv * rv;
+      rmax = fmax(rmax, fabs(rv));
       ys += y[m];
     }
     const double v[3] = {rr, rmax, ys};
-    block_partial<3>(v, sum3, a.part + (red & 1) * pbuf);
-    if (!grid_barrier(a.bar, epoch, a.rec)) return;
-    grid_combine<3>(a.part + (red & 1) * pbuf, sum3, tot);
-    ++red;
+    if (!grid_reduce<3>(v, m3, a.recs, ++epoch, a.rec, tot)) return;
     res = tot[1];
     ysum = tot[2];
   }
   // ---- S6: remove the constant mode of y and correct phi
-  const double ybar = ysum / (double)n;
+  const double ybar = ysum * a.inv_n;
   for (int m = tid; m < n; m += stride) {
     const double yv = a.y[m] - ybar;
     a.y[m] = yv;
@@ -248,6 +203,7 @@ int solve_blocks(int n_points) {
   if (per_sm < 1) per_sm = 1;
   int want = (n_points + kSolveThreads - 1) / kSolveThreads;
   int cap = sms * per_sm;
+  if (cap > kMaxReduceBlocks) cap = kMaxReduceBlocks;
   return want < cap ? want : cap;
 }
 

@@ -84,6 +84,7 @@ def _cfg(**over):
     (dict(tol=-1.0), "tol"),
     (dict(max_iter=0), "max_iter"),
     (dict(solver=7), "solver"),
+    (dict(solver=1, mg_pre=0), "mg_pre"),
     (dict(precision=9), "precision"),
 ])
 def test_invalid_config_rejected(lib, over, msg):
