@@ -174,7 +174,7 @@ def bench_reference(args, w):
 def config_dict(w, args):
     return {"workload": f"molten NaCl {w.n_ions} ions, L={w.L} A, {w.N}^3 grid, {w.T:.0f} K, dt={w.dt} fs, "
                         f"tol={w.tol:g}, P={w.order}, r_cut={w.rc} A",
-            "n_ions": w.n_ions, "grid": w.N, "solver": args.solver, "precision": "fp64",
+            "n_ions": w.n_ions, "grid": w.N, "solver": args.solver, "precision": getattr(args, "precision", "fp64"),
             "l2": "flushed between timed steps (256 MiB write outside the step events)"}
 
 
@@ -186,6 +186,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="nacl1000", choices=["nacl64", "nacl1000", "nacl512000"])
     ap.add_argument("--solver", default="mg", choices=["cg", "mg"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -213,8 +214,9 @@ def main():
     tf = synth.tosi_fumi_nacl()
     stream = torch.cuda.Stream(device=dev)
     solver = M.MAZE_SOLVER_MG if args.solver == "mg" else M.MAZE_SOLVER_CG
+    precision = M.MAZE_MIXED if args.precision == "mixed" else M.MAZE_FP64
     sim = M.MazeSim(pos, vel, types, w.L, w.N, tf, r_cut=w.rc, dt=w.dt, tol=w.tol, order=w.order,
-                    solver=solver, stream=stream.cuda_stream)
+                    solver=solver, precision=precision, stream=stream.cuda_stream)
     sim.set_timing(True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     s0 = sim.stats()
@@ -224,6 +226,7 @@ def main():
     s1 = sim.stats()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     solve_ms = []
+    phase_ms = []
     timing_error = None
     clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
     clocks.start()
@@ -239,7 +242,9 @@ def main():
             sim.step_async(1)
             ev[k][1].record(stream)
         try:
-            solve_ms.append(sim.timing()[2])     # synchronises: reads the in-graph phase events
+            ph = sim.timing()                    # synchronises: reads the in-graph phase events
+            solve_ms.append(ph[2])
+            phase_ms.append(ph)
         except Exception as e:                   # timing events unavailable: roofline left null
             timing_error = str(e)
     torch.cuda.synchronize()
@@ -314,6 +319,8 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(w, args),
             "p50_us": 1e3 * float(np.percentile(step_ms, 50)), "p99_us": 1e3 * float(np.percentile(step_ms, 99)),
             "iters_per_step": iters, "force_error": ferr,
+            "phase_us": dict(zip(["move_spread", "cells", "solve", "forces"],
+                                 [round(1e3 * float(v), 2) for v in np.mean(phase_ms, axis=0)])) if phase_ms else None,
             "solve_gbs": achieved, "solve_us": 1e6 * mean_solve_s,
             "roofline": {"kernel": "k_mg_solve" if args.solver == "mg" else "k_cg_solve", "bound": "hbm", "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,

@@ -50,6 +50,7 @@ struct maze_ctx {
   int* type = nullptr;
   float4* pos32 = nullptr;
   double* wbuf = nullptr;   // [n][3][4] B-spline weights of the current positions
+  float* wbuf32 = nullptr;  // FP32 weights (mixed precision)
   int4* wbase = nullptr;
   // grid
   unsigned long long* qfix = nullptr;
@@ -63,6 +64,11 @@ struct maze_ctx {
   // multigrid
   MgArgs mg = {};
   double *mg_x = nullptr, *mg_b = nullptr, *mg_r = nullptr, *mg_g = nullptr;
+  // mixed precision: phi, y, sigma hold double-float pairs (float2, 8 B)
+  bool mixed = false;
+  MixedArgs mx = {};
+  int mx_cluster = 0, mx_blocks = 0;
+  float *mx_e0 = nullptr, *mx_r0 = nullptr, *mx_lx = nullptr, *mx_lb = nullptr, *mx_lr = nullptr, *mx_g = nullptr;
   int sblocks = 0;
   // cells
   int nc = 0, ncell = 0;
@@ -113,7 +119,10 @@ maze_status validate(const maze_config* c) {
   if (c->solver == MAZE_SOLVER_MG && (c->mg_pre < 1 || c->mg_post < 1 || c->mg_pre > 8 || c->mg_post > 8))
     return fail(MAZE_ERR_INVALID, "mg_pre and mg_post must be in [1, 8]");
   if (c->order_P != 2 && c->order_P != 4) return fail(MAZE_ERR_INVALID, "order_P must be 2 or 4");
-  if (c->precision != MAZE_FP64) return fail(MAZE_ERR_INVALID, "precision: only MAZE_FP64 is available in this build");
+  if (c->precision != MAZE_FP64 && c->precision != MAZE_MIXED)
+    return fail(MAZE_ERR_INVALID, "precision must be MAZE_FP64 or MAZE_MIXED");
+  if (c->precision == MAZE_MIXED && c->solver != MAZE_SOLVER_MG)
+    return fail(MAZE_ERR_INVALID, "precision MAZE_MIXED runs the multigrid solver (MAZE_SOLVER_MG)");
   if (!c->pos || !c->vel || !c->type) return fail(MAZE_ERR_INVALID, "pos, vel and type must be non-NULL");
   if (!(c->mass[0] > 0) || !(c->mass[1] > 0)) return fail(MAZE_ERR_INVALID, "masses must be > 0");
   double qsum = 0, qabs = 0;
@@ -166,6 +175,7 @@ IonArgs ion_args(maze_ctx* c, int do_move, int do_spread) {
   a.rec = c->rec;
   a.gate = c->gate;
   a.wbuf = c->wbuf;
+  a.wbuf32 = c->mixed ? c->wbuf32 : nullptr;
   a.wbase = c->wbase;
   return a;
 }
@@ -199,6 +209,9 @@ ForceArgs force_args(maze_ctx* c, const double* phi, int do_kick, int count_step
   a.pos32 = c->pos32;
   a.type = c->type;
   a.phi = phi;
+  a.phi_df = c->mixed ? 1 : 0;
+  a.mixed = c->mixed ? 1 : 0;
+  a.wbuf32 = c->wbuf32;
   a.wbuf = c->wbuf;
   a.wbase = c->wbase;
   a.nc = c->nc;
@@ -223,6 +236,15 @@ ForceArgs force_args(maze_ctx* c, const double* phi, int do_kick, int count_step
   }
   a.B = g.tf_B;
   a.rc2 = rc * rc;
+  for (int k = 0; k < 3; ++k) {
+    a.Af[k] = (float)a.A[k];
+    a.sf[k] = (float)a.s[k];
+    a.Cf[k] = (float)a.C[k];
+    a.Df[k] = (float)a.D[k];
+    a.Vcf[k] = (float)a.Vc[k];
+  }
+  a.Bf = (float)g.tf_B;
+  a.rc2f = (float)(rc * rc);
   const double rcf = rc + 1e-3 + 1e-6 * c->L;
   a.rc2_filter = (float)(rcf * rcf);
   a.Lf = (float)c->L;
@@ -266,9 +288,30 @@ SolveArgs solve_args(maze_ctx* c, int zero_phi, double* q_out) {
 
 // --- sequences ------------------------------------------------------------
 
+MixedArgs mixed_args(maze_ctx* c, int zero_phi, double* q_out) {
+  MixedArgs a = c->mx;
+  a.phi_k = reinterpret_cast<const float2*>(c->phi[c->ik]);
+  a.phi_km1 = reinterpret_cast<const float2*>(c->phi[(c->ik + 1) % 3]);
+  a.phi_out = reinterpret_cast<float2*>(c->phi[(c->ik + 2) % 3]);
+  a.sigma = reinterpret_cast<float2*>(c->sigma);
+  a.y = reinterpret_cast<float2*>(c->y);
+  a.qfix = c->qfix;
+  a.q_out = q_out;
+  a.max_iter = zero_phi ? c->max_iter_init : c->cfg.max_iter;
+  a.zero_phi = zero_phi;
+  a.recs = c->recs;
+  a.bar = c->bar;
+  a.rec = c->rec;
+  a.gate = c->gate;
+  return a;
+}
+
 maze_status enqueue_solve(maze_ctx* c, int zero_phi, double* q_out) {
   CK(cudaMemsetAsync(c->recs, 0, c->recs_bytes, c->stream));
-  if (c->cfg.solver == MAZE_SOLVER_MG) {
+  if (c->mixed) {
+    CK(cudaMemsetAsync(c->bar, 0, sizeof(unsigned), c->stream));
+    CK(launch_mixed_solve(mixed_args(c, zero_phi, q_out), c->mx_cluster, c->mx_blocks, c->stream));
+  } else if (c->cfg.solver == MAZE_SOLVER_MG) {
     CK(cudaMemsetAsync(c->bar, 0, sizeof(unsigned), c->stream));
     CK(launch_mg_solve(solve_args(c, zero_phi, q_out), c->mg, c->sblocks, c->stream));
   } else {
@@ -467,6 +510,7 @@ maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
   AL(c->type, (size_t)n);
   AL(c->pos32, (size_t)n);
   AL(c->wbuf, 12 * (size_t)n);
+  AL(c->wbuf32, 12 * (size_t)n);
   AL(c->wbase, (size_t)n);
   AL(c->qfix, ng);
   AL(c->qd, ng);
@@ -506,6 +550,53 @@ maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
     g.r = c->mg_r;
     g.gker = c->mg_g;
   }
+  std::vector<float> gkf;
+  if (cfg->precision == MAZE_MIXED) {
+    c->mixed = true;
+    MixedArgs& m = c->mx;
+    m.N = c->N;
+    m.n = (int)ng;
+    m.L = c->mg.L;
+    size_t tot = 0;
+    for (int l = 0; l < m.L; ++l) {
+      m.Nl[l] = c->mg.Nl[l];
+      m.off[l] = c->mg.off[l];
+      m.lg[l] = -1;
+      for (int b = 1; b < 16; ++b)
+        if ((1 << b) == m.Nl[l]) m.lg[l] = b;
+      tot += (size_t)m.Nl[l] * m.Nl[l] * m.Nl[l];
+    }
+    m.nu1 = cfg->mg_pre;
+    m.nu2 = cfg->mg_post;
+    AL(c->mx_e0, ng);
+    AL(c->mx_r0, ng);
+    AL(c->mx_lx, tot);
+    AL(c->mx_lb, tot);
+    AL(c->mx_lr, tot);
+    gkf.assign(gk.begin(), gk.end());
+    AL(c->mx_g, gkf.size());
+    m.e0 = c->mx_e0;
+    m.r0 = c->mx_r0;
+    m.lx = c->mx_lx;
+    m.lb = c->mx_lb;
+    m.lr = c->mx_lr;
+    m.gkerf = c->mx_g;
+    const double cs = c->h / (4.0 * kPi), cp = 4.0 * kPi / c->h;
+    m.c_sig_h = (float)cs;
+    m.c_sig_l = (float)(cs - (double)m.c_sig_h);
+    m.c_phi_h = (float)cp;
+    m.c_phi_l = (float)(cp - (double)m.c_phi_h);
+    m.tol = cfg->tol;
+    m.inv_n = 1.0 / (double)ng;
+    // one cluster for boxes up to 64^3 (cluster barriers), a cooperative
+    // grid above
+    if (c->N <= 64) {
+      c->mx_cluster = mixed_cluster_size();
+    } else {
+      c->mx_blocks = mixed_grid_blocks((int)ng);
+      if (c->mx_blocks > c->sblocks) c->mx_blocks = c->sblocks;
+    }
+  }
   AL(c->cell_of, (size_t)n);
   if (c->nc >= 3) {
     AL(c->cell_count, (size_t)c->ncell);
@@ -542,6 +633,7 @@ maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
   CKC(cudaMemcpyAsync(c->vel, tmp.data(), tmp.size() * 8, cudaMemcpyHostToDevice, st));
   CKC(cudaMemcpyAsync(c->type, cfg->type, (size_t)n * 4, cudaMemcpyHostToDevice, st));
   if (!gk.empty()) CKC(cudaMemcpyAsync(c->mg_g, gk.data(), gk.size() * 8, cudaMemcpyHostToDevice, st));
+  if (!gkf.empty()) CKC(cudaMemcpyAsync(c->mx_g, gkf.data(), gkf.size() * 4, cudaMemcpyHostToDevice, st));
   CKC(cudaMemsetAsync(c->force, 0, 3 * (size_t)n * 8, st));
   CKC(cudaMemsetAsync(c->force_el, 0, 3 * (size_t)n * 8, st));
   CKC(cudaMemsetAsync(c->qfix, 0, ng * 8, st));
@@ -720,6 +812,14 @@ maze_status maze_get(maze_ctx* c, int32_t what, double* out) {
   } else {
     CK(cudaMemcpyAsync(out, src, c->ng * 8, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (c->mixed && what != MAZE_CHARGE) {
+      // double-float pairs (hi, lo) -> hi + lo
+      for (size_t i = 0; i < c->ng; ++i) {
+        float2 v;
+        memcpy(&v, &out[i], 8);
+        out[i] = (double)v.x + (double)v.y;
+      }
+    }
   }
   return MAZE_OK;
 }
@@ -746,6 +846,15 @@ maze_status maze_set(maze_ctx* c, int32_t what, const double* in) {
         tmp[(size_t)d * n + i] = what == MAZE_POS ? wrap_host(v, c->L) : v;
       }
     CK(cudaMemcpyAsync(dst, tmp.data(), tmp.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  } else if (c->mixed) {
+    // double -> double-float pair (hi = nearest float, lo = remainder)
+    std::vector<float2> tmp(c->ng);
+    for (size_t i = 0; i < c->ng; ++i) {
+      const float hi = (float)in[i];
+      tmp[i] = make_float2(hi, (float)(in[i] - (double)hi));
+    }
+    CK(cudaMemcpyAsync(dst, tmp.data(), c->ng * 8, cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
   } else {
     CK(cudaMemcpyAsync(dst, in, c->ng * 8, cudaMemcpyHostToDevice, c->stream));

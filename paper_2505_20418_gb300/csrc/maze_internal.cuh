@@ -54,6 +54,7 @@ struct IonArgs {
   maze_stats* rec;
   int* gate;             // set to 1 when the step starts after an error
   double* wbuf;          // [n][3][4] B-spline weights of the new positions
+  float* wbuf32;         // [n][3][4] FP32 weights (mixed precision) or nullptr
   int4* wbase;           // [n] first support node per axis
 };
 
@@ -78,9 +79,13 @@ struct ForceArgs {
   double* force_el;      // [3][n] electrostatic force (in: previous, out: new)
   const float4* pos32;
   const int* type;
-  const double* phi;     // [N^3]
+  const double* phi;     // [N^3] doubles, or double-float pairs when phi_df
+  int phi_df;            // 1: phi holds (hi, lo) float pairs (mixed precision)
   const double* wbuf;    // [n][3][4] weights written by k_ion_update
+  const float* wbuf32;   // [n][3][4] FP32 weights (mixed precision)
   const int4* wbase;     // [n]
+  int mixed;             // 1: FP32 gather and pair arithmetic
+  float Af[3], sf[3], Cf[3], Df[3], Vcf[3], Bf, rc2f;
   int nc;                // cells per edge; < 3 means all pairs
   const int* cell_start;
   const int* cell_ions;
@@ -141,6 +146,40 @@ struct MgArgs {
   int nu1, nu2;
 };
 
+// Mixed-precision solve (double-float outer iteration, FP32 V-cycle).
+constexpr int kMixedThreads = 1024;
+struct MixedArgs {
+  int N, n;
+  const float2* phi_k;     // double-float grids (hi, lo)
+  const float2* phi_km1;
+  float2* phi_out;
+  float2* sigma;
+  float2* y;
+  unsigned long long* qfix;  // read and cleared
+  double* q_out;           // optional copy of q
+  float* e0;               // [N^3] correction on level 0
+  float* r0;               // [N^3] outer residual (FP32) = level-0 rhs
+  float* lx;               // levels >= 1: corrections (packed, off[l])
+  float* lb;               // levels >= 1: right-hand sides
+  float* lr;               // all levels: residuals
+  const float* gkerf;      // [Nc^3] coarsest pseudo-inverse kernel
+  int L;
+  int Nl[kMaxLevels];
+  int lg[kMaxLevels];      // log2(N_l) for powers of two, else -1
+  size_t off[kMaxLevels];
+  int nu1, nu2;
+  float c_sig_h, c_sig_l;  // h/4pi as a double-float
+  float c_phi_h, c_phi_l;  // 4pi/h as a double-float
+  double tol;
+  int max_iter;
+  double inv_n;
+  int zero_phi;
+  LLRec* recs;             // grid form only
+  unsigned* bar;           // grid form only
+  maze_stats* rec;
+  const int* gate;
+};
+
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t s);   // k_move, then k_spread if a.qfix
 cudaError_t launch_q_to_double(const unsigned long long* qfix, double* q, int n, cudaStream_t s);
@@ -151,6 +190,9 @@ cudaError_t launch_cg_solve(const SolveArgs& a, int blocks, cudaStream_t s);
 int solve_blocks(int n_points);
 cudaError_t launch_mg_solve(const SolveArgs& a, const MgArgs& g, int blocks, cudaStream_t s);
 int mg_blocks(int n_points);
+cudaError_t launch_mixed_solve(const MixedArgs& a, int cluster, int blocks, cudaStream_t s);
+int mixed_cluster_size();
+int mixed_grid_blocks(int n_points);
 // Sets the message returned by maze_last_error on the calling thread.
 void set_last_error(const char* msg);
 

@@ -13,24 +13,34 @@ namespace maze {
 // The support starts at node floor(u) - (P/2 - 1); t = u - floor(u).
 // P = 2: linear B-spline (1 - t, t).
 // P = 4: cubic B-spline ((1-t)^3, 3t^3 - 6t^2 + 4, -3t^3 + 3t^2 + 3t + 1, t^3) / 6.
-__device__ __forceinline__ int axis_weights(double u, int P, int N, double* w) {
+// Split u into the first support node and the fractional offset t.
+__device__ __forceinline__ int axis_split(double u, int P, int N, double& t) {
   const double fl = floor(u);
-  const double t = u - fl;
+  t = u - fl;
   int first = (int)fl - (P / 2 - 1);
-  if (P == 2) {
-    w[0] = 1.0 - t;
-    w[1] = t;
-  } else {
-    const double t2 = t * t, t3 = t2 * t;
-    const double s = 1.0 - t;
-    w[0] = s * s * s * (1.0 / 6.0);
-    w[1] = (3.0 * t3 - 6.0 * t2 + 4.0) * (1.0 / 6.0);
-    w[2] = (-3.0 * t3 + 3.0 * t2 + 3.0 * t + 1.0) * (1.0 / 6.0);
-    w[3] = t3 * (1.0 / 6.0);
-  }
   if (first < 0) first += N;
   if (first >= N) first -= N;
   return first;
+}
+
+// The P weights at fractional offset t (R = double, or float in mixed mode);
+// for P = 2 the two unused slots are zero.
+template <typename R>
+__device__ __forceinline__ void bspline_weights(R t, int P, R* w) {
+  if (P == 2) {
+    w[0] = R(1) - t;
+    w[1] = t;
+    w[2] = R(0);
+    w[3] = R(0);
+  } else {
+    const R t2 = t * t, t3 = t2 * t;
+    const R s = R(1) - t;
+    const R sixth = R(1) / R(6);
+    w[0] = s * s * s * sixth;
+    w[1] = (R(3) * t3 - R(6) * t2 + R(4)) * sixth;
+    w[2] = (R(-3) * t3 + R(3) * t2 + R(3) * t + R(1)) * sixth;
+    w[3] = t3 * sixth;
+  }
 }
 
 __device__ __forceinline__ int wrap_idx(int a, int N) { return a >= N ? a - N : a; }
@@ -51,7 +61,6 @@ __global__ void __launch_bounds__(kIonThreads) k_move(IonArgs a) {
   const bool skip = a.rec->status != MAZE_OK;
   if (i == 0) *a.gate = skip ? 1 : 0;
   if (skip) return;
-  __shared__ double s_w[kIonThreads][12];
   const int N = a.N, P = a.P;
   if (i < a.n) {
     double x = a.pos[i], y = a.pos[a.n + i], z = a.pos[2 * a.n + i];
@@ -80,35 +89,71 @@ __global__ void __launch_bounds__(kIonThreads) k_move(IonArgs a) {
       a.cell_of[i] = c;
       atomicAdd(&a.cell_count[c], 1);
     }
-    double* w = s_w[threadIdx.x];
-    const int fx = axis_weights(x * a.inv_h, P, N, w);
-    const int fy = axis_weights(y * a.inv_h, P, N, w + 4);
-    const int fz = axis_weights(z * a.inv_h, P, N, w + 8);
-    if (P == 2) w[2] = w[3] = w[6] = w[7] = w[10] = w[11] = 0.0;
-    double* gw = a.wbuf + (size_t)i * 12;
+    double tx, ty, tz;
+    const int fx = axis_split(x * a.inv_h, P, N, tx);
+    const int fy = axis_split(y * a.inv_h, P, N, ty);
+    const int fz = axis_split(z * a.inv_h, P, N, tz);
+    if (a.wbuf32) {
+      // mixed precision: FP32 weights from the exact fractional offsets
+      float w[12];
+      bspline_weights<float>((float)tx, P, w);
+      bspline_weights<float>((float)ty, P, w + 4);
+      bspline_weights<float>((float)tz, P, w + 8);
+      float4* gw = reinterpret_cast<float4*>(a.wbuf32 + (size_t)i * 12);
+      gw[0] = make_float4(w[0], w[1], w[2], w[3]);
+      gw[1] = make_float4(w[4], w[5], w[6], w[7]);
+      gw[2] = make_float4(w[8], w[9], w[10], w[11]);
+    } else {
+      double w[12];
+      bspline_weights<double>(tx, P, w);
+      bspline_weights<double>(ty, P, w + 4);
+      bspline_weights<double>(tz, P, w + 8);
+      double* gw = a.wbuf + (size_t)i * 12;
 #pragma unroll
-    for (int k = 0; k < 12; ++k) gw[k] = w[k];
+      for (int k = 0; k < 12; ++k) gw[k] = w[k];
+    }
     a.wbase[i] = make_int4(fx, fy, fz, 0);
   }
 }
 
 // S3: q_n += Q W(r - r_n), W = w_x w_y w_z over the P^3 support, one warp per
-// ion (lane l takes support points l, l+32, ...), fixed-point atomics.
+// ion (lane l takes support points l and l+32), fixed-point atomics. The
+// ion's contributions are made to sum exactly to Q 2^50 (the rounding
+// remainder, found with an exact warp integer sum, goes to support point 0),
+// so a neutral system stays exactly neutral on the grid: the periodic M has
+// no inverse on the constant mode, and a rounding net charge would put a floor
+// under the constraint residual.
 __global__ void __launch_bounds__(kSpreadThreads) k_spread(IonArgs a) {
   if (*a.gate) return;
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * (kSpreadThreads / 32) + (threadIdx.x >> 5);
   if (i >= a.n) return;
   const int N = a.N, P = a.P, P3 = P * P * P;
-  const double* w = a.wbuf + (size_t)i * 12;
   const int4 b = a.wbase[i];
   const double Q = a.type[i] ? a.charge1 : a.charge0;
-  for (int sidx = lane; sidx < P3; sidx += 32) {
+  long long v[2] = {0, 0};
+  int idx[2] = {-1, -1};
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int sidx = lane + 32 * u;
+    if (sidx >= P3) continue;
     const int ia = sidx % P, ib = (sidx / P) % P, ic = sidx / (P * P);
-    const double v = Q * w[8 + ic] * w[4 + ib] * w[ia];
+    if (a.wbuf32) {
+      // mixed precision: FP32 products
+      const float* w = a.wbuf32 + (size_t)i * 12;
+      v[u] = __float2ll_rn((float)Q * w[8 + ic] * w[4 + ib] * w[ia] * (float)kQScale);
+    } else {
+      const double* w = a.wbuf + (size_t)i * 12;
+      v[u] = __double2ll_rn(Q * w[8 + ic] * w[4 + ib] * w[ia] * kQScale);
+    }
     const int ix = wrap_idx(b.x + ia, N), iy = wrap_idx(b.y + ib, N), iz = wrap_idx(b.z + ic, N);
-    atomicAdd(&a.qfix[((size_t)iz * N + iy) * N + ix], (unsigned long long)__double2ll_rn(v * kQScale));
+    idx[u] = (int)(((size_t)iz * N + iy) * N + ix);
   }
+  const long long total = warp_isum(v[0] + v[1]);
+  if (lane == 0) v[0] += __double2ll_rn(Q * kQScale) - total;
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+    if (idx[u] >= 0) atomicAdd(&a.qfix[idx[u]], (unsigned long long)v[u]);
 }
 
 __global__ void k_q_to_double(const unsigned long long* qfix, double* q, int n) {
@@ -250,31 +295,80 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(ForceArgs a) {
     const double Q = t ? a.charge1 : a.charge0;
     // --- S7: Eq. F_nostra, F = -k_e Q sum_n W (phi_{n+e} - phi_{n-e}) / 2h,
     // with the weights k_ion_update stored for this position
-    const double* w = a.wbuf + (size_t)i * 12;
     const int4 first = a.wbase[i];
     const int P3 = P * P * P;
     double gx = 0, gy = 0, gz = 0, vd = 0;
     const size_t NN = (size_t)N * N;
-    for (int sidx = lane; sidx < P3; sidx += 32) {
-      const int ia = sidx % P, ib = (sidx / P) % P, ic = sidx / (P * P);
-      const int ix = wrap_idx(first.x + ia, N), iy = wrap_idx(first.y + ib, N), iz = wrap_idx(first.z + ic, N);
-      const double wt = w[ia] * w[4 + ib] * w[8 + ic];
-      const size_t row = iz * NN + (size_t)iy * N;
-      const double* ph = a.phi;
-      const double px = ph[row + (ix == N - 1 ? 0 : ix + 1)] - ph[row + (ix == 0 ? N - 1 : ix - 1)];
-      const double py = ph[iz * NN + (size_t)(iy == N - 1 ? 0 : iy + 1) * N + ix] -
-                        ph[iz * NN + (size_t)(iy == 0 ? N - 1 : iy - 1) * N + ix];
-      const double pz = ph[(size_t)(iz == N - 1 ? 0 : iz + 1) * NN + (size_t)iy * N + ix] -
-                        ph[(size_t)(iz == 0 ? N - 1 : iz - 1) * NN + (size_t)iy * N + ix];
-      gx += wt * px;
-      gy += wt * py;
-      gz += wt * pz;
-      vd += wt * ph[row + ix];
+    if (a.mixed) {
+      // mixed precision: FP32 weights, differences of the double-float
+      // potential in FP32, FP32 sums
+      const float* w = a.wbuf32 + (size_t)i * 12;
+      const float2* f = reinterpret_cast<const float2*>(a.phi);
+      float sx = 0.f, sy = 0.f, sz = 0.f, s0 = 0.f;
+      for (int sidx = lane; sidx < P3; sidx += 32) {
+        const int ia = sidx % P, ib = (sidx / P) % P, ic = sidx / (P * P);
+        const int ix = wrap_idx(first.x + ia, N), iy = wrap_idx(first.y + ib, N), iz = wrap_idx(first.z + ic, N);
+        const float wt = w[ia] * w[4 + ib] * w[8 + ic];
+        const size_t row = iz * NN + (size_t)iy * N;
+        const float2 xp = f[row + (ix == N - 1 ? 0 : ix + 1)], xm = f[row + (ix == 0 ? N - 1 : ix - 1)];
+        const float2 yp = f[iz * NN + (size_t)(iy == N - 1 ? 0 : iy + 1) * N + ix];
+        const float2 ym = f[iz * NN + (size_t)(iy == 0 ? N - 1 : iy - 1) * N + ix];
+        const float2 zp = f[(size_t)(iz == N - 1 ? 0 : iz + 1) * NN + (size_t)iy * N + ix];
+        const float2 zm = f[(size_t)(iz == 0 ? N - 1 : iz - 1) * NN + (size_t)iy * N + ix];
+        const float2 c0 = f[row + ix];
+        sx += wt * ((xp.x - xm.x) + (xp.y - xm.y));
+        sy += wt * ((yp.x - ym.x) + (yp.y - ym.y));
+        sz += wt * ((zp.x - zm.x) + (zp.y - zm.y));
+        s0 += wt * (c0.x + c0.y);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      }
+      gx = sx;
+      gy = sy;
+      gz = sz;
+      vd = s0;
+    } else {
+      const double* w = a.wbuf + (size_t)i * 12;
+      for (int sidx = lane; sidx < P3; sidx += 32) {
+        const int ia = sidx % P, ib = (sidx / P) % P, ic = sidx / (P * P);
+        const int ix = wrap_idx(first.x + ia, N), iy = wrap_idx(first.y + ib, N), iz = wrap_idx(first.z + ic, N);
+        const double wt = w[ia] * w[4 + ib] * w[8 + ic];
+        const size_t row = iz * NN + (size_t)iy * N;
+        const size_t ixp = row + (ix == N - 1 ? 0 : ix + 1), ixm = row + (ix == 0 ? N - 1 : ix - 1);
+        const size_t iyp = iz * NN + (size_t)(iy == N - 1 ? 0 : iy + 1) * N + ix;
+        const size_t iym = iz * NN + (size_t)(iy == 0 ? N - 1 : iy - 1) * N + ix;
+        const size_t izp = (size_t)(iz == N - 1 ? 0 : iz + 1) * NN + (size_t)iy * N + ix;
+        const size_t izm = (size_t)(iz == 0 ? N - 1 : iz - 1) * NN + (size_t)iy * N + ix;
+        double px, py, pz, p0;
+        if (a.phi_df) {
+          // double-float potential: differences of the (hi, lo) pairs in FP32
+          const float2* f = reinterpret_cast<const float2*>(a.phi);
+          const float2 xp = f[ixp], xm = f[ixm], yp = f[iyp], ym = f[iym], zp = f[izp], zm = f[izm], c0 = f[row + ix];
+          px = (double)((xp.x - xm.x) + (xp.y - xm.y));
+          py = (double)((yp.x - ym.x) + (yp.y - ym.y));
+          pz = (double)((zp.x - zm.x) + (zp.y - zm.y));
+          p0 = (double)c0.x + (double)c0.y;
+        } else {
+          const double* ph = a.phi;
+          px = ph[ixp] - ph[ixm];
+          py = ph[iyp] - ph[iym];
+          pz = ph[izp] - ph[izm];
+          p0 = ph[row + ix];
+        }
+        gx += wt * px;
+        gy += wt * py;
+        gz += wt * pz;
+        vd += wt * p0;
+      }
+      gx = warp_sum(gx);
+      gy = warp_sum(gy);
+      gz = warp_sum(gz);
+      vd = warp_sum(vd);
     }
-    gx = warp_sum(gx);
-    gy = warp_sum(gy);
-    gz = warp_sum(gz);
-    vd = warp_sum(vd);
     const double fe = -MAZE_KE_EV_ANGSTROM * Q * a.inv_2h;
     const double Fex = fe * gx, Fey = fe * gy, Fez = fe * gz;
     // --- S8: Tosi-Fumi pairs, minimum image, r < r_c. Candidates pass an
@@ -286,8 +380,34 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(ForceArgs a) {
     int* q = s_queue[warp];
     int qn = 0;
     double ftx = 0, fty = 0, ftz = 0, vtf = 0;
+    float ftxf = 0.f, ftyf = 0.f, ftzf = 0.f, vtff = 0.f;
     auto pair = [&](int j) {
       const float4 pj = a.pos32[j];
+      if (a.mixed) {
+        // mixed precision: displacement in FP64 (exact minimum image), pair
+        // energy and force in FP32
+        const float iL = a.inv_Lf;
+        const float sx = rintf((pj.x - pi32.x) * iL), sy = rintf((pj.y - pi32.y) * iL), sz = rintf((pj.z - pi32.z) * iL);
+        const float dx = (float)((a.pos[j] - x) - (double)sx * a.L);
+        const float dy = (float)((a.pos[n + j] - y) - (double)sy * a.L);
+        const float dz = (float)((a.pos[2 * n + j] - z) - (double)sz * a.L);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 >= a.rc2f) return;
+        const int kind = t + a.type[j];
+        const float ir = rsqrtf(r2);
+        const float r = r2 * ir;
+        const float ir2 = ir * ir;
+        const float ir6 = ir2 * ir2 * ir2;
+        const float ir8 = ir6 * ir2;
+        const float ex = a.Af[kind] * expf(a.Bf * (a.sf[kind] - r));
+        const float V = ex - a.Cf[kind] * ir6 - a.Df[kind] * ir8 - a.Vcf[kind];
+        const float fr = a.Bf * ex * ir - 6.f * a.Cf[kind] * ir8 - 8.f * a.Df[kind] * ir8 * ir2;
+        ftxf -= fr * dx;
+        ftyf -= fr * dy;
+        ftzf -= fr * dz;
+        vtff += V;
+        return;
+      }
       const float iL = a.inv_Lf;
       const float sx = rintf((pj.x - pi32.x) * iL), sy = rintf((pj.y - pi32.y) * iL), sz = rintf((pj.z - pi32.z) * iL);
       const double ddx = (a.pos[j] - x) - (double)sx * a.L;
@@ -347,10 +467,23 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(ForceArgs a) {
       for (int j0 = 0; j0 < n; j0 += 32) offer(j0 + lane, j0 + lane < n);
     }
     if (lane < qn) pair(q[lane]);
-    ftx = warp_sum(ftx);
-    fty = warp_sum(fty);
-    ftz = warp_sum(ftz);
-    vtf = warp_sum(vtf);
+    if (a.mixed) {
+      for (int o = 16; o > 0; o >>= 1) {
+        ftxf += __shfl_xor_sync(0xffffffffu, ftxf, o);
+        ftyf += __shfl_xor_sync(0xffffffffu, ftyf, o);
+        ftzf += __shfl_xor_sync(0xffffffffu, ftzf, o);
+        vtff += __shfl_xor_sync(0xffffffffu, vtff, o);
+      }
+      ftx = ftxf;
+      fty = ftyf;
+      ftz = ftzf;
+      vtf = vtff;
+    } else {
+      ftx = warp_sum(ftx);
+      fty = warp_sum(fty);
+      ftz = warp_sum(ftz);
+      vtf = warp_sum(vtf);
+    }
     if (lane == 0) {
       const double Fx = Fex + ftx, Fy = Fey + fty, Fz = Fez + ftz;
       double vx = a.vel[i], vy = a.vel[n + i], vz = a.vel[2 * n + i];

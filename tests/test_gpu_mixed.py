@@ -1,0 +1,103 @@
+"""Mixed precision (FP32 V-cycle and grid arithmetic, double-float outer
+SHAKE iteration, exact integer reductions) against the FP64 oracle.
+
+Bar: per-ion force error |F - F_ref| / max(|F_ref|, rms|F_ref|) <= 1e-5 at the
+configured tolerance; the constraint residual itself meets tol.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2505_20418_gb300 import maze as M
+from paper_2505_20418_gb300 import synth
+from tests.test_gpu_parity import case, force_err
+
+pytestmark = pytest.mark.gpu
+
+MIXED_BAR = 1e-5
+
+
+def make(name, tol=1e-10, **kw):
+    pos, vel, types, L, N, rc, P = case(name)
+    tf = synth.tosi_fumi_nacl()
+    sim = M.MazeSim(pos, vel, types, L, N, tf, r_cut=rc, dt=1.0, tol=tol, order=P,
+                    solver=M.MAZE_SOLVER_MG, precision=M.MAZE_MIXED, **kw)
+    p = O.Params(L=L, N=N, dt=1.0, tol=tol, rc=rc, P=P, solver="mg")
+    return sim, p, tf, (pos, vel, types)
+
+
+@pytest.mark.parametrize("name", ["nacl64", "nacl64_P2", "nacl1000", "nacl216_N24", "nacl1728_N40", "tiny8_N8"])
+def test_mixed_step0_and_one_step(name):
+    sim, p, tf, (pos, vel, types) = make(name)
+    st = O.init(pos, vel, types, p, tf)
+    assert force_err(sim.get(M.MAZE_FORCE), st.F) < MIXED_BAR
+    s = sim.stats()
+    assert s["status"] == 0 and s["resid"] < p.tol
+    st = O.step(st, p, tf)
+    sim.step(1)
+    assert force_err(sim.get(M.MAZE_FORCE), st.F) < MIXED_BAR
+    s = sim.stats()
+    assert s["status"] == 0 and s["resid"] < p.tol and abs(s["iters"] - st.iters) <= 1
+    # the constraint holds on the whole grid for the GPU's own phi and q
+    x = sim.get(M.MAZE_POS)
+    Q = np.where(types == 0, 1.0, -1.0)
+    q = O.spread(x, Q, p.L, p.N, p.P)
+    sig = (p.h / (4 * np.pi)) * O.apply_M(sim.get(M.MAZE_PHI)) + q
+    assert O.inf_norm(sig) < p.tol + 1e-6    # FP32 spreading of q
+    sim.close()
+
+
+def test_mixed_vcycles_match_fp64_over_trajectory():
+    sim, p, tf, (pos, vel, types) = make("nacl1000")
+    st = O.init(pos, vel, types, p, tf)
+    for _ in range(20):
+        st = O.step(st, p, tf)
+        sim.step(1)
+        assert abs(sim.stats()["iters"] - st.iters) <= 1
+    assert force_err(sim.get(M.MAZE_FORCE), st.F) < MIXED_BAR
+
+
+def test_mixed_energy_conservation_and_determinism():
+    a, p, tf, _ = make("nacl1000")
+    b, _, _, _ = make("nacl1000")
+    E, Vw = [], []
+    for _ in range(50):
+        a.step(2)
+        s = a.stats()
+        E.append(s["e_tot"])
+        Vw.append(s["v_work"])
+    assert np.std(E) / np.std(Vw) < 2e-4
+    b.step(100)
+    assert np.array_equal(a.get(M.MAZE_POS), b.get(M.MAZE_POS))
+    blob = a.get_state()
+    a.step(5)
+    c, _, _, _ = make("nacl1000")
+    c.set_state(blob)
+    c.step(5)
+    for what in (M.MAZE_POS, M.MAZE_VEL, M.MAZE_PHI, M.MAZE_Y):
+        assert np.array_equal(a.get(what), c.get(what))
+    for s in (a, b, c):
+        s.close()
+
+
+@pytest.mark.slow
+def test_mixed_large_box_grid_form():
+    """512000 ions / 256^3: the cooperative-grid form of the mixed solver."""
+    w = synth.workload("nacl512000")
+    pos, vel, types = synth.make_state(w)
+    tf = synth.tosi_fumi_nacl()
+    sim = M.MazeSim(pos, vel, types, w.L, w.N, tf, r_cut=w.rc, dt=w.dt, tol=w.tol,
+                    solver=M.MAZE_SOLVER_MG, precision=M.MAZE_MIXED)
+    sim.step(1)
+    s = sim.stats()
+    assert s["status"] == 0 and s["resid"] < w.tol
+    x = sim.get(M.MAZE_POS)
+    phi = sim.get(M.MAZE_PHI)
+    F = sim.get(M.MAZE_FORCE)
+    Q = np.where(types == 0, 1.0, -1.0)
+    idx = np.random.default_rng(9).choice(len(x), 48, replace=False)
+    Fo = O.gather_forces(x[idx], Q[idx], phi, w.L, w.N, 4) + O.tf_forces_on(idx, x, types, w.L, tf, w.rc)
+    scale = np.sqrt((F ** 2).sum(1).mean())
+    err = np.linalg.norm(F[idx] - Fo, axis=1) / np.maximum(np.linalg.norm(Fo, axis=1), scale)
+    assert err.max() < MIXED_BAR
+    sim.close()
