@@ -102,22 +102,32 @@ def mg_levels(N):
     return sizes
 
 
-def solve_bytes_per_launch(N, iters, solver="cg", nu=(2, 2)):
-    """Algorithmic DRAM bytes of one solve launch (FP64, 8 B per value).
+def solve_bytes_per_launch(N, iters, solver="cg", nu=(2, 2), precision="fp64"):
+    """Algorithmic DRAM bytes of one solve launch (one pass per vector touch).
 
-    Common: S4 pass 56 B/pt (read phi^k, phi^{k-1}, q, y; write phi_p,
-    sigma_p, r) and the S6 correction 32 B/pt (read phi_p, y; write phi, y).
-    CG: 64 B/pt per iteration (read r, p, write p; read p, y, r, write y, r)
-    plus 24 B/pt for the true-residual confirmation.
-    MG, per V-cycle and level of n_l points: 32 B/pt per red-black sweep (x
-    read twice, b read, x written), residual 24 B/pt, full weighting 9 B/pt,
+    FP64 (8 B per value). Common: S4 pass 56 B/pt (read phi^k, phi^{k-1}, q,
+    y; write phi_p, sigma_p, r) and the S6 correction 32 B/pt (read phi_p, y;
+    write phi, y). CG: 64 B/pt per iteration (read r, p, write p; read p, y,
+    r, write y, r) plus 24 B/pt for the true-residual confirmation. MG, per
+    V-cycle and level of n_l points: 32 B/pt per red-black sweep (x read
+    twice, b read, x written), residual 24 B/pt, full weighting 9 B/pt,
     prolongation to black points 9 B/pt; coarsest solve 16 B/pt; residual
-    check on the finest level 16 B/pt."""
+    check on the finest level 16 B/pt.
+
+    Mixed (double-float pairs of 8 B for phi, y, sigma_p; FP32 V-cycle):
+    S4 40 B/pt (read phi^k, phi^{k-1}, q; write phi_p, sigma_p); per
+    residual check 20 B/pt (read y, sigma_p; write r in FP32); per V-cycle
+    level 16 B/pt per sweep, 12 residual, 4.5 restriction, 4.5
+    prolongation; per update 20 B/pt (read y, e; write y); S6 40 B/pt (mean of
+    y, then read y, phi_p; write y, phi)."""
     ng = N ** 3
+    lv = mg_levels(N)
+    if precision == "mixed":
+        per_v = sum(n ** 3 * ((nu[0] + nu[1]) * 16 + 12 + 4.5 + 4.5) for n in lv[:-1]) + lv[-1] ** 3 * 8
+        return ng * (40 + 40) + (iters + 1) * ng * 20 + iters * (per_v + ng * 20)
     base = ng * (56 + 32)
     if solver == "cg":
         return base + ng * (64 * iters + 24)
-    lv = mg_levels(N)
     per_v = sum(n ** 3 * ((nu[0] + nu[1]) * 32 + 24 + 9 + 9) for n in lv[:-1]) + lv[-1] ** 3 * 16 + ng * 16
     return base + per_v * iters
 
@@ -171,10 +181,34 @@ def bench_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def replica_workload(name, rank):
+    """The box a rank advances: same workload, independent seed per rank
+    (replicas shard one per GPU with no collective on the data path)."""
+    w = synth.workload(name)
+    w.seed = w.seed + rank
+    return w
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """Max of a per-rank float over all ranks (identity on one rank)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(world, steps_per_rank, rank_seconds):
+    """Whole-job throughput of independent replicas: all ranks' steps divided
+    by the slowest rank's time."""
+    return world * steps_per_rank / rank_seconds
+
+
 def config_dict(w, args):
     return {"workload": f"molten NaCl {w.n_ions} ions, L={w.L} A, {w.N}^3 grid, {w.T:.0f} K, dt={w.dt} fs, "
                         f"tol={w.tol:g}, P={w.order}, r_cut={w.rc} A",
-            "n_ions": w.n_ions, "grid": w.N, "solver": args.solver, "precision": getattr(args, "precision", "fp64"),
+            "n_ions": w.n_ions, "grid": w.N, "solver": args.solver, "precision": args.precision,
             "l2": "flushed between timed steps (256 MiB write outside the step events)"}
 
 
@@ -186,7 +220,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="nacl1000", choices=["nacl64", "nacl1000", "nacl512000"])
     ap.add_argument("--solver", default="mg", choices=["cg", "mg"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -209,7 +243,7 @@ def main():
     M.load()
 
     # every rank advances its own replica (independent seed)
-    w.seed = w.seed + rank
+    w = replica_workload(args.workload, rank)
     pos, vel, types = synth.make_state(w)
     tf = synth.tosi_fumi_nacl()
     stream = torch.cuda.Stream(device=dev)
@@ -249,11 +283,8 @@ def main():
             timing_error = str(e)
     torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1e3
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dist if world > 1 else None, dev)
     if world > 1:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
         dist.barrier()
     clk = clocks.stop()
     s2 = sim.stats()
@@ -271,9 +302,16 @@ def main():
         p = O.Params(L=w.L, N=w.N, dt=w.dt, tol=w.tol, rc=w.rc, P=w.order)
         phi_ex, _ = O.exact_potential(x, types, p)
         Q = np.where(types == 0, 1.0, -1.0)
-        Fo = O.gather_forces(x, Q, phi_ex, w.L, w.N, w.order) + O.tf_forces(x, types, w.L, tf, w.rc)[0]
+        if w.n_ions <= 5000:
+            idx = np.arange(w.n_ions)
+            Fo = O.gather_forces(x, Q, phi_ex, w.L, w.N, w.order) + O.tf_forces(x, types, w.L, tf, w.rc)[0]
+        else:   # large boxes: 64 sampled ions, brute-force pairs for those only
+            idx = np.random.default_rng(5).choice(w.n_ions, 64, replace=False)
+            Fo = (O.gather_forces(x[idx], Q[idx], phi_ex, w.L, w.N, w.order)
+                  + O.tf_forces_on(idx, x, types, w.L, tf, w.rc))
+        scale = np.sqrt((np.linalg.norm(F, axis=1) ** 2).mean())
         nrm = np.linalg.norm(Fo, axis=1)
-        ferr = float((np.linalg.norm(F - Fo, axis=1) / np.maximum(nrm, np.sqrt((nrm ** 2).mean()))).max())
+        ferr = float((np.linalg.norm(F[idx] - Fo, axis=1) / np.maximum(nrm, scale)).max())
 
     # end to end through the C ABI with host buffers: per step upload the ion
     # state from pinned host memory, run the step, read back positions + stats
@@ -295,28 +333,25 @@ def main():
             M.maze_get(sim.h, M.MAZE_POS, hpn)
             M.maze_get(sim.h, M.MAZE_VEL, hvn)
             sim.stats()
-        e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * n_e2e / e2e_s, "unit": "steps/s",
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist if world > 1 else None, dev)
+        e2e = {"value": weak_scaling_value(world, n_e2e, e2e_s), "unit": "steps/s",
                "h2d_bytes_per_step": 2 * 24 * w.n_ions,
                "d2h_bytes_per_step": 2 * 24 * w.n_ions + 104}
 
     if rank == 0:
         ng = w.N ** 3
-        bytes_launch = solve_bytes_per_launch(w.N, iters, args.solver)
+        bytes_launch = solve_bytes_per_launch(w.N, iters, args.solver, precision=args.precision)
         mean_solve_s = statistics.mean(solve_ms) / 1e3 if solve_ms else float("nan")
         achieved = bytes_launch / mean_solve_s / 1e9
         peak, peak_kind = peaks()
         cpu = None if args.no_cpu else run_cpu_baseline(w, args.solver)
         kps = KERNELS_PER_STEP_CELLS if int(np.floor(w.L / w.rc)) >= 3 else KERNELS_PER_STEP_NOCELLS
         line = {
-            "metric": METRIC, "value": world * args.steps / total_s, "unit": "steps/s",
+            "metric": METRIC, "value": weak_scaling_value(world, args.steps, total_s), "unit": "steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(w, args),
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f32x2",
+            "data": "synthetic", "config": config_dict(w, args),
             "p50_us": 1e3 * float(np.percentile(step_ms, 50)), "p99_us": 1e3 * float(np.percentile(step_ms, 99)),
             "iters_per_step": iters, "force_error": ferr,
             "phase_us": dict(zip(["move_spread", "cells", "solve", "forces"],

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -73,10 +74,13 @@ struct maze_ctx {
   // cells
   int nc = 0, ncell = 0;
   int *cell_of = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cursor = nullptr, *cell_ions = nullptr;
+  float4* pos_sorted = nullptr;
+  float4 *rel_hi = nullptr, *rel_lo = nullptr, *rel_hi_s = nullptr, *rel_lo_s = nullptr;
   // force reductions
   double* fpart = nullptr;
   unsigned* ticket = nullptr;
   int fblocks = 0;
+  int num_sms = 0;
   maze_stats* rec = nullptr;       // device
   int* gate = nullptr;             // device: current step skipped
   maze_stats* rec_host = nullptr;  // pinned
@@ -177,6 +181,9 @@ IonArgs ion_args(maze_ctx* c, int do_move, int do_spread) {
   a.wbuf = c->wbuf;
   a.wbuf32 = c->mixed ? c->wbuf32 : nullptr;
   a.wbase = c->wbase;
+  a.rel_hi = c->mixed ? c->rel_hi : nullptr;
+  a.rel_lo = c->mixed ? c->rel_lo : nullptr;
+  a.cell_len = c->nc >= 3 ? c->L / c->nc : c->L;
   return a;
 }
 
@@ -189,6 +196,12 @@ CellArgs cell_args(maze_ctx* c) {
   a.cell_start = c->cell_start;
   a.cursor = c->cursor;
   a.cell_ions = c->cell_ions;
+  a.pos32 = c->pos32;
+  a.pos_sorted = c->pos_sorted;
+  a.rel_hi = c->mixed ? c->rel_hi : nullptr;
+  a.rel_lo = c->rel_lo;
+  a.rel_hi_sorted = c->rel_hi_s;
+  a.rel_lo_sorted = c->rel_lo_s;
   a.rec = c->rec;
   return a;
 }
@@ -211,12 +224,27 @@ ForceArgs force_args(maze_ctx* c, const double* phi, int do_kick, int count_step
   a.phi = phi;
   a.phi_df = c->mixed ? 1 : 0;
   a.mixed = c->mixed ? 1 : 0;
+  a.rel_hi = c->rel_hi;
+  a.rel_lo = c->rel_lo;
+  a.rel_hi_sorted = c->rel_hi_s;
+  a.rel_lo_sorted = c->rel_lo_s;
+  {
+    const double cl = c->nc >= 3 ? c->L / c->nc : c->L;
+    a.cell_len_h = (float)cl;
+    a.cell_len_l = (float)(cl - (double)a.cell_len_h);
+    a.L_h = (float)c->L;
+    a.L_l = (float)(c->L - (double)a.L_h);
+  }
+  // one block per cell when the box has cells and either enough of them to
+  // fill the GPU or FP32 pair arithmetic (mixed precision)
+  a.by_cell = (c->nc >= 3 && (c->mixed || c->ncell >= 2 * c->num_sms)) ? 1 : 0;
   a.wbuf32 = c->wbuf32;
   a.wbuf = c->wbuf;
   a.wbase = c->wbase;
   a.nc = c->nc;
   a.cell_start = c->cell_start;
   a.cell_ions = c->cell_ions;
+  a.pos_sorted = c->pos_sorted;
   a.cell_of = c->cell_of;
   a.charge0 = g.charge[0];
   a.charge1 = g.charge[1];
@@ -495,6 +523,7 @@ maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
   c->ncell = c->nc * c->nc * c->nc;
   c->sblocks = cfg->solver == MAZE_SOLVER_MG ? mg_blocks((int)ng) : solve_blocks((int)ng);
   c->fblocks = force_blocks(n);
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) c->num_sms = 1;
 #define AL(p, cnt)                          \
   do {                                      \
     maze_status s_ = dalloc(c, &(p), (cnt)); \
@@ -511,6 +540,8 @@ maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
   AL(c->pos32, (size_t)n);
   AL(c->wbuf, 12 * (size_t)n);
   AL(c->wbuf32, 12 * (size_t)n);
+  AL(c->rel_hi, (size_t)n);
+  AL(c->rel_lo, (size_t)n);
   AL(c->wbase, (size_t)n);
   AL(c->qfix, ng);
   AL(c->qd, ng);
@@ -603,8 +634,11 @@ maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
     AL(c->cell_start, (size_t)c->ncell + 1);
     AL(c->cursor, (size_t)c->ncell);
     AL(c->cell_ions, (size_t)n);
+    AL(c->pos_sorted, (size_t)n);
+    AL(c->rel_hi_s, (size_t)n);
+    AL(c->rel_lo_s, (size_t)n);
   }
-  AL(c->fpart, (size_t)c->fblocks * 8);
+  AL(c->fpart, (size_t)std::max(c->fblocks, c->ncell) * 8);
   AL(c->ticket, 4);
   AL(c->rec, 1);
   AL(c->gate, 1);

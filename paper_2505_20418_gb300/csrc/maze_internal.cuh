@@ -55,6 +55,9 @@ struct IonArgs {
   int* gate;             // set to 1 when the step starts after an error
   double* wbuf;          // [n][3][4] B-spline weights of the new positions
   float* wbuf32;         // [n][3][4] FP32 weights (mixed precision) or nullptr
+  float4* rel_hi;        // [n] (x, y, z, Q): position relative to the own cell's
+  float4* rel_lo;        //     corner as hi + lo floats (mixed precision) or nullptr
+  double cell_len;       // L / nc (L when there is no cell list)
   int4* wbase;           // [n] first support node per axis
 };
 
@@ -65,6 +68,12 @@ struct CellArgs {
   int* cell_start;       // [ncell + 1]
   int* cursor;           // [ncell]
   int* cell_ions;        // [n]
+  const float4* pos32;   // [n] FP32 positions by ion
+  float4* pos_sorted;    // [n] FP32 positions by cell slot (written by the sort)
+  const float4* rel_hi;  // [n] cell-relative hi/lo positions (mixed) or nullptr
+  const float4* rel_lo;
+  float4* rel_hi_sorted; // [n] the same in cell-slot order
+  float4* rel_lo_sorted;
   maze_stats* rec;
 };
 
@@ -85,10 +94,18 @@ struct ForceArgs {
   const float* wbuf32;   // [n][3][4] FP32 weights (mixed precision)
   const int4* wbase;     // [n]
   int mixed;             // 1: FP32 gather and pair arithmetic
+  int by_cell;           // 1: one block per cell (k_forces_cells), else one warp per ion
+  const float4* rel_hi;  // [n] cell-relative hi/lo positions (mixed precision)
+  const float4* rel_lo;
+  const float4* rel_hi_sorted;  // [n] the same in cell-slot order
+  const float4* rel_lo_sorted;
+  float cell_len_h, cell_len_l;  // L / nc as hi + lo floats
+  float L_h, L_l;                // L as hi + lo floats
   float Af[3], sf[3], Cf[3], Df[3], Vcf[3], Bf, rc2f;
   int nc;                // cells per edge; < 3 means all pairs
   const int* cell_start;
   const int* cell_ions;
+  const float4* pos_sorted;  // [n] FP32 positions in cell-slot order
   const int* cell_of;
   double charge0, charge1, mass0, mass1;
   double kick0, kick1;

@@ -82,12 +82,23 @@ __global__ void __launch_bounds__(kIonThreads) k_move(IonArgs a) {
     }
     const double Q = t ? a.charge1 : a.charge0;
     a.pos32[i] = make_float4((float)x, (float)y, (float)z, (float)Q);
+    int cx = 0, cy = 0, cz = 0;
     if (a.nc >= 3) {
       const double cs = a.cell_scale;
-      int cx = min((int)(x * cs), a.nc - 1), cy = min((int)(y * cs), a.nc - 1), cz = min((int)(z * cs), a.nc - 1);
+      cx = min((int)(x * cs), a.nc - 1);
+      cy = min((int)(y * cs), a.nc - 1);
+      cz = min((int)(z * cs), a.nc - 1);
       const int c = cx + a.nc * (cy + a.nc * cz);
       a.cell_of[i] = c;
       atomicAdd(&a.cell_count[c], 1);
+    }
+    if (a.rel_hi) {
+      // position relative to the own cell's corner as a (hi, lo) float pair:
+      // pair displacements then need no FP64 arithmetic (mixed precision)
+      const double rx = x - cx * a.cell_len, ry = y - cy * a.cell_len, rz = z - cz * a.cell_len;
+      const float hx = (float)rx, hy = (float)ry, hz = (float)rz;
+      a.rel_hi[i] = make_float4(hx, hy, hz, (float)Q);
+      a.rel_lo[i] = make_float4((float)(rx - hx), (float)(ry - hy), (float)(rz - hz), (float)t);
     }
     double tx, ty, tz;
     const int fx = axis_split(x * a.inv_h, P, N, tx);
@@ -224,7 +235,7 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_cell_sort(CellArgs a) {
   const int c = blockIdx.x * kSortWarps + warp;
   if (c >= a.ncell) return;
   const int lo = a.cell_start[c], hi = a.cell_start[c + 1], m = hi - lo;
-  if (m <= 1) return;
+  if (m == 0) return;
   if (m > kSortCap) {
     if (lane == 0)
       for (int u = lo + 1; u < hi; ++u) {
@@ -236,6 +247,15 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_cell_sort(CellArgs a) {
         }
         a.cell_ions[w + 1] = v;
       }
+    __syncwarp();
+    for (int u = lo + lane; u < hi; u += 32) {
+      const int v = a.cell_ions[u];
+      a.pos_sorted[u] = a.pos32[v];
+      if (a.rel_hi) {
+        a.rel_hi_sorted[u] = a.rel_hi[v];
+        a.rel_lo_sorted[u] = a.rel_lo[v];
+      }
+    }
     return;
   }
   int* ids = s_ids[warp];
@@ -246,6 +266,11 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_cell_sort(CellArgs a) {
     int rank = 0;
     for (int k = 0; k < m; ++k) rank += ids[k] < v;
     a.cell_ions[lo + rank] = v;
+    a.pos_sorted[lo + rank] = a.pos32[v];
+    if (a.rel_hi) {
+      a.rel_hi_sorted[lo + rank] = a.rel_hi[v];
+      a.rel_lo_sorted[lo + rank] = a.rel_lo[v];
+    }
   }
 }
 
@@ -257,7 +282,10 @@ cudaError_t launch_cells(const CellArgs& a, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// S7-S9: one warp per ion.
+// S7-S9. Two schedules share the per-ion pieces below: one warp per ion over
+// the candidates in global memory (small boxes, FP64 pairs spread over every
+// SM), and one block per cell with the 27 neighbour cells' candidates staged
+// in shared memory (large boxes and mixed precision).
 
 __device__ __forceinline__ void tf_pair(const ForceArgs& a, int kind, double r2, double& fr, double& V) {
   // V = A exp(B (s - r)) - C r^-6 - D r^-8 - V(r_c);  fr = -(dV/dr) / r.
@@ -276,269 +304,265 @@ __device__ __forceinline__ void tf_pair(const ForceArgs& a, int kind, double r2,
   fr = a.B * ex * ir - 6.0 * a.C[kind] * ir8 - 8.0 * a.D[kind] * ir8 * ir2;
 }
 
-__global__ void __launch_bounds__(kForceThreads) k_forces(ForceArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  const int i = blockIdx.x * (kForceThreads / 32) + warp;
-  // a step whose solve hit max_iter still completes (forces, energies, step
-  // count); any other error stops the step
-  const int st0 = a.rec->status;
-  const bool live = i < a.n && *a.gate == 0 && (st0 == MAZE_OK || st0 == MAZE_ERR_NOT_CONVERGED);
-  // per-ion contributions to the block sums:
-  // 0 KE, 1 V_TF (pairs counted twice), 2 1/2 phi.q, 3 dV_work, 4-6 momentum
-  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-  __shared__ int s_queue[kForceThreads / 32][64];
-  if (live) {
-    const int n = a.n, N = a.N, P = a.P;
-    const double x = a.pos[i], y = a.pos[n + i], z = a.pos[2 * n + i];
-    const int t = a.type[i];
-    const double Q = t ? a.charge1 : a.charge0;
-    // --- S7: Eq. F_nostra, F = -k_e Q sum_n W (phi_{n+e} - phi_{n-e}) / 2h,
-    // with the weights k_ion_update stored for this position
-    const int4 first = a.wbase[i];
-    const int P3 = P * P * P;
-    double gx = 0, gy = 0, gz = 0, vd = 0;
-    const size_t NN = (size_t)N * N;
-    if (a.mixed) {
-      // mixed precision: FP32 weights, differences of the double-float
-      // potential in FP32, FP32 sums
-      const float* w = a.wbuf32 + (size_t)i * 12;
-      const float2* f = reinterpret_cast<const float2*>(a.phi);
-      float sx = 0.f, sy = 0.f, sz = 0.f, s0 = 0.f;
-      for (int sidx = lane; sidx < P3; sidx += 32) {
-        const int ia = sidx % P, ib = (sidx / P) % P, ic = sidx / (P * P);
-        const int ix = wrap_idx(first.x + ia, N), iy = wrap_idx(first.y + ib, N), iz = wrap_idx(first.z + ic, N);
-        const float wt = w[ia] * w[4 + ib] * w[8 + ic];
-        const size_t row = iz * NN + (size_t)iy * N;
-        const float2 xp = f[row + (ix == N - 1 ? 0 : ix + 1)], xm = f[row + (ix == 0 ? N - 1 : ix - 1)];
-        const float2 yp = f[iz * NN + (size_t)(iy == N - 1 ? 0 : iy + 1) * N + ix];
-        const float2 ym = f[iz * NN + (size_t)(iy == 0 ? N - 1 : iy - 1) * N + ix];
-        const float2 zp = f[(size_t)(iz == N - 1 ? 0 : iz + 1) * NN + (size_t)iy * N + ix];
-        const float2 zm = f[(size_t)(iz == 0 ? N - 1 : iz - 1) * NN + (size_t)iy * N + ix];
-        const float2 c0 = f[row + ix];
-        sx += wt * ((xp.x - xm.x) + (xp.y - xm.y));
-        sy += wt * ((yp.x - ym.x) + (yp.y - ym.y));
-        sz += wt * ((zp.x - zm.x) + (zp.y - zm.y));
-        s0 += wt * (c0.x + c0.y);
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        sx += __shfl_xor_sync(0xffffffffu, sx, o);
-        sy += __shfl_xor_sync(0xffffffffu, sy, o);
-        sz += __shfl_xor_sync(0xffffffffu, sz, o);
-        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-      }
-      gx = sx;
-      gy = sy;
-      gz = sz;
-      vd = s0;
-    } else {
-      const double* w = a.wbuf + (size_t)i * 12;
-      for (int sidx = lane; sidx < P3; sidx += 32) {
-        const int ia = sidx % P, ib = (sidx / P) % P, ic = sidx / (P * P);
-        const int ix = wrap_idx(first.x + ia, N), iy = wrap_idx(first.y + ib, N), iz = wrap_idx(first.z + ic, N);
-        const double wt = w[ia] * w[4 + ib] * w[8 + ic];
-        const size_t row = iz * NN + (size_t)iy * N;
-        const size_t ixp = row + (ix == N - 1 ? 0 : ix + 1), ixm = row + (ix == 0 ? N - 1 : ix - 1);
-        const size_t iyp = iz * NN + (size_t)(iy == N - 1 ? 0 : iy + 1) * N + ix;
-        const size_t iym = iz * NN + (size_t)(iy == 0 ? N - 1 : iy - 1) * N + ix;
-        const size_t izp = (size_t)(iz == N - 1 ? 0 : iz + 1) * NN + (size_t)iy * N + ix;
-        const size_t izm = (size_t)(iz == 0 ? N - 1 : iz - 1) * NN + (size_t)iy * N + ix;
-        double px, py, pz, p0;
-        if (a.phi_df) {
-          // double-float potential: differences of the (hi, lo) pairs in FP32
-          const float2* f = reinterpret_cast<const float2*>(a.phi);
-          const float2 xp = f[ixp], xm = f[ixm], yp = f[iyp], ym = f[iym], zp = f[izp], zm = f[izm], c0 = f[row + ix];
-          px = (double)((xp.x - xm.x) + (xp.y - xm.y));
-          py = (double)((yp.x - ym.x) + (yp.y - ym.y));
-          pz = (double)((zp.x - zm.x) + (zp.y - zm.y));
-          p0 = (double)c0.x + (double)c0.y;
-        } else {
-          const double* ph = a.phi;
-          px = ph[ixp] - ph[ixm];
-          py = ph[iyp] - ph[iym];
-          pz = ph[izp] - ph[izm];
-          p0 = ph[row + ix];
-        }
-        gx += wt * px;
-        gy += wt * py;
-        gz += wt * pz;
-        vd += wt * p0;
-      }
-      gx = warp_sum(gx);
-      gy = warp_sum(gy);
-      gz = warp_sum(gz);
-      vd = warp_sum(vd);
+// Per-lane pair sums (FP64 mode uses the doubles, mixed the floats).
+struct PairSum {
+  double fx = 0, fy = 0, fz = 0, v = 0;
+  float fxf = 0.f, fyf = 0.f, fzf = 0.f, vf = 0.f;
+};
+
+// Tosi-Fumi pair (i, j): minimum image from the FP32 shift and the exact FP64
+// displacement, exact cutoff test, FP64 (or FP32 in mixed mode) arithmetic.
+__device__ __forceinline__ void pair_add(const ForceArgs& a, int ti, double x, double y, double z, float4 pi32,
+                                         int tj, float4 pj, double xj, double yj, double zj, PairSum& ps) {
+  const float iL = a.inv_Lf;
+  const float sx = rintf((pj.x - pi32.x) * iL), sy = rintf((pj.y - pi32.y) * iL), sz = rintf((pj.z - pi32.z) * iL);
+  const double ddx = (xj - x) - (double)sx * a.L;
+  const double ddy = (yj - y) - (double)sy * a.L;
+  const double ddz = (zj - z) - (double)sz * a.L;
+  const int kind = ti + tj;
+  const double r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+  if (r2 >= a.rc2) return;
+  double fr, V;
+  tf_pair(a, kind, r2, fr, V);
+  ps.fx -= fr * ddx;
+  ps.fy -= fr * ddy;
+  ps.fz -= fr * ddz;
+  ps.v += V;
+}
+
+// (rj + off) - ri for positions and offset given as hi + lo float pairs,
+// each addition made error-free by Knuth's TwoSum: the FP32 result carries
+// the displacement to ~1e-7 relative, without FP64 arithmetic.
+__device__ __forceinline__ float disp_df(float rih, float ril, float rjh, float rjl, float offh, float offl) {
+  const float s = __fadd_rn(rjh, offh);
+  const float bb = __fsub_rn(s, rjh);
+  const float e1 = __fadd_rn(__fsub_rn(rjh, __fsub_rn(s, bb)), __fsub_rn(offh, bb));
+  const float d = __fsub_rn(s, rih);
+  const float cc = __fsub_rn(d, s);
+  const float e2 = __fadd_rn(__fsub_rn(s, __fsub_rn(d, cc)), __fsub_rn(-rih, cc));
+  return __fadd_rn(d, __fadd_rn(__fadd_rn(e1, e2), __fsub_rn(__fadd_rn(rjl, offl), ril)));
+}
+
+// Mixed-precision Tosi-Fumi pair from an FP32 displacement.
+__device__ __forceinline__ void pair_f(const ForceArgs& a, int kind, float dx, float dy, float dz, PairSum& ps) {
+  const float r2 = dx * dx + dy * dy + dz * dz;
+  if (r2 >= a.rc2f) return;
+  const float ir = rsqrtf(r2);
+  const float r = r2 * ir;
+  const float ir2 = ir * ir;
+  const float ir6 = ir2 * ir2 * ir2;
+  const float ir8 = ir6 * ir2;
+  const float ex = a.Af[kind] * expf(a.Bf * (a.sf[kind] - r));
+  const float V = ex - a.Cf[kind] * ir6 - a.Df[kind] * ir8 - a.Vcf[kind];
+  const float fr = a.Bf * ex * ir - 6.f * a.Cf[kind] * ir8 - 8.f * a.Df[kind] * ir8 * ir2;
+  ps.fxf -= fr * dx;
+  ps.fyf -= fr * dy;
+  ps.fzf -= fr * dz;
+  ps.vf += V;
+}
+
+// Warp sum of a PairSum into FP64 totals (every lane gets them).
+__device__ __forceinline__ void pair_total(const ForceArgs& a, PairSum& ps, double& fx, double& fy, double& fz, double& v) {
+  if (a.mixed) {
+    for (int o = 16; o > 0; o >>= 1) {
+      ps.fxf += __shfl_xor_sync(0xffffffffu, ps.fxf, o);
+      ps.fyf += __shfl_xor_sync(0xffffffffu, ps.fyf, o);
+      ps.fzf += __shfl_xor_sync(0xffffffffu, ps.fzf, o);
+      ps.vf += __shfl_xor_sync(0xffffffffu, ps.vf, o);
     }
-    const double fe = -MAZE_KE_EV_ANGSTROM * Q * a.inv_2h;
-    const double Fex = fe * gx, Fey = fe * gy, Fez = fe * gz;
-    // --- S8: Tosi-Fumi pairs, minimum image, r < r_c. Candidates pass an
-    // FP32 pre-filter with a safety margin; survivors are queued per warp and
-    // evaluated 32 at a time in FP64 (exact cutoff test), so the FP64 pipe
-    // sees full warps instead of the ~10 % of lanes that pass the filter.
-    const float4 pi32 = a.pos32[i];
-    const float Lf = a.Lf;
-    int* q = s_queue[warp];
-    int qn = 0;
-    double ftx = 0, fty = 0, ftz = 0, vtf = 0;
-    float ftxf = 0.f, ftyf = 0.f, ftzf = 0.f, vtff = 0.f;
-    auto pair = [&](int j) {
-      const float4 pj = a.pos32[j];
-      if (a.mixed) {
-        // mixed precision: displacement in FP64 (exact minimum image), pair
-        // energy and force in FP32
-        const float iL = a.inv_Lf;
-        const float sx = rintf((pj.x - pi32.x) * iL), sy = rintf((pj.y - pi32.y) * iL), sz = rintf((pj.z - pi32.z) * iL);
-        const float dx = (float)((a.pos[j] - x) - (double)sx * a.L);
-        const float dy = (float)((a.pos[n + j] - y) - (double)sy * a.L);
-        const float dz = (float)((a.pos[2 * n + j] - z) - (double)sz * a.L);
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 >= a.rc2f) return;
-        const int kind = t + a.type[j];
-        const float ir = rsqrtf(r2);
-        const float r = r2 * ir;
-        const float ir2 = ir * ir;
-        const float ir6 = ir2 * ir2 * ir2;
-        const float ir8 = ir6 * ir2;
-        const float ex = a.Af[kind] * expf(a.Bf * (a.sf[kind] - r));
-        const float V = ex - a.Cf[kind] * ir6 - a.Df[kind] * ir8 - a.Vcf[kind];
-        const float fr = a.Bf * ex * ir - 6.f * a.Cf[kind] * ir8 - 8.f * a.Df[kind] * ir8 * ir2;
-        ftxf -= fr * dx;
-        ftyf -= fr * dy;
-        ftzf -= fr * dz;
-        vtff += V;
-        return;
-      }
-      const float iL = a.inv_Lf;
-      const float sx = rintf((pj.x - pi32.x) * iL), sy = rintf((pj.y - pi32.y) * iL), sz = rintf((pj.z - pi32.z) * iL);
-      const double ddx = (a.pos[j] - x) - (double)sx * a.L;
-      const double ddy = (a.pos[n + j] - y) - (double)sy * a.L;
-      const double ddz = (a.pos[2 * n + j] - z) - (double)sz * a.L;
-      const double r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-      if (r2 >= a.rc2) return;
-      double fr, V;
-      tf_pair(a, t + a.type[j], r2, fr, V);
-      ftx -= fr * ddx;
-      fty -= fr * ddy;
-      ftz -= fr * ddz;
-      vtf += V;
-    };
-    auto offer = [&](int j, bool valid) {
-      bool pass = false;
-      if (valid && j != i) {
-        const float4 pj = a.pos32[j];
-        float dx = pj.x - pi32.x, dy = pj.y - pi32.y, dz = pj.z - pi32.z;
-        dx -= rintf(dx * a.inv_Lf) * Lf;
-        dy -= rintf(dy * a.inv_Lf) * Lf;
-        dz -= rintf(dz * a.inv_Lf) * Lf;
-        pass = dx * dx + dy * dy + dz * dz < a.rc2_filter;
-      }
-      const unsigned m = __ballot_sync(0xffffffffu, pass);
-      if (pass) q[qn + __popc(m & ((1u << lane) - 1u))] = j;
-      qn += __popc(m);
-      __syncwarp();
-      if (qn >= 32) {
-        pair(q[lane]);
-        __syncwarp();
-        if (lane < qn - 32) q[lane] = q[32 + lane];
-        __syncwarp();
-        qn -= 32;
-      }
-    };
-    if (a.nc >= 3) {
-      const int nc = a.nc;
-      const int c = a.cell_of[i];
-      const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
-      for (int dz = -1; dz <= 1; ++dz) {
-        const int zz = (cz + dz + nc) % nc;
-        for (int dy = -1; dy <= 1; ++dy) {
-          const int yy = (cy + dy + nc) % nc;
-          for (int dx = -1; dx <= 1; ++dx) {
-            const int xx = (cx + dx + nc) % nc;
-            const int cc = xx + nc * (yy + nc * zz);
-            const int lo = a.cell_start[cc], hi = a.cell_start[cc + 1];
-            for (int u0 = lo; u0 < hi; u0 += 32) {
-              const int u = u0 + lane;
-              offer(u < hi ? a.cell_ions[u] : -1, u < hi);
-            }
-          }
-        }
-      }
-    } else {
-      for (int j0 = 0; j0 < n; j0 += 32) offer(j0 + lane, j0 + lane < n);
-    }
-    if (lane < qn) pair(q[lane]);
-    if (a.mixed) {
-      for (int o = 16; o > 0; o >>= 1) {
-        ftxf += __shfl_xor_sync(0xffffffffu, ftxf, o);
-        ftyf += __shfl_xor_sync(0xffffffffu, ftyf, o);
-        ftzf += __shfl_xor_sync(0xffffffffu, ftzf, o);
-        vtff += __shfl_xor_sync(0xffffffffu, vtff, o);
-      }
-      ftx = ftxf;
-      fty = ftyf;
-      ftz = ftzf;
-      vtf = vtff;
-    } else {
-      ftx = warp_sum(ftx);
-      fty = warp_sum(fty);
-      ftz = warp_sum(ftz);
-      vtf = warp_sum(vtf);
-    }
-    if (lane == 0) {
-      const double Fx = Fex + ftx, Fy = Fey + fty, Fz = Fez + ftz;
-      double vx = a.vel[i], vy = a.vel[n + i], vz = a.vel[2 * n + i];
-      const double m = t ? a.mass1 : a.mass0;
-      if (a.do_kick) {
-        // Eq. E_nostra, trapezoid rule: dV_work = -1/2 (F_el^k + F_el^{k+1}) . dt v_half
-        const double ox = a.force_el[i], oy = a.force_el[n + i], oz = a.force_el[2 * n + i];
-        acc[3] = -0.5 * a.dt * ((ox + Fex) * vx + (oy + Fey) * vy + (oz + Fez) * vz);
-        const double kick = t ? a.kick1 : a.kick0;
-        vx += kick * Fx;
-        vy += kick * Fy;
-        vz += kick * Fz;
-        a.vel[i] = vx;
-        a.vel[n + i] = vy;
-        a.vel[2 * n + i] = vz;
-      }
-      a.force[i] = Fx;
-      a.force[n + i] = Fy;
-      a.force[2 * n + i] = Fz;
-      a.force_el[i] = Fex;
-      a.force_el[n + i] = Fey;
-      a.force_el[2 * n + i] = Fez;
-      acc[0] = a.ke_coef * m * (vx * vx + vy * vy + vz * vz);
-      acc[1] = 0.5 * vtf;
-      acc[2] = 0.5 * MAZE_KE_EV_ANGSTROM * Q * vd;
-      acc[4] = m * vx;
-      acc[5] = m * vy;
-      acc[6] = m * vz;
-    }
+    fx = ps.fxf;
+    fy = ps.fyf;
+    fz = ps.fzf;
+    v = ps.vf;
+  } else {
+    fx = warp_sum(ps.fx);
+    fy = warp_sum(ps.fy);
+    fz = warp_sum(ps.fz);
+    v = warp_sum(ps.v);
   }
-  // deterministic block sum: lane 0 of each warp holds its ion's values
-  __shared__ double s_acc[kForceThreads / 32][7];
-  if (lane == 0)
-    for (int k = 0; k < 7; ++k) s_acc[warp][k] = acc[k];
-  __syncthreads();
+}
+
+// FP32 pre-filter: minimum-image distance below the cutoff plus a margin.
+__device__ __forceinline__ bool pair_filter(const ForceArgs& a, float4 pi32, float4 pj) {
+  const float Lf = a.Lf;
+  float dx = pj.x - pi32.x, dy = pj.y - pi32.y, dz = pj.z - pi32.z;
+  dx -= rintf(dx * a.inv_Lf) * Lf;
+  dy -= rintf(dy * a.inv_Lf) * Lf;
+  dz -= rintf(dz * a.inv_Lf) * Lf;
+  return dx * dx + dy * dy + dz * dz < a.rc2_filter;
+}
+
+// S7 for ion i, one warp: Eq. F_nostra, F = -k_e Q sum_n W (phi_{n+e} -
+// phi_{n-e}) / 2h with the weights k_move stored for this position, and
+// sum_n W phi_n for the discrete energy. Every lane gets the sums.
+__device__ __forceinline__ void gather_el(const ForceArgs& a, int i, int lane, double& gx, double& gy, double& gz,
+                                          double& vd) {
+  const int N = a.N, P = a.P;
+  const int4 first = a.wbase[i];
+  const int P3 = P * P * P;
+  gx = gy = gz = vd = 0;
+  const size_t NN = (size_t)N * N;
+  if (a.mixed) {
+    // mixed precision: FP32 weights, differences of the double-float
+    // potential in FP32, FP32 sums
+    const float* w = a.wbuf32 + (size_t)i * 12;
+    const float2* f = reinterpret_cast<const float2*>(a.phi);
+    float sx = 0.f, sy = 0.f, sz = 0.f, s0 = 0.f;
+    for (int sidx = lane; sidx < P3; sidx += 32) {
+      const int ia = sidx % P, ib = (sidx / P) % P, ic = sidx / (P * P);
+      const int ix = wrap_idx(first.x + ia, N), iy = wrap_idx(first.y + ib, N), iz = wrap_idx(first.z + ic, N);
+      const float wt = w[ia] * w[4 + ib] * w[8 + ic];
+      const size_t row = iz * NN + (size_t)iy * N;
+      const float2 xp = f[row + (ix == N - 1 ? 0 : ix + 1)], xm = f[row + (ix == 0 ? N - 1 : ix - 1)];
+      const float2 yp = f[iz * NN + (size_t)(iy == N - 1 ? 0 : iy + 1) * N + ix];
+      const float2 ym = f[iz * NN + (size_t)(iy == 0 ? N - 1 : iy - 1) * N + ix];
+      const float2 zp = f[(size_t)(iz == N - 1 ? 0 : iz + 1) * NN + (size_t)iy * N + ix];
+      const float2 zm = f[(size_t)(iz == 0 ? N - 1 : iz - 1) * NN + (size_t)iy * N + ix];
+      const float2 c0 = f[row + ix];
+      sx += wt * ((xp.x - xm.x) + (xp.y - xm.y));
+      sy += wt * ((yp.x - ym.x) + (yp.y - ym.y));
+      sz += wt * ((zp.x - zm.x) + (zp.y - zm.y));
+      s0 += wt * (c0.x + c0.y);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      sz += __shfl_xor_sync(0xffffffffu, sz, o);
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    }
+    gx = sx;
+    gy = sy;
+    gz = sz;
+    vd = s0;
+  } else {
+    const double* w = a.wbuf + (size_t)i * 12;
+    for (int sidx = lane; sidx < P3; sidx += 32) {
+      const int ia = sidx % P, ib = (sidx / P) % P, ic = sidx / (P * P);
+      const int ix = wrap_idx(first.x + ia, N), iy = wrap_idx(first.y + ib, N), iz = wrap_idx(first.z + ic, N);
+      const double wt = w[ia] * w[4 + ib] * w[8 + ic];
+      const size_t row = iz * NN + (size_t)iy * N;
+      const size_t ixp = row + (ix == N - 1 ? 0 : ix + 1), ixm = row + (ix == 0 ? N - 1 : ix - 1);
+      const size_t iyp = iz * NN + (size_t)(iy == N - 1 ? 0 : iy + 1) * N + ix;
+      const size_t iym = iz * NN + (size_t)(iy == 0 ? N - 1 : iy - 1) * N + ix;
+      const size_t izp = (size_t)(iz == N - 1 ? 0 : iz + 1) * NN + (size_t)iy * N + ix;
+      const size_t izm = (size_t)(iz == 0 ? N - 1 : iz - 1) * NN + (size_t)iy * N + ix;
+      double px, py, pz, p0;
+      if (a.phi_df) {
+        // double-float potential: differences of the (hi, lo) pairs in FP32
+        const float2* f = reinterpret_cast<const float2*>(a.phi);
+        const float2 xp = f[ixp], xm = f[ixm], yp = f[iyp], ym = f[iym], zp = f[izp], zm = f[izm], c0 = f[row + ix];
+        px = (double)((xp.x - xm.x) + (xp.y - xm.y));
+        py = (double)((yp.x - ym.x) + (yp.y - ym.y));
+        pz = (double)((zp.x - zm.x) + (zp.y - zm.y));
+        p0 = (double)c0.x + (double)c0.y;
+      } else {
+        const double* ph = a.phi;
+        px = ph[ixp] - ph[ixm];
+        py = ph[iyp] - ph[iym];
+        pz = ph[izp] - ph[izm];
+        p0 = ph[row + ix];
+      }
+      gx += wt * px;
+      gy += wt * py;
+      gz += wt * pz;
+      vd += wt * p0;
+    }
+    gx = warp_sum(gx);
+    gy = warp_sum(gy);
+    gz = warp_sum(gz);
+    vd = warp_sum(vd);
+  }
+}
+
+// S9 for ion i (one lane): total force, second half kick, V_work increment
+// (Eq. E_nostra, trapezoid rule), and the ion's energy / momentum terms
+// 0 KE, 1 V_TF (pairs counted twice), 2 1/2 phi.q, 3 dV_work, 4-6 momentum.
+__device__ __forceinline__ void finish_ion(const ForceArgs& a, int i, double gx, double gy, double gz, double vd,
+                                           double ftx, double fty, double ftz, double vtf, double (&acc)[7]) {
+  const int n = a.n;
+  const int t = a.type[i];
+  const double Q = t ? a.charge1 : a.charge0;
+  const double fe = -MAZE_KE_EV_ANGSTROM * Q * a.inv_2h;
+  const double Fex = fe * gx, Fey = fe * gy, Fez = fe * gz;
+  const double Fx = Fex + ftx, Fy = Fey + fty, Fz = Fez + ftz;
+  double vx = a.vel[i], vy = a.vel[n + i], vz = a.vel[2 * n + i];
+  const double m = t ? a.mass1 : a.mass0;
+  double dw = 0.0;
+  if (a.do_kick) {
+    // dV_work = -1/2 (F_el^k + F_el^{k+1}) . dt v_half
+    const double ox = a.force_el[i], oy = a.force_el[n + i], oz = a.force_el[2 * n + i];
+    dw = -0.5 * a.dt * ((ox + Fex) * vx + (oy + Fey) * vy + (oz + Fez) * vz);
+    const double kick = t ? a.kick1 : a.kick0;
+    vx += kick * Fx;
+    vy += kick * Fy;
+    vz += kick * Fz;
+    a.vel[i] = vx;
+    a.vel[n + i] = vy;
+    a.vel[2 * n + i] = vz;
+  }
+  a.force[i] = Fx;
+  a.force[n + i] = Fy;
+  a.force[2 * n + i] = Fz;
+  a.force_el[i] = Fex;
+  a.force_el[n + i] = Fey;
+  a.force_el[2 * n + i] = Fez;
+  acc[0] += a.ke_coef * m * (vx * vx + vy * vy + vz * vz);
+  acc[1] += 0.5 * vtf;
+  acc[2] += 0.5 * MAZE_KE_EV_ANGSTROM * Q * vd;
+  acc[3] += dw;
+  acc[4] += m * vx;
+  acc[5] += m * vy;
+  acc[6] += m * vz;
+}
+
+// Deterministic energy sums: every thread holds the terms of the ions it
+// finished; the block sums them exactly (integer fixed point, see
+// grid_reduce), the last block to finish combines all block partials the
+// same way and publishes the step record.
+__device__ __forceinline__ void energy_reduce(const ForceArgs& a, const double (&acc)[7]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ int s_e[32][7];
+  __shared__ long long s_s[32][7];
   __shared__ bool s_last;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    const int e = (int)__reduce_max_sync(0xffffffffu, (unsigned)dbl_exp(acc[k]));
+    if (lane == 0) s_e[warp][k] = e;
+  }
+  __syncthreads();
+  int E[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    int m = 0;
+    for (int u = 0; u < nw; ++u) m = max(m, s_e[u][k]);
+    E[k] = m + 4;   // headroom for the sum over warps
+    const long long S = warp_isum(dbl_to_fix(acc[k], E[k]));
+    if (lane == 0) s_s[warp][k] = S;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    double b[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int wv = 0; wv < kForceThreads / 32; ++wv)
-      for (int k = 0; k < 7; ++k) b[k] += s_acc[wv][k];
-    for (int k = 0; k < 7; ++k) a.part[blockIdx.x * 8 + k] = b[k];
+    for (int k = 0; k < 7; ++k) {
+      long long S = 0;
+      for (int u = 0; u < nw; ++u) S += s_s[u][k];
+      a.part[blockIdx.x * 8 + k] = fix_to_dbl(S, E[k]);
+    }
     __threadfence();
     const unsigned tk = atomicAdd(a.ticket, 1u);
     s_last = (tk == gridDim.x - 1);
   }
   __syncthreads();
   if (!s_last) return;
-  // last block: sum the block partials in index order and publish the record
   __threadfence();
   if (threadIdx.x < 32) {
     double tot[7];
+    const int G = gridDim.x;
     for (int k = 0; k < 7; ++k) {
-      double v = 0;
-      for (int bb = threadIdx.x; bb < (int)gridDim.x; bb += 32) v += a.part[bb * 8 + k];
-      tot[k] = warp_sum(v);
+      int e = 0;
+      for (int bb = lane; bb < G; bb += 32) e = max(e, dbl_exp(__ldcg(&a.part[bb * 8 + k])));
+      const int Eg = (int)__reduce_max_sync(0xffffffffu, (unsigned)e) + 16;   // up to 2^16 partials per lane-sum
+      long long x = 0;
+      for (int bb = lane; bb < G; bb += 32) x += dbl_to_fix(__ldcg(&a.part[bb * 8 + k]), Eg);
+      tot[k] = fix_to_dbl(warp_isum(x), Eg);
     }
     if (threadIdx.x == 0) {
       maze_stats* r = a.rec;
@@ -559,10 +583,307 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(ForceArgs a) {
   }
 }
 
+// a step whose solve hit max_iter still completes (forces, energies, step
+// count); any other error stops the step
+__device__ __forceinline__ bool forces_live(const ForceArgs& a) {
+  const int st0 = a.rec->status;
+  return *a.gate == 0 && (st0 == MAZE_OK || st0 == MAZE_ERR_NOT_CONVERGED);
+}
+
+// One warp per ion; pair candidates from global memory, filter survivors
+// queued per warp and evaluated 32 at a time (full warps on the FP64 pipe).
+// The warps leave their sums in shared memory and the block finishes its
+// ions one per thread (FP64 work on full lanes).
+__global__ void __launch_bounds__(kForceThreads) k_forces(ForceArgs a) {
+  constexpr int kW = kForceThreads / 32;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * kW + warp;
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  __shared__ int s_queue[kW][64];
+  __shared__ double s_r[kW][8];
+  const bool live = forces_live(a);
+  if (i < a.n && live) {
+    const int n = a.n;
+    const double x = a.pos[i], y = a.pos[n + i], z = a.pos[2 * n + i];
+    const int t = a.type[i];
+    double gx, gy, gz, vd;
+    gather_el(a, i, lane, gx, gy, gz, vd);
+    const float4 pi32 = a.pos32[i];
+    // mixed precision runs this kernel only for boxes without cells, where
+    // the (hi, lo) coordinates are relative to the box corner
+    float4 rih = make_float4(0.f, 0.f, 0.f, 0.f), ril = rih;
+    if (a.mixed) {
+      rih = a.rel_hi[i];
+      ril = a.rel_lo[i];
+    }
+    int* q = s_queue[warp];
+    int qn = 0;
+    PairSum ps;
+    auto eval = [&](int j2) {
+      if (a.mixed) {
+        // box-relative hi/lo coordinates, minimum image -s L as hi/lo
+        const float4 jh = a.rel_hi[j2], jl = a.rel_lo[j2];
+        const float sx = rintf((jh.x - rih.x) * a.inv_Lf), sy = rintf((jh.y - rih.y) * a.inv_Lf),
+                    sz = rintf((jh.z - rih.z) * a.inv_Lf);
+        const float dx = disp_df(rih.x, ril.x, jh.x, jl.x, -sx * a.L_h, -sx * a.L_l);
+        const float dy = disp_df(rih.y, ril.y, jh.y, jl.y, -sy * a.L_h, -sy * a.L_l);
+        const float dz = disp_df(rih.z, ril.z, jh.z, jl.z, -sz * a.L_h, -sz * a.L_l);
+        pair_f(a, t + (int)jl.w, dx, dy, dz, ps);
+      } else {
+        pair_add(a, t, x, y, z, pi32, a.type[j2], a.pos32[j2], a.pos[j2], a.pos[n + j2], a.pos[2 * n + j2], ps);
+      }
+    };
+    auto offer = [&](int j, float4 pj, bool valid) {
+      const bool pass = valid && j != i && pair_filter(a, pi32, pj);
+      const unsigned m = __ballot_sync(0xffffffffu, pass);
+      if (pass) q[qn + __popc(m & ((1u << lane) - 1u))] = j;
+      qn += __popc(m);
+      __syncwarp();
+      if (qn >= 32) {
+        eval(q[lane]);
+        __syncwarp();
+        if (lane < qn - 32) q[lane] = q[32 + lane];
+        __syncwarp();
+        qn -= 32;
+      }
+    };
+    // candidate slots [lo, hi) in chunks of 32, the next chunk's loads issued
+    // before the current chunk is filtered
+    auto scan = [&](int lo, int hi, const int* ids, const float4* pp) {
+      int u = lo + lane;
+      bool v = u < hi;
+      int j = v ? (ids ? ids[u] : u) : -1;
+      float4 pj = v ? pp[u] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int u0 = lo; u0 < hi; u0 += 32) {
+        const int un = u0 + 32 + lane;
+        const bool vn = un < hi;
+        const int jn = vn ? (ids ? ids[un] : un) : -1;
+        const float4 pn = vn ? pp[un] : make_float4(0.f, 0.f, 0.f, 0.f);
+        offer(j, pj, v);
+        j = jn;
+        pj = pn;
+        v = vn;
+      }
+    };
+    if (a.nc >= 3) {
+      const int nc = a.nc;
+      const int c = a.cell_of[i];
+      const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+      int rlo = 0, rhi = 0;
+      if (lane < 27) {
+        const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+        const int cc = (cx + dx + nc) % nc + nc * ((cy + dy + nc) % nc + nc * ((cz + dz + nc) % nc));
+        rlo = a.cell_start[cc];
+        rhi = a.cell_start[cc + 1];
+      }
+      for (int tt = 0; tt < 27; ++tt) {
+        const int lo = __shfl_sync(0xffffffffu, rlo, tt), hi = __shfl_sync(0xffffffffu, rhi, tt);
+        scan(lo, hi, a.cell_ions, a.pos_sorted);
+      }
+    } else {
+      scan(0, n, nullptr, a.pos32);
+    }
+    if (lane < qn) eval(q[lane]);
+    double ftx, fty, ftz, vtf;
+    pair_total(a, ps, ftx, fty, ftz, vtf);
+    if (lane == 0) {
+      s_r[warp][0] = gx;
+      s_r[warp][1] = gy;
+      s_r[warp][2] = gz;
+      s_r[warp][3] = vd;
+      s_r[warp][4] = ftx;
+      s_r[warp][5] = fty;
+      s_r[warp][6] = ftz;
+      s_r[warp][7] = vtf;
+    }
+  }
+  __syncthreads();
+  if (live && threadIdx.x < kW) {
+    const int ii = blockIdx.x * kW + threadIdx.x;
+    if (ii < a.n) {
+      const double* r = s_r[threadIdx.x];
+      finish_ion(a, ii, r[0], r[1], r[2], r[3], r[4], r[5], r[6], r[7], acc);
+    }
+  }
+  energy_reduce(a, acc);
+}
+
+// One block per cell: the candidates of the 27 neighbour cells are staged in
+// shared memory in chunks; each warp takes ions of the cell, queues filter
+// survivors and evaluates them 32 at a time. Pair sums per ion accumulate in
+// shared memory in chunk order (deterministic). FP64 mode stages FP64
+// positions; mixed precision stages the cell-relative hi/lo floats with the
+// neighbour cell's offset folded in, so displacements are exact FP32 sums.
+constexpr int kPairChunk = 896;   // keeps the static shared memory under 48 KB
+constexpr int kCellGroup = 64;
+__global__ void __launch_bounds__(kForceThreads) k_forces_cells(ForceArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  constexpr int kW = kForceThreads / 32;
+  __shared__ float4 s_p[kPairChunk];                 // FP32 position (filter) / hi part
+  __shared__ __align__(16) double s_xyz[3][kPairChunk];  // FP64 positions; mixed: lo parts in rows 0-1
+  double* s_x = s_xyz[0];
+  double* s_y = s_xyz[1];
+  double* s_z = s_xyz[2];
+  __shared__ int s_j[kPairChunk];
+  __shared__ int s_lo[27], s_cum[28];
+  __shared__ double s_f[kCellGroup][8];              // pair sums, then gather sums
+  __shared__ int s_queue[kW][64];
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  const bool live = forces_live(a);
+  if (live) {
+    const int n = a.n, nc = a.nc;
+    const int c = blockIdx.x;
+    const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+    if (threadIdx.x < 27) {
+      const int t = threadIdx.x;
+      const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
+      const int cc = (cx + dx + nc) % nc + nc * ((cy + dy + nc) % nc + nc * ((cz + dz + nc) % nc));
+      s_lo[t] = a.cell_start[cc];
+      s_cum[t + 1] = a.cell_start[cc + 1] - a.cell_start[cc];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_cum[0] = 0;
+      for (int t = 0; t < 27; ++t) s_cum[t + 1] += s_cum[t];
+    }
+    __syncthreads();
+    const int total = s_cum[27];
+    const int clo = a.cell_start[c], chi = a.cell_start[c + 1];
+    float4* s_l = reinterpret_cast<float4*>(&s_xyz[0][0]);   // mixed: lo parts (+ type in w)
+    for (int g0 = clo; g0 < chi; g0 += kCellGroup) {
+      const int gn = min(kCellGroup, chi - g0);
+      for (int e = threadIdx.x; e < gn * 8; e += blockDim.x) s_f[e >> 3][e & 7] = 0.0;
+      for (int ch0 = 0; ch0 < total; ch0 += kPairChunk) {
+        const int len = min(kPairChunk, total - ch0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < len; e += blockDim.x) {
+          const int tt = ch0 + e;
+          int k = 0;
+          while (k < 26 && s_cum[k + 1] <= tt) ++k;
+          const int slot = s_lo[k] + (tt - s_cum[k]);
+          if (a.mixed) {
+            // neighbour offset (dx, dy, dz) * cell_len folded into hi/lo
+            const float ox = (float)(k % 3 - 1), oy = (float)((k / 3) % 3 - 1), oz = (float)(k / 9 - 1);
+            const float4 h = a.rel_hi_sorted[slot], l = a.rel_lo_sorted[slot];
+            float4 hh, ll;
+            // TwoSum of each coordinate with the offset's hi part
+            const float sx = __fadd_rn(h.x, ox * a.cell_len_h), sy = __fadd_rn(h.y, oy * a.cell_len_h),
+                        sz = __fadd_rn(h.z, oz * a.cell_len_h);
+            const float bx = __fsub_rn(sx, h.x), by = __fsub_rn(sy, h.y), bz = __fsub_rn(sz, h.z);
+            const float ex = __fadd_rn(__fsub_rn(h.x, __fsub_rn(sx, bx)), __fsub_rn(ox * a.cell_len_h, bx));
+            const float ey = __fadd_rn(__fsub_rn(h.y, __fsub_rn(sy, by)), __fsub_rn(oy * a.cell_len_h, by));
+            const float ez = __fadd_rn(__fsub_rn(h.z, __fsub_rn(sz, bz)), __fsub_rn(oz * a.cell_len_h, bz));
+            hh = make_float4(sx, sy, sz, h.w);
+            ll = make_float4(__fadd_rn(ex, __fadd_rn(l.x, ox * a.cell_len_l)), __fadd_rn(ey, __fadd_rn(l.y, oy * a.cell_len_l)),
+                             __fadd_rn(ez, __fadd_rn(l.z, oz * a.cell_len_l)), l.w);
+            s_p[e] = hh;
+            s_l[e] = ll;
+            s_j[e] = slot;
+          } else {
+            const int j = a.cell_ions[slot];
+            s_j[e] = j;
+            s_p[e] = a.pos_sorted[slot];
+            s_x[e] = a.pos[j];
+            s_y[e] = a.pos[n + j];
+            s_z[e] = a.pos[2 * n + j];
+          }
+        }
+        __syncthreads();
+        for (int gi = warp; gi < gn; gi += kW) {
+          const int islot = g0 + gi;
+          const int i = a.cell_ions[islot];
+          const double x = a.pos[i], y = a.pos[n + i], z = a.pos[2 * n + i];
+          const int t = a.type[i];
+          float4 pi32, ril = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (a.mixed) {
+            pi32 = a.rel_hi_sorted[islot];
+            ril = a.rel_lo_sorted[islot];
+          } else {
+            pi32 = a.pos_sorted[islot];
+          }
+          const int self = a.mixed ? islot : i;
+          int* q = s_queue[warp];
+          int qn = 0;
+          PairSum ps;
+          auto eval = [&](int e2) {
+            if (a.mixed) {
+              const float4 h = s_p[e2], l = s_l[e2];
+              const float dx = disp_df(pi32.x, ril.x, h.x, l.x, 0.f, 0.f);
+              const float dy = disp_df(pi32.y, ril.y, h.y, l.y, 0.f, 0.f);
+              const float dz = disp_df(pi32.z, ril.z, h.z, l.z, 0.f, 0.f);
+              pair_f(a, t + (int)l.w, dx, dy, dz, ps);
+            } else {
+              pair_add(a, t, x, y, z, pi32, a.type[s_j[e2]], s_p[e2], s_x[e2], s_y[e2], s_z[e2], ps);
+            }
+          };
+          for (int e0 = 0; e0 < len; e0 += 32) {
+            const int e = e0 + lane;
+            bool pass = false;
+            if (e < len && s_j[e] != self) {
+              if (a.mixed) {
+                const float4 h = s_p[e];
+                const float dx = h.x - pi32.x, dy = h.y - pi32.y, dz = h.z - pi32.z;
+                pass = dx * dx + dy * dy + dz * dz < a.rc2_filter;
+              } else {
+                pass = pair_filter(a, pi32, s_p[e]);
+              }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, pass);
+            if (pass) q[qn + __popc(m & ((1u << lane) - 1u))] = e;
+            qn += __popc(m);
+            __syncwarp();
+            if (qn >= 32) {
+              eval(q[lane]);
+              __syncwarp();
+              if (lane < qn - 32) q[lane] = q[32 + lane];
+              __syncwarp();
+              qn -= 32;
+            }
+          }
+          if (lane < qn) eval(q[lane]);
+          __syncwarp();
+          double fx, fy, fz, v;
+          pair_total(a, ps, fx, fy, fz, v);
+          if (lane == 0) {
+            s_f[gi][4] += fx;
+            s_f[gi][5] += fy;
+            s_f[gi][6] += fz;
+            s_f[gi][7] += v;
+          }
+        }
+      }
+      __syncthreads();
+      for (int gi = warp; gi < gn; gi += kW) {
+        double gx, gy, gz, vd;
+        gather_el(a, a.cell_ions[g0 + gi], lane, gx, gy, gz, vd);
+        if (lane == 0) {
+          s_f[gi][0] = gx;
+          s_f[gi][1] = gy;
+          s_f[gi][2] = gz;
+          s_f[gi][3] = vd;
+        }
+      }
+      __syncthreads();
+      // finish the group's ions, one per thread
+      if (threadIdx.x < gn) {
+        const double* r = s_f[threadIdx.x];
+        finish_ion(a, a.cell_ions[g0 + threadIdx.x], r[0], r[1], r[2], r[3], r[4], r[5], r[6], r[7], acc);
+      }
+      __syncthreads();
+    }
+  }
+  energy_reduce(a, acc);
+}
+
 int force_blocks(int n_ions) { return (n_ions + kForceThreads / 32 - 1) / (kForceThreads / 32); }
 
 cudaError_t launch_forces(const ForceArgs& a, int blocks, cudaStream_t s) {
-  k_forces<<<blocks, kForceThreads, 0, s>>>(a);
+  if (a.by_cell)
+    k_forces_cells<<<a.nc * a.nc * a.nc, kForceThreads, 0, s>>>(a);
+  else
+    k_forces<<<blocks, kForceThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -257,6 +257,40 @@ __device__ __forceinline__ df dsum6(const float2* x, const int (&q)[6]) {
   return df_add(df_add(a, b), c);
 }
 
+// One red-black half-sweep of colour c on a level: x = (sum of the six
+// neighbours - b) / 6 at every point of that colour (from_zero: the level's
+// guess is zero, so x = -b/6). A thread takes up to four points per round and
+// issues all of their loads before any store (the loads read the other
+// colour, the stores write this one, so batching is exact).
+__device__ __forceinline__ void half_sweep(float* x, const float* __restrict__ b, int N, int lg, int c,
+                                           bool from_zero, int tid, int stride) {
+  const int hcount = N * N * N / 2;
+  for (int h0 = tid; h0 < hcount; h0 += 4 * stride) {
+    int mm[4];
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int h = h0 + u * stride;
+      mm[u] = -1;
+      v[u] = 0.f;
+      if (h < hcount) {
+        int i, j, k;
+        mm[u] = colour_point(h, N, lg, c, i, j, k);
+        if (from_zero) {
+          v[u] = -b[mm[u]] * (1.f / 6.f);
+        } else {
+          int q[6];
+          nbr_idx<float>(i, j, k, N, q);
+          v[u] = (fsum6(x, q) - b[mm[u]]) * (1.f / 6.f);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (mm[u] >= 0) x[mm[u]] = v[u];
+  }
+}
+
 // The body shared by both launch forms. ``S`` is the sync domain; the
 // participating blocks stride over the points with tid/stride.
 template <class S>
@@ -296,16 +330,30 @@ __device__ void mixed_body(const MixedArgs& a, S& sync) {
     // ---- outer residual r = sigma - M y (double-float), its max, r -> FP32
     {
       float rmax = 0.f;
-      for (int m = tid; m < n; m += stride) {
-        int i, j, k;
-        split3(m, N0, a.lg[0], i, j, k);
-        int q[6];
-        nbr_idx<float>(i, j, k, N0, q);
-        const df My = df_sub(dsum6(a.y, q), df_mul_f(df_from(a.y[m]), 6.f));
-        const df r = df_sub(df_from(a.sigma[m]), My);
-        const float rf = r.h + r.l;
-        a.r0[m] = rf;
-        rmax = fmaxf(rmax, fabsf(rf));
+      for (int m0 = tid; m0 < n; m0 += 2 * stride) {
+        float rf[2];
+        int mm[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int m = m0 + u * stride;
+          mm[u] = m < n ? m : -1;
+          rf[u] = 0.f;
+          if (m < n) {
+            int i, j, k;
+            split3(m, N0, a.lg[0], i, j, k);
+            int q[6];
+            nbr_idx<float>(i, j, k, N0, q);
+            const df My = df_sub(dsum6(a.y, q), df_mul_f(df_from(a.y[m]), 6.f));
+            const df r = df_sub(df_from(a.sigma[m]), My);
+            rf[u] = r.h + r.l;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+          if (mm[u] >= 0) {
+            a.r0[mm[u]] = rf[u];
+            rmax = fmaxf(rmax, fabsf(rf[u]));
+          }
       }
       const double v[1] = {(double)rmax};
       double t[1];
@@ -320,18 +368,7 @@ __device__ void mixed_body(const MixedArgs& a, S& sync) {
       const float* __restrict__ b = l == 0 ? a.r0 : a.lb + a.off[l];
       for (int s = 0; s < a.nu1; ++s) {
         for (int c = 0; c < 2; ++c) {
-          const bool from_zero = (s == 0 && c == 0);
-          for (int h = tid; h < hcount; h += stride) {
-            int i, j, k;
-            const int m = colour_point(h, N, lg, c, i, j, k);
-            if (from_zero) {
-              x[m] = -b[m] * (1.f / 6.f);
-            } else {
-              int q[6];
-              nbr_idx<float>(i, j, k, N, q);
-              x[m] = (fsum6(x, q) - b[m]) * (1.f / 6.f);
-            }
-          }
+          half_sweep(x, b, N, lg, c, s == 0 && c == 0, tid, stride);
           if (!sync.barrier()) return;
         }
       }
@@ -368,23 +405,29 @@ __device__ void mixed_body(const MixedArgs& a, S& sync) {
       if (!sync.barrier()) return;
     }
     {
-      // coarsest: exact zero-mean solve by the pseudo-inverse kernel
+      // coarsest: exact zero-mean solve by the pseudo-inverse kernel. Every
+      // block stages the coarse rhs and the kernel (at most 7^3 values each)
+      // in shared memory; one warp per output point splits the sum.
+      __shared__ float s_cb[343], s_cg[343];
       const int Nc = a.Nl[a.L - 1], NNc = Nc * Nc, nc3 = Nc * NNc;
       const float* bc = a.lb + a.off[a.L - 1];
       float* xc = a.lx + a.off[a.L - 1];
-      for (int p = tid; p < nc3; p += stride) {
+      for (int q = threadIdx.x; q < nc3; q += blockDim.x) {
+        s_cb[q] = bc[q];
+        s_cg[q] = a.gkerf[q];
+      }
+      __syncthreads();
+      const int lane = threadIdx.x & 31;
+      const int wid = tid >> 5, nwarps = stride >> 5;
+      for (int p = wid; p < nc3; p += nwarps) {
         const int pk = p / NNc, pj = (p - pk * NNc) / Nc, pi = p - pk * NNc - pj * Nc;
-        float acc0 = 0.f, acc1 = 0.f;
-        for (int qq = 0; qq < nc3; qq += 2) {
-          const int qk = qq / NNc, qj = (qq - qk * NNc) / Nc, qi = qq - qk * NNc - qj * Nc;
-          acc0 += a.gkerf[wrapi(pi - qi, Nc) + Nc * (wrapi(pj - qj, Nc) + Nc * wrapi(pk - qk, Nc))] * bc[qq];
-          if (qq + 1 < nc3) {
-            const int q1 = qq + 1;
-            const int rk = q1 / NNc, rj = (q1 - rk * NNc) / Nc, ri = q1 - rk * NNc - rj * Nc;
-            acc1 += a.gkerf[wrapi(pi - ri, Nc) + Nc * (wrapi(pj - rj, Nc) + Nc * wrapi(pk - rk, Nc))] * bc[q1];
-          }
+        float acc = 0.f;
+        for (int q = lane; q < nc3; q += 32) {
+          const int qk = q / NNc, qj = (q - qk * NNc) / Nc, qi = q - qk * NNc - qj * Nc;
+          acc += s_cg[wrapi(pi - qi, Nc) + Nc * (wrapi(pj - qj, Nc) + Nc * wrapi(pk - qk, Nc))] * s_cb[q];
         }
-        xc[p] = acc0 + acc1;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) xc[p] = acc;
       }
       if (!sync.barrier()) return;
     }
@@ -408,13 +451,7 @@ __device__ void mixed_body(const MixedArgs& a, S& sync) {
       if (!sync.barrier()) return;
       for (int s = 0; s < a.nu2; ++s) {
         for (int c = 0; c < 2; ++c) {
-          for (int h = tid; h < hcount; h += stride) {
-            int i, j, k;
-            const int m = colour_point(h, N, lg, c, i, j, k);
-            int q[6];
-            nbr_idx<float>(i, j, k, N, q);
-            x[m] = (fsum6(x, q) - b[m]) * (1.f / 6.f);
-          }
+          half_sweep(x, b, N, lg, c, false, tid, stride);
           if (!sync.barrier()) return;
         }
       }
