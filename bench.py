@@ -212,6 +212,13 @@ def config_dict(w, args):
             "l2": "flushed between timed steps (256 MiB write outside the step events)"}
 
 
+def solve_kernel_name(args, w):
+    """The solve kernel a step launches for this precision, solver and grid."""
+    if args.precision == "mixed":
+        return "k_mixed_cluster" if w.N <= 64 else "k_mixed_grid"
+    return "k_mg_solve" if args.solver == "mg" else "k_cg_solve"
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -357,7 +364,7 @@ def main():
             "phase_us": dict(zip(["move_spread", "cells", "solve", "forces"],
                                  [round(1e3 * float(v), 2) for v in np.mean(phase_ms, axis=0)])) if phase_ms else None,
             "solve_gbs": achieved, "solve_us": 1e6 * mean_solve_s,
-            "roofline": {"kernel": "k_mg_solve" if args.solver == "mg" else "k_cg_solve", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "roofline": {"kernel": solve_kernel_name(args, w), "bound": "hbm", "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None,
                          "algorithmic_bytes_per_launch": bytes_launch},

@@ -239,6 +239,97 @@ maze_status maze_solve_shake_noalloc(int32_t grid_N, const double* sigma_p, doub
                                      int32_t max_iter, void* cuda_stream, int32_t* iters,
                                      double* resid_inf);
 
+/* ---------------------------------------------------------------------------
+ * Batched simulations (many independent MaZe boxes on one GPU).
+ *
+ * The paper advances one box at a time; these calls are this library's own
+ * engine for running many of them together. A batch owns one block of device
+ * memory (the arena) from which each admitted simulation takes its buffers,
+ * and a set of slots. Every simulation in a batch advances one MaZe step per
+ * launch of ONE persistent kernel: each thread-block cluster takes whole
+ * boxes, largest first, and runs all phases of that box's step (S1-S9 above)
+ * with cluster barriers, so boxes of different sizes share the GPU without
+ * waiting for each other. The step is replayed from a captured CUDA graph.
+ *
+ * Simulations in a batch run precision MAZE_MIXED with MAZE_SOLVER_MG and
+ * grid_N <= 64. A simulation advanced in a batch computes bit for bit the
+ * positions, velocities, forces and potential it computes alone in a context
+ * of the same configuration (energies agree to rounding).
+ *
+ * Simulation ids are slot indices in [0, max_sims); a removed simulation's id
+ * is reused by a later maze_batch_add. The cuda_stream field of the
+ * maze_config passed to maze_batch_add is ignored: all work of a batch runs
+ * on the batch's stream.
+ */
+typedef struct maze_batch maze_batch;
+
+typedef struct {
+  size_t arena_bytes;    /* device memory reserved for all simulations' buffers (>= 1 MiB) */
+  int32_t max_sims;      /* number of slots, in [1, 65536] */
+  int32_t cluster_ctas;  /* CTAs per cluster of the step kernel (the tile of one box):
+                            1, 2, 4, 8 or 16; 0 selects 4. maze_batch_tune changes it. */
+  void* cuda_stream;     /* cudaStream_t for all of the batch's work; NULL = the batch
+                            creates its own non-blocking stream */
+} maze_batch_config;
+
+/* Create an empty batch: allocates the arena and the per-slot tables.
+ * MAZE_ERR_INVALID for a bad config, MAZE_ERR_OOM when the arena cannot be
+ * allocated, MAZE_ERR_CUDA without an sm_103a device. *out is NULL on error. */
+maze_status maze_batch_create(const maze_batch_config* cfg, maze_batch** out);
+
+/* Arena bytes one simulation of this configuration takes (exact; the
+ * admission test of a serving loop). Needs a CUDA device; validates cfg. */
+maze_status maze_batch_box_bytes(const maze_config* cfg, size_t* bytes);
+
+/* Largest free block and total free bytes of the arena (either may be NULL). */
+maze_status maze_batch_free_bytes(maze_batch* b, size_t* largest_block, size_t* total_free);
+
+/* Admit one simulation: copy its state, take its buffers from the arena and
+ * run its step 0 (as maze_create does) on the batch's stream, synchronously.
+ * On success *id is its slot; it then advances with every maze_batch_step.
+ * MAZE_ERR_OOM when no slot is free or the arena has no room (nothing is
+ * changed; retry after a maze_batch_remove), MAZE_ERR_INVALID for a config
+ * maze_create would reject or that the batch cannot run (see above). */
+maze_status maze_batch_add(maze_batch* b, const maze_config* cfg, int32_t* id);
+
+/* Retire simulation id and return its buffers to the arena. */
+maze_status maze_batch_remove(maze_batch* b, int32_t id);
+
+/* Number of simulations, CTAs per cluster and resident clusters of the step
+ * kernel (any pointer may be NULL). */
+maze_status maze_batch_info(maze_batch* b, int32_t* count, int32_t* cluster_ctas, int32_t* clusters);
+
+/* Advance every simulation of the batch by nsteps MaZe steps (one kernel
+ * launch per step) and synchronise. A simulation whose step fails stops
+ * advancing for the rest of the call (as maze_step does for one context)
+ * while the others continue; the call then returns the first failing
+ * simulation's status and names it in maze_last_error, and
+ * maze_batch_get_stats gives each simulation's own status. */
+maze_status maze_batch_step(maze_batch* b, int32_t nsteps);
+
+/* As maze_batch_step, without waiting for the GPU or checking statuses. */
+maze_status maze_batch_step_async(maze_batch* b, int32_t nsteps);
+
+/* maze_get / maze_set / maze_get_stats for simulation id (synchronise the
+ * batch's stream first). */
+maze_status maze_batch_get(maze_batch* b, int32_t id, int32_t what, double* host_out);
+maze_status maze_batch_set(maze_batch* b, int32_t id, int32_t what, const double* host_in);
+maze_status maze_batch_get_stats(maze_batch* b, int32_t id, maze_stats* out);
+
+/* Statistics of every slot in one call: out[id] for id in [0, max_sims)
+ * (n >= max_sims); a free slot reads step = -1. */
+maze_status maze_batch_get_all_stats(maze_batch* b, maze_stats* out, int32_t n);
+
+/* Autotuner: time steps_per_trial steps with each cluster size the device
+ * can co-schedule (1, 2, 4, 8, 16 CTAs per box), keep the fastest. The
+ * simulations' state is saved before and restored after every trial, so
+ * tuning does not advance them; results do not depend on the cluster size.
+ * Needs a temporary device buffer the size of the arena's used part. */
+maze_status maze_batch_tune(maze_batch* b, int32_t steps_per_trial, int32_t* chosen_ctas, double* ms_per_step);
+
+/* Free every simulation and the batch (NULL-safe). */
+void maze_batch_destroy(maze_batch* b);
+
 /* Library version string, e.g. "maze-gb300 0.1". */
 const char* maze_version(void);
 

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmaze.so")
-SOURCES = ["maze_api.cu", "maze_ions.cu", "maze_solve.cu", "maze_mg.cu", "maze_mixed.cu", "maze_noalloc.cu"]
+SOURCES = ["maze_api.cu", "maze_ions.cu", "maze_solve.cu", "maze_mg.cu", "maze_mixed.cu", "maze_noalloc.cu",
+           "maze_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -36,8 +37,8 @@ def _stale(out: str, deps) -> bool:
 
 def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "maze_internal.cuh"),
-               os.path.join(os.path.dirname(HERE), "include", "maze.h")]
+    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".h"))]
+    headers.append(os.path.join(os.path.dirname(HERE), "include", "maze.h"))
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

@@ -1,0 +1,746 @@
+// Device bodies of the ion-side steps of a MaZe step, shared by the
+// single-box kernels (maze_ions.cu) and the batched step kernel:
+//   S1 half kick + drift, S3 charge spreading (Eq. A11 weights), S2 cell list,
+//   S7 gather of Eq. F_nostra, S8 Tosi-Fumi pairs, S9 half kick and energies.
+#pragma once
+#include <math.h>
+
+#include "maze_internal.cuh"
+
+namespace maze {
+
+// B-spline weights of one axis for an ion at grid coordinate u (Sec. II.A).
+// The support starts at node floor(u) - (P/2 - 1); t = u - floor(u).
+// P = 2: linear B-spline (1 - t, t).
+// P = 4: cubic B-spline ((1-t)^3, 3t^3 - 6t^2 + 4, -3t^3 + 3t^2 + 3t + 1, t^3) / 6.
+// Split u into the first support node and the fractional offset t.
+__device__ __forceinline__ int axis_split(double u, int P, int N, double& t) {
+  const double fl = floor(u);
+  t = u - fl;
+  int first = (int)fl - (P / 2 - 1);
+  if (first < 0) first += N;
+  if (first >= N) first -= N;
+  return first;
+}
+
+// The P weights at fractional offset t (R = double, or float in mixed mode);
+// for P = 2 the two unused slots are zero.
+template <typename R>
+__device__ __forceinline__ void bspline_weights(R t, int P, R* w) {
+  if (P == 2) {
+    w[0] = R(1) - t;
+    w[1] = t;
+    w[2] = R(0);
+    w[3] = R(0);
+  } else {
+    const R t2 = t * t, t3 = t2 * t;
+    const R s = R(1) - t;
+    const R sixth = R(1) / R(6);
+    w[0] = s * s * s * sixth;
+    w[1] = (R(3) * t3 - R(6) * t2 + R(4)) * sixth;
+    w[2] = (R(-3) * t3 + R(3) * t2 + R(3) * t + R(1)) * sixth;
+    w[3] = t3 * sixth;
+  }
+}
+
+__device__ __forceinline__ int wrap_idx(int a, int N) { return a >= N ? a - N : a; }
+
+__device__ __forceinline__ double wrap_pos(double x, double L, double inv_L) {
+  x -= L * floor(x * inv_L);
+  if (x < 0.0) x += L;
+  if (x >= L) x -= L;
+  return x;
+}
+
+// S1 for ion i: Verlet half kick and drift (when a.do_move), the FP32 copy,
+// the cell count and the B-spline weights of the new position (stored: the
+// spread and the gather of the same step reuse them).
+__device__ __forceinline__ void move_ion(const IonArgs& a, int i) {
+  const int N = a.N, P = a.P;
+  {
+    double x = a.pos[i], y = a.pos[a.n + i], z = a.pos[2 * a.n + i];
+    const int t = a.type[i];
+    if (a.do_move) {
+      const double kick = t ? a.kick1 : a.kick0;
+      double vx = a.vel[i] + kick * a.force[i];
+      double vy = a.vel[a.n + i] + kick * a.force[a.n + i];
+      double vz = a.vel[2 * a.n + i] + kick * a.force[2 * a.n + i];
+      a.vel[i] = vx;
+      a.vel[a.n + i] = vy;
+      a.vel[2 * a.n + i] = vz;
+      x = wrap_pos(x + a.dt * vx, a.L, a.inv_L);
+      y = wrap_pos(y + a.dt * vy, a.L, a.inv_L);
+      z = wrap_pos(z + a.dt * vz, a.L, a.inv_L);
+      a.pos[i] = x;
+      a.pos[a.n + i] = y;
+      a.pos[2 * a.n + i] = z;
+    }
+    const double Q = t ? a.charge1 : a.charge0;
+    a.pos32[i] = make_float4((float)x, (float)y, (float)z, (float)Q);
+    int cx = 0, cy = 0, cz = 0;
+    if (a.nc >= 3) {
+      const double cs = a.cell_scale;
+      cx = min((int)(x * cs), a.nc - 1);
+      cy = min((int)(y * cs), a.nc - 1);
+      cz = min((int)(z * cs), a.nc - 1);
+      const int c = cx + a.nc * (cy + a.nc * cz);
+      a.cell_of[i] = c;
+      atomicAdd(&a.cell_count[c], 1);
+    }
+    if (a.rel_hi) {
+      // position relative to the own cell's corner as a (hi, lo) float pair:
+      // pair displacements then need no FP64 arithmetic (mixed precision)
+      const double rx = x - cx * a.cell_len, ry = y - cy * a.cell_len, rz = z - cz * a.cell_len;
+      const float hx = (float)rx, hy = (float)ry, hz = (float)rz;
+      a.rel_hi[i] = make_float4(hx, hy, hz, (float)Q);
+      a.rel_lo[i] = make_float4((float)(rx - hx), (float)(ry - hy), (float)(rz - hz), (float)t);
+    }
+    double tx, ty, tz;
+    const int fx = axis_split(x * a.inv_h, P, N, tx);
+    const int fy = axis_split(y * a.inv_h, P, N, ty);
+    const int fz = axis_split(z * a.inv_h, P, N, tz);
+    if (a.wbuf32) {
+      // mixed precision: FP32 weights from the exact fractional offsets
+      float w[12];
+      bspline_weights<float>((float)tx, P, w);
+      bspline_weights<float>((float)ty, P, w + 4);
+      bspline_weights<float>((float)tz, P, w + 8);
+      float4* gw = reinterpret_cast<float4*>(a.wbuf32 + (size_t)i * 12);
+      gw[0] = make_float4(w[0], w[1], w[2], w[3]);
+      gw[1] = make_float4(w[4], w[5], w[6], w[7]);
+      gw[2] = make_float4(w[8], w[9], w[10], w[11]);
+    } else {
+      double w[12];
+      bspline_weights<double>(tx, P, w);
+      bspline_weights<double>(ty, P, w + 4);
+      bspline_weights<double>(tz, P, w + 8);
+      double* gw = a.wbuf + (size_t)i * 12;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) gw[k] = w[k];
+    }
+    a.wbase[i] = make_int4(fx, fy, fz, 0);
+  }
+}
+
+
+// S3: q_n += Q W(r - r_n), W = w_x w_y w_z over the P^3 support, one warp per
+// ion (lane l takes support points l and l+32), fixed-point atomics. The
+// ion's contributions are made to sum exactly to Q 2^50 (the rounding
+// remainder, found with an exact warp integer sum, goes to support point 0),
+// so a neutral system stays exactly neutral on the grid: the periodic M has
+// no inverse on the constant mode, and a rounding net charge would put a floor
+// under the constraint residual.
+__device__ __forceinline__ void spread_ion(const IonArgs& a, int i, int lane) {
+  const int N = a.N, P = a.P, P3 = P * P * P;
+  const int4 b = a.wbase[i];
+  const double Q = a.type[i] ? a.charge1 : a.charge0;
+  long long v[2] = {0, 0};
+  int idx[2] = {-1, -1};
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int sidx = lane + 32 * u;
+    if (sidx >= P3) continue;
+    const int ia = sidx % P, ib = (sidx / P) % P, ic = sidx / (P * P);
+    if (a.wbuf32) {
+      // mixed precision: FP32 products
+      const float* w = a.wbuf32 + (size_t)i * 12;
+      v[u] = __float2ll_rn((float)Q * w[8 + ic] * w[4 + ib] * w[ia] * (float)kQScale);
+    } else {
+      const double* w = a.wbuf + (size_t)i * 12;
+      v[u] = __double2ll_rn(Q * w[8 + ic] * w[4 + ib] * w[ia] * kQScale);
+    }
+    const int ix = wrap_idx(b.x + ia, N), iy = wrap_idx(b.y + ib, N), iz = wrap_idx(b.z + ic, N);
+    idx[u] = (int)(((size_t)iz * N + iy) * N + ix);
+  }
+  const long long total = warp_isum(v[0] + v[1]);
+  if (lane == 0) v[0] += __double2ll_rn(Q * kQScale) - total;
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+    if (idx[u] >= 0) atomicAdd(&a.qfix[idx[u]], (unsigned long long)v[u]);
+}
+
+// S2: cell list. One block scans the counts (and clears them for the next
+// step), ions claim slots, then each cell sorts its slots by ion index so the
+// pair sums run in a fixed order.
+
+// Exclusive scan of the cell counts by one block of up to 1024 threads.
+__device__ __forceinline__ void cell_scan_block(const CellArgs& a) {
+  __shared__ int s_part[1024];
+  const int T = blockDim.x;
+  const int chunk = (a.ncell + T - 1) / T;
+  const int lo = min(threadIdx.x * chunk, a.ncell), hi = min(lo + chunk, a.ncell);
+  int sum = 0;
+  for (int c = lo; c < hi; ++c) sum += a.cell_count[c];
+  s_part[threadIdx.x] = sum;
+  __syncthreads();
+  // Hillis-Steele inclusive scan over the per-thread sums
+  for (int o = 1; o < T; o <<= 1) {
+    const int v = threadIdx.x >= o ? s_part[threadIdx.x - o] : 0;
+    __syncthreads();
+    s_part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = s_part[threadIdx.x] - sum;
+  for (int c = lo; c < hi; ++c) {
+    a.cell_start[c] = run;
+    a.cursor[c] = run;
+    run += a.cell_count[c];
+    a.cell_count[c] = 0;
+  }
+  if (threadIdx.x == T - 1) a.cell_start[a.ncell] = s_part[T - 1];
+  __syncthreads();
+}
+
+__device__ __forceinline__ void cell_fill_ion(const CellArgs& a, int i) {
+  const int slot = atomicAdd(&a.cursor[a.cell_of[i]], 1);
+  a.cell_ions[slot] = i;
+}
+
+// One warp sorts cell c: each slot's rank among the cell's (distinct) ion
+// indices gives its sorted position (``ids``: kSortCap ints of shared memory).
+// Cells larger than that fall back to an insertion sort by lane 0.
+constexpr int kSortCap = 256;
+__device__ __forceinline__ void cell_sort_one(const CellArgs& a, int c, int lane, int* ids) {
+  const int lo = a.cell_start[c], hi = a.cell_start[c + 1], m = hi - lo;
+  if (m == 0) return;
+  if (m > kSortCap) {
+    if (lane == 0)
+      for (int u = lo + 1; u < hi; ++u) {
+        const int v = a.cell_ions[u];
+        int w = u - 1;
+        while (w >= lo && a.cell_ions[w] > v) {
+          a.cell_ions[w + 1] = a.cell_ions[w];
+          --w;
+        }
+        a.cell_ions[w + 1] = v;
+      }
+    __syncwarp();
+    for (int u = lo + lane; u < hi; u += 32) {
+      const int v = a.cell_ions[u];
+      a.pos_sorted[u] = a.pos32[v];
+      if (a.rel_hi) {
+        a.rel_hi_sorted[u] = a.rel_hi[v];
+        a.rel_lo_sorted[u] = a.rel_lo[v];
+      }
+    }
+    __syncwarp();
+    return;
+  }
+  for (int u = lane; u < m; u += 32) ids[u] = a.cell_ions[lo + u];
+  __syncwarp();
+  for (int u = lane; u < m; u += 32) {
+    const int v = ids[u];
+    int rank = 0;
+    for (int k = 0; k < m; ++k) rank += ids[k] < v;
+    a.cell_ions[lo + rank] = v;
+    a.pos_sorted[lo + rank] = a.pos32[v];
+    if (a.rel_hi) {
+      a.rel_hi_sorted[lo + rank] = a.rel_hi[v];
+      a.rel_lo_sorted[lo + rank] = a.rel_lo[v];
+    }
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void tf_pair(const ForceArgs& a, int kind, double r2, double& fr, double& V) {
+  // V = A exp(B (s - r)) - C r^-6 - D r^-8 - V(r_c);  fr = -(dV/dr) / r.
+  // 1/r by Newton-Raphson for the reciprocal square root, y <- y (3 - r2 y^2)/2,
+  // from an FP32 seed (two steps: ~2^-22 -> 2^-44 -> FP64 rounding), so no FP64
+  // square root or division is needed.
+  double ir = (double)rsqrtf((float)r2);
+  ir = ir * (1.5 - 0.5 * r2 * ir * ir);
+  ir = ir * (1.5 - 0.5 * r2 * ir * ir);
+  const double r = r2 * ir;
+  const double ir2 = ir * ir;
+  const double ir6 = ir2 * ir2 * ir2;
+  const double ir8 = ir6 * ir2;
+  const double ex = a.A[kind] * exp(a.B * (a.s[kind] - r));
+  V = ex - a.C[kind] * ir6 - a.D[kind] * ir8 - a.Vc[kind];
+  fr = a.B * ex * ir - 6.0 * a.C[kind] * ir8 - 8.0 * a.D[kind] * ir8 * ir2;
+}
+
+// Per-lane pair sums (FP64 mode uses the doubles, mixed the floats).
+struct PairSum {
+  double fx = 0, fy = 0, fz = 0, v = 0;
+  float fxf = 0.f, fyf = 0.f, fzf = 0.f, vf = 0.f;
+};
+
+// Tosi-Fumi pair (i, j): minimum image from the FP32 shift and the exact FP64
+// displacement, exact cutoff test, FP64 (or FP32 in mixed mode) arithmetic.
+__device__ __forceinline__ void pair_add(const ForceArgs& a, int ti, double x, double y, double z, float4 pi32,
+                                         int tj, float4 pj, double xj, double yj, double zj, PairSum& ps) {
+  const float iL = a.inv_Lf;
+  const float sx = rintf((pj.x - pi32.x) * iL), sy = rintf((pj.y - pi32.y) * iL), sz = rintf((pj.z - pi32.z) * iL);
+  const double ddx = (xj - x) - (double)sx * a.L;
+  const double ddy = (yj - y) - (double)sy * a.L;
+  const double ddz = (zj - z) - (double)sz * a.L;
+  const int kind = ti + tj;
+  const double r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+  if (r2 >= a.rc2) return;
+  double fr, V;
+  tf_pair(a, kind, r2, fr, V);
+  ps.fx -= fr * ddx;
+  ps.fy -= fr * ddy;
+  ps.fz -= fr * ddz;
+  ps.v += V;
+}
+
+// (rj + off) - ri for positions and offset given as hi + lo float pairs,
+// each addition made error-free by Knuth's TwoSum: the FP32 result carries
+// the displacement to ~1e-7 relative, without FP64 arithmetic.
+__device__ __forceinline__ float disp_df(float rih, float ril, float rjh, float rjl, float offh, float offl) {
+  const float s = __fadd_rn(rjh, offh);
+  const float bb = __fsub_rn(s, rjh);
+  const float e1 = __fadd_rn(__fsub_rn(rjh, __fsub_rn(s, bb)), __fsub_rn(offh, bb));
+  const float d = __fsub_rn(s, rih);
+  const float cc = __fsub_rn(d, s);
+  const float e2 = __fadd_rn(__fsub_rn(s, __fsub_rn(d, cc)), __fsub_rn(-rih, cc));
+  return __fadd_rn(d, __fadd_rn(__fadd_rn(e1, e2), __fsub_rn(__fadd_rn(rjl, offl), ril)));
+}
+
+// Mixed-precision Tosi-Fumi pair from an FP32 displacement.
+__device__ __forceinline__ void pair_f(const ForceArgs& a, int kind, float dx, float dy, float dz, PairSum& ps) {
+  const float r2 = dx * dx + dy * dy + dz * dz;
+  if (r2 >= a.rc2f) return;
+  const float ir = rsqrtf(r2);
+  const float r = r2 * ir;
+  const float ir2 = ir * ir;
+  const float ir6 = ir2 * ir2 * ir2;
+  const float ir8 = ir6 * ir2;
+  const float ex = a.Af[kind] * expf(a.Bf * (a.sf[kind] - r));
+  const float V = ex - a.Cf[kind] * ir6 - a.Df[kind] * ir8 - a.Vcf[kind];
+  const float fr = a.Bf * ex * ir - 6.f * a.Cf[kind] * ir8 - 8.f * a.Df[kind] * ir8 * ir2;
+  ps.fxf -= fr * dx;
+  ps.fyf -= fr * dy;
+  ps.fzf -= fr * dz;
+  ps.vf += V;
+}
+
+// Warp sum of a PairSum into FP64 totals (every lane gets them).
+__device__ __forceinline__ void pair_total(const ForceArgs& a, PairSum& ps, double& fx, double& fy, double& fz, double& v) {
+  if (a.mixed) {
+    for (int o = 16; o > 0; o >>= 1) {
+      ps.fxf += __shfl_xor_sync(0xffffffffu, ps.fxf, o);
+      ps.fyf += __shfl_xor_sync(0xffffffffu, ps.fyf, o);
+      ps.fzf += __shfl_xor_sync(0xffffffffu, ps.fzf, o);
+      ps.vf += __shfl_xor_sync(0xffffffffu, ps.vf, o);
+    }
+    fx = ps.fxf;
+    fy = ps.fyf;
+    fz = ps.fzf;
+    v = ps.vf;
+  } else {
+    fx = warp_sum(ps.fx);
+    fy = warp_sum(ps.fy);
+    fz = warp_sum(ps.fz);
+    v = warp_sum(ps.v);
+  }
+}
+
+// FP32 pre-filter: minimum-image distance below the cutoff plus a margin.
+__device__ __forceinline__ bool pair_filter(const ForceArgs& a, float4 pi32, float4 pj) {
+  const float Lf = a.Lf;
+  float dx = pj.x - pi32.x, dy = pj.y - pi32.y, dz = pj.z - pi32.z;
+  dx -= rintf(dx * a.inv_Lf) * Lf;
+  dy -= rintf(dy * a.inv_Lf) * Lf;
+  dz -= rintf(dz * a.inv_Lf) * Lf;
+  return dx * dx + dy * dy + dz * dz < a.rc2_filter;
+}
+
+// S7 for ion i, one warp: Eq. F_nostra, F = -k_e Q sum_n W (phi_{n+e} -
+// phi_{n-e}) / 2h with the weights k_move stored for this position, and
+// sum_n W phi_n for the discrete energy. Every lane gets the sums.
+__device__ __forceinline__ void gather_el(const ForceArgs& a, int i, int lane, double& gx, double& gy, double& gz,
+                                          double& vd) {
+  const int N = a.N, P = a.P;
+  const int4 first = a.wbase[i];
+  const int P3 = P * P * P;
+  gx = gy = gz = vd = 0;
+  const size_t NN = (size_t)N * N;
+  if (a.mixed) {
+    // mixed precision: FP32 weights, differences of the double-float
+    // potential in FP32, FP32 sums
+    const float* w = a.wbuf32 + (size_t)i * 12;
+    const float2* f = reinterpret_cast<const float2*>(a.phi);
+    float sx = 0.f, sy = 0.f, sz = 0.f, s0 = 0.f;
+    for (int sidx = lane; sidx < P3; sidx += 32) {
+      const int ia = sidx % P, ib = (sidx / P) % P, ic = sidx / (P * P);
+      const int ix = wrap_idx(first.x + ia, N), iy = wrap_idx(first.y + ib, N), iz = wrap_idx(first.z + ic, N);
+      const float wt = w[ia] * w[4 + ib] * w[8 + ic];
+      const size_t row = iz * NN + (size_t)iy * N;
+      const float2 xp = f[row + (ix == N - 1 ? 0 : ix + 1)], xm = f[row + (ix == 0 ? N - 1 : ix - 1)];
+      const float2 yp = f[iz * NN + (size_t)(iy == N - 1 ? 0 : iy + 1) * N + ix];
+      const float2 ym = f[iz * NN + (size_t)(iy == 0 ? N - 1 : iy - 1) * N + ix];
+      const float2 zp = f[(size_t)(iz == N - 1 ? 0 : iz + 1) * NN + (size_t)iy * N + ix];
+      const float2 zm = f[(size_t)(iz == 0 ? N - 1 : iz - 1) * NN + (size_t)iy * N + ix];
+      const float2 c0 = f[row + ix];
+      sx += wt * ((xp.x - xm.x) + (xp.y - xm.y));
+      sy += wt * ((yp.x - ym.x) + (yp.y - ym.y));
+      sz += wt * ((zp.x - zm.x) + (zp.y - zm.y));
+      s0 += wt * (c0.x + c0.y);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      sz += __shfl_xor_sync(0xffffffffu, sz, o);
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    }
+    gx = sx;
+    gy = sy;
+    gz = sz;
+    vd = s0;
+  } else {
+    const double* w = a.wbuf + (size_t)i * 12;
+    for (int sidx = lane; sidx < P3; sidx += 32) {
+      const int ia = sidx % P, ib = (sidx / P) % P, ic = sidx / (P * P);
+      const int ix = wrap_idx(first.x + ia, N), iy = wrap_idx(first.y + ib, N), iz = wrap_idx(first.z + ic, N);
+      const double wt = w[ia] * w[4 + ib] * w[8 + ic];
+      const size_t row = iz * NN + (size_t)iy * N;
+      const size_t ixp = row + (ix == N - 1 ? 0 : ix + 1), ixm = row + (ix == 0 ? N - 1 : ix - 1);
+      const size_t iyp = iz * NN + (size_t)(iy == N - 1 ? 0 : iy + 1) * N + ix;
+      const size_t iym = iz * NN + (size_t)(iy == 0 ? N - 1 : iy - 1) * N + ix;
+      const size_t izp = (size_t)(iz == N - 1 ? 0 : iz + 1) * NN + (size_t)iy * N + ix;
+      const size_t izm = (size_t)(iz == 0 ? N - 1 : iz - 1) * NN + (size_t)iy * N + ix;
+      double px, py, pz, p0;
+      if (a.phi_df) {
+        // double-float potential: differences of the (hi, lo) pairs in FP32
+        const float2* f = reinterpret_cast<const float2*>(a.phi);
+        const float2 xp = f[ixp], xm = f[ixm], yp = f[iyp], ym = f[iym], zp = f[izp], zm = f[izm], c0 = f[row + ix];
+        px = (double)((xp.x - xm.x) + (xp.y - xm.y));
+        py = (double)((yp.x - ym.x) + (yp.y - ym.y));
+        pz = (double)((zp.x - zm.x) + (zp.y - zm.y));
+        p0 = (double)c0.x + (double)c0.y;
+      } else {
+        const double* ph = a.phi;
+        px = ph[ixp] - ph[ixm];
+        py = ph[iyp] - ph[iym];
+        pz = ph[izp] - ph[izm];
+        p0 = ph[row + ix];
+      }
+      gx += wt * px;
+      gy += wt * py;
+      gz += wt * pz;
+      vd += wt * p0;
+    }
+    gx = warp_sum(gx);
+    gy = warp_sum(gy);
+    gz = warp_sum(gz);
+    vd = warp_sum(vd);
+  }
+}
+
+// S9 for ion i (one lane): total force, second half kick, V_work increment
+// (Eq. E_nostra, trapezoid rule), and the ion's energy / momentum terms
+// 0 KE, 1 V_TF (pairs counted twice), 2 1/2 phi.q, 3 dV_work, 4-6 momentum.
+__device__ __forceinline__ void finish_ion(const ForceArgs& a, int i, double gx, double gy, double gz, double vd,
+                                           double ftx, double fty, double ftz, double vtf, double (&acc)[7]) {
+  const int n = a.n;
+  const int t = a.type[i];
+  const double Q = t ? a.charge1 : a.charge0;
+  const double fe = -MAZE_KE_EV_ANGSTROM * Q * a.inv_2h;
+  const double Fex = fe * gx, Fey = fe * gy, Fez = fe * gz;
+  const double Fx = Fex + ftx, Fy = Fey + fty, Fz = Fez + ftz;
+  double vx = a.vel[i], vy = a.vel[n + i], vz = a.vel[2 * n + i];
+  const double m = t ? a.mass1 : a.mass0;
+  double dw = 0.0;
+  if (a.do_kick) {
+    // dV_work = -1/2 (F_el^k + F_el^{k+1}) . dt v_half
+    const double ox = a.force_el[i], oy = a.force_el[n + i], oz = a.force_el[2 * n + i];
+    dw = -0.5 * a.dt * ((ox + Fex) * vx + (oy + Fey) * vy + (oz + Fez) * vz);
+    const double kick = t ? a.kick1 : a.kick0;
+    vx += kick * Fx;
+    vy += kick * Fy;
+    vz += kick * Fz;
+    a.vel[i] = vx;
+    a.vel[n + i] = vy;
+    a.vel[2 * n + i] = vz;
+  }
+  a.force[i] = Fx;
+  a.force[n + i] = Fy;
+  a.force[2 * n + i] = Fz;
+  a.force_el[i] = Fex;
+  a.force_el[n + i] = Fey;
+  a.force_el[2 * n + i] = Fez;
+  acc[0] += a.ke_coef * m * (vx * vx + vy * vy + vz * vz);
+  acc[1] += 0.5 * vtf;
+  acc[2] += 0.5 * MAZE_KE_EV_ANGSTROM * Q * vd;
+  acc[3] += dw;
+  acc[4] += m * vx;
+  acc[5] += m * vy;
+  acc[6] += m * vz;
+}
+
+// a step whose solve hit max_iter still completes (forces, energies, step
+// count); any other error stops the step
+__device__ __forceinline__ bool forces_live(const ForceArgs& a) {
+  const int st0 = a.rec->status;
+  return *a.gate == 0 && (st0 == MAZE_OK || st0 == MAZE_ERR_NOT_CONVERGED);
+}
+
+// S7 + S8 for ion i, one warp: the gather of Eq. F_nostra and the Tosi-Fumi
+// pair sums over candidates from global memory (the cell list, or all ions),
+// filter survivors queued in ``q`` (64 ints of shared memory per warp) and
+// evaluated 32 at a time. Every lane returns r = (gx, gy, gz, vd, Fx, Fy, Fz,
+// V_TF). Mixed precision takes this path only for boxes without cells, where
+// the (hi, lo) coordinates are relative to the box corner.
+__device__ __forceinline__ void forces_ion_warp(const ForceArgs& a, int i, int lane, int* q, double (&r)[8]) {
+  const int n = a.n;
+  const double x = a.pos[i], y = a.pos[n + i], z = a.pos[2 * n + i];
+  const int t = a.type[i];
+  double gx, gy, gz, vd;
+  gather_el(a, i, lane, gx, gy, gz, vd);
+  const float4 pi32 = a.pos32[i];
+  float4 rih = make_float4(0.f, 0.f, 0.f, 0.f), ril = rih;
+  if (a.mixed) {
+    rih = a.rel_hi[i];
+    ril = a.rel_lo[i];
+  }
+  int qn = 0;
+  PairSum ps;
+  auto eval = [&](int j2) {
+    if (a.mixed) {
+      // box-relative hi/lo coordinates, minimum image -s L as hi/lo
+      const float4 jh = a.rel_hi[j2], jl = a.rel_lo[j2];
+      const float sx = rintf((jh.x - rih.x) * a.inv_Lf), sy = rintf((jh.y - rih.y) * a.inv_Lf),
+                  sz = rintf((jh.z - rih.z) * a.inv_Lf);
+      const float dx = disp_df(rih.x, ril.x, jh.x, jl.x, -sx * a.L_h, -sx * a.L_l);
+      const float dy = disp_df(rih.y, ril.y, jh.y, jl.y, -sy * a.L_h, -sy * a.L_l);
+      const float dz = disp_df(rih.z, ril.z, jh.z, jl.z, -sz * a.L_h, -sz * a.L_l);
+      pair_f(a, t + (int)jl.w, dx, dy, dz, ps);
+    } else {
+      pair_add(a, t, x, y, z, pi32, a.type[j2], a.pos32[j2], a.pos[j2], a.pos[n + j2], a.pos[2 * n + j2], ps);
+    }
+  };
+  auto offer = [&](int j, float4 pj, bool valid) {
+    const bool pass = valid && j != i && pair_filter(a, pi32, pj);
+    const unsigned m = __ballot_sync(0xffffffffu, pass);
+    if (pass) q[qn + __popc(m & ((1u << lane) - 1u))] = j;
+    qn += __popc(m);
+    __syncwarp();
+    if (qn >= 32) {
+      eval(q[lane]);
+      __syncwarp();
+      if (lane < qn - 32) q[lane] = q[32 + lane];
+      __syncwarp();
+      qn -= 32;
+    }
+  };
+  // candidate slots [lo, hi) in chunks of 32, the next chunk's loads issued
+  // before the current chunk is filtered
+  auto scan = [&](int lo, int hi, const int* ids, const float4* pp) {
+    int u = lo + lane;
+    bool v = u < hi;
+    int j = v ? (ids ? ids[u] : u) : -1;
+    float4 pj = v ? pp[u] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int u0 = lo; u0 < hi; u0 += 32) {
+      const int un = u0 + 32 + lane;
+      const bool vn = un < hi;
+      const int jn = vn ? (ids ? ids[un] : un) : -1;
+      const float4 pn = vn ? pp[un] : make_float4(0.f, 0.f, 0.f, 0.f);
+      offer(j, pj, v);
+      j = jn;
+      pj = pn;
+      v = vn;
+    }
+  };
+  if (a.nc >= 3) {
+    const int nc = a.nc;
+    const int c = a.cell_of[i];
+    const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+    int rlo = 0, rhi = 0;
+    if (lane < 27) {
+      const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+      const int cc = (cx + dx + nc) % nc + nc * ((cy + dy + nc) % nc + nc * ((cz + dz + nc) % nc));
+      rlo = a.cell_start[cc];
+      rhi = a.cell_start[cc + 1];
+    }
+    for (int tt = 0; tt < 27; ++tt) {
+      const int lo = __shfl_sync(0xffffffffu, rlo, tt), hi = __shfl_sync(0xffffffffu, rhi, tt);
+      scan(lo, hi, a.cell_ions, a.pos_sorted);
+    }
+  } else {
+    scan(0, n, nullptr, a.pos32);
+  }
+  if (lane < qn) eval(q[lane]);
+  double ftx, fty, ftz, vtf;
+  pair_total(a, ps, ftx, fty, ftz, vtf);
+  r[0] = gx;
+  r[1] = gy;
+  r[2] = gz;
+  r[3] = vd;
+  r[4] = ftx;
+  r[5] = fty;
+  r[6] = ftz;
+  r[7] = vtf;
+}
+
+// S7 + S8 for the ions of slice s (of ``split``) of cell c, one block of kW
+// warps: the candidates of the 27 neighbour cells are staged in shared memory
+// in chunks; each warp takes ions of the slice, queues filter survivors and
+// evaluates them 32 at a time. Pair sums per ion accumulate in shared memory
+// in chunk order, so the result does not depend on kW or the slicing. FP64
+// mode stages FP64 positions; mixed precision stages the cell-relative hi/lo
+// floats with the neighbour cell's offset folded in, so displacements are
+// exact FP32 sums. The slice's ions are finished one per thread into acc.
+constexpr int kPairChunk = 896;
+constexpr int kCellGroup = 64;
+template <int kW>
+struct CellSmem {
+  float4 p[kPairChunk];                          // FP32 position (filter) / hi part
+  __align__(16) double xyz[3][kPairChunk];       // FP64 positions; mixed: lo parts in rows 0-1
+  int j[kPairChunk];
+  int lo[27], cum[28];
+  double f[kCellGroup][8];                       // pair sums, then gather sums
+  int queue[kW][64];
+};
+
+template <int kW>
+__device__ __forceinline__ void forces_cell_slice(const ForceArgs& a, int c, int s, int split, CellSmem<kW>& sm,
+                                                  double (&acc)[7]) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int n = a.n, nc = a.nc;
+  __syncthreads();   // the previous slice's readers of sm are done
+  const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+  if (threadIdx.x < 27) {
+    const int t = threadIdx.x;
+    const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
+    const int cc = (cx + dx + nc) % nc + nc * ((cy + dy + nc) % nc + nc * ((cz + dz + nc) % nc));
+    sm.lo[t] = a.cell_start[cc];
+    sm.cum[t + 1] = a.cell_start[cc + 1] - a.cell_start[cc];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sm.cum[0] = 0;
+    for (int t = 0; t < 27; ++t) sm.cum[t + 1] += sm.cum[t];
+  }
+  __syncthreads();
+  const int total = sm.cum[27];
+  const int c0 = a.cell_start[c], cn = a.cell_start[c + 1] - c0;
+  const int per = (cn + split - 1) / split;
+  const int clo = c0 + min(cn, s * per), chi = c0 + min(cn, (s + 1) * per);
+  float4* s_l = reinterpret_cast<float4*>(&sm.xyz[0][0]);   // mixed: lo parts (+ type in w)
+  for (int g0 = clo; g0 < chi; g0 += kCellGroup) {
+    const int gn = min(kCellGroup, chi - g0);
+    for (int e = threadIdx.x; e < gn * 8; e += blockDim.x) sm.f[e >> 3][e & 7] = 0.0;
+    for (int ch0 = 0; ch0 < total; ch0 += kPairChunk) {
+      const int len = min(kPairChunk, total - ch0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < len; e += blockDim.x) {
+        const int tt = ch0 + e;
+        int k = 0;
+        while (k < 26 && sm.cum[k + 1] <= tt) ++k;
+        const int slot = sm.lo[k] + (tt - sm.cum[k]);
+        if (a.mixed) {
+          // neighbour offset (dx, dy, dz) * cell_len folded into hi/lo
+          const float ox = (float)(k % 3 - 1), oy = (float)((k / 3) % 3 - 1), oz = (float)(k / 9 - 1);
+          const float4 h = a.rel_hi_sorted[slot], l = a.rel_lo_sorted[slot];
+          float4 hh, ll;
+          // TwoSum of each coordinate with the offset's hi part
+          const float sx = __fadd_rn(h.x, ox * a.cell_len_h), sy = __fadd_rn(h.y, oy * a.cell_len_h),
+                      sz = __fadd_rn(h.z, oz * a.cell_len_h);
+          const float bx = __fsub_rn(sx, h.x), by = __fsub_rn(sy, h.y), bz = __fsub_rn(sz, h.z);
+          const float ex = __fadd_rn(__fsub_rn(h.x, __fsub_rn(sx, bx)), __fsub_rn(ox * a.cell_len_h, bx));
+          const float ey = __fadd_rn(__fsub_rn(h.y, __fsub_rn(sy, by)), __fsub_rn(oy * a.cell_len_h, by));
+          const float ez = __fadd_rn(__fsub_rn(h.z, __fsub_rn(sz, bz)), __fsub_rn(oz * a.cell_len_h, bz));
+          hh = make_float4(sx, sy, sz, h.w);
+          ll = make_float4(__fadd_rn(ex, __fadd_rn(l.x, ox * a.cell_len_l)), __fadd_rn(ey, __fadd_rn(l.y, oy * a.cell_len_l)),
+                           __fadd_rn(ez, __fadd_rn(l.z, oz * a.cell_len_l)), l.w);
+          sm.p[e] = hh;
+          s_l[e] = ll;
+          sm.j[e] = slot;
+        } else {
+          const int j = a.cell_ions[slot];
+          sm.j[e] = j;
+          sm.p[e] = a.pos_sorted[slot];
+          sm.xyz[0][e] = a.pos[j];
+          sm.xyz[1][e] = a.pos[n + j];
+          sm.xyz[2][e] = a.pos[2 * n + j];
+        }
+      }
+      __syncthreads();
+      for (int gi = warp; gi < gn; gi += kW) {
+        const int islot = g0 + gi;
+        const int i = a.cell_ions[islot];
+        const double x = a.pos[i], y = a.pos[n + i], z = a.pos[2 * n + i];
+        const int t = a.type[i];
+        float4 pi32, ril = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (a.mixed) {
+          pi32 = a.rel_hi_sorted[islot];
+          ril = a.rel_lo_sorted[islot];
+        } else {
+          pi32 = a.pos_sorted[islot];
+        }
+        const int self = a.mixed ? islot : i;
+        int* q = sm.queue[warp];
+        int qn = 0;
+        PairSum ps;
+        auto eval = [&](int e2) {
+          if (a.mixed) {
+            const float4 h = sm.p[e2], l = s_l[e2];
+            const float dx = disp_df(pi32.x, ril.x, h.x, l.x, 0.f, 0.f);
+            const float dy = disp_df(pi32.y, ril.y, h.y, l.y, 0.f, 0.f);
+            const float dz = disp_df(pi32.z, ril.z, h.z, l.z, 0.f, 0.f);
+            pair_f(a, t + (int)l.w, dx, dy, dz, ps);
+          } else {
+            pair_add(a, t, x, y, z, pi32, a.type[sm.j[e2]], sm.p[e2], sm.xyz[0][e2], sm.xyz[1][e2], sm.xyz[2][e2], ps);
+          }
+        };
+        for (int e0 = 0; e0 < len; e0 += 32) {
+          const int e = e0 + lane;
+          bool pass = false;
+          if (e < len && sm.j[e] != self) {
+            if (a.mixed) {
+              const float4 h = sm.p[e];
+              const float dx = h.x - pi32.x, dy = h.y - pi32.y, dz = h.z - pi32.z;
+              pass = dx * dx + dy * dy + dz * dz < a.rc2_filter;
+            } else {
+              pass = pair_filter(a, pi32, sm.p[e]);
+            }
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, pass);
+          if (pass) q[qn + __popc(m & ((1u << lane) - 1u))] = e;
+          qn += __popc(m);
+          __syncwarp();
+          if (qn >= 32) {
+            eval(q[lane]);
+            __syncwarp();
+            if (lane < qn - 32) q[lane] = q[32 + lane];
+            __syncwarp();
+            qn -= 32;
+          }
+        }
+        if (lane < qn) eval(q[lane]);
+        __syncwarp();
+        double fx, fy, fz, v;
+        pair_total(a, ps, fx, fy, fz, v);
+        if (lane == 0) {
+          sm.f[gi][4] += fx;
+          sm.f[gi][5] += fy;
+          sm.f[gi][6] += fz;
+          sm.f[gi][7] += v;
+        }
+      }
+    }
+    __syncthreads();
+    for (int gi = warp; gi < gn; gi += kW) {
+      double gx, gy, gz, vd;
+      gather_el(a, a.cell_ions[g0 + gi], lane, gx, gy, gz, vd);
+      if (lane == 0) {
+        sm.f[gi][0] = gx;
+        sm.f[gi][1] = gy;
+        sm.f[gi][2] = gz;
+        sm.f[gi][3] = vd;
+      }
+    }
+    __syncthreads();
+    // finish the group's ions, one per thread
+    if (threadIdx.x < gn) {
+      const double* r = sm.f[threadIdx.x];
+      finish_ion(a, a.cell_ions[g0 + threadIdx.x], r[0], r[1], r[2], r[3], r[4], r[5], r[6], r[7], acc);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace maze

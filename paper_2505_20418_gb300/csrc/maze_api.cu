@@ -10,15 +10,16 @@
 #include <string>
 #include <vector>
 
-#include "maze_internal.cuh"
+#include "maze_ctx.h"
 
 using namespace maze;
 
 namespace {
-
 thread_local std::string g_err;
+constexpr uint64_t kBlobMagic = 0x4d415a4530314250ull;  // "MAZE01BP"
+}  // namespace
 
-maze_status fail(maze_status s, const std::string& msg) {
+maze_status maze::fail(maze_status s, const std::string& msg) {
   g_err = msg;
   return s;
 }
@@ -32,75 +33,23 @@ maze_status fail(maze_status s, const std::string& msg) {
     }                                                                                         \
   } while (0)
 
-constexpr double kPi = 3.14159265358979323846;
-constexpr uint64_t kBlobMagic = 0x4d415a4530314250ull;  // "MAZE01BP"
-
-}  // namespace
-
 void maze::set_last_error(const char* msg) { g_err = msg; }
 
-struct maze_ctx {
-  maze_config cfg;
-  int n = 0, N = 0, P = 4;
-  size_t ng = 0;
-  double L = 0, h = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  // ions, SoA [3][n]
-  double *pos = nullptr, *vel = nullptr, *force = nullptr, *force_el = nullptr;
-  int* type = nullptr;
-  float4* pos32 = nullptr;
-  double* wbuf = nullptr;   // [n][3][4] B-spline weights of the current positions
-  float* wbuf32 = nullptr;  // FP32 weights (mixed precision)
-  int4* wbase = nullptr;
-  // grid
-  unsigned long long* qfix = nullptr;
-  double* qd = nullptr;
-  double* phi[3] = {nullptr, nullptr, nullptr};
-  int ik = 0;  // phi^k is phi[ik], phi^{k-1} phi[(ik+1)%3], scratch phi[(ik+2)%3]
-  double *sigma = nullptr, *y = nullptr, *r = nullptr, *p = nullptr, *p1 = nullptr, *Mp = nullptr;
-  LLRec* recs = nullptr;
-  size_t recs_bytes = 0;
-  unsigned* bar = nullptr;
-  // multigrid
-  MgArgs mg = {};
-  double *mg_x = nullptr, *mg_b = nullptr, *mg_r = nullptr, *mg_g = nullptr;
-  // mixed precision: phi, y, sigma hold double-float pairs (float2, 8 B)
-  bool mixed = false;
-  MixedArgs mx = {};
-  int mx_cluster = 0, mx_blocks = 0;
-  float *mx_e0 = nullptr, *mx_r0 = nullptr, *mx_lx = nullptr, *mx_lb = nullptr, *mx_lr = nullptr, *mx_g = nullptr;
-  int sblocks = 0;
-  // cells
-  int nc = 0, ncell = 0;
-  int *cell_of = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cursor = nullptr, *cell_ions = nullptr;
-  float4* pos_sorted = nullptr;
-  float4 *rel_hi = nullptr, *rel_lo = nullptr, *rel_hi_s = nullptr, *rel_lo_s = nullptr;
-  // force reductions
-  double* fpart = nullptr;
-  unsigned* ticket = nullptr;
-  int fblocks = 0;
-  int num_sms = 0;
-  maze_stats* rec = nullptr;       // device
-  int* gate = nullptr;             // device: current step skipped
-  maze_stats* rec_host = nullptr;  // pinned
-  cudaGraphExec_t graph[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
-  bool graphs_tried[2] = {false, false}, graphs_ok[2] = {false, false};
-  int timing = 0;
-  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  int max_iter_init = 20000;
-  std::vector<void*> allocs;
-};
 
-namespace {
+namespace maze {
 
 template <typename T>
 maze_status dalloc(maze_ctx* c, T** p, size_t count) {
   void* v = nullptr;
-  cudaError_t e = cudaMalloc(&v, count * sizeof(T) + 16);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(MAZE_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  if (c->arena) {
+    v = c->arena->alloc(count * sizeof(T) + 16);
+    if (!v) return fail(MAZE_ERR_OOM, "the batch's device memory arena is full");
+  } else {
+    cudaError_t e = cudaMalloc(&v, count * sizeof(T) + 16);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MAZE_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
   }
   c->allocs.push_back(v);
   *p = static_cast<T*>(v);
@@ -238,6 +187,7 @@ ForceArgs force_args(maze_ctx* c, const double* phi, int do_kick, int count_step
   // one block per cell when the box has cells and either enough of them to
   // fill the GPU or FP32 pair arithmetic (mixed precision)
   a.by_cell = (c->nc >= 3 && (c->mixed || c->ncell >= 2 * c->num_sms)) ? 1 : 0;
+  a.cell_split = c->cell_split;
   a.wbuf32 = c->wbuf32;
   a.wbuf = c->wbuf;
   a.wbase = c->wbase;
@@ -467,13 +417,16 @@ void free_ctx(maze_ctx* c) {
       if (c->graph[t][g]) cudaGraphExecDestroy(c->graph[t][g]);
   for (int k = 0; k < 5; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
-  for (void* p : c->allocs) cudaFree(p);
+  for (void* p : c->allocs) {
+    if (c->arena) c->arena->release(p);
+    else cudaFree(p);
+  }
   if (c->rec_host) cudaFreeHost(c->rec_host);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
 
-}  // namespace
+}  // namespace maze
 
 extern "C" {
 
@@ -481,8 +434,13 @@ const char* maze_last_error(void) { return g_err.c_str(); }
 
 const char* maze_version(void) { return "maze-gb300 0.1"; }
 
-maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
-  if (!out) return fail(MAZE_ERR_INVALID, "out is NULL");
+}  // extern "C"
+
+namespace maze {
+
+// Checks, layout and device buffers of a context (no uploads, no kernels).
+// With a counting arena nothing is allocated and no stream is created.
+maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
   *out = nullptr;
   maze_status s = validate(cfg);
   if (s != MAZE_OK) return s;
@@ -498,6 +456,7 @@ maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
   if (!coop) return fail(MAZE_ERR_CUDA, "device does not support cooperative launch");
 
   maze_ctx* c = new maze_ctx();
+  c->arena = arena;
   c->cfg = *cfg;
   c->cfg.pos = c->cfg.vel = nullptr;
   c->cfg.type = nullptr;
@@ -509,7 +468,7 @@ maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
   c->h = cfg->box_L / cfg->grid_N;
   if (cfg->cuda_stream) {
     c->stream = (cudaStream_t)cfg->cuda_stream;
-  } else {
+  } else if (!(arena && arena->counting())) {
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
       delete c;
       return fail(MAZE_ERR_CUDA, "cudaStreamCreate failed");
@@ -524,6 +483,14 @@ maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
   c->sblocks = cfg->solver == MAZE_SOLVER_MG ? mg_blocks((int)ng) : solve_blocks((int)ng);
   c->fblocks = force_blocks(n);
   if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) c->num_sms = 1;
+  if (c->ncell > 0) {
+    // few cells (small boxes): split each cell's ions over several blocks of
+    // the by-cell force kernel, about one ion per warp, up to two blocks per SM
+    const int per_warp = (n + c->ncell - 1) / c->ncell;
+    const int by_ions = (per_warp + kForceThreads / 32 - 1) / (kForceThreads / 32);
+    const int by_sms = (2 * c->num_sms + c->ncell - 1) / c->ncell;
+    c->cell_split = std::max(1, std::min(by_ions, by_sms));
+  }
 #define AL(p, cnt)                          \
   do {                                      \
     maze_status s_ = dalloc(c, &(p), (cnt)); \
@@ -538,24 +505,31 @@ maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
   AL(c->force_el, 3 * (size_t)n);
   AL(c->type, (size_t)n);
   AL(c->pos32, (size_t)n);
-  AL(c->wbuf, 12 * (size_t)n);
-  AL(c->wbuf32, 12 * (size_t)n);
-  AL(c->rel_hi, (size_t)n);
-  AL(c->rel_lo, (size_t)n);
+  // each precision allocates only the buffers its kernels touch
+  const bool mixed = cfg->precision == MAZE_MIXED;
+  if (mixed) {
+    AL(c->wbuf32, 12 * (size_t)n);
+    AL(c->rel_hi, (size_t)n);
+    AL(c->rel_lo, (size_t)n);
+  } else {
+    AL(c->wbuf, 12 * (size_t)n);
+  }
   AL(c->wbase, (size_t)n);
   AL(c->qfix, ng);
   AL(c->qd, ng);
   for (int g = 0; g < 3; ++g) AL(c->phi[g], ng);
   AL(c->sigma, ng);
   AL(c->y, ng);
-  AL(c->r, ng);
-  AL(c->p, ng);
-  AL(c->p1, ng);
-  AL(c->Mp, ng);
+  if (cfg->solver == MAZE_SOLVER_CG) {
+    AL(c->r, ng);
+    AL(c->p, ng);
+    AL(c->p1, ng);
+    AL(c->Mp, ng);
+  }
   c->recs_bytes = 2 * (size_t)c->sblocks * 4 * 16;
   AL(c->recs, 2 * (size_t)c->sblocks * 4);
   AL(c->bar, 4);
-  std::vector<double> gk;
+  std::vector<double>& gk = c->gk;
   if (cfg->solver == MAZE_SOLVER_MG) {
     // hierarchy: halve while the edge is even and >= 8
     MgArgs& g = c->mg;
@@ -570,18 +544,19 @@ maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
     }
     g.nu1 = cfg->mg_pre;
     g.nu2 = cfg->mg_post;
-    AL(c->mg_x, tot);
-    AL(c->mg_b, tot);
-    AL(c->mg_r, tot);
+    if (!mixed) {
+      AL(c->mg_x, tot);
+      AL(c->mg_b, tot);
+      AL(c->mg_r, tot);
+    }
     const int Nc = g.Nl[g.L - 1];
     gk = coarse_kernel(Nc);
-    AL(c->mg_g, gk.size());
+    if (!mixed) AL(c->mg_g, gk.size());
     g.x = c->mg_x;
     g.b = c->mg_b;
     g.r = c->mg_r;
     g.gker = c->mg_g;
   }
-  std::vector<float> gkf;
   if (cfg->precision == MAZE_MIXED) {
     c->mixed = true;
     MixedArgs& m = c->mx;
@@ -604,8 +579,7 @@ maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
     AL(c->mx_lx, tot);
     AL(c->mx_lb, tot);
     AL(c->mx_lr, tot);
-    gkf.assign(gk.begin(), gk.end());
-    AL(c->mx_g, gkf.size());
+    AL(c->mx_g, gk.size());
     m.e0 = c->mx_e0;
     m.r0 = c->mx_r0;
     m.lx = c->mx_lx;
@@ -635,14 +609,32 @@ maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
     AL(c->cursor, (size_t)c->ncell);
     AL(c->cell_ions, (size_t)n);
     AL(c->pos_sorted, (size_t)n);
-    AL(c->rel_hi_s, (size_t)n);
-    AL(c->rel_lo_s, (size_t)n);
+    if (mixed) {
+      AL(c->rel_hi_s, (size_t)n);
+      AL(c->rel_lo_s, (size_t)n);
+    }
   }
-  AL(c->fpart, (size_t)std::max(c->fblocks, c->ncell) * 8);
+  AL(c->fpart, (size_t)std::max(c->fblocks, c->ncell * c->cell_split) * 8);
   AL(c->ticket, 4);
   AL(c->rec, 1);
   AL(c->gate, 1);
 #undef AL
+  *out = c;
+  return MAZE_OK;
+}
+
+// Full creation: setup, pinned stats buffer, upload, step 0 (spread, solve
+// from zero, phi^{-1} = phi^0, y = 0, forces F^0 and energies).
+maze_status ctx_create(const maze_config* cfg, Arena* arena, maze_ctx** out) {
+  if (!out) return fail(MAZE_ERR_INVALID, "out is NULL");
+  maze_ctx* c = nullptr;
+  maze_status s = ctx_setup(cfg, arena, &c);
+  if (s != MAZE_OK) return s;
+  const int n = c->n;
+  const size_t ng = c->ng;
+  const std::vector<double>& gk = c->gk;
+  std::vector<float> gkf;
+  if (c->mixed) gkf.assign(gk.begin(), gk.end());
   if (cudaMallocHost(&c->rec_host, sizeof(maze_stats)) != cudaSuccess) {
     free_ctx(c);
     return fail(MAZE_ERR_OOM, "cudaMallocHost failed");
@@ -666,7 +658,7 @@ maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
     for (int i = 0; i < n; ++i) tmp[(size_t)d * n + i] = cfg->vel[3 * i + d];
   CKC(cudaMemcpyAsync(c->vel, tmp.data(), tmp.size() * 8, cudaMemcpyHostToDevice, st));
   CKC(cudaMemcpyAsync(c->type, cfg->type, (size_t)n * 4, cudaMemcpyHostToDevice, st));
-  if (!gk.empty()) CKC(cudaMemcpyAsync(c->mg_g, gk.data(), gk.size() * 8, cudaMemcpyHostToDevice, st));
+  if (!gk.empty() && c->mg_g) CKC(cudaMemcpyAsync(c->mg_g, gk.data(), gk.size() * 8, cudaMemcpyHostToDevice, st));
   if (!gkf.empty()) CKC(cudaMemcpyAsync(c->mx_g, gkf.data(), gkf.size() * 4, cudaMemcpyHostToDevice, st));
   CKC(cudaMemsetAsync(c->force, 0, 3 * (size_t)n * 8, st));
   CKC(cudaMemsetAsync(c->force_el, 0, 3 * (size_t)n * 8, st));
@@ -709,6 +701,24 @@ maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
   *out = c;
   return MAZE_OK;
 }
+
+maze_status ctx_bytes(const maze_config* cfg, size_t* bytes) {
+  if (!bytes) return fail(MAZE_ERR_INVALID, "bytes is NULL");
+  Arena counter(nullptr, (size_t)1 << 62);
+  maze_ctx* c = nullptr;
+  maze_status s = ctx_setup(cfg, &counter, &c);
+  if (s != MAZE_OK) return s;
+  *bytes = counter.used();
+  free_ctx(c);
+  return MAZE_OK;
+}
+
+}  // namespace maze
+
+extern "C" {
+
+maze_status maze_create(const maze_config* cfg, maze_ctx** out) { return ctx_create(cfg, nullptr, out); }
+
 
 void maze_destroy(maze_ctx* ctx) { free_ctx(ctx); }
 

@@ -1,0 +1,712 @@
+// Batched MaZe: many independent simulations ("boxes", each a full MaZe
+// context with its own ions, grid and warm-start potential) resident in one
+// device-memory arena and advanced by ONE persistent kernel launch per step,
+// replayed from a captured CUDA graph.
+//
+// Each thread-block cluster of the step kernel takes whole boxes from a work
+// queue (largest first) and runs every phase of that box's step with cluster
+// barriers only: S1 move, S3 spread, S2 cell list, S4-S6 mixed-precision
+// constraint solve (the body of the single-box cluster solver), S7-S9 forces,
+// half kick and energies. Boxes never synchronise with each other, so there
+// is no grid-wide barrier; a box's data (a few MB) stays in L2 for its step.
+//
+// The device bodies are the ones the single-box kernels run, and every
+// reduction in them is exact or partition-independent, so a box advanced in
+// a batch produces bit for bit the positions, velocities, forces and
+// potential of the same box advanced alone (energies agree to rounding).
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <iterator>
+#include <string>
+#include <vector>
+
+#include "ion_body.cuh"
+#include "maze_ctx.h"
+#include "mixed_body.cuh"
+
+namespace maze {
+
+// ---------------------------------------------------------------------------
+// Arena
+
+Arena::Arena(char* base, size_t capacity) : base_(base), cap_(capacity), counting_(base == nullptr) {
+  if (!counting_) free_[0] = capacity;
+}
+
+void* Arena::alloc(size_t bytes) {
+  const size_t need = (bytes + 255) & ~(size_t)255;
+  if (counting_) {
+    const size_t off = used_bytes_;
+    used_bytes_ += need;
+    return reinterpret_cast<void*>((uintptr_t)4096 + off);
+  }
+  for (auto it = free_.begin(); it != free_.end(); ++it) {
+    if (it->second < need) continue;
+    const size_t off = it->first, rest = it->second - need;
+    free_.erase(it);
+    if (rest) free_[off + need] = rest;
+    taken_[off] = need;
+    used_bytes_ += need;
+    return base_ + off;
+  }
+  return nullptr;
+}
+
+void Arena::release(void* p) {
+  if (counting_ || !p) return;
+  const size_t off = (size_t)(static_cast<char*>(p) - base_);
+  auto t = taken_.find(off);
+  if (t == taken_.end()) return;
+  size_t size = t->second;
+  taken_.erase(t);
+  used_bytes_ -= size;
+  auto nx = free_.lower_bound(off);
+  if (nx != free_.end() && off + size == nx->first) {
+    size += nx->second;
+    nx = free_.erase(nx);
+  }
+  if (nx != free_.begin()) {
+    auto pv = std::prev(nx);
+    if (pv->first + pv->second == off) {
+      pv->second += size;
+      return;
+    }
+  }
+  free_[off] = size;
+}
+
+size_t Arena::largest_free() const {
+  size_t m = 0;
+  for (const auto& kv : free_) m = std::max(m, kv.second);
+  return m;
+}
+
+size_t Arena::high_water() const { return taken_.empty() ? 0 : taken_.rbegin()->first + taken_.rbegin()->second; }
+
+// ---------------------------------------------------------------------------
+// Device side
+
+// Everything one box's step needs; phi pointers are patched per step from
+// the box's rotation index.
+struct __align__(16) BoxDesc {
+  IonArgs ion;
+  CellArgs cell;
+  ForceArgs force;
+  MixedArgs mixed;
+  float2* phi[3];
+  int split;   // (cell, slice) work items per cell in the force phase
+};
+
+constexpr int kBatchThreads = 1024;
+constexpr int kBatchWarps = kBatchThreads / 32;
+static_assert(sizeof(CellSmem<kBatchWarps>) >= (size_t)kBatchWarps * kSortCap * sizeof(int),
+              "the sort's id buffers alias the force staging buffer");
+
+struct BatchArgs {
+  const BoxDesc* desc;  // [slots]
+  int* ik;              // [slots] phi^k of each box is phi[ik]
+  const int* order;     // [count] slots, most expensive first
+  const int* count;
+  unsigned* queue;      // next entry of ``order``; zero before each launch
+};
+
+__device__ __forceinline__ int cluster_ld_int(const int* p, unsigned rank) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  unsigned r;
+  int v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(r) : "memory");
+  return v;
+}
+
+__global__ void __launch_bounds__(kBatchThreads, 1) k_batch_step(BatchArgs b) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  CellSmem<kBatchWarps>& csm = *reinterpret_cast<CellSmem<kBatchWarps>*>(dyn);
+  __shared__ BoxDesc d;
+  __shared__ int s_box[2];
+  ClusterSync sync;
+  const unsigned rank = (unsigned)sync.rank();
+  const int C = sync.size();
+  const int tid = (int)rank * blockDim.x + threadIdx.x, stride = C * blockDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gwarp = tid >> 5, nwarps = stride >> 5;
+  const int count = *b.count;
+  const bool msum7[7] = {false, false, false, false, false, false, false};
+  for (int it = 0;; ++it) {
+    // the first CTA claims the next box; the others read its claim over
+    // DSMEM (double-buffered: a claim is overwritten two barriers later)
+    const int par = it & 1;
+    if (rank == 0 && threadIdx.x == 0) s_box[par] = (int)atomicAdd(b.queue, 1u);
+    sync.barrier();
+    const int k = cluster_ld_int(&s_box[par], 0);
+    if (k >= count) break;
+    const int slot = b.order[k];
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(b.desc + slot);
+      uint4* dst = reinterpret_cast<uint4*>(&d);
+      for (int w = threadIdx.x; w < (int)(sizeof(BoxDesc) / 16); w += blockDim.x) dst[w] = src[w];
+    }
+    const int ik = b.ik[slot];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      d.mixed.phi_k = d.phi[ik];
+      d.mixed.phi_km1 = d.phi[(ik + 1) % 3];
+      d.mixed.phi_out = d.phi[(ik + 2) % 3];
+      d.force.phi = reinterpret_cast<const double*>(d.phi[(ik + 2) % 3]);
+    }
+    __syncthreads();
+    // a box whose earlier step in this call failed is skipped (every CTA
+    // reads the same value: nothing writes it before the next barrier)
+    if (__ldcg(&d.ion.rec->status) != MAZE_OK) continue;
+    const int n = d.ion.n, nc = d.ion.nc;
+    // S1: half kick + drift, weights, cell counts
+    for (int i = tid; i < n; i += stride) move_ion(d.ion, i);
+    sync.barrier();
+    // S3: spread (one warp per ion); S2: the first CTA scans the cell counts
+    if (nc >= 3 && rank == 0) cell_scan_block(d.cell);
+    for (int i = gwarp; i < n; i += nwarps) spread_ion(d.ion, i, lane);
+    sync.barrier();
+    if (nc >= 3) {
+      for (int i = tid; i < n; i += stride) cell_fill_ion(d.cell, i);
+      sync.barrier();
+      // the sort's buffers alias the force staging, which is used only after
+      // the solve's barriers
+      int* ids = reinterpret_cast<int*>(dyn) + warp * kSortCap;
+      for (int c = gwarp; c < d.cell.ncell; c += nwarps) cell_sort_one(d.cell, c, lane, ids);
+    }
+    // S4-S6 (its first barrier also orders the sort before the forces)
+    mixed_body(d.mixed, sync);
+    const int st = __ldcg(&d.force.rec->status);
+    if (st != MAZE_OK && st != MAZE_ERR_NOT_CONVERGED) continue;
+    // S7-S9
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (nc >= 3) {
+      const int items = d.cell.ncell * d.split;
+      for (int w = (int)rank; w < items; w += C)
+        forces_cell_slice<kBatchWarps>(d.force, w / d.split, w % d.split, d.split, csm, acc);
+    } else {
+      for (int i = gwarp; i < n; i += nwarps) {
+        double r[8];
+        forces_ion_warp(d.force, i, lane, csm.queue[warp], r);
+        if (lane == 0) finish_ion(d.force, i, r[0], r[1], r[2], r[3], r[4], r[5], r[6], r[7], acc);
+      }
+    }
+    double tot[7];
+    sync.reduce(acc, msum7, tot);
+    if (rank == 0 && threadIdx.x == 0) {
+      maze_stats* r = d.force.rec;
+      r->ke = tot[0];
+      r->v_tf = tot[1];
+      r->v_disc = tot[2];
+      r->v_work += tot[3];
+      r->e_tot = tot[0] + tot[1] + r->v_work;
+      r->momentum[0] = tot[4];
+      r->momentum[1] = tot[5];
+      r->momentum[2] = tot[6];
+      r->step += 1;
+      if (!isfinite(r->e_tot)) r->status = MAZE_ERR_NONFINITE;
+      b.ik[slot] = (ik + 2) % 3;
+    }
+  }
+  // no CTA leaves while another may still read its shared memory
+  sync.barrier();
+}
+
+__global__ void k_batch_clear(const BoxDesc* desc, const int* order, const int* count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < *count) desc[order[i]].ion.rec->status = MAZE_OK;
+}
+
+__global__ void k_batch_stats(const BoxDesc* desc, const int* order, const int* count, maze_stats* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < *count) {
+    const int s = order[i];
+    out[s] = *desc[s].ion.rec;
+  }
+}
+
+}  // namespace maze
+
+using namespace maze;
+
+struct maze_batch {
+  maze_batch_config cfg = {};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  char* arena_base = nullptr;
+  Arena* arena = nullptr;
+  std::vector<maze_ctx*> box;     // [slots]; nullptr = free slot
+  std::vector<double> cost;       // [slots] relative cost of one step
+  std::vector<int> active;        // scheduling order of the last upload
+  BoxDesc* d_desc = nullptr;
+  int* d_ik = nullptr;
+  int* d_order = nullptr;
+  int* d_count = nullptr;
+  unsigned* d_queue = nullptr;
+  maze_stats* d_stats = nullptr;
+  int* h_order = nullptr;         // pinned: order + count
+  maze_stats* h_stats = nullptr;  // pinned
+  int* h_ik = nullptr;            // pinned
+  bool dirty = true;
+  int cluster = 4;
+  int nclusters = 0;
+  cudaGraphExec_t graph = nullptr;
+  int graph_cluster = 0;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) {                                                                  \
+      return fail(e_ == cudaErrorMemoryAllocation ? MAZE_ERR_OOM : MAZE_ERR_CUDA,             \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+    }                                                                                         \
+  } while (0)
+
+int slots(const maze_batch* b) { return (int)b->box.size(); }
+
+maze_status check_id(const maze_batch* b, int id) {
+  if (!b) return fail(MAZE_ERR_INVALID, "batch is NULL");
+  if (id < 0 || id >= slots(b) || !b->box[id]) return fail(MAZE_ERR_INVALID, "no simulation with this id");
+  return MAZE_OK;
+}
+
+// Largest cluster of the step kernel the device co-schedules (16 needs the
+// non-portable size), and the number of such clusters resident at once.
+int max_clusters(int cta) {
+  cudaFuncSetAttribute(k_batch_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(CellSmem<kBatchWarps>));
+  if (cta > 8) cudaFuncSetAttribute(k_batch_step, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cta);
+  cfg.blockDim = dim3(kBatchThreads);
+  cfg.dynamicSmemBytes = sizeof(CellSmem<kBatchWarps>);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cta;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_batch_step, &cfg) != cudaSuccess) n = 0;
+  cudaGetLastError();
+  return n;
+}
+
+maze_status launch_step(maze_batch* b) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(b->nclusters * b->cluster);
+  cfg.blockDim = dim3(kBatchThreads);
+  cfg.dynamicSmemBytes = sizeof(CellSmem<kBatchWarps>);
+  cfg.stream = b->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = b->cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  BatchArgs a;
+  a.desc = b->d_desc;
+  a.ik = b->d_ik;
+  a.order = b->d_order;
+  a.count = b->d_count;
+  a.queue = b->d_queue;
+  CK(cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned), b->stream));
+  CK(cudaLaunchKernelEx(&cfg, k_batch_step, a));
+  return MAZE_OK;
+}
+
+maze_status set_cluster(maze_batch* b, int cta) {
+  const int n = max_clusters(cta);
+  if (n < 1) return fail(MAZE_ERR_INVALID, "the device cannot co-schedule a cluster of " + std::to_string(cta) + " CTAs");
+  b->cluster = cta;
+  b->nclusters = n;
+  return MAZE_OK;
+}
+
+// One graph per step: reset the work queue, launch the persistent kernel.
+maze_status build_graph(maze_batch* b) {
+  if (b->graph && b->graph_cluster == b->cluster) return MAZE_OK;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  maze_status s = launch_step(b);
+  cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+  if (s != MAZE_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) return fail(MAZE_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(MAZE_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  b->graph_cluster = b->cluster;
+  return MAZE_OK;
+}
+
+// Upload the scheduling order (longest-processing-time first) after a
+// change of membership.
+maze_status upload_order(maze_batch* b) {
+  if (!b->dirty) return MAZE_OK;
+  CK(cudaStreamSynchronize(b->stream));
+  b->active.clear();
+  for (int s = 0; s < slots(b); ++s)
+    if (b->box[s]) b->active.push_back(s);
+  std::stable_sort(b->active.begin(), b->active.end(), [&](int x, int y) { return b->cost[x] > b->cost[y]; });
+  const int n = (int)b->active.size();
+  for (int k = 0; k < n; ++k) b->h_order[k] = b->active[k];
+  b->h_order[slots(b)] = n;
+  CK(cudaMemcpyAsync(b->d_order, b->h_order, sizeof(int) * (size_t)std::max(n, 1), cudaMemcpyHostToDevice, b->stream));
+  CK(cudaMemcpyAsync(b->d_count, b->h_order + slots(b), sizeof(int), cudaMemcpyHostToDevice, b->stream));
+  b->dirty = false;
+  return MAZE_OK;
+}
+
+maze_status read_all_stats(maze_batch* b) {
+  const int n = (int)b->active.size();
+  if (n > 0) {
+    k_batch_stats<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_desc, b->d_order, b->d_count, b->d_stats);
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemcpyAsync(b->h_stats, b->d_stats, sizeof(maze_stats) * (size_t)slots(b), cudaMemcpyDeviceToHost, b->stream));
+  CK(cudaMemcpyAsync(b->h_ik, b->d_ik, sizeof(int) * (size_t)slots(b), cudaMemcpyDeviceToHost, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  for (int s : b->active) b->box[s]->ik = b->h_ik[s];
+  return MAZE_OK;
+}
+
+// Bring a box's host-side rotation index up to date before a host access.
+maze_status sync_box(maze_batch* b, int id) {
+  CK(cudaStreamSynchronize(b->stream));
+  int ik = 0;
+  CK(cudaMemcpy(&ik, b->d_ik + id, sizeof(int), cudaMemcpyDeviceToHost));
+  b->box[id]->ik = ik;
+  return MAZE_OK;
+}
+
+maze_status step_async(maze_batch* b, int nsteps) {
+  maze_status s = upload_order(b);
+  if (s != MAZE_OK) return s;
+  if (b->active.empty() || nsteps == 0) return MAZE_OK;
+  s = build_graph(b);
+  if (s != MAZE_OK) return s;
+  const int n = (int)b->active.size();
+  k_batch_clear<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_desc, b->d_order, b->d_count);
+  CK(cudaGetLastError());
+  for (int k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(b->graph, b->stream));
+  return MAZE_OK;
+}
+
+void destroy(maze_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (maze_ctx* c : b->box)
+    if (c) free_ctx(c);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (auto& e : b->ev)
+    if (e) cudaEventDestroy(e);
+  cudaFree(b->d_desc);
+  cudaFree(b->d_ik);
+  cudaFree(b->d_order);
+  cudaFree(b->d_count);
+  cudaFree(b->d_queue);
+  cudaFree(b->d_stats);
+  if (b->h_order) cudaFreeHost(b->h_order);
+  if (b->h_stats) cudaFreeHost(b->h_stats);
+  if (b->h_ik) cudaFreeHost(b->h_ik);
+  delete b->arena;
+  cudaFree(b->arena_base);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+maze_status maze_batch_create(const maze_batch_config* cfg, maze_batch** out) {
+  if (!out) return fail(MAZE_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return fail(MAZE_ERR_INVALID, "config is NULL");
+  if (cfg->max_sims < 1 || cfg->max_sims > 65536) return fail(MAZE_ERR_INVALID, "max_sims must be in [1, 65536]");
+  if (cfg->arena_bytes < ((size_t)1 << 20)) return fail(MAZE_ERR_INVALID, "arena_bytes must be at least 1 MiB");
+  const int cta = cfg->cluster_ctas ? cfg->cluster_ctas : 4;
+  if (cta != 1 && cta != 2 && cta != 4 && cta != 8 && cta != 16)
+    return fail(MAZE_ERR_INVALID, "cluster_ctas must be 0, 1, 2, 4, 8 or 16");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, dev));
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(MAZE_ERR_CUDA, "libmaze is built for sm_103a (GB300); this device is sm_" +
+                                   std::to_string(prop.major) + std::to_string(prop.minor));
+  maze_batch* b = new maze_batch();
+  b->cfg = *cfg;
+  const int S = cfg->max_sims;
+  b->box.assign(S, nullptr);
+  b->cost.assign(S, 0.0);
+  auto bad = [&](maze_status s) {
+    std::string keep = maze_last_error();
+    destroy(b);
+    return fail(s, keep);
+  };
+#define BK(call)                                                                                      \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess) {                                                                          \
+      fail(e_ == cudaErrorMemoryAllocation ? MAZE_ERR_OOM : MAZE_ERR_CUDA,                            \
+           std::string(#call) + ": " + cudaGetErrorString(e_));                                       \
+      return bad(e_ == cudaErrorMemoryAllocation ? MAZE_ERR_OOM : MAZE_ERR_CUDA);                     \
+    }                                                                                                 \
+  } while (0)
+  if (cfg->cuda_stream) {
+    b->stream = (cudaStream_t)cfg->cuda_stream;
+  } else {
+    BK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+    b->own_stream = true;
+  }
+  BK(cudaMalloc(&b->arena_base, cfg->arena_bytes));
+  b->arena = new Arena(b->arena_base, cfg->arena_bytes);
+  BK(cudaMalloc(&b->d_desc, sizeof(BoxDesc) * (size_t)S));
+  BK(cudaMalloc(&b->d_ik, sizeof(int) * (size_t)S));
+  BK(cudaMalloc(&b->d_order, sizeof(int) * (size_t)S));
+  BK(cudaMalloc(&b->d_count, sizeof(int)));
+  BK(cudaMalloc(&b->d_queue, sizeof(unsigned)));
+  BK(cudaMalloc(&b->d_stats, sizeof(maze_stats) * (size_t)S));
+  BK(cudaMallocHost(&b->h_order, sizeof(int) * (size_t)(S + 1)));
+  BK(cudaMallocHost(&b->h_stats, sizeof(maze_stats) * (size_t)S));
+  BK(cudaMallocHost(&b->h_ik, sizeof(int) * (size_t)S));
+  BK(cudaMemsetAsync(b->d_ik, 0, sizeof(int) * (size_t)S, b->stream));
+  BK(cudaMemsetAsync(b->d_count, 0, sizeof(int), b->stream));
+  BK(cudaMemsetAsync(b->d_stats, 0, sizeof(maze_stats) * (size_t)S, b->stream));
+  BK(cudaEventCreate(&b->ev[0]));
+  BK(cudaEventCreate(&b->ev[1]));
+  BK(cudaStreamSynchronize(b->stream));
+#undef BK
+  maze_status s = set_cluster(b, cta);
+  if (s != MAZE_OK) return bad(s);
+  *out = b;
+  return MAZE_OK;
+}
+
+void maze_batch_destroy(maze_batch* b) { destroy(b); }
+
+maze_status maze_batch_box_bytes(const maze_config* cfg, size_t* bytes) {
+  if (!cfg || !bytes) return fail(MAZE_ERR_INVALID, "NULL argument");
+  if (cfg->precision != MAZE_MIXED || cfg->solver != MAZE_SOLVER_MG)
+    return fail(MAZE_ERR_INVALID, "batched simulations run mixed precision with the multigrid solver");
+  if (cfg->grid_N > 64) return fail(MAZE_ERR_INVALID, "batched simulations need grid_N <= 64");
+  return ctx_bytes(cfg, bytes);
+}
+
+maze_status maze_batch_free_bytes(maze_batch* b, size_t* largest_block, size_t* total_free) {
+  if (!b) return fail(MAZE_ERR_INVALID, "batch is NULL");
+  if (largest_block) *largest_block = b->arena->largest_free();
+  if (total_free) *total_free = b->arena->capacity() - b->arena->used();
+  return MAZE_OK;
+}
+
+maze_status maze_batch_add(maze_batch* b, const maze_config* cfg, int32_t* id) {
+  if (!b || !cfg || !id) return fail(MAZE_ERR_INVALID, "NULL argument");
+  *id = -1;
+  if (cfg->precision != MAZE_MIXED || cfg->solver != MAZE_SOLVER_MG)
+    return fail(MAZE_ERR_INVALID, "batched simulations run mixed precision with the multigrid solver");
+  if (cfg->grid_N > 64) return fail(MAZE_ERR_INVALID, "batched simulations need grid_N <= 64");
+  int slot = -1;
+  for (int s = 0; s < slots(b); ++s)
+    if (!b->box[s]) {
+      slot = s;
+      break;
+    }
+  if (slot < 0) return fail(MAZE_ERR_OOM, "every simulation slot of the batch is in use");
+  CK(cudaStreamSynchronize(b->stream));
+  maze_config c2 = *cfg;
+  c2.cuda_stream = b->stream;
+  maze_ctx* c = nullptr;
+  maze_status s = ctx_create(&c2, b->arena, &c);
+  if (s != MAZE_OK) return s;
+  BoxDesc d;
+  memset(&d, 0, sizeof d);
+  d.ion = ion_args(c, 1, 1);
+  d.cell = cell_args(c);
+  d.force = force_args(c, nullptr, 1, 1);
+  d.mixed = mixed_args(c, 0, nullptr);
+  for (int g = 0; g < 3; ++g) d.phi[g] = reinterpret_cast<float2*>(c->phi[g]);
+  const int per_cell = c->ncell > 0 ? (c->n + c->ncell - 1) / c->ncell : 0;
+  d.split = std::max(1, (per_cell + kBatchWarps - 1) / kBatchWarps);
+  cudaError_t e = cudaMemcpyAsync(b->d_desc + slot, &d, sizeof d, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_ik + slot, &c->ik, sizeof(int), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    free_ctx(c);
+    return fail(MAZE_ERR_CUDA, std::string("upload of the box descriptor: ") + cudaGetErrorString(e));
+  }
+  b->box[slot] = c;
+  // relative cost of one step: grid points (V-cycles) and ions (pairs)
+  b->cost[slot] = (double)c->ng + 24.0 * c->n;
+  b->dirty = true;
+  *id = slot;
+  return MAZE_OK;
+}
+
+maze_status maze_batch_remove(maze_batch* b, int32_t id) {
+  maze_status s = check_id(b, id);
+  if (s != MAZE_OK) return s;
+  CK(cudaStreamSynchronize(b->stream));
+  free_ctx(b->box[id]);
+  b->box[id] = nullptr;
+  b->cost[id] = 0.0;
+  b->dirty = true;
+  return MAZE_OK;
+}
+
+maze_status maze_batch_info(maze_batch* b, int32_t* count, int32_t* cluster_ctas, int32_t* clusters) {
+  if (!b) return fail(MAZE_ERR_INVALID, "batch is NULL");
+  int n = 0;
+  for (maze_ctx* c : b->box) n += c ? 1 : 0;
+  if (count) *count = n;
+  if (cluster_ctas) *cluster_ctas = b->cluster;
+  if (clusters) *clusters = b->nclusters;
+  return MAZE_OK;
+}
+
+maze_status maze_batch_step_async(maze_batch* b, int32_t nsteps) {
+  if (!b) return fail(MAZE_ERR_INVALID, "batch is NULL");
+  if (nsteps < 0) return fail(MAZE_ERR_INVALID, "nsteps must be >= 0");
+  return step_async(b, nsteps);
+}
+
+maze_status maze_batch_step(maze_batch* b, int32_t nsteps) {
+  if (!b) return fail(MAZE_ERR_INVALID, "batch is NULL");
+  if (nsteps < 0) return fail(MAZE_ERR_INVALID, "nsteps must be >= 0");
+  maze_status s = step_async(b, nsteps);
+  if (s != MAZE_OK) return s;
+  s = read_all_stats(b);
+  if (s != MAZE_OK) return s;
+  for (int id : b->active) {
+    const int st = b->h_stats[id].status;
+    if (st == MAZE_OK) continue;
+    char buf[200];
+    snprintf(buf, sizeof buf, "simulation %d: device status %d (residual %.3e after %d iterations)", id, st,
+             b->h_stats[id].resid, b->h_stats[id].iters);
+    return fail((maze_status)st, buf);
+  }
+  return MAZE_OK;
+}
+
+maze_status maze_batch_get(maze_batch* b, int32_t id, int32_t what, double* out) {
+  maze_status s = check_id(b, id);
+  if (s != MAZE_OK) return s;
+  s = sync_box(b, id);
+  if (s != MAZE_OK) return s;
+  return maze_get(b->box[id], what, out);
+}
+
+maze_status maze_batch_set(maze_batch* b, int32_t id, int32_t what, const double* in) {
+  maze_status s = check_id(b, id);
+  if (s != MAZE_OK) return s;
+  s = sync_box(b, id);
+  if (s != MAZE_OK) return s;
+  return maze_set(b->box[id], what, in);
+}
+
+maze_status maze_batch_get_stats(maze_batch* b, int32_t id, maze_stats* out) {
+  maze_status s = check_id(b, id);
+  if (s != MAZE_OK) return s;
+  s = sync_box(b, id);
+  if (s != MAZE_OK) return s;
+  return maze_get_stats(b->box[id], out);
+}
+
+maze_status maze_batch_get_all_stats(maze_batch* b, maze_stats* out, int32_t n) {
+  if (!b || !out) return fail(MAZE_ERR_INVALID, "NULL argument");
+  if (n < slots(b)) return fail(MAZE_ERR_INVALID, "out must hold max_sims entries");
+  maze_status s = upload_order(b);
+  if (s != MAZE_OK) return s;
+  s = read_all_stats(b);
+  if (s != MAZE_OK) return s;
+  for (int i = 0; i < slots(b); ++i) {
+    if (b->box[i]) {
+      out[i] = b->h_stats[i];
+    } else {
+      memset(&out[i], 0, sizeof(maze_stats));
+      out[i].step = -1;
+    }
+  }
+  return MAZE_OK;
+}
+
+maze_status maze_batch_tune(maze_batch* b, int32_t steps_per_trial, int32_t* chosen_ctas, double* ms_per_step) {
+  if (!b) return fail(MAZE_ERR_INVALID, "batch is NULL");
+  if (steps_per_trial < 1) return fail(MAZE_ERR_INVALID, "steps_per_trial must be >= 1");
+  maze_status s = upload_order(b);
+  if (s != MAZE_OK) return s;
+  if (b->active.empty()) return fail(MAZE_ERR_INVALID, "the batch holds no simulation");
+  // every trial starts from the same state: snapshot the arena (all boxes'
+  // buffers and statistics) and the rotation indices, restore after each
+  const size_t hw = b->arena->high_water();
+  const size_t ikb = sizeof(int) * (size_t)slots(b);
+  char* snap = nullptr;
+  CK(cudaStreamSynchronize(b->stream));
+  CK(cudaMalloc(&snap, hw + ikb));
+  auto save = [&]() -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(snap, b->arena_base, hw, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(snap + hw, b->d_ik, ikb, cudaMemcpyDeviceToDevice, b->stream);
+    return e;
+  };
+  auto restore = [&]() -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(b->arena_base, snap, hw, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_ik, snap + hw, ikb, cudaMemcpyDeviceToDevice, b->stream);
+    return e;
+  };
+  const int cand[5] = {1, 2, 4, 8, 16};
+  const int keep = b->cluster;
+  int best = keep;
+  double best_ms = 1e300;
+  maze_status res = MAZE_OK;
+  cudaError_t e = save();
+  for (int k = 0; k < 5 && e == cudaSuccess && res == MAZE_OK; ++k) {
+    if (max_clusters(cand[k]) < 1) continue;
+    res = set_cluster(b, cand[k]);
+    if (res == MAZE_OK) res = step_async(b, 1);   // warm-up (module load, caches)
+    if (res != MAZE_OK) break;
+    e = restore();
+    if (e != cudaSuccess) break;
+    e = cudaEventRecord(b->ev[0], b->stream);
+    if (e == cudaSuccess) res = step_async(b, steps_per_trial);
+    if (res != MAZE_OK) break;
+    e = cudaEventRecord(b->ev[1], b->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b->ev[1]);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]);
+    if (e == cudaSuccess && ms / steps_per_trial < best_ms) {
+      best_ms = ms / steps_per_trial;
+      best = cand[k];
+    }
+    if (e == cudaSuccess) e = restore();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  cudaFree(snap);
+  if (res != MAZE_OK) return res;
+  if (e != cudaSuccess) return fail(MAZE_ERR_CUDA, std::string("tuning: ") + cudaGetErrorString(e));
+  s = set_cluster(b, best);
+  if (s != MAZE_OK) return s;
+  s = build_graph(b);
+  if (s != MAZE_OK) return s;
+  if (chosen_ctas) *chosen_ctas = best;
+  if (ms_per_step) *ms_per_step = best_ms;
+  return MAZE_OK;
+}
+
+}  // extern "C"

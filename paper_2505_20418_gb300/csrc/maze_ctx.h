@@ -1,0 +1,118 @@
+// Host-side state of one MaZe simulation (a context) and the internal host
+// functions that the single-box entry points (maze_api.cu) and the batched
+// engine (maze_batch.cu) share. Not part of the public C ABI.
+#pragma once
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "maze_internal.cuh"
+
+namespace maze {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// First-fit sub-allocator over one device allocation (256-byte aligned
+// blocks, neighbouring free blocks merged on release). A counting arena
+// (base == nullptr) hands out fake addresses and only measures.
+class Arena {
+ public:
+  Arena(char* base, size_t capacity);
+  void* alloc(size_t bytes);          // nullptr when no free block is large enough
+  void release(void* p);
+  size_t used() const { return used_bytes_; }
+  size_t capacity() const { return cap_; }
+  size_t largest_free() const;
+  size_t high_water() const;          // end of the highest block in use
+  bool counting() const { return counting_; }
+  char* base() const { return base_; }
+
+ private:
+  char* base_;
+  size_t cap_;
+  bool counting_;
+  size_t used_bytes_ = 0;
+  std::map<size_t, size_t> free_;     // offset -> size
+  std::map<size_t, size_t> taken_;    // offset -> size
+};
+
+}  // namespace maze
+
+struct maze_ctx {
+  maze_config cfg;
+  int n = 0, N = 0, P = 4;
+  size_t ng = 0;
+  double L = 0, h = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  // ions, SoA [3][n]
+  double *pos = nullptr, *vel = nullptr, *force = nullptr, *force_el = nullptr;
+  int* type = nullptr;
+  float4* pos32 = nullptr;
+  double* wbuf = nullptr;   // [n][3][4] B-spline weights of the current positions
+  float* wbuf32 = nullptr;  // FP32 weights (mixed precision)
+  int4* wbase = nullptr;
+  // grid
+  unsigned long long* qfix = nullptr;
+  double* qd = nullptr;
+  double* phi[3] = {nullptr, nullptr, nullptr};
+  int ik = 0;  // phi^k is phi[ik], phi^{k-1} phi[(ik+1)%3], scratch phi[(ik+2)%3]
+  double *sigma = nullptr, *y = nullptr, *r = nullptr, *p = nullptr, *p1 = nullptr, *Mp = nullptr;
+  maze::LLRec* recs = nullptr;
+  size_t recs_bytes = 0;
+  unsigned* bar = nullptr;
+  // multigrid
+  maze::MgArgs mg = {};
+  double *mg_x = nullptr, *mg_b = nullptr, *mg_r = nullptr, *mg_g = nullptr;
+  // mixed precision: phi, y, sigma hold double-float pairs (float2, 8 B)
+  bool mixed = false;
+  maze::MixedArgs mx = {};
+  int mx_cluster = 0, mx_blocks = 0;
+  float *mx_e0 = nullptr, *mx_r0 = nullptr, *mx_lx = nullptr, *mx_lb = nullptr, *mx_lr = nullptr, *mx_g = nullptr;
+  int sblocks = 0;
+  // cells
+  int nc = 0, ncell = 0, cell_split = 1;
+  int *cell_of = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cursor = nullptr, *cell_ions = nullptr;
+  float4* pos_sorted = nullptr;
+  float4 *rel_hi = nullptr, *rel_lo = nullptr, *rel_hi_s = nullptr, *rel_lo_s = nullptr;
+  // force reductions
+  double* fpart = nullptr;
+  unsigned* ticket = nullptr;
+  int fblocks = 0;
+  int num_sms = 0;
+  maze_stats* rec = nullptr;       // device
+  int* gate = nullptr;             // device: current step skipped
+  maze_stats* rec_host = nullptr;  // pinned
+  cudaGraphExec_t graph[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  bool graphs_tried[2] = {false, false}, graphs_ok[2] = {false, false};
+  int timing = 0;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int max_iter_init = 20000;
+  std::vector<void*> allocs;
+  maze::Arena* arena = nullptr;   // device buffers come from this arena (batched boxes), else cudaMalloc
+  std::vector<double> gk;         // coarsest-level kernel (host copy for the upload)
+};
+
+
+namespace maze {
+
+maze_status fail(maze_status s, const std::string& msg);
+maze_status validate(const maze_config* c);
+IonArgs ion_args(maze_ctx* c, int do_move, int do_spread);
+CellArgs cell_args(maze_ctx* c);
+ForceArgs force_args(maze_ctx* c, const double* phi, int do_kick, int count_step);
+MixedArgs mixed_args(maze_ctx* c, int zero_phi, double* q_out);
+maze_status read_stats(maze_ctx* c);
+maze_status status_message(maze_ctx* c);
+void free_ctx(maze_ctx* c);
+// Validates cfg, allocates every buffer (from ``arena`` when given), uploads
+// the state and runs step 0 on ``stream`` (the config's stream when null).
+maze_status ctx_create(const maze_config* cfg, Arena* arena, maze_ctx** out);
+// Device bytes a context of this configuration takes from an arena.
+maze_status ctx_bytes(const maze_config* cfg, size_t* bytes);
+
+}  // namespace maze

@@ -95,6 +95,7 @@ struct ForceArgs {
   const int4* wbase;     // [n]
   int mixed;             // 1: FP32 gather and pair arithmetic
   int by_cell;           // 1: one block per cell (k_forces_cells), else one warp per ion
+  int cell_split;        // blocks per cell in k_forces_cells (each takes a slice of the cell's ions)
   const float4* rel_hi;  // [n] cell-relative hi/lo positions (mixed precision)
   const float4* rel_lo;
   const float4* rel_hi_sorted;  // [n] the same in cell-slot order

@@ -26,7 +26,12 @@ MAZE_PHI, MAZE_PHI_PREV, MAZE_Y, MAZE_CHARGE, MAZE_SIGMA = 4, 5, 6, 7, 8
 EXPORTS = ("maze_create", "maze_spread", "maze_solve", "maze_gather", "maze_step",
            "maze_step_async", "maze_get", "maze_set", "maze_get_stats", "maze_get_state",
            "maze_set_state", "maze_destroy", "maze_last_error", "maze_version",
-           "maze_set_timing", "maze_get_timing", "maze_solve_shake_noalloc")
+           "maze_set_timing", "maze_get_timing", "maze_solve_shake_noalloc",
+           "maze_batch_create", "maze_batch_box_bytes", "maze_batch_free_bytes", "maze_batch_add",
+           "maze_batch_remove", "maze_batch_info", "maze_batch_step", "maze_batch_step_async",
+           "maze_batch_get", "maze_batch_set", "maze_batch_get_stats", "maze_batch_get_all_stats",
+           "maze_batch_tune",
+           "maze_batch_destroy")
 
 _D = ctypes.c_double
 _I = ctypes.c_int32
@@ -55,6 +60,11 @@ class MazeStats(ctypes.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["momentum"] = list(self.momentum)
         return d
+
+
+class MazeBatchConfig(ctypes.Structure):
+    _fields_ = [("arena_bytes", ctypes.c_size_t), ("max_sims", _I), ("cluster_ctas", _I),
+                ("cuda_stream", ctypes.c_void_p)]
 
 
 class MazeError(RuntimeError):
@@ -91,10 +101,26 @@ def load(path: str = LIB_PATH):
     lib.maze_solve_shake_noalloc.argtypes = [_I, P, P, _D, _I, P, ctypes.POINTER(_I), ctypes.POINTER(_D)]
     lib.maze_destroy.argtypes = [P]
     lib.maze_destroy.restype = None
+    SZ = ctypes.POINTER(ctypes.c_size_t)
+    lib.maze_batch_create.argtypes = [ctypes.POINTER(MazeBatchConfig), ctypes.POINTER(P)]
+    lib.maze_batch_box_bytes.argtypes = [ctypes.POINTER(MazeConfig), SZ]
+    lib.maze_batch_free_bytes.argtypes = [P, SZ, SZ]
+    lib.maze_batch_add.argtypes = [P, ctypes.POINTER(MazeConfig), ctypes.POINTER(_I)]
+    lib.maze_batch_remove.argtypes = [P, _I]
+    lib.maze_batch_info.argtypes = [P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]
+    lib.maze_batch_step.argtypes = [P, _I]
+    lib.maze_batch_step_async.argtypes = [P, _I]
+    lib.maze_batch_get.argtypes = [P, _I, _I, ctypes.POINTER(_D)]
+    lib.maze_batch_set.argtypes = [P, _I, _I, ctypes.POINTER(_D)]
+    lib.maze_batch_get_stats.argtypes = [P, _I, ctypes.POINTER(MazeStats)]
+    lib.maze_batch_get_all_stats.argtypes = [P, ctypes.POINTER(MazeStats), _I]
+    lib.maze_batch_tune.argtypes = [P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]
+    lib.maze_batch_destroy.argtypes = [P]
+    lib.maze_batch_destroy.restype = None
     lib.maze_last_error.restype = ctypes.c_char_p
     lib.maze_version.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("maze_destroy", "maze_last_error", "maze_version"):
+        if name not in ("maze_destroy", "maze_last_error", "maze_version", "maze_batch_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -304,3 +330,120 @@ class MazeSim:
 
     def set_state(self, blob: bytes):
         maze_set_state(self.h, blob)
+
+
+# ---- batched simulations -----------------------------------------------------
+
+def maze_batch_box_bytes(cfg: MazeConfig) -> int:
+    n = ctypes.c_size_t()
+    _check(load().maze_batch_box_bytes(ctypes.byref(cfg), ctypes.byref(n)))
+    return n.value
+
+
+class MazeBatch:
+    """Many independent MaZe simulations advanced together (maze_batch_*).
+
+    Every simulation runs mixed precision with the multigrid solver; ids are
+    slot numbers. ``add`` takes the same arguments as :class:`MazeSim`.
+    """
+
+    def __init__(self, arena_bytes: int, max_sims: int, cluster_ctas: int = 0, stream=None):
+        c = MazeBatchConfig()
+        c.arena_bytes = int(arena_bytes)
+        c.max_sims = int(max_sims)
+        c.cluster_ctas = int(cluster_ctas)
+        c.cuda_stream = stream
+        self.h = ctypes.c_void_p()
+        _check(load().maze_batch_create(ctypes.byref(c), ctypes.byref(self.h)))
+        self.shape = {}
+        self.max_sims = int(max_sims)
+
+    def close(self):
+        if self.h:
+            load().maze_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def config(pos, vel, types, L, N, tf, **kw):
+        kw.setdefault("solver", MAZE_SOLVER_MG)
+        kw.setdefault("precision", MAZE_MIXED)
+        return make_config(pos, vel, types, L, N, tf, **kw)
+
+    @staticmethod
+    def box_bytes(pos, vel, types, L, N, tf, **kw) -> int:
+        """Arena bytes one simulation of this configuration takes."""
+        cfg, keep = MazeBatch.config(pos, vel, types, L, N, tf, **kw)
+        return maze_batch_box_bytes(cfg)
+
+    def add(self, pos, vel, types, L, N, tf, **kw) -> int:
+        """Admit one simulation (runs its step 0); raises MazeError with status
+        MAZE_ERR_OOM when no slot or arena room is free."""
+        cfg, keep = self.config(pos, vel, types, L, N, tf, **kw)
+        i = _I()
+        _check(load().maze_batch_add(self.h, ctypes.byref(cfg), ctypes.byref(i)))
+        self.shape[i.value] = (cfg.n_ions, int(N))
+        return i.value
+
+    def try_add(self, pos, vel, types, L, N, tf, **kw):
+        """As add, but returns None instead of raising when the batch is full."""
+        try:
+            return self.add(pos, vel, types, L, N, tf, **kw)
+        except MazeError as e:
+            if e.status == MAZE_ERR_OOM:
+                return None
+            raise
+
+    def remove(self, i: int):
+        _check(load().maze_batch_remove(self.h, int(i)))
+        self.shape.pop(int(i), None)
+
+    def free_bytes(self):
+        a, b = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(load().maze_batch_free_bytes(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def info(self) -> dict:
+        n, c, k = _I(), _I(), _I()
+        _check(load().maze_batch_info(self.h, ctypes.byref(n), ctypes.byref(c), ctypes.byref(k)))
+        return {"count": n.value, "cluster_ctas": c.value, "clusters": k.value}
+
+    def step(self, nsteps: int = 1):
+        _check(load().maze_batch_step(self.h, int(nsteps)))
+
+    def step_status(self, nsteps: int = 1) -> int:
+        return load().maze_batch_step(self.h, int(nsteps))
+
+    def step_async(self, nsteps: int = 1):
+        _check(load().maze_batch_step_async(self.h, int(nsteps)))
+
+    def get(self, i: int, what: int) -> np.ndarray:
+        n, N = self.shape[int(i)]
+        out = np.empty((n, 3)) if what <= MAZE_FORCE_EL else np.empty((N, N, N))
+        _check(load().maze_batch_get(self.h, int(i), int(what), _dptr(out)))
+        return out
+
+    def set(self, i: int, what: int, arr):
+        arr = np.ascontiguousarray(arr, dtype=np.float64)
+        _check(load().maze_batch_set(self.h, int(i), int(what), _dptr(arr)))
+
+    def stats(self, i: int) -> dict:
+        s = MazeStats()
+        _check(load().maze_batch_get_stats(self.h, int(i), ctypes.byref(s)))
+        return s.as_dict()
+
+    def all_stats(self) -> list:
+        """Statistics of every slot (a free slot has step == -1), one call."""
+        arr = (MazeStats * self.max_sims)()
+        _check(load().maze_batch_get_all_stats(self.h, arr, self.max_sims))
+        return [arr[i].as_dict() for i in range(self.max_sims)]
+
+    def tune(self, steps_per_trial: int = 5):
+        c, ms = _I(), _D()
+        _check(load().maze_batch_tune(self.h, int(steps_per_trial), ctypes.byref(c), ctypes.byref(ms)))
+        return c.value, ms.value

@@ -177,3 +177,20 @@ REPLICA_SIZES = {
     4096: (16, 50.4, 48),
     13824: (24, 75.6, 64),
 }
+
+
+def replica(n_ions: int, seed: int, **kw) -> Workload:
+    """One replica box of a standard size (see REPLICA_SIZES)."""
+    n_side, L, N = REPLICA_SIZES[n_ions]
+    return Workload(f"nacl{n_ions}_L{L}_N{N}", n_side, L, N, seed=seed, **kw)
+
+
+BATCH_SIZES = (216, 512, 1000, 1728, 4096)
+
+
+def batch_workloads(n_boxes: int, seed: int = 3000, sizes=BATCH_SIZES, **kw) -> list:
+    """Replica boxes with ion counts drawn uniformly from ``sizes`` by
+    PCG64(seed); replica r has its own seed, seed + 1 + r."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    counts = rng.choice(np.asarray(sizes), size=n_boxes)
+    return [replica(int(n), seed + 1 + r, **kw) for r, n in enumerate(counts)]

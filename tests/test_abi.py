@@ -47,12 +47,15 @@ def test_struct_layout_matches_c():
     """Compile a probe against the header with gcc and compare sizes/offsets."""
     fields_cfg = [f for f, _ in M.MazeConfig._fields_]
     fields_st = [f for f, _ in M.MazeStats._fields_]
+    fields_b = [f for f, _ in M.MazeBatchConfig._fields_]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "maze.h"', "int main(void){"]
-    lines.append('printf("%zu %zu\\n", sizeof(maze_config), sizeof(maze_stats));')
+    lines.append('printf("%zu %zu %zu\\n", sizeof(maze_config), sizeof(maze_stats), sizeof(maze_batch_config));')
     for f in fields_cfg:
         lines.append(f'printf("%zu\\n", offsetof(maze_config, {f}));')
     for f in fields_st:
         lines.append(f'printf("%zu\\n", offsetof(maze_stats, {f}));')
+    for f in fields_b:
+        lines.append(f'printf("%zu\\n", offsetof(maze_batch_config, {f}));')
     lines.append("return 0;}")
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "probe.c")
@@ -63,8 +66,10 @@ def test_struct_layout_matches_c():
     vals = [int(v) for v in vals]
     assert vals[0] == ctypes.sizeof(M.MazeConfig)
     assert vals[1] == ctypes.sizeof(M.MazeStats)
-    offs = vals[2:]
-    py = [getattr(M.MazeConfig, f).offset for f in fields_cfg] + [getattr(M.MazeStats, f).offset for f in fields_st]
+    assert vals[2] == ctypes.sizeof(M.MazeBatchConfig)
+    offs = vals[3:]
+    py = ([getattr(M.MazeConfig, f).offset for f in fields_cfg] + [getattr(M.MazeStats, f).offset for f in fields_st]
+          + [getattr(M.MazeBatchConfig, f).offset for f in fields_b])
     assert offs == py
 
 
@@ -117,6 +122,9 @@ def test_non_neutral_and_bad_grid_rejected(lib):
 
 
 def test_null_context_calls_are_errors(lib):
+    assert lib.maze_batch_step(None, 1) == M.MAZE_ERR_INVALID
+    assert lib.maze_batch_remove(None, 0) == M.MAZE_ERR_INVALID
+    lib.maze_batch_destroy(None)  # NULL-safe
     assert lib.maze_spread(None) == M.MAZE_ERR_INVALID
     assert lib.maze_step(None, 1) == M.MAZE_ERR_INVALID
     assert lib.maze_gather(None) == M.MAZE_ERR_INVALID
