@@ -3,11 +3,18 @@
 A step is one full MaZe MD step (S1-S9) of one synthetic molten-NaCl box.
 Default workload: 1000 ions (500 Na+, 500 Cl-), L = 31.5 Angstrom, 32^3 grid,
 1200 K, dt = 1 fs, constraint tolerance 1e-10, cubic B-spline assignment,
-warm-started CG constraint solve, FP64. Inputs are resident in HBM when the
-timed region starts; L2 is flushed (256 MiB write) between timed steps,
-outside the per-step CUDA events.
+warm-started multigrid constraint solve in mixed precision (FP32 V-cycle,
+double-float outer iteration, exact integer reductions). Inputs are resident
+in HBM when the timed region starts; L2 is flushed (256 MiB write) between
+timed steps, outside the per-step CUDA events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload nacl64|nacl1000|nacl512000|batch128|serve]
+                  [--solver cg|mg] [--precision fp64|mixed]
+
+--workload batch128 advances 128 replica boxes (216-4096 ions, 16^3-48^3
+grids) together, one persistent kernel launch per step; --workload serve runs
+the continuous-batching serving loop on a Poisson request stream.
 
 Under torchrun every rank runs an independent replica box (weak scaling, no
 collective on the data path); value = steps of all ranks / max rank time.
@@ -24,7 +31,11 @@ import sys
 import threading
 import time
 
-import numpy as np
+if "reference" in sys.argv:
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -225,13 +236,23 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="nacl1000", choices=["nacl64", "nacl1000", "nacl512000"])
+    ap.add_argument("--workload", default="nacl1000",
+                    choices=["nacl64", "nacl1000", "nacl512000", "batch128", "serve"])
+    ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--solver", default="mg", choices=["cg", "mg"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.workload == "batch128":
+        if args.impl == "reference":
+            return bench_batch_reference(args)
+        return bench_batch(args)
+    if args.workload == "serve":
+        if args.impl == "reference":
+            return bench_serve_reference(args)
+        return bench_serve(args)
     w = synth.workload(args.workload)
     if args.impl == "reference":
         return bench_reference(args, w)
@@ -375,6 +396,243 @@ def main():
     sim.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# Batched replicas and serving
+
+BATCH_BOXES = 128
+
+
+def oracle_box_step_seconds(w, steps=2):
+    """Seconds per MD step of the FP64 oracle on one box (after step 0)."""
+    import oracle as O
+    pos, vel, types = synth.make_state(w)
+    tf = synth.tosi_fumi_nacl()
+    p = O.Params(L=w.L, N=w.N, dt=w.dt, tol=w.tol, rc=w.rc, P=w.order, solver="mg")
+    st = O.init(pos, vel, types, p, tf)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st = O.step(st, p, tf)
+    return (time.perf_counter() - t0) / steps
+
+
+def mix_rate(ws, per_size_seconds):
+    """Box-steps/s of advancing the boxes ``ws`` one after another, given the
+    seconds per step of one box of each size."""
+    t = sum(per_size_seconds[w.n_ions] for w in ws) / len(ws)
+    return 1.0 / t
+
+
+def batch_cpu_baseline(ws, steps=2):
+    sizes = sorted({w.n_ions for w in ws})
+    t0 = time.perf_counter()
+    per = {n: oracle_box_step_seconds(next(w for w in ws if w.n_ions == n), steps) for n in sizes}
+    dt = time.perf_counter() - t0
+    return {"value": mix_rate(ws, per), "unit": "box-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} MD steps of one box of each size {sizes} (after its step 0), numpy FP64, one "
+                      f"thread ({dt:.1f} s), weighted by the size mix of the {len(ws)} boxes"}
+
+
+def batch_config(ws, extra=None):
+    from collections import Counter
+    c = Counter(w.n_ions for w in ws)
+    d = {"workload": f"{len(ws)} molten-NaCl replica boxes, ion counts drawn uniformly from "
+                     f"{sorted(c)} (grids 16^3-48^3, ~1 A spacing), 1200 K, dt=1 fs, tol=1e-10, P=4, "
+                     f"r_cut=min(L/2, 9 A), seeds 3001-{3000 + len(ws)}",
+         "boxes": len(ws), "mix": {str(k): v for k, v in sorted(c.items())},
+         "ions_total": sum(w.n_ions for w in ws), "grid_points_total": sum(w.N ** 3 for w in ws),
+         "solver": "mg", "precision": "mixed"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def bench_batch(args):
+    import torch
+    from paper_2505_20418_gb300 import maze as M
+    torch.cuda.set_device(0)
+    M.load()
+    ws = synth.batch_workloads(BATCH_BOXES)
+    tf = synth.tosi_fumi_nacl()
+    stream = torch.cuda.Stream()
+    states = [synth.make_state(w) for w in ws]
+    need = sum(M.MazeBatch.box_bytes(*st, w.L, w.N, tf, r_cut=w.rc, dt=w.dt, tol=w.tol, order=w.order)
+               for w, st in zip(ws, states))
+    b = M.MazeBatch(need + (64 << 20), len(ws), stream=stream.cuda_stream)
+    ids = [b.add(*st, w.L, w.N, tf, r_cut=w.rc, dt=w.dt, tol=w.tol, order=w.order) for w, st in zip(ws, states)]
+    cta, tune_ms = b.tune(3)
+    b.step(args.warmup)
+    it0 = sum(b.stats(i)["total_iters"] for i in ids)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    big = need > (160 << 20)
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            if not big:
+                flush.zero_()
+            ev[k][0].record(stream)
+            b.step_async(1)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(c) for a, c in ev]
+    total_s = sum(step_ms) / 1e3
+    st = b.step_status(0)
+    stats = [b.stats(i) for i in ids]
+    if any(s["status"] != 0 for s in stats) or st != 0:
+        raise RuntimeError("a box failed during the timed steps")
+    iters = (sum(s["total_iters"] for s in stats) - it0) / (args.steps * len(ids))
+    # force error of one box of each size against the oracle's exact
+    # discrete solution on the GPU's current positions (not timed)
+    import oracle as O
+    ferr = 0.0
+    for n in sorted({w.n_ions for w in ws}):
+        j = next(k for k, w in enumerate(ws) if w.n_ions == n)
+        w = ws[j]
+        x = b.get(ids[j], M.MAZE_POS)
+        F = b.get(ids[j], M.MAZE_FORCE)
+        types = states[j][2]
+        p = O.Params(L=w.L, N=w.N, dt=w.dt, tol=w.tol, rc=w.rc, P=w.order)
+        phi_ex, _ = O.exact_potential(x, types, p)
+        Q = np.where(types == 0, 1.0, -1.0)
+        Fo = O.gather_forces(x, Q, phi_ex, w.L, w.N, w.order) + O.tf_forces(x, types, w.L, tf, w.rc)[0]
+        scale = np.sqrt((np.linalg.norm(F, axis=1) ** 2).mean())
+        ferr = max(ferr, float((np.linalg.norm(F - Fo, axis=1) / np.maximum(np.linalg.norm(Fo, axis=1), scale)).max()))
+    # the same boxes advanced one after another by single-box contexts:
+    # the plain FP64 path and the single-box mixed path (per size class)
+    single = {}
+    for prec in ("fp64", "mixed"):
+        per = {}
+        for n in sorted({w.n_ions for w in ws}):
+            j = next(k for k, w in enumerate(ws) if w.n_ions == n)
+            w = ws[j]
+            sim = M.MazeSim(*states[j], w.L, w.N, tf, r_cut=w.rc, dt=w.dt, tol=w.tol, order=w.order,
+                            solver=M.MAZE_SOLVER_MG, precision=M.MAZE_MIXED if prec == "mixed" else M.MAZE_FP64,
+                            stream=stream.cuda_stream)
+            sim.step(3)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                sim.step_async(20)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            per[n] = e0.elapsed_time(e1) / 1e3 / 20
+            sim.close()
+        single[prec] = mix_rate(ws, per)
+    # end to end through the C ABI with host buffers: per step every box's
+    # positions and velocities go up from pinned host memory, the step runs,
+    # positions, velocities and statistics come back
+    e2e = None
+    if not args.no_e2e:
+        host = [(torch.from_numpy(b.get(i, M.MAZE_POS)).pin_memory(), torch.from_numpy(b.get(i, M.MAZE_VEL)).pin_memory())
+                for i in ids]
+        n_e2e = 5
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            for i, (hp, hv) in zip(ids, host):
+                b.set(i, M.MAZE_POS, hp.numpy())
+                b.set(i, M.MAZE_VEL, hv.numpy())
+            b.step(1)
+            for i, (hp, hv) in zip(ids, host):
+                hp.numpy()[:] = b.get(i, M.MAZE_POS)
+                hv.numpy()[:] = b.get(i, M.MAZE_VEL)
+            b.all_stats()
+        e2e_s = time.perf_counter() - t0
+        nion = sum(w.n_ions for w in ws)
+        e2e = {"value": len(ids) * n_e2e / e2e_s, "unit": "box-steps/s", "h2d_bytes_per_step": 2 * 24 * nion,
+               "d2h_bytes_per_step": 2 * 24 * nion + 104 * len(ids)}
+    bytes_launch = sum(solve_bytes_per_launch(w.N, iters, "mg", precision="mixed") + 200 * w.n_ions for w in ws)
+    mean_s = total_s / args.steps
+    achieved = bytes_launch / mean_s / 1e9
+    peak, peak_kind = peaks()
+    cpu = None if args.no_cpu else batch_cpu_baseline(ws)
+    b.close()
+    line = {
+        "metric": METRIC, "value": len(ids) * args.steps / total_s, "unit": "box-steps/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * mean_s, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f32x2", "data": "synthetic",
+        "config": batch_config(ws, {"cluster_ctas": cta, "tune_ms_per_step": tune_ms,
+                                    "l2": "working set larger than L2, not flushed" if big else
+                                    "flushed between timed steps (256 MiB write outside the step events)"}),
+        "batch_steps_per_s": args.steps / total_s,
+        "ion_steps_per_s": sum(w.n_ions for w in ws) * args.steps / total_s,
+        "p50_us": 1e3 * float(np.percentile(step_ms, 50)), "p99_us": 1e3 * float(np.percentile(step_ms, 99)),
+        "iters_per_step": iters, "force_error": ferr,
+        "single_box_paths": {"fp64_box_steps_per_s": single["fp64"], "mixed_box_steps_per_s": single["mixed"],
+                             "how": "one box of each size timed alone (20 steps, CUDA events), weighted by the mix"},
+        "roofline": {"kernel": "k_batch_step", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "algorithmic_bytes_per_launch": bytes_launch},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def bench_batch_reference(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    ws = synth.batch_workloads(BATCH_BOXES)
+    cpu = batch_cpu_baseline(ws, steps=max(1, min(args.steps, 2)))
+    v = cpu["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "box-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * BATCH_BOXES / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": batch_config(ws), "cpu_baseline": cpu,
+            "e2e": {"value": v, "unit": "box-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+SERVE_RATE = 200.0
+
+
+def bench_serve(args):
+    import torch
+    from paper_2505_20418_gb300 import maze as M
+    from paper_2505_20418_gb300 import serve
+    torch.cuda.set_device(0)
+    M.load()
+    reqs = serve.poisson_requests(args.requests, SERVE_RATE)
+    stream = torch.cuda.Stream()
+    srv = serve.Server(16 << 30, 512, stream=stream.cuda_stream, chunk=4)
+    # warm-up: a few short requests through the same server (module load, graph)
+    srv.run(serve.poisson_requests(4, 1000.0, seed=4999, sizes=(216, 1000), steps=(args.warmup, args.warmup)),
+            realtime=False)
+    clocks = ClockSampler(0)
+    clocks.start()
+    out = srv.run(reqs, realtime=True, max_wall=300.0)
+    clk = clocks.stop()
+    info = srv.batch.info()
+    srv.close()
+    line = {
+        "metric": METRIC, "value": out["steps_per_s"], "unit": "box-steps/s", "n_gpus": 1,
+        "steps": out["box_steps"], "warmup": args.warmup, "ms_per_step": out["p50_step_ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f32x2",
+        "data": "synthetic",
+        "config": {"workload": f"serving loop: {args.requests} requests, Poisson arrivals at {SERVE_RATE:g}/s, "
+                               "boxes of 64-13824 ions (grids 16^3-64^3), 50-2000 steps each, mixed precision, "
+                               "admission by device memory (16 GiB arena, 512 slots), continuous batching",
+                   "requests": args.requests, "rate_per_s": SERVE_RATE, "cluster_ctas": info["cluster_ctas"]},
+        "p50_step_ms": out["p50_step_ms"], "p99_step_ms": out["p99_step_ms"], "served": out["served"],
+        "wall_s": out["wall_s"], "ion_steps_per_s": out["ion_steps"] / out["wall_s"],
+        "roofline": None, "cpu_baseline": None,
+        "e2e": {"value": out["steps_per_s"], "unit": "box-steps/s",
+                "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                "note": "the serving loop itself is end to end: host state in, final state out per request"},
+        "gpu_launches": out["launches"], "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def bench_serve_reference(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    print(json.dumps({"impl": "reference", "unavailable": "the oracle has no serving loop; see --workload batch128 "
+                      "--impl reference for the oracle's per-box rate"}), flush=True)
 
 
 if __name__ == "__main__":
