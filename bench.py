@@ -237,8 +237,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="nacl1000",
-                    choices=["nacl64", "nacl1000", "nacl512000", "batch128", "serve"])
+                    choices=["nacl64", "nacl1000", "nacl512000", "batch128", "serve", "study"])
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
+    ap.add_argument("--boxes", type=int, default=128, help="batch128: number of replica boxes")
+    ap.add_argument("--cluster-ctas", type=int, default=0, help="batch128: CTAs per box (0: autotune)")
     ap.add_argument("--solver", default="mg", choices=["cg", "mg"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu", action="store_true")
@@ -249,6 +251,12 @@ def main():
         if args.impl == "reference":
             return bench_batch_reference(args)
         return bench_batch(args)
+    if args.workload == "study":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the iteration study is a GPU measurement; the "
+                              "oracle's iteration counts are pinned in tests/test_oracle_pins.py"}), flush=True)
+            return None
+        return bench_study(args)
     if args.workload == "serve":
         if args.impl == "reference":
             return bench_serve_reference(args)
@@ -453,15 +461,18 @@ def bench_batch(args):
     from paper_2505_20418_gb300 import maze as M
     torch.cuda.set_device(0)
     M.load()
-    ws = synth.batch_workloads(BATCH_BOXES)
+    ws = synth.batch_workloads(args.boxes)
     tf = synth.tosi_fumi_nacl()
     stream = torch.cuda.Stream()
     states = [synth.make_state(w) for w in ws]
     need = sum(M.MazeBatch.box_bytes(*st, w.L, w.N, tf, r_cut=w.rc, dt=w.dt, tol=w.tol, order=w.order)
                for w, st in zip(ws, states))
-    b = M.MazeBatch(need + (64 << 20), len(ws), stream=stream.cuda_stream)
+    b = M.MazeBatch(need + (64 << 20), len(ws), cluster_ctas=args.cluster_ctas, stream=stream.cuda_stream)
     ids = [b.add(*st, w.L, w.N, tf, r_cut=w.rc, dt=w.dt, tol=w.tol, order=w.order) for w, st in zip(ws, states)]
-    cta, tune_ms = b.tune(3)
+    if args.cluster_ctas == 0:
+        cta, tune_ms = b.tune(3)
+    else:
+        cta, tune_ms = args.cluster_ctas, None
     b.step(args.warmup)
     it0 = sum(b.stats(i)["total_iters"] for i in ids)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -576,11 +587,11 @@ def bench_batch(args):
 def bench_batch_reference(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return
-    ws = synth.batch_workloads(BATCH_BOXES)
+    ws = synth.batch_workloads(args.boxes)
     cpu = batch_cpu_baseline(ws, steps=max(1, min(args.steps, 2)))
     v = cpu["value"]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "box-steps/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * BATCH_BOXES / v,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * len(ws) / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": batch_config(ws), "cpu_baseline": cpu,
             "e2e": {"value": v, "unit": "box-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -633,6 +644,52 @@ def bench_serve_reference(args):
         return
     print(json.dumps({"impl": "reference", "unavailable": "the oracle has no serving loop; see --workload batch128 "
                       "--impl reference for the oracle's per-box rate"}), flush=True)
+
+
+def bench_study(args):
+    """Iteration counts of Sec. III.A on synthetic molten NaCl: V-cycles per
+    step to tol = 1e-7 for the MaZe solve and the direct multigrid solves
+    with static and time-propagated starts (Fig. tol_vs_v_cycles), on the
+    1000-ion box, and the solid-vs-molten comparison of Table
+    convergence_solid_molten on a 512-ion box (300 K with 0.05 A lattice
+    noise vs 2800 K), mixed precision, averaged over steps 50-150."""
+    import torch
+    from paper_2505_20418_gb300 import maze as M
+    torch.cuda.set_device(0)
+    M.load()
+    tf = synth.tosi_fumi_nacl()
+    schemes = {"maze": M.MAZE_SCHEME_MAZE, "mg-timeprop": M.MAZE_SCHEME_MG_TIMEPROP,
+               "mg-static": M.MAZE_SCHEME_MG_STATIC}
+
+    def vcycles(w, scheme, skip=50, count=100):
+        pos, vel, types = synth.make_state(w)
+        sim = M.MazeSim(pos, vel, types, w.L, w.N, tf, r_cut=w.rc, dt=w.dt, tol=1e-7, order=w.order,
+                        solver=M.MAZE_SOLVER_MG, precision=M.MAZE_MIXED, scheme=schemes[scheme])
+        sim.step(skip)
+        a = sim.stats()["total_iters"]
+        sim.step(count)
+        v = (sim.stats()["total_iters"] - a) / count
+        sim.close()
+        return v
+
+    molten = synth.workload("nacl1000")
+    e3 = {k: vcycles(molten, k) for k in schemes}
+    solid = synth.replica(512, 6001, T=300.0, sigma=0.05)
+    hot = synth.replica(512, 6001, T=2800.0)
+    e5 = {}
+    for k in schemes:
+        s_, m_ = vcycles(solid, k), vcycles(hot, k)
+        e5[k] = {"solid_300K": s_, "molten_2800K": m_, "slowdown": m_ / s_ if s_ > 0 else None}
+    line = {"metric": "V-cycles per MD step to tol 1e-7 (Sec. III.A)", "value": e3["maze"], "unit": "V-cycles/step",
+            "n_gpus": 1, "higher_is_better": False, "data": "synthetic", "dtype": "f32+f32x2",
+            "config": {"workload": "iteration study: molten NaCl 1000 ions / 32^3 (1200 K start), and 512 ions / "
+                                   "24^3 solid (300 K, 0.05 A noise) vs hot (2800 K); steps 50-150, mixed precision"},
+            "convergence_by_scheme_1000_ions": e3,
+            "ratio_vs_maze": {k: e3[k] / e3["maze"] for k in e3},
+            "solid_vs_molten_512_ions": e5,
+            "paper_for_context": {"h_A": 0.172, "maze": 4, "mg-timeprop": "about 8", "mg-static": "about 28",
+                                  "solid_vs_molten": {"maze": "2 -> 5", "mg-timeprop": "3 -> 11", "mg-static": "7 -> 22"}}}
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

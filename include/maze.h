@@ -57,10 +57,25 @@ typedef enum {
 
 enum { MAZE_SOLVER_CG = 0, MAZE_SOLVER_MG = 1 };
 enum { MAZE_FP64 = 0, MAZE_MIXED = 1 };
+/* How a step obtains phi^{k+1} (Sec. III.A compares the three):
+ *  MAZE_SCHEME_MAZE          SHAKE: phi_p = 2 phi^k - phi^{k-1}, solve M y = sigma_p
+ *                            from the previous step's y (Eqs. SHAKE-SHAKEPhiFinal)
+ *  MAZE_SCHEME_MG_STATIC     direct solve of M phi = -4 pi q / h (Eq. linearproblem)
+ *                            starting from phi^k
+ *  MAZE_SCHEME_MG_TIMEPROP   direct solve starting from 2 phi^k - phi^{k-1}
+ * The direct schemes stop on max_n |(M phi + (4 pi/h) q)_n| < tol (Eq. res_poisson). */
+enum { MAZE_SCHEME_MAZE = 0, MAZE_SCHEME_MG_STATIC = 1, MAZE_SCHEME_MG_TIMEPROP = 2 };
+/* Electrostatic force estimator:
+ *  MAZE_FORCE_CD      Eq. F_nostra: the assignment weights times the central-
+ *                     difference field on the grid (conserves momentum)
+ *  MAZE_FORCE_GRADW   Eq. F_Benoit: minus the gradient of the assignment weights
+ *                     times phi (the exact gradient of 1/2 phi.q at fixed phi) */
+enum { MAZE_FORCE_CD = 0, MAZE_FORCE_GRADW = 1 };
 
 /* Physical constants used by the library (CODATA 2018). */
 #define MAZE_KE_EV_ANGSTROM 14.399645478425668  /* e^2/(4 pi eps0) in eV*Angstrom */
 #define MAZE_ACC_UNIT 9.648533215665327e-3      /* e/u * 1e-20: 1 eV/(amu*Angstrom) in Angstrom/fs^2 */
+#define MAZE_KB_EV_PER_K 8.617333262145179e-5   /* Boltzmann constant k_B / e, eV/K */
 
 /*
  * Run configuration; everything is host memory and is copied by maze_create.
@@ -87,6 +102,13 @@ enum { MAZE_FP64 = 0, MAZE_MIXED = 1 };
  * order_P     assignment order: 2 (linear B-spline over the 8 nearest points)
  *             or 4 (cubic B-spline over 4^3 points), Sec. II.A
  * precision   MAZE_FP64, or MAZE_MIXED (FP32 grid arithmetic, FP64 reductions)
+ * scheme      MAZE_SCHEME_* above (0 = MaZe)
+ * force_estimator  MAZE_FORCE_* above (0 = Eq. F_nostra)
+ * langevin_gamma   friction gamma (1/fs) of the OVRVO Langevin integrator
+ *             (Sec. III); 0 gives velocity Verlet (NVE)
+ * langevin_T  bath temperature (K) of the O steps
+ * seed        key of the counter-based generator (Philox-4x32-10) that draws
+ *             the O steps' Gaussian numbers; the counter is (ion, step, stage)
  * cuda_stream cudaStream_t to issue work on; NULL makes the context create
  *             and own a non-blocking stream
  */
@@ -113,6 +135,11 @@ typedef struct {
   int32_t mg_post;
   int32_t order_P;
   int32_t precision;
+  int32_t scheme;
+  int32_t force_estimator;
+  double langevin_gamma;
+  double langevin_T;
+  uint64_t seed;
   void* cuda_stream;
 } maze_config;
 

@@ -23,7 +23,10 @@ Everything here is a direct restatement of the paper, in its notation:
   * V_work = -sum_alpha int F . dr (Eq. E_nostra), discrete energy
     1/2 phi^T q (Eq. energy_discr);
   * Tosi-Fumi pair energy A exp(B(s - r)) - C/r^6 - D/r^8 (Sec. III);
-  * velocity Verlet for the ions (Sec. II, Sec. III).
+  * velocity Verlet for the ions (Sec. II, Sec. III), or its Langevin
+    extension OVRVO (Sec. III) with Philox-4x32-10 Gaussian numbers;
+  * the direct Poisson baselines of Sec. III.A (static and time-propagated
+    starts) and the force estimator of Eq. F_Benoit.
 
 Readings where the paper is silent (each listed in the design notes):
   * assignment order P in {2, 4}: P=2 is the linear B-spline over the 8
@@ -183,7 +186,7 @@ def gather_forces(pos, Q, phi, L, N, P):
 
 def gather_forces_tilde(pos, Q, phi, L, N, P):
     """The alternative estimator F~ = -sum_n Q grad_r W(r - r_n) phi_n
-    (Eq. F_Benoit), eV/Angstrom. Not momentum-conserving; diagnostic only."""
+    (Eq. F_Benoit), eV/Angstrom. Not momentum-conserving."""
     h = L / N
     nodes, dist = support(pos, L, N, P)
     w = bspline(dist, P)
@@ -426,6 +429,17 @@ class Params:
     rc: float = 9.0
     solver: str = "cg"
     max_iter: int = 10000
+    # "maze" (SHAKE, Eqs. SHAKE-SHAKEPhiFinal), or a direct solve of
+    # Eq. linearproblem from the previous potential ("mg-static") or from
+    # 2 phi^k - phi^{k-1} ("mg-timeprop"), Sec. III.A
+    scheme: str = "maze"
+    # electrostatic force: "cd" (Eq. F_nostra) or "gradw" (Eq. F_Benoit)
+    force: str = "cd"
+    # OVRVO Langevin integrator (Sec. III): friction (1/fs), bath temperature
+    # (K), generator key; gamma = 0 is velocity Verlet
+    gamma: float = 0.0
+    T_bath: float = 0.0
+    seed: int = 0
 
     @property
     def h(self):
@@ -477,7 +491,7 @@ def init(pos, vel, types, p: Params, tf) -> State:
     q = spread(pos, Q, p.L, N, p.P)
     y0, info = solve(q, np.zeros_like(q), p.tol, p.solver, p.max_iter)   # sigma_p = q at phi_p = 0
     phi = -(4.0 * np.pi / p.h) * (y0 - y0.mean())
-    F_el = gather_forces(pos, Q, phi, p.L, N, p.P)
+    F_el = electrostatic_forces(pos, Q, phi, p)
     F_tf, V_tf = tf_forces(pos, types, p.L, tf, p.rc)
     st = State(pos=pos, vel=np.array(vel, dtype=np.float64), types=np.asarray(types),
                phi=phi, phi_prev=phi.copy(), y=np.zeros_like(phi),
@@ -497,22 +511,107 @@ def step(st: State, p: Params, tf) -> State:
     Q = _charges(st.types, p)
     m = _masses(st.types, p)[:, None]
     F_el_old = st.F_el
-    v_half = st.vel + (0.5 * p.dt * ACC) * st.F / m
+    vel0 = o_step(st.vel, st.types, p, st.step, 0) if p.gamma > 0 else st.vel
+    v_half = vel0 + (0.5 * p.dt * ACC) * st.F / m
     dr = p.dt * v_half
     pos = wrap(st.pos + dr, p.L)
     q = spread(pos, Q, p.L, p.N, p.P)
-    phi_p, sp = sigma_p(st.phi, st.phi_prev, q, p.h)
-    y, info = solve(sp, st.y, p.tol, p.solver, p.max_iter)
-    y = y - y.mean()
-    phi_new = phi_p - (4.0 * np.pi / p.h) * y
-    F_el = gather_forces(pos, Q, phi_new, p.L, p.N, p.P)
+    if p.scheme == "maze":
+        phi_p, sp = sigma_p(st.phi, st.phi_prev, q, p.h)
+        y, info = solve(sp, st.y, p.tol, p.solver, p.max_iter)
+        y = y - y.mean()
+        phi_new = phi_p - (4.0 * np.pi / p.h) * y
+    else:
+        phi_new, y, info = direct_solve(st, q, p)
+    F_el = electrostatic_forces(pos, Q, phi_new, p)
     F_tf, V_tf = tf_forces(pos, st.types, p.L, tf, p.rc)
     vel = v_half + (0.5 * p.dt * ACC) * (F_el + F_tf) / m
+    if p.gamma > 0:
+        vel = o_step(vel, st.types, p, st.step, 1)
     V_work = st.V_work - 0.5 * float(np.sum((F_el_old + F_el) * dr))
     return State(pos=pos, vel=vel, types=st.types, phi=phi_new, phi_prev=st.phi, y=y,
                  F_el=F_el, F_tf=F_tf, V_tf=V_tf, V_work=V_work,
                  V_disc=discrete_energy(q, phi_new), step=st.step + 1,
                  iters=info.iters, resid=info.resid)
+
+
+# ---------------------------------------------------------------------------
+# Counter-based random numbers for the O steps: Philox-4x32-10 (Salmon,
+# Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC 2011),
+# written from its published definition, and the Box-Muller transform.
+
+_PHILOX_M0, _PHILOX_M1 = 0xD2511F53, 0xCD9E8D57
+_PHILOX_W0, _PHILOX_W1 = 0x9E3779B9, 0xBB67AE85
+_U32 = 0xFFFFFFFF
+
+
+def philox4x32(ctr, key, rounds=10):
+    """Philox-4x32 on arrays of counters: ``ctr`` is a tuple of four uint64
+    arrays (values < 2^32), ``key`` a pair of ints. Each round multiplies
+    words 0 and 2 by the Philox constants, splits the 64-bit products into
+    high and low halves and mixes them with words 1 and 3 and the round key;
+    the key advances by the Weyl constants between rounds."""
+    c0, c1, c2, c3 = (np.asarray(c, dtype=np.uint64) & _U32 for c in ctr)
+    k0, k1 = np.uint64(key[0] & _U32), np.uint64(key[1] & _U32)
+    for r in range(rounds):
+        if r:
+            k0 = np.uint64((int(k0) + _PHILOX_W0) & _U32)
+            k1 = np.uint64((int(k1) + _PHILOX_W1) & _U32)
+        p0 = np.uint64(_PHILOX_M0) * c0
+        p1 = np.uint64(_PHILOX_M1) * c2
+        hi0, lo0 = p0 >> np.uint64(32), p0 & np.uint64(_U32)
+        hi1, lo1 = p1 >> np.uint64(32), p1 & np.uint64(_U32)
+        c0, c1, c2, c3 = hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0
+    return c0, c1, c2, c3
+
+
+def gaussians(n_ions: int, step: int, stage: int, seed: int):
+    """Three standard normals per ion for one O step: Philox-4x32-10 with
+    counter (ion, step, stage, 0) and key (seed low, seed high); uniforms
+    u = (x + 1/2) 2^-32 and the Box-Muller transform
+    (sqrt(-2 ln u0) cos 2 pi u1, sqrt(-2 ln u0) sin 2 pi u1, sqrt(-2 ln u2) cos 2 pi u3)."""
+    i = np.arange(n_ions, dtype=np.uint64)
+    z = np.zeros(n_ions, dtype=np.uint64)
+    x = philox4x32((i, z + np.uint64(step & _U32), z + np.uint64(stage), z), (seed & _U32, (seed >> 32) & _U32))
+    u = [(xk.astype(np.float64) + 0.5) * 2.0 ** -32 for xk in x]
+    r01 = np.sqrt(-2.0 * np.log(u[0]))
+    r23 = np.sqrt(-2.0 * np.log(u[2]))
+    return np.stack([r01 * np.cos(2 * np.pi * u[1]), r01 * np.sin(2 * np.pi * u[1]),
+                     r23 * np.cos(2 * np.pi * u[3])], axis=1)
+
+
+def o_step(vel, types, p: Params, step: int, stage: int):
+    """O part of OVRVO (Sivak, Chodera, Crooks 2013) over a half step:
+    v <- a v + sqrt((1 - a^2) k_B T / m) xi, a = exp(-gamma dt / 2)."""
+    a = math.exp(-p.gamma * p.dt / 2.0)
+    m = _masses(types, p)[:, None]
+    sd = np.sqrt((1.0 - a * a) * K_B * p.T_bath * ACC / m)
+    return a * vel + sd * gaussians(vel.shape[0], step, stage, p.seed)
+
+
+def direct_solve(st: State, q, p: Params):
+    """The direct Poisson baselines of Sec. III.A: solve M phi = -(4 pi/h) q
+    (Eq. linearproblem) with the same solver, stopping on
+    max_n |(M phi + (4 pi/h) q)_n| < tol (Eq. res_poisson), from the converged
+    potential of the previous step ("mg-static") or from the putative
+    2 phi^k - phi^{k-1} ("mg-timeprop"). The zero-mean solution is kept; y is
+    not used by these schemes (returned as zeros)."""
+    if p.scheme == "mg-static":
+        phi0 = st.phi
+    elif p.scheme == "mg-timeprop":
+        phi0 = 2.0 * st.phi - st.phi_prev
+    else:
+        raise ValueError(p.scheme)
+    phi, info = solve(-(4.0 * np.pi / p.h) * q, phi0, p.tol, p.solver, p.max_iter)
+    return phi - phi.mean(), np.zeros_like(phi), info
+
+
+def electrostatic_forces(pos, Q, phi, p: Params):
+    if p.force == "cd":
+        return gather_forces(pos, Q, phi, p.L, p.N, p.P)
+    if p.force == "gradw":
+        return gather_forces_tilde(pos, Q, phi, p.L, p.N, p.P)
+    raise ValueError(p.force)
 
 
 def kinetic(st: State, p: Params) -> float:

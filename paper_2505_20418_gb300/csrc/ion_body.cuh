@@ -43,7 +43,63 @@ __device__ __forceinline__ void bspline_weights(R t, int P, R* w) {
   }
 }
 
+// d w_a / dt of the weights above (the estimator of Eq. F_Benoit); for
+// P = 4: (-(1-t)^2, 3t^2 - 4t, -3t^2 + 2t + 1, t^2) / 2, for P = 2: (-1, 1).
+template <typename R>
+__device__ __forceinline__ void bspline_dweights(R t, int P, R* d) {
+  if (P == 2) {
+    d[0] = R(-1);
+    d[1] = R(1);
+    d[2] = R(0);
+    d[3] = R(0);
+  } else {
+    const R s = R(1) - t;
+    const R half = R(1) / R(2);
+    d[0] = -s * s * half;
+    d[1] = (R(3) * t * t - R(4) * t) * half;
+    d[2] = (R(-3) * t * t + R(2) * t + R(1)) * half;
+    d[3] = t * t * half;
+  }
+}
+
 __device__ __forceinline__ int wrap_idx(int a, int N) { return a >= N ? a - N : a; }
+
+// Philox-4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC 2011): each
+// round multiplies words 0 and 2 by the Philox constants, mixes the high and
+// low halves of the products with words 1 and 3 and the round key; the key
+// advances by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// OVRVO's O step for ion i (Sivak, Chodera, Crooks 2013): v <- a v + sd xi,
+// three standard normals by the Box-Muller transform of the four uniforms
+// u = (x + 1/2) 2^-32 of one Philox block with counter (i, step, stage, 0).
+__device__ __forceinline__ void o_step(const LangevinArgs& o, int i, int t, unsigned step, unsigned stage,
+                                       double& vx, double& vy, double& vz) {
+  const uint4 x = philox4x32_10(make_uint4((unsigned)i, step, stage, 0u), o.key0, o.key1);
+  const double s32 = 2.3283064365386963e-10;   // 2^-32
+  const double u0 = ((double)x.x + 0.5) * s32, u1 = ((double)x.y + 0.5) * s32;
+  const double u2 = ((double)x.z + 0.5) * s32, u3 = ((double)x.w + 0.5) * s32;
+  const double r01 = sqrt(-2.0 * log(u0)), r23 = sqrt(-2.0 * log(u2));
+  double s1, c1, s3, c3;
+  sincospi(2.0 * u1, &s1, &c1);
+  sincospi(2.0 * u3, &s3, &c3);
+  const double sd = t ? o.sd1 : o.sd0;
+  vx = o.a * vx + sd * (r01 * c1);
+  vy = o.a * vy + sd * (r01 * s1);
+  vz = o.a * vz + sd * (r23 * c3);
+}
 
 __device__ __forceinline__ double wrap_pos(double x, double L, double inv_L) {
   x -= L * floor(x * inv_L);
@@ -62,9 +118,11 @@ __device__ __forceinline__ void move_ion(const IonArgs& a, int i) {
     const int t = a.type[i];
     if (a.do_move) {
       const double kick = t ? a.kick1 : a.kick0;
-      double vx = a.vel[i] + kick * a.force[i];
-      double vy = a.vel[a.n + i] + kick * a.force[a.n + i];
-      double vz = a.vel[2 * a.n + i] + kick * a.force[2 * a.n + i];
+      double vx = a.vel[i], vy = a.vel[a.n + i], vz = a.vel[2 * a.n + i];
+      if (a.ou.on) o_step(a.ou, i, t, (unsigned)a.rec->step, 0u, vx, vy, vz);
+      vx += kick * a.force[i];
+      vy += kick * a.force[a.n + i];
+      vz += kick * a.force[2 * a.n + i];
       a.vel[i] = vx;
       a.vel[a.n + i] = vy;
       a.vel[2 * a.n + i] = vz;
@@ -109,6 +167,15 @@ __device__ __forceinline__ void move_ion(const IonArgs& a, int i) {
       gw[0] = make_float4(w[0], w[1], w[2], w[3]);
       gw[1] = make_float4(w[4], w[5], w[6], w[7]);
       gw[2] = make_float4(w[8], w[9], w[10], w[11]);
+      if (a.wdbuf32) {
+        bspline_dweights<float>((float)tx, P, w);
+        bspline_dweights<float>((float)ty, P, w + 4);
+        bspline_dweights<float>((float)tz, P, w + 8);
+        float4* gd = reinterpret_cast<float4*>(a.wdbuf32 + (size_t)i * 12);
+        gd[0] = make_float4(w[0], w[1], w[2], w[3]);
+        gd[1] = make_float4(w[4], w[5], w[6], w[7]);
+        gd[2] = make_float4(w[8], w[9], w[10], w[11]);
+      }
     } else {
       double w[12];
       bspline_weights<double>(tx, P, w);
@@ -117,6 +184,14 @@ __device__ __forceinline__ void move_ion(const IonArgs& a, int i) {
       double* gw = a.wbuf + (size_t)i * 12;
 #pragma unroll
       for (int k = 0; k < 12; ++k) gw[k] = w[k];
+      if (a.wdbuf) {
+        bspline_dweights<double>(tx, P, w);
+        bspline_dweights<double>(ty, P, w + 4);
+        bspline_dweights<double>(tz, P, w + 8);
+        double* gd = a.wdbuf + (size_t)i * 12;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) gd[k] = w[k];
+      }
     }
     a.wbase[i] = make_int4(fx, fy, fz, 0);
   }
@@ -357,6 +432,62 @@ __device__ __forceinline__ void gather_el(const ForceArgs& a, int i, int lane, d
   const int P3 = P * P * P;
   gx = gy = gz = vd = 0;
   const size_t NN = (size_t)N * N;
+  if (a.gradw) {
+    // Eq. F_Benoit: sum_n grad W phi_n; returned as 2 sum_n (dW/dt) phi_n so
+    // that the common prefactor -k_e Q / 2h gives -k_e Q sum_n grad W phi_n
+    if (a.mixed) {
+      const float* w = a.wbuf32 + (size_t)i * 12;
+      const float* d = a.wdbuf32 + (size_t)i * 12;
+      const float2* f = reinterpret_cast<const float2*>(a.phi);
+      float sx = 0.f, sy = 0.f, sz = 0.f, s0 = 0.f;
+      for (int sidx = lane; sidx < P3; sidx += 32) {
+        const int ia = sidx % P, ib = (sidx / P) % P, ic = sidx / (P * P);
+        const int ix = wrap_idx(first.x + ia, N), iy = wrap_idx(first.y + ib, N), iz = wrap_idx(first.z + ic, N);
+        const float2 c0 = f[iz * NN + (size_t)iy * N + ix];
+        const float ph = c0.x + c0.y;
+        const float wyz = w[4 + ib] * w[8 + ic];
+        sx += d[ia] * wyz * ph;
+        sy += w[ia] * d[4 + ib] * w[8 + ic] * ph;
+        sz += w[ia] * w[4 + ib] * d[8 + ic] * ph;
+        s0 += w[ia] * wyz * ph;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      }
+      gx = 2.0 * (double)sx;
+      gy = 2.0 * (double)sy;
+      gz = 2.0 * (double)sz;
+      vd = s0;
+    } else {
+      const double* w = a.wbuf + (size_t)i * 12;
+      const double* d = a.wdbuf + (size_t)i * 12;
+      for (int sidx = lane; sidx < P3; sidx += 32) {
+        const int ia = sidx % P, ib = (sidx / P) % P, ic = sidx / (P * P);
+        const int ix = wrap_idx(first.x + ia, N), iy = wrap_idx(first.y + ib, N), iz = wrap_idx(first.z + ic, N);
+        const size_t at = iz * NN + (size_t)iy * N + ix;
+        double ph;
+        if (a.phi_df) {
+          const float2 c0 = reinterpret_cast<const float2*>(a.phi)[at];
+          ph = (double)c0.x + (double)c0.y;
+        } else {
+          ph = a.phi[at];
+        }
+        const double wyz = w[4 + ib] * w[8 + ic];
+        gx += d[ia] * wyz * ph;
+        gy += w[ia] * d[4 + ib] * w[8 + ic] * ph;
+        gz += w[ia] * w[4 + ib] * d[8 + ic] * ph;
+        vd += w[ia] * wyz * ph;
+      }
+      gx = 2.0 * warp_sum(gx);
+      gy = 2.0 * warp_sum(gy);
+      gz = 2.0 * warp_sum(gz);
+      vd = warp_sum(vd);
+    }
+    return;
+  }
   if (a.mixed) {
     // mixed precision: FP32 weights, differences of the double-float
     // potential in FP32, FP32 sums
@@ -451,6 +582,7 @@ __device__ __forceinline__ void finish_ion(const ForceArgs& a, int i, double gx,
     vx += kick * Fx;
     vy += kick * Fy;
     vz += kick * Fz;
+    if (a.ou.on) o_step(a.ou, i, t, (unsigned)a.rec->step, 1u, vx, vy, vz);
     a.vel[i] = vx;
     a.vel[n + i] = vy;
     a.vel[2 * n + i] = vz;

@@ -76,6 +76,14 @@ maze_status validate(const maze_config* c) {
     return fail(MAZE_ERR_INVALID, "precision must be MAZE_FP64 or MAZE_MIXED");
   if (c->precision == MAZE_MIXED && c->solver != MAZE_SOLVER_MG)
     return fail(MAZE_ERR_INVALID, "precision MAZE_MIXED runs the multigrid solver (MAZE_SOLVER_MG)");
+  if (c->scheme != MAZE_SCHEME_MAZE && c->scheme != MAZE_SCHEME_MG_STATIC && c->scheme != MAZE_SCHEME_MG_TIMEPROP)
+    return fail(MAZE_ERR_INVALID, "scheme must be one of MAZE_SCHEME_*");
+  if (c->force_estimator != MAZE_FORCE_CD && c->force_estimator != MAZE_FORCE_GRADW)
+    return fail(MAZE_ERR_INVALID, "force_estimator must be MAZE_FORCE_CD or MAZE_FORCE_GRADW");
+  if (!(c->langevin_gamma >= 0) || !isfinite(c->langevin_gamma))
+    return fail(MAZE_ERR_INVALID, "langevin_gamma must be finite and >= 0");
+  if (!(c->langevin_T >= 0) || !isfinite(c->langevin_T))
+    return fail(MAZE_ERR_INVALID, "langevin_T must be finite and >= 0");
   if (!c->pos || !c->vel || !c->type) return fail(MAZE_ERR_INVALID, "pos, vel and type must be non-NULL");
   if (!(c->mass[0] > 0) || !(c->mass[1] > 0)) return fail(MAZE_ERR_INVALID, "masses must be > 0");
   double qsum = 0, qabs = 0;
@@ -99,6 +107,19 @@ double wrap_host(double x, double L) {
 }
 
 // --- argument blocks for the current rotation ------------------------------
+
+LangevinArgs langevin_args(maze_ctx* c) {
+  LangevinArgs o = {};
+  const maze_config& g = c->cfg;
+  o.on = g.langevin_gamma > 0 ? 1 : 0;
+  o.a = exp(-0.5 * g.langevin_gamma * g.dt);
+  const double v2 = (1.0 - o.a * o.a) * MAZE_KB_EV_PER_K * g.langevin_T * MAZE_ACC_UNIT;
+  o.sd0 = sqrt(v2 / g.mass[0]);
+  o.sd1 = sqrt(v2 / g.mass[1]);
+  o.key0 = (unsigned)(g.seed & 0xffffffffu);
+  o.key1 = (unsigned)(g.seed >> 32);
+  return o;
+}
 
 IonArgs ion_args(maze_ctx* c, int do_move, int do_spread) {
   IonArgs a;
@@ -133,6 +154,9 @@ IonArgs ion_args(maze_ctx* c, int do_move, int do_spread) {
   a.rel_hi = c->mixed ? c->rel_hi : nullptr;
   a.rel_lo = c->mixed ? c->rel_lo : nullptr;
   a.cell_len = c->nc >= 3 ? c->L / c->nc : c->L;
+  a.wdbuf = c->wdbuf;
+  a.wdbuf32 = c->wdbuf32;
+  a.ou = langevin_args(c);
   return a;
 }
 
@@ -191,6 +215,9 @@ ForceArgs force_args(maze_ctx* c, const double* phi, int do_kick, int count_step
   a.wbuf32 = c->wbuf32;
   a.wbuf = c->wbuf;
   a.wbase = c->wbase;
+  a.wdbuf = c->wdbuf;
+  a.wdbuf32 = c->wdbuf32;
+  a.gradw = c->cfg.force_estimator == MAZE_FORCE_GRADW ? 1 : 0;
   a.nc = c->nc;
   a.cell_start = c->cell_start;
   a.cell_ions = c->cell_ions;
@@ -229,11 +256,22 @@ ForceArgs force_args(maze_ctx* c, const double* phi, int do_kick, int count_step
   a.inv_Lf = (float)(1.0 / c->L);
   a.do_kick = do_kick;
   a.count_step = count_step;
+  a.ou = langevin_args(c);
   a.part = c->fpart;
   a.ticket = c->ticket;
   a.rec = c->rec;
   a.gate = c->gate;
   return a;
+}
+
+// The direct schemes solve M phi = -4pi q/h from phi_p; in correction form
+// phi = phi_p - (4pi/h) y with M y = sigma(phi_p) from y = 0, and their
+// residual max|M phi + (4pi/h) q| (Eq. res_poisson) is (4pi/h) max|M y - sigma|.
+void set_scheme(maze_ctx* c, int zero_phi, int& static_guess, double& tol, double& res_scale) {
+  const bool direct = !zero_phi && c->cfg.scheme != MAZE_SCHEME_MAZE;
+  static_guess = (!zero_phi && c->cfg.scheme == MAZE_SCHEME_MG_STATIC) ? 1 : 0;
+  res_scale = direct ? 4.0 * kPi / c->h : 1.0;
+  tol = c->cfg.tol / res_scale;
 }
 
 SolveArgs solve_args(maze_ctx* c, int zero_phi, double* q_out) {
@@ -260,6 +298,7 @@ SolveArgs solve_args(maze_ctx* c, int zero_phi, double* q_out) {
   a.tol = c->cfg.tol;
   a.max_iter = zero_phi ? c->max_iter_init : c->cfg.max_iter;
   a.zero_phi = zero_phi;
+  set_scheme(c, zero_phi, a.static_guess, a.tol, a.res_scale);
   a.gate = c->gate;
   return a;
 }
@@ -277,6 +316,8 @@ MixedArgs mixed_args(maze_ctx* c, int zero_phi, double* q_out) {
   a.q_out = q_out;
   a.max_iter = zero_phi ? c->max_iter_init : c->cfg.max_iter;
   a.zero_phi = zero_phi;
+  set_scheme(c, zero_phi, a.static_guess, a.tol, a.res_scale);
+  a.y_reset = (!zero_phi && c->cfg.scheme != MAZE_SCHEME_MAZE) ? 1 : 0;
   a.recs = c->recs;
   a.bar = c->bar;
   a.rec = c->rec;
@@ -286,6 +327,7 @@ MixedArgs mixed_args(maze_ctx* c, int zero_phi, double* q_out) {
 
 maze_status enqueue_solve(maze_ctx* c, int zero_phi, double* q_out) {
   CK(cudaMemsetAsync(c->recs, 0, c->recs_bytes, c->stream));
+  if (!zero_phi && c->cfg.scheme != MAZE_SCHEME_MAZE) CK(cudaMemsetAsync(c->y, 0, c->ng * 8, c->stream));
   if (c->mixed) {
     CK(cudaMemsetAsync(c->bar, 0, sizeof(unsigned), c->stream));
     CK(launch_mixed_solve(mixed_args(c, zero_phi, q_out), c->mx_cluster, c->mx_blocks, c->stream));
@@ -507,12 +549,15 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
   AL(c->pos32, (size_t)n);
   // each precision allocates only the buffers its kernels touch
   const bool mixed = cfg->precision == MAZE_MIXED;
+  const bool gradw = cfg->force_estimator == MAZE_FORCE_GRADW;
   if (mixed) {
     AL(c->wbuf32, 12 * (size_t)n);
+    if (gradw) AL(c->wdbuf32, 12 * (size_t)n);
     AL(c->rel_hi, (size_t)n);
     AL(c->rel_lo, (size_t)n);
   } else {
     AL(c->wbuf, 12 * (size_t)n);
+    if (gradw) AL(c->wdbuf, 12 * (size_t)n);
   }
   AL(c->wbase, (size_t)n);
   AL(c->qfix, ng);

@@ -162,8 +162,11 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_step(BatchArgs b) {
     // reads the same value: nothing writes it before the next barrier)
     if (__ldcg(&d.ion.rec->status) != MAZE_OK) continue;
     const int n = d.ion.n, nc = d.ion.nc;
-    // S1: half kick + drift, weights, cell counts
+    // S1: half kick + drift, weights, cell counts; the direct schemes solve
+    // from y = 0
     for (int i = tid; i < n; i += stride) move_ion(d.ion, i);
+    if (d.mixed.y_reset)
+      for (int m = tid; m < d.mixed.n; m += stride) d.mixed.y[m] = make_float2(0.f, 0.f);
     sync.barrier();
     // S3: spread (one warp per ion); S2: the first CTA scans the cell counts
     if (nc >= 3 && rank == 0) cell_scan_block(d.cell);

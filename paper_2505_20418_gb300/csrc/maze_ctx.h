@@ -55,6 +55,8 @@ struct maze_ctx {
   float4* pos32 = nullptr;
   double* wbuf = nullptr;   // [n][3][4] B-spline weights of the current positions
   float* wbuf32 = nullptr;  // FP32 weights (mixed precision)
+  double* wdbuf = nullptr;  // weight derivatives (force estimator of Eq. F_Benoit)
+  float* wdbuf32 = nullptr;
   int4* wbase = nullptr;
   // grid
   unsigned long long* qfix = nullptr;

@@ -32,6 +32,15 @@ struct LLRec;  // flag-carrying reduction record (defined below)
 // ---------------------------------------------------------------------------
 // Kernel argument blocks (plain device pointers).
 
+// O part of the OVRVO Langevin integrator: v <- a v + sd[type] xi over a half
+// step, xi from Philox-4x32-10 with counter (ion, step, stage, 0).
+struct LangevinArgs {
+  int on;
+  double a;              // exp(-gamma dt / 2)
+  double sd0, sd1;       // sqrt((1 - a^2) k_B T / m) per species, Angstrom/fs
+  unsigned key0, key1;   // generator key (seed)
+};
+
 struct IonArgs {
   int n;                 // ions
   double L, h;           // box edge, grid spacing
@@ -59,6 +68,9 @@ struct IonArgs {
   float4* rel_lo;        //     corner as hi + lo floats (mixed precision) or nullptr
   double cell_len;       // L / nc (L when there is no cell list)
   int4* wbase;           // [n] first support node per axis
+  double* wdbuf;         // [n][3][4] weight derivatives dW/dt (Eq. F_Benoit, FP64) or nullptr
+  float* wdbuf32;        // the same in FP32 (mixed precision) or nullptr
+  LangevinArgs ou;       // OVRVO O steps (off when ou.on == 0)
 };
 
 struct CellArgs {
@@ -93,6 +105,9 @@ struct ForceArgs {
   const double* wbuf;    // [n][3][4] weights written by k_ion_update
   const float* wbuf32;   // [n][3][4] FP32 weights (mixed precision)
   const int4* wbase;     // [n]
+  const double* wdbuf;   // [n][3][4] weight derivatives (force estimator of Eq. F_Benoit)
+  const float* wdbuf32;
+  int gradw;             // 1: F = -k_e Q sum_n grad W phi_n (Eq. F_Benoit), else Eq. F_nostra
   int mixed;             // 1: FP32 gather and pair arithmetic
   int by_cell;           // 1: one block per cell (k_forces_cells), else one warp per ion
   int cell_split;        // blocks per cell in k_forces_cells (each takes a slice of the cell's ions)
@@ -120,6 +135,7 @@ struct ForceArgs {
   float Lf, inv_Lf;
   int do_kick;           // 1: second half kick + V_work increment
   int count_step;        // 1: this completes an MD step
+  LangevinArgs ou;       // second O step after the kick (when do_kick)
   double* part;          // [gridDim][8] block partials
   unsigned* ticket;      // last-block ticket (self-resetting)
   maze_stats* rec;
@@ -148,6 +164,8 @@ struct SolveArgs {
   double tol;
   int max_iter;
   int zero_phi;          // step 0: phi^k = phi^{k-1} = 0
+  int static_guess;      // 1: phi_p = phi^k (direct solve from the previous potential)
+  double res_scale;      // reported residual = res_scale * max|M y - sigma_p|
   const int* gate;       // 1: this step was skipped
 };
 
@@ -192,6 +210,9 @@ struct MixedArgs {
   int max_iter;
   double inv_n;
   int zero_phi;
+  int static_guess;        // 1: phi_p = phi^k (direct solve from the previous potential)
+  int y_reset;             // 1: the solve starts from y = 0 (direct schemes; batch kernel clears y)
+  double res_scale;        // reported residual = res_scale * max|M y - sigma_p|
   LLRec* recs;             // grid form only
   unsigned* bar;           // grid form only
   maze_stats* rec;

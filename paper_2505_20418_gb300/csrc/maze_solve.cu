@@ -48,10 +48,15 @@ __global__ void __launch_bounds__(kSolveThreads) k_cg_solve(SolveArgs a) {
       if (!a.zero_phi) {
         const double* pk = a.phi_k;
         const double* pm = a.phi_km1;
-        php = 2.0 * pk[m] - pm[m];
         const double nk = (pk[b.xm] + pk[b.xp]) + (pk[b.ym] + pk[b.yp]) + (pk[b.zm] + pk[b.zp]);
-        const double nm = (pm[b.xm] + pm[b.xp]) + (pm[b.ym] + pm[b.yp]) + (pm[b.zm] + pm[b.zp]);
-        Mphp = 2.0 * nk - nm - 6.0 * php;
+        if (a.static_guess) {
+          php = pk[m];
+          Mphp = nk - 6.0 * php;
+        } else {
+          php = 2.0 * pk[m] - pm[m];
+          const double nm = (pm[b.xm] + pm[b.xp]) + (pm[b.ym] + pm[b.yp]) + (pm[b.zm] + pm[b.zp]);
+          Mphp = 2.0 * nk - nm - 6.0 * php;
+        }
       }
       const double sg = a.c_sig * Mphp + q;
       a.phi_out[m] = php;
@@ -188,7 +193,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_cg_solve(SolveArgs a) {
   if (tid == 0) {
     maze_stats* r = a.rec;
     r->iters = it;
-    r->resid = res;
+    r->resid = res * a.res_scale;
     r->total_iters += it;
     if (!isfinite(res)) r->status = MAZE_ERR_NONFINITE;
     else if (!(res < a.tol)) r->status = MAZE_ERR_NOT_CONVERGED;

@@ -315,7 +315,11 @@ __device__ void mixed_body(const MixedArgs& a, S& sync) {
     a.qfix[m] = 0ull;
     if (a.q_out) a.q_out[m] = (double)qi * kQInv;
     df php = {0.f, 0.f}, Mphp = {0.f, 0.f};
-    if (!a.zero_phi) {
+    if (a.zero_phi) {
+    } else if (a.static_guess) {
+      php = df_from(a.phi_k[m]);
+      Mphp = df_sub(dsum6(a.phi_k, q), df_mul_f(php, 6.f));
+    } else {
       php = df_sub(df_twice(df_from(a.phi_k[m])), df_from(a.phi_km1[m]));
       const df nk = dsum6(a.phi_k, q), nm = dsum6(a.phi_km1, q);
       const df s6 = df_sub(df_twice(nk), nm);
@@ -498,7 +502,7 @@ __device__ void mixed_body(const MixedArgs& a, S& sync) {
   if (tid == 0) {
     maze_stats* r = a.rec;
     r->iters = it;
-    r->resid = res;
+    r->resid = res * a.res_scale;
     r->total_iters += it;
     if (!isfinite(res)) r->status = MAZE_ERR_NONFINITE;
     else if (!(res < a.tol)) r->status = MAZE_ERR_NOT_CONVERGED;

@@ -19,6 +19,8 @@ MAZE_OK, MAZE_ERR_INVALID, MAZE_ERR_OOM, MAZE_ERR_NOT_CONVERGED = 0, 1, 2, 3
 MAZE_ERR_NONFINITE, MAZE_ERR_TIMEOUT, MAZE_ERR_CUDA = 4, 5, 6
 MAZE_SOLVER_CG, MAZE_SOLVER_MG = 0, 1
 MAZE_FP64, MAZE_MIXED = 0, 1
+MAZE_SCHEME_MAZE, MAZE_SCHEME_MG_STATIC, MAZE_SCHEME_MG_TIMEPROP = 0, 1, 2
+MAZE_FORCE_CD, MAZE_FORCE_GRADW = 0, 1
 MAZE_POS, MAZE_VEL, MAZE_FORCE, MAZE_FORCE_EL = 0, 1, 2, 3
 MAZE_PHI, MAZE_PHI_PREV, MAZE_Y, MAZE_CHARGE, MAZE_SIGMA = 4, 5, 6, 7, 8
 
@@ -45,7 +47,9 @@ class MazeConfig(ctypes.Structure):
         ("tf_A", _D * 3), ("tf_B", _D), ("tf_s", _D * 3), ("tf_C", _D * 3), ("tf_D", _D * 3),
         ("r_cut", _D), ("dt", _D), ("tol", _D),
         ("max_iter", _I), ("solver", _I), ("mg_pre", _I), ("mg_post", _I),
-        ("order_P", _I), ("precision", _I), ("cuda_stream", ctypes.c_void_p),
+        ("order_P", _I), ("precision", _I), ("scheme", _I), ("force_estimator", _I),
+        ("langevin_gamma", _D), ("langevin_T", _D), ("seed", ctypes.c_uint64),
+        ("cuda_stream", ctypes.c_void_p),
     ]
 
 
@@ -232,7 +236,8 @@ def maze_version() -> str:
 
 def make_config(pos, vel, types, L, N, tf, *, r_cut, dt=1.0, tol=1e-10, max_iter=10000,
                 solver=MAZE_SOLVER_CG, order=4, precision=MAZE_FP64, charge=(1.0, -1.0),
-                mass=(22.98977, 35.453), mg_pre=2, mg_post=2, stream=None):
+                mass=(22.98977, 35.453), mg_pre=2, mg_post=2, stream=None, scheme=MAZE_SCHEME_MAZE,
+                force_estimator=MAZE_FORCE_CD, langevin_gamma=0.0, langevin_T=0.0, seed=0):
     """Build a MazeConfig; the returned tuple keeps the host arrays alive."""
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     vel = np.ascontiguousarray(vel, dtype=np.float64)
@@ -260,6 +265,11 @@ def make_config(pos, vel, types, L, N, tf, *, r_cut, dt=1.0, tol=1e-10, max_iter
     c.mg_post = int(mg_post)
     c.order_P = int(order)
     c.precision = int(precision)
+    c.scheme = int(scheme)
+    c.force_estimator = int(force_estimator)
+    c.langevin_gamma = float(langevin_gamma)
+    c.langevin_T = float(langevin_T)
+    c.seed = int(seed)
     c.cuda_stream = stream
     return c, (pos, vel, types)
 

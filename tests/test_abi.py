@@ -91,6 +91,10 @@ def _cfg(**over):
     (dict(solver=7), "solver"),
     (dict(solver=1, mg_pre=0), "mg_pre"),
     (dict(precision=9), "precision"),
+    (dict(scheme=3), "scheme"),
+    (dict(force_estimator=2), "force_estimator"),
+    (dict(langevin_gamma=-1.0), "langevin_gamma"),
+    (dict(langevin_T=float("nan")), "langevin_T"),
 ])
 def test_invalid_config_rejected(lib, over, msg):
     cfg, keep = _cfg(**over)

@@ -373,3 +373,124 @@ def test_cg_and_mg_agree_on_trajectory():
     _, p2, _, r2 = _short_run(10, tol=1e-13, solver="mg")
     for a, b in zip(r1, r2):
         assert np.abs(a.F - b.F).max() < 1e-10 * np.abs(a.F).max()
+
+
+# ---------------------------------------------------------------------------
+# The direct Poisson baselines of Sec. III.A (static / time-propagated start)
+
+@pytest.mark.parametrize("scheme", ["mg-static", "mg-timeprop"])
+def test_direct_schemes_reach_the_exact_potential(scheme):
+    """A direct solve of Eq. linearproblem to max|M phi + 4 pi q/h| < tol lands
+    on the DFT solution: |phi - phi_exact| <= ||M^+||_inf tol."""
+    w = synth.workload("nacl64")
+    pos, vel, types = synth.make_state(w)
+    tf = synth.tosi_fumi_nacl()
+    p = O.Params(L=w.L, N=w.N, dt=w.dt, tol=1e-9, rc=w.rc, solver="mg", scheme=scheme)
+    st = O.init(pos, vel, types, p, tf)
+    for _ in range(4):
+        st = O.step(st, p, tf)
+        assert st.resid < p.tol and st.iters >= 1
+        phi_ex, q = O.exact_potential(st.pos, st.types, p)
+        # residual of Eq. res_poisson recomputed from scratch
+        assert O.inf_norm(O.apply_M(st.phi) + (4 * np.pi / p.h) * q) < p.tol
+        # ||M^+||_inf <= N^3 / min|lambda| bounds the error of a tol-residual
+        lam = np.abs(O.M_eigenvalues(p.N)).ravel()
+        bound = p.N ** 3 / lam[lam > 1e-12].min() * p.tol
+        assert O.inf_norm(st.phi - phi_ex) < bound
+
+
+def test_timeprop_from_zero_y_is_the_maze_step():
+    """With y^0 = 0 (the first step after step 0) the SHAKE solve is, by
+    linearity, the direct solve started from phi_p = 2 phi^k - phi^{k-1}:
+    phi^nu = phi_p - (4 pi/h) y^nu iterate by iterate, so the two take the
+    same number of V-cycles when the tolerances match (tol_direct =
+    (4 pi/h) tol_maze) and end on the same potential."""
+    w = synth.workload("nacl64")
+    pos, vel, types = synth.make_state(w)
+    tf = synth.tosi_fumi_nacl()
+    pm = O.Params(L=w.L, N=w.N, dt=w.dt, tol=1e-10, rc=w.rc, solver="mg")
+    pd = O.Params(L=w.L, N=w.N, dt=w.dt, tol=1e-10 * 4 * np.pi / pm.h, rc=w.rc, solver="mg",
+                  scheme="mg-timeprop")
+    st = O.init(pos, vel, types, pm, tf)
+    a = O.step(st, pm, tf)
+    b = O.step(st, pd, tf)
+    assert a.iters == b.iters >= 2
+    assert np.abs(a.phi - b.phi).max() < 1e-9 * np.abs(a.phi).max()
+
+
+@pytest.mark.parametrize("scheme", ["mg-static", "mg-timeprop"])
+def test_direct_schemes_still_system_needs_no_work(scheme):
+    """Ions at rest: the start value (phi^k, or 2 phi^k - phi^{k-1} = phi^k)
+    already solves Eq. linearproblem, so no V-cycle runs."""
+    L, n = 12.6, 4
+    pos, types = synth.rocksalt(n, L, 0.0, np.random.default_rng(0))
+    tf = synth.TosiFumi(A=(0.0,) * 3, B=1.0, s=(0.0,) * 3, C=(0.0,) * 3, D=(0.0,) * 3)
+    p = O.Params(L=L, N=16, dt=1.0, tol=1e-8, rc=6.3, solver="mg", scheme=scheme)
+    # step 0 to a tolerance well inside the direct one ((4 pi/h) 1e-12 << 1e-8)
+    p0 = O.Params(L=L, N=16, dt=1.0, tol=1e-12, rc=6.3, solver="mg")
+    st = O.init(pos, np.zeros_like(pos), types, p0, tf)
+    for _ in range(3):
+        st = O.step(st, p, tf)
+        assert st.iters == 0
+
+
+# ---------------------------------------------------------------------------
+# OVRVO Langevin (Sec. III) and its counter-based Gaussian numbers
+
+def test_philox_known_answers():
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        ctr = tuple(np.array([c], dtype=np.uint64) for c in v[:4])
+        out = O.philox4x32(ctr, (v[4], v[5]))
+        assert [int(o[0]) for o in out] == v[6:]
+
+
+def test_gaussians_have_unit_normal_moments():
+    z = np.concatenate([O.gaussians(20000, s, st, 12345) for s in range(5) for st in (0, 1)]).ravel()
+    n = z.size
+    assert abs(z.mean()) < 5 / math.sqrt(n)
+    assert abs(z.var() - 1) < 5 * math.sqrt(2 / n)
+    assert abs((z ** 4).mean() - 3) < 5 * math.sqrt(96 / n)
+    # distinct counters are uncorrelated; the same counter repeats
+    a, b = O.gaussians(20000, 7, 0, 1), O.gaussians(20000, 7, 1, 1)
+    assert abs(np.corrcoef(a.ravel(), b.ravel())[0, 1]) < 5 / math.sqrt(a.size)
+    assert np.array_equal(a, O.gaussians(20000, 7, 0, 1))
+    assert not np.array_equal(a, O.gaussians(20000, 7, 0, 2))
+
+
+def test_o_step_preserves_and_reaches_maxwell():
+    """The O step is an exact Ornstein-Uhlenbeck update: v ~ N(0, kT/m) stays
+    N(0, kT/m); from v = 0 the variance after one step is (1 - a^2) kT/m."""
+    n = 50000
+    types = (np.arange(n) % 2).astype(np.int32)
+    p = O.Params(L=10.0, N=8, dt=1.0, tol=1e-8, gamma=0.05, T_bath=1200.0, seed=99)
+    m = np.asarray(p.mass)[types][:, None]
+    kt_m = O.K_B * p.T_bath * O.ACC / m
+    v0 = np.sqrt(kt_m) * np.random.default_rng(3).normal(size=(n, 3))
+    v1 = O.o_step(v0, types, p, 0, 0)
+    ratio = (v1 ** 2 / kt_m).mean()
+    assert abs(ratio - 1) < 5 * math.sqrt(2 / (3 * n))
+    a = math.exp(-p.gamma * p.dt / 2)
+    v2 = O.o_step(np.zeros((n, 3)), types, p, 0, 1)
+    assert abs((v2 ** 2 / kt_m).mean() - (1 - a * a)) < 5 * (1 - a * a) * math.sqrt(2 / (3 * n))
+
+
+def test_ovrvo_tends_to_verlet_and_thermalises():
+    w = synth.workload("nacl64")
+    pos, vel, types = synth.make_state(w)
+    tf = synth.tosi_fumi_nacl()
+    # gamma -> 0: the O steps vanish, the trajectory is velocity Verlet's (the
+    # noise left at gamma = 1e-13 moves ions by ~1e-8 Angstrom in 5 steps)
+    pv = O.Params(L=w.L, N=w.N, dt=w.dt, tol=1e-10, rc=w.rc, solver="mg")
+    pl = O.Params(L=w.L, N=w.N, dt=w.dt, tol=1e-10, rc=w.rc, solver="mg", gamma=1e-13, T_bath=1200.0, seed=5)
+    a = O.run(pos, vel, types, pv, tf, 5)
+    b = O.run(pos, vel, types, pl, tf, 5)
+    assert np.abs(a.pos - b.pos).max() < 1e-6
+    # strong friction towards a hot bath from a cold start heats the ions
+    cold = np.zeros_like(vel)
+    ph = O.Params(L=w.L, N=w.N, dt=w.dt, tol=1e-8, rc=w.rc, solver="mg", gamma=0.2, T_bath=3000.0, seed=6)
+    st = O.run(pos, cold, types, ph, tf, 30)
+    T = 2 * O.kinetic(st, ph) / (3 * len(types) * O.K_B)
+    assert 1500 < T < 6000
