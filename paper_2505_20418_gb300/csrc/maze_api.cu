@@ -312,6 +312,7 @@ MixedArgs mixed_args(maze_ctx* c, int zero_phi, double* q_out) {
   a.phi_out = reinterpret_cast<float2*>(c->phi[(c->ik + 2) % 3]);
   a.sigma = reinterpret_cast<float2*>(c->sigma);
   a.y = reinterpret_cast<float2*>(c->y);
+  a.y2 = reinterpret_cast<float2*>(c->y2);
   a.qfix = c->qfix;
   a.q_out = q_out;
   a.max_iter = zero_phi ? c->max_iter_init : c->cfg.max_iter;
@@ -608,28 +609,22 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
     m.N = c->N;
     m.n = (int)ng;
     m.L = c->mg.L;
-    size_t tot = 0;
     for (int l = 0; l < m.L; ++l) {
       m.Nl[l] = c->mg.Nl[l];
-      m.off[l] = c->mg.off[l];
       m.lg[l] = -1;
       for (int b = 1; b < 16; ++b)
         if ((1 << b) == m.Nl[l]) m.lg[l] = b;
-      tot += (size_t)m.Nl[l] * m.Nl[l] * m.Nl[l];
     }
     m.nu1 = cfg->mg_pre;
     m.nu2 = cfg->mg_post;
-    AL(c->mx_e0, ng);
-    AL(c->mx_r0, ng);
-    AL(c->mx_lx, tot);
-    AL(c->mx_lb, tot);
-    AL(c->mx_lr, tot);
+    // the global form of the V-cycle storage: one part holding every level,
+    // sized by the same layout function the kernels use
+    const size_t tot = resident_bytes_host(m, 1) / sizeof(float);
+    m.scratch_floats = tot;
+    AL(c->y2, ng);
+    AL(c->mx_scratch, tot);
     AL(c->mx_g, gk.size());
-    m.e0 = c->mx_e0;
-    m.r0 = c->mx_r0;
-    m.lx = c->mx_lx;
-    m.lb = c->mx_lb;
-    m.lr = c->mx_lr;
+    m.scratch = c->mx_scratch;
     m.gkerf = c->mx_g;
     const double cs = c->h / (4.0 * kPi), cp = 4.0 * kPi / c->h;
     m.c_sig_h = (float)cs;
@@ -642,6 +637,7 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
     // grid above
     if (c->N <= 64) {
       c->mx_cluster = mixed_cluster_size();
+      m.resident = resident_bytes_host(m, c->mx_cluster) <= (size_t)kResidentSmem ? 1 : 0;
     } else {
       c->mx_blocks = mixed_grid_blocks((int)ng);
       if (c->mx_blocks > c->sblocks) c->mx_blocks = c->sblocks;

@@ -100,10 +100,14 @@ struct __align__(16) BoxDesc {
   int split;   // (cell, slice) work items per cell in the force phase
 };
 
-constexpr int kBatchThreads = 1024;
+constexpr int kBatchThreads = 512;
 constexpr int kBatchWarps = kBatchThreads / 32;
-static_assert(sizeof(CellSmem<kBatchWarps>) >= (size_t)kBatchWarps * kSortCap * sizeof(int),
-              "the sort's id buffers alias the force staging buffer");
+// dynamic shared memory of the step kernel: the force staging, the sort's
+// buffers and (when a box fits) the cluster-resident V-cycle share it
+constexpr int kBatchSmem = kResidentSmem;
+static_assert(sizeof(CellSmem<kBatchWarps>) <= (size_t)kBatchSmem &&
+                  (size_t)kBatchWarps * kSortCap * sizeof(int) <= (size_t)kBatchSmem,
+              "the force staging and the sort's buffers fit the dynamic shared memory");
 
 struct BatchArgs {
   const BoxDesc* desc;  // [slots]
@@ -152,6 +156,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_step(BatchArgs b) {
     const int ik = b.ik[slot];
     __syncthreads();
     if (threadIdx.x == 0) {
+      d.mixed.resident = resident_bytes(d.mixed, C) <= (size_t)kBatchSmem ? 1 : 0;
       d.mixed.phi_k = d.phi[ik];
       d.mixed.phi_km1 = d.phi[(ik + 1) % 3];
       d.mixed.phi_out = d.phi[(ik + 2) % 3];
@@ -180,8 +185,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_step(BatchArgs b) {
       int* ids = reinterpret_cast<int*>(dyn) + warp * kSortCap;
       for (int c = gwarp; c < d.cell.ncell; c += nwarps) cell_sort_one(d.cell, c, lane, ids);
     }
-    // S4-S6 (its first barrier also orders the sort before the forces)
-    mixed_body(d.mixed, sync);
+    // S4-S6 (its first barrier also orders the sort before the forces); the
+    // resident form reuses the shared memory of the sort and the forces
+    __syncthreads();
+    mixed_body(d.mixed, sync, d.mixed.resident ? reinterpret_cast<float*>(dyn) : nullptr);
     const int st = __ldcg(&d.force.rec->status);
     if (st != MAZE_OK && st != MAZE_ERR_NOT_CONVERGED) continue;
     // S7-S9
@@ -283,13 +290,12 @@ maze_status check_id(const maze_batch* b, int id) {
 // Largest cluster of the step kernel the device co-schedules (16 needs the
 // non-portable size), and the number of such clusters resident at once.
 int max_clusters(int cta) {
-  cudaFuncSetAttribute(k_batch_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sizeof(CellSmem<kBatchWarps>));
+  cudaFuncSetAttribute(k_batch_step, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchSmem);
   if (cta > 8) cudaFuncSetAttribute(k_batch_step, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cta);
   cfg.blockDim = dim3(kBatchThreads);
-  cfg.dynamicSmemBytes = sizeof(CellSmem<kBatchWarps>);
+  cfg.dynamicSmemBytes = kBatchSmem;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = cta;
@@ -307,7 +313,7 @@ maze_status launch_step(maze_batch* b) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(b->nclusters * b->cluster);
   cfg.blockDim = dim3(kBatchThreads);
-  cfg.dynamicSmemBytes = sizeof(CellSmem<kBatchWarps>);
+  cfg.dynamicSmemBytes = kBatchSmem;
   cfg.stream = b->stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

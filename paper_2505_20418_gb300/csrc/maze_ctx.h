@@ -64,6 +64,7 @@ struct maze_ctx {
   double* phi[3] = {nullptr, nullptr, nullptr};
   int ik = 0;  // phi^k is phi[ik], phi^{k-1} phi[(ik+1)%3], scratch phi[(ik+2)%3]
   double *sigma = nullptr, *y = nullptr, *r = nullptr, *p = nullptr, *p1 = nullptr, *Mp = nullptr;
+  double* y2 = nullptr;   // second y buffer (mixed precision, cluster-resident solve)
   maze::LLRec* recs = nullptr;
   size_t recs_bytes = 0;
   unsigned* bar = nullptr;
@@ -74,7 +75,7 @@ struct maze_ctx {
   bool mixed = false;
   maze::MixedArgs mx = {};
   int mx_cluster = 0, mx_blocks = 0;
-  float *mx_e0 = nullptr, *mx_r0 = nullptr, *mx_lx = nullptr, *mx_lb = nullptr, *mx_lr = nullptr, *mx_g = nullptr;
+  float *mx_scratch = nullptr, *mx_g = nullptr;
   int sblocks = 0;
   // cells
   int nc = 0, ncell = 0, cell_split = 1;

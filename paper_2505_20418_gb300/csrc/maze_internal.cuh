@@ -183,7 +183,10 @@ struct MgArgs {
 };
 
 // Mixed-precision solve (double-float outer iteration, FP32 V-cycle).
-constexpr int kMixedThreads = 1024;
+constexpr int kMixedClusterThreads = 512;   // one cluster per box
+constexpr int kMixedGridThreads = 512;      // cooperative grid (large boxes)
+// Dynamic shared memory a CTA may give the cluster-resident V-cycle.
+constexpr int kResidentSmem = 200 * 1024;
 struct MixedArgs {
   int N, n;
   const float2* phi_k;     // double-float grids (hi, lo)
@@ -191,18 +194,16 @@ struct MixedArgs {
   float2* phi_out;
   float2* sigma;
   float2* y;
+  float2* y2;              // second y buffer of the cluster-resident form
+  int resident;            // 1: V-cycle vectors in the cluster's shared memory
   unsigned long long* qfix;  // read and cleared
   double* q_out;           // optional copy of q
-  float* e0;               // [N^3] correction on level 0
-  float* r0;               // [N^3] outer residual (FP32) = level-0 rhs
-  float* lx;               // levels >= 1: corrections (packed, off[l])
-  float* lb;               // levels >= 1: right-hand sides
-  float* lr;               // all levels: residuals
+  float* scratch;          // global form of the V-cycle storage (slab layout of one part)
+  size_t scratch_floats;   // its size; the kernels refuse a layout that does not fit
   const float* gkerf;      // [Nc^3] coarsest pseudo-inverse kernel
   int L;
   int Nl[kMaxLevels];
   int lg[kMaxLevels];      // log2(N_l) for powers of two, else -1
-  size_t off[kMaxLevels];
   int nu1, nu2;
   float c_sig_h, c_sig_l;  // h/4pi as a double-float
   float c_phi_h, c_phi_l;  // 4pi/h as a double-float
@@ -231,6 +232,8 @@ cudaError_t launch_mg_solve(const SolveArgs& a, const MgArgs& g, int blocks, cud
 int mg_blocks(int n_points);
 cudaError_t launch_mixed_solve(const MixedArgs& a, int cluster, int blocks, cudaStream_t s);
 int mixed_cluster_size();
+// Shared-memory bytes per CTA of the cluster-resident V-cycle for C CTAs.
+size_t resident_bytes_host(const MixedArgs& a, int C);
 int mixed_grid_blocks(int n_points);
 // Sets the message returned by maze_last_error on the calling thread.
 void set_last_error(const char* msg);

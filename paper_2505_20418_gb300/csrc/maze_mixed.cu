@@ -5,20 +5,23 @@
 
 namespace maze {
 
-__global__ void __launch_bounds__(kMixedThreads) k_mixed_cluster(MixedArgs a) {
+__global__ void __launch_bounds__(kMixedClusterThreads) k_mixed_cluster(MixedArgs a) {
+  extern __shared__ __align__(16) float dsm[];
   if (*a.gate != 0 || a.rec->status != MAZE_OK) return;
   ClusterSync s;
-  mixed_body(a, s);
+  mixed_body(a, s, a.resident ? dsm : nullptr);
 }
 
-__global__ void __launch_bounds__(kMixedThreads) k_mixed_grid(MixedArgs a) {
+__global__ void __launch_bounds__(kMixedGridThreads) k_mixed_grid(MixedArgs a) {
   if (*a.gate != 0 || a.rec->status != MAZE_OK) return;
   GridSync s;
   s.recs = a.recs;
   s.bar = a.bar;
   s.rec = a.rec;
-  mixed_body(a, s);
+  mixed_body(a, s, nullptr);
 }
+
+size_t resident_bytes_host(const MixedArgs& a, int C) { return resident_bytes(a, C); }
 
 int mixed_cluster_size() {
   // 16 CTAs when the device can co-schedule a 16-CTA cluster of this kernel,
@@ -26,9 +29,11 @@ int mixed_cluster_size() {
   static int cached = 0;
   if (cached) return cached;
   cudaFuncSetAttribute(k_mixed_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(k_mixed_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, kResidentSmem);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(16);
-  cfg.blockDim = dim3(kMixedThreads);
+  cfg.blockDim = dim3(kMixedClusterThreads);
+  cfg.dynamicSmemBytes = kResidentSmem;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 16;
@@ -49,9 +54,9 @@ int mixed_grid_blocks(int n_points) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mixed_grid, kMixedThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mixed_grid, kMixedGridThreads, 0);
   if (per_sm < 1) per_sm = 1;
-  int want = (n_points + kMixedThreads - 1) / kMixedThreads;
+  int want = (n_points + kMixedGridThreads - 1) / kMixedGridThreads;
   int cap = sms * per_sm;
   if (cap > kMaxReduceBlocks) cap = kMaxReduceBlocks;
   return want < cap ? want : cap;
@@ -59,11 +64,12 @@ int mixed_grid_blocks(int n_points) {
 
 cudaError_t launch_mixed_solve(const MixedArgs& a, int cluster, int blocks, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
-  cfg.blockDim = dim3(kMixedThreads);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   if (cluster > 0) {
+    cfg.blockDim = dim3(kMixedClusterThreads);
     cfg.gridDim = dim3(cluster);
+    cfg.dynamicSmemBytes = a.resident ? resident_bytes(a, cluster) : 0;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = cluster;
     attr[0].val.clusterDim.y = 1;
@@ -72,6 +78,7 @@ cudaError_t launch_mixed_solve(const MixedArgs& a, int cluster, int blocks, cuda
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_mixed_cluster, a);
   }
+  cfg.blockDim = dim3(kMixedGridThreads);
   cfg.gridDim = dim3(blocks);
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;

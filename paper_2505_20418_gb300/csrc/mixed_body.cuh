@@ -203,38 +203,6 @@ struct ClusterSync {
 };
 
 // ---- grid helpers --------------------------------------------------------------
-// Point of colour c (0 red, 1 black) with half-index h on an N^3 grid, N
-// even; lg = log2(N) when N is a power of two (shifts), else -1.
-__device__ __forceinline__ int colour_point(int h, int N, int lg, int c, int& i, int& j, int& k) {
-  int row, t;
-  if (lg > 0) {
-    row = h >> (lg - 1);
-    t = h & ((N >> 1) - 1);
-    k = row >> lg;
-    j = row & (N - 1);
-  } else {
-    const int half = N >> 1;
-    row = h / half;
-    t = h - row * half;
-    k = row / N;
-    j = row - k * N;
-  }
-  i = 2 * t + ((j + k + c) & 1);
-  return i + N * (j + N * k);
-}
-
-__device__ __forceinline__ void split3(int m, int N, int lg, int& i, int& j, int& k) {
-  if (lg > 0) {
-    i = m & (N - 1);
-    j = (m >> lg) & (N - 1);
-    k = m >> (2 * lg);
-  } else {
-    k = m / (N * N);
-    j = (m / N) % N;
-    i = m % N;
-  }
-}
-
 __device__ __forceinline__ int wrapi(int a, int N) { return a < 0 ? a + N : (a >= N ? a - N : a); }
 
 template <typename T>
@@ -248,10 +216,6 @@ __device__ __forceinline__ void nbr_idx(int i, int j, int k, int N, int (&q)[6])
   q[5] = k == N - 1 ? n - NN * (N - 1) : n + NN;
 }
 
-__device__ __forceinline__ float fsum6(const float* x, const int (&q)[6]) {
-  return ((x[q[0]] + x[q[1]]) + (x[q[2]] + x[q[3]])) + (x[q[4]] + x[q[5]]);
-}
-
 __device__ __forceinline__ df dsum6(const float2* x, const int (&q)[6]) {
   const df a = df_add(df_from(x[q[0]]), df_from(x[q[1]]));
   const df b = df_add(df_from(x[q[2]]), df_from(x[q[3]]));
@@ -259,242 +223,485 @@ __device__ __forceinline__ df dsum6(const float2* x, const int (&q)[6]) {
   return df_add(df_add(a, b), c);
 }
 
-// One red-black half-sweep of colour c on a level: x = (sum of the six
-// neighbours - b) / 6 at every point of that colour (from_zero: the level's
-// guess is zero, so x = -b/6). A thread takes up to four points per round and
-// issues all of their loads before any store (the loads read the other
-// colour, the stores write this one, so batching is exact).
-__device__ __forceinline__ void half_sweep(float* x, const float* __restrict__ b, int N, int lg, int c,
-                                           bool from_zero, int tid, int stride) {
-  const int hcount = N * N * N / 2;
-  for (int h0 = tid; h0 < hcount; h0 += 4 * stride) {
-    int mm[4];
-    float v[4];
+// ---- storage of the FP32 V-cycle ----------------------------------------------
+// Level l's correction x, right-hand side b and red-point residual r are held
+// as z-slabs: a "part" q of Q owns planes [q P_l, min((q+1) P_l, N_l)) with
+// P_l = ceil(N_l / Q) and stores x[P_l][N_l^2], b[P_l][N_l^2] and (above the
+// coarsest level) r[P_l][N_l^2 / 2] of every level at the same offsets. Two forms share every phase:
+//  * cluster-resident: a part per CTA of the cluster, in its dynamic shared
+//    memory; planes owned by another CTA are read over DSMEM (generic
+//    addresses from mapa). Threads stride over their own CTA's points.
+//  * global: one part (Q = 1) in a global scratch buffer; the threads of the
+//    whole sync domain stride over all points.
+// Every point is computed by the same arithmetic in both forms, so results do
+// not depend on the form or on how many CTAs take part.
+struct RLevel {
+  int N, NN, P, lg;
+  int z0, z1;        // planes of this part
+  unsigned off;      // float offset of x in a part; b at off + P NN, r at off + 2 P NN
+};
+
+struct Slabs {
+  float* sm;         // this part's storage
+  unsigned me, Q;    // part index and count
+  int L;
+  int tail;          // first level held whole by part 0 (the tail of the V-cycle)
+  bool dsmem;
+  RLevel lv[kMaxLevels];
+  // pointer to plane z (0 <= z < N_l) of array arr (0 x, 1 b) of level l
+  __device__ __forceinline__ float* plane(int l, int arr, int z) const {
+    const RLevel& v = lv[l];
+    const unsigned q = (unsigned)(z / v.P);
+    float* p = sm + v.off + (unsigned)(arr * v.P * v.NN) + (unsigned)((z - (int)q * v.P) * v.NN);
+    if (q == me) return p;
+    float* r;
+    asm volatile("mapa.u64 %0, %1, %2;" : "=l"(r) : "l"(p), "r"(q));
+    return r;
+  }
+  // pointer to the red-point residuals of plane z of level l (N_l^2 / 2 values)
+  __device__ __forceinline__ float* rplane(int l, int z) const {
+    const RLevel& v = lv[l];
+    const unsigned q = (unsigned)(z / v.P);
+    float* p = sm + v.off + (unsigned)(2 * v.P * v.NN) + (unsigned)((z - (int)q * v.P) * (v.NN / 2));
+    if (q == me) return p;
+    float* r;
+    asm volatile("mapa.u64 %0, %1, %2;" : "=l"(r) : "l"(p), "r"(q));
+    return r;
+  }
+};
+
+// The tail of the V-cycle: the levels of at most 8^3 points, run by one CTA
+// (part 0) with block barriers instead of cluster or grid barriers. (A 16^3
+// half-sweep already costs one SM ~0.8 us, as much as a cluster barrier
+// phase; an 8^3 one ~0.2 us.)
+constexpr int kTailN = 8;
+__host__ __device__ __forceinline__ int tail_level(const MixedArgs& a) {
+  for (int l = 0; l < a.L; ++l)
+    if (a.Nl[l] <= kTailN) return l;
+  return a.L - 1;
+}
+
+// Planes per part of level l for Q parts (tail levels: all planes in part 0).
+__host__ __device__ __forceinline__ int slab_planes(const MixedArgs& a, int l, int Q) {
+  return l >= tail_level(a) ? a.Nl[l] : (a.Nl[l] + Q - 1) / Q;
+}
+
+// Floats of one part for Q parts.
+__host__ __device__ __forceinline__ size_t slab_floats(const MixedArgs& a, int Q) {
+  size_t tot = 0;
+  for (int l = 0; l < a.L; ++l) {
+    const size_t N = (size_t)a.Nl[l], P = (size_t)slab_planes(a, l, Q);
+    tot += 2 * P * N * N + (l < a.L - 1 ? P * (N * N / 2) : 0);
+  }
+  return tot;
+}
+
+__host__ __device__ __forceinline__ size_t resident_bytes(const MixedArgs& a, int C) {
+  return slab_floats(a, C) * sizeof(float);
+}
+
+__device__ __forceinline__ void slabs_setup(Slabs& R, const MixedArgs& a, float* sm, unsigned me, unsigned Q,
+                                            bool dsmem) {
+  R.sm = sm;
+  R.me = me;
+  R.Q = Q;
+  R.L = a.L;
+  R.tail = tail_level(a);
+  R.dsmem = dsmem;
+  unsigned off = 0;
+  for (int l = 0; l < a.L; ++l) {
+    RLevel& v = R.lv[l];
+    v.N = a.Nl[l];
+    v.NN = v.N * v.N;
+    v.P = slab_planes(a, l, (int)Q);
+    v.lg = a.lg[l];
+    v.z0 = min(v.N, (int)me * v.P);
+    v.z1 = min(v.N, ((int)me + 1) * v.P);
+    v.off = off;
+    off += 2u * (unsigned)(v.P * v.NN) + (l < a.L - 1 ? (unsigned)(v.P * (v.NN / 2)) : 0u);
+  }
+}
+
+// Own point h of colour c (0 red = i+j+k even, 1 black) of level v: local
+// plane kl, row j, column i; returns the index within the part.
+__device__ __forceinline__ int slab_colour_point(const RLevel& v, int h, int c, int& i, int& j, int& kl) {
+  const int half = v.N >> 1;
+  int row, t;
+  if (v.lg > 0) {
+    row = h >> (v.lg - 1);
+    t = h & (half - 1);
+    kl = row >> v.lg;
+    j = row & (v.N - 1);
+  } else {
+    row = h / half;
+    t = h - row * half;
+    kl = row / v.N;
+    j = row - kl * v.N;
+  }
+  i = 2 * t + ((j + v.z0 + kl + c) & 1);
+  return kl * v.NN + j * v.N + i;
+}
+
+// One red-black half-sweep of colour c: x = (sum of the six neighbours - b) / 6
+// at the part's points of that colour (from_zero: the guess is zero, x =
+// -b/6). A thread issues the loads of two points before either store (the
+// loads read the other colour, the stores write this one).
+__device__ __forceinline__ void res_half_sweep(const Slabs& R, int l, int c, bool from_zero, int t0, int ts) {
+  const RLevel& v = R.lv[l];
+  const int own = v.z1 - v.z0;
+  if (own <= 0) return;
+  float* x = R.sm + v.off;
+  const float* b = x + v.P * v.NN;
+  const int N = v.N, NN = v.NN;
+  const int hcount = own * NN / 2;
+  const float* xlo = from_zero ? nullptr : R.plane(l, 0, (v.z0 - 1 + N) % N);
+  const float* xhi = from_zero ? nullptr : R.plane(l, 0, v.z1 % N);
+  for (int h0 = t0; h0 < hcount; h0 += 2 * ts) {
+    int mm[2];
+    float val[2];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int h = h0 + u * stride;
+    for (int u = 0; u < 2; ++u) {
+      const int h = h0 + u * ts;
       mm[u] = -1;
-      v[u] = 0.f;
+      val[u] = 0.f;
       if (h < hcount) {
-        int i, j, k;
-        mm[u] = colour_point(h, N, lg, c, i, j, k);
+        int i, j, kl;
+        const int m = slab_colour_point(v, h, c, i, j, kl);
+        mm[u] = m;
         if (from_zero) {
-          v[u] = -b[mm[u]] * (1.f / 6.f);
+          val[u] = -b[m] * (1.f / 6.f);
         } else {
-          int q[6];
-          nbr_idx<float>(i, j, k, N, q);
-          v[u] = (fsum6(x, q) - b[mm[u]]) * (1.f / 6.f);
+          const int row = kl * NN + j * N;
+          const float* xp = x + row;
+          const float sx = xp[i == 0 ? N - 1 : i - 1] + xp[i == N - 1 ? 0 : i + 1];
+          const float sy = x[kl * NN + (j == 0 ? N - 1 : j - 1) * N + i] + x[kl * NN + (j == N - 1 ? 0 : j + 1) * N + i];
+          const float zm = kl > 0 ? x[row - NN + i] : xlo[j * N + i];
+          const float zp = kl < own - 1 ? x[row + NN + i] : xhi[j * N + i];
+          val[u] = (((sx + sy) + (zm + zp)) - b[m]) * (1.f / 6.f);
         }
       }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (mm[u] >= 0) x[mm[u]] = v[u];
+    for (int u = 0; u < 2; ++u)
+      if (mm[u] >= 0) x[mm[u]] = val[u];
   }
 }
 
-// The body shared by both launch forms. ``S`` is the sync domain; the
-// participating blocks stride over the points with tid/stride.
+// Residual r = b - M x of level l at the part's red points (after the black
+// half-sweep the residual at the black points is zero).
+__device__ __forceinline__ void res_residual(const Slabs& R, int l, int t0, int ts) {
+  const RLevel& v = R.lv[l];
+  const int own = v.z1 - v.z0;
+  if (own <= 0) return;
+  const float* x = R.sm + v.off;
+  const float* b = x + v.P * v.NN;
+  float* r = R.sm + v.off + 2 * v.P * v.NN;
+  const int N = v.N, NN = v.NN;
+  const int hcount = own * NN / 2;
+  const float* xlo = R.plane(l, 0, (v.z0 - 1 + N) % N);
+  const float* xhi = R.plane(l, 0, v.z1 % N);
+  for (int h = t0; h < hcount; h += ts) {
+    int i, j, kl;
+    const int m = slab_colour_point(v, h, 0, i, j, kl);
+    const int row = kl * NN + j * N;
+    const float* xp = x + row;
+    const float s6 = ((xp[i == 0 ? N - 1 : i - 1] + xp[i == N - 1 ? 0 : i + 1]) +
+                      (x[kl * NN + (j == 0 ? N - 1 : j - 1) * N + i] + x[kl * NN + (j == N - 1 ? 0 : j + 1) * N + i])) +
+                     ((kl > 0 ? x[row - NN + i] : xlo[j * N + i]) + (kl < own - 1 ? x[row + NN + i] : xhi[j * N + i]));
+    r[h] = b[m] - (s6 - 6.f * x[m]);
+  }
+}
+
+// Coarse rhs of level l+1 = 4 x 27-point full weighting of the fine residual
+// (4 because M is h^2-scaled): with the residual zero at the black fine
+// points only the centre (weight 1/8) and the 12 edge neighbours (1/32),
+// all red, count. Coarse plane K is computed by the part that owns fine
+// plane 2K and stored into the part that owns K (another CTA's shared
+// memory when they differ).
+__device__ __forceinline__ void res_restrict(const Slabs& R, int l, int t0, int ts) {
+  const RLevel& f = R.lv[l];
+  const RLevel& cv = R.lv[l + 1];
+  const int K0 = (f.z0 + 1) / 2, own = (f.z1 + 1) / 2 - K0;
+  if (own <= 0) return;
+  const int N = f.N, H = N / 2, Nc = cv.N, NNc = cv.NN;
+  const int count = own * NNc;
+  for (int m = t0; m < count; m += ts) {
+    const int kl = m / NNc, J = (m - kl * NNc) / Nc, I = m - kl * NNc - J * Nc;
+    const int K = K0 + kl;
+    const float* rp[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) rp[d] = R.rplane(l, (2 * K - 1 + d + N) % N);
+    // red-point residual at fine (i, j) of plane 2K + dz
+    auto res = [&](int i, int j, int dz) -> float { return rp[dz + 1][j * H + (i >> 1)]; };
+    const int i0 = 2 * I, j0 = 2 * J;
+    const int im = i0 == 0 ? N - 1 : i0 - 1, ip = i0 + 1 == N ? 0 : i0 + 1;
+    const int jm = j0 == 0 ? N - 1 : j0 - 1, jp = j0 + 1 == N ? 0 : j0 + 1;
+    const float edges = ((res(im, jm, 0) + res(ip, jm, 0)) + (res(im, jp, 0) + res(ip, jp, 0))) +
+                        ((res(im, j0, -1) + res(ip, j0, -1)) + (res(im, j0, 1) + res(ip, j0, 1))) +
+                        ((res(i0, jm, -1) + res(i0, jp, -1)) + (res(i0, jm, 1) + res(i0, jp, 1)));
+    R.plane(l + 1, 1, K)[J * Nc + I] = 4.f * (0.125f * res(i0, j0, 0) + 0.03125f * edges);
+  }
+}
+
+// Trilinear prolongation of level l+1's correction onto level l's black
+// points (the next red half-sweep overwrites the red ones).
+__device__ __forceinline__ void res_prolong(const Slabs& R, int l, int t0, int ts) {
+  const RLevel& f = R.lv[l];
+  const RLevel& cv = R.lv[l + 1];
+  const int own = f.z1 - f.z0;
+  if (own <= 0) return;
+  float* x = R.sm + f.off;
+  const int Nc = cv.N, hcount = own * f.NN / 2;
+  for (int h = t0; h < hcount; h += ts) {
+    int i, j, kl;
+    const int m = slab_colour_point(f, h, 1, i, j, kl);
+    const int k = f.z0 + kl;
+    const int i0 = i >> 1, i1 = (i & 1) ? (i0 + 1 == Nc ? 0 : i0 + 1) : i0;
+    const int j0 = j >> 1, j1 = (j & 1) ? (j0 + 1 == Nc ? 0 : j0 + 1) : j0;
+    const int k0 = k >> 1, k1 = (k & 1) ? (k0 + 1 == Nc ? 0 : k0 + 1) : k0;
+    const float* c0 = R.plane(l + 1, 0, k0);
+    const float* c1 = R.plane(l + 1, 0, k1);
+    x[m] += 0.125f * (((c0[j0 * Nc + i0] + c0[j0 * Nc + i1]) + (c0[j1 * Nc + i0] + c0[j1 * Nc + i1])) +
+                      ((c1[j0 * Nc + i0] + c1[j0 * Nc + i1]) + (c1[j1 * Nc + i0] + c1[j1 * Nc + i1])));
+  }
+}
+
+// Coarsest level (in the tail, part 0): the exact zero-mean solve by the
+// pseudo-inverse kernel. The block stages the coarse rhs and the kernel (at
+// most 7^3 values each) in shared memory; one warp per output point splits
+// the sum.
+__device__ __forceinline__ void res_coarsest(const Slabs& R, const float* s_cg, int tid, int stride) {
+  __shared__ float s_cb[343];
+  const int l = R.L - 1;
+  const RLevel& v = R.lv[l];
+  const int Nc = v.N, NNc = v.NN, nc3 = Nc * NNc;
+  for (int q = threadIdx.x; q < nc3; q += blockDim.x) {
+    const int qk = q / NNc;
+    s_cb[q] = R.plane(l, 1, qk)[q - qk * NNc];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int wid = tid >> 5, nwarps = stride >> 5;
+  for (int p = wid; p < nc3; p += nwarps) {
+    const int pk = p / NNc, pj = (p - pk * NNc) / Nc, pi = p - pk * NNc - pj * Nc;
+    float acc = 0.f;
+    for (int q = lane; q < nc3; q += 32) {
+      const int qk = q / NNc, qj = (q - qk * NNc) / Nc, qi = q - qk * NNc - qj * Nc;
+      acc += s_cg[wrapi(pi - qi, Nc) + Nc * (wrapi(pj - qj, Nc) + Nc * wrapi(pk - qk, Nc))] * s_cb[q];
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) R.plane(l, 0, pk)[pj * Nc + pi] = acc;
+  }
+}
+
+// S4 for one point m (double-float): phi_p and sigma_p written, sigma_p returned.
+__device__ __forceinline__ df s4_point(const MixedArgs& a, int m, const int (&q)[6], df c_sig) {
+  const long long qi = (long long)a.qfix[m];
+  a.qfix[m] = 0ull;
+  if (a.q_out) a.q_out[m] = (double)qi * kQInv;
+  df php = {0.f, 0.f}, Mphp = {0.f, 0.f};
+  if (a.zero_phi) {
+  } else if (a.static_guess) {
+    php = df_from(a.phi_k[m]);
+    Mphp = df_sub(dsum6(a.phi_k, q), df_mul_f(php, 6.f));
+  } else {
+    php = df_sub(df_twice(df_from(a.phi_k[m])), df_from(a.phi_km1[m]));
+    const df nk = dsum6(a.phi_k, q), nm = dsum6(a.phi_km1, q);
+    const df s6 = df_sub(df_twice(nk), nm);
+    Mphp = df_sub(s6, df_mul_f(php, 6.f));
+  }
+  a.phi_out[m] = df_to(php);
+  const df sg = df_add(df_mul(Mphp, c_sig), df_from_fix(qi));
+  a.sigma[m] = df_to(sg);
+  return sg;
+}
+
+// The solve (S4-S6) shared by every launch form. ``S`` is the sync domain;
+// ``dsm`` is the CTA's dynamic shared memory for the cluster-resident form,
+// or nullptr for the global form (a.scratch). The outer SHAKE iteration
+// runs on double-float y (double-buffered: y_next = y + e is formed inside
+// the next residual pass), the V-cycle on the FP32 slabs.
 template <class S>
-__device__ void mixed_body(const MixedArgs& a, S& sync) {
-  const int n = a.n, N0 = a.N;
-  const int tid = sync.rank() * blockDim.x + threadIdx.x;
-  const int stride = sync.size() * blockDim.x;
+__device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
+  __shared__ Slabs R;
+  const unsigned me = (unsigned)sync.rank(), C = (unsigned)sync.size();
+  const int tid = (int)me * blockDim.x + threadIdx.x;
+  const int stride = (int)C * blockDim.x;
+  // the coarsest level's pseudo-inverse kernel, staged once per solve
+  __shared__ float s_cg[343];
+  if (threadIdx.x == 0) {
+    if (dsm)
+      slabs_setup(R, a, dsm, me, C, true);
+    else
+      slabs_setup(R, a, a.scratch, 0, 1, false);
+  }
+  {
+    const int Nc = a.Nl[a.L - 1];
+    for (int q = threadIdx.x; q < Nc * Nc * Nc; q += blockDim.x) s_cg[q] = a.gkerf[q];
+  }
+  __syncthreads();
+  // the storage must hold the layout (uniform decision: every CTA computes
+  // the same sizes); a mismatch is an error, never an out-of-bounds access
+  unsigned dyn_bytes;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
+  if (dsm ? resident_bytes(a, (int)C) > (size_t)dyn_bytes : slab_floats(a, 1) > a.scratch_floats) {
+    if (tid == 0) a.rec->status = MAZE_ERR_INVALID;
+    sync.barrier();
+    return;
+  }
+  // this thread's first point and stride within its part
+  const int t0 = dsm ? (int)threadIdx.x : tid, ts = dsm ? (int)blockDim.x : stride;
   const df c_sig = {a.c_sig_h, a.c_sig_l};
   const df c_phi = {a.c_phi_h, a.c_phi_l};
   const bool mmax[2] = {true, true};
   const bool msum[4] = {false, false, false, false};
-
-  // ---- S4: phi_p = 2 phi^k - phi^{k-1}, sigma_p = (h/4pi) M phi_p + q
-  for (int m = tid; m < n; m += stride) {
-    int i, j, k;
-    split3(m, N0, a.lg[0], i, j, k);
-    int q[6];
-    nbr_idx<float>(i, j, k, N0, q);
-    const long long qi = (long long)a.qfix[m];
-    a.qfix[m] = 0ull;
-    if (a.q_out) a.q_out[m] = (double)qi * kQInv;
-    df php = {0.f, 0.f}, Mphp = {0.f, 0.f};
-    if (a.zero_phi) {
-    } else if (a.static_guess) {
-      php = df_from(a.phi_k[m]);
-      Mphp = df_sub(dsum6(a.phi_k, q), df_mul_f(php, 6.f));
-    } else {
-      php = df_sub(df_twice(df_from(a.phi_k[m])), df_from(a.phi_km1[m]));
-      const df nk = dsum6(a.phi_k, q), nm = dsum6(a.phi_km1, q);
-      const df s6 = df_sub(df_twice(nk), nm);
-      Mphp = df_sub(s6, df_mul_f(php, 6.f));
-    }
-    a.phi_out[m] = df_to(php);
-    a.sigma[m] = df_to(df_add(df_mul(Mphp, c_sig), df_from_fix(qi)));
-  }
-  if (!sync.barrier()) return;
-
+  const RLevel v0 = R.lv[0];
+  const int N0 = v0.N, NN0 = v0.NN, own0 = v0.z1 - v0.z0, cnt0 = own0 * NN0;
+  float* e0 = R.sm + v0.off;
+  float* r0 = e0 + v0.P * NN0;
+  float2* ycur = a.y;
+  float2* ynext = a.y2;
   int it = 0;
   double res = 0.0, ymax_all = 0.0;
-  while (true) {
-    // ---- outer residual r = sigma - M y (double-float), its max, r -> FP32
-    {
-      float rmax = 0.f, ymax = 0.f;
-      for (int m0 = tid; m0 < n; m0 += 2 * stride) {
-        float rf[2];
-        int mm[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int m = m0 + u * stride;
-          mm[u] = m < n ? m : -1;
-          rf[u] = 0.f;
-          if (m < n) {
-            int i, j, k;
-            split3(m, N0, a.lg[0], i, j, k);
-            int q[6];
-            nbr_idx<float>(i, j, k, N0, q);
-            const df ym = df_from(a.y[m]);
-            ymax = fmaxf(ymax, fabsf(ym.h));
-            const df My = df_sub(dsum6(a.y, q), df_mul_f(ym, 6.f));
-            const df r = df_sub(df_from(a.sigma[m]), My);
-            rf[u] = r.h + r.l;
-          }
+  // ---- S4 fused with the first outer residual r = sigma_p - M y
+  {
+    float rmax = 0.f, ymax = 0.f;
+    for (int ml = t0; ml < cnt0; ml += ts) {
+      const int kl = ml / NN0, rem = ml - kl * NN0, j = rem / N0, i = rem - j * N0;
+      const int m = (v0.z0 + kl) * NN0 + rem;
+      int q[6];
+      nbr_idx<float>(i, j, v0.z0 + kl, N0, q);
+      const df sg = s4_point(a, m, q, c_sig);
+      const df ym = df_from(ycur[m]);
+      ymax = fmaxf(ymax, fabsf(ym.h));
+      const df r = df_sub(sg, df_sub(dsum6(ycur, q), df_mul_f(ym, 6.f)));
+      const float rf = r.h + r.l;
+      r0[ml] = rf;
+      rmax = fmaxf(rmax, fabsf(rf));
+    }
+    const double vv[2] = {(double)rmax, (double)ymax};
+    double t[2];
+    if (!sync.reduce(vv, mmax, t)) return;
+    res = t[0];
+    ymax_all = t[1];
+  }
+  while (isfinite(res) && !(res < a.tol) && it < a.max_iter) {
+    // ---- FP32 V-cycle on M e = r from e = 0: the levels above the tail
+    // across the sync domain, the tail in one CTA
+    const int lt = R.tail;
+    for (int l = 0; l < lt; ++l) {
+      for (int s = 0; s < a.nu1; ++s)
+        for (int c = 0; c < 2; ++c) {
+          res_half_sweep(R, l, c, s == 0 && c == 0, t0, ts);
+          if (!sync.barrier()) return;
         }
-#pragma unroll
-        for (int u = 0; u < 2; ++u)
-          if (mm[u] >= 0) {
-            a.r0[mm[u]] = rf[u];
-            rmax = fmaxf(rmax, fabsf(rf[u]));
+      res_residual(R, l, t0, ts);
+      if (!sync.barrier()) return;
+      res_restrict(R, l, t0, ts);
+      if (!sync.barrier()) return;
+    }
+    if (sync.rank() == 0) {
+      const int u0 = threadIdx.x, us = blockDim.x;
+      for (int l = lt; l < a.L - 1; ++l) {
+        for (int s = 0; s < a.nu1; ++s)
+          for (int c = 0; c < 2; ++c) {
+            res_half_sweep(R, l, c, s == 0 && c == 0, u0, us);
+            __syncthreads();
+          }
+        res_residual(R, l, u0, us);
+        __syncthreads();
+        res_restrict(R, l, u0, us);
+        __syncthreads();
+      }
+      res_coarsest(R, s_cg, u0, us);
+      __syncthreads();
+      for (int l = a.L - 2; l >= lt; --l) {
+        res_prolong(R, l, u0, us);
+        __syncthreads();
+        for (int s = 0; s < a.nu2; ++s)
+          for (int c = 0; c < 2; ++c) {
+            res_half_sweep(R, l, c, false, u0, us);
+            __syncthreads();
           }
       }
-      const double v[2] = {(double)rmax, (double)ymax};
+    }
+    if (lt > 0 && !sync.barrier()) return;
+    for (int l = lt - 1; l >= 0; --l) {
+      res_prolong(R, l, t0, ts);
+      if (!sync.barrier()) return;
+      for (int s = 0; s < a.nu2; ++s)
+        for (int c = 0; c < 2; ++c) {
+          res_half_sweep(R, l, c, false, t0, ts);
+          if (!sync.barrier()) return;
+        }
+    }
+    if (lt == 0 && !sync.barrier()) return;
+    // ---- y_next = y + e and the next outer residual r = sigma_p - M y_next
+    {
+      const float* elo = R.plane(0, 0, (v0.z0 - 1 + N0) % N0);
+      const float* ehi = R.plane(0, 0, v0.z1 % N0);
+      float rmax = 0.f, ymax = 0.f;
+      for (int ml = t0; ml < cnt0; ml += ts) {
+        const int kl = ml / NN0, rem = ml - kl * NN0, j = rem / N0, i = rem - j * N0;
+        const int m = (v0.z0 + kl) * NN0 + rem;
+        int q[6];
+        nbr_idx<float>(i, j, v0.z0 + kl, N0, q);
+        const int row = kl * NN0 + j * N0;
+        const float en[6] = {e0[row + (i == 0 ? N0 - 1 : i - 1)], e0[row + (i == N0 - 1 ? 0 : i + 1)],
+                             e0[kl * NN0 + (j == 0 ? N0 - 1 : j - 1) * N0 + i],
+                             e0[kl * NN0 + (j == N0 - 1 ? 0 : j + 1) * N0 + i],
+                             kl > 0 ? e0[row - NN0 + i] : elo[j * N0 + i],
+                             kl < own0 - 1 ? e0[row + NN0 + i] : ehi[j * N0 + i]};
+        df yn6[6];
+#pragma unroll
+        for (int u = 0; u < 6; ++u) yn6[u] = df_add_f(df_from(ycur[q[u]]), en[u]);
+        const df sn = df_add(df_add(df_add(yn6[0], yn6[1]), df_add(yn6[2], yn6[3])), df_add(yn6[4], yn6[5]));
+        const df ym = df_add_f(df_from(ycur[m]), e0[ml]);
+        ynext[m] = df_to(ym);
+        ymax = fmaxf(ymax, fabsf(ym.h));
+        const df r = df_sub(df_from(a.sigma[m]), df_sub(sn, df_mul_f(ym, 6.f)));
+        const float rf = r.h + r.l;
+        r0[ml] = rf;
+        rmax = fmaxf(rmax, fabsf(rf));
+      }
+      ++it;
+      float2* t2 = ycur;
+      ycur = ynext;
+      ynext = t2;
+      const double vv[2] = {(double)rmax, (double)ymax};
       double t[2];
-      if (!sync.reduce(v, mmax, t)) return;
+      if (!sync.reduce(vv, mmax, t)) return;
       res = t[0];
       ymax_all = t[1];
     }
-    if (!isfinite(res) || res < a.tol || it >= a.max_iter) break;
-    // ---- FP32 V-cycle on M e = r from e = 0
-    for (int l = 0; l < a.L - 1; ++l) {
-      const int N = a.Nl[l], NN = N * N, hcount = N * NN / 2, lg = a.lg[l];
-      float* x = l == 0 ? a.e0 : a.lx + a.off[l];
-      const float* __restrict__ b = l == 0 ? a.r0 : a.lb + a.off[l];
-      for (int s = 0; s < a.nu1; ++s) {
-        for (int c = 0; c < 2; ++c) {
-          half_sweep(x, b, N, lg, c, s == 0 && c == 0, tid, stride);
-          if (!sync.barrier()) return;
-        }
-      }
-      float* __restrict__ rl = a.lr + a.off[l];
-      const float* __restrict__ xr = x;
-      for (int m = tid; m < N * NN; m += stride) {
-        int i, j, k;
-        split3(m, N, lg, i, j, k);
-        int q[6];
-        nbr_idx<float>(i, j, k, N, q);
-        rl[m] = b[m] - (fsum6(xr, q) - 6.f * xr[m]);
-      }
-      if (!sync.barrier()) return;
-      // coarse rhs = 4 * 27-point full weighting of the residual
-      const int Nc = a.Nl[l + 1], NNc = Nc * Nc;
-      float* bc = a.lb + a.off[l + 1];
-      for (int m = tid; m < Nc * NNc; m += stride) {
-        const int K = m / NNc, J = (m - K * NNc) / Nc, I = m - K * NNc - J * Nc;
-        float acc = 0.f;
-#pragma unroll
-        for (int dz = -1; dz <= 1; ++dz) {
-          const int z = wrapi(2 * K + dz, N);
-          const float wz = dz == 0 ? 0.5f : 0.25f;
-#pragma unroll
-          for (int dy = -1; dy <= 1; ++dy) {
-            const int yy = wrapi(2 * J + dy, N);
-            const float wzy = wz * (dy == 0 ? 0.5f : 0.25f);
-            const float* row = rl + (size_t)z * NN + (size_t)yy * N;
-            acc += wzy * (0.25f * row[wrapi(2 * I - 1, N)] + 0.5f * row[2 * I] + 0.25f * row[wrapi(2 * I + 1, N)]);
-          }
-        }
-        bc[m] = 4.f * acc;
-      }
-      if (!sync.barrier()) return;
-    }
-    {
-      // coarsest: exact zero-mean solve by the pseudo-inverse kernel. Every
-      // block stages the coarse rhs and the kernel (at most 7^3 values each)
-      // in shared memory; one warp per output point splits the sum.
-      __shared__ float s_cb[343], s_cg[343];
-      const int Nc = a.Nl[a.L - 1], NNc = Nc * Nc, nc3 = Nc * NNc;
-      const float* bc = a.lb + a.off[a.L - 1];
-      float* xc = a.lx + a.off[a.L - 1];
-      for (int q = threadIdx.x; q < nc3; q += blockDim.x) {
-        s_cb[q] = bc[q];
-        s_cg[q] = a.gkerf[q];
-      }
-      __syncthreads();
-      const int lane = threadIdx.x & 31;
-      const int wid = tid >> 5, nwarps = stride >> 5;
-      for (int p = wid; p < nc3; p += nwarps) {
-        const int pk = p / NNc, pj = (p - pk * NNc) / Nc, pi = p - pk * NNc - pj * Nc;
-        float acc = 0.f;
-        for (int q = lane; q < nc3; q += 32) {
-          const int qk = q / NNc, qj = (q - qk * NNc) / Nc, qi = q - qk * NNc - qj * Nc;
-          acc += s_cg[wrapi(pi - qi, Nc) + Nc * (wrapi(pj - qj, Nc) + Nc * wrapi(pk - qk, Nc))] * s_cb[q];
-        }
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) xc[p] = acc;
-      }
-      if (!sync.barrier()) return;
-    }
-    for (int l = a.L - 2; l >= 0; --l) {
-      const int N = a.Nl[l], NN = N * N, hcount = N * NN / 2, lg = a.lg[l];
-      const int Nc = a.Nl[l + 1], NNc = Nc * Nc;
-      float* x = l == 0 ? a.e0 : a.lx + a.off[l];
-      const float* __restrict__ b = l == 0 ? a.r0 : a.lb + a.off[l];
-      const float* __restrict__ xc = a.lx + a.off[l + 1];
-      for (int h = tid; h < hcount; h += stride) {
-        int i, j, k;
-        const int m = colour_point(h, N, lg, 1, i, j, k);
-        const int i0 = i >> 1, i1 = (i & 1) ? wrapi(i0 + 1, Nc) : i0;
-        const int j0 = j >> 1, j1 = (j & 1) ? wrapi(j0 + 1, Nc) : j0;
-        const int k0 = k >> 1, k1 = (k & 1) ? wrapi(k0 + 1, Nc) : k0;
-        const float* c0 = xc + (size_t)k0 * NNc;
-        const float* c1 = xc + (size_t)k1 * NNc;
-        x[m] += 0.125f * (((c0[j0 * Nc + i0] + c0[j0 * Nc + i1]) + (c0[j1 * Nc + i0] + c0[j1 * Nc + i1])) +
-                          ((c1[j0 * Nc + i0] + c1[j0 * Nc + i1]) + (c1[j1 * Nc + i0] + c1[j1 * Nc + i1])));
-      }
-      if (!sync.barrier()) return;
-      for (int s = 0; s < a.nu2; ++s) {
-        for (int c = 0; c < 2; ++c) {
-          half_sweep(x, b, N, lg, c, false, tid, stride);
-          if (!sync.barrier()) return;
-        }
-      }
-    }
-    // ---- y += e (double-float)
-    for (int m = tid; m < n; m += stride) a.y[m] = df_to(df_add_f(df_from(a.y[m]), a.e0[m]));
-    ++it;
-    if (!sync.barrier()) return;
   }
-  // ---- S6: mean of y, exact and independent of how the points are split
-  // over blocks: every point's hi and lo parts are rounded to one fixed-point
-  // grid set by max|y| over the box (2^-41 of it), the integers are summed
-  // modulo 2^64 (the true sum fits), and the sum crosses the domain as four
-  // 16-bit chunk sums, small integers that the reduction adds exactly.
+  // ---- S6: mean of y, exact and independent of how the points are split:
+  // every point's hi and lo parts are rounded to one fixed-point grid set by
+  // max|y| over the box (2^-41 of it), the integers are summed modulo 2^64
+  // (the true sum fits), and the sum crosses the domain as four 16-bit chunk
+  // sums, small integers that the reduction adds exactly. Then the
+  // correction phi = phi_p - (4pi/h)(y - mean y) and y -> a.y.
   {
     const int E = dbl_exp(ymax_all) + 11;
     unsigned long long u = 0;
     if (ymax_all > 0.0)
-      for (int m = tid; m < n; m += stride) {
-        const float2 yv = a.y[m];
+      for (int ml = t0; ml < cnt0; ml += ts) {
+        const float2 yv = ycur[v0.z0 * NN0 + ml];
         u += (unsigned long long)(dbl_to_fix((double)yv.x, E) + dbl_to_fix((double)yv.y, E));
       }
-    const double v[4] = {(double)(u & 0xffffu), (double)((u >> 16) & 0xffffu), (double)((u >> 32) & 0xffffu),
-                         (double)(u >> 48)};
+    const double vv[4] = {(double)(u & 0xffffu), (double)((u >> 16) & 0xffffu), (double)((u >> 32) & 0xffffu),
+                          (double)(u >> 48)};
     double t[4];
-    if (!sync.reduce(v, msum, t)) return;
+    if (!sync.reduce(vv, msum, t)) return;
     const unsigned long long tot = (unsigned long long)(long long)t[0] + ((unsigned long long)(long long)t[1] << 16) +
                                    ((unsigned long long)(long long)t[2] << 32) +
                                    ((unsigned long long)(long long)t[3] << 48);
     const double ybar = ymax_all > 0.0 ? fix_to_dbl((long long)tot, E) * a.inv_n : 0.0;
     const float ybh = (float)ybar;
     const df yb = {ybh, (float)(ybar - (double)ybh)};
-    for (int m = tid; m < n; m += stride) {
-      const df yv = df_sub(df_from(a.y[m]), yb);
+    for (int ml = t0; ml < cnt0; ml += ts) {
+      const int m = v0.z0 * NN0 + ml;
+      const df yv = df_sub(df_from(ycur[m]), yb);
       a.y[m] = df_to(yv);
       a.phi_out[m] = df_to(df_sub(df_from(a.phi_out[m]), df_mul(yv, c_phi)));
     }
@@ -507,7 +714,8 @@ __device__ void mixed_body(const MixedArgs& a, S& sync) {
     if (!isfinite(res)) r->status = MAZE_ERR_NONFINITE;
     else if (!(res < a.tol)) r->status = MAZE_ERR_NOT_CONVERGED;
   }
-  // no block leaves while another may still read its shared memory (DSMEM)
+  // no block leaves (or reuses its shared memory) while another may still
+  // read it
   sync.barrier();
 }
 
