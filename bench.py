@@ -45,6 +45,7 @@ from paper_2505_20418_gb300 import synth  # noqa: E402
 METRIC = "MaZe steps/s, solve GB/s vs HBM peak, p50/p99 step latency at stated force error"
 KERNELS_PER_STEP_CELLS = 7    # move, spread, 3 cell-list kernels, solve, forces
 KERNELS_PER_STEP_NOCELLS = 4
+KERNELS_PER_STEP_FUSED = 2     # mixed precision up to 64^3: S1-S6 in one cluster launch, then the forces
 
 
 def peaks():
@@ -226,7 +227,7 @@ def config_dict(w, args):
 def solve_kernel_name(args, w):
     """The solve kernel a step launches for this precision, solver and grid."""
     if args.precision == "mixed":
-        return "k_mixed_cluster" if w.N <= 64 else "k_mixed_grid"
+        return "k_cluster_step" if w.N <= 64 else "k_mixed_grid"
     return "k_mg_solve" if args.solver == "mg" else "k_cg_solve"
 
 
@@ -381,7 +382,10 @@ def main():
         achieved = bytes_launch / mean_solve_s / 1e9
         peak, peak_kind = peaks()
         cpu = None if args.no_cpu else run_cpu_baseline(w, args.solver)
-        kps = KERNELS_PER_STEP_CELLS if int(np.floor(w.L / w.rc)) >= 3 else KERNELS_PER_STEP_NOCELLS
+        if args.precision == "mixed" and w.N <= 64:
+            kps = KERNELS_PER_STEP_FUSED
+        else:
+            kps = KERNELS_PER_STEP_CELLS if int(np.floor(w.L / w.rc)) >= 3 else KERNELS_PER_STEP_NOCELLS
         line = {
             "metric": METRIC, "value": weak_scaling_value(world, args.steps, total_s), "unit": "steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

@@ -676,19 +676,23 @@ __device__ __forceinline__ void forces_ion_warp(const ForceArgs& a, int i, int l
     }
   };
   if (a.nc >= 3) {
-    const int nc = a.nc;
+    const int nc = a.nc, R = a.reach, S = 2 * R + 1, NB = S * S * S;
     const int c = a.cell_of[i];
     const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
-    int rlo = 0, rhi = 0;
-    if (lane < 27) {
-      const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
-      const int cc = (cx + dx + nc) % nc + nc * ((cy + dy + nc) % nc + nc * ((cz + dz + nc) % nc));
-      rlo = a.cell_start[cc];
-      rhi = a.cell_start[cc + 1];
-    }
-    for (int tt = 0; tt < 27; ++tt) {
-      const int lo = __shfl_sync(0xffffffffu, rlo, tt), hi = __shfl_sync(0xffffffffu, rhi, tt);
-      scan(lo, hi, a.cell_ions, a.pos_sorted);
+    for (int base = 0; base < NB; base += 32) {
+      int rlo = 0, rhi = 0;
+      const int t = base + lane;
+      if (t < NB) {
+        const int dx = t % S - R, dy = (t / S) % S - R, dz = t / (S * S) - R;
+        const int cc = (cx + dx + nc) % nc + nc * ((cy + dy + nc) % nc + nc * ((cz + dz + nc) % nc));
+        rlo = a.cell_start[cc];
+        rhi = a.cell_start[cc + 1];
+      }
+      const int cnt = min(32, NB - base);
+      for (int tt = 0; tt < cnt; ++tt) {
+        const int lo = __shfl_sync(0xffffffffu, rlo, tt), hi = __shfl_sync(0xffffffffu, rhi, tt);
+        scan(lo, hi, a.cell_ions, a.pos_sorted);
+      }
     }
   } else {
     scan(0, n, nullptr, a.pos32);
@@ -707,21 +711,22 @@ __device__ __forceinline__ void forces_ion_warp(const ForceArgs& a, int i, int l
 }
 
 // S7 + S8 for the ions of slice s (of ``split``) of cell c, one block of kW
-// warps: the candidates of the 27 neighbour cells are staged in shared memory
-// in chunks; each warp takes ions of the slice, queues filter survivors and
+// warps: the candidates of the (2 reach + 1)^3 neighbour cells are staged in
+// shared memory in chunks; each warp takes ions of the slice, queues filter survivors and
 // evaluates them 32 at a time. Pair sums per ion accumulate in shared memory
 // in chunk order, so the result does not depend on kW or the slicing. FP64
 // mode stages FP64 positions; mixed precision stages the cell-relative hi/lo
 // floats with the neighbour cell's offset folded in, so displacements are
 // exact FP32 sums. The slice's ions are finished one per thread into acc.
-constexpr int kPairChunk = 896;
+constexpr int kPairChunk = 864;
 constexpr int kCellGroup = 64;
+constexpr int kMaxNbr = 125;   // (2 reach + 1)^3 for reach <= 2
 template <int kW>
 struct CellSmem {
   float4 p[kPairChunk];                          // FP32 position (filter) / hi part
   __align__(16) double xyz[3][kPairChunk];       // FP64 positions; mixed: lo parts in rows 0-1
   int j[kPairChunk];
-  int lo[27], cum[28];
+  int lo[kMaxNbr], cum[kMaxNbr + 1];
   double f[kCellGroup][8];                       // pair sums, then gather sums
   int queue[kW][64];
 };
@@ -731,12 +736,11 @@ __device__ __forceinline__ void forces_cell_slice(const ForceArgs& a, int c, int
                                                   double (&acc)[7]) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int n = a.n, nc = a.nc;
+  const int n = a.n, nc = a.nc, R = a.reach, S = 2 * R + 1, NB = S * S * S;
   __syncthreads();   // the previous slice's readers of sm are done
   const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
-  if (threadIdx.x < 27) {
-    const int t = threadIdx.x;
-    const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
+  for (int t = threadIdx.x; t < NB; t += blockDim.x) {
+    const int dx = t % S - R, dy = (t / S) % S - R, dz = t / (S * S) - R;
     const int cc = (cx + dx + nc) % nc + nc * ((cy + dy + nc) % nc + nc * ((cz + dz + nc) % nc));
     sm.lo[t] = a.cell_start[cc];
     sm.cum[t + 1] = a.cell_start[cc + 1] - a.cell_start[cc];
@@ -744,10 +748,10 @@ __device__ __forceinline__ void forces_cell_slice(const ForceArgs& a, int c, int
   __syncthreads();
   if (threadIdx.x == 0) {
     sm.cum[0] = 0;
-    for (int t = 0; t < 27; ++t) sm.cum[t + 1] += sm.cum[t];
+    for (int t = 0; t < NB; ++t) sm.cum[t + 1] += sm.cum[t];
   }
   __syncthreads();
-  const int total = sm.cum[27];
+  const int total = sm.cum[NB];
   const int c0 = a.cell_start[c], cn = a.cell_start[c + 1] - c0;
   const int per = (cn + split - 1) / split;
   const int clo = c0 + min(cn, s * per), chi = c0 + min(cn, (s + 1) * per);
@@ -760,12 +764,14 @@ __device__ __forceinline__ void forces_cell_slice(const ForceArgs& a, int c, int
       __syncthreads();
       for (int e = threadIdx.x; e < len; e += blockDim.x) {
         const int tt = ch0 + e;
+        // neighbour cell k of candidate tt: the last k with cum[k] <= tt
         int k = 0;
-        while (k < 26 && sm.cum[k + 1] <= tt) ++k;
+        for (int step = 64; step > 0; step >>= 1)
+          if (k + step < NB && sm.cum[k + step] <= tt) k += step;
         const int slot = sm.lo[k] + (tt - sm.cum[k]);
         if (a.mixed) {
           // neighbour offset (dx, dy, dz) * cell_len folded into hi/lo
-          const float ox = (float)(k % 3 - 1), oy = (float)((k / 3) % 3 - 1), oz = (float)(k / 9 - 1);
+          const float ox = (float)(k % S - R), oy = (float)((k / S) % S - R), oz = (float)(k / (S * S) - R);
           const float4 h = a.rel_hi_sorted[slot], l = a.rel_lo_sorted[slot];
           float4 hh, ll;
           // TwoSum of each coordinate with the offset's hi part

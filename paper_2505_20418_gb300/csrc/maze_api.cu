@@ -219,6 +219,7 @@ ForceArgs force_args(maze_ctx* c, const double* phi, int do_kick, int count_step
   a.wdbuf32 = c->wdbuf32;
   a.gradw = c->cfg.force_estimator == MAZE_FORCE_GRADW ? 1 : 0;
   a.nc = c->nc;
+  a.reach = c->reach;
   a.cell_start = c->cell_start;
   a.cell_ions = c->cell_ions;
   a.pos_sorted = c->pos_sorted;
@@ -374,6 +375,20 @@ maze_status enqueue_cells(maze_ctx* c) {
 // One MaZe step for the current rotation (does not rotate). With timing on,
 // events bracket the four phases.
 maze_status enqueue_step(maze_ctx* c, int timed) {
+  if (c->mixed && c->fused_step) {
+    // mixed precision up to 64^3: S1-S6 in one cluster launch, then the
+    // forces; the move/spread and cell phases are timed as part of the solve
+    if (timed) {
+      CK(cudaEventRecordWithFlags(c->ev[0], c->stream, cudaEventRecordExternal));
+      CK(cudaEventRecordWithFlags(c->ev[1], c->stream, cudaEventRecordExternal));
+      CK(cudaEventRecordWithFlags(c->ev[2], c->stream, cudaEventRecordExternal));
+    }
+    CK(launch_cluster_step(ion_args(c, 1, 1), cell_args(c), mixed_args(c, 0, nullptr), c->mx_cluster, c->stream));
+    if (timed) CK(cudaEventRecordWithFlags(c->ev[3], c->stream, cudaEventRecordExternal));
+    CK(launch_forces(force_args(c, c->phi[(c->ik + 2) % 3], 1, 1), c->fblocks, c->stream));
+    if (timed) CK(cudaEventRecordWithFlags(c->ev[4], c->stream, cudaEventRecordExternal));
+    return MAZE_OK;
+  }
   if (timed) CK(cudaEventRecordWithFlags(c->ev[0], c->stream, cudaEventRecordExternal));
   CK(launch_ion_update(ion_args(c, 1, 1), c->stream));
   if (timed) CK(cudaEventRecordWithFlags(c->ev[1], c->stream, cudaEventRecordExternal));
@@ -520,6 +535,11 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
   }
   const int n = c->n;
   const size_t ng = c->ng;
+  // cell list: cells of at least r_cut with a 3^3 neighbourhood (the force
+  // kernels also take cells of r_cut / 2 with a 5^3 neighbourhood, reach 2,
+  // but with ~3 ions per cell the per-cell staging costs more than the fewer
+  // candidates save: measured 5x slower on the 512000-ion box)
+  c->reach = 1;
   c->nc = (int)floor(c->L / cfg->r_cut);
   if (c->nc < 3) c->nc = 0;
   c->ncell = c->nc * c->nc * c->nc;
@@ -636,7 +656,10 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
     // one cluster for boxes up to 64^3 (cluster barriers), a cooperative
     // grid above
     if (c->N <= 64) {
-      c->mx_cluster = mixed_cluster_size();
+      // the step's cluster launch and the step-0 solve use the same size
+      const int cs = cluster_step_size();
+      c->mx_cluster = cs > 0 ? std::min(cs, mixed_cluster_size()) : mixed_cluster_size();
+      c->fused_step = cs > 0 && cs >= c->mx_cluster;
       m.resident = resident_bytes_host(m, c->mx_cluster) <= (size_t)kResidentSmem ? 1 : 0;
     } else {
       c->mx_blocks = mixed_grid_blocks((int)ng);

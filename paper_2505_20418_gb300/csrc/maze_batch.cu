@@ -100,7 +100,7 @@ struct __align__(16) BoxDesc {
   int split;   // (cell, slice) work items per cell in the force phase
 };
 
-constexpr int kBatchThreads = 512;
+constexpr int kBatchThreads = 1024;
 constexpr int kBatchWarps = kBatchThreads / 32;
 // dynamic shared memory of the step kernel: the force staging, the sort's
 // buffers and (when a box fits) the cluster-resident V-cycle share it
@@ -223,6 +223,91 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_step(BatchArgs b) {
   }
   // no CTA leaves while another may still read its shared memory
   sync.barrier();
+}
+
+// One single-box step's S1-S6 in one cluster launch (mixed precision, boxes up
+// to 64^3): move, spread and cell list with cluster barriers, then the solve.
+// The forces (S7-S9) follow as their own wide launch.
+constexpr size_t kStepSortBytes = (size_t)(kMixedClusterThreads / 32) * kSortCap * sizeof(int);
+__global__ void __launch_bounds__(kMixedClusterThreads) k_cluster_step(IonArgs ia, CellArgs ca, MixedArgs ma) {
+  // dynamic shared memory: the cell sort's buffers, then (after a barrier)
+  // the resident V-cycle
+  extern __shared__ __align__(16) float dsm[];
+  ClusterSync sync;
+  const unsigned rank = (unsigned)sync.rank();
+  const int C = sync.size();
+  const int tid = (int)rank * blockDim.x + threadIdx.x, stride = C * blockDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gwarp = tid >> 5, nwarps = stride >> 5;
+  // the step decides once whether it runs (an earlier step of the call failed);
+  // every CTA reads the same value: nothing writes it during this launch
+  const bool skip = __ldcg(&ia.rec->status) != MAZE_OK;
+  if (rank == 0 && threadIdx.x == 0) *ia.gate = skip ? 1 : 0;
+  if (skip) return;
+  const int n = ia.n, nc = ia.nc;
+  for (int i = tid; i < n; i += stride) move_ion(ia, i);
+  if (ma.y_reset)
+    for (int m = tid; m < ma.n; m += stride) ma.y[m] = make_float2(0.f, 0.f);
+  sync.barrier();
+  if (nc >= 3 && rank == 0) cell_scan_block(ca);
+  for (int i = gwarp; i < n; i += nwarps) spread_ion(ia, i, lane);
+  sync.barrier();
+  if (nc >= 3) {
+    for (int i = tid; i < n; i += stride) cell_fill_ion(ca, i);
+    sync.barrier();
+    int* ids = reinterpret_cast<int*>(dsm) + warp * kSortCap;
+    for (int c = gwarp; c < ca.ncell; c += nwarps) cell_sort_one(ca, c, lane, ids);
+  }
+  __syncthreads();
+  mixed_body(ma, sync, ma.resident ? dsm : nullptr);
+}
+
+// Largest cluster (16, else 8) of the fused step kernel the device can
+// co-schedule with the shared memory the resident solve may take; 0 if none.
+// Sets the kernel's attributes (outside any stream capture: called at create).
+int cluster_step_size() {
+  static int cached = -1;
+  if (cached >= 0) return cached;
+  cudaFuncSetAttribute(k_cluster_step, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(k_cluster_step, cudaFuncAttributeMaxDynamicSharedMemorySize, kResidentSmem);
+  cached = 0;
+  for (int cta : {16, 8}) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cta);
+    cfg.blockDim = dim3(kMixedClusterThreads);
+    cfg.dynamicSmemBytes = kResidentSmem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cta;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_cluster_step, &cfg) == cudaSuccess && n >= 1) {
+      cached = cta;
+      break;
+    }
+  }
+  cudaGetLastError();
+  return cached;
+}
+
+cudaError_t launch_cluster_step(const IonArgs& ia, const CellArgs& ca, const MixedArgs& ma, int cluster,
+                                cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(kMixedClusterThreads);
+  cfg.gridDim = dim3(cluster);
+  cfg.dynamicSmemBytes = std::max(ma.resident ? resident_bytes(ma, cluster) : (size_t)0, kStepSortBytes);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_cluster_step, ia, ca, ma);
 }
 
 __global__ void k_batch_clear(const BoxDesc* desc, const int* order, const int* count) {

@@ -75,10 +75,11 @@ struct maze_ctx {
   bool mixed = false;
   maze::MixedArgs mx = {};
   int mx_cluster = 0, mx_blocks = 0;
+  bool fused_step = false;   // S1-S6 in one cluster launch (k_cluster_step)
   float *mx_scratch = nullptr, *mx_g = nullptr;
   int sblocks = 0;
   // cells
-  int nc = 0, ncell = 0, cell_split = 1;
+  int nc = 0, ncell = 0, cell_split = 1, reach = 1;
   int *cell_of = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cursor = nullptr, *cell_ions = nullptr;
   float4* pos_sorted = nullptr;
   float4 *rel_hi = nullptr, *rel_lo = nullptr, *rel_hi_s = nullptr, *rel_lo_s = nullptr;

@@ -119,6 +119,7 @@ struct ForceArgs {
   float L_h, L_l;                // L as hi + lo floats
   float Af[3], sf[3], Cf[3], Df[3], Vcf[3], Bf, rc2f;
   int nc;                // cells per edge; < 3 means all pairs
+  int reach;             // neighbour cells within +-reach per axis (cells >= r_cut / reach)
   const int* cell_start;
   const int* cell_ions;
   const float4* pos_sorted;  // [n] FP32 positions in cell-slot order
@@ -184,7 +185,7 @@ struct MgArgs {
 
 // Mixed-precision solve (double-float outer iteration, FP32 V-cycle).
 constexpr int kMixedClusterThreads = 512;   // one cluster per box
-constexpr int kMixedGridThreads = 512;      // cooperative grid (large boxes)
+constexpr int kMixedGridThreads = 1024;     // cooperative grid (large boxes)
 // Dynamic shared memory a CTA may give the cluster-resident V-cycle.
 constexpr int kResidentSmem = 200 * 1024;
 struct MixedArgs {
@@ -232,6 +233,10 @@ cudaError_t launch_mg_solve(const SolveArgs& a, const MgArgs& g, int blocks, cud
 int mg_blocks(int n_points);
 cudaError_t launch_mixed_solve(const MixedArgs& a, int cluster, int blocks, cudaStream_t s);
 int mixed_cluster_size();
+int cluster_step_size();
+// S1-S6 of one mixed-precision step of a box up to 64^3 in one cluster launch.
+cudaError_t launch_cluster_step(const IonArgs& ia, const CellArgs& ca, const MixedArgs& ma, int cluster,
+                                cudaStream_t s);
 // Shared-memory bytes per CTA of the cluster-resident V-cycle for C CTAs.
 size_t resident_bytes_host(const MixedArgs& a, int C);
 int mixed_grid_blocks(int n_points);
