@@ -238,7 +238,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="nacl1000",
-                    choices=["nacl64", "nacl1000", "nacl512000", "batch128", "serve", "study"])
+                    choices=["nacl64", "nacl1000", "nacl64000", "nacl512000", "batch128", "serve", "study"])
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--boxes", type=int, default=128, help="batch128: number of replica boxes")
     ap.add_argument("--cluster-ctas", type=int, default=0, help="batch128: CTAs per box (0: autotune)")
