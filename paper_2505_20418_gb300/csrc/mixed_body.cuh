@@ -239,6 +239,7 @@ struct RLevel {
   int N, NN, P, lg;
   int z0, z1;        // planes of this part
   unsigned off;      // float offset of x in a part; b at off + P NN, r at off + 2 P NN
+  unsigned Pinv;     // ceil(2^32 / P) for P > 1: z / P = umulhi(z, Pinv) for z < 2^16
 };
 
 struct Slabs {
@@ -248,20 +249,22 @@ struct Slabs {
   int tail;          // first level held whole by part 0 (the tail of the V-cycle)
   bool dsmem;
   RLevel lv[kMaxLevels];
-  // pointer to plane z (0 <= z < N_l) of array arr (0 x, 1 b) of level l
-  __device__ __forceinline__ float* plane(int l, int arr, int z) const {
-    const RLevel& v = lv[l];
-    const unsigned q = (unsigned)(z / v.P);
+  // pointer to plane z (0 <= z < N_l) of array arr (0 x, 1 b) of level v (a
+  // register copy of lv[l]); one part (the global form) needs no lookup
+  __device__ __forceinline__ float* plane(const RLevel& v, int arr, int z) const {
+    if (Q == 1) return sm + v.off + (unsigned)(arr * v.P * v.NN) + (unsigned)(z * v.NN);
+    const unsigned q = v.P == 1 ? (unsigned)z : __umulhi((unsigned)z, v.Pinv);
     float* p = sm + v.off + (unsigned)(arr * v.P * v.NN) + (unsigned)((z - (int)q * v.P) * v.NN);
     if (q == me) return p;
     float* r;
     asm volatile("mapa.u64 %0, %1, %2;" : "=l"(r) : "l"(p), "r"(q));
     return r;
   }
-  // pointer to the red-point residuals of plane z of level l (N_l^2 / 2 values)
-  __device__ __forceinline__ float* rplane(int l, int z) const {
-    const RLevel& v = lv[l];
-    const unsigned q = (unsigned)(z / v.P);
+  __device__ __forceinline__ float* plane(int l, int arr, int z) const { return plane(lv[l], arr, z); }
+  // pointer to the red-point residuals of plane z of level v (N_l^2 / 2 values)
+  __device__ __forceinline__ float* rplane(const RLevel& v, int z) const {
+    if (Q == 1) return sm + v.off + (unsigned)(2 * v.P * v.NN) + (unsigned)(z * (v.NN / 2));
+    const unsigned q = v.P == 1 ? (unsigned)z : __umulhi((unsigned)z, v.Pinv);
     float* p = sm + v.off + (unsigned)(2 * v.P * v.NN) + (unsigned)((z - (int)q * v.P) * (v.NN / 2));
     if (q == me) return p;
     float* r;
@@ -318,6 +321,8 @@ __device__ __forceinline__ void slabs_setup(Slabs& R, const MixedArgs& a, float*
     v.z0 = min(v.N, (int)me * v.P);
     v.z1 = min(v.N, ((int)me + 1) * v.P);
     v.off = off;
+    // (P = 1 would need 2^32, which does not fit: owner() treats it apart)
+    v.Pinv = v.P > 1 ? (unsigned)((0x100000000ull + (unsigned long long)v.P - 1) / (unsigned long long)v.P) : 0u;
     off += 2u * (unsigned)(v.P * v.NN) + (l < a.L - 1 ? (unsigned)(v.P * (v.NN / 2)) : 0u);
   }
 }
@@ -347,15 +352,15 @@ __device__ __forceinline__ int slab_colour_point(const RLevel& v, int h, int c, 
 // -b/6). A thread issues the loads of two points before either store (the
 // loads read the other colour, the stores write this one).
 __device__ __forceinline__ void res_half_sweep(const Slabs& R, int l, int c, bool from_zero, int t0, int ts) {
-  const RLevel& v = R.lv[l];
+  const RLevel v = R.lv[l];
   const int own = v.z1 - v.z0;
   if (own <= 0) return;
   float* x = R.sm + v.off;
   const float* b = x + v.P * v.NN;
   const int N = v.N, NN = v.NN;
   const int hcount = own * NN / 2;
-  const float* xlo = from_zero ? nullptr : R.plane(l, 0, (v.z0 - 1 + N) % N);
-  const float* xhi = from_zero ? nullptr : R.plane(l, 0, v.z1 % N);
+  const float* xlo = from_zero ? nullptr : R.plane(v, 0, (v.z0 - 1 + N) % N);
+  const float* xhi = from_zero ? nullptr : R.plane(v, 0, v.z1 % N);
   for (int h0 = t0; h0 < hcount; h0 += 2 * ts) {
     int mm[2];
     float val[2];
@@ -390,7 +395,7 @@ __device__ __forceinline__ void res_half_sweep(const Slabs& R, int l, int c, boo
 // Residual r = b - M x of level l at the part's red points (after the black
 // half-sweep the residual at the black points is zero).
 __device__ __forceinline__ void res_residual(const Slabs& R, int l, int t0, int ts) {
-  const RLevel& v = R.lv[l];
+  const RLevel v = R.lv[l];
   const int own = v.z1 - v.z0;
   if (own <= 0) return;
   const float* x = R.sm + v.off;
@@ -398,8 +403,8 @@ __device__ __forceinline__ void res_residual(const Slabs& R, int l, int t0, int 
   float* r = R.sm + v.off + 2 * v.P * v.NN;
   const int N = v.N, NN = v.NN;
   const int hcount = own * NN / 2;
-  const float* xlo = R.plane(l, 0, (v.z0 - 1 + N) % N);
-  const float* xhi = R.plane(l, 0, v.z1 % N);
+  const float* xlo = R.plane(v, 0, (v.z0 - 1 + N) % N);
+  const float* xhi = R.plane(v, 0, v.z1 % N);
   for (int h = t0; h < hcount; h += ts) {
     int i, j, kl;
     const int m = slab_colour_point(v, h, 0, i, j, kl);
@@ -419,8 +424,8 @@ __device__ __forceinline__ void res_residual(const Slabs& R, int l, int t0, int 
 // plane 2K and stored into the part that owns K (another CTA's shared
 // memory when they differ).
 __device__ __forceinline__ void res_restrict(const Slabs& R, int l, int t0, int ts) {
-  const RLevel& f = R.lv[l];
-  const RLevel& cv = R.lv[l + 1];
+  const RLevel f = R.lv[l];
+  const RLevel cv = R.lv[l + 1];
   const int K0 = (f.z0 + 1) / 2, own = (f.z1 + 1) / 2 - K0;
   if (own <= 0) return;
   const int N = f.N, H = N / 2, Nc = cv.N, NNc = cv.NN;
@@ -430,7 +435,7 @@ __device__ __forceinline__ void res_restrict(const Slabs& R, int l, int t0, int 
     const int K = K0 + kl;
     const float* rp[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) rp[d] = R.rplane(l, (2 * K - 1 + d + N) % N);
+    for (int d = 0; d < 3; ++d) rp[d] = R.rplane(f, (2 * K - 1 + d + N) % N);
     // red-point residual at fine (i, j) of plane 2K + dz
     auto res = [&](int i, int j, int dz) -> float { return rp[dz + 1][j * H + (i >> 1)]; };
     const int i0 = 2 * I, j0 = 2 * J;
@@ -439,15 +444,15 @@ __device__ __forceinline__ void res_restrict(const Slabs& R, int l, int t0, int 
     const float edges = ((res(im, jm, 0) + res(ip, jm, 0)) + (res(im, jp, 0) + res(ip, jp, 0))) +
                         ((res(im, j0, -1) + res(ip, j0, -1)) + (res(im, j0, 1) + res(ip, j0, 1))) +
                         ((res(i0, jm, -1) + res(i0, jp, -1)) + (res(i0, jm, 1) + res(i0, jp, 1)));
-    R.plane(l + 1, 1, K)[J * Nc + I] = 4.f * (0.125f * res(i0, j0, 0) + 0.03125f * edges);
+    R.plane(cv, 1, K)[J * Nc + I] = 4.f * (0.125f * res(i0, j0, 0) + 0.03125f * edges);
   }
 }
 
 // Trilinear prolongation of level l+1's correction onto level l's black
 // points (the next red half-sweep overwrites the red ones).
 __device__ __forceinline__ void res_prolong(const Slabs& R, int l, int t0, int ts) {
-  const RLevel& f = R.lv[l];
-  const RLevel& cv = R.lv[l + 1];
+  const RLevel f = R.lv[l];
+  const RLevel cv = R.lv[l + 1];
   const int own = f.z1 - f.z0;
   if (own <= 0) return;
   float* x = R.sm + f.off;
@@ -459,8 +464,8 @@ __device__ __forceinline__ void res_prolong(const Slabs& R, int l, int t0, int t
     const int i0 = i >> 1, i1 = (i & 1) ? (i0 + 1 == Nc ? 0 : i0 + 1) : i0;
     const int j0 = j >> 1, j1 = (j & 1) ? (j0 + 1 == Nc ? 0 : j0 + 1) : j0;
     const int k0 = k >> 1, k1 = (k & 1) ? (k0 + 1 == Nc ? 0 : k0 + 1) : k0;
-    const float* c0 = R.plane(l + 1, 0, k0);
-    const float* c1 = R.plane(l + 1, 0, k1);
+    const float* c0 = R.plane(cv, 0, k0);
+    const float* c1 = R.plane(cv, 0, k1);
     x[m] += 0.125f * (((c0[j0 * Nc + i0] + c0[j0 * Nc + i1]) + (c0[j1 * Nc + i0] + c0[j1 * Nc + i1])) +
                       ((c1[j0 * Nc + i0] + c1[j0 * Nc + i1]) + (c1[j1 * Nc + i0] + c1[j1 * Nc + i1])));
   }
