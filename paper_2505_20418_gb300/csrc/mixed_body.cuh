@@ -240,7 +240,15 @@ struct RLevel {
   int z0, z1;        // planes of this part
   unsigned off;      // float offset of x in a part; b at off + P NN, r at off + 2 P NN
   unsigned Pinv;     // ceil(2^32 / P) for P > 1: z / P = umulhi(z, Pinv) for z < 2^16
+  unsigned mH, mN, mNN;  // ceil(2^32 / d) for d = N/2, N, N^2 when N <= 64 (else 0: divide)
 };
+
+// x / d by a multiply-high with m = ceil(2^32 / d): exact while x d < 2^32
+// (every index of a grid of at most 64^3 points against d <= 4096); m = 0
+// falls back to the division.
+__device__ __forceinline__ int fdiv(int x, int d, unsigned m) {
+  return m ? (int)__umulhi((unsigned)x, m) : x / d;
+}
 
 struct Slabs {
   float* sm;         // this part's storage
@@ -323,6 +331,13 @@ __device__ __forceinline__ void slabs_setup(Slabs& R, const MixedArgs& a, float*
     v.off = off;
     // (P = 1 would need 2^32, which does not fit: owner() treats it apart)
     v.Pinv = v.P > 1 ? (unsigned)((0x100000000ull + (unsigned long long)v.P - 1) / (unsigned long long)v.P) : 0u;
+    auto magic = [&](int d) -> unsigned {
+      return (v.N <= 64 && d > 1) ? (unsigned)((0x100000000ull + (unsigned long long)d - 1) / (unsigned long long)d)
+                                  : 0u;
+    };
+    v.mH = magic(v.N / 2);
+    v.mN = magic(v.N);
+    v.mNN = magic(v.NN);
     off += 2u * (unsigned)(v.P * v.NN) + (l < a.L - 1 ? (unsigned)(v.P * (v.NN / 2)) : 0u);
   }
 }
@@ -338,9 +353,9 @@ __device__ __forceinline__ int slab_colour_point(const RLevel& v, int h, int c, 
     kl = row >> v.lg;
     j = row & (v.N - 1);
   } else {
-    row = h / half;
+    row = fdiv(h, half, v.mH);
     t = h - row * half;
-    kl = row / v.N;
+    kl = fdiv(row, v.N, v.mN);
     j = row - kl * v.N;
   }
   i = 2 * t + ((j + v.z0 + kl + c) & 1);
@@ -431,7 +446,7 @@ __device__ __forceinline__ void res_restrict(const Slabs& R, int l, int t0, int 
   const int N = f.N, H = N / 2, Nc = cv.N, NNc = cv.NN;
   const int count = own * NNc;
   for (int m = t0; m < count; m += ts) {
-    const int kl = m / NNc, J = (m - kl * NNc) / Nc, I = m - kl * NNc - J * Nc;
+    const int kl = fdiv(m, NNc, cv.mNN), rem = m - kl * NNc, J = fdiv(rem, Nc, cv.mN), I = rem - J * Nc;
     const int K = K0 + kl;
     const float* rp[3];
 #pragma unroll
@@ -572,7 +587,7 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
   {
     float rmax = 0.f, ymax = 0.f;
     for (int ml = t0; ml < cnt0; ml += ts) {
-      const int kl = ml / NN0, rem = ml - kl * NN0, j = rem / N0, i = rem - j * N0;
+      const int kl = fdiv(ml, NN0, v0.mNN), rem = ml - kl * NN0, j = fdiv(rem, N0, v0.mN), i = rem - j * N0;
       const int m = (v0.z0 + kl) * NN0 + rem;
       int q[6];
       nbr_idx<float>(i, j, v0.z0 + kl, N0, q);
@@ -647,7 +662,7 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
       const float* ehi = R.plane(0, 0, v0.z1 % N0);
       float rmax = 0.f, ymax = 0.f;
       for (int ml = t0; ml < cnt0; ml += ts) {
-        const int kl = ml / NN0, rem = ml - kl * NN0, j = rem / N0, i = rem - j * N0;
+        const int kl = fdiv(ml, NN0, v0.mNN), rem = ml - kl * NN0, j = fdiv(rem, N0, v0.mN), i = rem - j * N0;
         const int m = (v0.z0 + kl) * NN0 + rem;
         int q[6];
         nbr_idx<float>(i, j, v0.z0 + kl, N0, q);
