@@ -69,11 +69,14 @@ cudaError_t launch_cells(const CellArgs& a, cudaStream_t s) {
 // Deterministic energy sums: every thread holds the terms of the ions it
 // finished; the block sums them exactly (integer fixed point, see
 // grid_reduce), the last block to finish combines all block partials the
-// same way and publishes the step record.
+// same way and publishes the step record. The seven values are combined one
+// per lane, and the last block sweeps the partials with all of its threads.
 __device__ __forceinline__ void energy_reduce(const ForceArgs& a, const double (&acc)[7]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __shared__ int s_e[32][7];
-  __shared__ long long s_s[32][7];
+  __shared__ int s_e[32][8];
+  __shared__ long long s_s[32][8];
+  __shared__ int s_E[8];
+  __shared__ double s_tot[8];
   __shared__ bool s_last;
 #pragma unroll
   for (int k = 0; k < 7; ++k) {
@@ -81,55 +84,82 @@ __device__ __forceinline__ void energy_reduce(const ForceArgs& a, const double (
     if (lane == 0) s_e[warp][k] = e;
   }
   __syncthreads();
-  int E[7];
+  if (warp == 0 && lane < 7) {
+    int m = 0;
+    for (int u = 0; u < nw; ++u) m = max(m, s_e[u][lane]);
+    s_E[lane] = m + 4;   // headroom for the sum over warps
+  }
+  __syncthreads();
 #pragma unroll
   for (int k = 0; k < 7; ++k) {
-    int m = 0;
-    for (int u = 0; u < nw; ++u) m = max(m, s_e[u][k]);
-    E[k] = m + 4;   // headroom for the sum over warps
-    const long long S = warp_isum(dbl_to_fix(acc[k], E[k]));
+    const long long S = warp_isum(dbl_to_fix(acc[k], s_E[k]));
     if (lane == 0) s_s[warp][k] = S;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < 7; ++k) {
+  if (warp == 0) {
+    if (lane < 7) {
       long long S = 0;
-      for (int u = 0; u < nw; ++u) S += s_s[u][k];
-      a.part[blockIdx.x * 8 + k] = fix_to_dbl(S, E[k]);
+      for (int u = 0; u < nw; ++u) S += s_s[u][lane];
+      a.part[blockIdx.x * 8 + lane] = fix_to_dbl(S, s_E[lane]);
+      __threadfence();
     }
-    __threadfence();
-    const unsigned tk = atomicAdd(a.ticket, 1u);
-    s_last = (tk == gridDim.x - 1);
+    __syncwarp();
+    if (lane == 0) {
+      const unsigned tk = atomicAdd(a.ticket, 1u);
+      s_last = (tk == gridDim.x - 1);
+    }
   }
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  if (threadIdx.x < 32) {
-    double tot[7];
-    const int G = gridDim.x;
-    for (int k = 0; k < 7; ++k) {
-      int e = 0;
-      for (int bb = lane; bb < G; bb += 32) e = max(e, dbl_exp(__ldcg(&a.part[bb * 8 + k])));
-      const int Eg = (int)__reduce_max_sync(0xffffffffu, (unsigned)e) + 16;   // up to 2^16 partials per lane-sum
-      long long x = 0;
-      for (int bb = lane; bb < G; bb += 32) x += dbl_to_fix(__ldcg(&a.part[bb * 8 + k]), Eg);
-      tot[k] = fix_to_dbl(warp_isum(x), Eg);
-    }
-    if (threadIdx.x == 0) {
-      maze_stats* r = a.rec;
-      *a.ticket = 0;
-      if (*a.gate == 0 && (r->status == MAZE_OK || r->status == MAZE_ERR_NOT_CONVERGED)) {
-        r->ke = tot[0];
-        r->v_tf = tot[1];
-        r->v_disc = tot[2];
-        r->v_work += tot[3];
-        r->e_tot = tot[0] + tot[1] + r->v_work;
-        r->momentum[0] = tot[4];
-        r->momentum[1] = tot[5];
-        r->momentum[2] = tot[6];
-        if (a.count_step) r->step += 1;
-        if (!isfinite(r->e_tot)) r->status = MAZE_ERR_NONFINITE;
-      }
+  const int G = gridDim.x;
+  int e[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int bb = threadIdx.x; bb < G; bb += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 7; ++k) e[k] = max(e[k], dbl_exp(__ldcg(&a.part[bb * 8 + k])));
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    const int m = (int)__reduce_max_sync(0xffffffffu, (unsigned)e[k]);
+    if (lane == 0) s_e[warp][k] = m;
+  }
+  __syncthreads();
+  if (warp == 0 && lane < 7) {
+    int m = 0;
+    for (int u = 0; u < nw; ++u) m = max(m, s_e[u][lane]);
+    s_E[lane] = m + 16;   // up to 2^16 partials
+  }
+  __syncthreads();
+  long long x[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int bb = threadIdx.x; bb < G; bb += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 7; ++k) x[k] += dbl_to_fix(__ldcg(&a.part[bb * 8 + k]), s_E[k]);
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    const long long S = warp_isum(x[k]);
+    if (lane == 0) s_s[warp][k] = S;
+  }
+  __syncthreads();
+  if (warp == 0 && lane < 7) {
+    long long S = 0;
+    for (int u = 0; u < nw; ++u) S += s_s[u][lane];
+    s_tot[lane] = fix_to_dbl(S, s_E[lane]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double* tot = s_tot;
+    maze_stats* r = a.rec;
+    *a.ticket = 0;
+    if (*a.gate == 0 && (r->status == MAZE_OK || r->status == MAZE_ERR_NOT_CONVERGED)) {
+      r->ke = tot[0];
+      r->v_tf = tot[1];
+      r->v_disc = tot[2];
+      r->v_work += tot[3];
+      r->e_tot = tot[0] + tot[1] + r->v_work;
+      r->momentum[0] = tot[4];
+      r->momentum[1] = tot[5];
+      r->momentum[2] = tot[6];
+      if (a.count_step) r->step += 1;
+      if (!isfinite(r->e_tot)) r->status = MAZE_ERR_NONFINITE;
     }
   }
 }
