@@ -514,26 +514,91 @@ __device__ __forceinline__ void res_coarsest(const Slabs& R, const float* s_cg, 
   }
 }
 
-// S4 for one point m (double-float): phi_p and sigma_p written, sigma_p returned.
-__device__ __forceinline__ df s4_point(const MixedArgs& a, int m, const int (&q)[6], df c_sig) {
-  const long long qi = (long long)a.qfix[m];
-  a.qfix[m] = 0ull;
-  if (a.q_out) a.q_out[m] = (double)qi * kQInv;
-  df php = {0.f, 0.f}, Mphp = {0.f, 0.f};
-  if (a.zero_phi) {
-  } else if (a.static_guess) {
-    php = df_from(a.phi_k[m]);
-    Mphp = df_sub(dsum6(a.phi_k, q), df_mul_f(php, 6.f));
-  } else {
-    php = df_sub(df_twice(df_from(a.phi_k[m])), df_from(a.phi_km1[m]));
-    const df nk = dsum6(a.phi_k, q), nm = dsum6(a.phi_km1, q);
-    const df s6 = df_sub(df_twice(nk), nm);
-    Mphp = df_sub(s6, df_mul_f(php, 6.f));
+// Level-0 pointers of the outer passes. The arrays are distinct (the three
+// potentials rotate through separate buffers, y and y2 are separate, the
+// V-cycle storage is its own region), so the passes take them as restrict
+// parameters: each point's loads may then issue together, ahead of the
+// previous point's stores.
+//
+// S4 fused with the first outer residual r = sigma_p - M y at the part's
+// level-0 points: phi_p and sigma_p written, r into r0, max|r| and max|y|
+// returned.
+__device__ __forceinline__ void s4_pass(const RLevel& v0, int t0, int ts, df c_sig, bool zero_phi, bool static_guess,
+                                        unsigned long long* __restrict__ qfix, double* __restrict__ q_out,
+                                        const float2* __restrict__ phk, const float2* __restrict__ phm,
+                                        float2* __restrict__ phout, float2* __restrict__ sig,
+                                        const float2* __restrict__ y, float* __restrict__ r0, float& rmax_o,
+                                        float& ymax_o) {
+  const int N0 = v0.N, NN0 = v0.NN, cnt0 = (v0.z1 - v0.z0) * NN0;
+  float rmax = 0.f, ymax = 0.f;
+  for (int ml = t0; ml < cnt0; ml += ts) {
+    const int kl = fdiv(ml, NN0, v0.mNN), rem = ml - kl * NN0, j = fdiv(rem, N0, v0.mN), i = rem - j * N0;
+    const int m = (v0.z0 + kl) * NN0 + rem;
+    int q[6];
+    nbr_idx<float>(i, j, v0.z0 + kl, N0, q);
+    const long long qi = (long long)qfix[m];
+    df php = {0.f, 0.f}, Mphp = {0.f, 0.f};
+    if (zero_phi) {
+    } else if (static_guess) {
+      php = df_from(phk[m]);
+      Mphp = df_sub(dsum6(phk, q), df_mul_f(php, 6.f));
+    } else {
+      php = df_sub(df_twice(df_from(phk[m])), df_from(phm[m]));
+      const df nk = dsum6(phk, q), nm = dsum6(phm, q);
+      const df s6 = df_sub(df_twice(nk), nm);
+      Mphp = df_sub(s6, df_mul_f(php, 6.f));
+    }
+    const df sg = df_add(df_mul(Mphp, c_sig), df_from_fix(qi));
+    const df ym = df_from(y[m]);
+    const df r = df_sub(sg, df_sub(dsum6(y, q), df_mul_f(ym, 6.f)));
+    const float rf = r.h + r.l;
+    qfix[m] = 0ull;
+    if (q_out) q_out[m] = (double)qi * kQInv;
+    phout[m] = df_to(php);
+    sig[m] = df_to(sg);
+    r0[ml] = rf;
+    ymax = fmaxf(ymax, fabsf(ym.h));
+    rmax = fmaxf(rmax, fabsf(rf));
   }
-  a.phi_out[m] = df_to(php);
-  const df sg = df_add(df_mul(Mphp, c_sig), df_from_fix(qi));
-  a.sigma[m] = df_to(sg);
-  return sg;
+  rmax_o = rmax;
+  ymax_o = ymax;
+}
+
+// y_next = y + e and the next outer residual r = sigma_p - M y_next at the
+// part's level-0 points (e0: this part's correction planes, elo/ehi: the
+// neighbouring parts' boundary planes); max|r| and max|y_next| returned.
+__device__ __forceinline__ void update_pass(const RLevel& v0, int t0, int ts, const float* __restrict__ e0,
+                                            const float* __restrict__ elo, const float* __restrict__ ehi,
+                                            const float2* __restrict__ ycur, float2* __restrict__ ynext,
+                                            const float2* __restrict__ sig, float* __restrict__ r0, float& rmax_o,
+                                            float& ymax_o) {
+  const int N0 = v0.N, NN0 = v0.NN, own0 = v0.z1 - v0.z0, cnt0 = own0 * NN0;
+  float rmax = 0.f, ymax = 0.f;
+  for (int ml = t0; ml < cnt0; ml += ts) {
+    const int kl = fdiv(ml, NN0, v0.mNN), rem = ml - kl * NN0, j = fdiv(rem, N0, v0.mN), i = rem - j * N0;
+    const int m = (v0.z0 + kl) * NN0 + rem;
+    int q[6];
+    nbr_idx<float>(i, j, v0.z0 + kl, N0, q);
+    const int row = kl * NN0 + j * N0;
+    const float en[6] = {e0[row + (i == 0 ? N0 - 1 : i - 1)], e0[row + (i == N0 - 1 ? 0 : i + 1)],
+                         e0[kl * NN0 + (j == 0 ? N0 - 1 : j - 1) * N0 + i],
+                         e0[kl * NN0 + (j == N0 - 1 ? 0 : j + 1) * N0 + i],
+                         kl > 0 ? e0[row - NN0 + i] : elo[j * N0 + i],
+                         kl < own0 - 1 ? e0[row + NN0 + i] : ehi[j * N0 + i]};
+    df yn6[6];
+#pragma unroll
+    for (int u = 0; u < 6; ++u) yn6[u] = df_add_f(df_from(ycur[q[u]]), en[u]);
+    const df sn = df_add(df_add(df_add(yn6[0], yn6[1]), df_add(yn6[2], yn6[3])), df_add(yn6[4], yn6[5]));
+    const df ym = df_add_f(df_from(ycur[m]), e0[ml]);
+    const df r = df_sub(df_from(sig[m]), df_sub(sn, df_mul_f(ym, 6.f)));
+    const float rf = r.h + r.l;
+    ynext[m] = df_to(ym);
+    r0[ml] = rf;
+    ymax = fmaxf(ymax, fabsf(ym.h));
+    rmax = fmaxf(rmax, fabsf(rf));
+  }
+  rmax_o = rmax;
+  ymax_o = ymax;
 }
 
 // The solve (S4-S6) shared by every launch form. ``S`` is the sync domain;
@@ -585,20 +650,9 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
   double res = 0.0, ymax_all = 0.0;
   // ---- S4 fused with the first outer residual r = sigma_p - M y
   {
-    float rmax = 0.f, ymax = 0.f;
-    for (int ml = t0; ml < cnt0; ml += ts) {
-      const int kl = fdiv(ml, NN0, v0.mNN), rem = ml - kl * NN0, j = fdiv(rem, N0, v0.mN), i = rem - j * N0;
-      const int m = (v0.z0 + kl) * NN0 + rem;
-      int q[6];
-      nbr_idx<float>(i, j, v0.z0 + kl, N0, q);
-      const df sg = s4_point(a, m, q, c_sig);
-      const df ym = df_from(ycur[m]);
-      ymax = fmaxf(ymax, fabsf(ym.h));
-      const df r = df_sub(sg, df_sub(dsum6(ycur, q), df_mul_f(ym, 6.f)));
-      const float rf = r.h + r.l;
-      r0[ml] = rf;
-      rmax = fmaxf(rmax, fabsf(rf));
-    }
+    float rmax, ymax;
+    s4_pass(v0, t0, ts, c_sig, a.zero_phi, a.static_guess, a.qfix, a.q_out, a.phi_k, a.phi_km1, a.phi_out, a.sigma,
+            ycur, r0, rmax, ymax);
     const double vv[2] = {(double)rmax, (double)ymax};
     double t[2];
     if (!sync.reduce(vv, mmax, t)) return;
@@ -660,30 +714,8 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
     {
       const float* elo = R.plane(0, 0, (v0.z0 - 1 + N0) % N0);
       const float* ehi = R.plane(0, 0, v0.z1 % N0);
-      float rmax = 0.f, ymax = 0.f;
-      for (int ml = t0; ml < cnt0; ml += ts) {
-        const int kl = fdiv(ml, NN0, v0.mNN), rem = ml - kl * NN0, j = fdiv(rem, N0, v0.mN), i = rem - j * N0;
-        const int m = (v0.z0 + kl) * NN0 + rem;
-        int q[6];
-        nbr_idx<float>(i, j, v0.z0 + kl, N0, q);
-        const int row = kl * NN0 + j * N0;
-        const float en[6] = {e0[row + (i == 0 ? N0 - 1 : i - 1)], e0[row + (i == N0 - 1 ? 0 : i + 1)],
-                             e0[kl * NN0 + (j == 0 ? N0 - 1 : j - 1) * N0 + i],
-                             e0[kl * NN0 + (j == N0 - 1 ? 0 : j + 1) * N0 + i],
-                             kl > 0 ? e0[row - NN0 + i] : elo[j * N0 + i],
-                             kl < own0 - 1 ? e0[row + NN0 + i] : ehi[j * N0 + i]};
-        df yn6[6];
-#pragma unroll
-        for (int u = 0; u < 6; ++u) yn6[u] = df_add_f(df_from(ycur[q[u]]), en[u]);
-        const df sn = df_add(df_add(df_add(yn6[0], yn6[1]), df_add(yn6[2], yn6[3])), df_add(yn6[4], yn6[5]));
-        const df ym = df_add_f(df_from(ycur[m]), e0[ml]);
-        ynext[m] = df_to(ym);
-        ymax = fmaxf(ymax, fabsf(ym.h));
-        const df r = df_sub(df_from(a.sigma[m]), df_sub(sn, df_mul_f(ym, 6.f)));
-        const float rf = r.h + r.l;
-        r0[ml] = rf;
-        rmax = fmaxf(rmax, fabsf(rf));
-      }
+      float rmax, ymax;
+      update_pass(v0, t0, ts, e0, elo, ehi, ycur, ynext, a.sigma, r0, rmax, ymax);
       ++it;
       float2* t2 = ycur;
       ycur = ynext;
@@ -704,11 +736,17 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
   {
     const int E = dbl_exp(ymax_all) + 11;
     unsigned long long u = 0;
-    if (ymax_all > 0.0)
-      for (int ml = t0; ml < cnt0; ml += ts) {
-        const float2 yv = ycur[v0.z0 * NN0 + ml];
-        u += (unsigned long long)(dbl_to_fix((double)yv.x, E) + dbl_to_fix((double)yv.y, E));
+    if (ymax_all > 0.0) {
+      const float2* yc = ycur + v0.z0 * NN0;
+      for (int ml = t0; ml < cnt0; ml += 4 * ts) {
+        float2 yv[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) yv[w] = ml + w * ts < cnt0 ? yc[ml + w * ts] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+          u += (unsigned long long)(dbl_to_fix((double)yv[w].x, E) + dbl_to_fix((double)yv[w].y, E));
       }
+    }
     const double vv[4] = {(double)(u & 0xffffu), (double)((u >> 16) & 0xffffu), (double)((u >> 32) & 0xffffu),
                           (double)(u >> 48)};
     double t[4];
@@ -719,11 +757,19 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
     const double ybar = ymax_all > 0.0 ? fix_to_dbl((long long)tot, E) * a.inv_n : 0.0;
     const float ybh = (float)ybar;
     const df yb = {ybh, (float)(ybar - (double)ybh)};
-    for (int ml = t0; ml < cnt0; ml += ts) {
-      const int m = v0.z0 * NN0 + ml;
-      const df yv = df_sub(df_from(ycur[m]), yb);
-      a.y[m] = df_to(yv);
-      a.phi_out[m] = df_to(df_sub(df_from(a.phi_out[m]), df_mul(yv, c_phi)));
+    for (int ml = t0; ml < cnt0; ml += 2 * ts) {
+      // both points' loads ahead of the stores (a.y may be ycur itself)
+      const int m0 = v0.z0 * NN0 + ml, m1 = m0 + ts;
+      const bool two = ml + ts < cnt0;
+      const float2 y0 = ycur[m0], p0 = a.phi_out[m0];
+      const float2 y1 = two ? ycur[m1] : make_float2(0.f, 0.f), p1 = two ? a.phi_out[m1] : make_float2(0.f, 0.f);
+      const df yv0 = df_sub(df_from(y0), yb), yv1 = df_sub(df_from(y1), yb);
+      a.y[m0] = df_to(yv0);
+      a.phi_out[m0] = df_to(df_sub(df_from(p0), df_mul(yv0, c_phi)));
+      if (two) {
+        a.y[m1] = df_to(yv1);
+        a.phi_out[m1] = df_to(df_sub(df_from(p1), df_mul(yv1, c_phi)));
+      }
     }
   }
   if (tid == 0) {
