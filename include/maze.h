@@ -81,7 +81,10 @@ enum { MAZE_FORCE_CD = 0, MAZE_FORCE_GRADW = 1 };
  * Run configuration; everything is host memory and is copied by maze_create.
  *
  * n_ions      number of ions N_p (>= 2)
- * grid_N      grid points per box edge N (even, 8 <= N <= 1024)
+ * grid_N      grid points per box edge N (even, 8 <= N <= 1024); with
+ *             MAZE_SOLVER_MG, halving N while it is even and >= 8 must end
+ *             at an edge <= 7 (the exactly solved coarsest level), e.g. 16,
+ *             32, 48, 56, 64, 128, 256; otherwise MAZE_ERR_INVALID
  * box_L       cubic box edge L in Angstrom; grid spacing h = L / N
  * pos, vel    [n_ions * 3] x,y,z per ion (Angstrom, Angstrom/fs); pos may lie
  *             outside [0, L) and is wrapped

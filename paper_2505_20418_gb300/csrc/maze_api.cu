@@ -71,6 +71,14 @@ maze_status validate(const maze_config* c) {
     return fail(MAZE_ERR_INVALID, "solver must be MAZE_SOLVER_CG or MAZE_SOLVER_MG");
   if (c->solver == MAZE_SOLVER_MG && (c->mg_pre < 1 || c->mg_post < 1 || c->mg_pre > 8 || c->mg_post > 8))
     return fail(MAZE_ERR_INVALID, "mg_pre and mg_post must be in [1, 8]");
+  if (c->solver == MAZE_SOLVER_MG) {
+    // the hierarchy halves the edge while it is even and >= 8; its coarsest
+    // level is solved exactly by a dense kernel of at most 7^3 points
+    int Nc = c->grid_N;
+    while (Nc % 2 == 0 && Nc >= 8) Nc /= 2;
+    if (Nc > 7)
+      return fail(MAZE_ERR_INVALID, "multigrid needs grid_N = m * 2^k with a coarsest edge m <= 7 (e.g. 32, 48, 56)");
+  }
   if (c->order_P != 2 && c->order_P != 4) return fail(MAZE_ERR_INVALID, "order_P must be 2 or 4");
   if (c->precision != MAZE_FP64 && c->precision != MAZE_MIXED)
     return fail(MAZE_ERR_INVALID, "precision must be MAZE_FP64 or MAZE_MIXED");

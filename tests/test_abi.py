@@ -78,8 +78,9 @@ def _cfg(**over):
     pos, vel, types = synth.make_state(w)
     kw = dict(r_cut=w.rc, dt=w.dt, tol=w.tol)
     types = over.pop("types", types)
+    N = over.pop("N", w.N)
     kw.update(over)
-    return M.make_config(pos, vel, types, w.L, over.pop("N", w.N), synth.tosi_fumi_nacl(), **kw)
+    return M.make_config(pos, vel, types, w.L, N, synth.tosi_fumi_nacl(), **kw)
 
 
 @pytest.mark.parametrize("over, msg", [
@@ -95,6 +96,8 @@ def _cfg(**over):
     (dict(force_estimator=2), "force_estimator"),
     (dict(langevin_gamma=-1.0), "langevin_gamma"),
     (dict(langevin_T=float("nan")), "langevin_T"),
+    (dict(solver=1, N=36), "coarsest edge"),    # 36 -> 18 -> 9: a 9^3 coarsest level
+    (dict(solver=1, N=250), "coarsest edge"),   # 250 -> 125
 ])
 def test_invalid_config_rejected(lib, over, msg):
     cfg, keep = _cfg(**over)
