@@ -226,21 +226,31 @@ __device__ __forceinline__ df dsum6(const float2* x, const int (&q)[6]) {
 // ---- storage of the FP32 V-cycle ----------------------------------------------
 // Level l's correction x, right-hand side b and red-point residual r are held
 // as z-slabs: a "part" q of Q owns planes [q P_l, min((q+1) P_l, N_l)) with
-// P_l = ceil(N_l / Q) and stores x[P_l][N_l^2], b[P_l][N_l^2] and (above the
-// coarsest level) r[P_l][N_l^2 / 2] of every level at the same offsets. Two forms share every phase:
+// P_l = ceil(N_l / Q) and stores x, b (P_l N_l^2 values each) and, above the
+// coarsest level, r (P_l N_l^2 / 2) of every level at the same offsets.
+// The smoothed levels keep x and b in red-black order: the red points (i + j
+// + k even) of the part first, then the black ones, each colour plane by
+// plane and row by row, point (i, j) of a row at half-row index t = i / 2.
+// A half-sweep then reads whole lines of the other colour and writes whole
+// lines of its own (the natural order would move every line twice); a
+// point's x-neighbours sit at t or t -+ 1 of the other colour, its y- and
+// z-neighbours at the same t. r holds the red points in the same order. The
+// coarsest level (solved exactly, never swept) stays in natural order.
+// Two forms share every phase:
 //  * cluster-resident: a part per CTA of the cluster, in its dynamic shared
 //    memory; planes owned by another CTA are read over DSMEM (generic
 //    addresses from mapa). Threads stride over their own CTA's points.
 //  * global: one part (Q = 1) in a global scratch buffer; the threads of the
 //    whole sync domain stride over all points.
-// Every point is computed by the same arithmetic in both forms, so results do
-// not depend on the form or on how many CTAs take part.
+// Every point is computed by the same arithmetic in both forms and in either
+// order, so results do not depend on the form or on how many CTAs take part.
 struct RLevel {
   int N, NN, P, lg;
   int z0, z1;        // planes of this part
   unsigned off;      // float offset of x in a part; b at off + P NN, r at off + 2 P NN
   unsigned Pinv;     // ceil(2^32 / P) for P > 1: z / P = umulhi(z, Pinv) for z < 2^16
   unsigned mH, mN, mNN;  // ceil(2^32 / d) for d = N/2, N, N^2 when N <= 64 (else 0: divide)
+  int split;         // x and b in red-black order (every level but the coarsest)
 };
 
 // x / d by a multiply-high with m = ceil(2^32 / d): exact while x d < 2^32
@@ -269,6 +279,18 @@ struct Slabs {
     return r;
   }
   __device__ __forceinline__ float* plane(int l, int arr, int z) const { return plane(lv[l], arr, z); }
+  // pointer to the colour-c half of plane z of array arr of a red-black
+  // ordered level v (N_l^2 / 2 values, row j at j N_l / 2)
+  __device__ __forceinline__ float* cplane(const RLevel& v, int arr, int c, int z) const {
+    const unsigned HH = (unsigned)(v.NN >> 1);
+    if (Q == 1) return sm + v.off + (unsigned)(arr * v.P * v.NN) + (unsigned)(c * v.P) * HH + (unsigned)z * HH;
+    const unsigned q = v.P == 1 ? (unsigned)z : __umulhi((unsigned)z, v.Pinv);
+    float* p = sm + v.off + (unsigned)(arr * v.P * v.NN) + (unsigned)(c * v.P) * HH + (unsigned)(z - (int)q * v.P) * HH;
+    if (q == me) return p;
+    float* r;
+    asm volatile("mapa.u64 %0, %1, %2;" : "=l"(r) : "l"(p), "r"(q));
+    return r;
+  }
   // pointer to the red-point residuals of plane z of level v (N_l^2 / 2 values)
   __device__ __forceinline__ float* rplane(const RLevel& v, int z) const {
     if (Q == 1) return sm + v.off + (unsigned)(2 * v.P * v.NN) + (unsigned)(z * (v.NN / 2));
@@ -338,15 +360,17 @@ __device__ __forceinline__ void slabs_setup(Slabs& R, const MixedArgs& a, float*
     v.mH = magic(v.N / 2);
     v.mN = magic(v.N);
     v.mNN = magic(v.NN);
+    v.split = l < a.L - 1 ? 1 : 0;
     off += 2u * (unsigned)(v.P * v.NN) + (l < a.L - 1 ? (unsigned)(v.P * (v.NN / 2)) : 0u);
   }
 }
 
-// Own point h of colour c (0 red = i+j+k even, 1 black) of level v: local
-// plane kl, row j, column i; returns the index within the part.
-__device__ __forceinline__ int slab_colour_point(const RLevel& v, int h, int c, int& i, int& j, int& kl) {
+// Own point h of colour c (0 red = i+j+k even, 1 black) of a red-black
+// ordered level v: local plane kl, row j, half-row index t (h is also the
+// point's index within its colour); returns the column parity p, i = 2t + p.
+__device__ __forceinline__ int colour_point(const RLevel& v, int h, int c, int& t, int& j, int& kl) {
   const int half = v.N >> 1;
-  int row, t;
+  int row;
   if (v.lg > 0) {
     row = h >> (v.lg - 1);
     t = h & (half - 1);
@@ -358,9 +382,56 @@ __device__ __forceinline__ int slab_colour_point(const RLevel& v, int h, int c, 
     kl = fdiv(row, v.N, v.mN);
     j = row - kl * v.N;
   }
-  i = 2 * t + ((j + v.z0 + kl + c) & 1);
-  return kl * v.NN + j * v.N + i;
+  return (j + v.z0 + kl + c) & 1;
 }
+
+// Sum of the six neighbours (all of the other colour, array xo of the part,
+// boundary planes xlo / xhi) of the own point (t, j, kl) with parity p, in the
+// fixed order ((x- + x+) + (y- + y+)) + (z- + z+).
+__device__ __forceinline__ float colour_nbr_sum(const float* xo, const float* xlo, const float* xhi, int N, int own,
+                                                int t, int j, int kl, int p) {
+  const int H = N >> 1, HH = H * N;
+  const int rowb = kl * HH + j * H;
+  const float sx = xo[rowb + (p ? t : (t == 0 ? H - 1 : t - 1))] + xo[rowb + (p ? (t == H - 1 ? 0 : t + 1) : t)];
+  const float sy = xo[kl * HH + (j == 0 ? N - 1 : j - 1) * H + t] + xo[kl * HH + (j == N - 1 ? 0 : j + 1) * H + t];
+  const float zm = kl > 0 ? xo[rowb - HH + t] : xlo[j * H + t];
+  const float zp = kl < own - 1 ? xo[rowb + HH + t] : xhi[j * H + t];
+  return (sx + sy) + (zm + zp);
+}
+
+// 16-byte loads and stores of four consecutive values.
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
+// Four consecutive own points (half-row indices t .. t+3 of one row, t a
+// multiple of 4, parity p): the six-neighbour sums in the order of
+// colour_nbr_sum. Their y- and z-neighbours are the other colour's values at
+// the same t (four loads of 16 bytes), their x-neighbours the other colour's
+// t .. t+3 of the row and one more value at t-1 (p = 0) or t+4 (p = 1).
+__device__ __forceinline__ float4 colour_nbr_sum4(const float* xo, const float* xlo, const float* xhi, int N, int own,
+                                                  int t, int j, int kl, int p) {
+  const int H = N >> 1, HH = H * N;
+  const int rowb = kl * HH + j * H;
+  const float4 xr = ld4(xo + rowb + t);
+  const float xe = p ? xo[rowb + (t + 4 == H ? 0 : t + 4)] : xo[rowb + (t == 0 ? H - 1 : t - 1)];
+  const float4 ym = ld4(xo + kl * HH + (j == 0 ? N - 1 : j - 1) * H + t);
+  const float4 yp = ld4(xo + kl * HH + (j == N - 1 ? 0 : j + 1) * H + t);
+  const float4 zm = ld4((kl > 0 ? xo + rowb - HH : xlo + j * H) + t);
+  const float4 zp = ld4((kl < own - 1 ? xo + rowb + HH : xhi + j * H) + t);
+  const float4 xmn = p ? xr : make_float4(xe, xr.x, xr.y, xr.z);
+  const float4 xpl = p ? make_float4(xr.y, xr.z, xr.w, xe) : xr;
+  float4 s;
+  s.x = ((xmn.x + xpl.x) + (ym.x + yp.x)) + (zm.x + zp.x);
+  s.y = ((xmn.y + xpl.y) + (ym.y + yp.y)) + (zm.y + zp.y);
+  s.z = ((xmn.z + xpl.z) + (ym.z + yp.z)) + (zm.z + zp.z);
+  s.w = ((xmn.w + xpl.w) + (ym.w + yp.w)) + (zm.w + zp.w);
+  return s;
+}
+
+// Levels whose rows hold a multiple of 4 values of each colour (N a multiple
+// of 8) take the four-point forms; their storage offsets are then multiples
+// of 16 bytes.
+__device__ __forceinline__ bool quad_level(const RLevel& v) { return (v.N & 7) == 0; }
 
 // One red-black half-sweep of colour c: x = (sum of the six neighbours - b) / 6
 // at the part's points of that colour (from_zero: the guess is zero, x =
@@ -370,40 +441,56 @@ __device__ __forceinline__ void res_half_sweep(const Slabs& R, int l, int c, boo
   const RLevel v = R.lv[l];
   const int own = v.z1 - v.z0;
   if (own <= 0) return;
-  float* x = R.sm + v.off;
-  const float* b = x + v.P * v.NN;
-  const int N = v.N, NN = v.NN;
-  const int hcount = own * NN / 2;
-  const float* xlo = from_zero ? nullptr : R.plane(v, 0, (v.z0 - 1 + N) % N);
-  const float* xhi = from_zero ? nullptr : R.plane(v, 0, v.z1 % N);
+  const int PH = v.P * (v.NN >> 1);
+  float* xc = R.sm + v.off + c * PH;
+  const float* xo = R.sm + v.off + (1 - c) * PH;
+  const float* bc = R.sm + v.off + v.P * v.NN + c * PH;
+  const int N = v.N;
+  const int hcount = own * (v.NN >> 1);
+  const float* xlo = from_zero ? nullptr : R.cplane(v, 0, 1 - c, (v.z0 - 1 + N) % N);
+  const float* xhi = from_zero ? nullptr : R.cplane(v, 0, 1 - c, v.z1 % N);
+  if (quad_level(v)) {
+    for (int g = t0; g < (hcount >> 2); g += ts) {
+      const int h = g << 2;
+      const float4 b = ld4(bc + h);
+      float4 s;
+      if (from_zero) {
+        s = make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        int t, j, kl;
+        const int p = colour_point(v, h, c, t, j, kl);
+        s = colour_nbr_sum4(xo, xlo, xhi, N, own, t, j, kl, p);
+      }
+      float4 o;
+      if (from_zero) {
+        o = make_float4(-b.x * (1.f / 6.f), -b.y * (1.f / 6.f), -b.z * (1.f / 6.f), -b.w * (1.f / 6.f));
+      } else {
+        o = make_float4((s.x - b.x) * (1.f / 6.f), (s.y - b.y) * (1.f / 6.f), (s.z - b.z) * (1.f / 6.f),
+                        (s.w - b.w) * (1.f / 6.f));
+      }
+      st4(xc + h, o);
+    }
+    return;
+  }
   for (int h0 = t0; h0 < hcount; h0 += 2 * ts) {
-    int mm[2];
     float val[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int h = h0 + u * ts;
-      mm[u] = -1;
       val[u] = 0.f;
       if (h < hcount) {
-        int i, j, kl;
-        const int m = slab_colour_point(v, h, c, i, j, kl);
-        mm[u] = m;
         if (from_zero) {
-          val[u] = -b[m] * (1.f / 6.f);
+          val[u] = -bc[h] * (1.f / 6.f);
         } else {
-          const int row = kl * NN + j * N;
-          const float* xp = x + row;
-          const float sx = xp[i == 0 ? N - 1 : i - 1] + xp[i == N - 1 ? 0 : i + 1];
-          const float sy = x[kl * NN + (j == 0 ? N - 1 : j - 1) * N + i] + x[kl * NN + (j == N - 1 ? 0 : j + 1) * N + i];
-          const float zm = kl > 0 ? x[row - NN + i] : xlo[j * N + i];
-          const float zp = kl < own - 1 ? x[row + NN + i] : xhi[j * N + i];
-          val[u] = (((sx + sy) + (zm + zp)) - b[m]) * (1.f / 6.f);
+          int t, j, kl;
+          const int p = colour_point(v, h, c, t, j, kl);
+          val[u] = (colour_nbr_sum(xo, xlo, xhi, N, own, t, j, kl, p) - bc[h]) * (1.f / 6.f);
         }
       }
     }
 #pragma unroll
     for (int u = 0; u < 2; ++u)
-      if (mm[u] >= 0) x[mm[u]] = val[u];
+      if (h0 + u * ts < hcount) xc[h0 + u * ts] = val[u];
   }
 }
 
@@ -413,22 +500,32 @@ __device__ __forceinline__ void res_residual(const Slabs& R, int l, int t0, int 
   const RLevel v = R.lv[l];
   const int own = v.z1 - v.z0;
   if (own <= 0) return;
-  const float* x = R.sm + v.off;
-  const float* b = x + v.P * v.NN;
+  const int PH = v.P * (v.NN >> 1);
+  const float* xr = R.sm + v.off;
+  const float* xb = xr + PH;
+  const float* br = R.sm + v.off + v.P * v.NN;
   float* r = R.sm + v.off + 2 * v.P * v.NN;
-  const int N = v.N, NN = v.NN;
-  const int hcount = own * NN / 2;
-  const float* xlo = R.plane(v, 0, (v.z0 - 1 + N) % N);
-  const float* xhi = R.plane(v, 0, v.z1 % N);
+  const int N = v.N;
+  const int hcount = own * (v.NN >> 1);
+  const float* xlo = R.cplane(v, 0, 1, (v.z0 - 1 + N) % N);
+  const float* xhi = R.cplane(v, 0, 1, v.z1 % N);
+  if (quad_level(v)) {
+    for (int g = t0; g < (hcount >> 2); g += ts) {
+      const int h = g << 2;
+      int t, j, kl;
+      const int p = colour_point(v, h, 0, t, j, kl);
+      const float4 s6 = colour_nbr_sum4(xb, xlo, xhi, N, own, t, j, kl, p);
+      const float4 b = ld4(br + h), x = ld4(xr + h);
+      st4(r + h, make_float4(b.x - (s6.x - 6.f * x.x), b.y - (s6.y - 6.f * x.y), b.z - (s6.z - 6.f * x.z),
+                             b.w - (s6.w - 6.f * x.w)));
+    }
+    return;
+  }
   for (int h = t0; h < hcount; h += ts) {
-    int i, j, kl;
-    const int m = slab_colour_point(v, h, 0, i, j, kl);
-    const int row = kl * NN + j * N;
-    const float* xp = x + row;
-    const float s6 = ((xp[i == 0 ? N - 1 : i - 1] + xp[i == N - 1 ? 0 : i + 1]) +
-                      (x[kl * NN + (j == 0 ? N - 1 : j - 1) * N + i] + x[kl * NN + (j == N - 1 ? 0 : j + 1) * N + i])) +
-                     ((kl > 0 ? x[row - NN + i] : xlo[j * N + i]) + (kl < own - 1 ? x[row + NN + i] : xhi[j * N + i]));
-    r[h] = b[m] - (s6 - 6.f * x[m]);
+    int t, j, kl;
+    const int p = colour_point(v, h, 0, t, j, kl);
+    const float s6 = colour_nbr_sum(xb, xlo, xhi, N, own, t, j, kl, p);
+    r[h] = br[h] - (s6 - 6.f * xr[h]);
   }
 }
 
@@ -437,7 +534,8 @@ __device__ __forceinline__ void res_residual(const Slabs& R, int l, int t0, int 
 // points only the centre (weight 1/8) and the 12 edge neighbours (1/32),
 // all red, count. Coarse plane K is computed by the part that owns fine
 // plane 2K and stored into the part that owns K (another CTA's shared
-// memory when they differ).
+// memory when they differ), red-black ordered unless level l+1 is the
+// coarsest.
 __device__ __forceinline__ void res_restrict(const Slabs& R, int l, int t0, int ts) {
   const RLevel f = R.lv[l];
   const RLevel cv = R.lv[l + 1];
@@ -459,7 +557,11 @@ __device__ __forceinline__ void res_restrict(const Slabs& R, int l, int t0, int 
     const float edges = ((res(im, jm, 0) + res(ip, jm, 0)) + (res(im, jp, 0) + res(ip, jp, 0))) +
                         ((res(im, j0, -1) + res(ip, j0, -1)) + (res(im, j0, 1) + res(ip, j0, 1))) +
                         ((res(i0, jm, -1) + res(i0, jp, -1)) + (res(i0, jm, 1) + res(i0, jp, 1)));
-    R.plane(cv, 1, K)[J * Nc + I] = 4.f * (0.125f * res(i0, j0, 0) + 0.03125f * edges);
+    const float val = 4.f * (0.125f * res(i0, j0, 0) + 0.03125f * edges);
+    if (cv.split)
+      R.cplane(cv, 1, (I + J + K) & 1, K)[J * (Nc >> 1) + (I >> 1)] = val;
+    else
+      R.plane(cv, 1, K)[J * Nc + I] = val;
   }
 }
 
@@ -470,19 +572,47 @@ __device__ __forceinline__ void res_prolong(const Slabs& R, int l, int t0, int t
   const RLevel cv = R.lv[l + 1];
   const int own = f.z1 - f.z0;
   if (own <= 0) return;
-  float* x = R.sm + f.off;
-  const int Nc = cv.N, hcount = own * f.NN / 2;
+  float* xb = R.sm + f.off + f.P * (f.NN >> 1);
+  const int Nc = cv.N, Hc = Nc >> 1, hcount = own * (f.NN >> 1);
   for (int h = t0; h < hcount; h += ts) {
-    int i, j, kl;
-    const int m = slab_colour_point(f, h, 1, i, j, kl);
+    int t, j, kl;
+    const int p = colour_point(f, h, 1, t, j, kl);
+    const int i = 2 * t + p;
     const int k = f.z0 + kl;
     const int i0 = i >> 1, i1 = (i & 1) ? (i0 + 1 == Nc ? 0 : i0 + 1) : i0;
     const int j0 = j >> 1, j1 = (j & 1) ? (j0 + 1 == Nc ? 0 : j0 + 1) : j0;
     const int k0 = k >> 1, k1 = (k & 1) ? (k0 + 1 == Nc ? 0 : k0 + 1) : k0;
-    const float* c0 = R.plane(cv, 0, k0);
-    const float* c1 = R.plane(cv, 0, k1);
-    x[m] += 0.125f * (((c0[j0 * Nc + i0] + c0[j0 * Nc + i1]) + (c0[j1 * Nc + i0] + c0[j1 * Nc + i1])) +
-                      ((c1[j0 * Nc + i0] + c1[j0 * Nc + i1]) + (c1[j1 * Nc + i0] + c1[j1 * Nc + i1])));
+    float c8[8];
+    if (cv.split) {
+      // coarse point (I, J, K) lies in colour (I + J + K) & 1 at J Hc + I / 2
+      const float* c0r = R.cplane(cv, 0, 0, k0);
+      const float* c0b = R.cplane(cv, 0, 1, k0);
+      const float* c1r = R.cplane(cv, 0, 0, k1);
+      const float* c1b = R.cplane(cv, 0, 1, k1);
+      auto at = [&](int I, int J, int K, const float* pr, const float* pb) -> float {
+        return (((I + J + K) & 1) ? pb : pr)[J * Hc + (I >> 1)];
+      };
+      c8[0] = at(i0, j0, k0, c0r, c0b);
+      c8[1] = at(i1, j0, k0, c0r, c0b);
+      c8[2] = at(i0, j1, k0, c0r, c0b);
+      c8[3] = at(i1, j1, k0, c0r, c0b);
+      c8[4] = at(i0, j0, k1, c1r, c1b);
+      c8[5] = at(i1, j0, k1, c1r, c1b);
+      c8[6] = at(i0, j1, k1, c1r, c1b);
+      c8[7] = at(i1, j1, k1, c1r, c1b);
+    } else {
+      const float* c0 = R.plane(cv, 0, k0);
+      const float* c1 = R.plane(cv, 0, k1);
+      c8[0] = c0[j0 * Nc + i0];
+      c8[1] = c0[j0 * Nc + i1];
+      c8[2] = c0[j1 * Nc + i0];
+      c8[3] = c0[j1 * Nc + i1];
+      c8[4] = c1[j0 * Nc + i0];
+      c8[5] = c1[j0 * Nc + i1];
+      c8[6] = c1[j1 * Nc + i0];
+      c8[7] = c1[j1 * Nc + i1];
+    }
+    xb[h] += 0.125f * (((c8[0] + c8[1]) + (c8[2] + c8[3])) + ((c8[4] + c8[5]) + (c8[6] + c8[7])));
   }
 }
 
@@ -521,15 +651,15 @@ __device__ __forceinline__ void res_coarsest(const Slabs& R, const float* s_cg, 
 // previous point's stores.
 //
 // S4 fused with the first outer residual r = sigma_p - M y at the part's
-// level-0 points: phi_p and sigma_p written, r into r0, max|r| and max|y|
-// returned.
+// level-0 points: phi_p and sigma_p written, r into the V-cycle's level-0
+// right-hand side b0 (red-black order), max|r| and max|y| returned.
 __device__ __forceinline__ void s4_pass(const RLevel& v0, int t0, int ts, df c_sig, bool zero_phi, bool static_guess,
                                         unsigned long long* __restrict__ qfix, double* __restrict__ q_out,
                                         const float2* __restrict__ phk, const float2* __restrict__ phm,
                                         float2* __restrict__ phout, float2* __restrict__ sig,
-                                        const float2* __restrict__ y, float* __restrict__ r0, float& rmax_o,
+                                        const float2* __restrict__ y, float* __restrict__ b0, float& rmax_o,
                                         float& ymax_o) {
-  const int N0 = v0.N, NN0 = v0.NN, cnt0 = (v0.z1 - v0.z0) * NN0;
+  const int N0 = v0.N, NN0 = v0.NN, cnt0 = (v0.z1 - v0.z0) * NN0, PH0 = v0.P * (NN0 >> 1);
   float rmax = 0.f, ymax = 0.f;
   for (int ml = t0; ml < cnt0; ml += ts) {
     const int kl = fdiv(ml, NN0, v0.mNN), rem = ml - kl * NN0, j = fdiv(rem, N0, v0.mN), i = rem - j * N0;
@@ -556,7 +686,7 @@ __device__ __forceinline__ void s4_pass(const RLevel& v0, int t0, int ts, df c_s
     if (q_out) q_out[m] = (double)qi * kQInv;
     phout[m] = df_to(php);
     sig[m] = df_to(sg);
-    r0[ml] = rf;
+    b0[((i + j + v0.z0 + kl) & 1) * PH0 + (rem >> 1) + kl * (NN0 >> 1)] = rf;
     ymax = fmaxf(ymax, fabsf(ym.h));
     rmax = fmaxf(rmax, fabsf(rf));
   }
@@ -565,35 +695,42 @@ __device__ __forceinline__ void s4_pass(const RLevel& v0, int t0, int ts, df c_s
 }
 
 // y_next = y + e and the next outer residual r = sigma_p - M y_next at the
-// part's level-0 points (e0: this part's correction planes, elo/ehi: the
-// neighbouring parts' boundary planes); max|r| and max|y_next| returned.
+// part's level-0 points (e0: this part's correction, red-black ordered;
+// elo0/elo1, ehi0/ehi1: red / black halves of the neighbouring parts'
+// boundary planes); r into b0 (red-black order), max|r| and max|y_next|
+// returned.
 __device__ __forceinline__ void update_pass(const RLevel& v0, int t0, int ts, const float* __restrict__ e0,
-                                            const float* __restrict__ elo, const float* __restrict__ ehi,
-                                            const float2* __restrict__ ycur, float2* __restrict__ ynext,
-                                            const float2* __restrict__ sig, float* __restrict__ r0, float& rmax_o,
+                                            const float* elo0, const float* elo1, const float* ehi0,
+                                            const float* ehi1, const float2* __restrict__ ycur, float2* __restrict__ ynext,
+                                            const float2* __restrict__ sig, float* __restrict__ b0, float& rmax_o,
                                             float& ymax_o) {
   const int N0 = v0.N, NN0 = v0.NN, own0 = v0.z1 - v0.z0, cnt0 = own0 * NN0;
+  const int H0 = N0 >> 1, HH0 = NN0 >> 1, PH0 = v0.P * HH0;
   float rmax = 0.f, ymax = 0.f;
   for (int ml = t0; ml < cnt0; ml += ts) {
     const int kl = fdiv(ml, NN0, v0.mNN), rem = ml - kl * NN0, j = fdiv(rem, N0, v0.mN), i = rem - j * N0;
     const int m = (v0.z0 + kl) * NN0 + rem;
     int q[6];
     nbr_idx<float>(i, j, v0.z0 + kl, N0, q);
-    const int row = kl * NN0 + j * N0;
-    const float en[6] = {e0[row + (i == 0 ? N0 - 1 : i - 1)], e0[row + (i == N0 - 1 ? 0 : i + 1)],
-                         e0[kl * NN0 + (j == 0 ? N0 - 1 : j - 1) * N0 + i],
-                         e0[kl * NN0 + (j == N0 - 1 ? 0 : j + 1) * N0 + i],
-                         kl > 0 ? e0[row - NN0 + i] : elo[j * N0 + i],
-                         kl < own0 - 1 ? e0[row + NN0 + i] : ehi[j * N0 + i]};
+    // own colour c; every neighbour is of the other colour
+    const int c = (i + j + v0.z0 + kl) & 1;
+    const float* eo = e0 + (1 - c) * PH0;
+    const int t = i >> 1, rowb = kl * HH0 + j * H0;
+    const int im = i == 0 ? N0 - 1 : i - 1, ip = i == N0 - 1 ? 0 : i + 1;
+    const float en[6] = {eo[rowb + (im >> 1)], eo[rowb + (ip >> 1)],
+                         eo[kl * HH0 + (j == 0 ? N0 - 1 : j - 1) * H0 + t],
+                         eo[kl * HH0 + (j == N0 - 1 ? 0 : j + 1) * H0 + t],
+                         kl > 0 ? eo[rowb - HH0 + t] : (c ? elo0 : elo1)[j * H0 + t],
+                         kl < own0 - 1 ? eo[rowb + HH0 + t] : (c ? ehi0 : ehi1)[j * H0 + t]};
     df yn6[6];
 #pragma unroll
     for (int u = 0; u < 6; ++u) yn6[u] = df_add_f(df_from(ycur[q[u]]), en[u]);
     const df sn = df_add(df_add(df_add(yn6[0], yn6[1]), df_add(yn6[2], yn6[3])), df_add(yn6[4], yn6[5]));
-    const df ym = df_add_f(df_from(ycur[m]), e0[ml]);
+    const df ym = df_add_f(df_from(ycur[m]), e0[c * PH0 + rowb + t]);
     const df r = df_sub(df_from(sig[m]), df_sub(sn, df_mul_f(ym, 6.f)));
     const float rf = r.h + r.l;
     ynext[m] = df_to(ym);
-    r0[ml] = rf;
+    b0[c * PH0 + rowb + t] = rf;
     ymax = fmaxf(ymax, fabsf(ym.h));
     rmax = fmaxf(rmax, fabsf(rf));
   }
@@ -712,10 +849,10 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
     if (lt == 0 && !sync.barrier()) return;
     // ---- y_next = y + e and the next outer residual r = sigma_p - M y_next
     {
-      const float* elo = R.plane(0, 0, (v0.z0 - 1 + N0) % N0);
-      const float* ehi = R.plane(0, 0, v0.z1 % N0);
+      const int zlo = (v0.z0 - 1 + N0) % N0, zhi = v0.z1 % N0;
       float rmax, ymax;
-      update_pass(v0, t0, ts, e0, elo, ehi, ycur, ynext, a.sigma, r0, rmax, ymax);
+      update_pass(v0, t0, ts, e0, R.cplane(v0, 0, 0, zlo), R.cplane(v0, 0, 1, zlo), R.cplane(v0, 0, 0, zhi),
+                  R.cplane(v0, 0, 1, zhi), ycur, ynext, a.sigma, r0, rmax, ymax);
       ++it;
       float2* t2 = ycur;
       ycur = ynext;
