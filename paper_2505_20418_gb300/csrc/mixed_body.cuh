@@ -694,45 +694,79 @@ __device__ __forceinline__ void s4_pass(const RLevel& v0, int t0, int ts, df c_s
   ymax_o = ymax;
 }
 
+// One point of the update pass: y_next = y + e (returned in ynew) and the
+// residual r = sigma_p - (sum of the six (y + e) neighbours - 6 y_next) as a
+// float; yn / en are the neighbours' y and e in the order x-, x+, y-, y+,
+// z-, z+.
+__device__ __forceinline__ void upd_point(const float2 (&yn)[6], const float (&en)[6], float2 yo, float eo, float2 sg,
+                                          float2& ynew, float& rf) {
+  df yn6[6];
+#pragma unroll
+  for (int u = 0; u < 6; ++u) yn6[u] = df_add_f(df_from(yn[u]), en[u]);
+  const df sn = df_add(df_add(df_add(yn6[0], yn6[1]), df_add(yn6[2], yn6[3])), df_add(yn6[4], yn6[5]));
+  const df ym = df_add_f(df_from(yo), eo);
+  const df r = df_sub(df_from(sg), df_sub(sn, df_mul_f(ym, 6.f)));
+  ynew = df_to(ym);
+  rf = r.h + r.l;
+}
+
 // y_next = y + e and the next outer residual r = sigma_p - M y_next at the
 // part's level-0 points (e0: this part's correction, red-black ordered;
 // elo0/elo1, ehi0/ehi1: red / black halves of the neighbouring parts'
 // boundary planes); r into b0 (red-black order), max|r| and max|y_next|
-// returned.
+// returned. A thread takes two x-adjacent points at a time (one of each
+// colour): 16-byte loads of y and sigma_p, each point's partner supplies one
+// of its x-neighbours.
 __device__ __forceinline__ void update_pass(const RLevel& v0, int t0, int ts, const float* __restrict__ e0,
                                             const float* elo0, const float* elo1, const float* ehi0,
-                                            const float* ehi1, const float2* __restrict__ ycur, float2* __restrict__ ynext,
-                                            const float2* __restrict__ sig, float* __restrict__ b0, float& rmax_o,
-                                            float& ymax_o) {
+                                            const float* ehi1, const float2* __restrict__ ycur,
+                                            float2* __restrict__ ynext, const float2* __restrict__ sig,
+                                            float* __restrict__ b0, float& rmax_o, float& ymax_o) {
   const int N0 = v0.N, NN0 = v0.NN, own0 = v0.z1 - v0.z0, cnt0 = own0 * NN0;
   const int H0 = N0 >> 1, HH0 = NN0 >> 1, PH0 = v0.P * HH0;
+  auto ld2x2 = [](const float2* p, float2& a, float2& b) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+  };
   float rmax = 0.f, ymax = 0.f;
-  for (int ml = t0; ml < cnt0; ml += ts) {
-    const int kl = fdiv(ml, NN0, v0.mNN), rem = ml - kl * NN0, j = fdiv(rem, N0, v0.mN), i = rem - j * N0;
-    const int m = (v0.z0 + kl) * NN0 + rem;
-    int q[6];
-    nbr_idx<float>(i, j, v0.z0 + kl, N0, q);
-    // own colour c; every neighbour is of the other colour
-    const int c = (i + j + v0.z0 + kl) & 1;
-    const float* eo = e0 + (1 - c) * PH0;
-    const int t = i >> 1, rowb = kl * HH0 + j * H0;
-    const int im = i == 0 ? N0 - 1 : i - 1, ip = i == N0 - 1 ? 0 : i + 1;
-    const float en[6] = {eo[rowb + (im >> 1)], eo[rowb + (ip >> 1)],
-                         eo[kl * HH0 + (j == 0 ? N0 - 1 : j - 1) * H0 + t],
-                         eo[kl * HH0 + (j == N0 - 1 ? 0 : j + 1) * H0 + t],
-                         kl > 0 ? eo[rowb - HH0 + t] : (c ? elo0 : elo1)[j * H0 + t],
-                         kl < own0 - 1 ? eo[rowb + HH0 + t] : (c ? ehi0 : ehi1)[j * H0 + t]};
-    df yn6[6];
-#pragma unroll
-    for (int u = 0; u < 6; ++u) yn6[u] = df_add_f(df_from(ycur[q[u]]), en[u]);
-    const df sn = df_add(df_add(df_add(yn6[0], yn6[1]), df_add(yn6[2], yn6[3])), df_add(yn6[4], yn6[5]));
-    const df ym = df_add_f(df_from(ycur[m]), e0[c * PH0 + rowb + t]);
-    const df r = df_sub(df_from(sig[m]), df_sub(sn, df_mul_f(ym, 6.f)));
-    const float rf = r.h + r.l;
-    ynext[m] = df_to(ym);
-    b0[c * PH0 + rowb + t] = rf;
-    ymax = fmaxf(ymax, fabsf(ym.h));
-    rmax = fmaxf(rmax, fabsf(rf));
+  for (int g = t0; g < (cnt0 >> 1); g += ts) {
+    const int ml = g << 1;
+    const int kl = fdiv(ml, NN0, v0.mNN), rem = ml - kl * NN0, j = fdiv(rem, N0, v0.mN), i0 = rem - j * N0;
+    const int k = v0.z0 + kl;
+    const int m = k * NN0 + rem;
+    // the pair: A = (i0, j, k) of colour c0, B = (i0 + 1, j, k) of colour 1 - c0
+    const int c0 = (i0 + j + k) & 1, t = i0 >> 1, rowb = kl * HH0 + j * H0;
+    const float* EA = e0 + c0 * PH0;
+    const float* EB = e0 + (1 - c0) * PH0;
+    const int rjm = kl * HH0 + (j == 0 ? N0 - 1 : j - 1) * H0 + t, rjp = kl * HH0 + (j == N0 - 1 ? 0 : j + 1) * H0 + t;
+    const float* lA = kl > 0 ? EB + rowb - HH0 : (c0 ? elo0 : elo1) + j * H0;
+    const float* lB = kl > 0 ? EA + rowb - HH0 : (c0 ? elo1 : elo0) + j * H0;
+    const float* hA = kl < own0 - 1 ? EB + rowb + HH0 : (c0 ? ehi0 : ehi1) + j * H0;
+    const float* hB = kl < own0 - 1 ? EA + rowb + HH0 : (c0 ? ehi1 : ehi0) + j * H0;
+    const float eA = EA[rowb + t], eB = EB[rowb + t];
+    const float enA[6] = {EB[rowb + (i0 == 0 ? H0 - 1 : t - 1)], eB, EB[rjm], EB[rjp], lA[t], hA[t]};
+    const float enB[6] = {eA, EA[rowb + (i0 + 2 == N0 ? 0 : t + 1)], EA[rjm], EA[rjp], lB[t], hB[t]};
+    float2 yA, yB, ymA, ymB, ypA, ypB, zmA, zmB, zpA, zpB, sA, sB;
+    ld2x2(ycur + m, yA, yB);
+    ld2x2(ycur + (j == 0 ? m + NN0 - N0 : m - N0), ymA, ymB);
+    ld2x2(ycur + (j == N0 - 1 ? m - NN0 + N0 : m + N0), ypA, ypB);
+    ld2x2(ycur + (k == 0 ? m + NN0 * (N0 - 1) : m - NN0), zmA, zmB);
+    ld2x2(ycur + (k == N0 - 1 ? m - NN0 * (N0 - 1) : m + NN0), zpA, zpB);
+    ld2x2(sig + m, sA, sB);
+    const float2 yxm = ycur[i0 == 0 ? m + N0 - 1 : m - 1];
+    const float2 yxp = ycur[i0 + 2 == N0 ? m + 2 - N0 : m + 2];
+    const float2 ynA[6] = {yxm, yB, ymA, ypA, zmA, zpA};
+    const float2 ynB[6] = {yA, yxp, ymB, ypB, zmB, zpB};
+    float2 nA, nB;
+    float rA, rB;
+    upd_point(ynA, enA, yA, eA, sA, nA, rA);
+    upd_point(ynB, enB, yB, eB, sB, nB, rB);
+    *reinterpret_cast<float4*>(ynext + m) = make_float4(nA.x, nA.y, nB.x, nB.y);
+    b0[c0 * PH0 + rowb + t] = rA;
+    b0[(1 - c0) * PH0 + rowb + t] = rB;
+    ymax = fmaxf(ymax, fmaxf(fabsf(nA.x), fabsf(nB.x)));
+    rmax = fmaxf(rmax, fmaxf(fabsf(rA), fabsf(rB)));
   }
   rmax_o = rmax;
   ymax_o = ymax;
