@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_step(BatchArgs b) {
 // to 64^3): move, spread and cell list with cluster barriers, then the solve.
 // The forces (S7-S9) follow as their own wide launch.
 constexpr size_t kStepSortBytes = (size_t)(kMixedClusterThreads / 32) * kSortCap * sizeof(int);
-__global__ void __launch_bounds__(kMixedClusterThreads) k_cluster_step(IonArgs ia, CellArgs ca, MixedArgs ma) {
+__global__ void __launch_bounds__(kMixedClusterThreads, 1) k_cluster_step(IonArgs ia, CellArgs ca, MixedArgs ma) {
   // dynamic shared memory: the cell sort's buffers, then (after a barrier)
   // the resident V-cycle
   extern __shared__ __align__(16) float dsm[];

@@ -5,7 +5,7 @@
 
 namespace maze {
 
-__global__ void __launch_bounds__(kMixedClusterThreads) k_mixed_cluster(MixedArgs a) {
+__global__ void __launch_bounds__(kMixedClusterThreads, 1) k_mixed_cluster(MixedArgs a) {
   extern __shared__ __align__(16) float dsm[];
   if (*a.gate != 0 || a.rec->status != MAZE_OK) return;
   ClusterSync s;

@@ -543,6 +543,47 @@ __device__ __forceinline__ void res_restrict(const Slabs& R, int l, int t0, int 
   if (own <= 0) return;
   const int N = f.N, H = N / 2, Nc = cv.N, NNc = cv.NN;
   const int count = own * NNc;
+  if (quad_level(f) && cv.split) {
+    // four coarse columns I .. I+3 (I a multiple of 4) of one coarse row: the
+    // red fine residuals they read lie at half-row indices I-1 .. I+3 of
+    // nine fine rows (16-byte loads plus one value at I-1 where needed);
+    // the even columns go to colour (J + K) & 1, the odd ones to the other
+    // (8-byte stores).
+    const int Hc = Nc >> 1;
+    for (int g = t0; g < (count >> 2); g += ts) {
+      const int m = g << 2;
+      const int kl = fdiv(m, NNc, cv.mNN), rem = m - kl * NNc, J = fdiv(rem, Nc, cv.mN), I = rem - J * Nc;
+      const int K = K0 + kl;
+      const int j0 = 2 * J, jm = j0 == 0 ? N - 1 : j0 - 1, jp = j0 + 1 == N ? 0 : j0 + 1;
+      const int Im = I == 0 ? H - 1 : I - 1;
+      const float* rz = R.rplane(f, 2 * K);
+      const float* rl = R.rplane(f, (2 * K - 1 + N) % N);
+      const float* rh = R.rplane(f, (2 * K + 1) % N);
+      // per fine row: the values at I .. I+3 and (where read) at I-1
+      const float4 a_jm = ld4(rz + jm * H + I), a_j0 = ld4(rz + j0 * H + I), a_jp = ld4(rz + jp * H + I);
+      const float e_jm = rz[jm * H + Im], e_jp = rz[jp * H + Im];
+      const float4 l_j0 = ld4(rl + j0 * H + I), l_jm = ld4(rl + jm * H + I), l_jp = ld4(rl + jp * H + I);
+      const float4 h_j0 = ld4(rh + j0 * H + I), h_jm = ld4(rh + jm * H + I), h_jp = ld4(rh + jp * H + I);
+      const float el_j0 = rl[j0 * H + Im], eh_j0 = rh[j0 * H + Im];
+      auto col = [](float4 v, float e, int u) -> float { return u == 0 ? e : (u == 1 ? v.x : (u == 2 ? v.y : v.z)); };
+      auto at = [](float4 v, int u) -> float { return u == 0 ? v.x : (u == 1 ? v.y : (u == 2 ? v.z : v.w)); };
+      float o[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        // fine columns im = 2(I+u)-1 -> half index I+u-1, ip = 2(I+u)+1 and
+        // i0 = 2(I+u) -> I+u
+        const float edges = ((col(a_jm, e_jm, u) + at(a_jm, u)) + (col(a_jp, e_jp, u) + at(a_jp, u))) +
+                            ((col(l_j0, el_j0, u) + at(l_j0, u)) + (col(h_j0, eh_j0, u) + at(h_j0, u))) +
+                            ((at(l_jm, u) + at(l_jp, u)) + (at(h_jm, u) + at(h_jp, u)));
+        o[u] = 4.f * (0.125f * at(a_j0, u) + 0.03125f * edges);
+      }
+      const int ce = (I + J + K) & 1, th = rem >> 1;   // = J Hc + I / 2
+      *reinterpret_cast<float2*>(R.cplane(cv, 1, ce, K) + th) = make_float2(o[0], o[2]);
+      *reinterpret_cast<float2*>(R.cplane(cv, 1, 1 - ce, K) + th) = make_float2(o[1], o[3]);
+      (void)Hc;
+    }
+    return;
+  }
   for (int m = t0; m < count; m += ts) {
     const int kl = fdiv(m, NNc, cv.mNN), rem = m - kl * NNc, J = fdiv(rem, Nc, cv.mN), I = rem - J * Nc;
     const int K = K0 + kl;
@@ -574,6 +615,53 @@ __device__ __forceinline__ void res_prolong(const Slabs& R, int l, int t0, int t
   if (own <= 0) return;
   float* xb = R.sm + f.off + f.P * (f.NN >> 1);
   const int Nc = cv.N, Hc = Nc >> 1, hcount = own * (f.NN >> 1);
+  if (quad_level(f) && cv.split) {
+    // four black points t .. t+3 of a fine row (t a multiple of 4, parity p):
+    // point u reads coarse columns I0 = t + u and I1 = t + u + p of the
+    // coarse rows J in {j0, j1} and planes K in {k0, k1}. Of the coarse
+    // columns t .. t+4 of one (J, K), the even ones lie in colour (J + K) & 1
+    // at half-row indices t/2 .. t/2 + 2 and the odd ones in the other
+    // colour at t/2, t/2 + 1 (8-byte loads; t + 4 wraps to column 0).
+    for (int g = t0; g < (hcount >> 2); g += ts) {
+      const int h = g << 2;
+      int t, j, kl;
+      const int p = colour_point(f, h, 1, t, j, kl);
+      const int k = f.z0 + kl;
+      const int j0 = j >> 1, j1 = (j & 1) ? (j0 + 1 == Nc ? 0 : j0 + 1) : j0;
+      const int k0 = k >> 1, k1 = (k & 1) ? (k0 + 1 == Nc ? 0 : k0 + 1) : k0;
+      const int th = t >> 1, te = t + 4 == Nc ? 0 : th + 2;
+      float V[4][5];   // [(J, K) = (j0,k0), (j1,k0), (j0,k1), (j1,k1)][column t .. t+4]
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int J = (q & 1) ? j1 : j0, K = (q & 2) ? k1 : k0;
+        const int ce = (J + K) & 1;
+        const float* pe = R.cplane(cv, 0, ce, K) + J * Hc;
+        const float* po = R.cplane(cv, 0, 1 - ce, K) + J * Hc;
+        const float2 ev = *reinterpret_cast<const float2*>(pe + th);
+        const float2 od = *reinterpret_cast<const float2*>(po + th);
+        V[q][0] = ev.x;
+        V[q][1] = od.x;
+        V[q][2] = ev.y;
+        V[q][3] = od.y;
+        V[q][4] = p ? pe[te] : 0.f;
+      }
+      float4 x = ld4(xb + h);
+      float o[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        // column I1 is t + u + p (a select: no runtime index into V)
+        const float b0 = p ? V[0][u + 1] : V[0][u], b1 = p ? V[1][u + 1] : V[1][u];
+        const float b2 = p ? V[2][u + 1] : V[2][u], b3 = p ? V[3][u + 1] : V[3][u];
+        o[u] = 0.125f * (((V[0][u] + b0) + (V[1][u] + b1)) + ((V[2][u] + b2) + (V[3][u] + b3)));
+      }
+      x.x += o[0];
+      x.y += o[1];
+      x.z += o[2];
+      x.w += o[3];
+      st4(xb + h, x);
+    }
+    return;
+  }
   for (int h = t0; h < hcount; h += ts) {
     int t, j, kl;
     const int p = colour_point(f, h, 1, t, j, kl);
