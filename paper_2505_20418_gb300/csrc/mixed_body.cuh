@@ -705,30 +705,51 @@ __device__ __forceinline__ void res_prolong(const Slabs& R, int l, int t0, int t
 }
 
 // Coarsest level (in the tail, part 0): the exact zero-mean solve by the
-// pseudo-inverse kernel. The block stages the coarse rhs and the kernel (at
-// most 7^3 values each) in shared memory; one warp per output point splits
-// the sum.
-__device__ __forceinline__ void res_coarsest(const Slabs& R, const float* s_cg, int tid, int stride) {
+// pseudo-inverse kernel. The block stages the coarse rhs (at most 7^3
+// values) in shared memory; s_co holds every coarse point's coordinates
+// packed as i | j << 8 | k << 16 (staged once per solve, no divisions
+// here). A warp computes four output points at once; each output's sum runs
+// over q = lane, lane + 32, ... and then a butterfly over the lanes.
+__device__ __forceinline__ void res_coarsest(const Slabs& R, const float* s_cg, const int* s_co, int tid, int stride) {
   __shared__ float s_cb[343];
   const int l = R.L - 1;
   const RLevel& v = R.lv[l];
   const int Nc = v.N, NNc = v.NN, nc3 = Nc * NNc;
   for (int q = threadIdx.x; q < nc3; q += blockDim.x) {
-    const int qk = q / NNc;
+    const int qk = s_co[q] >> 16;
     s_cb[q] = R.plane(l, 1, qk)[q - qk * NNc];
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int wid = tid >> 5, nwarps = stride >> 5;
-  for (int p = wid; p < nc3; p += nwarps) {
-    const int pk = p / NNc, pj = (p - pk * NNc) / Nc, pi = p - pk * NNc - pj * Nc;
-    float acc = 0.f;
-    for (int q = lane; q < nc3; q += 32) {
-      const int qk = q / NNc, qj = (q - qk * NNc) / Nc, qi = q - qk * NNc - qj * Nc;
-      acc += s_cg[wrapi(pi - qi, Nc) + Nc * (wrapi(pj - qj, Nc) + Nc * wrapi(pk - qk, Nc))] * s_cb[q];
+  for (int p0 = wid; p0 < nc3; p0 += 4 * nwarps) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    int pi[4], pj[4], pk[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = s_co[min(p0 + u * nwarps, nc3 - 1)];
+      pi[u] = c & 255;
+      pj[u] = (c >> 8) & 255;
+      pk[u] = c >> 16;
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) R.plane(l, 0, pk)[pj * Nc + pi] = acc;
+    for (int q = lane; q < nc3; q += 32) {
+      const int c = s_co[q];
+      const int qi = c & 255, qj = (c >> 8) & 255, qk = c >> 16;
+      const float bq = s_cb[q];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        acc[u] += s_cg[wrapi(pi[u] - qi, Nc) + Nc * (wrapi(pj[u] - qj, Nc) + Nc * wrapi(pk[u] - qk, Nc))] * bq;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+    if (lane == 0)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int p = p0 + u * nwarps;
+        if (p < nc3) R.plane(l, 0, pk[u])[pj[u] * Nc + pi[u]] = acc[u];
+      }
   }
 }
 
@@ -873,6 +894,7 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
   const int stride = (int)C * blockDim.x;
   // the coarsest level's pseudo-inverse kernel, staged once per solve
   __shared__ float s_cg[343];
+  __shared__ int s_co[343];
   if (threadIdx.x == 0) {
     if (dsm)
       slabs_setup(R, a, dsm, me, C, true);
@@ -881,7 +903,11 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
   }
   {
     const int Nc = a.Nl[a.L - 1];
-    for (int q = threadIdx.x; q < Nc * Nc * Nc; q += blockDim.x) s_cg[q] = a.gkerf[q];
+    for (int q = threadIdx.x; q < Nc * Nc * Nc; q += blockDim.x) {
+      s_cg[q] = a.gkerf[q];
+      const int qk = q / (Nc * Nc), qj = (q - qk * Nc * Nc) / Nc;
+      s_co[q] = (q - qk * Nc * Nc - qj * Nc) | (qj << 8) | (qk << 16);
+    }
   }
   __syncthreads();
   // the storage must hold the layout (uniform decision: every CTA computes
@@ -946,7 +972,7 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
         res_restrict(R, l, u0, us);
         __syncthreads();
       }
-      res_coarsest(R, s_cg, u0, us);
+      res_coarsest(R, s_cg, s_co, u0, us);
       __syncthreads();
       for (int l = a.L - 2; l >= lt; --l) {
         res_prolong(R, l, u0, us);
