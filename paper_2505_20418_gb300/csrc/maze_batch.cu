@@ -126,6 +126,18 @@ __device__ __forceinline__ int cluster_ld_int(const int* p, unsigned rank) {
   return v;
 }
 
+// Ions [0, n) in C contiguous chunks of a multiple of 32 (one per CTA of the
+// cluster), so that every CTA takes a share of the per-ion work however few
+// ions there are; thread threadIdx.x of CTA rank strides over its chunk.
+struct IonChunk {
+  int lo, hi;
+};
+__device__ __forceinline__ IonChunk ion_chunk(int n, int rank, int C) {
+  const int per = (((n + C - 1) / C) + 31) & ~31;
+  const int lo = min(n, rank * per);
+  return {lo, min(n, lo + per)};
+}
+
 __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_step(BatchArgs b) {
   extern __shared__ __align__(16) unsigned char dyn[];
   CellSmem<kBatchWarps>& csm = *reinterpret_cast<CellSmem<kBatchWarps>*>(dyn);
@@ -169,7 +181,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_step(BatchArgs b) {
     const int n = d.ion.n, nc = d.ion.nc;
     // S1: half kick + drift, weights, cell counts; the direct schemes solve
     // from y = 0
-    for (int i = tid; i < n; i += stride) move_ion(d.ion, i);
+    const IonChunk ch = ion_chunk(n, (int)rank, C);
+    for (int i = ch.lo + (int)threadIdx.x; i < ch.hi; i += blockDim.x) move_ion(d.ion, i);
     if (d.mixed.y_reset)
       for (int m = tid; m < d.mixed.n; m += stride) d.mixed.y[m] = make_float2(0.f, 0.f);
     sync.barrier();
@@ -178,12 +191,13 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_step(BatchArgs b) {
     for (int i = gwarp; i < n; i += nwarps) spread_ion(d.ion, i, lane);
     sync.barrier();
     if (nc >= 3) {
-      for (int i = tid; i < n; i += stride) cell_fill_ion(d.cell, i);
+      for (int i = ch.lo + (int)threadIdx.x; i < ch.hi; i += blockDim.x) cell_fill_ion(d.cell, i);
       sync.barrier();
       // the sort's buffers alias the force staging, which is used only after
       // the solve's barriers
       int* ids = reinterpret_cast<int*>(dyn) + warp * kSortCap;
-      for (int c = gwarp; c < d.cell.ncell; c += nwarps) cell_sort_one(d.cell, c, lane, ids);
+      for (int c = (int)rank + C * warp; c < d.cell.ncell; c += C * (int)(blockDim.x >> 5))
+        cell_sort_one(d.cell, c, lane, ids);
     }
     // S4-S6 (its first barrier also orders the sort before the forces); the
     // resident form reuses the shared memory of the sort and the forces
@@ -245,7 +259,8 @@ __global__ void __launch_bounds__(kMixedClusterThreads, 1) k_cluster_step(IonArg
   if (rank == 0 && threadIdx.x == 0) *ia.gate = skip ? 1 : 0;
   if (skip) return;
   const int n = ia.n, nc = ia.nc;
-  for (int i = tid; i < n; i += stride) move_ion(ia, i);
+  const IonChunk ch = ion_chunk(n, (int)rank, C);
+  for (int i = ch.lo + (int)threadIdx.x; i < ch.hi; i += blockDim.x) move_ion(ia, i);
   if (ma.y_reset)
     for (int m = tid; m < ma.n; m += stride) ma.y[m] = make_float2(0.f, 0.f);
   sync.barrier();
@@ -253,10 +268,10 @@ __global__ void __launch_bounds__(kMixedClusterThreads, 1) k_cluster_step(IonArg
   for (int i = gwarp; i < n; i += nwarps) spread_ion(ia, i, lane);
   sync.barrier();
   if (nc >= 3) {
-    for (int i = tid; i < n; i += stride) cell_fill_ion(ca, i);
+    for (int i = ch.lo + (int)threadIdx.x; i < ch.hi; i += blockDim.x) cell_fill_ion(ca, i);
     sync.barrier();
     int* ids = reinterpret_cast<int*>(dsm) + warp * kSortCap;
-    for (int c = gwarp; c < ca.ncell; c += nwarps) cell_sort_one(ca, c, lane, ids);
+    for (int c = (int)rank + C * warp; c < ca.ncell; c += C * (int)(blockDim.x >> 5)) cell_sort_one(ca, c, lane, ids);
   }
   __syncthreads();
   mixed_body(ma, sync, ma.resident ? dsm : nullptr);

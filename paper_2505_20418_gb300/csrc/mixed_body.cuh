@@ -333,16 +333,17 @@ __host__ __device__ __forceinline__ size_t resident_bytes(const MixedArgs& a, in
   return slab_floats(a, C) * sizeof(float);
 }
 
+// ceil(2^32 / d) for d >= 2 in 32-bit arithmetic: (2^32 - 1) / d + 1.
+__device__ __forceinline__ unsigned ceil_recip32(unsigned d) { return 0xffffffffu / d + 1u; }
+
+// The level descriptors of the slab storage, built by the block's first L
+// threads (one level each; offsets then by a prefix sum in thread 0), then a
+// block barrier.
 __device__ __forceinline__ void slabs_setup(Slabs& R, const MixedArgs& a, float* sm, unsigned me, unsigned Q,
                                             bool dsmem) {
-  R.sm = sm;
-  R.me = me;
-  R.Q = Q;
-  R.L = a.L;
-  R.tail = tail_level(a);
-  R.dsmem = dsmem;
-  unsigned off = 0;
-  for (int l = 0; l < a.L; ++l) {
+  __shared__ unsigned s_size[kMaxLevels];
+  const int l = threadIdx.x;
+  if (l < a.L) {
     RLevel& v = R.lv[l];
     v.N = a.Nl[l];
     v.NN = v.N * v.N;
@@ -350,18 +351,28 @@ __device__ __forceinline__ void slabs_setup(Slabs& R, const MixedArgs& a, float*
     v.lg = a.lg[l];
     v.z0 = min(v.N, (int)me * v.P);
     v.z1 = min(v.N, ((int)me + 1) * v.P);
-    v.off = off;
     // (P = 1 would need 2^32, which does not fit: owner() treats it apart)
-    v.Pinv = v.P > 1 ? (unsigned)((0x100000000ull + (unsigned long long)v.P - 1) / (unsigned long long)v.P) : 0u;
-    auto magic = [&](int d) -> unsigned {
-      return (v.N <= 64 && d > 1) ? (unsigned)((0x100000000ull + (unsigned long long)d - 1) / (unsigned long long)d)
-                                  : 0u;
-    };
+    v.Pinv = v.P > 1 ? ceil_recip32((unsigned)v.P) : 0u;
+    auto magic = [&](int d) -> unsigned { return (v.N <= 64 && d > 1) ? ceil_recip32((unsigned)d) : 0u; };
     v.mH = magic(v.N / 2);
     v.mN = magic(v.N);
     v.mNN = magic(v.NN);
     v.split = l < a.L - 1 ? 1 : 0;
-    off += 2u * (unsigned)(v.P * v.NN) + (l < a.L - 1 ? (unsigned)(v.P * (v.NN / 2)) : 0u);
+    s_size[l] = 2u * (unsigned)(v.P * v.NN) + (l < a.L - 1 ? (unsigned)(v.P * (v.NN / 2)) : 0u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    R.sm = sm;
+    R.me = me;
+    R.Q = Q;
+    R.L = a.L;
+    R.tail = tail_level(a);
+    R.dsmem = dsmem;
+    unsigned off = 0;
+    for (int k = 0; k < a.L; ++k) {
+      R.lv[k].off = off;
+      off += s_size[k];
+    }
   }
 }
 
@@ -895,12 +906,10 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
   // the coarsest level's pseudo-inverse kernel, staged once per solve
   __shared__ float s_cg[343];
   __shared__ int s_co[343];
-  if (threadIdx.x == 0) {
-    if (dsm)
-      slabs_setup(R, a, dsm, me, C, true);
-    else
-      slabs_setup(R, a, a.scratch, 0, 1, false);
-  }
+  if (dsm)
+    slabs_setup(R, a, dsm, me, C, true);
+  else
+    slabs_setup(R, a, a.scratch, 0, 1, false);
   {
     const int Nc = a.Nl[a.L - 1];
     for (int q = threadIdx.x; q < Nc * Nc * Nc; q += blockDim.x) {
