@@ -570,6 +570,63 @@ __device__ __forceinline__ bool grid_reduce(const double (&v)[K], const bool (&i
   return ok;
 }
 
+// Grid-wide sum of one unsigned 64-bit value per thread, modulo 2^64 (exact
+// integer totals; same publication records and epochs as grid_reduce). Every
+// thread of every block gets the total in ``out``.
+__device__ __forceinline__ bool grid_reduce_u64(unsigned long long v, LLRec* recs, unsigned epoch, maze_stats* rec,
+                                                unsigned long long& out) {
+  __shared__ unsigned long long s_w[32];
+  __shared__ unsigned long long s_tot;
+  __shared__ int s_ok;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned long long w = (unsigned long long)warp_isum((long long)v);
+  if (lane == 0) s_w[warp] = w;
+  __syncthreads();
+  LLRec* buf = recs + (size_t)(epoch & 1u) * gridDim.x * 4;
+  if (warp == 0) {
+    if (lane == 0) {
+      unsigned long long S = 0;
+      for (int u = 0; u < nw; ++u) S += s_w[u];
+      ll_store(&buf[blockIdx.x * 4], __longlong_as_double((long long)S), epoch);
+    }
+    constexpr int kMaxPer = kMaxReduceBlocks / 32;
+    double val[kMaxPer];
+    unsigned pending = 0;
+#pragma unroll
+    for (int j = 0; j < kMaxPer; ++j) {
+      val[j] = 0.0;
+      if (lane + 32 * j < (int)gridDim.x) pending |= 1u << j;
+    }
+    int ok = 1;
+    unsigned spins = 0;
+    while (pending) {
+#pragma unroll
+      for (int j = 0; j < kMaxPer; ++j)
+        if ((pending >> j) & 1u)
+          if (ll_load(&buf[(lane + 32 * j) * 4], epoch, val[j])) pending &= ~(1u << j);
+      if (pending && ++spins > kSpinLimit) {
+        ok = 0;
+        break;
+      }
+    }
+    unsigned long long x = 0;
+#pragma unroll
+    for (int j = 0; j < kMaxPer; ++j) x += (unsigned long long)__double_as_longlong(val[j]);
+    const unsigned long long t = (unsigned long long)warp_isum((long long)x);
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0) {
+      if (!ok) atomicCAS(&rec->status, MAZE_OK, MAZE_ERR_TIMEOUT);
+      s_ok = ok;
+      s_tot = t;
+    }
+  }
+  __syncthreads();
+  out = s_tot;
+  const bool ok = s_ok != 0;
+  __syncthreads();
+  return ok;
+}
+
 #endif  // __CUDACC__
 
 }  // namespace maze

@@ -101,6 +101,9 @@ struct GridSync {
   __device__ bool reduce(const double (&v)[K], const bool (&is_max)[K], double (&out)[K]) {
     return grid_reduce<K>(v, is_max, recs, ++epoch, rec, out);
   }
+  __device__ bool reduce_u64(unsigned long long v, unsigned long long& out) {
+    return grid_reduce_u64(v, recs, ++epoch, rec, out);
+  }
 };
 
 // One cluster: barrier.cluster for synchronisation; reductions combine the
@@ -196,6 +199,39 @@ struct ClusterSync {
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < K; ++k) out[k] = s_out[k];
+    parity ^= 1;
+    __syncthreads();
+    return true;
+  }
+  // sum of one unsigned 64-bit value per thread over the cluster, modulo
+  // 2^64 (exact integer total in every thread)
+  __device__ bool reduce_u64(unsigned long long v, unsigned long long& out) {
+    __shared__ unsigned long long s_p[2];   // [parity]: this CTA's partial
+    __shared__ unsigned long long s_w[32];
+    __shared__ unsigned long long s_t;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const unsigned long long w = (unsigned long long)warp_isum((long long)v);
+    if (lane == 0) s_w[warp] = w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long S = 0;
+      for (int u = 0; u < nw; ++u) S += s_w[u];
+      s_p[parity] = S;
+    }
+    barrier();
+    if (warp == 0) {
+      long long a = 0;
+      if (lane < size()) {
+        const unsigned loc = (unsigned)__cvta_generic_to_shared(&s_p[parity]);
+        unsigned r;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(loc), "r"((unsigned)lane));
+        asm volatile("ld.shared::cluster.s64 %0, [%1];" : "=l"(a) : "r"(r) : "memory");
+      }
+      const long long t = warp_isum(a);
+      if (lane == 0) s_t = (unsigned long long)t;
+    }
+    __syncthreads();
+    out = s_t;
     parity ^= 1;
     __syncthreads();
     return true;
@@ -773,42 +809,110 @@ __device__ __forceinline__ void res_coarsest(const Slabs& R, const float* s_cg, 
 // S4 fused with the first outer residual r = sigma_p - M y at the part's
 // level-0 points: phi_p and sigma_p written, r into the V-cycle's level-0
 // right-hand side b0 (red-black order), max|r| and max|y| returned.
+// A point pair (i0, i0 + 1) of a row and the neighbours of both: x- of the
+// first, x+ of the second, and the pairs of the rows j -+ 1 and planes
+// k -+ 1 (16-byte loads; m even).
+struct Pair6 {
+  float2 a, b, xm, xp, jmA, jmB, jpA, jpB, kmA, kmB, kpA, kpB;
+};
+__device__ __forceinline__ Pair6 load_pair6(const float2* __restrict__ x, int m, int xm, int xp, int jm, int jp,
+                                            int km, int kp) {
+  auto ld = [&](int at, float2& u, float2& w) {
+    const float4 v = *reinterpret_cast<const float4*>(x + at);
+    u = make_float2(v.x, v.y);
+    w = make_float2(v.z, v.w);
+  };
+  Pair6 P;
+  ld(m, P.a, P.b);
+  P.xm = x[xm];
+  P.xp = x[xp];
+  ld(jm, P.jmA, P.jmB);
+  ld(jp, P.jpA, P.jpB);
+  ld(km, P.kmA, P.kmB);
+  ld(kp, P.kpA, P.kpB);
+  return P;
+}
+// the six-neighbour double-float sums of the pair, in the order of dsum6
+__device__ __forceinline__ df pair_sumA(const Pair6& P) {
+  return df_add(df_add(df_add(df_from(P.xm), df_from(P.b)), df_add(df_from(P.jmA), df_from(P.jpA))),
+                df_add(df_from(P.kmA), df_from(P.kpA)));
+}
+__device__ __forceinline__ df pair_sumB(const Pair6& P) {
+  return df_add(df_add(df_add(df_from(P.a), df_from(P.xp)), df_add(df_from(P.jmB), df_from(P.jpB))),
+                df_add(df_from(P.kmB), df_from(P.kpB)));
+}
+
+// S4 for one point from its potentials' centre values and neighbour sums:
+// phi_p = 2 phi_k - phi_{k-1} (or phi_k, or 0) and M phi_p.
+__device__ __forceinline__ void s4_php(bool zero_phi, bool static_guess, float2 pk, float2 pm, df nk, df nm, df& php,
+                                       df& Mphp) {
+  php = {0.f, 0.f};
+  Mphp = {0.f, 0.f};
+  if (zero_phi) {
+  } else if (static_guess) {
+    php = df_from(pk);
+    Mphp = df_sub(nk, df_mul_f(php, 6.f));
+  } else {
+    php = df_sub(df_twice(df_from(pk)), df_from(pm));
+    const df s6 = df_sub(df_twice(nk), nm);
+    Mphp = df_sub(s6, df_mul_f(php, 6.f));
+  }
+}
+
+// S4 fused with the first outer residual r = sigma_p - M y at the part's
+// level-0 points: phi_p and sigma_p written, r into the V-cycle's level-0
+// right-hand side b0 (red-black order), max|r| and max|y| returned. A thread
+// takes two x-adjacent points at a time (16-byte loads and stores).
 __device__ __forceinline__ void s4_pass(const RLevel& v0, int t0, int ts, df c_sig, bool zero_phi, bool static_guess,
                                         unsigned long long* __restrict__ qfix, double* __restrict__ q_out,
                                         const float2* __restrict__ phk, const float2* __restrict__ phm,
                                         float2* __restrict__ phout, float2* __restrict__ sig,
                                         const float2* __restrict__ y, float* __restrict__ b0, float& rmax_o,
                                         float& ymax_o) {
-  const int N0 = v0.N, NN0 = v0.NN, cnt0 = (v0.z1 - v0.z0) * NN0, PH0 = v0.P * (NN0 >> 1);
+  const int N0 = v0.N, NN0 = v0.NN, cnt0 = (v0.z1 - v0.z0) * NN0, H0 = N0 >> 1, HH0 = NN0 >> 1;
+  const int PH0 = v0.P * HH0;
   float rmax = 0.f, ymax = 0.f;
-  for (int ml = t0; ml < cnt0; ml += ts) {
-    const int kl = fdiv(ml, NN0, v0.mNN), rem = ml - kl * NN0, j = fdiv(rem, N0, v0.mN), i = rem - j * N0;
-    const int m = (v0.z0 + kl) * NN0 + rem;
-    int q[6];
-    nbr_idx<float>(i, j, v0.z0 + kl, N0, q);
-    const long long qi = (long long)qfix[m];
-    df php = {0.f, 0.f}, Mphp = {0.f, 0.f};
+  for (int g = t0; g < (cnt0 >> 1); g += ts) {
+    const int ml = g << 1;
+    const int kl = fdiv(ml, NN0, v0.mNN), rem = ml - kl * NN0, j = fdiv(rem, N0, v0.mN), i0 = rem - j * N0;
+    const int k = v0.z0 + kl;
+    const int m = k * NN0 + rem;
+    const int xm = i0 == 0 ? m + N0 - 1 : m - 1, xp = i0 + 2 == N0 ? m + 2 - N0 : m + 2;
+    const int jm = j == 0 ? m + NN0 - N0 : m - N0, jp = j == N0 - 1 ? m - NN0 + N0 : m + N0;
+    const int km = k == 0 ? m + NN0 * (N0 - 1) : m - NN0, kp = k == N0 - 1 ? m - NN0 * (N0 - 1) : m + NN0;
+    const ulonglong2 qq = *reinterpret_cast<const ulonglong2*>(qfix + m);
+    const long long qA = (long long)qq.x, qB = (long long)qq.y;
+    df phA, phB, MA, MB;
     if (zero_phi) {
-    } else if (static_guess) {
-      php = df_from(phk[m]);
-      Mphp = df_sub(dsum6(phk, q), df_mul_f(php, 6.f));
+      s4_php(true, false, {}, {}, {}, {}, phA, MA);
+      s4_php(true, false, {}, {}, {}, {}, phB, MB);
     } else {
-      php = df_sub(df_twice(df_from(phk[m])), df_from(phm[m]));
-      const df nk = dsum6(phk, q), nm = dsum6(phm, q);
-      const df s6 = df_sub(df_twice(nk), nm);
-      Mphp = df_sub(s6, df_mul_f(php, 6.f));
+      const Pair6 K6 = load_pair6(phk, m, xm, xp, jm, jp, km, kp);
+      const df nkA = pair_sumA(K6), nkB = pair_sumB(K6);
+      if (static_guess) {
+        s4_php(false, true, K6.a, {}, nkA, {}, phA, MA);
+        s4_php(false, true, K6.b, {}, nkB, {}, phB, MB);
+      } else {
+        const Pair6 M6 = load_pair6(phm, m, xm, xp, jm, jp, km, kp);
+        s4_php(false, false, K6.a, M6.a, nkA, pair_sumA(M6), phA, MA);
+        s4_php(false, false, K6.b, M6.b, nkB, pair_sumB(M6), phB, MB);
+      }
     }
-    const df sg = df_add(df_mul(Mphp, c_sig), df_from_fix(qi));
-    const df ym = df_from(y[m]);
-    const df r = df_sub(sg, df_sub(dsum6(y, q), df_mul_f(ym, 6.f)));
-    const float rf = r.h + r.l;
-    qfix[m] = 0ull;
-    if (q_out) q_out[m] = (double)qi * kQInv;
-    phout[m] = df_to(php);
-    sig[m] = df_to(sg);
-    b0[((i + j + v0.z0 + kl) & 1) * PH0 + (rem >> 1) + kl * (NN0 >> 1)] = rf;
-    ymax = fmaxf(ymax, fabsf(ym.h));
-    rmax = fmaxf(rmax, fabsf(rf));
+    const df sgA = df_add(df_mul(MA, c_sig), df_from_fix(qA)), sgB = df_add(df_mul(MB, c_sig), df_from_fix(qB));
+    const Pair6 Y6 = load_pair6(y, m, xm, xp, jm, jp, km, kp);
+    const df yA = df_from(Y6.a), yB = df_from(Y6.b);
+    const df rA = df_sub(sgA, df_sub(pair_sumA(Y6), df_mul_f(yA, 6.f)));
+    const df rB = df_sub(sgB, df_sub(pair_sumB(Y6), df_mul_f(yB, 6.f)));
+    const float rfA = rA.h + rA.l, rfB = rB.h + rB.l;
+    *reinterpret_cast<ulonglong2*>(qfix + m) = make_ulonglong2(0ull, 0ull);
+    if (q_out) *reinterpret_cast<double2*>(q_out + m) = make_double2((double)qA * kQInv, (double)qB * kQInv);
+    *reinterpret_cast<float4*>(phout + m) = make_float4(phA.h, phA.l, phB.h, phB.l);
+    *reinterpret_cast<float4*>(sig + m) = make_float4(sgA.h, sgA.l, sgB.h, sgB.l);
+    const int c0 = (i0 + j + k) & 1, hb = kl * HH0 + j * H0 + (i0 >> 1);
+    b0[c0 * PH0 + hb] = rfA;
+    b0[(1 - c0) * PH0 + hb] = rfB;
+    ymax = fmaxf(ymax, fmaxf(fabsf(yA.h), fabsf(yB.h)));
+    rmax = fmaxf(rmax, fmaxf(fabsf(rfA), fabsf(rfB)));
   }
   rmax_o = rmax;
   ymax_o = ymax;
@@ -933,7 +1037,6 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
   const df c_sig = {a.c_sig_h, a.c_sig_l};
   const df c_phi = {a.c_phi_h, a.c_phi_l};
   const bool mmax[2] = {true, true};
-  const bool msum[4] = {false, false, false, false};
   const RLevel v0 = R.lv[0];
   const int N0 = v0.N, NN0 = v0.NN, own0 = v0.z1 - v0.z0, cnt0 = own0 * NN0;
   float* e0 = R.sm + v0.off;
@@ -1023,10 +1126,9 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
   }
   // ---- S6: mean of y, exact and independent of how the points are split:
   // every point's hi and lo parts are rounded to one fixed-point grid set by
-  // max|y| over the box (2^-41 of it), the integers are summed modulo 2^64
-  // (the true sum fits), and the sum crosses the domain as four 16-bit chunk
-  // sums, small integers that the reduction adds exactly. Then the
-  // correction phi = phi_p - (4pi/h)(y - mean y) and y -> a.y.
+  // max|y| over the box (2^-41 of it) and the integers are summed modulo
+  // 2^64 across the domain (the true sum fits). Then the correction
+  // phi = phi_p - (4pi/h)(y - mean y) and y -> a.y.
   {
     const int E = dbl_exp(ymax_all) + 11;
     unsigned long long u = 0;
@@ -1041,13 +1143,8 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
           u += (unsigned long long)(dbl_to_fix((double)yv[w].x, E) + dbl_to_fix((double)yv[w].y, E));
       }
     }
-    const double vv[4] = {(double)(u & 0xffffu), (double)((u >> 16) & 0xffffu), (double)((u >> 32) & 0xffffu),
-                          (double)(u >> 48)};
-    double t[4];
-    if (!sync.reduce(vv, msum, t)) return;
-    const unsigned long long tot = (unsigned long long)(long long)t[0] + ((unsigned long long)(long long)t[1] << 16) +
-                                   ((unsigned long long)(long long)t[2] << 32) +
-                                   ((unsigned long long)(long long)t[3] << 48);
+    unsigned long long tot;
+    if (!sync.reduce_u64(u, tot)) return;
     const double ybar = ymax_all > 0.0 ? fix_to_dbl((long long)tot, E) * a.inv_n : 0.0;
     const float ybh = (float)ybar;
     const df yb = {ybh, (float)(ybar - (double)ybh)};
