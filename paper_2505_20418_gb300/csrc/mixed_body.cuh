@@ -435,14 +435,20 @@ __device__ __forceinline__ int colour_point(const RLevel& v, int h, int c, int& 
 // Sum of the six neighbours (all of the other colour, array xo of the part,
 // boundary planes xlo / xhi) of the own point (t, j, kl) with parity p, in the
 // fixed order ((x- + x+) + (y- + y+)) + (z- + z+).
+// (F: transform of each loaded neighbour value; the identity for a sweep)
+struct Ident {
+  __device__ float operator()(float v) const { return v; }
+};
+template <class F = Ident>
 __device__ __forceinline__ float colour_nbr_sum(const float* xo, const float* xlo, const float* xhi, int N, int own,
-                                                int t, int j, int kl, int p) {
+                                                int t, int j, int kl, int p, F f = F()) {
   const int H = N >> 1, HH = H * N;
   const int rowb = kl * HH + j * H;
-  const float sx = xo[rowb + (p ? t : (t == 0 ? H - 1 : t - 1))] + xo[rowb + (p ? (t == H - 1 ? 0 : t + 1) : t)];
-  const float sy = xo[kl * HH + (j == 0 ? N - 1 : j - 1) * H + t] + xo[kl * HH + (j == N - 1 ? 0 : j + 1) * H + t];
-  const float zm = kl > 0 ? xo[rowb - HH + t] : xlo[j * H + t];
-  const float zp = kl < own - 1 ? xo[rowb + HH + t] : xhi[j * H + t];
+  const float sx = f(xo[rowb + (p ? t : (t == 0 ? H - 1 : t - 1))]) + f(xo[rowb + (p ? (t == H - 1 ? 0 : t + 1) : t)]);
+  const float sy =
+      f(xo[kl * HH + (j == 0 ? N - 1 : j - 1) * H + t]) + f(xo[kl * HH + (j == N - 1 ? 0 : j + 1) * H + t]);
+  const float zm = f(kl > 0 ? xo[rowb - HH + t] : xlo[j * H + t]);
+  const float zp = f(kl < own - 1 ? xo[rowb + HH + t] : xhi[j * H + t]);
   return (sx + sy) + (zm + zp);
 }
 
@@ -455,16 +461,18 @@ __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<floa
 // colour_nbr_sum. Their y- and z-neighbours are the other colour's values at
 // the same t (four loads of 16 bytes), their x-neighbours the other colour's
 // t .. t+3 of the row and one more value at t-1 (p = 0) or t+4 (p = 1).
+template <class F = Ident>
 __device__ __forceinline__ float4 colour_nbr_sum4(const float* xo, const float* xlo, const float* xhi, int N, int own,
-                                                  int t, int j, int kl, int p) {
+                                                  int t, int j, int kl, int p, F f = F()) {
   const int H = N >> 1, HH = H * N;
   const int rowb = kl * HH + j * H;
-  const float4 xr = ld4(xo + rowb + t);
-  const float xe = p ? xo[rowb + (t + 4 == H ? 0 : t + 4)] : xo[rowb + (t == 0 ? H - 1 : t - 1)];
-  const float4 ym = ld4(xo + kl * HH + (j == 0 ? N - 1 : j - 1) * H + t);
-  const float4 yp = ld4(xo + kl * HH + (j == N - 1 ? 0 : j + 1) * H + t);
-  const float4 zm = ld4((kl > 0 ? xo + rowb - HH : xlo + j * H) + t);
-  const float4 zp = ld4((kl < own - 1 ? xo + rowb + HH : xhi + j * H) + t);
+  auto f4 = [&](float4 v) { return make_float4(f(v.x), f(v.y), f(v.z), f(v.w)); };
+  const float4 xr = f4(ld4(xo + rowb + t));
+  const float xe = f(p ? xo[rowb + (t + 4 == H ? 0 : t + 4)] : xo[rowb + (t == 0 ? H - 1 : t - 1)]);
+  const float4 ym = f4(ld4(xo + kl * HH + (j == 0 ? N - 1 : j - 1) * H + t));
+  const float4 yp = f4(ld4(xo + kl * HH + (j == N - 1 ? 0 : j + 1) * H + t));
+  const float4 zm = f4(ld4((kl > 0 ? xo + rowb - HH : xlo + j * H) + t));
+  const float4 zp = f4(ld4((kl < own - 1 ? xo + rowb + HH : xhi + j * H) + t));
   const float4 xmn = p ? xr : make_float4(xe, xr.x, xr.y, xr.z);
   const float4 xpl = p ? make_float4(xr.y, xr.z, xr.w, xe) : xr;
   float4 s;
@@ -481,10 +489,10 @@ __device__ __forceinline__ float4 colour_nbr_sum4(const float* xo, const float* 
 __device__ __forceinline__ bool quad_level(const RLevel& v) { return (v.N & 7) == 0; }
 
 // One red-black half-sweep of colour c: x = (sum of the six neighbours - b) / 6
-// at the part's points of that colour (from_zero: the guess is zero, x =
-// -b/6). A thread issues the loads of two points before either store (the
-// loads read the other colour, the stores write this one).
-__device__ __forceinline__ void res_half_sweep(const Slabs& R, int l, int c, bool from_zero, int t0, int ts) {
+// at the part's points of that colour. A thread issues the loads of its
+// points before their stores (the loads read the other colour, the stores
+// write this one).
+__device__ __forceinline__ void res_half_sweep(const Slabs& R, int l, int c, int t0, int ts) {
   const RLevel v = R.lv[l];
   const int own = v.z1 - v.z0;
   if (own <= 0) return;
@@ -494,28 +502,17 @@ __device__ __forceinline__ void res_half_sweep(const Slabs& R, int l, int c, boo
   const float* bc = R.sm + v.off + v.P * v.NN + c * PH;
   const int N = v.N;
   const int hcount = own * (v.NN >> 1);
-  const float* xlo = from_zero ? nullptr : R.cplane(v, 0, 1 - c, (v.z0 - 1 + N) % N);
-  const float* xhi = from_zero ? nullptr : R.cplane(v, 0, 1 - c, v.z1 % N);
+  const float* xlo = R.cplane(v, 0, 1 - c, (v.z0 - 1 + N) % N);
+  const float* xhi = R.cplane(v, 0, 1 - c, v.z1 % N);
   if (quad_level(v)) {
     for (int g = t0; g < (hcount >> 2); g += ts) {
       const int h = g << 2;
       const float4 b = ld4(bc + h);
-      float4 s;
-      if (from_zero) {
-        s = make_float4(0.f, 0.f, 0.f, 0.f);
-      } else {
-        int t, j, kl;
-        const int p = colour_point(v, h, c, t, j, kl);
-        s = colour_nbr_sum4(xo, xlo, xhi, N, own, t, j, kl, p);
-      }
-      float4 o;
-      if (from_zero) {
-        o = make_float4(-b.x * (1.f / 6.f), -b.y * (1.f / 6.f), -b.z * (1.f / 6.f), -b.w * (1.f / 6.f));
-      } else {
-        o = make_float4((s.x - b.x) * (1.f / 6.f), (s.y - b.y) * (1.f / 6.f), (s.z - b.z) * (1.f / 6.f),
-                        (s.w - b.w) * (1.f / 6.f));
-      }
-      st4(xc + h, o);
+      int t, j, kl;
+      const int p = colour_point(v, h, c, t, j, kl);
+      const float4 s = colour_nbr_sum4(xo, xlo, xhi, N, own, t, j, kl, p);
+      st4(xc + h, make_float4((s.x - b.x) * (1.f / 6.f), (s.y - b.y) * (1.f / 6.f), (s.z - b.z) * (1.f / 6.f),
+                              (s.w - b.w) * (1.f / 6.f)));
     }
     return;
   }
@@ -526,18 +523,59 @@ __device__ __forceinline__ void res_half_sweep(const Slabs& R, int l, int c, boo
       const int h = h0 + u * ts;
       val[u] = 0.f;
       if (h < hcount) {
-        if (from_zero) {
-          val[u] = -bc[h] * (1.f / 6.f);
-        } else {
-          int t, j, kl;
-          const int p = colour_point(v, h, c, t, j, kl);
-          val[u] = (colour_nbr_sum(xo, xlo, xhi, N, own, t, j, kl, p) - bc[h]) * (1.f / 6.f);
-        }
+        int t, j, kl;
+        const int p = colour_point(v, h, c, t, j, kl);
+        val[u] = (colour_nbr_sum(xo, xlo, xhi, N, own, t, j, kl, p) - bc[h]) * (1.f / 6.f);
       }
     }
 #pragma unroll
     for (int u = 0; u < 2; ++u)
       if (h0 + u * ts < hcount) xc[h0 + u * ts] = val[u];
+  }
+}
+
+// The first sweep from the zero guess in one phase: the red half-sweep sets
+// x = -b/6 at the red points, and the black half-sweep that follows reads
+// those values, so its red neighbours are formed from b directly (the same
+// products as the red half-sweep computes, hence the same values).
+// (__fmul_rn: the product is rounded on its own, never contracted into the
+// sum that follows, exactly as the stored red values are.)
+struct NegSixth {
+  __device__ float operator()(float v) const { return __fmul_rn(-v, 1.f / 6.f); }
+};
+__device__ __forceinline__ void res_first_sweep(const Slabs& R, int l, int t0, int ts) {
+  const RLevel v = R.lv[l];
+  const int own = v.z1 - v.z0;
+  if (own <= 0) return;
+  const int PH = v.P * (v.NN >> 1);
+  float* xr = R.sm + v.off;
+  float* xb = xr + PH;
+  const float* br = R.sm + v.off + v.P * v.NN;
+  const float* bb = br + PH;
+  const int N = v.N;
+  const int hcount = own * (v.NN >> 1);
+  const float* blo = R.cplane(v, 1, 0, (v.z0 - 1 + N) % N);
+  const float* bhi = R.cplane(v, 1, 0, v.z1 % N);
+  const NegSixth f;
+  if (quad_level(v)) {
+    for (int g = t0; g < (hcount >> 2); g += ts) {
+      const int h = g << 2;
+      const float4 r = ld4(br + h);
+      st4(xr + h, make_float4(f(r.x), f(r.y), f(r.z), f(r.w)));
+      int t, j, kl;
+      const int p = colour_point(v, h, 1, t, j, kl);
+      const float4 s = colour_nbr_sum4(br, blo, bhi, N, own, t, j, kl, p, f);
+      const float4 b = ld4(bb + h);
+      st4(xb + h, make_float4((s.x - b.x) * (1.f / 6.f), (s.y - b.y) * (1.f / 6.f), (s.z - b.z) * (1.f / 6.f),
+                              (s.w - b.w) * (1.f / 6.f)));
+    }
+    return;
+  }
+  for (int h = t0; h < hcount; h += ts) {
+    xr[h] = f(br[h]);
+    int t, j, kl;
+    const int p = colour_point(v, h, 1, t, j, kl);
+    xb[h] = (colour_nbr_sum(br, blo, bhi, N, own, t, j, kl, p, f) - bb[h]) * (1.f / 6.f);
   }
 }
 
@@ -1061,9 +1099,11 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
     // across the sync domain, the tail in one CTA
     const int lt = R.tail;
     for (int l = 0; l < lt; ++l) {
-      for (int s = 0; s < a.nu1; ++s)
+      res_first_sweep(R, l, t0, ts);
+      if (!sync.barrier()) return;
+      for (int s = 1; s < a.nu1; ++s)
         for (int c = 0; c < 2; ++c) {
-          res_half_sweep(R, l, c, s == 0 && c == 0, t0, ts);
+          res_half_sweep(R, l, c, t0, ts);
           if (!sync.barrier()) return;
         }
       res_residual(R, l, t0, ts);
@@ -1074,9 +1114,11 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
     if (sync.rank() == 0) {
       const int u0 = threadIdx.x, us = blockDim.x;
       for (int l = lt; l < a.L - 1; ++l) {
-        for (int s = 0; s < a.nu1; ++s)
+        res_first_sweep(R, l, u0, us);
+        __syncthreads();
+        for (int s = 1; s < a.nu1; ++s)
           for (int c = 0; c < 2; ++c) {
-            res_half_sweep(R, l, c, s == 0 && c == 0, u0, us);
+            res_half_sweep(R, l, c, u0, us);
             __syncthreads();
           }
         res_residual(R, l, u0, us);
@@ -1091,7 +1133,7 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
         __syncthreads();
         for (int s = 0; s < a.nu2; ++s)
           for (int c = 0; c < 2; ++c) {
-            res_half_sweep(R, l, c, false, u0, us);
+            res_half_sweep(R, l, c, u0, us);
             __syncthreads();
           }
       }
@@ -1102,7 +1144,7 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
       if (!sync.barrier()) return;
       for (int s = 0; s < a.nu2; ++s)
         for (int c = 0; c < 2; ++c) {
-          res_half_sweep(R, l, c, false, t0, ts);
+          res_half_sweep(R, l, c, t0, ts);
           if (!sync.barrier()) return;
         }
     }
