@@ -686,8 +686,15 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
       AL(c->rel_lo_s, (size_t)n);
     }
   }
-  AL(c->fpart, (size_t)std::max(c->fblocks, c->ncell * c->cell_split) * 8);
-  AL(c->ticket, 4);
+  {
+    // block partials, then group partials; a ticket per group after the
+    // global one (the force kernel's two-level energy combine)
+    const size_t G = (size_t)std::max(c->fblocks, c->ncell * c->cell_split);
+    const size_t ngroups = (G + kEnergyGroup - 1) / kEnergyGroup;
+    AL(c->fpart, (G + ngroups) * 8);
+    AL(c->ticket, ngroups + 4);
+    c->ticket_count = ngroups + 4;
+  }
   AL(c->rec, 1);
   AL(c->gate, 1);
 #undef AL
@@ -740,7 +747,7 @@ maze_status ctx_create(const maze_config* cfg, Arena* arena, maze_ctx** out) {
   CKC(cudaMemsetAsync(c->phi[1], 0, ng * 8, st));
   CKC(cudaMemsetAsync(c->phi[2], 0, ng * 8, st));
   CKC(cudaMemsetAsync(c->rec, 0, sizeof(maze_stats), st));
-  CKC(cudaMemsetAsync(c->ticket, 0, 4, st));
+  CKC(cudaMemsetAsync(c->ticket, 0, c->ticket_count * sizeof(unsigned), st));
   CKC(cudaMemsetAsync(c->gate, 0, 4, st));
   if (c->nc >= 3) CKC(cudaMemsetAsync(c->cell_count, 0, (size_t)c->ncell * 4, st));
   CKC(cudaStreamSynchronize(st));

@@ -86,6 +86,7 @@ struct maze_ctx {
   // force reductions
   double* fpart = nullptr;
   unsigned* ticket = nullptr;
+  size_t ticket_count = 0;
   int fblocks = 0;
   int num_sms = 0;
   maze_stats* rec = nullptr;       // device

@@ -24,6 +24,7 @@ constexpr int kMaxReduceBlocks = 256;
 
 constexpr int kSolveThreads = 256;
 constexpr int kForceThreads = 256;   // 8 ions (one warp each) per block
+constexpr int kEnergyGroup = 128;    // force blocks per group of the two-level energy combine
 constexpr int kIonThreads = 128;
 constexpr int kSpreadThreads = 256;  // 8 ions (one warp each) per block
 

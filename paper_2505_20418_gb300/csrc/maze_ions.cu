@@ -66,18 +66,68 @@ cudaError_t launch_cells(const CellArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Exact sum (integer fixed point at the largest exponent + 16, see
+// grid_reduce) of the seven values of partials [first, first + count) of
+// part (8 doubles per partial), by all threads of the block; every thread
+// gets the seven totals, each rounded once to a double.
+__device__ __forceinline__ void combine_partials(const double* part, int first, int count, double (&tot)[7]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ int c_e[32][8];
+  __shared__ long long c_s[32][8];
+  __shared__ int c_E[8];
+  __shared__ double c_tot[8];
+  int e[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int bb = threadIdx.x; bb < count; bb += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 7; ++k) e[k] = max(e[k], dbl_exp(__ldcg(&part[(first + bb) * 8 + k])));
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    const int m = (int)__reduce_max_sync(0xffffffffu, (unsigned)e[k]);
+    if (lane == 0) c_e[warp][k] = m;
+  }
+  __syncthreads();
+  if (warp == 0 && lane < 7) {
+    int m = 0;
+    for (int u = 0; u < nw; ++u) m = max(m, c_e[u][lane]);
+    c_E[lane] = m + 16;   // up to 2^25 partials
+  }
+  __syncthreads();
+  long long x[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int bb = threadIdx.x; bb < count; bb += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 7; ++k) x[k] += dbl_to_fix(__ldcg(&part[(first + bb) * 8 + k]), c_E[k]);
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    const long long S = warp_isum(x[k]);
+    if (lane == 0) c_s[warp][k] = S;
+  }
+  __syncthreads();
+  if (warp == 0 && lane < 7) {
+    long long S = 0;
+    for (int u = 0; u < nw; ++u) S += c_s[u][lane];
+    c_tot[lane] = fix_to_dbl(S, c_E[lane]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 7; ++k) tot[k] = c_tot[k];
+  __syncthreads();
+}
+
 // Deterministic energy sums: every thread holds the terms of the ions it
 // finished; the block sums them exactly (integer fixed point, see
-// grid_reduce), the last block to finish combines all block partials the
-// same way and publishes the step record. The seven values are combined one
-// per lane, and the last block sweeps the partials with all of its threads.
+// grid_reduce) and rounds the block's sums once; the last block to finish
+// combines all block partials the same way and publishes the step record.
+// Large grids (more than 2 kEnergyGroup blocks) combine in two
+// levels: the last block of each group of kEnergyGroup blocks combines its
+// group into a group partial, the last group combines the groups, so that no
+// single block sweeps every partial. ticket[0] counts groups (or blocks),
+// ticket[1 + g] the blocks of group g; all reset by their last user.
 __device__ __forceinline__ void energy_reduce(const ForceArgs& a, const double (&acc)[7]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __shared__ int s_e[32][8];
   __shared__ long long s_s[32][8];
   __shared__ int s_E[8];
-  __shared__ double s_tot[8];
-  __shared__ bool s_last;
+  __shared__ int s_last;
 #pragma unroll
   for (int k = 0; k < 7; ++k) {
     const int e = (int)__reduce_max_sync(0xffffffffu, (unsigned)dbl_exp(acc[k]));
@@ -96,6 +146,10 @@ __device__ __forceinline__ void energy_reduce(const ForceArgs& a, const double (
     if (lane == 0) s_s[warp][k] = S;
   }
   __syncthreads();
+  const int G = gridDim.x;
+  const bool two_level = G > 2 * kEnergyGroup;
+  const int ngroups = (G + kEnergyGroup - 1) / kEnergyGroup;
+  const int g = blockIdx.x / kEnergyGroup;
   if (warp == 0) {
     if (lane < 7) {
       long long S = 0;
@@ -105,48 +159,36 @@ __device__ __forceinline__ void energy_reduce(const ForceArgs& a, const double (
     }
     __syncwarp();
     if (lane == 0) {
-      const unsigned tk = atomicAdd(a.ticket, 1u);
-      s_last = (tk == gridDim.x - 1);
+      if (two_level) {
+        const int gsize = min(kEnergyGroup, G - g * kEnergyGroup);
+        s_last = atomicAdd(&a.ticket[1 + g], 1u) == (unsigned)(gsize - 1) ? 1 : 0;
+      } else {
+        s_last = atomicAdd(a.ticket, 1u) == (unsigned)(G - 1) ? 2 : 0;
+      }
     }
   }
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  const int G = gridDim.x;
-  int e[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (int bb = threadIdx.x; bb < G; bb += blockDim.x)
-#pragma unroll
-    for (int k = 0; k < 7; ++k) e[k] = max(e[k], dbl_exp(__ldcg(&a.part[bb * 8 + k])));
-#pragma unroll
-  for (int k = 0; k < 7; ++k) {
-    const int m = (int)__reduce_max_sync(0xffffffffu, (unsigned)e[k]);
-    if (lane == 0) s_e[warp][k] = m;
+  double tot[7];
+  if (s_last == 1) {
+    // the group's last block: its group partial, then the group ticket
+    const int gsize = min(kEnergyGroup, G - g * kEnergyGroup);
+    combine_partials(a.part, g * kEnergyGroup, gsize, tot);
+    if (threadIdx.x == 0) {
+      a.ticket[1 + g] = 0;
+      for (int k = 0; k < 7; ++k) a.part[(G + g) * 8 + k] = tot[k];
+      __threadfence();
+      s_last = atomicAdd(a.ticket, 1u) == (unsigned)(ngroups - 1) ? 2 : 0;
+    }
+    __syncthreads();
+    if (s_last != 2) return;
+    __threadfence();
+    combine_partials(a.part, G, ngroups, tot);
+  } else {
+    combine_partials(a.part, 0, G, tot);
   }
-  __syncthreads();
-  if (warp == 0 && lane < 7) {
-    int m = 0;
-    for (int u = 0; u < nw; ++u) m = max(m, s_e[u][lane]);
-    s_E[lane] = m + 16;   // up to 2^16 partials
-  }
-  __syncthreads();
-  long long x[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (int bb = threadIdx.x; bb < G; bb += blockDim.x)
-#pragma unroll
-    for (int k = 0; k < 7; ++k) x[k] += dbl_to_fix(__ldcg(&a.part[bb * 8 + k]), s_E[k]);
-#pragma unroll
-  for (int k = 0; k < 7; ++k) {
-    const long long S = warp_isum(x[k]);
-    if (lane == 0) s_s[warp][k] = S;
-  }
-  __syncthreads();
-  if (warp == 0 && lane < 7) {
-    long long S = 0;
-    for (int u = 0; u < nw; ++u) S += s_s[u][lane];
-    s_tot[lane] = fix_to_dbl(S, s_E[lane]);
-  }
-  __syncthreads();
   if (threadIdx.x == 0) {
-    const double* tot = s_tot;
     maze_stats* r = a.rec;
     *a.ticket = 0;
     if (*a.gate == 0 && (r->status == MAZE_OK || r->status == MAZE_ERR_NOT_CONVERGED)) {
