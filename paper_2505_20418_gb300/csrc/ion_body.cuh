@@ -215,7 +215,9 @@ __device__ __forceinline__ void spread_ion(const IonArgs& a, int i, int lane) {
   for (int u = 0; u < 2; ++u) {
     const int sidx = lane + 32 * u;
     if (sidx >= P3) continue;
-    const int ia = sidx % P, ib = (sidx / P) % P, ic = sidx / (P * P);
+    // P is 2 or 4: sidx = ia + P (ib + P ic) by shifts
+    const int lp = P == 4 ? 2 : 1;
+    const int ia = sidx & (P - 1), ib = (sidx >> lp) & (P - 1), ic = sidx >> (2 * lp);
     if (a.wbuf32) {
       // mixed precision: FP32 products
       const float* w = a.wbuf32 + (size_t)i * 12;
@@ -431,7 +433,10 @@ __device__ __forceinline__ void gather_el(const ForceArgs& a, int i, int lane, d
   const int4 first = a.wbase[i];
   const int P3 = P * P * P;
   gx = gy = gz = vd = 0;
-  const size_t NN = (size_t)N * N;
+  // P is 2 or 4: support index sidx = ia + P (ib + P ic) by shifts; grid
+  // indices fit 32 bits (N <= 1024)
+  const int lp = P == 4 ? 2 : 1;
+  const int NN = N * N;
   if (a.gradw) {
     // Eq. F_Benoit: sum_n grad W phi_n; returned as 2 sum_n (dW/dt) phi_n so
     // that the common prefactor -k_e Q / 2h gives -k_e Q sum_n grad W phi_n
@@ -441,9 +446,9 @@ __device__ __forceinline__ void gather_el(const ForceArgs& a, int i, int lane, d
       const float2* f = reinterpret_cast<const float2*>(a.phi);
       float sx = 0.f, sy = 0.f, sz = 0.f, s0 = 0.f;
       for (int sidx = lane; sidx < P3; sidx += 32) {
-        const int ia = sidx % P, ib = (sidx / P) % P, ic = sidx / (P * P);
+        const int ia = sidx & (P - 1), ib = (sidx >> lp) & (P - 1), ic = sidx >> (2 * lp);
         const int ix = wrap_idx(first.x + ia, N), iy = wrap_idx(first.y + ib, N), iz = wrap_idx(first.z + ic, N);
-        const float2 c0 = f[iz * NN + (size_t)iy * N + ix];
+        const float2 c0 = f[iz * NN + iy * N + ix];
         const float ph = c0.x + c0.y;
         const float wyz = w[4 + ib] * w[8 + ic];
         sx += d[ia] * wyz * ph;
@@ -465,9 +470,9 @@ __device__ __forceinline__ void gather_el(const ForceArgs& a, int i, int lane, d
       const double* w = a.wbuf + (size_t)i * 12;
       const double* d = a.wdbuf + (size_t)i * 12;
       for (int sidx = lane; sidx < P3; sidx += 32) {
-        const int ia = sidx % P, ib = (sidx / P) % P, ic = sidx / (P * P);
+        const int ia = sidx & (P - 1), ib = (sidx >> lp) & (P - 1), ic = sidx >> (2 * lp);
         const int ix = wrap_idx(first.x + ia, N), iy = wrap_idx(first.y + ib, N), iz = wrap_idx(first.z + ic, N);
-        const size_t at = iz * NN + (size_t)iy * N + ix;
+        const int at = iz * NN + iy * N + ix;
         double ph;
         if (a.phi_df) {
           const float2 c0 = reinterpret_cast<const float2*>(a.phi)[at];
@@ -495,15 +500,15 @@ __device__ __forceinline__ void gather_el(const ForceArgs& a, int i, int lane, d
     const float2* f = reinterpret_cast<const float2*>(a.phi);
     float sx = 0.f, sy = 0.f, sz = 0.f, s0 = 0.f;
     for (int sidx = lane; sidx < P3; sidx += 32) {
-      const int ia = sidx % P, ib = (sidx / P) % P, ic = sidx / (P * P);
+      const int ia = sidx & (P - 1), ib = (sidx >> lp) & (P - 1), ic = sidx >> (2 * lp);
       const int ix = wrap_idx(first.x + ia, N), iy = wrap_idx(first.y + ib, N), iz = wrap_idx(first.z + ic, N);
       const float wt = w[ia] * w[4 + ib] * w[8 + ic];
-      const size_t row = iz * NN + (size_t)iy * N;
+      const int row = iz * NN + iy * N;
       const float2 xp = f[row + (ix == N - 1 ? 0 : ix + 1)], xm = f[row + (ix == 0 ? N - 1 : ix - 1)];
-      const float2 yp = f[iz * NN + (size_t)(iy == N - 1 ? 0 : iy + 1) * N + ix];
-      const float2 ym = f[iz * NN + (size_t)(iy == 0 ? N - 1 : iy - 1) * N + ix];
-      const float2 zp = f[(size_t)(iz == N - 1 ? 0 : iz + 1) * NN + (size_t)iy * N + ix];
-      const float2 zm = f[(size_t)(iz == 0 ? N - 1 : iz - 1) * NN + (size_t)iy * N + ix];
+      const float2 yp = f[iz * NN + (iy == N - 1 ? 0 : iy + 1) * N + ix];
+      const float2 ym = f[iz * NN + (iy == 0 ? N - 1 : iy - 1) * N + ix];
+      const float2 zp = f[(iz == N - 1 ? 0 : iz + 1) * NN + iy * N + ix];
+      const float2 zm = f[(iz == 0 ? N - 1 : iz - 1) * NN + iy * N + ix];
       const float2 c0 = f[row + ix];
       sx += wt * ((xp.x - xm.x) + (xp.y - xm.y));
       sy += wt * ((yp.x - ym.x) + (yp.y - ym.y));
@@ -523,15 +528,15 @@ __device__ __forceinline__ void gather_el(const ForceArgs& a, int i, int lane, d
   } else {
     const double* w = a.wbuf + (size_t)i * 12;
     for (int sidx = lane; sidx < P3; sidx += 32) {
-      const int ia = sidx % P, ib = (sidx / P) % P, ic = sidx / (P * P);
+      const int ia = sidx & (P - 1), ib = (sidx >> lp) & (P - 1), ic = sidx >> (2 * lp);
       const int ix = wrap_idx(first.x + ia, N), iy = wrap_idx(first.y + ib, N), iz = wrap_idx(first.z + ic, N);
       const double wt = w[ia] * w[4 + ib] * w[8 + ic];
-      const size_t row = iz * NN + (size_t)iy * N;
-      const size_t ixp = row + (ix == N - 1 ? 0 : ix + 1), ixm = row + (ix == 0 ? N - 1 : ix - 1);
-      const size_t iyp = iz * NN + (size_t)(iy == N - 1 ? 0 : iy + 1) * N + ix;
-      const size_t iym = iz * NN + (size_t)(iy == 0 ? N - 1 : iy - 1) * N + ix;
-      const size_t izp = (size_t)(iz == N - 1 ? 0 : iz + 1) * NN + (size_t)iy * N + ix;
-      const size_t izm = (size_t)(iz == 0 ? N - 1 : iz - 1) * NN + (size_t)iy * N + ix;
+      const int row = iz * NN + iy * N;
+      const int ixp = row + (ix == N - 1 ? 0 : ix + 1), ixm = row + (ix == 0 ? N - 1 : ix - 1);
+      const int iyp = iz * NN + (iy == N - 1 ? 0 : iy + 1) * N + ix;
+      const int iym = iz * NN + (iy == 0 ? N - 1 : iy - 1) * N + ix;
+      const int izp = (iz == N - 1 ? 0 : iz + 1) * NN + iy * N + ix;
+      const int izm = (iz == 0 ? N - 1 : iz - 1) * NN + iy * N + ix;
       double px, py, pz, p0;
       if (a.phi_df) {
         // double-float potential: differences of the (hi, lo) pairs in FP32
@@ -771,7 +776,10 @@ __device__ __forceinline__ void forces_cell_slice(const ForceArgs& a, int c, int
         const int slot = sm.lo[k] + (tt - sm.cum[k]);
         if (a.mixed) {
           // neighbour offset (dx, dy, dz) * cell_len folded into hi/lo
-          const float ox = (float)(k % S - R), oy = (float)((k / S) % S - R), oz = (float)(k / (S * S) - R);
+          // (reach 1, the usual case: constant divisors)
+          const int kx = S == 3 ? k % 3 : k % S, ky = S == 3 ? (k / 3) % 3 : (k / S) % S,
+                    kz = S == 3 ? k / 9 : k / (S * S);
+          const float ox = (float)(kx - R), oy = (float)(ky - R), oz = (float)(kz - R);
           const float4 h = a.rel_hi_sorted[slot], l = a.rel_lo_sorted[slot];
           float4 hh, ll;
           // TwoSum of each coordinate with the offset's hi part
