@@ -82,9 +82,9 @@ enum { MAZE_FORCE_CD = 0, MAZE_FORCE_GRADW = 1 };
  *
  * n_ions      number of ions N_p (>= 2)
  * grid_N      grid points per box edge N (even, 8 <= N <= 1024); with
- *             MAZE_SOLVER_MG, halving N while it is even and >= 8 must end
- *             at an edge <= 7 (the exactly solved coarsest level), e.g. 16,
- *             32, 48, 56, 64, 128, 256; otherwise MAZE_ERR_INVALID
+ *             MAZE_SOLVER_MG, halving N while it is even and above 8 must
+ *             end at an edge <= 8 (the exactly solved coarsest level), e.g.
+ *             16, 32, 40, 48, 56, 64, 128, 256; otherwise MAZE_ERR_INVALID
  * box_L       cubic box edge L in Angstrom; grid spacing h = L / N
  * pos, vel    [n_ions * 3] x,y,z per ion (Angstrom, Angstrom/fs); pos may lie
  *             outside [0, L) and is wrapped

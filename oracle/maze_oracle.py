@@ -262,9 +262,12 @@ def plcg(b, y0, tol, max_iter=10000):
 # --- multigrid (Sec. III.A) --------------------------------------------------
 
 def mg_levels(N: int):
-    """Grid sizes of the hierarchy: halve while the size is even and >= 8."""
+    """Grid sizes of the hierarchy: halve while the size is even and above 8
+    (an 8^3 grid once, so that there are at least two levels); the coarsest
+    level, of at most 8^3 points, is solved exactly. Sec. III.A leaves the
+    depth of the hierarchy open."""
     sizes = [N]
-    while sizes[-1] % 2 == 0 and sizes[-1] >= 8:
+    while sizes[-1] % 2 == 0 and (sizes[-1] > 8 or (sizes[-1] == 8 and len(sizes) == 1)):
         sizes.append(sizes[-1] // 2)
     return sizes
 
@@ -324,16 +327,18 @@ def coarse_cg(b, tol):
     return y - y.mean()
 
 
-def vcycle(x, b, tol, nu1=2, nu2=2):
-    """One V-cycle for M x = b on the hierarchy of ``mg_levels``."""
-    N = x.shape[0]
-    if len(mg_levels(N)) == 1:
+def vcycle(x, b, tol, nu1=2, nu2=2, levels=None):
+    """One V-cycle for M x = b on the hierarchy ``levels`` (default
+    ``mg_levels`` of the grid), finest first."""
+    if levels is None:
+        levels = mg_levels(x.shape[0])
+    if len(levels) == 1:
         return coarse_cg(b, tol)
     for _ in range(nu1):
         x = rbgs_sweep(x, b)
     r = b - apply_M(x)
     bc = 4.0 * restrict_fw(r)        # M is h^2-scaled: coarse rhs picks up (2h/h)^2
-    ec = vcycle(np.zeros_like(bc), bc, tol, nu1, nu2)
+    ec = vcycle(np.zeros_like(bc), bc, tol, nu1, nu2, levels[1:])
     x = x + prolong_trilinear(ec)
     for _ in range(nu2):
         x = rbgs_sweep(x, b)

@@ -56,6 +56,12 @@ maze_status dalloc(maze_ctx* c, T** p, size_t count) {
   return MAZE_OK;
 }
 
+// Whether the multigrid hierarchy halves level L - 1 of edge N once more:
+// while the edge is even and above 8, and an 8^3 finest level once (so that
+// every hierarchy has at least two levels). The coarsest level, of at most
+// 8^3 points, is solved exactly.
+bool mg_halves(int N, int L) { return N % 2 == 0 && (N > 8 || (N == 8 && L == 1)); }
+
 maze_status validate(const maze_config* c) {
   if (!c) return fail(MAZE_ERR_INVALID, "config is NULL");
   if (c->n_ions < 2) return fail(MAZE_ERR_INVALID, "n_ions must be >= 2");
@@ -72,12 +78,12 @@ maze_status validate(const maze_config* c) {
   if (c->solver == MAZE_SOLVER_MG && (c->mg_pre < 1 || c->mg_post < 1 || c->mg_pre > 8 || c->mg_post > 8))
     return fail(MAZE_ERR_INVALID, "mg_pre and mg_post must be in [1, 8]");
   if (c->solver == MAZE_SOLVER_MG) {
-    // the hierarchy halves the edge while it is even and >= 8; its coarsest
-    // level is solved exactly by a dense kernel of at most 7^3 points
+    // the hierarchy halves the edge while it is even and above 8; its
+    // coarsest level is solved exactly by a dense kernel of at most 8^3 points
     int Nc = c->grid_N;
-    while (Nc % 2 == 0 && Nc >= 8) Nc /= 2;
-    if (Nc > 7)
-      return fail(MAZE_ERR_INVALID, "multigrid needs grid_N = m * 2^k with a coarsest edge m <= 7 (e.g. 32, 48, 56)");
+    for (int L = 1; mg_halves(Nc, L); ++L) Nc /= 2;
+    if (Nc > 8)
+      return fail(MAZE_ERR_INVALID, "multigrid needs grid_N = m * 2^k with a coarsest edge m <= 8 (e.g. 32, 48, 56)");
   }
   if (c->order_P != 2 && c->order_P != 4) return fail(MAZE_ERR_INVALID, "order_P must be 2 or 4");
   if (c->precision != MAZE_FP64 && c->precision != MAZE_MIXED)
@@ -605,7 +611,7 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
   AL(c->bar, 4);
   std::vector<double>& gk = c->gk;
   if (cfg->solver == MAZE_SOLVER_MG) {
-    // hierarchy: halve while the edge is even and >= 8
+    // hierarchy: halve while the edge is even and above 8 (an 8^3 box: once)
     MgArgs& g = c->mg;
     g.L = 0;
     size_t tot = 0;
@@ -614,7 +620,7 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
       g.off[g.L] = tot;
       tot += (size_t)N * N * N;
       ++g.L;
-      if (!(N % 2 == 0 && N >= 8) || g.L == kMaxLevels) break;
+      if (!mg_halves(N, g.L) || g.L == kMaxLevels) break;
     }
     g.nu1 = cfg->mg_pre;
     g.nu2 = cfg->mg_post;

@@ -6,12 +6,12 @@
 //       V-cycle (Eqs. SHAKEy, res_poisson_maze)
 //   S6  phi^{k+1} = phi_p - (4pi/h)(y - mean y)                          (Eq. SHAKEPhiFinal)
 //
-// V-cycle on levels l = 0..L-1 (N_l halves while even and >= 8), operators of
+// V-cycle on levels l = 0..L-1 (N_l halves while even and above 8), operators of
 // Sec. III.A: nu1 red-black Gauss-Seidel sweeps (red = i+j+k even; a point is
 // set to (sum of its six neighbours - b)/6), residual r = b - M x, coarse rhs
 // 4 * (27-point full weighting of r) (M is h^2-scaled), recursion from a zero
 // coarse guess, trilinear prolongation of the coarse correction, nu2 sweeps.
-// The coarsest grid (at most 7^3 points) is solved exactly: the paper runs CG
+// The coarsest grid (at most 8^3 points) is solved exactly: the paper runs CG
 // to convergence there; here the exact zero-mean solution is one product with
 // the pseudo-inverse of the circulant coarsest M, a periodic convolution
 // kernel g computed once on the host from M's eigenvalues.

@@ -789,14 +789,16 @@ __device__ __forceinline__ void res_prolong(const Slabs& R, int l, int t0, int t
   }
 }
 
-// Coarsest level (in the tail, part 0): the exact zero-mean solve by the
-// pseudo-inverse kernel. The block stages the coarse rhs (at most 7^3
-// values) in shared memory; s_co holds every coarse point's coordinates
-// packed as i | j << 8 | k << 16 (staged once per solve, no divisions
-// here). A warp computes four output points at once; each output's sum runs
-// over q = lane, lane + 32, ... and then a butterfly over the lanes.
-__device__ __forceinline__ void res_coarsest(const Slabs& R, const float* s_cg, const int* s_co, int tid, int stride) {
-  __shared__ float s_cb[343];
+// Coarsest level: the exact zero-mean solve by the pseudo-inverse kernel
+// (at most 8^3 points). s_co holds every coarse point's coordinates packed
+// as i | j << 8 | k << 16 (staged once per solve, no divisions here); s_cb
+// receives the coarse rhs. Outputs [plo, phi) are computed by this CTA (all
+// of them when one CTA runs the tail; a share of them when the coarsest
+// level is split over the sync domain). A warp computes four outputs at
+// once; each output's sum runs over q = lane, lane + 32, ... and then a
+// butterfly over the lanes.
+__device__ __forceinline__ void res_coarsest(const Slabs& R, const float* s_cg, const int* s_co, float* s_cb, int plo,
+                                             int phi) {
   const int l = R.L - 1;
   const RLevel& v = R.lv[l];
   const int Nc = v.N, NNc = v.NN, nc3 = Nc * NNc;
@@ -806,13 +808,13 @@ __device__ __forceinline__ void res_coarsest(const Slabs& R, const float* s_cg, 
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int wid = tid >> 5, nwarps = stride >> 5;
-  for (int p0 = wid; p0 < nc3; p0 += 4 * nwarps) {
+  const int wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int p0 = plo + wid; p0 < phi; p0 += 4 * nwarps) {
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     int pi[4], pj[4], pk[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int c = s_co[min(p0 + u * nwarps, nc3 - 1)];
+      const int c = s_co[min(p0 + u * nwarps, phi - 1)];
       pi[u] = c & 255;
       pj[u] = (c >> 8) & 255;
       pk[u] = c >> 16;
@@ -833,7 +835,7 @@ __device__ __forceinline__ void res_coarsest(const Slabs& R, const float* s_cg, 
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int p = p0 + u * nwarps;
-        if (p < nc3) R.plane(l, 0, pk[u])[pj[u] * Nc + pi[u]] = acc[u];
+        if (p < phi) R.plane(l, 0, pk[u])[pj[u] * Nc + pi[u]] = acc[u];
       }
   }
 }
@@ -1046,8 +1048,9 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
   const int tid = (int)me * blockDim.x + threadIdx.x;
   const int stride = (int)C * blockDim.x;
   // the coarsest level's pseudo-inverse kernel, staged once per solve
-  __shared__ float s_cg[343];
-  __shared__ int s_co[343];
+  __shared__ float s_cg[512];
+  __shared__ int s_co[512];
+  __shared__ float s_cb[512];
   if (dsm)
     slabs_setup(R, a, dsm, me, C, true);
   else
@@ -1111,7 +1114,14 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
       res_restrict(R, l, t0, ts);
       if (!sync.barrier()) return;
     }
-    if (sync.rank() == 0) {
+    if (lt == a.L - 1) {
+      // the coarsest level alone below the domain's levels: its exact solve
+      // split over the domain (part p computes outputs [p per, (p+1) per))
+      const int nc3 = R.lv[a.L - 1].NN * R.lv[a.L - 1].N, per = (nc3 + (int)C - 1) / (int)C;
+      const int plo = min(nc3, (int)me * per);
+      res_coarsest(R, s_cg, s_co, s_cb, plo, min(nc3, plo + per));
+      if (!sync.barrier()) return;
+    } else if (sync.rank() == 0) {
       const int u0 = threadIdx.x, us = blockDim.x;
       for (int l = lt; l < a.L - 1; ++l) {
         res_first_sweep(R, l, u0, us);
@@ -1126,7 +1136,7 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
         res_restrict(R, l, u0, us);
         __syncthreads();
       }
-      res_coarsest(R, s_cg, s_co, u0, us);
+      res_coarsest(R, s_cg, s_co, s_cb, 0, R.lv[a.L - 1].NN * R.lv[a.L - 1].N);
       __syncthreads();
       for (int l = a.L - 2; l >= lt; --l) {
         res_prolong(R, l, u0, us);
@@ -1138,7 +1148,7 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
           }
       }
     }
-    if (lt > 0 && !sync.barrier()) return;
+    if (lt > 0 && lt < a.L - 1 && !sync.barrier()) return;
     for (int l = lt - 1; l >= 0; --l) {
       res_prolong(R, l, t0, ts);
       if (!sync.barrier()) return;
