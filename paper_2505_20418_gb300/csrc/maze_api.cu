@@ -657,7 +657,9 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
     m.scratch_floats = tot;
     AL(c->y2, ng);
     AL(c->mx_scratch, tot);
-    AL(c->mx_g, gk.size());
+    // the coarsest level's spectral solve: 1/(N_c^3 lambda(k)), then cos
+    // and sin of 2 pi t / N_c
+    AL(c->mx_g, gk.size() + 2 * (size_t)c->mg.Nl[c->mg.L - 1]);
     m.scratch = c->mx_scratch;
     m.gkerf = c->mx_g;
     const double cs = c->h / (4.0 * kPi), cp = 4.0 * kPi / c->h;
@@ -719,7 +721,27 @@ maze_status ctx_create(const maze_config* cfg, Arena* arena, maze_ctx** out) {
   const size_t ng = c->ng;
   const std::vector<double>& gk = c->gk;
   std::vector<float> gkf;
-  if (c->mixed) gkf.assign(gk.begin(), gk.end());
+  if (c->mixed) {
+    // M e^{i k.p} = lambda(k) e^{i k.p}, lambda = 2 (cos kx + cos ky + cos kz) - 6
+    // (k in units of 2 pi / N_c): the zero-mean inverse multiplies the
+    // transform by 1 / lambda (0 at k = 0); the 1 / N_c^3 of the inverse
+    // transform is folded in
+    const int Nc = c->mg.Nl[c->mg.L - 1], nc3 = Nc * Nc * Nc;
+    gkf.assign((size_t)nc3 + 2 * Nc, 0.f);
+    std::vector<double> cs(Nc);
+    for (int t = 0; t < Nc; ++t) cs[t] = cos(2.0 * kPi * t / Nc);
+    for (int kz = 0; kz < Nc; ++kz)
+      for (int ky = 0; ky < Nc; ++ky)
+        for (int kx = 0; kx < Nc; ++kx) {
+          if (!kx && !ky && !kz) continue;
+          const double lam = 2.0 * (cs[kx] + cs[ky] + cs[kz]) - 6.0;
+          gkf[kx + Nc * (ky + Nc * kz)] = (float)(1.0 / (lam * nc3));
+        }
+    for (int t = 0; t < Nc; ++t) {
+      gkf[nc3 + t] = (float)cs[t];
+      gkf[nc3 + Nc + t] = (float)sin(2.0 * kPi * t / Nc);
+    }
+  }
   if (cudaMallocHost(&c->rec_host, sizeof(maze_stats)) != cudaSuccess) {
     free_ctx(c);
     return fail(MAZE_ERR_OOM, "cudaMallocHost failed");

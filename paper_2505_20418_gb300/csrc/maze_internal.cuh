@@ -202,7 +202,8 @@ struct MixedArgs {
   double* q_out;           // optional copy of q
   float* scratch;          // global form of the V-cycle storage (slab layout of one part)
   size_t scratch_floats;   // its size; the kernels refuse a layout that does not fit
-  const float* gkerf;      // [Nc^3] coarsest pseudo-inverse kernel
+  const float* gkerf;      // [Nc^3] 1/(Nc^3 lambda(k)) of the coarsest M (0 at k = 0), then [Nc] cos and
+                           // [Nc] sin of 2 pi t / Nc
   int L;
   int Nl[kMaxLevels];
   int lg[kMaxLevels];      // log2(N_l) for powers of two, else -1

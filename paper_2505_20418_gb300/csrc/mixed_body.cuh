@@ -789,55 +789,67 @@ __device__ __forceinline__ void res_prolong(const Slabs& R, int l, int t0, int t
   }
 }
 
-// Coarsest level: the exact zero-mean solve by the pseudo-inverse kernel
-// (at most 8^3 points). s_co holds every coarse point's coordinates packed
-// as i | j << 8 | k << 16 (staged once per solve, no divisions here); s_cb
-// receives the coarse rhs. Outputs [plo, phi) are computed by this CTA (all
-// of them when one CTA runs the tail; a share of them when the coarsest
-// level is split over the sync domain). A warp computes four outputs at
-// once; each output's sum runs over q = lane, lane + 32, ... and then a
-// butterfly over the lanes.
-__device__ __forceinline__ void res_coarsest(const Slabs& R, const float* s_cg, const int* s_co, float* s_cb, int plo,
-                                             int phi) {
+// Coarsest level (at most 8^3 points, solved by one CTA): the exact
+// zero-mean solve. M is circulant, so the discrete Fourier transform
+// diagonalises it: x = F^-1 (F b / lambda) with lambda(k) = 2 (cos kx + cos
+// ky + cos kz) - 6 and the k = 0 mode dropped. The three forward and three
+// inverse passes are direct N_c-point transforms along one axis each, one
+// point per thread (s_re / s_im in shared memory, the pass's outputs kept in
+// registers across a barrier); s_il holds 1/(N_c^3 lambda), s_tc / s_ts the
+// cosines and sines of 2 pi t / N_c, s_co the packed coordinates. Needs
+// blockDim.x >= N_c^3 (512 threads).
+__device__ __noinline__ void res_coarsest(const Slabs& R, const float* s_il, const float* s_tc, const float* s_ts,
+                                          const int* s_co, float* s_re, float* s_im, maze_stats* rec) {
   const int l = R.L - 1;
   const RLevel& v = R.lv[l];
   const int Nc = v.N, NNc = v.NN, nc3 = Nc * NNc;
-  for (int q = threadIdx.x; q < nc3; q += blockDim.x) {
-    const int qk = s_co[q] >> 16;
-    s_cb[q] = R.plane(l, 1, qk)[q - qk * NNc];
+  // (the host admits coarsest levels of at most 8^3 points and launches 512
+  // or more threads; anything else is an error, never an overrun)
+  if (Nc > 8 || nc3 > (int)blockDim.x) {
+    if (threadIdx.x == 0) atomicCAS(&rec->status, MAZE_OK, MAZE_ERR_INVALID);
+    return;
+  }
+  const int p = threadIdx.x;
+  int pi = 0, pj = 0, pk = 0;
+  if (p < nc3) {
+    const int c = s_co[p];
+    pi = c & 255;
+    pj = (c >> 8) & 255;
+    pk = c >> 16;
+    s_re[p] = R.plane(l, 1, pk)[pj * Nc + pi];
+    s_im[p] = 0.f;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  for (int p0 = plo + wid; p0 < phi; p0 += 4 * nwarps) {
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    int pi[4], pj[4], pk[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int c = s_co[min(p0 + u * nwarps, phi - 1)];
-      pi[u] = c & 255;
-      pj[u] = (c >> 8) & 255;
-      pk[u] = c >> 16;
-    }
-    for (int q = lane; q < nc3; q += 32) {
-      const int c = s_co[q];
-      const int qi = c & 255, qj = (c >> 8) & 255, qk = c >> 16;
-      const float bq = s_cb[q];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        acc[u] += s_cg[wrapi(pi[u] - qi, Nc) + Nc * (wrapi(pj[u] - qj, Nc) + Nc * wrapi(pk[u] - qk, Nc))] * bq;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-      for (int u = 0; u < 4; ++u) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
-    if (lane == 0)
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int p = p0 + u * nwarps;
-        if (p < phi) R.plane(l, 0, pk[u])[pj[u] * Nc + pi[u]] = acc[u];
+  for (int pass = 0; pass < 6; ++pass) {
+    const int ax = pass % 3;
+    const float sg = pass < 3 ? -1.f : 1.f;   // forward e^{-i..}, inverse e^{+i..}
+    float re = 0.f, im = 0.f;
+    if (p < nc3) {
+      const int idx = ax == 0 ? pi : (ax == 1 ? pj : pk);
+      const int stride = ax == 0 ? 1 : (ax == 1 ? Nc : NNc);
+      const int base = p - idx * stride;
+      int t = 0;   // idx * m mod N_c
+      for (int m = 0; m < Nc; ++m) {
+        const float ar = s_re[base + m * stride], ai = s_im[base + m * stride];
+        const float c = s_tc[t], sn = sg * s_ts[t];
+        re += ar * c - ai * sn;
+        im += ar * sn + ai * c;
+        t += idx;
+        if (t >= Nc) t -= Nc;
       }
+      if (pass == 2) {
+        re *= s_il[p];
+        im *= s_il[p];
+      }
+    }
+    __syncthreads();
+    if (p < nc3) {
+      s_re[p] = re;
+      s_im[p] = im;
+    }
+    __syncthreads();
   }
+  if (p < nc3) R.plane(l, 0, pk)[pj * Nc + pi] = s_re[p];
 }
 
 // Level-0 pointers of the outer passes. The arrays are distinct (the three
@@ -1048,16 +1060,22 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
   const int tid = (int)me * blockDim.x + threadIdx.x;
   const int stride = (int)C * blockDim.x;
   // the coarsest level's pseudo-inverse kernel, staged once per solve
-  __shared__ float s_cg[512];
+  __shared__ float s_cg[512];   // 1/(N_c^3 lambda) of the coarsest level
   __shared__ int s_co[512];
-  __shared__ float s_cb[512];
+  __shared__ float s_re[512], s_im[512];
+  __shared__ float s_tc[8], s_ts[8];
   if (dsm)
     slabs_setup(R, a, dsm, me, C, true);
   else
     slabs_setup(R, a, a.scratch, 0, 1, false);
   {
     const int Nc = a.Nl[a.L - 1];
-    for (int q = threadIdx.x; q < Nc * Nc * Nc; q += blockDim.x) {
+    // (at most 8^3 values: larger coarsest levels are rejected below)
+    if (threadIdx.x < Nc && Nc <= 8) {
+      s_tc[threadIdx.x] = a.gkerf[Nc * Nc * Nc + threadIdx.x];
+      s_ts[threadIdx.x] = a.gkerf[Nc * Nc * Nc + Nc + threadIdx.x];
+    }
+    for (int q = threadIdx.x; q < min(Nc * Nc * Nc, 512); q += blockDim.x) {
       s_cg[q] = a.gkerf[q];
       const int qk = q / (Nc * Nc), qj = (q - qk * Nc * Nc) / Nc;
       s_co[q] = (q - qk * Nc * Nc - qj * Nc) | (qj << 8) | (qk << 16);
@@ -1116,10 +1134,8 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
     }
     if (lt == a.L - 1) {
       // the coarsest level alone below the domain's levels: its exact solve
-      // split over the domain (part p computes outputs [p per, (p+1) per))
-      const int nc3 = R.lv[a.L - 1].NN * R.lv[a.L - 1].N, per = (nc3 + (int)C - 1) / (int)C;
-      const int plo = min(nc3, (int)me * per);
-      res_coarsest(R, s_cg, s_co, s_cb, plo, min(nc3, plo + per));
+      // in the first CTA
+      if (sync.rank() == 0) res_coarsest(R, s_cg, s_tc, s_ts, s_co, s_re, s_im, a.rec);
       if (!sync.barrier()) return;
     } else if (sync.rank() == 0) {
       const int u0 = threadIdx.x, us = blockDim.x;
@@ -1136,7 +1152,7 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
         res_restrict(R, l, u0, us);
         __syncthreads();
       }
-      res_coarsest(R, s_cg, s_co, s_cb, 0, R.lv[a.L - 1].NN * R.lv[a.L - 1].N);
+      res_coarsest(R, s_cg, s_tc, s_ts, s_co, s_re, s_im, a.rec);
       __syncthreads();
       for (int l = a.L - 2; l >= lt; --l) {
         res_prolong(R, l, u0, us);
