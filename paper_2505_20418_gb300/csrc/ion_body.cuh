@@ -133,6 +133,14 @@ __device__ __forceinline__ void move_ion(const IonArgs& a, int i) {
       a.pos[a.n + i] = y;
       a.pos[2 * a.n + i] = z;
     }
+    // every index below comes from a position in [0, L): a position that is
+    // not (NaN, or so large that the wrap lost it) is replaced by the box
+    // origin and the step is marked non-finite, so no index can leave its
+    // array and the next step does not run
+    if (!(x >= 0.0 && x < a.L && y >= 0.0 && y < a.L && z >= 0.0 && z < a.L)) {
+      x = y = z = 0.0;
+      atomicCAS(&a.rec->status, MAZE_OK, MAZE_ERR_NONFINITE);
+    }
     const double Q = t ? a.charge1 : a.charge0;
     a.pos32[i] = make_float4((float)x, (float)y, (float)z, (float)Q);
     int cx = 0, cy = 0, cz = 0;
