@@ -976,10 +976,25 @@ __device__ __forceinline__ void s4_pass(const RLevel& v0, int t0, int ts, df c_s
 // z-, z+.
 __device__ __forceinline__ void upd_point(const float2 (&yn)[6], const float (&en)[6], float2 yo, float eo, float2 sg,
                                           float2& ynew, float& rf) {
-  df yn6[6];
+  // the neighbour sum of y + e: the high parts summed error-free (TwoSum
+  // chain, errors collected in c), the low parts and the corrections e added
+  // into c, one renormalisation (Ogita, Rump and Oishi's Sum2, SIAM J. Sci.
+  // Comput. 26, 2005): the accuracy of the double-float sum at ~40 % of its
+  // operations
+  float sh = yn[0].x, c = 0.f;
 #pragma unroll
-  for (int u = 0; u < 6; ++u) yn6[u] = df_add_f(df_from(yn[u]), en[u]);
-  const df sn = df_add(df_add(df_add(yn6[0], yn6[1]), df_add(yn6[2], yn6[3])), df_add(yn6[4], yn6[5]));
+  for (int u = 1; u < 6; ++u) {
+    const float s2 = __fadd_rn(sh, yn[u].x);
+    const float bb = __fsub_rn(s2, sh);
+    c = __fadd_rn(c, __fadd_rn(__fsub_rn(sh, __fsub_rn(s2, bb)), __fsub_rn(yn[u].x, bb)));
+    sh = s2;
+  }
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(yn[0].y, yn[1].y), __fadd_rn(yn[2].y, yn[3].y)),
+                             __fadd_rn(yn[4].y, yn[5].y));
+  const float es = __fadd_rn(__fadd_rn(__fadd_rn(en[0], en[1]), __fadd_rn(en[2], en[3])), __fadd_rn(en[4], en[5]));
+  c = __fadd_rn(c, __fadd_rn(lo, es));
+  const float snh = __fadd_rn(sh, c);
+  const df sn = {snh, __fsub_rn(c, __fsub_rn(snh, sh))};
   const df ym = df_add_f(df_from(yo), eo);
   const df r = df_sub(df_from(sg), df_sub(sn, df_mul_f(ym, 6.f)));
   ynew = df_to(ym);
