@@ -258,6 +258,24 @@ __global__ void __launch_bounds__(kMixedClusterThreads, 1) k_cluster_step(IonArg
   const bool skip = __ldcg(&ia.rec->status) != MAZE_OK;
   if (rank == 0 && threadIdx.x == 0) *ia.gate = skip ? 1 : 0;
   if (skip) return;
+  if (threadIdx.x == 0) {
+    // S4 reads both potentials and y of the whole box after S1-S3: start them
+    // on their way into L2 now, each CTA one share (a hint: addresses inside
+    // the buffers, 16-byte aligned, sizes multiples of 16)
+    const unsigned bytes = (unsigned)ma.n * (unsigned)sizeof(float2);
+    const unsigned share = ((bytes + (unsigned)C - 1u) / (unsigned)C + 15u) & ~15u;
+    const unsigned lo = rank * share;
+    if (lo < bytes) {
+      const unsigned len = min(share, bytes - lo) & ~15u;
+      const float2* arr[3] = {ma.phi_k, ma.phi_km1, ma.y};
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+        if (len)
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<const char*>(arr[u]) + lo),
+                       "r"(len)
+                       : "memory");
+    }
+  }
   const int n = ia.n, nc = ia.nc;
   const IonChunk ch = ion_chunk(n, (int)rank, C);
   for (int i = ch.lo + (int)threadIdx.x; i < ch.hi; i += blockDim.x) move_ion(ia, i);
