@@ -224,6 +224,21 @@ def config_dict(w, args):
             "l2": "flushed between timed steps (256 MiB write outside the step events)"}
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# roofline kernel, from one ncu capture of the kernels as they stand; the
+# command and the other counters are in the named summary under profiles/.
+# A kernel changed after its capture must drop its entry (traffic null).
+MEASURED_TRAFFIC = {
+    ("nacl1000", "k_cluster_step", "mixed", "mg"): (1305856, "profiles/k_cluster_step_nacl1000.md"),
+    ("nacl512000", "k_mixed_grid", "mixed", "mg"): (10804688000, "profiles/k_mixed_grid_nacl512000.md"),
+}
+
+
+def measured_traffic(workload, kernel, precision, solver):
+    hit = MEASURED_TRAFFIC.get((workload, kernel, precision, solver))
+    return None if hit is None else hit[0]
+
+
 def solve_kernel_name(args, w):
     """The solve kernel a step launches for this precision, solver and grid."""
     if args.precision == "mixed":
@@ -399,7 +414,8 @@ def main():
             "solve_gbs": achieved, "solve_us": 1e6 * mean_solve_s,
             "roofline": {"kernel": solve_kernel_name(args, w), "bound": "hbm", "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None,
+                         "traffic": measured_traffic(args.workload, solve_kernel_name(args, w), args.precision,
+                                                     args.solver),
                          "algorithmic_bytes_per_launch": bytes_launch},
             "cpu_baseline": cpu, "e2e": e2e, "timing_error": timing_error,
             "gpu_launches": kps * args.steps, "clocks": clk,
