@@ -742,6 +742,7 @@ struct CellSmem {
   int lo[kMaxNbr], cum[kMaxNbr + 1];
   double f[kCellGroup][8];                       // pair sums, then gather sums
   int queue[kW][64];
+  int queue2[kW][64];                            // second ion of a warp's pair (mixed, large cells)
 };
 
 template <int kW>
@@ -813,7 +814,87 @@ __device__ __forceinline__ void forces_cell_slice(const ForceArgs& a, int c, int
         }
       }
       __syncthreads();
-      for (int gi = warp; gi < gn; gi += kW) {
+      // mixed precision with at least two ions per warp: a warp filters each
+      // staged candidate against two home ions at once (one load, two
+      // ballots); each ion keeps its own queue, batches and sums, so its
+      // result is that of the one-ion loop below
+      const bool two = a.mixed && gn >= 2 * kW;
+      if (two)
+        for (int gp = warp; 2 * gp < gn; gp += kW) {
+          const int gA = 2 * gp, gB = 2 * gp + 1;
+          const bool hasB = gB < gn;
+          const int sA = g0 + gA, sB = g0 + (hasB ? gB : gA);
+          const float4 hA = a.rel_hi_sorted[sA], lA = a.rel_lo_sorted[sA];
+          const float4 hB = a.rel_hi_sorted[sB], lB = a.rel_lo_sorted[sB];
+          const int tA = a.type[a.cell_ions[sA]], tB = a.type[a.cell_ions[sB]];
+          int* qA = sm.queue[warp];
+          int* qB = sm.queue2[warp];
+          int nA = 0, nB = 0;
+          PairSum pA, pB;
+          auto evalm = [&](int e2, float4 pi32, float4 ril, int t, PairSum& ps) {
+            const float4 h = sm.p[e2], l = s_l[e2];
+            const float dx = disp_df(pi32.x, ril.x, h.x, l.x, 0.f, 0.f);
+            const float dy = disp_df(pi32.y, ril.y, h.y, l.y, 0.f, 0.f);
+            const float dz = disp_df(pi32.z, ril.z, h.z, l.z, 0.f, 0.f);
+            pair_f(a, t + (int)l.w, dx, dy, dz, ps);
+          };
+          for (int e0 = 0; e0 < len; e0 += 32) {
+            const int e = e0 + lane;
+            bool passA = false, passB = false;
+            if (e < len) {
+              const int je = sm.j[e];
+              const float4 h = sm.p[e];
+              if (je != sA) {
+                const float dx = h.x - hA.x, dy = h.y - hA.y, dz = h.z - hA.z;
+                passA = dx * dx + dy * dy + dz * dz < a.rc2_filter;
+              }
+              if (hasB && je != sB) {
+                const float dx = h.x - hB.x, dy = h.y - hB.y, dz = h.z - hB.z;
+                passB = dx * dx + dy * dy + dz * dz < a.rc2_filter;
+              }
+            }
+            const unsigned mA = __ballot_sync(0xffffffffu, passA);
+            const unsigned mB = __ballot_sync(0xffffffffu, passB);
+            if (passA) qA[nA + __popc(mA & ((1u << lane) - 1u))] = e;
+            if (passB) qB[nB + __popc(mB & ((1u << lane) - 1u))] = e;
+            nA += __popc(mA);
+            nB += __popc(mB);
+            __syncwarp();
+            if (nA >= 32) {
+              evalm(qA[lane], hA, lA, tA, pA);
+              __syncwarp();
+              if (lane < nA - 32) qA[lane] = qA[32 + lane];
+              __syncwarp();
+              nA -= 32;
+            }
+            if (nB >= 32) {
+              evalm(qB[lane], hB, lB, tB, pB);
+              __syncwarp();
+              if (lane < nB - 32) qB[lane] = qB[32 + lane];
+              __syncwarp();
+              nB -= 32;
+            }
+          }
+          if (lane < nA) evalm(qA[lane], hA, lA, tA, pA);
+          if (lane < nB) evalm(qB[lane], hB, lB, tB, pB);
+          __syncwarp();
+          double fx, fy, fz, v;
+          pair_total(a, pA, fx, fy, fz, v);
+          if (lane == 0) {
+            sm.f[gA][4] += fx;
+            sm.f[gA][5] += fy;
+            sm.f[gA][6] += fz;
+            sm.f[gA][7] += v;
+          }
+          pair_total(a, pB, fx, fy, fz, v);
+          if (lane == 0 && hasB) {
+            sm.f[gB][4] += fx;
+            sm.f[gB][5] += fy;
+            sm.f[gB][6] += fz;
+            sm.f[gB][7] += v;
+          }
+        }
+      for (int gi = warp; gi < (two ? 0 : gn); gi += kW) {
         const int islot = g0 + gi;
         const int i = a.cell_ions[islot];
         const double x = a.pos[i], y = a.pos[n + i], z = a.pos[2 * n + i];
