@@ -214,7 +214,10 @@ maze_status maze_get(maze_ctx* ctx, int32_t what, double* host_out);
 
 /* Overwrite a quantity (MAZE_POS, MAZE_VEL, MAZE_PHI, MAZE_PHI_PREV, MAZE_Y)
  * from host memory. Setting MAZE_POS wraps the positions into [0, L); the
- * forces are not recomputed (call maze_gather). */
+ * forces are not recomputed (call maze_gather). host_in is read during the
+ * call; MAZE_POS and MAZE_VEL of a standalone context are then uploaded
+ * asynchronously on the context's stream from a pinned copy the context
+ * owns (work issued later on the stream sees the new values). */
 maze_status maze_set(maze_ctx* ctx, int32_t what, const double* host_in);
 
 /* Copy the per-step record to *out. Synchronises. */

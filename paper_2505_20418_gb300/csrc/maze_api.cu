@@ -455,6 +455,7 @@ maze_status build_graphs(maze_ctx* c, int timed) {
 }
 
 maze_status clear_status(maze_ctx* c) {
+  c->rec_dirty = true;
   CK(cudaMemsetAsync(&c->rec->status, 0, sizeof(int32_t), c->stream));
   return MAZE_OK;
 }
@@ -462,6 +463,20 @@ maze_status clear_status(maze_ctx* c) {
 maze_status read_stats(maze_ctx* c) {
   CK(cudaMemcpyAsync(c->rec_host, c->rec, sizeof(maze_stats), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  c->rec_dirty = false;
+  return MAZE_OK;
+}
+
+// The pinned staging buffer k of the per-ion host copies (3 n doubles), made
+// on first use.
+maze_status stage_buffer(maze_ctx* c, int k) {
+  if (c->stage[k]) return MAZE_OK;
+  if (cudaMallocHost(&c->stage[k], 3 * (size_t)c->n * sizeof(double)) != cudaSuccess) {
+    c->stage[k] = nullptr;
+    cudaGetLastError();
+    return fail(MAZE_ERR_OOM, "cudaMallocHost failed");
+  }
+  if (k < 2) CK(cudaEventCreateWithFlags(&c->stage_ev[k], cudaEventDisableTiming));
   return MAZE_OK;
 }
 
@@ -494,6 +509,10 @@ void free_ctx(maze_ctx* c) {
     else cudaFree(p);
   }
   if (c->rec_host) cudaFreeHost(c->rec_host);
+  for (int k = 0; k < 3; ++k)
+    if (c->stage[k]) cudaFreeHost(c->stage[k]);
+  for (int k = 0; k < 2; ++k)
+    if (c->stage_ev[k]) cudaEventDestroy(c->stage_ev[k]);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -871,6 +890,7 @@ maze_status maze_gather(maze_ctx* c) {
 maze_status maze_step_async(maze_ctx* c, int32_t nsteps) {
   if (!c) return fail(MAZE_ERR_INVALID, "ctx is NULL");
   if (nsteps < 0) return fail(MAZE_ERR_INVALID, "nsteps must be >= 0");
+  c->rec_dirty = true;
   const int t = c->timing;
   if (!c->graphs_tried[t]) {
     maze_status s = build_graphs(c, t);
@@ -890,8 +910,11 @@ maze_status maze_step_async(maze_ctx* c, int32_t nsteps) {
 
 maze_status maze_step(maze_ctx* c, int32_t nsteps) {
   if (!c) return fail(MAZE_ERR_INVALID, "ctx is NULL");
-  maze_status s = read_stats(c);
-  if (s != MAZE_OK) return s;
+  maze_status s = MAZE_OK;
+  if (c->rec_dirty) {   // (the record a synchronising call left is current)
+    s = read_stats(c);
+    if (s != MAZE_OK) return s;
+  }
   const int64_t before = c->rec_host->step;
   s = clear_status(c);
   if (s != MAZE_OK) return s;
@@ -954,9 +977,21 @@ maze_status maze_get(maze_ctx* c, int32_t what, double* out) {
     default: return fail(MAZE_ERR_INVALID, "unknown quantity");
   }
   if (ion) {
+    // a standalone context reads through its pinned stage; a batch box (its
+    // buffers in the batch's arena) through a temporary, so that admitting
+    // and retiring boxes allocates no pinned memory
     const int n = c->n;
-    std::vector<double> tmp(3 * (size_t)n);
-    CK(cudaMemcpyAsync(tmp.data(), src, tmp.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    std::vector<double> tmpv;
+    double* tmp = nullptr;
+    if (c->arena) {
+      tmpv.resize(3 * (size_t)n);
+      tmp = tmpv.data();
+    } else {
+      maze_status st = stage_buffer(c, 2);
+      if (st != MAZE_OK) return st;
+      tmp = c->stage[2];
+    }
+    CK(cudaMemcpyAsync(tmp, src, 3 * (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     for (int d = 0; d < 3; ++d)
       for (int i = 0; i < n; ++i) out[3 * i + d] = tmp[(size_t)d * n + i];
@@ -988,16 +1023,34 @@ maze_status maze_set(maze_ctx* c, int32_t what, const double* in) {
     default: return fail(MAZE_ERR_INVALID, "quantity cannot be set");
   }
   if (ion) {
+    // the values go through a pinned stage of the context, so the upload is
+    // asynchronous on the stream: the caller's buffer is read only here
     const int n = c->n;
-    std::vector<double> tmp(3 * (size_t)n);
+    for (int d = 0; d < 3; ++d)
+      for (int i = 0; i < n; ++i)
+        if (!isfinite(in[3 * i + d])) return fail(MAZE_ERR_INVALID, "non-finite input");
+    const int k = what == MAZE_POS ? 0 : 1;
+    std::vector<double> tmpv;
+    double* tmp = nullptr;
+    if (c->arena) {   // a batch box: a temporary and a synchronous copy
+      tmpv.resize(3 * (size_t)n);
+      tmp = tmpv.data();
+    } else {
+      maze_status st = stage_buffer(c, k);
+      if (st != MAZE_OK) return st;
+      CK(cudaEventSynchronize(c->stage_ev[k]));   // the stage's previous upload has been read
+      tmp = c->stage[k];
+    }
     for (int d = 0; d < 3; ++d)
       for (int i = 0; i < n; ++i) {
         const double v = in[3 * i + d];
-        if (!isfinite(v)) return fail(MAZE_ERR_INVALID, "non-finite input");
         tmp[(size_t)d * n + i] = what == MAZE_POS ? wrap_host(v, c->L) : v;
       }
-    CK(cudaMemcpyAsync(dst, tmp.data(), tmp.size() * 8, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpyAsync(dst, tmp, 3 * (size_t)n * 8, cudaMemcpyHostToDevice, c->stream));
+    if (c->arena)
+      CK(cudaStreamSynchronize(c->stream));
+    else
+      CK(cudaEventRecord(c->stage_ev[k], c->stream));
   } else if (c->mixed) {
     // double -> double-float pair (hi = nearest float, lo = remainder)
     std::vector<float2> tmp(c->ng);
@@ -1068,6 +1121,7 @@ maze_status maze_set_state(maze_ctx* c, const void* blob, size_t nbytes) {
   st.v_work = vw;
   st.status = MAZE_OK;
   *c->rec_host = st;
+  c->rec_dirty = true;
   CK(cudaMemcpyAsync(c->rec, c->rec_host, sizeof(maze_stats), cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return MAZE_OK;
