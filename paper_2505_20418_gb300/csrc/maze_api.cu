@@ -954,8 +954,13 @@ maze_status maze_get_timing(maze_ctx* c, double* out) {
 
 maze_status maze_get_stats(maze_ctx* c, maze_stats* out) {
   if (!c || !out) return fail(MAZE_ERR_INVALID, "NULL argument");
-  maze_status s = read_stats(c);
-  if (s != MAZE_OK) return s;
+  // a standalone context's record changes only through the calls that mark
+  // it dirty, so a current copy is returned as is; a batch box's record is
+  // written by the batch's launches and always read
+  if (c->arena || c->rec_dirty) {
+    maze_status s = read_stats(c);
+    if (s != MAZE_OK) return s;
+  }
   *out = *c->rec_host;
   return MAZE_OK;
 }
