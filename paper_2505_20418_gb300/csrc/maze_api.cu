@@ -456,6 +456,7 @@ maze_status build_graphs(maze_ctx* c, int timed) {
 
 maze_status clear_status(maze_ctx* c) {
   c->rec_dirty = true;
+  c->staged_fresh[0] = c->staged_fresh[1] = false;
   CK(cudaMemsetAsync(&c->rec->status, 0, sizeof(int32_t), c->stream));
   return MAZE_OK;
 }
@@ -509,7 +510,7 @@ void free_ctx(maze_ctx* c) {
     else cudaFree(p);
   }
   if (c->rec_host) cudaFreeHost(c->rec_host);
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < 4; ++k)
     if (c->stage[k]) cudaFreeHost(c->stage[k]);
   for (int k = 0; k < 2; ++k)
     if (c->stage_ev[k]) cudaEventDestroy(c->stage_ev[k]);
@@ -891,6 +892,7 @@ maze_status maze_step_async(maze_ctx* c, int32_t nsteps) {
   if (!c) return fail(MAZE_ERR_INVALID, "ctx is NULL");
   if (nsteps < 0) return fail(MAZE_ERR_INVALID, "nsteps must be >= 0");
   c->rec_dirty = true;
+  c->staged_fresh[0] = c->staged_fresh[1] = false;
   const int t = c->timing;
   if (!c->graphs_tried[t]) {
     maze_status s = build_graphs(c, t);
@@ -921,7 +923,21 @@ maze_status maze_step(maze_ctx* c, int32_t nsteps) {
   const int ik0 = c->ik;
   s = maze_step_async(c, nsteps);
   if (s != MAZE_OK) return s;
+  // positions and velocities were read back after the previous step: queue
+  // their copies now, so that the record read below waits for all at once
+  bool queued[2] = {false, false};
+  if (!c->arena)
+    for (int k = 0; k < 2; ++k)
+      if (c->want_ion[k] && stage_buffer(c, 2 + k) == MAZE_OK) {
+        CK(cudaMemcpyAsync(c->stage[2 + k], k == 0 ? c->pos : c->vel, 3 * (size_t)c->n * 8, cudaMemcpyDeviceToHost,
+                           c->stream));
+        queued[k] = true;
+        c->want_ion[k] = false;
+      }
   s = read_stats(c);
+  if (s != MAZE_OK) return s;
+  c->staged_fresh[0] = queued[0];
+  c->staged_fresh[1] = queued[1];
   if (s != MAZE_OK) return s;
   if (c->rec_host->status != MAZE_OK) {
     // later steps were skipped on the device: put the rotation where the
@@ -988,16 +1004,26 @@ maze_status maze_get(maze_ctx* c, int32_t what, double* out) {
     const int n = c->n;
     std::vector<double> tmpv;
     double* tmp = nullptr;
+    const int kk = what == MAZE_POS ? 0 : (what == MAZE_VEL ? 1 : -1);
     if (c->arena) {
       tmpv.resize(3 * (size_t)n);
       tmp = tmpv.data();
     } else {
-      maze_status st = stage_buffer(c, 2);
+      const int sk = kk == 0 ? 2 : 3;
+      maze_status st = stage_buffer(c, sk);
       if (st != MAZE_OK) return st;
-      tmp = c->stage[2];
+      tmp = c->stage[sk];
+      if (kk >= 0)
+        c->want_ion[kk] = true;
+      else
+        c->staged_fresh[1] = false;   // the forces go through the velocities' stage
     }
-    CK(cudaMemcpyAsync(tmp, src, 3 * (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    if (kk >= 0 && !c->arena && c->staged_fresh[kk]) {
+      // copied by the last maze_step together with its record read
+    } else {
+      CK(cudaMemcpyAsync(tmp, src, 3 * (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+    }
     for (int d = 0; d < 3; ++d)
       for (int i = 0; i < n; ++i) out[3 * i + d] = tmp[(size_t)d * n + i];
   } else {
@@ -1035,6 +1061,7 @@ maze_status maze_set(maze_ctx* c, int32_t what, const double* in) {
       for (int i = 0; i < n; ++i)
         if (!isfinite(in[3 * i + d])) return fail(MAZE_ERR_INVALID, "non-finite input");
     const int k = what == MAZE_POS ? 0 : 1;
+    c->staged_fresh[k] = false;
     std::vector<double> tmpv;
     double* tmp = nullptr;
     if (c->arena) {   // a batch box: a temporary and a synchronous copy
@@ -1127,6 +1154,7 @@ maze_status maze_set_state(maze_ctx* c, const void* blob, size_t nbytes) {
   st.status = MAZE_OK;
   *c->rec_host = st;
   c->rec_dirty = true;
+  c->staged_fresh[0] = c->staged_fresh[1] = false;
   CK(cudaMemcpyAsync(c->rec, c->rec_host, sizeof(maze_stats), cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return MAZE_OK;

@@ -94,10 +94,16 @@ struct maze_ctx {
   maze_stats* rec_host = nullptr;  // pinned
   bool rec_dirty = true;           // device record may differ from rec_host
   // pinned staging of the per-ion host copies (standalone contexts, made on
-  // first use): [0] maze_set of positions, [1] of velocities, [2] maze_get;
-  // an uploaded stage is reused only after its copy's event
-  double* stage[3] = {nullptr, nullptr, nullptr};
+  // first use): [0] maze_set of positions, [1] of velocities, [2] maze_get of
+  // positions, [3] of velocities (and of the forces); an uploaded stage is
+  // reused only after its copy's event
+  double* stage[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+  // positions / velocities read back after the last step: maze_step then
+  // queues their copies with its record read (staged_fresh: the stage holds
+  // the device values, nothing has been issued since)
+  bool want_ion[2] = {false, false};
+  bool staged_fresh[2] = {false, false};
   cudaGraphExec_t graph[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
   bool graphs_tried[2] = {false, false}, graphs_ok[2] = {false, false};
   int timing = 0;

@@ -1,0 +1,64 @@
+"""Host copies of a standalone context (maze_set / maze_get / maze_get_stats).
+
+maze_set uploads positions and velocities from a pinned stage without
+synchronising, maze_step queues the copies of the positions and velocities
+the caller read after the previous step together with its record read, and
+maze_get_stats serves a record that no call has changed since it was read.
+These tests interleave the calls in the orders a caller may use and check
+every value against a second context driven with step_async and explicit
+reads, which takes none of those shortcuts' state."""
+import numpy as np
+import pytest
+
+from paper_2505_20418_gb300 import maze as M
+from paper_2505_20418_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def make(w):
+    pos, vel, types = synth.make_state(w)
+    return M.MazeSim(pos, vel, types, w.L, w.N, synth.tosi_fumi_nacl(), r_cut=w.rc, dt=w.dt, tol=w.tol,
+                     order=w.order, solver=M.MAZE_SOLVER_MG, precision=M.MAZE_MIXED)
+
+
+def test_interleaved_gets_sets_and_steps_match_a_plain_context():
+    w = synth.workload("nacl1000")
+    a, b = make(w), make(w)
+    rng = np.random.default_rng(3)
+    for k in range(6):
+        if k == 3:
+            # a caller's edit between steps: new positions and velocities
+            x = a.get(M.MAZE_POS) + rng.normal(scale=1e-3, size=(w.n_ions, 3))
+            v = a.get(M.MAZE_VEL) * 0.999
+            for s in (a, b):
+                s.set(M.MAZE_POS, x)
+                s.set(M.MAZE_VEL, v)
+        assert M.maze_step(a.h, 1) == M.MAZE_OK
+        b.step_async(1)
+        sb = b.stats()
+        sa = a.stats()
+        assert sa["step"] == sb["step"] and sa["ke"] == sb["ke"]
+        # reads in varying orders, the forces through the velocities' stage
+        order = [M.MAZE_POS, M.MAZE_VEL, M.MAZE_FORCE, M.MAZE_VEL] if k % 2 else \
+            [M.MAZE_FORCE, M.MAZE_VEL, M.MAZE_POS, M.MAZE_POS]
+        for what in order:
+            assert np.array_equal(a.get(what), b.get(what)), (k, what)
+    a.close()
+    b.close()
+
+
+def test_set_then_get_without_a_step_returns_the_new_values():
+    w = synth.workload("nacl1000")
+    a = make(w)
+    assert M.maze_step(a.h, 1) == M.MAZE_OK
+    a.get(M.MAZE_POS)
+    a.get(M.MAZE_VEL)
+    assert M.maze_step(a.h, 1) == M.MAZE_OK     # queues both copies
+    v = a.get(M.MAZE_VEL) + 0.25
+    a.set(M.MAZE_VEL, v)
+    assert np.array_equal(a.get(M.MAZE_VEL), v)
+    x = np.mod(a.get(M.MAZE_POS) + 0.5, w.L)
+    a.set(M.MAZE_POS, x)
+    assert np.allclose(a.get(M.MAZE_POS), x, atol=0, rtol=0)
+    a.close()
