@@ -45,7 +45,8 @@ from paper_2505_20418_gb300 import synth  # noqa: E402
 METRIC = "MaZe steps/s, solve GB/s vs HBM peak, p50/p99 step latency at stated force error"
 KERNELS_PER_STEP_CELLS = 7    # move, spread, 3 cell-list kernels, solve, forces
 KERNELS_PER_STEP_NOCELLS = 4
-KERNELS_PER_STEP_FUSED = 2     # mixed precision up to 64^3: S1-S6 in one cluster launch, then the forces
+KERNELS_PER_STEP_FUSED = 2     # mixed precision up to 64^3, no cell list: S1-S6 in one cluster launch, the forces
+KERNELS_PER_STEP_SPLIT = 4     # mixed up to 64^3 with a cell list: S1-S3, S8 beside the solve, S7/S9
 
 
 def peaks():
@@ -229,7 +230,7 @@ def config_dict(w, args):
 # command and the other counters are in the named summary under profiles/.
 # A kernel changed after its capture must drop its entry (traffic null).
 MEASURED_TRAFFIC = {
-    ("nacl1000", "k_cluster_step", "mixed", "mg"): (1305856, "profiles/k_cluster_step_nacl1000.md"),
+    ("nacl1000", "k_mixed_cluster", "mixed", "mg"): (1190144, "profiles/k_mixed_cluster_nacl1000.md"),
     ("nacl512000", "k_mixed_grid", "mixed", "mg"): (10804688000, "profiles/k_mixed_grid_nacl512000.md"),
 }
 
@@ -239,10 +240,17 @@ def measured_traffic(workload, kernel, precision, solver):
     return None if hit is None else hit[0]
 
 
+def has_cells(w):
+    """True when the box takes the cell list (at least 3 cells of r_cut a side)."""
+    return int(np.floor(w.L / w.rc)) >= 3
+
+
 def solve_kernel_name(args, w):
     """The solve kernel a step launches for this precision, solver and grid."""
     if args.precision == "mixed":
-        return "k_cluster_step" if w.N <= 64 else "k_mixed_grid"
+        if w.N > 64:
+            return "k_mixed_grid"
+        return "k_mixed_cluster" if has_cells(w) else "k_cluster_step"
     return "k_mg_solve" if args.solver == "mg" else "k_cg_solve"
 
 
@@ -398,9 +406,9 @@ def main():
         peak, peak_kind = peaks()
         cpu = None if args.no_cpu else run_cpu_baseline(w, args.solver)
         if args.precision == "mixed" and w.N <= 64:
-            kps = KERNELS_PER_STEP_FUSED
+            kps = KERNELS_PER_STEP_SPLIT if has_cells(w) else KERNELS_PER_STEP_FUSED
         else:
-            kps = KERNELS_PER_STEP_CELLS if int(np.floor(w.L / w.rc)) >= 3 else KERNELS_PER_STEP_NOCELLS
+            kps = KERNELS_PER_STEP_CELLS if has_cells(w) else KERNELS_PER_STEP_NOCELLS
         line = {
             "metric": METRIC, "value": weak_scaling_value(world, args.steps, total_s), "unit": "steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

@@ -821,7 +821,10 @@ __device__ __forceinline__ void scan_ions_mixed(const ForceArgs& a, const float4
   }
 }
 
-template <int kW>
+// kPairsOnly: S8 alone (the pair sums of each ion to a.pair_out, 4 doubles
+// per ion: force x, y, z and energy); the gather and the finishing then run
+// in k_gather_finish, with the same per-ion arithmetic.
+template <int kW, bool kPairsOnly = false>
 __device__ __forceinline__ void forces_cell_slice(const ForceArgs& a, int c, int s, int split, CellSmem<kW>& sm,
                                                   double (&acc)[7]) {
   const int lane = threadIdx.x & 31;
@@ -962,6 +965,12 @@ __device__ __forceinline__ void forces_cell_slice(const ForceArgs& a, int c, int
       }
     }
     __syncthreads();
+    if (kPairsOnly) {
+      for (int e = threadIdx.x; e < gn * 4; e += blockDim.x)
+        a.pair_out[(size_t)a.cell_ions[g0 + (e >> 2)] * 4 + (e & 3)] = sm.f[e >> 2][4 + (e & 3)];
+      __syncthreads();
+      continue;
+    }
     for (int gi = warp; gi < gn; gi += kW) {
       double gx, gy, gz, vd;
       gather_el(a, a.cell_ions[g0 + gi], lane, gx, gy, gz, vd);

@@ -274,6 +274,7 @@ ForceArgs force_args(maze_ctx* c, const double* phi, int do_kick, int count_step
   a.ou = langevin_args(c);
   a.part = c->fpart;
   a.ticket = c->ticket;
+  a.pair_out = c->pair_out;
   a.rec = c->rec;
   a.gate = c->gate;
   return a;
@@ -403,6 +404,31 @@ maze_status enqueue_step(maze_ctx* c, int timed) {
     if (timed) CK(cudaEventRecordWithFlags(c->ev[4], c->stream, cudaEventRecordExternal));
     return MAZE_OK;
   }
+  if (c->pair_out) {
+    // mixed precision, one-cluster solve: S1-S3 in one cluster launch, then
+    // S8 (pairs) on the side stream beside the solve (S4-S6, one cluster on
+    // a few SMs), joined before S7/S9
+    if (timed) {
+      CK(cudaEventRecordWithFlags(c->ev[0], c->stream, cudaEventRecordExternal));
+      CK(cudaEventRecordWithFlags(c->ev[1], c->stream, cudaEventRecordExternal));
+    }
+    CK(launch_cluster_front(ion_args(c, 1, 1), cell_args(c), mixed_args(c, 0, nullptr), c->mx_cluster, c->stream));
+    if (timed) CK(cudaEventRecordWithFlags(c->ev[2], c->stream, cudaEventRecordExternal));
+    maze_status s;
+    const ForceArgs fa = force_args(c, c->phi[(c->ik + 2) % 3], 1, 1);
+    CK(cudaEventRecord(c->ev_fork, c->stream));
+    CK(cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
+    CK(launch_pairs(fa, c->side_stream));
+    CK(cudaEventRecord(c->ev_join, c->side_stream));
+    s = enqueue_solve(c, 0, nullptr);
+    if (timed && s == MAZE_OK) CK(cudaEventRecordWithFlags(c->ev[3], c->stream, cudaEventRecordExternal));
+    // join the side stream before any return (a capture must not end forked)
+    CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    if (s != MAZE_OK) return s;
+    CK(launch_gather_finish(fa, c->fblocks, c->stream));
+    if (timed) CK(cudaEventRecordWithFlags(c->ev[4], c->stream, cudaEventRecordExternal));
+    return MAZE_OK;
+  }
   if (timed) CK(cudaEventRecordWithFlags(c->ev[0], c->stream, cudaEventRecordExternal));
   CK(launch_ion_update(ion_args(c, 1, 1), c->stream));
   if (timed) CK(cudaEventRecordWithFlags(c->ev[1], c->stream, cudaEventRecordExternal));
@@ -514,6 +540,9 @@ void free_ctx(maze_ctx* c) {
     if (c->stage[k]) cudaFreeHost(c->stage[k]);
   for (int k = 0; k < 2; ++k)
     if (c->stage_ev[k]) cudaEventDestroy(c->stage_ev[k]);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side_stream) cudaStreamDestroy(c->side_stream);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -695,7 +724,10 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
       // the step's cluster launch and the step-0 solve use the same size
       const int cs = cluster_step_size();
       c->mx_cluster = cs > 0 ? std::min(cs, mixed_cluster_size()) : mixed_cluster_size();
-      c->fused_step = cs > 0 && cs >= c->mx_cluster;
+      // standalone boxes with a cell list take the split step (S8 beside the
+      // solve); the others S1-S6 in one cluster launch
+      c->split_step = cs > 0 && cs >= c->mx_cluster && !arena && c->nc >= 3;
+      c->fused_step = cs > 0 && cs >= c->mx_cluster && !c->split_step;
       m.resident = resident_bytes_host(m, c->mx_cluster) <= (size_t)kResidentSmem ? 1 : 0;
     } else {
       c->mx_blocks = mixed_grid_blocks((int)ng);
@@ -722,6 +754,16 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
     AL(c->fpart, (G + ngroups) * 8);
     AL(c->ticket, ngroups + 4);
     c->ticket_count = ngroups + 4;
+  }
+  if (c->split_step) {
+    AL(c->pair_out, 4 * (size_t)n);
+    if (cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      free_ctx(c);
+      return fail(MAZE_ERR_CUDA, "cudaStreamCreate / cudaEventCreate failed");
+    }
   }
   AL(c->rec, 1);
   AL(c->gate, 1);

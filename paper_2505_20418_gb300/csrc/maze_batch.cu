@@ -243,11 +243,12 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_step(BatchArgs b) {
 // to 64^3): move, spread and cell list with cluster barriers, then the solve.
 // The forces (S7-S9) follow as their own wide launch.
 constexpr size_t kStepSortBytes = (size_t)(kMixedClusterThreads / 32) * kSortCap * sizeof(int);
-__global__ void __launch_bounds__(kMixedClusterThreads, 1) k_cluster_step(IonArgs ia, CellArgs ca, MixedArgs ma) {
+// S1-S3 of one single-box step in one cluster (move, spread, cell list);
+// false when the step does not run (an earlier step of the call failed).
+__device__ __forceinline__ bool cluster_front(const IonArgs& ia, const CellArgs& ca, const MixedArgs& ma,
+                                             ClusterSync& sync, float* dsm) {
   // dynamic shared memory: the cell sort's buffers, then (after a barrier)
   // the resident V-cycle
-  extern __shared__ __align__(16) float dsm[];
-  ClusterSync sync;
   const unsigned rank = (unsigned)sync.rank();
   const int C = sync.size();
   const int tid = (int)rank * blockDim.x + threadIdx.x, stride = C * blockDim.x;
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(kMixedClusterThreads, 1) k_cluster_step(IonArg
   // every CTA reads the same value: nothing writes it during this launch
   const bool skip = __ldcg(&ia.rec->status) != MAZE_OK;
   if (rank == 0 && threadIdx.x == 0) *ia.gate = skip ? 1 : 0;
-  if (skip) return;
+  if (skip) return false;
   if (threadIdx.x == 0) {
     // S4 reads both potentials and y of the whole box after S1-S3: start them
     // on their way into L2 now, each CTA one share (a hint: addresses inside
@@ -292,7 +293,23 @@ __global__ void __launch_bounds__(kMixedClusterThreads, 1) k_cluster_step(IonArg
     for (int c = (int)rank + C * warp; c < ca.ncell; c += C * (int)(blockDim.x >> 5)) cell_sort_one(ca, c, lane, ids);
   }
   __syncthreads();
+  return true;
+}
+
+__global__ void __launch_bounds__(kMixedClusterThreads, 1) k_cluster_step(IonArgs ia, CellArgs ca, MixedArgs ma) {
+  // dynamic shared memory: the cell sort's buffers, then (after a barrier)
+  // the resident V-cycle
+  extern __shared__ __align__(16) float dsm[];
+  ClusterSync sync;
+  if (!cluster_front(ia, ca, ma, sync, dsm)) return;
   mixed_body(ma, sync, ma.resident ? dsm : nullptr);
+}
+
+// S1-S3 alone (the split step: the pairs then run beside the solve).
+__global__ void __launch_bounds__(kMixedClusterThreads, 1) k_cluster_front(IonArgs ia, CellArgs ca, MixedArgs ma) {
+  extern __shared__ __align__(16) float dsm[];
+  ClusterSync sync;
+  cluster_front(ia, ca, ma, sync, dsm);
 }
 
 // Largest cluster (16, else 8) of the fused step kernel the device can
@@ -302,6 +319,7 @@ int cluster_step_size() {
   static int cached = -1;
   if (cached >= 0) return cached;
   cudaFuncSetAttribute(k_cluster_step, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(k_cluster_front, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaFuncSetAttribute(k_cluster_step, cudaFuncAttributeMaxDynamicSharedMemorySize, kResidentSmem);
   cached = 0;
   for (int cta : {16, 8}) {
@@ -341,6 +359,23 @@ cudaError_t launch_cluster_step(const IonArgs& ia, const CellArgs& ca, const Mix
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_cluster_step, ia, ca, ma);
+}
+
+cudaError_t launch_cluster_front(const IonArgs& ia, const CellArgs& ca, const MixedArgs& ma, int cluster,
+                                 cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(kMixedClusterThreads);
+  cfg.gridDim = dim3(cluster);
+  cfg.dynamicSmemBytes = kStepSortBytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_cluster_front, ia, ca, ma);
 }
 
 __global__ void k_batch_clear(const BoxDesc* desc, const int* order, const int* count) {

@@ -76,6 +76,7 @@ struct maze_ctx {
   maze::MixedArgs mx = {};
   int mx_cluster = 0, mx_blocks = 0;
   bool fused_step = false;   // S1-S6 in one cluster launch (k_cluster_step)
+  bool split_step = false;   // S8 beside the one-cluster solve (k_pairs_cells, k_gather_finish)
   float *mx_scratch = nullptr, *mx_g = nullptr;
   int sblocks = 0;
   // cells
@@ -93,6 +94,11 @@ struct maze_ctx {
   int* gate = nullptr;             // device: current step skipped
   maze_stats* rec_host = nullptr;  // pinned
   bool rec_dirty = true;           // device record may differ from rec_host
+  // the split single-box step (mixed, one cluster): S8 on side_stream beside
+  // the solve, joined before S7/S9
+  double* pair_out = nullptr;
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // pinned staging of the per-ion host copies (standalone contexts, made on
   // first use): [0] maze_set of positions, [1] of velocities, [2] maze_get of
   // positions, [3] of velocities (and of the forces); an uploaded stage is

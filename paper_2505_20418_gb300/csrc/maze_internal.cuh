@@ -140,6 +140,7 @@ struct ForceArgs {
   LangevinArgs ou;       // second O step after the kick (when do_kick)
   double* part;          // [gridDim][8] block partials
   unsigned* ticket;      // last-block ticket (self-resetting)
+  double* pair_out;      // [n][4] pair sums per ion (the split step: S8 apart from S7/S9) or nullptr
   maze_stats* rec;
   const int* gate;       // 1: this step was skipped
 };
@@ -228,6 +229,10 @@ cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t s);   // k_move, th
 cudaError_t launch_q_to_double(const unsigned long long* qfix, double* q, int n, cudaStream_t s);
 cudaError_t launch_cells(const CellArgs& a, cudaStream_t s);
 cudaError_t launch_forces(const ForceArgs& a, int blocks, cudaStream_t s);
+cudaError_t launch_pairs(const ForceArgs& a, cudaStream_t s);
+cudaError_t launch_cluster_front(const IonArgs& ia, const CellArgs& ca, const MixedArgs& ma, int cluster,
+                                 cudaStream_t s);
+cudaError_t launch_gather_finish(const ForceArgs& a, int blocks, cudaStream_t s);
 int force_blocks(int n_ions);
 cudaError_t launch_cg_solve(const SolveArgs& a, int blocks, cudaStream_t s);
 int solve_blocks(int n_points);

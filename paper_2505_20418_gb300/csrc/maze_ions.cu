@@ -247,6 +247,60 @@ __global__ void __launch_bounds__(kForceThreads) k_forces_cells(ForceArgs a) {
   energy_reduce(a, acc);
 }
 
+// S8 alone, one block per (cell, slice): the pair sums of every ion to
+// a.pair_out (run beside the solve, which it does not depend on).
+__global__ void __launch_bounds__(kForceThreads) k_pairs_cells(ForceArgs a) {
+  __shared__ CellSmem<kForceThreads / 32> sm;
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  if (forces_live(a)) {
+    const int c = blockIdx.x / a.cell_split, s = blockIdx.x - c * a.cell_split;
+    forces_cell_slice<kForceThreads / 32, true>(a, c, s, a.cell_split, sm, acc);
+  }
+}
+
+// S7 + S9 after the solve: one warp gathers each ion's electrostatic force,
+// its pair sums come from a.pair_out, and the block finishes its ions one
+// per thread (the per-ion arithmetic of k_forces_cells).
+__global__ void __launch_bounds__(kForceThreads) k_gather_finish(ForceArgs a) {
+  constexpr int kW = kForceThreads / 32;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * kW + warp;
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  __shared__ double s_r[kW][8];
+  const bool live = forces_live(a);
+  if (i < a.n && live) {
+    double gx, gy, gz, vd;
+    gather_el(a, i, lane, gx, gy, gz, vd);
+    if (lane == 0) {
+      s_r[warp][0] = gx;
+      s_r[warp][1] = gy;
+      s_r[warp][2] = gz;
+      s_r[warp][3] = vd;
+    }
+    if (lane < 4) s_r[warp][4 + lane] = a.pair_out[(size_t)i * 4 + lane];
+  }
+  __syncthreads();
+  if (live && threadIdx.x < kW) {
+    const int ii = blockIdx.x * kW + threadIdx.x;
+    if (ii < a.n) {
+      const double* r = s_r[threadIdx.x];
+      finish_ion(a, ii, r[0], r[1], r[2], r[3], r[4], r[5], r[6], r[7], acc);
+    }
+  }
+  energy_reduce(a, acc);
+}
+
+cudaError_t launch_pairs(const ForceArgs& a, cudaStream_t s) {
+  k_pairs_cells<<<a.nc * a.nc * a.nc * a.cell_split, kForceThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_finish(const ForceArgs& a, int blocks, cudaStream_t s) {
+  k_gather_finish<<<blocks, kForceThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 int force_blocks(int n_ions) { return (n_ions + kForceThreads / 32 - 1) / (kForceThreads / 32); }
 
 cudaError_t launch_forces(const ForceArgs& a, int blocks, cudaStream_t s) {
