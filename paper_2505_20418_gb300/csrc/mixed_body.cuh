@@ -296,6 +296,23 @@ __device__ __forceinline__ int fdiv(int x, int d, unsigned m) {
   return m ? (int)__umulhi((unsigned)x, m) : x / d;
 }
 
+// Plane (local), in-plane offset, row and column of the natural-order index
+// m of a level: shifts when N is a power of two, else the multiply-high
+// division (or the division itself above 64^3).
+__device__ __forceinline__ void point_kji(const RLevel& v, int m, int& kl, int& rem, int& j, int& i) {
+  if (v.lg > 0) {
+    kl = m >> (2 * v.lg);
+    rem = m & (v.NN - 1);
+    j = rem >> v.lg;
+    i = rem & (v.N - 1);
+  } else {
+    kl = fdiv(m, v.NN, v.mNN);
+    rem = m - kl * v.NN;
+    j = fdiv(rem, v.N, v.mN);
+    i = rem - j * v.N;
+  }
+}
+
 struct Slabs {
   float* sm;         // this part's storage
   unsigned me, Q;    // part index and count
@@ -339,20 +356,22 @@ struct Slabs {
   }
 };
 
-// The tail of the V-cycle: the levels of at most 8^3 points, run by one CTA
-// (part 0) with block barriers instead of cluster or grid barriers. (A 16^3
-// half-sweep already costs one SM ~0.8 us, as much as a cluster barrier
-// phase; an 8^3 one ~0.2 us.)
-constexpr int kTailN = 8;
-__host__ __device__ __forceinline__ int tail_level(const MixedArgs& a) {
+// The tail of the V-cycle: the coarse levels run by one CTA (part 0) with
+// block barriers instead of cluster or grid barriers. In a cluster, the
+// levels of at most 8^3 points (a 16^3 half-sweep already costs one SM
+// ~0.8 us, as much as a cluster barrier phase; an 8^3 one ~0.2 us); in the
+// global form (one part, grid barriers of ~2 us), those of at most 16^3.
+// The global form keeps every level whole in its one part either way.
+__host__ __device__ __forceinline__ int tail_level(const MixedArgs& a, int Q) {
+  const int tn = Q == 1 ? 16 : 8;
   for (int l = 0; l < a.L; ++l)
-    if (a.Nl[l] <= kTailN) return l;
+    if (a.Nl[l] <= tn) return l;
   return a.L - 1;
 }
 
 // Planes per part of level l for Q parts (tail levels: all planes in part 0).
 __host__ __device__ __forceinline__ int slab_planes(const MixedArgs& a, int l, int Q) {
-  return l >= tail_level(a) ? a.Nl[l] : (a.Nl[l] + Q - 1) / Q;
+  return l >= tail_level(a, Q) ? a.Nl[l] : (a.Nl[l] + Q - 1) / Q;
 }
 
 // Floats of one part for Q parts.
@@ -402,7 +421,7 @@ __device__ __forceinline__ void slabs_setup(Slabs& R, const MixedArgs& a, float*
     R.me = me;
     R.Q = Q;
     R.L = a.L;
-    R.tail = tail_level(a);
+    R.tail = tail_level(a, (int)Q);
     R.dsmem = dsmem;
     unsigned off = 0;
     for (int k = 0; k < a.L; ++k) {
@@ -637,7 +656,8 @@ __device__ __forceinline__ void res_restrict(const Slabs& R, int l, int t0, int 
     const int Hc = Nc >> 1;
     for (int g = t0; g < (count >> 2); g += ts) {
       const int m = g << 2;
-      const int kl = fdiv(m, NNc, cv.mNN), rem = m - kl * NNc, J = fdiv(rem, Nc, cv.mN), I = rem - J * Nc;
+      int kl, rem, J, I;
+      point_kji(cv, m, kl, rem, J, I);
       const int K = K0 + kl;
       const int j0 = 2 * J, jm = j0 == 0 ? N - 1 : j0 - 1, jp = j0 + 1 == N ? 0 : j0 + 1;
       const int Im = I == 0 ? H - 1 : I - 1;
@@ -670,7 +690,8 @@ __device__ __forceinline__ void res_restrict(const Slabs& R, int l, int t0, int 
     return;
   }
   for (int m = t0; m < count; m += ts) {
-    const int kl = fdiv(m, NNc, cv.mNN), rem = m - kl * NNc, J = fdiv(rem, Nc, cv.mN), I = rem - J * Nc;
+    int kl, rem, J, I;
+    point_kji(cv, m, kl, rem, J, I);
     const int K = K0 + kl;
     const float* rp[3];
 #pragma unroll
@@ -938,7 +959,8 @@ __device__ __forceinline__ void s4_pass(const RLevel& v0, int t0, int ts, df c_s
   float rmax = 0.f, ymax = 0.f;
   for (int g = t0; g < (cnt0 >> 1); g += ts) {
     const int ml = g << 1;
-    const int kl = fdiv(ml, NN0, v0.mNN), rem = ml - kl * NN0, j = fdiv(rem, N0, v0.mN), i0 = rem - j * N0;
+    int kl, rem, j, i0;
+    point_kji(v0, ml, kl, rem, j, i0);
     const int k = v0.z0 + kl;
     const int m = k * NN0 + rem;
     const int xm = i0 == 0 ? m + N0 - 1 : m - 1, xp = i0 + 2 == N0 ? m + 2 - N0 : m + 2;
@@ -1035,7 +1057,8 @@ __device__ __forceinline__ void update_pass(const RLevel& v0, int t0, int ts, co
   float rmax = 0.f, ymax = 0.f;
   for (int g = t0; g < (cnt0 >> 1); g += ts) {
     const int ml = g << 1;
-    const int kl = fdiv(ml, NN0, v0.mNN), rem = ml - kl * NN0, j = fdiv(rem, N0, v0.mN), i0 = rem - j * N0;
+    int kl, rem, j, i0;
+    point_kji(v0, ml, kl, rem, j, i0);
     const int k = v0.z0 + kl;
     const int m = k * NN0 + rem;
     // the pair: A = (i0, j, k) of colour c0, B = (i0 + 1, j, k) of colour 1 - c0
@@ -1070,6 +1093,94 @@ __device__ __forceinline__ void update_pass(const RLevel& v0, int t0, int ts, co
     b0[(1 - c0) * PH0 + rowb + t] = rB;
     ymax = fmaxf(ymax, fmaxf(fabsf(nA.x), fabsf(nB.x)));
     rmax = fmaxf(rmax, fmaxf(fabsf(rA), fabsf(rB)));
+  }
+  rmax_o = rmax;
+  ymax_o = ymax;
+}
+
+// update_pass on four-point levels: a thread takes four x-adjacent points
+// P0 .. P3 (i0 a multiple of 4; P0, P2 of colour c0 at half-row indices t,
+// t+1, P1, P3 of the other colour at the same indices), each with the
+// arithmetic and neighbour order of update_pass (same results): 16-byte
+// loads of y, sigma_p and the neighbour rows, 8-byte loads of e, 8-byte
+// stores of r.
+__device__ __forceinline__ void update_pass4(const RLevel& v0, int t0, int ts, const float* __restrict__ e0,
+                                             const float* elo0, const float* elo1, const float* ehi0,
+                                             const float* ehi1, const float2* __restrict__ ycur,
+                                             float2* __restrict__ ynext, const float2* __restrict__ sig,
+                                             float* __restrict__ b0, float& rmax_o, float& ymax_o) {
+  const int N0 = v0.N, NN0 = v0.NN, own0 = v0.z1 - v0.z0, cnt0 = own0 * NN0;
+  const int H0 = N0 >> 1, HH0 = NN0 >> 1, PH0 = v0.P * HH0;
+  auto ld2x2 = [](const float2* p, float2& a, float2& b) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+  };
+  auto ldf2 = [](const float* p) { return *reinterpret_cast<const float2*>(p); };
+  float rmax = 0.f, ymax = 0.f;
+  for (int g = t0; g < (cnt0 >> 2); g += ts) {
+    const int ml = g << 2;
+    int kl, rem, j, i0;
+    point_kji(v0, ml, kl, rem, j, i0);
+    const int k = v0.z0 + kl;
+    const int m = k * NN0 + rem;
+    const int c0 = (i0 + j + k) & 1, t = i0 >> 1, rowb = kl * HH0 + j * H0;
+    const float* EA = e0 + c0 * PH0;
+    const float* EB = e0 + (1 - c0) * PH0;
+    const int rjm = kl * HH0 + (j == 0 ? N0 - 1 : j - 1) * H0 + t, rjp = kl * HH0 + (j == N0 - 1 ? 0 : j + 1) * H0 + t;
+    const float* lA = kl > 0 ? EB + rowb - HH0 : (c0 ? elo0 : elo1) + j * H0;
+    const float* lB = kl > 0 ? EA + rowb - HH0 : (c0 ? elo1 : elo0) + j * H0;
+    const float* hA = kl < own0 - 1 ? EB + rowb + HH0 : (c0 ? ehi0 : ehi1) + j * H0;
+    const float* hB = kl < own0 - 1 ? EA + rowb + HH0 : (c0 ? ehi1 : ehi0) + j * H0;
+    const float2 eA = ldf2(EA + rowb + t), eB = ldf2(EB + rowb + t);
+    const float eBm = EB[rowb + (t == 0 ? H0 - 1 : t - 1)], eAp = EA[rowb + (t + 2 == H0 ? 0 : t + 2)];
+    const float2 eBjm = ldf2(EB + rjm), eBjp = ldf2(EB + rjp), eAjm = ldf2(EA + rjm), eAjp = ldf2(EA + rjp);
+    const float2 lA2 = ldf2(lA + t), lB2 = ldf2(lB + t), hA2 = ldf2(hA + t), hB2 = ldf2(hB + t);
+    float2 y0, y1, y2, y3, ym0, ym1, ym2, ym3, yp0, yp1, yp2, yp3, zm0, zm1, zm2, zm3, zp0, zp1, zp2, zp3, s0, s1, s2, s3;
+    const int mjm = j == 0 ? m + NN0 - N0 : m - N0, mjp = j == N0 - 1 ? m - NN0 + N0 : m + N0;
+    const int mkm = k == 0 ? m + NN0 * (N0 - 1) : m - NN0, mkp = k == N0 - 1 ? m - NN0 * (N0 - 1) : m + NN0;
+    ld2x2(ycur + m, y0, y1);
+    ld2x2(ycur + m + 2, y2, y3);
+    ld2x2(ycur + mjm, ym0, ym1);
+    ld2x2(ycur + mjm + 2, ym2, ym3);
+    ld2x2(ycur + mjp, yp0, yp1);
+    ld2x2(ycur + mjp + 2, yp2, yp3);
+    ld2x2(ycur + mkm, zm0, zm1);
+    ld2x2(ycur + mkm + 2, zm2, zm3);
+    ld2x2(ycur + mkp, zp0, zp1);
+    ld2x2(ycur + mkp + 2, zp2, zp3);
+    ld2x2(sig + m, s0, s1);
+    ld2x2(sig + m + 2, s2, s3);
+    const float2 yxm = ycur[i0 == 0 ? m + N0 - 1 : m - 1];
+    const float2 yxp = ycur[i0 + 4 == N0 ? m + 4 - N0 : m + 4];
+    float2 n0, n1, n2, n3;
+    float r0, r1, r2, r3;
+    {
+      const float2 yn[6] = {yxm, y1, ym0, yp0, zm0, zp0};
+      const float en[6] = {eBm, eB.x, eBjm.x, eBjp.x, lA2.x, hA2.x};
+      upd_point(yn, en, y0, eA.x, s0, n0, r0);
+    }
+    {
+      const float2 yn[6] = {y0, y2, ym1, yp1, zm1, zp1};
+      const float en[6] = {eA.x, eA.y, eAjm.x, eAjp.x, lB2.x, hB2.x};
+      upd_point(yn, en, y1, eB.x, s1, n1, r1);
+    }
+    {
+      const float2 yn[6] = {y1, y3, ym2, yp2, zm2, zp2};
+      const float en[6] = {eB.x, eB.y, eBjm.y, eBjp.y, lA2.y, hA2.y};
+      upd_point(yn, en, y2, eA.y, s2, n2, r2);
+    }
+    {
+      const float2 yn[6] = {y2, yxp, ym3, yp3, zm3, zp3};
+      const float en[6] = {eA.y, eAp, eAjm.y, eAjp.y, lB2.y, hB2.y};
+      upd_point(yn, en, y3, eB.y, s3, n3, r3);
+    }
+    *reinterpret_cast<float4*>(ynext + m) = make_float4(n0.x, n0.y, n1.x, n1.y);
+    *reinterpret_cast<float4*>(ynext + m + 2) = make_float4(n2.x, n2.y, n3.x, n3.y);
+    *reinterpret_cast<float2*>(b0 + c0 * PH0 + rowb + t) = make_float2(r0, r2);
+    *reinterpret_cast<float2*>(b0 + (1 - c0) * PH0 + rowb + t) = make_float2(r1, r3);
+    ymax = fmaxf(ymax, fmaxf(fmaxf(fabsf(n0.x), fabsf(n1.x)), fmaxf(fabsf(n2.x), fabsf(n3.x))));
+    rmax = fmaxf(rmax, fmaxf(fmaxf(fabsf(r0), fabsf(r1)), fmaxf(fabsf(r2), fabsf(r3))));
   }
   rmax_o = rmax;
   ymax_o = ymax;
@@ -1206,8 +1317,12 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
     {
       const int zlo = (v0.z0 - 1 + N0) % N0, zhi = v0.z1 % N0;
       float rmax, ymax;
-      update_pass(v0, t0, ts, e0, R.cplane(v0, 0, 0, zlo), R.cplane(v0, 0, 1, zlo), R.cplane(v0, 0, 0, zhi),
-                  R.cplane(v0, 0, 1, zhi), ycur, ynext, a.sigma, r0, rmax, ymax);
+      if (quad_level(v0))
+        update_pass4(v0, t0, ts, e0, R.cplane(v0, 0, 0, zlo), R.cplane(v0, 0, 1, zlo), R.cplane(v0, 0, 0, zhi),
+                     R.cplane(v0, 0, 1, zhi), ycur, ynext, a.sigma, r0, rmax, ymax);
+      else
+        update_pass(v0, t0, ts, e0, R.cplane(v0, 0, 0, zlo), R.cplane(v0, 0, 1, zlo), R.cplane(v0, 0, 0, zhi),
+                    R.cplane(v0, 0, 1, zhi), ycur, ynext, a.sigma, r0, rmax, ymax);
       ++it;
       float2* t2 = ycur;
       ycur = ynext;
