@@ -383,14 +383,12 @@ def main():
         n_e2e = min(args.steps, 100)
         if world > 1:
             dist.barrier()
+        rec = M.MazeStats()
         t0 = time.perf_counter()
         for _ in range(n_e2e):
-            sim.set(M.MAZE_POS, hpn)
-            sim.set(M.MAZE_VEL, hvn)
-            sim.step(1)
-            M.maze_get(sim.h, M.MAZE_POS, hpn)
-            M.maze_get(sim.h, M.MAZE_VEL, hvn)
-            sim.stats()
+            # maze_step_io: upload, one step, positions, velocities and the
+            # record back, one synchronisation
+            sim.step_io(1, pos=hpn, vel=hvn, out_pos=hpn, out_vel=hvn, stats=rec)
         e2e_s = max_over_ranks(time.perf_counter() - t0, dist if world > 1 else None, dev)
         e2e = {"value": weak_scaling_value(world, n_e2e, e2e_s), "unit": "steps/s",
                "h2d_bytes_per_step": 2 * 24 * w.n_ions,

@@ -223,6 +223,21 @@ maze_status maze_set(maze_ctx* ctx, int32_t what, const double* host_in);
 /* Copy the per-step record to *out. Synchronises. */
 maze_status maze_get_stats(maze_ctx* ctx, maze_stats* out);
 
+/* One exchange of a host-driven simulation in a single call: optional new
+ * positions and velocities (host memory, [n][3], as maze_set: positions
+ * wrapped into [0, L), forces not recomputed), then nsteps steps (S1..S9 as
+ * maze_step), then optional copies of the positions and velocities
+ * ([n][3]) and of the per-step record to host memory. Synchronises once.
+ * Any of pos_in, vel_in, pos_out, vel_out, stats_out may be NULL. A
+ * non-finite input returns MAZE_ERR_INVALID before anything is uploaded or
+ * run. The return value is maze_step's; when the steps ran (also with
+ * MAZE_ERR_NOT_CONVERGED, MAZE_ERR_NONFINITE or MAZE_ERR_TIMEOUT) the
+ * outputs hold the state they left; after a CUDA or argument error they
+ * are not written. The results equal maze_set, maze_step, maze_get and
+ * maze_get_stats called in that order. */
+maze_status maze_step_io(maze_ctx* ctx, const double* pos_in, const double* vel_in, int32_t nsteps,
+                         double* pos_out, double* vel_out, maze_stats* stats_out);
+
 /* Checkpoint: the full dynamical state (step, V_work, positions, velocities,
  * forces, phi^k, phi^{k-1}, y) as an opaque blob. With blob == NULL,
  * maze_get_state stores the needed size in *n. Restoring a blob from a

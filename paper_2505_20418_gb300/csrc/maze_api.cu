@@ -115,8 +115,10 @@ maze_status validate(const maze_config* c) {
 }
 
 double wrap_host(double x, double L) {
+  if (x >= 0.0 && x < L) return x;
   x -= L * floor(x / L);
-  if (x >= L) x -= L;
+  if (x < 0.0) x += L;   // (x / L rounded up to the next integer)
+  if (x >= L) x = 0.0;   // (within rounding of L, i.e. of 0)
   return x;
 }
 
@@ -495,15 +497,23 @@ maze_status read_stats(maze_ctx* c) {
 }
 
 // The pinned staging buffer k of the per-ion host copies (3 n doubles), made
-// on first use.
+// on first use in pairs: stages 0 and 1 (uploads of the positions and
+// velocities) are one block, 2 and 3 (their reads) another, each laid out as
+// the device's positions followed by its velocities, so that both move in
+// one copy.
 maze_status stage_buffer(maze_ctx* c, int k) {
   if (c->stage[k]) return MAZE_OK;
-  if (cudaMallocHost(&c->stage[k], 3 * (size_t)c->n * sizeof(double)) != cudaSuccess) {
-    c->stage[k] = nullptr;
+  const int k0 = k & ~1;
+  const size_t n3 = 3 * (size_t)c->n;
+  double* b = nullptr;
+  if (cudaMallocHost(&b, 2 * n3 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return fail(MAZE_ERR_OOM, "cudaMallocHost failed");
   }
-  if (k < 2) CK(cudaEventCreateWithFlags(&c->stage_ev[k], cudaEventDisableTiming));
+  c->stage[k0] = b;
+  c->stage[k0 + 1] = b + n3;
+  if (k0 == 0)
+    for (int q = 0; q < 2; ++q) CK(cudaEventCreateWithFlags(&c->stage_ev[q], cudaEventDisableTiming));
   return MAZE_OK;
 }
 
@@ -537,7 +547,7 @@ void free_ctx(maze_ctx* c) {
   }
   if (c->rec_host) cudaFreeHost(c->rec_host);
   for (int k = 0; k < 4; ++k)
-    if (c->stage[k]) cudaFreeHost(c->stage[k]);
+    if (c->stage[k] && !(k & 1)) cudaFreeHost(c->stage[k]);   // (odd stages live in the even ones' blocks)
   for (int k = 0; k < 2; ++k)
     if (c->stage_ev[k]) cudaEventDestroy(c->stage_ev[k]);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -545,6 +555,77 @@ void free_ctx(maze_ctx* c) {
   if (c->side_stream) cudaStreamDestroy(c->side_stream);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
+}
+
+bool ion_finite(const maze_ctx* c, const double* in) {
+  for (size_t i = 0; i < 3 * (size_t)c->n; ++i)
+    if (!isfinite(in[i])) return false;
+  return true;
+}
+
+// [n][3] host order -> [3][n] (positions wrapped into [0, L) when wrap).
+void to_soa(const double* in, double* out, int n, bool wrap, double L) {
+  double* o0 = out;
+  double* o1 = out + n;
+  double* o2 = out + 2 * (size_t)n;
+  for (int i = 0; i < n; ++i) {
+    const double* p = in + 3 * (size_t)i;
+    o0[i] = wrap ? wrap_host(p[0], L) : p[0];
+    o1[i] = wrap ? wrap_host(p[1], L) : p[1];
+    o2[i] = wrap ? wrap_host(p[2], L) : p[2];
+  }
+}
+
+// [3][n] -> [n][3] host order.
+void to_aos(const double* in, double* out, int n) {
+  const double* i0 = in;
+  const double* i1 = in + n;
+  const double* i2 = in + 2 * (size_t)n;
+  for (int i = 0; i < n; ++i) {
+    double* p = out + 3 * (size_t)i;
+    p[0] = i0[i];
+    p[1] = i1[i];
+    p[2] = i2[i];
+  }
+}
+
+// Upload of the positions (in[0], wrapped into [0, L)) and / or velocities
+// (in[1]) from host memory in [n][3] order, checked finite by the caller.
+// The values go through pinned stages of the context, so the upload is
+// asynchronous on the stream: the caller's buffers are read only here. Both
+// together move in one copy (the device keeps the velocities right after
+// the positions, the stages likewise).
+maze_status upload_ions(maze_ctx* c, const double* const (&in)[2]) {
+  const int n = c->n;
+  const size_t n3 = 3 * (size_t)n;
+  if (c->arena) {   // a batch box: a temporary and a synchronous copy
+    std::vector<double> tmp(n3);
+    for (int k = 0; k < 2; ++k) {
+      if (!in[k]) continue;
+      c->staged_fresh[k] = false;
+      to_soa(in[k], tmp.data(), n, k == 0, c->L);
+      CK(cudaMemcpyAsync(k == 0 ? c->pos : c->vel, tmp.data(), n3 * 8, cudaMemcpyHostToDevice, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+    }
+    return MAZE_OK;
+  }
+  maze_status st = stage_buffer(c, 0);
+  if (st != MAZE_OK) return st;
+  for (int k = 0; k < 2; ++k) {
+    if (!in[k]) continue;
+    c->staged_fresh[k] = false;
+    CK(cudaEventSynchronize(c->stage_ev[k]));   // the stage's previous upload has been read
+    to_soa(in[k], c->stage[k], n, k == 0, c->L);
+  }
+  if (in[0] && in[1]) {
+    CK(cudaMemcpyAsync(c->pos, c->stage[0], 2 * n3 * 8, cudaMemcpyHostToDevice, c->stream));
+  } else {
+    const int k = in[0] ? 0 : 1;
+    CK(cudaMemcpyAsync(k == 0 ? c->pos : c->vel, c->stage[k], n3 * 8, cudaMemcpyHostToDevice, c->stream));
+  }
+  for (int k = 0; k < 2; ++k)
+    if (in[k]) CK(cudaEventRecord(c->stage_ev[k], c->stream));
+  return MAZE_OK;
 }
 
 }  // namespace maze
@@ -625,8 +706,8 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
       return s_;                            \
     }                                       \
   } while (0)
-  AL(c->pos, 3 * (size_t)n);
-  AL(c->vel, 3 * (size_t)n);
+  AL(c->pos, 6 * (size_t)n);   // the velocities right after the positions (one copy moves both)
+  c->vel = c->pos + 3 * (size_t)n;
   AL(c->force, 3 * (size_t)n);
   AL(c->force_el, 3 * (size_t)n);
   AL(c->type, (size_t)n);
@@ -968,14 +1049,19 @@ maze_status maze_step(maze_ctx* c, int32_t nsteps) {
   // positions and velocities were read back after the previous step: queue
   // their copies now, so that the record read below waits for all at once
   bool queued[2] = {false, false};
-  if (!c->arena)
-    for (int k = 0; k < 2; ++k)
-      if (c->want_ion[k] && stage_buffer(c, 2 + k) == MAZE_OK) {
-        CK(cudaMemcpyAsync(c->stage[2 + k], k == 0 ? c->pos : c->vel, 3 * (size_t)c->n * 8, cudaMemcpyDeviceToHost,
-                           c->stream));
-        queued[k] = true;
-        c->want_ion[k] = false;
-      }
+  if (!c->arena && (c->want_ion[0] || c->want_ion[1]) && stage_buffer(c, 2) == MAZE_OK) {
+    const size_t n3 = 3 * (size_t)c->n;
+    if (c->want_ion[0] && c->want_ion[1]) {
+      CK(cudaMemcpyAsync(c->stage[2], c->pos, 2 * n3 * 8, cudaMemcpyDeviceToHost, c->stream));
+    } else {
+      const int k = c->want_ion[0] ? 0 : 1;
+      CK(cudaMemcpyAsync(c->stage[2 + k], k == 0 ? c->pos : c->vel, n3 * 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+    for (int k = 0; k < 2; ++k) {
+      queued[k] = c->want_ion[k];
+      c->want_ion[k] = false;
+    }
+  }
   s = read_stats(c);
   if (s != MAZE_OK) return s;
   c->staged_fresh[0] = queued[0];
@@ -1066,8 +1152,7 @@ maze_status maze_get(maze_ctx* c, int32_t what, double* out) {
       CK(cudaMemcpyAsync(tmp, src, 3 * (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream));
       CK(cudaStreamSynchronize(c->stream));
     }
-    for (int d = 0; d < 3; ++d)
-      for (int i = 0; i < n; ++i) out[3 * i + d] = tmp[(size_t)d * n + i];
+    to_aos(tmp, out, n);
   } else {
     CK(cudaMemcpyAsync(out, src, c->ng * 8, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -1096,35 +1181,9 @@ maze_status maze_set(maze_ctx* c, int32_t what, const double* in) {
     default: return fail(MAZE_ERR_INVALID, "quantity cannot be set");
   }
   if (ion) {
-    // the values go through a pinned stage of the context, so the upload is
-    // asynchronous on the stream: the caller's buffer is read only here
-    const int n = c->n;
-    for (int d = 0; d < 3; ++d)
-      for (int i = 0; i < n; ++i)
-        if (!isfinite(in[3 * i + d])) return fail(MAZE_ERR_INVALID, "non-finite input");
-    const int k = what == MAZE_POS ? 0 : 1;
-    c->staged_fresh[k] = false;
-    std::vector<double> tmpv;
-    double* tmp = nullptr;
-    if (c->arena) {   // a batch box: a temporary and a synchronous copy
-      tmpv.resize(3 * (size_t)n);
-      tmp = tmpv.data();
-    } else {
-      maze_status st = stage_buffer(c, k);
-      if (st != MAZE_OK) return st;
-      CK(cudaEventSynchronize(c->stage_ev[k]));   // the stage's previous upload has been read
-      tmp = c->stage[k];
-    }
-    for (int d = 0; d < 3; ++d)
-      for (int i = 0; i < n; ++i) {
-        const double v = in[3 * i + d];
-        tmp[(size_t)d * n + i] = what == MAZE_POS ? wrap_host(v, c->L) : v;
-      }
-    CK(cudaMemcpyAsync(dst, tmp, 3 * (size_t)n * 8, cudaMemcpyHostToDevice, c->stream));
-    if (c->arena)
-      CK(cudaStreamSynchronize(c->stream));
-    else
-      CK(cudaEventRecord(c->stage_ev[k], c->stream));
+    if (!ion_finite(c, in)) return fail(MAZE_ERR_INVALID, "non-finite input");
+    const double* const ins[2] = {what == MAZE_POS ? in : nullptr, what == MAZE_VEL ? in : nullptr};
+    return upload_ions(c, ins);
   } else if (c->mixed) {
     // double -> double-float pair (hi = nearest float, lo = remainder)
     std::vector<float2> tmp(c->ng);
@@ -1138,6 +1197,41 @@ maze_status maze_set(maze_ctx* c, int32_t what, const double* in) {
     CK(cudaMemcpyAsync(dst, in, c->ng * 8, cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
   }
+  return MAZE_OK;
+}
+
+maze_status maze_step_io(maze_ctx* c, const double* pos_in, const double* vel_in, int32_t nsteps, double* pos_out,
+                         double* vel_out, maze_stats* stats_out) {
+  if (!c) return fail(MAZE_ERR_INVALID, "ctx is NULL");
+  if (nsteps < 0) return fail(MAZE_ERR_INVALID, "nsteps must be >= 0");
+  // both inputs are checked before anything is uploaded or run
+  if ((pos_in && !ion_finite(c, pos_in)) || (vel_in && !ion_finite(c, vel_in)))
+    return fail(MAZE_ERR_INVALID, "non-finite input");
+  maze_status s;
+  if (pos_in || vel_in) {
+    const double* const ins[2] = {pos_in, vel_in};
+    if ((s = upload_ions(c, ins)) != MAZE_OK) return s;
+  }
+  // maze_step queues the copies of the wanted quantities together with its
+  // record read (one synchronisation)
+  if (!c->arena) {
+    c->want_ion[0] = pos_out != nullptr;
+    c->want_ion[1] = vel_out != nullptr;
+  }
+  s = maze_step(c, nsteps);
+  if (c->rec_dirty) return s;   // the step did not reach its record read: no outputs
+  double* outs[2] = {pos_out, vel_out};
+  for (int k = 0; k < 2; ++k) {
+    if (!outs[k]) continue;
+    if (!c->arena && c->staged_fresh[k]) {
+      to_aos(c->stage[2 + k], outs[k], c->n);
+    } else {
+      const maze_status g = maze_get(c, k == 0 ? MAZE_POS : MAZE_VEL, outs[k]);
+      if (g != MAZE_OK) return g;
+    }
+  }
+  if (stats_out) *stats_out = *c->rec_host;
+  if (s != MAZE_OK) return status_message(c);   // (the step's message again, after maze_get)
   return MAZE_OK;
 }
 

@@ -26,7 +26,7 @@ MAZE_PHI, MAZE_PHI_PREV, MAZE_Y, MAZE_CHARGE, MAZE_SIGMA = 4, 5, 6, 7, 8
 
 # every entry point declared in include/maze.h
 EXPORTS = ("maze_create", "maze_spread", "maze_solve", "maze_gather", "maze_step",
-           "maze_step_async", "maze_get", "maze_set", "maze_get_stats", "maze_get_state",
+           "maze_step_async", "maze_get", "maze_set", "maze_get_stats", "maze_step_io", "maze_get_state",
            "maze_set_state", "maze_destroy", "maze_last_error", "maze_version",
            "maze_set_timing", "maze_get_timing", "maze_solve_shake_noalloc",
            "maze_batch_create", "maze_batch_box_bytes", "maze_batch_free_bytes", "maze_batch_add",
@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH):
     lib.maze_get.argtypes = [P, _I, ctypes.POINTER(_D)]
     lib.maze_set.argtypes = [P, _I, ctypes.POINTER(_D)]
     lib.maze_get_stats.argtypes = [P, ctypes.POINTER(MazeStats)]
+    lib.maze_step_io.argtypes = [P, P, P, _I, P, P, ctypes.POINTER(MazeStats)]
     lib.maze_get_state.argtypes = [P, P, ctypes.POINTER(ctypes.c_size_t)]
     lib.maze_set_state.argtypes = [P, P, ctypes.c_size_t]
     lib.maze_set_timing.argtypes = [P, _I]
@@ -183,6 +184,24 @@ def maze_get_stats(h) -> MazeStats:
     s = MazeStats()
     _check(load().maze_get_stats(h, ctypes.byref(s)))
     return s
+
+
+def _ion_ptr(a, n, writable):
+    """Address of an [n][3] float64 C-contiguous array (None -> NULL)."""
+    if a is None:
+        return None
+    if (type(a) is not np.ndarray or a.dtype != np.float64 or a.shape != (n, 3)
+            or not a.flags.c_contiguous or (writable and not a.flags.writeable)):
+        raise ValueError(f"expected a C-contiguous float64 array of shape ({n}, 3)")
+    return a.ctypes.data
+
+
+def maze_step_io(h, n: int, pos_in, vel_in, nsteps: int, pos_out, vel_out, stats=None):
+    """maze_step_io: inputs, steps and outputs in one call (arrays [n][3] or
+    None; stats a MazeStats or None). Returns the status, as maze_step."""
+    return load().maze_step_io(h, _ion_ptr(pos_in, n, False), _ion_ptr(vel_in, n, False), int(nsteps),
+                               _ion_ptr(pos_out, n, True), _ion_ptr(vel_out, n, True),
+                               None if stats is None else ctypes.byref(stats))
 
 
 def maze_get_state(h) -> bytes:
@@ -313,6 +332,11 @@ class MazeSim:
 
     def step_async(self, nsteps=1):
         maze_step_async(self.h, nsteps)
+
+    def step_io(self, nsteps=1, pos=None, vel=None, out_pos=None, out_vel=None, stats=None):
+        """Upload pos / vel (if given), run nsteps steps, fill out_pos / out_vel
+        / stats (if given): one call, one synchronisation."""
+        _check(maze_step_io(self.h, self.n, pos, vel, nsteps, out_pos, out_vel, stats))
 
     def spread(self):
         maze_spread(self.h)

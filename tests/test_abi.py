@@ -135,5 +135,6 @@ def test_null_context_calls_are_errors(lib):
     assert lib.maze_spread(None) == M.MAZE_ERR_INVALID
     assert lib.maze_step(None, 1) == M.MAZE_ERR_INVALID
     assert lib.maze_gather(None) == M.MAZE_ERR_INVALID
+    assert lib.maze_step_io(None, None, None, 1, None, None, None) == M.MAZE_ERR_INVALID
     lib.maze_destroy(None)  # NULL-safe
     assert M.maze_version().startswith("maze-gb300")

@@ -1,4 +1,5 @@
-"""Host copies of a standalone context (maze_set / maze_get / maze_get_stats).
+"""Host copies of a standalone context (maze_set / maze_get / maze_get_stats
+and the one-call exchange maze_step_io).
 
 maze_set uploads positions and velocities from a pinned stage without
 synchronising, maze_step queues the copies of the positions and velocities
@@ -61,4 +62,59 @@ def test_set_then_get_without_a_step_returns_the_new_values():
     x = np.mod(a.get(M.MAZE_POS) + 0.5, w.L)
     a.set(M.MAZE_POS, x)
     assert np.allclose(a.get(M.MAZE_POS), x, atol=0, rtol=0)
+    a.close()
+
+
+def test_step_io_equals_set_step_get_stats():
+    """maze_step_io against maze_set, maze_step, maze_get and maze_get_stats
+    on a twin context, bit for bit, with and without inputs and outputs."""
+    w = synth.workload("nacl1000")
+    a, b = make(w), make(w)
+    n = w.n_ions
+    rng = np.random.default_rng(11)
+    x, v = a.get(M.MAZE_POS), a.get(M.MAZE_VEL)
+    cases = [(True, True, 1, True, True), (False, False, 2, True, False), (True, False, 1, False, True),
+             (False, True, 0, True, True), (False, False, 1, False, False), (True, True, 3, True, True)]
+    for pin, vin, nsteps, pout, vout in cases:
+        x = np.mod(x + rng.normal(scale=1e-3, size=(n, 3)), w.L)
+        v = v * 0.9995
+        st = M.MazeStats()
+        po = np.full((n, 3), np.nan) if pout else None
+        vo = np.full((n, 3), np.nan) if vout else None
+        a.step_io(nsteps, pos=x if pin else None, vel=v if vin else None, out_pos=po, out_vel=vo, stats=st)
+        if pin:
+            b.set(M.MAZE_POS, x)
+        if vin:
+            b.set(M.MAZE_VEL, v)
+        assert M.maze_step(b.h, nsteps) == M.MAZE_OK
+        sb = b.stats()
+        sa = st.as_dict()
+        assert sa == sb, (pin, vin, nsteps)
+        if pout:
+            assert np.array_equal(po, b.get(M.MAZE_POS))
+        if vout:
+            assert np.array_equal(vo, b.get(M.MAZE_VEL))
+        # and the context's own reads agree afterwards
+        assert np.array_equal(a.get(M.MAZE_FORCE), b.get(M.MAZE_FORCE))
+        x, v = b.get(M.MAZE_POS), b.get(M.MAZE_VEL)
+    a.close()
+    b.close()
+
+
+def test_step_io_rejects_non_finite_input_before_running():
+    w = synth.workload("nacl1000")
+    a = make(w)
+    a.step(1)
+    before = a.stats()["step"]
+    x = a.get(M.MAZE_POS)
+    v = a.get(M.MAZE_VEL)
+    v[7, 2] = np.inf
+    po = np.zeros_like(x)
+    st = M.maze_step_io(a.h, w.n_ions, x + 0.1, v, 1, po, None)
+    assert st == M.MAZE_ERR_INVALID
+    assert a.stats()["step"] == before
+    assert np.array_equal(a.get(M.MAZE_POS), x)     # the valid positions were not uploaded either
+    assert not po.any()
+    with pytest.raises(ValueError):
+        a.step_io(1, out_pos=np.zeros((w.n_ions, 2)))
     a.close()
