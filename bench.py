@@ -230,6 +230,8 @@ def config_dict(w, args):
 # command and the other counters are in the named summary under profiles/.
 # A kernel changed after its capture must drop its entry (traffic null).
 MEASURED_TRAFFIC = {
+    ("nacl1000", "k_mixed_cluster", "mixed", "mg"): (1195520, "profiles/k_mixed_cluster_nacl1000.md"),
+    ("nacl512000", "k_mixed_grid", "mixed", "mg"): (10840736000, "profiles/k_mixed_grid_nacl512000.md"),
 }
 
 
