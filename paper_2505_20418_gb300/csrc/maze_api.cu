@@ -7,7 +7,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "maze_ctx.h"
@@ -557,36 +559,63 @@ void free_ctx(maze_ctx* c) {
   delete c;
 }
 
+// fn(lo, hi) over [0, n) in chunks on host threads for large n (the per-ion
+// host loops of big boxes), else in the calling thread.
+template <class F>
+void host_ranges(int n, F fn) {
+  constexpr int kMinPerThread = 16384;
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int T = std::min(std::min(16, hw > 1 ? (int)hw / 2 : 1), n / kMinPerThread);
+  if (T <= 1) {
+    fn(0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(T - 1);
+  const int chunk = (n + T - 1) / T;
+  for (int t = 1; t < T; ++t) th.emplace_back(fn, std::min(n, t * chunk), std::min(n, (t + 1) * chunk));
+  fn(0, std::min(n, chunk));
+  for (auto& x : th) x.join();
+}
+
 bool ion_finite(const maze_ctx* c, const double* in) {
-  for (size_t i = 0; i < 3 * (size_t)c->n; ++i)
-    if (!isfinite(in[i])) return false;
-  return true;
+  std::atomic<bool> bad{false};
+  host_ranges(c->n, [&](int lo, int hi) {
+    bool b = false;
+    for (size_t i = 3 * (size_t)lo; i < 3 * (size_t)hi; ++i) b |= !isfinite(in[i]);
+    if (b) bad.store(true, std::memory_order_relaxed);
+  });
+  return !bad.load();
 }
 
 // [n][3] host order -> [3][n] (positions wrapped into [0, L) when wrap).
 void to_soa(const double* in, double* out, int n, bool wrap, double L) {
-  double* o0 = out;
-  double* o1 = out + n;
-  double* o2 = out + 2 * (size_t)n;
-  for (int i = 0; i < n; ++i) {
-    const double* p = in + 3 * (size_t)i;
-    o0[i] = wrap ? wrap_host(p[0], L) : p[0];
-    o1[i] = wrap ? wrap_host(p[1], L) : p[1];
-    o2[i] = wrap ? wrap_host(p[2], L) : p[2];
-  }
+  host_ranges(n, [=](int lo, int hi) {
+    double* o0 = out;
+    double* o1 = out + n;
+    double* o2 = out + 2 * (size_t)n;
+    for (int i = lo; i < hi; ++i) {
+      const double* p = in + 3 * (size_t)i;
+      o0[i] = wrap ? wrap_host(p[0], L) : p[0];
+      o1[i] = wrap ? wrap_host(p[1], L) : p[1];
+      o2[i] = wrap ? wrap_host(p[2], L) : p[2];
+    }
+  });
 }
 
 // [3][n] -> [n][3] host order.
 void to_aos(const double* in, double* out, int n) {
-  const double* i0 = in;
-  const double* i1 = in + n;
-  const double* i2 = in + 2 * (size_t)n;
-  for (int i = 0; i < n; ++i) {
-    double* p = out + 3 * (size_t)i;
-    p[0] = i0[i];
-    p[1] = i1[i];
-    p[2] = i2[i];
-  }
+  host_ranges(n, [=](int lo, int hi) {
+    const double* i0 = in;
+    const double* i1 = in + n;
+    const double* i2 = in + 2 * (size_t)n;
+    for (int i = lo; i < hi; ++i) {
+      double* p = out + 3 * (size_t)i;
+      p[0] = i0[i];
+      p[1] = i1[i];
+      p[2] = i2[i];
+    }
+  });
 }
 
 // Upload of the positions (in[0], wrapped into [0, L)) and / or velocities

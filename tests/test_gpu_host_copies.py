@@ -118,3 +118,26 @@ def test_step_io_rejects_non_finite_input_before_running():
     with pytest.raises(ValueError):
         a.step_io(1, out_pos=np.zeros((w.n_ions, 2)))
     a.close()
+
+
+def test_step_io_large_box_host_threads():
+    """64000 ions: the host transposes and checks run on several threads;
+    the results equal the single-call sequence bit for bit."""
+    w = synth.workload("nacl64000")
+    a, b = make(w), make(w)
+    n = w.n_ions
+    x = np.mod(a.get(M.MAZE_POS) + 1e-3, w.L)
+    v = a.get(M.MAZE_VEL) * 0.999
+    po, vo = np.empty((n, 3)), np.empty((n, 3))
+    st = M.MazeStats()
+    a.step_io(1, pos=x, vel=v, out_pos=po, out_vel=vo, stats=st)
+    b.set(M.MAZE_POS, x)
+    b.set(M.MAZE_VEL, v)
+    assert M.maze_step(b.h, 1) == M.MAZE_OK
+    assert st.as_dict() == b.stats()
+    assert np.array_equal(po, b.get(M.MAZE_POS))
+    assert np.array_equal(vo, b.get(M.MAZE_VEL))
+    v[n - 1, 0] = np.nan     # in the last thread's range
+    assert M.maze_step_io(a.h, n, None, v, 1, None, None) == M.MAZE_ERR_INVALID
+    a.close()
+    b.close()
