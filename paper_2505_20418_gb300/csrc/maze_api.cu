@@ -347,10 +347,13 @@ MixedArgs mixed_args(maze_ctx* c, int zero_phi, double* q_out) {
 }
 
 maze_status enqueue_solve(maze_ctx* c, int zero_phi, double* q_out) {
-  CK(cudaMemsetAsync(c->recs, 0, c->recs_bytes, c->stream));
+  // (the one-cluster mixed solve synchronises and reduces in shared memory:
+  // no grid counters or reduction records to clear)
+  const bool cluster = c->mixed && c->mx_cluster > 0;
+  if (!cluster) CK(cudaMemsetAsync(c->recs, 0, c->recs_bytes, c->stream));
   if (!zero_phi && c->cfg.scheme != MAZE_SCHEME_MAZE) CK(cudaMemsetAsync(c->y, 0, c->ng * 8, c->stream));
   if (c->mixed) {
-    CK(cudaMemsetAsync(c->bar, 0, sizeof(unsigned), c->stream));
+    if (!cluster) CK(cudaMemsetAsync(c->bar, 0, sizeof(unsigned), c->stream));
     CK(launch_mixed_solve(mixed_args(c, zero_phi, q_out), c->mx_cluster, c->mx_blocks, c->stream));
   } else if (c->cfg.solver == MAZE_SOLVER_MG) {
     CK(cudaMemsetAsync(c->bar, 0, sizeof(unsigned), c->stream));
