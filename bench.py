@@ -377,23 +377,18 @@ def main():
     # state from pinned host memory, run the step, read back positions + stats
     e2e = None
     if not args.no_e2e:
-        hp = torch.empty((w.n_ions, 3), dtype=torch.float64).pin_memory()
-        hv = torch.empty((w.n_ions, 3), dtype=torch.float64).pin_memory()
-        hp.copy_(torch.from_numpy(sim.get(M.MAZE_POS)))
-        hv.copy_(torch.from_numpy(sim.get(M.MAZE_VEL)))
-        hpn, hvn = hp.numpy(), hv.numpy()
+        io = sim.exchange_buffers()   # pinned host positions and velocities
         n_e2e = min(args.steps, 100)
-        rec = M.MazeStats()
         sim.set_timing(False)    # a user's step: no phase events in the graph
         for _ in range(5):       # untimed warm-up (the GPU idled during the force check)
-            sim.step_io(1, pos=hpn, vel=hvn, out_pos=hpn, out_vel=hvn, stats=rec)
+            sim.exchange(io)
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(n_e2e):
             # maze_step_io: upload, one step, positions, velocities and the
             # record back, one synchronisation
-            sim.step_io(1, pos=hpn, vel=hvn, out_pos=hpn, out_vel=hvn, stats=rec)
+            sim.exchange(io)
         e2e_s = max_over_ranks(time.perf_counter() - t0, dist if world > 1 else None, dev)
         e2e = {"value": weak_scaling_value(world, n_e2e, e2e_s), "unit": "steps/s",
                "h2d_bytes_per_step": 2 * 24 * w.n_ions,

@@ -544,6 +544,8 @@ void free_ctx(maze_ctx* c) {
   for (int t = 0; t < 2; ++t)
     for (int g = 0; g < 3; ++g)
       if (c->graph[t][g]) cudaGraphExecDestroy(c->graph[t][g]);
+  for (int g = 0; g < 3; ++g)
+    if (c->io_graph[g]) cudaGraphExecDestroy(c->io_graph[g]);
   for (int k = 0; k < 5; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   for (void* p : c->allocs) {
@@ -995,6 +997,93 @@ maze_status ctx_bytes(const maze_config* cfg, size_t* bytes) {
   return MAZE_OK;
 }
 
+// The exchange graphs of maze_step_io (one per rotation): the step's status
+// cleared, positions and velocities uploaded from their pinned stages, one
+// step, positions, velocities and the record read back into pinned memory:
+// the operations maze_set, maze_step and maze_get issue, in their order, on
+// the same stream. On any capture failure the calls keep their separate form.
+maze_status build_io_graphs(maze_ctx* c) {
+  c->io_tried = true;
+  maze_status s = stage_buffer(c, 0);
+  if (s != MAZE_OK) return s;
+  s = stage_buffer(c, 2);
+  if (s != MAZE_OK) return s;
+  const size_t bytes = 6 * (size_t)c->n * 8;
+  static_assert(sizeof(maze_stats) % 8 == 0, "the record moves as 8-byte words");
+  void *st_in = nullptr, *st_out = nullptr, *rec_out = nullptr;
+  if (cudaHostGetDevicePointer(&st_in, c->stage[0], 0) != cudaSuccess ||
+      cudaHostGetDevicePointer(&st_out, c->stage[2], 0) != cudaSuccess ||
+      cudaHostGetDevicePointer(&rec_out, c->rec_host, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return MAZE_OK;   // (no device addresses: the separate form)
+  }
+  const int ik0 = c->ik;
+  for (int g = 0; g < 3; ++g) {
+    c->ik = g;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      c->ik = ik0;
+      return MAZE_OK;
+    }
+    // the pinned stages and record are read and written by the SMs
+    // directly (device addresses of the host allocations)
+    bool ok = cudaMemsetAsync(&c->rec->status, 0, sizeof(int32_t), c->stream) == cudaSuccess &&
+              launch_copy_words(st_in, c->pos, bytes, nullptr, nullptr, 0, c->stream) == cudaSuccess;
+    ok = ok && enqueue_step(c, 0) == MAZE_OK;
+    ok = ok && launch_copy_words(c->pos, st_out, bytes, c->rec, rec_out, sizeof(maze_stats), c->stream) == cudaSuccess;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    if (!ok || e != cudaSuccess || !graph ||
+        cudaGraphInstantiate(&c->io_graph[g], graph, 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (graph) cudaGraphDestroy(graph);
+      for (int q = 0; q < 3; ++q)
+        if (c->io_graph[q]) {
+          cudaGraphExecDestroy(c->io_graph[q]);
+          c->io_graph[q] = nullptr;
+        }
+      c->ik = ik0;
+      return MAZE_OK;
+    }
+    cudaGraphDestroy(graph);
+  }
+  c->ik = ik0;
+  c->io_ok = true;
+  return MAZE_OK;
+}
+
+// maze_step_io of one step with every input and output, through the
+// exchange graph (inputs checked finite by the caller).
+maze_status step_io_graph(maze_ctx* c, const double* pos_in, const double* vel_in, double* pos_out,
+                          double* vel_out, maze_stats* stats_out) {
+  if (c->rec_dirty) {   // (the step count before the step, as maze_step keeps it)
+    maze_status s = read_stats(c);
+    if (s != MAZE_OK) return s;
+  }
+  const int64_t before = c->rec_host->step;
+  const int ik0 = c->ik;
+  for (int k = 0; k < 2; ++k) CK(cudaEventSynchronize(c->stage_ev[k]));   // an earlier maze_set's upload was read
+  to_soa(pos_in, c->stage[0], c->n, true, c->L);
+  to_soa(vel_in, c->stage[1], c->n, false, c->L);
+  c->rec_dirty = true;
+  c->staged_fresh[0] = c->staged_fresh[1] = false;
+  c->want_ion[0] = c->want_ion[1] = false;
+  CK(cudaGraphLaunch(c->io_graph[c->ik], c->stream));
+  rotate(c, 1);
+  CK(cudaStreamSynchronize(c->stream));
+  c->rec_dirty = false;
+  c->staged_fresh[0] = c->staged_fresh[1] = true;
+  if (c->rec_host->status != MAZE_OK) {
+    // the step was skipped on the device: the rotation stays where it was
+    const int64_t done = c->rec_host->step - before;
+    c->ik = (int)((ik0 + 2 * (done % 3)) % 3);
+  }
+  to_aos(c->stage[2], pos_out, c->n);
+  to_aos(c->stage[3], vel_out, c->n);
+  if (stats_out) *stats_out = *c->rec_host;
+  return status_message(c);
+}
+
 }  // namespace maze
 
 extern "C" {
@@ -1240,6 +1329,14 @@ maze_status maze_step_io(maze_ctx* c, const double* pos_in, const double* vel_in
   if ((pos_in && !ion_finite(c, pos_in)) || (vel_in && !ion_finite(c, vel_in)))
     return fail(MAZE_ERR_INVALID, "non-finite input");
   maze_status s;
+  // the full exchange of one step: one graph launch and one synchronisation
+  if (!c->arena && nsteps == 1 && pos_in && vel_in && pos_out && vel_out && !c->timing) {
+    if (!c->io_tried) {
+      s = build_io_graphs(c);
+      if (s != MAZE_OK) return s;
+    }
+    if (c->io_ok) return step_io_graph(c, pos_in, vel_in, pos_out, vel_out, stats_out);
+  }
   if (pos_in || vel_in) {
     const double* const ins[2] = {pos_in, vel_in};
     if ((s = upload_ions(c, ins)) != MAZE_OK) return s;

@@ -112,6 +112,10 @@ struct maze_ctx {
   bool staged_fresh[2] = {false, false};
   cudaGraphExec_t graph[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
   bool graphs_tried[2] = {false, false}, graphs_ok[2] = {false, false};
+  // one host exchange of maze_step_io (status clear, upload of positions and
+  // velocities, one step, their read-back and the record's) per rotation
+  cudaGraphExec_t io_graph[3] = {nullptr, nullptr, nullptr};
+  bool io_tried = false, io_ok = false;
   int timing = 0;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   int max_iter_init = 20000;

@@ -38,6 +38,30 @@ cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Copies of up to two word arrays by the SMs (the host exchange of
+// maze_step_io: pinned host memory read or written directly, no copy
+// engine between the step's kernels and the host).
+__global__ void k_copy_words(const unsigned long long* s0, unsigned long long* d0, int n0,
+                             const unsigned long long* s1, unsigned long long* d1, int n1) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n0 + n1; i += gridDim.x * blockDim.x) {
+    if (i < n0)
+      d0[i] = s0[i];
+    else
+      d1[i - n0] = s1[i - n0];
+  }
+}
+
+cudaError_t launch_copy_words(const void* s0, void* d0, size_t bytes0, const void* s1, void* d1, size_t bytes1,
+                              cudaStream_t s) {
+  const int n0 = (int)(bytes0 / 8), n1 = (int)(bytes1 / 8);
+  const int blocks = std::min(64, (n0 + n1 + 255) / 256);
+  k_copy_words<<<std::max(1, blocks), 256, 0, s>>>(static_cast<const unsigned long long*>(s0),
+                                                   static_cast<unsigned long long*>(d0), n0,
+                                                   static_cast<const unsigned long long*>(s1),
+                                                   static_cast<unsigned long long*>(d1), n1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_q_to_double(const unsigned long long* qfix, double* q, int n, cudaStream_t s) {
   k_q_to_double<<<(n + 255) / 256, 256, 0, s>>>(qfix, q, n);
   return cudaGetLastError();

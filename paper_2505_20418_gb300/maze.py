@@ -293,6 +293,20 @@ def make_config(pos, vel, types, L, N, tf, *, r_cut, dt=1.0, tol=1e-10, max_iter
     return c, (pos, vel, types)
 
 
+class ExchangeBuffers:
+    """Pinned host buffers for a host-driven loop of maze_step_io exchanges:
+    positions and velocities ([n][3], read as the step's inputs and
+    overwritten with its results) and the step record, with their addresses
+    taken once (MazeSim.exchange)."""
+
+    def __init__(self, n: int):
+        import torch
+        self._keep = [torch.empty((n, 3), dtype=torch.float64).pin_memory() for _ in range(2)]
+        self.pos, self.vel = (t.numpy() for t in self._keep)
+        self.stats = MazeStats()
+        self._args = (self.pos.ctypes.data, self.vel.ctypes.data, ctypes.byref(self.stats))
+
+
 class MazeSim:
     """One MaZe simulation context on the current CUDA device."""
 
@@ -332,6 +346,21 @@ class MazeSim:
 
     def step_async(self, nsteps=1):
         maze_step_async(self.h, nsteps)
+
+    def exchange_buffers(self) -> ExchangeBuffers:
+        """Pinned exchange buffers holding the current positions and velocities."""
+        io = ExchangeBuffers(self.n)
+        maze_get(self.h, MAZE_POS, io.pos)
+        maze_get(self.h, MAZE_VEL, io.vel)
+        return io
+
+    def exchange(self, io: ExchangeBuffers, nsteps: int = 1):
+        """maze_step_io with io's positions and velocities in and out and its
+        record filled: one call, one synchronisation."""
+        p, v, st = io._args
+        status = load().maze_step_io(self.h, p, v, nsteps, p, v, st)
+        if status:
+            _check(status)
 
     def step_io(self, nsteps=1, pos=None, vel=None, out_pos=None, out_vel=None, stats=None):
         """Upload pos / vel (if given), run nsteps steps, fill out_pos / out_vel

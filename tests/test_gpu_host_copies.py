@@ -141,3 +141,58 @@ def test_step_io_large_box_host_threads():
     assert M.maze_step_io(a.h, n, None, v, 1, None, None) == M.MAZE_ERR_INVALID
     a.close()
     b.close()
+
+
+def test_step_io_exchange_graph_over_rotations_and_mixed_calls():
+    """Full one-step exchanges (the single-graph form) for seven steps in a
+    row, every rotation of the potentials twice, then interleaved with
+    plain steps, sets and gets: bit for bit the six-call sequence."""
+    w = synth.workload("nacl1000")
+    a, b = make(w), make(w)
+    n = w.n_ions
+    x, v = a.get(M.MAZE_POS), a.get(M.MAZE_VEL)
+    st = M.MazeStats()
+
+    def twin(x, v, nsteps=1):
+        b.set(M.MAZE_POS, x)
+        b.set(M.MAZE_VEL, v)
+        assert M.maze_step(b.h, nsteps) == M.MAZE_OK
+        return b.get(M.MAZE_POS), b.get(M.MAZE_VEL), b.stats()
+
+    for k in range(7):
+        po, vo = np.empty((n, 3)), np.empty((n, 3))
+        a.step_io(1, pos=x, vel=v, out_pos=po, out_vel=vo, stats=st)
+        bx, bv, bs = twin(x, v)
+        assert np.array_equal(po, bx) and np.array_equal(vo, bv) and st.as_dict() == bs, k
+        x, v = po, vo * 0.9999
+    # interleaved with the other calls
+    a.step(2)
+    b.step(2)
+    assert np.array_equal(a.get(M.MAZE_POS), b.get(M.MAZE_POS))
+    x, v = a.get(M.MAZE_POS), a.get(M.MAZE_VEL)
+    a.set(M.MAZE_VEL, v * 1.0001)
+    b.set(M.MAZE_VEL, v * 1.0001)
+    po, vo = np.empty((n, 3)), np.empty((n, 3))
+    a.step_io(1, pos=x, vel=v, out_pos=po, out_vel=vo, stats=st)
+    bx, bv, bs = twin(x, v)
+    assert np.array_equal(po, bx) and np.array_equal(vo, bv) and st.as_dict() == bs
+    assert np.array_equal(a.get(M.MAZE_FORCE), b.get(M.MAZE_FORCE))
+    assert np.array_equal(a.get(M.MAZE_VEL), vo)
+    a.close()
+    b.close()
+
+
+def test_exchange_buffers_equal_step_io():
+    """MazeSim.exchange on pinned buffers against step_io on plain arrays."""
+    w = synth.workload("nacl1000")
+    a, b = make(w), make(w)
+    io = a.exchange_buffers()
+    x, v = b.get(M.MAZE_POS), b.get(M.MAZE_VEL)
+    st = M.MazeStats()
+    for _ in range(4):
+        a.exchange(io)
+        b.step_io(1, pos=x, vel=v, out_pos=x, out_vel=v, stats=st)
+        assert np.array_equal(io.pos, x) and np.array_equal(io.vel, v)
+        assert io.stats.as_dict() == st.as_dict()
+    a.close()
+    b.close()
