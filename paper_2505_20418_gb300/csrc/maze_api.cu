@@ -546,6 +546,7 @@ void free_ctx(maze_ctx* c) {
       if (c->graph[t][g]) cudaGraphExecDestroy(c->graph[t][g]);
   for (int g = 0; g < 3; ++g)
     if (c->io_graph[g]) cudaGraphExecDestroy(c->io_graph[g]);
+  if (c->io_stage) cudaFreeHost(c->io_stage);
   for (int k = 0; k < 5; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   for (void* p : c->allocs) {
@@ -1004,19 +1005,21 @@ maze_status ctx_bytes(const maze_config* cfg, size_t* bytes) {
 // the same stream. On any capture failure the calls keep their separate form.
 maze_status build_io_graphs(maze_ctx* c) {
   c->io_tried = true;
-  maze_status s = stage_buffer(c, 0);
-  if (s != MAZE_OK) return s;
-  s = stage_buffer(c, 2);
-  if (s != MAZE_OK) return s;
-  const size_t bytes = 6 * (size_t)c->n * 8;
+  const size_t n6 = 6 * (size_t)c->n;
+  if (cudaMallocHost(&c->io_stage, 2 * n6 * sizeof(double)) != cudaSuccess) {
+    c->io_stage = nullptr;
+    cudaGetLastError();
+    return fail(MAZE_ERR_OOM, "cudaMallocHost failed");
+  }
   static_assert(sizeof(maze_stats) % 8 == 0, "the record moves as 8-byte words");
-  void *st_in = nullptr, *st_out = nullptr, *rec_out = nullptr;
-  if (cudaHostGetDevicePointer(&st_in, c->stage[0], 0) != cudaSuccess ||
-      cudaHostGetDevicePointer(&st_out, c->stage[2], 0) != cudaSuccess ||
+  void *st = nullptr, *rec_out = nullptr;
+  if (cudaHostGetDevicePointer(&st, c->io_stage, 0) != cudaSuccess ||
       cudaHostGetDevicePointer(&rec_out, c->rec_host, 0) != cudaSuccess) {
     cudaGetLastError();
     return MAZE_OK;   // (no device addresses: the separate form)
   }
+  const double* st_in = static_cast<const double*>(st);
+  double* st_out = static_cast<double*>(st) + n6;
   const int ik0 = c->ik;
   for (int g = 0; g < 3; ++g) {
     c->ik = g;
@@ -1029,9 +1032,9 @@ maze_status build_io_graphs(maze_ctx* c) {
     // the pinned stages and record are read and written by the SMs
     // directly (device addresses of the host allocations)
     bool ok = cudaMemsetAsync(&c->rec->status, 0, sizeof(int32_t), c->stream) == cudaSuccess &&
-              launch_copy_words(st_in, c->pos, bytes, nullptr, nullptr, 0, c->stream) == cudaSuccess;
+              launch_io_in(st_in, c->pos, c->n, c->stream) == cudaSuccess;
     ok = ok && enqueue_step(c, 0) == MAZE_OK;
-    ok = ok && launch_copy_words(c->pos, st_out, bytes, c->rec, rec_out, sizeof(maze_stats), c->stream) == cudaSuccess;
+    ok = ok && launch_io_out(c->pos, st_out, c->n, c->rec, rec_out, sizeof(maze_stats), c->stream) == cudaSuccess;
     const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
     if (!ok || e != cudaSuccess || !graph ||
         cudaGraphInstantiate(&c->io_graph[g], graph, 0) != cudaSuccess) {
@@ -1062,9 +1065,18 @@ maze_status step_io_graph(maze_ctx* c, const double* pos_in, const double* vel_i
   }
   const int64_t before = c->rec_host->step;
   const int ik0 = c->ik;
-  for (int k = 0; k < 2; ++k) CK(cudaEventSynchronize(c->stage_ev[k]));   // an earlier maze_set's upload was read
-  to_soa(pos_in, c->stage[0], c->n, true, c->L);
-  to_soa(vel_in, c->stage[1], c->n, false, c->L);
+  // inputs into the exchange stage in the caller's order (positions wrapped
+  // into [0, L) as maze_set does); the graph reorders them on the device
+  const size_t n3 = 3 * (size_t)c->n;
+  double* in = c->io_stage;
+  const double* out = c->io_stage + 2 * n3;
+  const double L = c->L;
+  host_ranges(c->n, [=](int lo, int hi) {
+    for (size_t e = 3 * (size_t)lo; e < 3 * (size_t)hi; ++e) {
+      in[e] = wrap_host(pos_in[e], L);
+      in[n3 + e] = vel_in[e];
+    }
+  });
   c->rec_dirty = true;
   c->staged_fresh[0] = c->staged_fresh[1] = false;
   c->want_ion[0] = c->want_ion[1] = false;
@@ -1072,14 +1084,15 @@ maze_status step_io_graph(maze_ctx* c, const double* pos_in, const double* vel_i
   rotate(c, 1);
   CK(cudaStreamSynchronize(c->stream));
   c->rec_dirty = false;
-  c->staged_fresh[0] = c->staged_fresh[1] = true;
   if (c->rec_host->status != MAZE_OK) {
     // the step was skipped on the device: the rotation stays where it was
     const int64_t done = c->rec_host->step - before;
     c->ik = (int)((ik0 + 2 * (done % 3)) % 3);
   }
-  to_aos(c->stage[2], pos_out, c->n);
-  to_aos(c->stage[3], vel_out, c->n);
+  host_ranges(c->n, [=](int lo, int hi) {
+    memcpy(pos_out + 3 * (size_t)lo, out + 3 * (size_t)lo, 3 * (size_t)(hi - lo) * sizeof(double));
+    memcpy(vel_out + 3 * (size_t)lo, out + n3 + 3 * (size_t)lo, 3 * (size_t)(hi - lo) * sizeof(double));
+  });
   if (stats_out) *stats_out = *c->rec_host;
   return status_message(c);
 }

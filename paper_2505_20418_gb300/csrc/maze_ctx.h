@@ -116,6 +116,7 @@ struct maze_ctx {
   // velocities, one step, their read-back and the record's) per rotation
   cudaGraphExec_t io_graph[3] = {nullptr, nullptr, nullptr};
   bool io_tried = false, io_ok = false;
+  double* io_stage = nullptr;   // pinned [2][2][n][3]: positions, velocities in; then out
   int timing = 0;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   int max_iter_init = 20000;

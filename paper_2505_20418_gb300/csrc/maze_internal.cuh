@@ -227,9 +227,12 @@ struct MixedArgs {
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t s);   // k_move, then k_spread if a.qfix
 cudaError_t launch_q_to_double(const unsigned long long* qfix, double* q, int n, cudaStream_t s);
-// k_copy_words: 8-byte words, byte counts multiples of 8, device-accessible pointers
-cudaError_t launch_copy_words(const void* s0, void* d0, size_t bytes0, const void* s1, void* d1, size_t bytes1,
-                              cudaStream_t s);
+// maze_step_io's exchange (device-accessible pinned pointers): [2][n][3]
+// host order <-> the device's [2][3][n]; k_io_out also copies the record
+// (rec_bytes a multiple of 8)
+cudaError_t launch_io_in(const double* aos, double* soa, int n, cudaStream_t s);
+cudaError_t launch_io_out(const double* soa, double* aos, int n, const void* rec, void* rec_out, size_t rec_bytes,
+                          cudaStream_t s);
 cudaError_t launch_cells(const CellArgs& a, cudaStream_t s);
 cudaError_t launch_forces(const ForceArgs& a, int blocks, cudaStream_t s);
 cudaError_t launch_pairs(const ForceArgs& a, cudaStream_t s);

@@ -38,27 +38,45 @@ cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Copies of up to two word arrays by the SMs (the host exchange of
-// maze_step_io: pinned host memory read or written directly, no copy
-// engine between the step's kernels and the host).
-__global__ void k_copy_words(const unsigned long long* s0, unsigned long long* d0, int n0,
-                             const unsigned long long* s1, unsigned long long* d1, int n1) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n0 + n1; i += gridDim.x * blockDim.x) {
-    if (i < n0)
-      d0[i] = s0[i];
-    else
-      d1[i - n0] = s1[i - n0];
+// The host exchange of maze_step_io, by the SMs on pinned host memory
+// (device addresses of the host allocations; no copy engine between the
+// step's kernels and the host). In: positions then velocities in [n][3]
+// order -> the device's [3][n] arrays (positions, velocities after them).
+// Out: the reverse, and the record's words.
+__global__ void k_io_in(const double* __restrict__ aos, double* __restrict__ soa, int n) {
+  const int n3 = 3 * n;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 2 * n3; e += gridDim.x * blockDim.x) {
+    const int a = e >= n3 ? 1 : 0, r = e - a * n3, i = r / 3, d = r - 3 * i;
+    soa[a * n3 + d * n + i] = aos[e];
   }
 }
 
-cudaError_t launch_copy_words(const void* s0, void* d0, size_t bytes0, const void* s1, void* d1, size_t bytes1,
-                              cudaStream_t s) {
-  const int n0 = (int)(bytes0 / 8), n1 = (int)(bytes1 / 8);
-  const int blocks = std::min(64, (n0 + n1 + 255) / 256);
-  k_copy_words<<<std::max(1, blocks), 256, 0, s>>>(static_cast<const unsigned long long*>(s0),
-                                                   static_cast<unsigned long long*>(d0), n0,
-                                                   static_cast<const unsigned long long*>(s1),
-                                                   static_cast<unsigned long long*>(d1), n1);
+__global__ void k_io_out(const double* __restrict__ soa, double* __restrict__ aos, int n,
+                         const unsigned long long* __restrict__ rec, unsigned long long* __restrict__ rec_out,
+                         int rec_words) {
+  const int n3 = 3 * n;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 2 * n3 + rec_words; e += gridDim.x * blockDim.x) {
+    if (e < 2 * n3) {
+      const int a = e >= n3 ? 1 : 0, r = e - a * n3, i = r / 3, d = r - 3 * i;
+      aos[e] = soa[a * n3 + d * n + i];
+    } else {
+      rec_out[e - 2 * n3] = rec[e - 2 * n3];
+    }
+  }
+}
+
+static int io_blocks(int items) { return std::max(1, std::min(1216, (items + 255) / 256)); }
+
+cudaError_t launch_io_in(const double* aos, double* soa, int n, cudaStream_t s) {
+  k_io_in<<<io_blocks(6 * n), 256, 0, s>>>(aos, soa, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_io_out(const double* soa, double* aos, int n, const void* rec, void* rec_out, size_t rec_bytes,
+                          cudaStream_t s) {
+  const int words = (int)(rec_bytes / 8);
+  k_io_out<<<io_blocks(6 * n + words), 256, 0, s>>>(soa, aos, n, static_cast<const unsigned long long*>(rec),
+                                                    static_cast<unsigned long long*>(rec_out), words);
   return cudaGetLastError();
 }
 
