@@ -1056,7 +1056,7 @@ maze_status build_io_graphs(maze_ctx* c) {
 }
 
 // maze_step_io of one step with every input and output, through the
-// exchange graph (inputs checked finite by the caller).
+// exchange graph.
 maze_status step_io_graph(maze_ctx* c, const double* pos_in, const double* vel_in, double* pos_out,
                           double* vel_out, maze_stats* stats_out) {
   if (c->rec_dirty) {   // (the step count before the step, as maze_step keeps it)
@@ -1071,12 +1071,18 @@ maze_status step_io_graph(maze_ctx* c, const double* pos_in, const double* vel_i
   double* in = c->io_stage;
   const double* out = c->io_stage + 2 * n3;
   const double L = c->L;
-  host_ranges(c->n, [=](int lo, int hi) {
+  std::atomic<bool> bad{false};
+  host_ranges(c->n, [&, in, L](int lo, int hi) {
+    bool b = false;
     for (size_t e = 3 * (size_t)lo; e < 3 * (size_t)hi; ++e) {
-      in[e] = wrap_host(pos_in[e], L);
-      in[n3 + e] = vel_in[e];
+      const double x = pos_in[e], v = vel_in[e];
+      b |= !isfinite(x) || !isfinite(v);
+      in[e] = wrap_host(x, L);
+      in[n3 + e] = v;
     }
+    if (b) bad.store(true, std::memory_order_relaxed);
   });
+  if (bad.load()) return fail(MAZE_ERR_INVALID, "non-finite input");   // (nothing uploaded or run)
   c->rec_dirty = true;
   c->staged_fresh[0] = c->staged_fresh[1] = false;
   c->want_ion[0] = c->want_ion[1] = false;
@@ -1338,11 +1344,9 @@ maze_status maze_step_io(maze_ctx* c, const double* pos_in, const double* vel_in
                          double* vel_out, maze_stats* stats_out) {
   if (!c) return fail(MAZE_ERR_INVALID, "ctx is NULL");
   if (nsteps < 0) return fail(MAZE_ERR_INVALID, "nsteps must be >= 0");
-  // both inputs are checked before anything is uploaded or run
-  if ((pos_in && !ion_finite(c, pos_in)) || (vel_in && !ion_finite(c, vel_in)))
-    return fail(MAZE_ERR_INVALID, "non-finite input");
   maze_status s;
   // the full exchange of one step: one graph launch and one synchronisation
+  // (its staging pass checks the inputs before anything runs)
   if (!c->arena && nsteps == 1 && pos_in && vel_in && pos_out && vel_out && !c->timing) {
     if (!c->io_tried) {
       s = build_io_graphs(c);
@@ -1350,6 +1354,9 @@ maze_status maze_step_io(maze_ctx* c, const double* pos_in, const double* vel_in
     }
     if (c->io_ok) return step_io_graph(c, pos_in, vel_in, pos_out, vel_out, stats_out);
   }
+  // both inputs are checked before anything is uploaded or run
+  if ((pos_in && !ion_finite(c, pos_in)) || (vel_in && !ion_finite(c, vel_in)))
+    return fail(MAZE_ERR_INVALID, "non-finite input");
   if (pos_in || vel_in) {
     const double* const ins[2] = {pos_in, vel_in};
     if ((s = upload_ions(c, ins)) != MAZE_OK) return s;

@@ -196,3 +196,23 @@ def test_exchange_buffers_equal_step_io():
         assert io.stats.as_dict() == st.as_dict()
     a.close()
     b.close()
+
+
+def test_full_exchange_rejects_non_finite_input_before_running():
+    """The one-graph exchange checks its inputs in its staging pass: a NaN
+    returns MAZE_ERR_INVALID with nothing uploaded or run."""
+    w = synth.workload("nacl1000")
+    a = make(w)
+    io = a.exchange_buffers()
+    a.exchange(io)                          # the exchange graph is built and used
+    before = a.stats()["step"]
+    x0, v0 = io.pos.copy(), io.vel.copy()
+    io.vel[w.n_ions - 1, 1] = np.nan
+    with pytest.raises(M.MazeError):
+        a.exchange(io)
+    assert a.stats()["step"] == before
+    assert np.array_equal(a.get(M.MAZE_POS), x0) and np.array_equal(a.get(M.MAZE_VEL), v0)
+    io.vel[w.n_ions - 1, 1] = v0[w.n_ions - 1, 1]
+    a.exchange(io)                          # and the context carries on
+    assert a.stats()["step"] == before + 1
+    a.close()
