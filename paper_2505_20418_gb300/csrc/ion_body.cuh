@@ -114,11 +114,23 @@ __device__ __forceinline__ double wrap_pos(double x, double L, double inv_L) {
 __device__ __forceinline__ void move_ion(const IonArgs& a, int i) {
   const int N = a.N, P = a.P;
   {
-    double x = a.pos[i], y = a.pos[a.n + i], z = a.pos[2 * a.n + i];
+    // (maze_step_io's exchange: this step's positions and velocities straight
+    // from the caller's pinned [n][3] copy)
+    const double* pin = a.io_in ? a.io_in + 3 * (size_t)i : nullptr;
+    const double* vin = a.io_in ? a.io_in + 3 * ((size_t)a.n + i) : nullptr;
+    double x = pin ? pin[0] : a.pos[i], y = pin ? pin[1] : a.pos[a.n + i], z = pin ? pin[2] : a.pos[2 * a.n + i];
     const int t = a.type[i];
+    if (pin && !a.do_move) {
+      a.pos[i] = x;
+      a.pos[a.n + i] = y;
+      a.pos[2 * a.n + i] = z;
+      a.vel[i] = vin[0];
+      a.vel[a.n + i] = vin[1];
+      a.vel[2 * a.n + i] = vin[2];
+    }
     if (a.do_move) {
       const double kick = t ? a.kick1 : a.kick0;
-      double vx = a.vel[i], vy = a.vel[a.n + i], vz = a.vel[2 * a.n + i];
+      double vx = vin ? vin[0] : a.vel[i], vy = vin ? vin[1] : a.vel[a.n + i], vz = vin ? vin[2] : a.vel[2 * a.n + i];
       if (a.ou.on) o_step(a.ou, i, t, (unsigned)a.rec->step, 0u, vx, vy, vz);
       vx += kick * a.force[i];
       vy += kick * a.force[a.n + i];

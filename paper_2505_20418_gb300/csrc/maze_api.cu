@@ -169,6 +169,7 @@ IonArgs ion_args(maze_ctx* c, int do_move, int do_spread) {
   a.wbuf = c->wbuf;
   a.wbuf32 = c->mixed ? c->wbuf32 : nullptr;
   a.wbase = c->wbase;
+  a.io_in = do_move ? c->io_in_dev : nullptr;
   a.rel_hi = c->mixed ? c->rel_hi : nullptr;
   a.rel_lo = c->mixed ? c->rel_lo : nullptr;
   a.cell_len = c->nc >= 3 ? c->L / c->nc : c->L;
@@ -1020,6 +1021,12 @@ maze_status build_io_graphs(maze_ctx* c) {
   }
   const double* st_in = static_cast<const double*>(st);
   double* st_out = static_cast<double*>(st) + n6;
+  // read by the captured step's S1, and only there: cleared on every way out
+  c->io_in_dev = st_in;
+  struct Clear {
+    maze_ctx* c;
+    ~Clear() { c->io_in_dev = nullptr; }
+  } clear{c};
   const int ik0 = c->ik;
   for (int g = 0; g < 3; ++g) {
     c->ik = g;
@@ -1031,8 +1038,7 @@ maze_status build_io_graphs(maze_ctx* c) {
     }
     // the pinned stages and record are read and written by the SMs
     // directly (device addresses of the host allocations)
-    bool ok = cudaMemsetAsync(&c->rec->status, 0, sizeof(int32_t), c->stream) == cudaSuccess &&
-              launch_io_in(st_in, c->pos, c->n, c->stream) == cudaSuccess;
+    bool ok = cudaMemsetAsync(&c->rec->status, 0, sizeof(int32_t), c->stream) == cudaSuccess;
     ok = ok && enqueue_step(c, 0) == MAZE_OK;
     ok = ok && launch_io_out(c->pos, st_out, c->n, c->rec, rec_out, sizeof(maze_stats), c->stream) == cudaSuccess;
     const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);

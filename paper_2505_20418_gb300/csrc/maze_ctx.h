@@ -117,6 +117,7 @@ struct maze_ctx {
   cudaGraphExec_t io_graph[3] = {nullptr, nullptr, nullptr};
   bool io_tried = false, io_ok = false;
   double* io_stage = nullptr;   // pinned [2][2][n][3]: positions, velocities in; then out
+  const double* io_in_dev = nullptr;   // device address of its input half, while the graphs are captured
   int timing = 0;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   int max_iter_init = 20000;

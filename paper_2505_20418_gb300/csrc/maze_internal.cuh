@@ -72,6 +72,8 @@ struct IonArgs {
   double* wdbuf;         // [n][3][4] weight derivatives dW/dt (Eq. F_Benoit, FP64) or nullptr
   float* wdbuf32;        // the same in FP32 (mixed precision) or nullptr
   LangevinArgs ou;       // OVRVO O steps (off when ou.on == 0)
+  const double* io_in;   // [2][n][3] positions, velocities in the caller's order (pinned, device
+                         // address: maze_step_io's exchange), read instead of pos / vel, or nullptr
 };
 
 struct CellArgs {
@@ -227,10 +229,9 @@ struct MixedArgs {
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t s);   // k_move, then k_spread if a.qfix
 cudaError_t launch_q_to_double(const unsigned long long* qfix, double* q, int n, cudaStream_t s);
-// maze_step_io's exchange (device-accessible pinned pointers): [2][n][3]
-// host order <-> the device's [2][3][n]; k_io_out also copies the record
-// (rec_bytes a multiple of 8)
-cudaError_t launch_io_in(const double* aos, double* soa, int n, cudaStream_t s);
+// maze_step_io's exchange (device-accessible pinned pointers): the device's
+// [2][3][n] positions and velocities -> [2][n][3] host order, and the
+// record (rec_bytes a multiple of 8)
 cudaError_t launch_io_out(const double* soa, double* aos, int n, const void* rec, void* rec_out, size_t rec_bytes,
                           cudaStream_t s);
 cudaError_t launch_cells(const CellArgs& a, cudaStream_t s);

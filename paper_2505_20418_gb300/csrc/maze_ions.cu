@@ -38,18 +38,11 @@ cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// The host exchange of maze_step_io, by the SMs on pinned host memory
-// (device addresses of the host allocations; no copy engine between the
-// step's kernels and the host). In: positions then velocities in [n][3]
-// order -> the device's [3][n] arrays (positions, velocities after them).
-// Out: the reverse, and the record's words.
-__global__ void k_io_in(const double* __restrict__ aos, double* __restrict__ soa, int n) {
-  const int n3 = 3 * n;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 2 * n3; e += gridDim.x * blockDim.x) {
-    const int a = e >= n3 ? 1 : 0, r = e - a * n3, i = r / 3, d = r - 3 * i;
-    soa[a * n3 + d * n + i] = aos[e];
-  }
-}
+// The read-back of maze_step_io's exchange, by the SMs on pinned host
+// memory (device addresses of the host allocations; no copy engine between
+// the step's kernels and the host): the device's [3][n] positions and
+// velocities (velocities after positions) -> [n][3] order, and the record's
+// words. (The inputs are read by the step's S1 itself: IonArgs::io_in.)
 
 __global__ void k_io_out(const double* __restrict__ soa, double* __restrict__ aos, int n,
                          const unsigned long long* __restrict__ rec, unsigned long long* __restrict__ rec_out,
@@ -66,11 +59,6 @@ __global__ void k_io_out(const double* __restrict__ soa, double* __restrict__ ao
 }
 
 static int io_blocks(int items) { return std::max(1, std::min(1216, (items + 255) / 256)); }
-
-cudaError_t launch_io_in(const double* aos, double* soa, int n, cudaStream_t s) {
-  k_io_in<<<io_blocks(6 * n), 256, 0, s>>>(aos, soa, n);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_io_out(const double* soa, double* aos, int n, const void* rec, void* rec_out, size_t rec_bytes,
                           cudaStream_t s) {
