@@ -216,3 +216,28 @@ def test_full_exchange_rejects_non_finite_input_before_running():
     a.exchange(io)                          # and the context carries on
     assert a.stats()["step"] == before + 1
     a.close()
+
+
+@pytest.mark.parametrize("wl,precision", [("nacl64", M.MAZE_MIXED), ("nacl1000", M.MAZE_FP64),
+                                          ("nacl64000", M.MAZE_MIXED)])
+def test_exchange_other_step_forms(wl, precision):
+    """The exchange graph over the other step forms: a box without cells
+    (S1-S6 in one cluster launch), the FP64 path (separate launches, the
+    cooperative solve) and a box solved on the whole grid; bit for bit the
+    separate calls."""
+    w = synth.workload(wl)
+    pos, vel, types = synth.make_state(w)
+    kw = dict(r_cut=w.rc, dt=w.dt, tol=w.tol, order=w.order, solver=M.MAZE_SOLVER_MG, precision=precision)
+    a = M.MazeSim(pos, vel, types, w.L, w.N, synth.tosi_fumi_nacl(), **kw)
+    b = M.MazeSim(pos, vel, types, w.L, w.N, synth.tosi_fumi_nacl(), **kw)
+    io = a.exchange_buffers()
+    for _ in range(4):
+        x, v = io.pos.copy(), io.vel.copy()
+        a.exchange(io)
+        b.set(M.MAZE_POS, x)
+        b.set(M.MAZE_VEL, v)
+        assert M.maze_step(b.h, 1) == M.MAZE_OK
+        assert np.array_equal(io.pos, b.get(M.MAZE_POS)) and np.array_equal(io.vel, b.get(M.MAZE_VEL))
+        assert io.stats.as_dict() == b.stats()
+    a.close()
+    b.close()
