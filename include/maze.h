@@ -74,7 +74,7 @@ enum { MAZE_FORCE_CD = 0, MAZE_FORCE_GRADW = 1 };
 
 /* Physical constants used by the library (CODATA 2018). */
 #define MAZE_KE_EV_ANGSTROM 14.399645478425668  /* e^2/(4 pi eps0) in eV*Angstrom */
-#define MAZE_ACC_UNIT 9.648533215665327e-3      /* e/u * 1e-20: 1 eV/(amu*Angstrom) in Angstrom/fs^2 */
+#define MAZE_ACC_UNIT 9.648533215665327e-3      /* e/u * 1e-10: 1 eV/(amu*Angstrom) in Angstrom/fs^2 */
 #define MAZE_KB_EV_PER_K 8.617333262145179e-5   /* Boltzmann constant k_B / e, eV/K */
 
 /*

@@ -406,6 +406,74 @@ def tf_forces(pos, types, L, tf, rc):
     return F, V
 
 
+def tf_forces_cells(pos, types, L, tf, rc, chunk=2048):
+    """The same sum as :func:`tf_forces`, with the candidate pairs taken from
+    a cell list instead of all pairs (needed for boxes of ~10^5 ions and more).
+
+    The box is cut into n_c = floor(L / r_c) >= 3 cells per edge, so a cell
+    is at least r_c wide and every pair closer than r_c (minimum image, r_c <=
+    L/2) lies in the same or in adjacent cells. Each unordered pair of ions is
+    visited once: ion pairs a < b within a cell, and all ion pairs between a
+    cell and the 13 neighbours of its "upper" half shell (offsets (dz, dy, dx)
+    after (0, 0, 0) in lexicographic order). With n_c >= 3 the 27 neighbour
+    cells of a cell are distinct, so no cell pair is visited twice. Returns
+    (F (N_p, 3), V_TF)."""
+    n = pos.shape[0]
+    nc = int(math.floor(L / rc))
+    if nc < 3:
+        return tf_forces(pos, types, L, tf, rc)
+    side = L / nc
+    c3 = np.minimum((np.floor(pos / side)).astype(np.int64), nc - 1)     # (n, 3) cell coordinates
+    cid = (c3[:, 2] * nc + c3[:, 1]) * nc + c3[:, 0]
+    order = np.argsort(cid, kind="stable")
+    counts = np.bincount(cid, minlength=nc ** 3)
+    starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
+    mo = int(counts.max())
+    table = np.full((nc ** 3, mo), -1, dtype=np.int64)    # ions of each cell, padded with -1
+    slot = np.arange(n) - starts[cid[order]]
+    table[cid[order], slot] = order
+    cz, cy, cx = np.meshgrid(np.arange(nc), np.arange(nc), np.arange(nc), indexing="ij")
+    cz, cy, cx = cz.ravel(), cy.ravel(), cx.ravel()        # cell id = (cz nc + cy) nc + cx
+    offsets = [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+               if (dz, dy, dx) > (0, 0, 0)]
+    F = np.zeros((n, 3))
+    V = 0.0
+    for off in [(0, 0, 0)] + offsets:
+        dz, dy, dx = off
+        nb = ((((cz + dz) % nc) * nc + (cy + dy) % nc) * nc + (cx + dx) % nc)
+        for c0 in range(0, nc ** 3, chunk):
+            A = table[c0:c0 + chunk]                    # (c, mo) ions of the cells
+            B = table[nb[c0:c0 + chunk]]                # (c, mo) ions of their neighbour cells
+            a = np.broadcast_to(A[:, :, None], (A.shape[0], mo, mo)).ravel()
+            b = np.broadcast_to(B[:, None, :], (A.shape[0], mo, mo)).ravel()
+            keep = (a >= 0) & (b >= 0)
+            if off == (0, 0, 0):
+                keep &= a < b
+            a, b = a[keep], b[keep]
+            d = pos[b] - pos[a]
+            d -= L * np.round(d / L)
+            r = np.sqrt((d * d).sum(axis=1))
+            m = r < rc
+            a, b, d, r = a[m], b[m], d[m], r[m]
+            k = types[a] + types[b]
+            Vp, f = _tf_pair(r, k, tf)
+            Vc, _ = _tf_pair(np.full(r.shape, rc), k, tf)
+            V += float((Vp - Vc).sum())
+            fvec = (f / r)[:, None] * d                 # force on b
+            for ax in range(3):
+                F[:, ax] += np.bincount(b, weights=fvec[:, ax], minlength=n)
+                F[:, ax] -= np.bincount(a, weights=fvec[:, ax], minlength=n)
+    return F, V
+
+
+def pair_forces(pos, types, L, tf, rc):
+    """Tosi-Fumi forces and energy: all pairs for small boxes, the cell-list
+    sum above 4096 ions (identical up to summation order)."""
+    if pos.shape[0] > 4096 and math.floor(L / rc) >= 3:
+        return tf_forces_cells(pos, types, L, tf, rc)
+    return tf_forces(pos, types, L, tf, rc)
+
+
 def tf_forces_on(idx, pos, types, L, tf, rc):
     """Tosi-Fumi force on the selected ions only, by brute force over all others."""
     out = np.zeros((len(idx), 3))
@@ -497,7 +565,7 @@ def init(pos, vel, types, p: Params, tf) -> State:
     y0, info = solve(q, np.zeros_like(q), p.tol, p.solver, p.max_iter)   # sigma_p = q at phi_p = 0
     phi = -(4.0 * np.pi / p.h) * (y0 - y0.mean())
     F_el = electrostatic_forces(pos, Q, phi, p)
-    F_tf, V_tf = tf_forces(pos, types, p.L, tf, p.rc)
+    F_tf, V_tf = pair_forces(pos, types, p.L, tf, p.rc)
     st = State(pos=pos, vel=np.array(vel, dtype=np.float64), types=np.asarray(types),
                phi=phi, phi_prev=phi.copy(), y=np.zeros_like(phi),
                F_el=F_el, F_tf=F_tf, V_tf=V_tf, iters=info.iters, resid=info.resid)
@@ -529,7 +597,7 @@ def step(st: State, p: Params, tf) -> State:
     else:
         phi_new, y, info = direct_solve(st, q, p)
     F_el = electrostatic_forces(pos, Q, phi_new, p)
-    F_tf, V_tf = tf_forces(pos, st.types, p.L, tf, p.rc)
+    F_tf, V_tf = pair_forces(pos, st.types, p.L, tf, p.rc)
     vel = v_half + (0.5 * p.dt * ACC) * (F_el + F_tf) / m
     if p.gamma > 0:
         vel = o_step(vel, st.types, p, st.step, 1)

@@ -494,3 +494,89 @@ def test_ovrvo_tends_to_verlet_and_thermalises():
     st = O.run(pos, cold, types, ph, tf, 30)
     T = 2 * O.kinetic(st, ph) / (3 * len(types) * O.K_B)
     assert 1500 < T < 6000
+
+
+# ---------------------------------------------------------------------------
+# Unit constants (Sec. II Gaussian units; Sec. III Angstrom / fs / amu) against
+# published CODATA 2018 values reached by other routes than the oracle's.
+
+def codata():
+    out = {}
+    with open(os.path.join(GOLDEN, "codata2018.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                out[k] = float(v)
+    return out
+
+
+def header_constants():
+    """The unit constants the CUDA path compiles in (include/maze.h)."""
+    out = {}
+    with open(os.path.join(os.path.dirname(GOLDEN), "..", "include", "maze.h")) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 3 and parts[0] == "#define" and parts[1] in (
+                    "MAZE_KE_EV_ANGSTROM", "MAZE_ACC_UNIT", "MAZE_KB_EV_PER_K"):
+                out[parts[1]] = float(parts[2])
+    return out
+
+
+def test_unit_constants_match_codata_2018():
+    c = codata()
+    ke = c["hartree_energy_eV"] * c["bohr_radius_angstrom"]       # e^2/(4 pi eps0) = E_h a_0
+    acc = c["faraday_C_per_mol"] / c["molar_mass_constant_kg_per_mol"] * 1e-10   # e/u, (m/s^2 -> A/fs^2)
+    kb = c["boltzmann_eV_per_K"]
+    assert abs(O.K_E / ke - 1.0) < 1e-9
+    assert abs(O.ACC / acc - 1.0) < 1e-9
+    assert abs(O.K_B / kb - 1.0) < 1e-9
+    h = header_constants()
+    assert set(h) == {"MAZE_KE_EV_ANGSTROM", "MAZE_ACC_UNIT", "MAZE_KB_EV_PER_K"}
+    assert abs(h["MAZE_KE_EV_ANGSTROM"] / ke - 1.0) < 1e-9
+    assert abs(h["MAZE_ACC_UNIT"] / acc - 1.0) < 1e-9
+    assert abs(h["MAZE_KB_EV_PER_K"] / kb - 1.0) < 1e-9
+    # a slip by a power of ten (or a missing 4 pi) fails these by orders of magnitude
+    assert 14.39 < O.K_E < 14.40 and 9.64e-3 < O.ACC < 9.65e-3
+
+
+def test_tf_energy_is_continuous_at_the_cutoff():
+    """Reading G9: the pair energy is shifted by V(r_c), so a pair entering or
+    leaving the cutoff sphere changes V_TF by (almost) nothing, while the
+    unshifted energy would jump by V(r_c)."""
+    tf = synth.tosi_fumi_nacl()
+    L, rc = 40.0, 9.0
+    types = np.array([0, 1], dtype=np.int32)
+    for eps in (1e-6, 1e-9):
+        inside = np.array([[5.0, 5.0, 5.0], [5.0 + rc - eps, 5.0, 5.0]])
+        outside = np.array([[5.0, 5.0, 5.0], [5.0 + rc + eps, 5.0, 5.0]])
+        _, Vin = O.tf_forces(inside, types, L, tf, rc)
+        _, Vout = O.tf_forces(outside, types, L, tf, rc)
+        F, _ = O.tf_forces(inside, types, L, tf, rc)
+        assert Vout == 0.0
+        # the shifted energy just inside the cutoff is |dV/dr| * eps to first order
+        assert abs(Vin) <= 2.0 * np.abs(F[0, 0]) * eps + 1e-15
+    # and the shift is the unshifted pair energy at r_c
+    V_rc = tf.A[1] * math.exp(tf.B * (tf.s[1] - rc)) - tf.C[1] / rc ** 6 - tf.D[1] / rc ** 8
+    assert abs(V_rc) > 1e-6            # the jump the shift removes (~1.3e-5 eV for Na-Cl at 9 A)
+    near = np.array([[5.0, 5.0, 5.0], [5.0 + 3.0, 5.0, 5.0]])
+    _, Vn = O.tf_forces(near, types, L, tf, rc)
+    Vn_raw = tf.A[1] * math.exp(tf.B * (tf.s[1] - 3.0)) - tf.C[1] / 3.0 ** 6 - tf.D[1] / 3.0 ** 8
+    assert abs(Vn - (Vn_raw - V_rc)) < 1e-12
+
+
+@pytest.mark.parametrize("n_ions,rc", [(64, 4.0), (216, 6.0), (216, 9.0), (1000, 9.0), (1000, 5.0)])
+def test_cell_list_pairs_equal_all_pairs(n_ions, rc):
+    """The cell-list pair sum (large boxes) against the all-pairs loop: same
+    pairs, same forces and energy up to summation order."""
+    tf = synth.tosi_fumi_nacl()
+    if n_ions == 64:
+        w = synth.workload("nacl64")
+    else:
+        w = synth.replica(n_ions, 11 + n_ions)
+    pos, _, types = synth.make_state(w)
+    F1, V1 = O.tf_forces(pos, types, w.L, tf, rc)
+    F2, V2 = O.tf_forces_cells(pos, types, w.L, tf, rc)
+    scale = np.sqrt((F1 ** 2).sum(1).mean())
+    assert np.abs(F2 - F1).max() <= 1e-12 * scale
+    assert abs(V2 - V1) <= 1e-12 * abs(V1)
+    assert np.abs(F2.sum(0)).max() < 1e-9 * scale * n_ions
