@@ -1,15 +1,16 @@
 """Benchmark of the GB300 Poisson MaZe step (one JSON line on rank 0).
 
 A step is one full MaZe MD step (S1-S9) of one synthetic molten-NaCl box.
-Default workload: 1000 ions (500 Na+, 500 Cl-), L = 31.5 Angstrom, 32^3 grid,
-1200 K, dt = 1 fs, constraint tolerance 1e-10, cubic B-spline assignment,
-warm-started multigrid constraint solve in mixed precision (FP32 V-cycle,
-double-float outer iteration, exact integer reductions). Inputs are resident
-in HBM when the timed region starts; L2 is flushed (256 MiB write) between
-timed steps, outside the per-step CUDA events.
+Default workload: 512000 ions (256000 Na+, 256000 Cl-), L = 252 Angstrom,
+256^3 grid, 1200 K, dt = 1 fs, constraint tolerance 1e-10, cubic B-spline
+assignment, warm-started multigrid constraint solve in FP64; the same box in
+mixed precision (FP32 V-cycle, double-float outer iteration, exact integer
+reductions) is timed after it and reported under "mixed". Inputs are
+resident in HBM when the timed region starts; L2 is flushed (256 MiB write)
+between timed steps, outside the per-step CUDA events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload nacl64|nacl1000|nacl512000|batch128|serve]
+                  [--workload nacl64|nacl1000|nacl8000|nacl64000|nacl512000|batch128|serve|study]
                   [--solver cg|mg] [--precision fp64|mixed]
 
 --workload batch128 advances 128 replica boxes (216-4096 ions, 16^3-48^3
@@ -109,8 +110,11 @@ class ClockSampler:
 
 
 def mg_levels(N):
+    """Grid sizes of the multigrid hierarchy as the kernels build it: halve
+    while the edge is even and above 8 (an 8^3 grid once), so the coarsest
+    level has at most 8^3 points."""
     sizes = [N]
-    while sizes[-1] % 2 == 0 and sizes[-1] >= 8:
+    while sizes[-1] % 2 == 0 and (sizes[-1] > 8 or (sizes[-1] == 8 and len(sizes) == 1)):
         sizes.append(sizes[-1] // 2)
     return sizes
 
@@ -145,51 +149,176 @@ def solve_bytes_per_launch(N, iters, solver="cg", nu=(2, 2), precision="fp64"):
     return base + per_v * iters
 
 
-def run_cpu_baseline(w, solver="mg", budget_s=15.0):
-    """The FP64 oracle as it stands, on a bounded sample of the same workload."""
+def survey_bytes_per_launch(N, iters, solver="mg", precision="fp64"):
+    """The same launch on the coarser per-point unit of the hot-path scope
+    table: 167 B/pt per FP64 V-cycle over all levels, 64 B/pt per FP64 CG
+    iteration, 72 B/pt of S4/S6/charge clearing per solve; mixed precision
+    halves every figure."""
+    ng = N ** 3
+    per = 167.0 if solver == "mg" else 64.0
+    b = ng * (72.0 + per * iters)
+    return b / 2 if precision == "mixed" else b
+
+
+def fp64_mg_ops_per_launch(N, iters, nu=(2, 2)):
+    """Algorithmic FP64 operations of one FP64 multigrid solve launch, one per
+    add, multiply or fused multiply-add (the FP64 pipe issues each of them at
+    the same rate), for the operations the method states and nothing else:
+
+      S4, per point: phi_p = 2 phi^k - phi^{k-1} (1), the two six-neighbour
+        sums of phi^k and phi^{k-1} (10), M phi_p = 2 s_k - s_{k-1} - 6 phi_p
+        (2), sigma_p = (h/4pi) M phi_p + q (1): 14;
+      first residual of the warm start, every point: six-neighbour sum (5),
+        -6 y (1), subtraction (1): 7;
+      per V-cycle, each level of n_l points above the coarsest: a red-black
+        Gauss-Seidel update (six-neighbour sum, then (s - b)/6 as one FMA on
+        a pre-scaled b: 6) per point and sweep, less 5 of the 6 at the red
+        half of the first sweep from a zero guess on coarse levels; the
+        residual at red points (7 per red point; black residuals are zero
+        after the black half-sweep); full weighting from the 13 red points
+        of the 27 (13 per coarse point); trilinear prolongation to black
+        points (2 for the 3/4 of them with one odd coordinate, 8 for the
+        rest; the red ones are overwritten by the next half-sweep); the
+        coarsest level: a dense product with the pseudo-inverse (n_c^2);
+      per V-cycle, the convergence test: residual at red points (7 each);
+      the mean of y (1 per point) and S6 phi = phi_p - (4pi/h)(y - mean) (2).
+    """
+    ng = N ** 3
+    lv = mg_levels(N)
+    sweeps = nu[0] + nu[1]
+    per_v = 0.0
+    for l, n in enumerate(lv[:-1]):
+        p = n ** 3
+        sm = sweeps * 6.0 - (2.5 if l > 0 else 0.0)
+        per_v += p * (sm + 3.5 + 1.75) + (p / 8.0) * 13.0
+    per_v += float(lv[-1] ** 3) ** 2 + ng * 3.5
+    return ng * (14.0 + 7.0 + 1.0 + 2.0) + iters * per_v
+
+
+def fp64_peak_tops(sms):
+    """FP64 pipe peak of a GB300: 2 FP64 operations per clock per SM (the
+    rate ncu lists for the FP64 pipe: 64 lanes of 1/32 rate per SM) times
+    the SMs times the maximum SM clock, in 10^12 operations per second."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        mhz = 2070.0
+    return 2.0 * sms * mhz * 1e6 / 1e12
+
+
+def oracle_sample(w):
+    """The bounded sample the oracle is timed on: the box itself when one of
+    its steps takes a few seconds; for the 256^3 and 128^3 boxes, the
+    8000-ion 64^3 box of the same molten NaCl (same density, grid spacing,
+    temperature, tolerance and seed recipe), whose per-step work (ions, grid
+    points, pairs) is 1/64 (1/8) of theirs. Returns (workload, work ratio)."""
+    if w.n_ions > 8000:
+        s = synth.workload("nacl8000")
+        return s, float(w.n_ions) / s.n_ions
+    return w, 1.0
+
+
+def _oracle_steps(name_or_w, solver, budget_s, max_steps, warmup=0):
+    """Oracle MD steps of one box for up to ``budget_s`` seconds (at least
+    one): (steps, seconds, per-step seconds)."""
     import oracle as O
+    w = synth.workload(name_or_w) if isinstance(name_or_w, str) else name_or_w
     pos, vel, types = synth.make_state(w)
     tf = synth.tosi_fumi_nacl()
     p = O.Params(L=w.L, N=w.N, dt=w.dt, tol=w.tol, rc=w.rc, P=w.order, solver=solver)
     st = O.init(pos, vel, types, p, tf)
-    n = 0
-    t0 = time.perf_counter()
-    while time.perf_counter() - t0 < budget_s:
+    for _ in range(warmup):
         st = O.step(st, p, tf)
-        n += 1
-    dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} MD steps of the same {w.n_ions}-ion {w.N}^3 box from its initial state, "
-                      f"numpy FP64, single thread ({dt:.1f} s)"}
+    times = []
+    t0 = time.perf_counter()
+    while not times or (time.perf_counter() - t0 < budget_s and len(times) < max_steps):
+        t1 = time.perf_counter()
+        st = O.step(st, p, tf)
+        times.append(time.perf_counter() - t1)
+    return len(times), sum(times), times
+
+
+def _oracle_worker(args):
+    name, solver, budget_s = args
+    n, dt, _ = _oracle_steps(name, solver, budget_s, 10 ** 6)
+    return n, dt
+
+
+def run_cpu_baseline(w, solver="mg", budget_s=15.0):
+    """The FP64 oracle as it stands, on a bounded sample of the same workload,
+    on one host thread."""
+    ws, ratio = oracle_sample(w)
+    n, dt, _ = _oracle_steps(ws, solver, budget_s, 10 ** 6)
+    what = (f"{n} MD steps of the same {w.n_ions}-ion {w.N}^3 box from its initial state" if ratio == 1.0 else
+            f"{n} MD steps of the {ws.n_ions}-ion {ws.N}^3 box of the same molten NaCl (1/{ratio:g} of the "
+            f"{w.n_ions}-ion {w.N}^3 box's ions and grid points), value scaled by 1/{ratio:g}")
+    return {"value": n / dt / ratio, "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{what}; numpy FP64, single thread ({dt:.1f} s)"}
+
+
+def run_cpu_all_cores(w, solver="mg", budget_s=10.0):
+    """The same oracle sample on every host core at once: one independent
+    single-thread oracle process per core, each advancing its own copy of the
+    sample box (spawned processes, so the parent's CUDA context is not
+    inherited). Aggregate throughput, scaled like the single-thread figure,
+    and the seconds per grid point per V-cycle of one oracle V-cycle."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import oracle as O
+    ws, ratio = oracle_sample(w)
+    cores = os.cpu_count() or 1
+    with cf.ProcessPoolExecutor(cores, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_oracle_worker, [(_sample_name(ws), solver, budget_s)] * cores))
+    rate = sum(n / dt for n, dt in res)
+    # one V-cycle of the oracle on the sample grid (context for the paper's
+    # CPU seconds per grid point per V-cycle)
+    rng = np.random.default_rng(7)
+    b = rng.normal(size=(ws.N,) * 3)
+    b -= b.mean()
+    x = np.zeros_like(b)
+    t0 = time.perf_counter()
+    nv = 3
+    for _ in range(nv):
+        x = O.vcycle(x, b, 1e-10)
+    tv = (time.perf_counter() - t0) / nv
+    return {"value": rate / ratio, "unit": "steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} independent single-thread oracle processes, each advancing its own "
+                      f"{ws.n_ions}-ion {ws.N}^3 box for {budget_s:g} s; aggregate steps/s scaled by 1/{ratio:g}",
+            "s_per_point_per_vcycle": tv / ws.N ** 3}
+
+
+def _sample_name(ws):
+    for name in ("nacl64", "nacl1000", "nacl8000", "nacl64000", "nacl512000"):
+        if synth.workload(name).name == ws.name:
+            return name
+    raise KeyError(ws.name)
 
 
 def bench_reference(args, w):
+    """--impl reference: the oracle on the host cores. Each timed step is one
+    oracle MD step of the bounded sample box (oracle_sample); the value is
+    scaled by the work ratio to steps/s of the named workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     os.environ.setdefault("OMP_NUM_THREADS", "1")
-    import oracle as O
-    pos, vel, types = synth.make_state(w)
-    tf = synth.tosi_fumi_nacl()
-    p = O.Params(L=w.L, N=w.N, dt=w.dt, tol=w.tol, rc=w.rc, P=w.order, solver=args.solver)
-    st = O.init(pos, vel, types, p, tf)
-    for _ in range(args.warmup):
-        st = O.step(st, p, tf)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        st = O.step(st, p, tf)
-        times.append(time.perf_counter() - t0)
-    tot = sum(times)
-    val = args.steps / tot
+    ws, ratio = oracle_sample(w)
+    n, tot, times = _oracle_steps(ws, args.solver, float("inf"), args.steps, warmup=args.warmup)
+    val = args.steps / tot / ratio
+    what = (f"{args.steps} timed MD steps after {args.warmup} warm-up steps of the {w.n_ions}-ion {w.N}^3 box"
+            if ratio == 1.0 else
+            f"{args.steps} timed MD steps after {args.warmup} warm-up steps of the {ws.n_ions}-ion {ws.N}^3 box "
+            f"of the same molten NaCl (1/{ratio:g} of the {w.n_ions}-ion {w.N}^3 box's ions and grid points), "
+            f"steps/s scaled by 1/{ratio:g}")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "steps/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps * ratio,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict(w, args),
-            "p50_us": 1e6 * float(np.percentile(times, 50)), "p99_us": 1e6 * float(np.percentile(times, 99)),
+            "data": "synthetic", "config": config_dict(w, args, reference=True),
+            "p50_us": 1e6 * ratio * float(np.percentile(times, 50)),
+            "p99_us": 1e6 * ratio * float(np.percentile(times, 99)),
             "cpu_baseline": {"value": val, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} timed MD steps after {args.warmup} warm-up steps of the "
-                                       f"{w.n_ions}-ion {w.N}^3 box, numpy FP64, one host thread"},
+                             "sample": f"{what}; numpy FP64, one host thread"},
             "e2e": {"value": val, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -218,10 +347,13 @@ def weak_scaling_value(world, steps_per_rank, rank_seconds):
     return world * steps_per_rank / rank_seconds
 
 
-def config_dict(w, args):
+def config_dict(w, args, reference=False):
+    """The workload of the line. The CUDA arm's headline precision is the
+    one --precision names; the reference arm is always the FP64 oracle."""
+    prec = "fp64" if reference else args.precision
     return {"workload": f"molten NaCl {w.n_ions} ions, L={w.L} A, {w.N}^3 grid, {w.T:.0f} K, dt={w.dt} fs, "
                         f"tol={w.tol:g}, P={w.order}, r_cut={w.rc} A",
-            "n_ions": w.n_ions, "grid": w.N, "solver": args.solver, "precision": args.precision,
+            "n_ions": w.n_ions, "grid": w.N, "solver": args.solver, "precision": prec,
             "l2": "flushed between timed steps and before each timed e2e exchange (256 MiB write outside "
                   "the timing)"}
 
@@ -232,7 +364,6 @@ def config_dict(w, args):
 # A kernel changed after its capture must drop its entry (traffic null).
 MEASURED_TRAFFIC = {
     ("nacl1000", "k_mixed_cluster", "mixed", "mg"): (1195520, "profiles/k_mixed_cluster_nacl1000.md"),
-    ("nacl512000", "k_mixed_grid", "mixed", "mg"): (10840736000, "profiles/k_mixed_grid_nacl512000.md"),
 }
 
 
@@ -246,30 +377,166 @@ def has_cells(w):
     return int(np.floor(w.L / w.rc)) >= 3
 
 
-def solve_kernel_name(args, w):
+def solve_kernel_name(precision, solver, w):
     """The solve kernel a step launches for this precision, solver and grid."""
-    if args.precision == "mixed":
+    if precision == "mixed":
         if w.N > 64:
             return "k_mixed_grid"
         return "k_mixed_cluster" if has_cells(w) else "k_cluster_step"
-    return "k_mg_solve" if args.solver == "mg" else "k_cg_solve"
+    return "k_mg_solve" if solver == "mg" else "k_cg_solve"
+
+
+def kernels_per_step(precision, w):
+    if precision == "mixed" and w.N <= 64:
+        return KERNELS_PER_STEP_SPLIT if has_cells(w) else KERNELS_PER_STEP_FUSED
+    return KERNELS_PER_STEP_CELLS if has_cells(w) else KERNELS_PER_STEP_NOCELLS
+
+
+def force_error_vs_oracle(M, sim, w, types, tf):
+    """Per-ion force error of the GPU's current forces against the oracle's
+    exact discrete solution on the GPU's current positions (all ions up to
+    5000, else 64 sampled ions with brute-force pairs for those)."""
+    import oracle as O
+    x = sim.get(M.MAZE_POS)
+    F = sim.get(M.MAZE_FORCE)
+    p = O.Params(L=w.L, N=w.N, dt=w.dt, tol=w.tol, rc=w.rc, P=w.order)
+    phi_ex, _ = O.exact_potential(x, types, p)
+    Q = np.where(types == 0, 1.0, -1.0)
+    if w.n_ions <= 5000:
+        idx = np.arange(w.n_ions)
+        Fo = O.gather_forces(x, Q, phi_ex, w.L, w.N, w.order) + O.tf_forces(x, types, w.L, tf, w.rc)[0]
+    else:
+        idx = np.random.default_rng(5).choice(w.n_ions, 64, replace=False)
+        Fo = (O.gather_forces(x[idx], Q[idx], phi_ex, w.L, w.N, w.order)
+              + O.tf_forces_on(idx, x, types, w.L, tf, w.rc))
+    scale = np.sqrt((np.linalg.norm(F, axis=1) ** 2).mean())
+    nrm = np.linalg.norm(Fo, axis=1)
+    return float((np.linalg.norm(F[idx] - Fo, axis=1) / np.maximum(nrm, scale)).max())
+
+
+def time_box(args, M, w, precision, solver, stream, flush, dist=None, dev="cpu", world=1, rank=0, e2e=True):
+    """Time ``args.steps`` steps of one box (after ``args.warmup`` untimed
+    ones): per-step CUDA events on the context stream with an L2 flush
+    between steps outside the events, the solve kernel's time from events
+    inside the step graph; then the force error against the oracle (rank 0)
+    and, when asked, the end-to-end exchange through the C ABI."""
+    import torch
+    pos, vel, types = synth.make_state(w)
+    tf = synth.tosi_fumi_nacl()
+    sim = M.MazeSim(pos, vel, types, w.L, w.N, tf, r_cut=w.rc, dt=w.dt, tol=w.tol, order=w.order,
+                    solver=M.MAZE_SOLVER_MG if solver == "mg" else M.MAZE_SOLVER_CG,
+                    precision=M.MAZE_MIXED if precision == "mixed" else M.MAZE_FP64, stream=stream.cuda_stream)
+    sim.set_timing(True)
+    for _ in range(args.warmup):
+        sim.step_async(1)
+    torch.cuda.synchronize()
+    s1 = sim.stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    solve_ms, phase_ms, timing_error = [], [], None
+    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else
+                          int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            ev[k][0].record(stream)
+            sim.step_async(1)
+            ev[k][1].record(stream)
+        try:
+            ph = sim.timing()                    # synchronises: reads the in-graph phase events
+            solve_ms.append(ph[2])
+            phase_ms.append(ph)
+        except Exception as e:                   # timing events unavailable: roofline left null
+            timing_error = str(e)
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dist if world > 1 else None, dev)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    s2 = sim.stats()
+    if s2["status"] != 0:
+        raise RuntimeError(f"step failed: {s2}")
+    out = {"steps_per_s": weak_scaling_value(world, args.steps, total_s), "total_s": total_s,
+           "ms_per_step": 1e3 * total_s / args.steps, "step_ms": step_ms,
+           "iters_per_step": (s2["total_iters"] - s1["total_iters"]) / args.steps,
+           "solve_s": statistics.mean(solve_ms) / 1e3 if solve_ms else float("nan"),
+           "phase_us": dict(zip(["move_spread", "cells", "solve", "forces"],
+                                [round(1e3 * float(v), 2) for v in np.mean(phase_ms, axis=0)])) if phase_ms else None,
+           "timing_error": timing_error, "clocks": clk, "force_error": None, "e2e": None}
+    if rank == 0:
+        out["force_error"] = force_error_vs_oracle(M, sim, w, types, tf)
+    if e2e:
+        # end to end through the C ABI with host buffers: per step upload the
+        # ion state from pinned host memory, run the step, read back
+        # positions, velocities and the record (maze_step_io, one sync)
+        io = sim.exchange_buffers()
+        n_e2e = min(args.steps, 100)
+        sim.set_timing(False)    # a user's step: no phase events in the graph
+        for _ in range(5):       # untimed warm-up (the GPU idled during the force check)
+            sim.exchange(io)
+        if world > 1:
+            dist.barrier()
+        e2e_s = 0.0
+        for _ in range(n_e2e):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sim.exchange(io)
+            e2e_s += time.perf_counter() - t0
+        e2e_s = max_over_ranks(e2e_s, dist if world > 1 else None, dev)
+        out["e2e"] = {"value": weak_scaling_value(world, n_e2e, e2e_s), "unit": "steps/s",
+                      "h2d_bytes_per_step": 2 * 24 * w.n_ions, "d2h_bytes_per_step": 2 * 24 * w.n_ions + 104}
+    sim.close()
+    return out
+
+
+def rooflines(w, precision, solver, iters, solve_s, workload, sms):
+    """The solve kernel against its roofs: HBM (measured copy peak) always;
+    for FP64 multigrid also the FP64 pipe. ``roofline`` is the binding one
+    (the roof whose time for the algorithmic work is longer)."""
+    kernel = solve_kernel_name(precision, solver, w)
+    peak, peak_kind = peaks()
+    b = solve_bytes_per_launch(w.N, iters, solver, precision=precision)
+    hbm = {"kernel": kernel, "bound": "hbm", "achieved": b / solve_s / 1e9, "peak": peak,
+           "peak_kind": peak_kind, "unit": "GB/s", "frac": b / solve_s / 1e9 / peak,
+           "traffic": measured_traffic(workload, kernel, precision, solver), "algorithmic_bytes_per_launch": b,
+           "survey_unit_frac": survey_bytes_per_launch(w.N, iters, solver, precision) / solve_s / 1e9 / peak}
+    if precision != "fp64" or solver != "mg":
+        return hbm, None
+    ops = fp64_mg_ops_per_launch(w.N, iters)
+    pk = fp64_peak_tops(sms)
+    alu = {"kernel": kernel, "bound": "alu", "achieved": ops / solve_s / 1e12, "peak": pk,
+           "peak_kind": "derived: 2 FP64 operations per clock per SM x SMs x maximum SM clock",
+           "unit": "TOP/s (FP64 add, multiply or FMA = 1 operation)", "frac": ops / solve_s / 1e12 / pk,
+           "traffic": hbm["traffic"], "algorithmic_ops_per_launch": ops, "algorithmic_bytes_per_launch": b}
+    if ops / (pk * 1e12) >= b / (peak * 1e9):
+        return alu, hbm
+    return hbm, alu
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="nacl1000",
-                    choices=["nacl64", "nacl1000", "nacl64000", "nacl512000", "batch128", "serve", "study"])
+    ap.add_argument("--workload", default="nacl512000",
+                    choices=["nacl64", "nacl1000", "nacl8000", "nacl64000", "nacl512000", "batch128", "serve",
+                             "study"])
     ap.add_argument("--requests", type=int, default=200, help="serve: number of requests")
     ap.add_argument("--boxes", type=int, default=128, help="batch128: number of replica boxes")
     ap.add_argument("--cluster-ctas", type=int, default=0, help="batch128: CTAs per box (0: autotune)")
     ap.add_argument("--solver", default="mg", choices=["cg", "mg"])
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision run beside an FP64 line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.workload == "batch128":
@@ -302,138 +569,55 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     M.load()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
     # every rank advances its own replica (independent seed)
     w = replica_workload(args.workload, rank)
-    pos, vel, types = synth.make_state(w)
-    tf = synth.tosi_fumi_nacl()
     stream = torch.cuda.Stream(device=dev)
-    solver = M.MAZE_SOLVER_MG if args.solver == "mg" else M.MAZE_SOLVER_CG
-    precision = M.MAZE_MIXED if args.precision == "mixed" else M.MAZE_FP64
-    sim = M.MazeSim(pos, vel, types, w.L, w.N, tf, r_cut=w.rc, dt=w.dt, tol=w.tol, order=w.order,
-                    solver=solver, precision=precision, stream=stream.cuda_stream)
-    sim.set_timing(True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    s0 = sim.stats()
-    for _ in range(args.warmup):
-        sim.step_async(1)
-    torch.cuda.synchronize()
-    s1 = sim.stats()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    solve_ms = []
-    phase_ms = []
-    timing_error = None
-    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
-    clocks.start()
-    time.sleep(0.3)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    it_before = s1["total_iters"]
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-            ev[k][0].record(stream)
-            sim.step_async(1)
-            ev[k][1].record(stream)
-        try:
-            ph = sim.timing()                    # synchronises: reads the in-graph phase events
-            solve_ms.append(ph[2])
-            phase_ms.append(ph)
-        except Exception as e:                   # timing events unavailable: roofline left null
-            timing_error = str(e)
-    torch.cuda.synchronize()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = max_over_ranks(sum(step_ms) / 1e3, dist if world > 1 else None, dev)
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    s2 = sim.stats()
-    if s2["status"] != 0:
-        raise RuntimeError(f"step failed: {s2}")
-    iters = (s2["total_iters"] - it_before) / args.steps
-
-    # force error at the stated tolerance: GPU forces vs the oracle's exact
-    # discrete solution on the GPU's final positions (rank 0, not timed)
-    ferr = None
-    if rank == 0:
-        import oracle as O
-        x = sim.get(M.MAZE_POS)
-        F = sim.get(M.MAZE_FORCE)
-        p = O.Params(L=w.L, N=w.N, dt=w.dt, tol=w.tol, rc=w.rc, P=w.order)
-        phi_ex, _ = O.exact_potential(x, types, p)
-        Q = np.where(types == 0, 1.0, -1.0)
-        if w.n_ions <= 5000:
-            idx = np.arange(w.n_ions)
-            Fo = O.gather_forces(x, Q, phi_ex, w.L, w.N, w.order) + O.tf_forces(x, types, w.L, tf, w.rc)[0]
-        else:   # large boxes: 64 sampled ions, brute-force pairs for those only
-            idx = np.random.default_rng(5).choice(w.n_ions, 64, replace=False)
-            Fo = (O.gather_forces(x[idx], Q[idx], phi_ex, w.L, w.N, w.order)
-                  + O.tf_forces_on(idx, x, types, w.L, tf, w.rc))
-        scale = np.sqrt((np.linalg.norm(F, axis=1) ** 2).mean())
-        nrm = np.linalg.norm(Fo, axis=1)
-        ferr = float((np.linalg.norm(F[idx] - Fo, axis=1) / np.maximum(nrm, scale)).max())
-
-    # end to end through the C ABI with host buffers: per step upload the ion
-    # state from pinned host memory, run the step, read back positions + stats
-    e2e = None
-    if not args.no_e2e:
-        io = sim.exchange_buffers()   # pinned host positions and velocities
-        n_e2e = min(args.steps, 100)
-        sim.set_timing(False)    # a user's step: no phase events in the graph
-        for _ in range(5):       # untimed warm-up (the GPU idled during the force check)
-            sim.exchange(io)
-        if world > 1:
-            dist.barrier()
-        e2e_s = 0.0
-        for _ in range(n_e2e):
-            # L2 flushed before each exchange, outside its timing (as for the
-            # device-timed steps)
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            # maze_step_io: upload, one step, positions, velocities and the
-            # record back, one synchronisation
-            sim.exchange(io)
-            e2e_s += time.perf_counter() - t0
-        e2e_s = max_over_ranks(e2e_s, dist if world > 1 else None, dev)
-        e2e = {"value": weak_scaling_value(world, n_e2e, e2e_s), "unit": "steps/s",
-               "h2d_bytes_per_step": 2 * 24 * w.n_ions,
-               "d2h_bytes_per_step": 2 * 24 * w.n_ions + 104}
+    head = time_box(args, M, w, args.precision, args.solver, stream, flush, dist, dev, world, rank,
+                    e2e=not args.no_e2e)
+    # the same box in mixed precision beside an FP64 headline (extra keys)
+    mixed = None
+    if args.precision == "fp64" and args.solver == "mg" and not args.no_mixed:
+        mixed = time_box(args, M, w, "mixed", "mg", stream, flush, dist, dev, world, rank, e2e=False)
 
     if rank == 0:
-        ng = w.N ** 3
-        bytes_launch = solve_bytes_per_launch(w.N, iters, args.solver, precision=args.precision)
-        mean_solve_s = statistics.mean(solve_ms) / 1e3 if solve_ms else float("nan")
-        achieved = bytes_launch / mean_solve_s / 1e9
-        peak, peak_kind = peaks()
+        roof, other = rooflines(w, args.precision, args.solver, head["iters_per_step"], head["solve_s"],
+                                args.workload, sms)
         cpu = None if args.no_cpu else run_cpu_baseline(w, args.solver)
-        if args.precision == "mixed" and w.N <= 64:
-            kps = KERNELS_PER_STEP_SPLIT if has_cells(w) else KERNELS_PER_STEP_FUSED
-        else:
-            kps = KERNELS_PER_STEP_CELLS if has_cells(w) else KERNELS_PER_STEP_NOCELLS
+        cpu_all = None
+        if not args.no_cpu:
+            try:
+                cpu_all = run_cpu_all_cores(w, args.solver)
+            except Exception as e:          # a worker that could not start: reported, not fatal
+                cpu_all = {"unavailable": f"{type(e).__name__}: {e}"}
         line = {
-            "metric": METRIC, "value": weak_scaling_value(world, args.steps, total_s), "unit": "steps/s",
+            "metric": METRIC, "value": head["steps_per_s"], "unit": "steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f32x2",
             "data": "synthetic", "config": config_dict(w, args),
-            "p50_us": 1e3 * float(np.percentile(step_ms, 50)), "p99_us": 1e3 * float(np.percentile(step_ms, 99)),
-            "iters_per_step": iters, "force_error": ferr,
-            "phase_us": dict(zip(["move_spread", "cells", "solve", "forces"],
-                                 [round(1e3 * float(v), 2) for v in np.mean(phase_ms, axis=0)])) if phase_ms else None,
-            "solve_gbs": achieved, "solve_us": 1e6 * mean_solve_s,
-            "roofline": {"kernel": solve_kernel_name(args, w), "bound": "hbm", "achieved": achieved, "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": measured_traffic(args.workload, solve_kernel_name(args, w), args.precision,
-                                                     args.solver),
-                         "algorithmic_bytes_per_launch": bytes_launch},
-            "cpu_baseline": cpu, "e2e": e2e, "timing_error": timing_error,
-            "gpu_launches": kps * args.steps, "clocks": clk,
+            "p50_us": 1e3 * float(np.percentile(head["step_ms"], 50)),
+            "p99_us": 1e3 * float(np.percentile(head["step_ms"], 99)),
+            "iters_per_step": head["iters_per_step"], "force_error": head["force_error"],
+            "phase_us": head["phase_us"], "solve_us": 1e6 * head["solve_s"],
+            "roofline": roof, "roofline_other": other,
+            "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": head["e2e"],
+            "timing_error": head["timing_error"],
+            "gpu_launches": kernels_per_step(args.precision, w) * args.steps, "clocks": head["clocks"],
         }
+        if mixed is not None:
+            mroof, _ = rooflines(w, "mixed", "mg", mixed["iters_per_step"], mixed["solve_s"], args.workload, sms)
+            line["mixed"] = {
+                "what": "the same box and steps in mixed precision (FP32 V-cycle, double-float outer SHAKE "
+                        "iteration, FP64 reductions), timed the same way after the FP64 run",
+                "steps_per_s": mixed["steps_per_s"], "ms_per_step": mixed["ms_per_step"],
+                "speedup_vs_fp64": mixed["steps_per_s"] / head["steps_per_s"],
+                "iters_per_step": mixed["iters_per_step"], "force_error": mixed["force_error"],
+                "phase_us": mixed["phase_us"], "solve_us": 1e6 * mixed["solve_s"], "roofline": mroof,
+                "gpu_launches": kernels_per_step("mixed", w) * args.steps, "clocks": mixed["clocks"]}
         print(json.dumps(line), flush=True)
-    sim.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -268,19 +268,27 @@ maze_status maze_get_timing(maze_ctx* ctx, double* out4);
  * same warm-started CG and stopping rule as maze_solve, then removes the mean
  * of y.
  *   grid_N     grid edge N, even, 8 <= N <= 64
- *   sigma_p    [N^3] device pointer, read only, flat index n = i + jN + kN^2
- *   y          [N^3] device pointer; in: warm start, out: zero-mean solution
+ *   sigma_p    [N^3] device pointer, read only, flat index n = i + jN + kN^2;
+ *              its entries must sum to zero (the periodic M is singular and
+ *              only a zero-mean right-hand side has a solution: a charge-
+ *              neutral box gives one), else the call runs to max_iter and
+ *              returns MAZE_ERR_NOT_CONVERGED
+ *   y          [N^3] device pointer, not overlapping sigma_p (sigma_p == y is
+ *              rejected with MAZE_ERR_INVALID); in: warm start, out: zero-mean
+ *              solution
  *   tol        stop when max_n |(M y - sigma_p)_n| < tol
  *   max_iter   CG iteration cap
  *   cuda_stream stream to run on (NULL = legacy default stream); the call
- *              synchronises it before returning
+ *              synchronises it before returning, so it must never be made
+ *              while that stream is being captured into a CUDA graph
  *   iters, resid_inf  optional outputs (host pointers)
  * It allocates nothing: its work vectors live in one file-scope device array
  * of about 6.4 MB (3 x 64^3 doubles plus a small status block), which every
  * GPU that loads the library holds until the process exits. Larger grids are
  * rejected with MAZE_ERR_INVALID. The first call on a device, with that device
- * current, resolves the array's device address and the launch size; make that
- * first call before any stream capture. Every call shares the one array and
+ * current, resolves the array's device address and the launch size. A NaN or
+ * infinity in sigma_p or in the warm start ends the call with
+ * MAZE_ERR_NONFINITE. Every call shares the one array and
  * keeps the last call's contents in it, so calls that overlap on the GPU (on
  * different streams or threads) race and must be serialised by the caller. */
 maze_status maze_solve_shake_noalloc(int32_t grid_N, const double* sigma_p, double* y, double tol,

@@ -358,6 +358,23 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+// Max-norm accumulation on the integer pipe: |v| as its IEEE bit pattern. For
+// non-negative doubles the integer order is the numeric order and every NaN
+// sorts above +inf, so a NaN entry is never dropped (fmax would drop it).
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+}
+// The accumulated maximum as a double, a NaN reported as +inf (non-finite
+// either way, and +inf survives an fmax-based combine).
+__device__ __forceinline__ double absmax_value(unsigned long long u) {
+  return u > 0x7ff0000000000000ULL ? __longlong_as_double(0x7ff0000000000000LL) : __longlong_as_double((long long)u);
+}
+// FP32 form: |v|, a NaN mapped to +inf.
+__device__ __forceinline__ float abs_nan_inf(float v) {
+  const float a = fabsf(v);
+  return a == a ? a : __int_as_float(0x7f800000);
+}
+
 // Periodic neighbours of flat index n = i + jN + kN^2.
 struct Nbr {
   int xm, xp, ym, yp, zm, zp;

@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_mg_solve(SolveArgs a, MgArgs 
 
   // ---- S4 and the initial residual of the warm start
   {
-    double rmax = 0, ys = 0;
+    double ys = 0;
+    unsigned long long rmax = 0;
     for (int m = tid; m < n; m += stride) {
       const Nbr b = neighbours(m, N0);
       const double q = (double)(long long)a.qfix[m] * kQInv;
@@ -89,15 +90,15 @@ __global__ void __launch_bounds__(kSolveThreads) k_mg_solve(SolveArgs a, MgArgs 
       a.sigma[m] = sg;
       const double* y = a.y;
       const double My = (y[b.xm] + y[b.xp]) + (y[b.ym] + y[b.yp]) + (y[b.zm] + y[b.zp]) - 6.0 * y[m];
-      rmax = fmax(rmax, fabs(sg - My));
+      rmax = max(rmax, abs_bits(sg - My));
       ys += y[m];
     }
-    const double v[2] = {rmax, ys};
+    const double v[2] = {absmax_value(rmax), ys};
     if (!grid_reduce<2>(v, m2, a.recs, ++epoch, a.rec, tot)) return;
   }
   double res = tot[0], ysum = tot[1];
   int it = 0;
-  bool finite = isfinite(res);
+  bool finite = isfinite(res) && isfinite(ysum);
 
   while (finite && !(res < a.tol) && it < a.max_iter) {
     // ---- down: smooth, residual, restrict
@@ -202,19 +203,20 @@ __global__ void __launch_bounds__(kSolveThreads) k_mg_solve(SolveArgs a, MgArgs 
     ++it;
     // ---- residual check (Eq. res_poisson_maze) and sum y
     {
-      double rmax = 0, ys = 0;
+      double ys = 0;
+      unsigned long long rmax = 0;
       const double* y = a.y;
       for (int m = tid; m < n; m += stride) {
         const Nbr b = neighbours(m, N0);
         const double My = (y[b.xm] + y[b.xp]) + (y[b.ym] + y[b.yp]) + (y[b.zm] + y[b.zp]) - 6.0 * y[m];
-        rmax = fmax(rmax, fabs(a.sigma[m] - My));
+        rmax = max(rmax, abs_bits(a.sigma[m] - My));
         ys += y[m];
       }
-      const double v[2] = {rmax, ys};
+      const double v[2] = {absmax_value(rmax), ys};
       if (!grid_reduce<2>(v, m2, a.recs, ++epoch, a.rec, tot)) return;
       res = tot[0];
       ysum = tot[1];
-      finite = isfinite(res);
+      finite = isfinite(res) && isfinite(ysum);
     }
   }
   // ---- S6
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_mg_solve(SolveArgs a, MgArgs 
     r->iters = it;
     r->resid = res * a.res_scale;
     r->total_iters += it;
-    if (!isfinite(res)) r->status = MAZE_ERR_NONFINITE;
+    if (!isfinite(res) || !isfinite(ysum)) r->status = MAZE_ERR_NONFINITE;
     else if (!(res < a.tol)) r->status = MAZE_ERR_NOT_CONVERGED;
   }
 }

@@ -98,17 +98,18 @@ k_shake_cg_noalloc(int N, const double* __restrict__ sigma, double* __restrict__
   double tot[3];
 
   auto true_residual = [&](bool store) {
-    double rr = 0, rmax = 0, ys = 0;
+    double rr = 0, ys = 0;
+    unsigned long long rmax = 0;
     for (int m = tid; m < n; m += stride) {
       const Nbr b = neighbours(m, N);
       const double My = (y[b.xm] + y[b.xp]) + (y[b.ym] + y[b.yp]) + (y[b.zm] + y[b.zp]) - 6.0 * y[m];
       const double rv = sigma[m] - My;
       if (store) r[m] = rv;
       rr += rv * rv;
-      rmax = fmax(rmax, fabs(rv));
+      rmax = max(rmax, abs_bits(rv));
       ys += y[m];
     }
-    const double v[3] = {rr, rmax, ys};
+    const double v[3] = {rr, absmax_value(rmax), ys};
     na_partial(v, m3, 3, part + (red & 1) * pbuf);
   };
 
@@ -118,7 +119,8 @@ k_shake_cg_noalloc(int N, const double* __restrict__ sigma, double* __restrict__
   ++red;
   double rho = tot[0], res = tot[1], ysum = tot[2];
   int it = 0;
-  bool conv = res < tol, fresh = true, have_ysum = true, finite = isfinite(res);
+  bool conv = res < tol, fresh = true, have_ysum = true;
+  bool finite = isfinite(res) && isfinite(rho) && isfinite(ysum);
   double beta = 0.0;
   while (!conv && finite && it < max_iter) {
     have_ysum = false;
@@ -140,17 +142,22 @@ k_shake_cg_noalloc(int N, const double* __restrict__ sigma, double* __restrict__
     double t1[1];
     na_combine(part + (red & 1) * pbuf, m1, 1, t1);
     ++red;
+    if (!isfinite(t1[0])) {
+      finite = false;
+      break;
+    }
     const double alpha = rho / t1[0];
     {
-      double rr = 0, rmax = 0;
+      double rr = 0;
+      unsigned long long rmax = 0;
       for (int m = tid; m < n; m += stride) {
         y[m] += alpha * p[m];
         const double rv = r[m] - alpha * Mp[m];
         r[m] = rv;
         rr += rv * rv;
-        rmax = fmax(rmax, fabs(rv));
+        rmax = max(rmax, abs_bits(rv));
       }
-      const double v[2] = {rr, rmax};
+      const double v[2] = {rr, absmax_value(rmax)};
       na_partial(v, m2, 2, part + (red & 1) * pbuf);
     }
     if (!grid_barrier(bar, epoch, rec)) return;
@@ -169,6 +176,10 @@ k_shake_cg_noalloc(int N, const double* __restrict__ sigma, double* __restrict__
       res = tot[1];
       ysum = tot[2];
       have_ysum = true;
+      if (!isfinite(res) || !isfinite(ysum) || !isfinite(tot[0])) {
+        finite = false;
+        break;
+      }
       if (res < tol) {
         conv = true;
         break;
@@ -195,7 +206,7 @@ k_shake_cg_noalloc(int N, const double* __restrict__ sigma, double* __restrict__
     rec->iters = it;
     rec->resid = res;
     if (rec->status == MAZE_OK) {
-      if (!isfinite(res)) rec->status = MAZE_ERR_NONFINITE;
+      if (!finite || !isfinite(res) || !isfinite(ysum)) rec->status = MAZE_ERR_NONFINITE;
       else if (!(res < tol)) rec->status = MAZE_ERR_NOT_CONVERGED;
     }
   }
@@ -226,6 +237,8 @@ extern "C" maze_status maze_solve_shake_noalloc(int32_t grid_N, const double* si
                                                double* resid_inf) {
   using namespace maze;
   if (!sigma_p || !y) return na_fail(MAZE_ERR_INVALID, "sigma_p and y must be device pointers");
+  if ((const void*)sigma_p == (const void*)y)
+    return na_fail(MAZE_ERR_INVALID, "sigma_p and y must be distinct buffers (y is overwritten while sigma_p is read)");
   if (grid_N < 8 || grid_N % 2)
     return na_fail(MAZE_ERR_INVALID, "grid_N must be even and >= 8");
   if (grid_N > kNoAllocMaxN)

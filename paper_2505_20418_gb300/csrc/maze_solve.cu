@@ -38,7 +38,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_cg_solve(SolveArgs a) {
 
   // ---- S4 and the initial residual r0 = sigma_p - M y0
   {
-    double rr = 0, rmax = 0, ys = 0;
+    double rr = 0, ys = 0;
+    unsigned long long rmax = 0;
     for (int m = tid; m < n; m += stride) {
       const Nbr b = neighbours(m, N);
       const double q = (double)(long long)a.qfix[m] * kQInv;
@@ -66,10 +67,10 @@ __global__ void __launch_bounds__(kSolveThreads) k_cg_solve(SolveArgs a) {
       const double r = sg - My;
       a.r[m] = r;
       rr += r * r;
-      rmax = fmax(rmax, fabs(r));
+      rmax = max(rmax, abs_bits(r));
       ys += y[m];
     }
-    const double v[3] = {rr, rmax, ys};
+    const double v[3] = {rr, absmax_value(rmax), ys};
     if (!grid_reduce<3>(v, m3, a.recs, ++epoch, a.rec, tot)) return;
   }
   double rho = tot[0], res = tot[1], ysum = tot[2];
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_cg_solve(SolveArgs a) {
   bool fresh = true;
   bool have_ysum = true;
   double beta = 0.0;
-  bool finite = isfinite(res);
+  bool finite = isfinite(res) && isfinite(rho) && isfinite(ysum);
   int cur = 0;          // p_old lives in p[cur], p_new goes to p[cur ^ 1]
 
   while (!conv && finite && it < a.max_iter) {
@@ -116,15 +117,16 @@ __global__ void __launch_bounds__(kSolveThreads) k_cg_solve(SolveArgs a) {
                           [rho_c](const double* t) { return rho_c * recip_newton(t[0]); }, &alpha))
         return;
       // phase C: y += alpha p_new, r -= alpha Mp; r.r and max|r|
-      double rr = 0, rmax = 0;
+      double rr = 0;
+      unsigned long long rmax = 0;
       for (int m = tid; m < n; m += stride) {
         a.y[m] += alpha * pn[m];
         const double rv = a.r[m] - alpha * a.Mp[m];
         a.r[m] = rv;
         rr += rv * rv;
-        rmax = fmax(rmax, fabs(rv));
+        rmax = max(rmax, abs_bits(rv));
       }
-      const double v2[2] = {rr, rmax};
+      const double v2[2] = {rr, absmax_value(rmax)};
       double t2[2], beta_new;
       const double rho_old = rho;
       if (!grid_reduce<2>(v2, m2, a.recs, ++epoch, a.rec, t2,
@@ -137,7 +139,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_cg_solve(SolveArgs a) {
       if (!finite) break;
       if (res < a.tol) {
         // confirm with the true residual sigma_p - M y (also gives sum y)
-        double rr3 = 0, rmax3 = 0, ys = 0;
+        double rr3 = 0, ys = 0;
+        unsigned long long rmax3 = 0;
         const double* y = a.y;
         for (int m = tid; m < n; m += stride) {
           const Nbr b = neighbours(m, N);
@@ -145,10 +148,10 @@ __global__ void __launch_bounds__(kSolveThreads) k_cg_solve(SolveArgs a) {
           const double rv = a.sigma[m] - My;
           a.r[m] = rv;
           rr3 += rv * rv;
-          rmax3 = fmax(rmax3, fabs(rv));
+          rmax3 = max(rmax3, abs_bits(rv));
           ys += y[m];
         }
-        const double v3[3] = {rr3, rmax3, ys};
+        const double v3[3] = {rr3, absmax_value(rmax3), ys};
         if (!grid_reduce<3>(v3, m3, a.recs, ++epoch, a.rec, tot)) return;
         res = tot[1];
         ysum = tot[2];
@@ -168,17 +171,18 @@ __global__ void __launch_bounds__(kSolveThreads) k_cg_solve(SolveArgs a) {
   }
   if (!have_ysum) {
     // stopped at max_iter or on a non-finite value: true residual and sum y
-    double rr = 0, rmax = 0, ys = 0;
+    double rr = 0, ys = 0;
+    unsigned long long rmax = 0;
     const double* y = a.y;
     for (int m = tid; m < n; m += stride) {
       const Nbr b = neighbours(m, N);
       const double My = (y[b.xm] + y[b.xp]) + (y[b.ym] + y[b.yp]) + (y[b.zm] + y[b.zp]) - 6.0 * y[m];
       const double rv = a.sigma[m] - My;
       rr += rv * rv;
-      rmax = fmax(rmax, fabs(rv));
+      rmax = max(rmax, abs_bits(rv));
       ys += y[m];
     }
-    const double v[3] = {rr, rmax, ys};
+    const double v[3] = {rr, absmax_value(rmax), ys};
     if (!grid_reduce<3>(v, m3, a.recs, ++epoch, a.rec, tot)) return;
     res = tot[1];
     ysum = tot[2];
@@ -195,7 +199,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_cg_solve(SolveArgs a) {
     r->iters = it;
     r->resid = res * a.res_scale;
     r->total_iters += it;
-    if (!isfinite(res)) r->status = MAZE_ERR_NONFINITE;
+    if (!isfinite(res) || !isfinite(ysum)) r->status = MAZE_ERR_NONFINITE;
     else if (!(res < a.tol)) r->status = MAZE_ERR_NOT_CONVERGED;
   }
 }

@@ -997,8 +997,8 @@ __device__ __forceinline__ void s4_pass(const RLevel& v0, int t0, int ts, df c_s
     const int c0 = (i0 + j + k) & 1, hb = kl * HH0 + j * H0 + (i0 >> 1);
     b0[c0 * PH0 + hb] = rfA;
     b0[(1 - c0) * PH0 + hb] = rfB;
-    ymax = fmaxf(ymax, fmaxf(fabsf(yA.h), fabsf(yB.h)));
-    rmax = fmaxf(rmax, fmaxf(fabsf(rfA), fabsf(rfB)));
+    ymax = fmaxf(ymax, fmaxf(abs_nan_inf(yA.h), abs_nan_inf(yB.h)));
+    rmax = fmaxf(rmax, fmaxf(abs_nan_inf(rfA), abs_nan_inf(rfB)));
   }
   rmax_o = rmax;
   ymax_o = ymax;
@@ -1091,8 +1091,8 @@ __device__ __forceinline__ void update_pass(const RLevel& v0, int t0, int ts, co
     *reinterpret_cast<float4*>(ynext + m) = make_float4(nA.x, nA.y, nB.x, nB.y);
     b0[c0 * PH0 + rowb + t] = rA;
     b0[(1 - c0) * PH0 + rowb + t] = rB;
-    ymax = fmaxf(ymax, fmaxf(fabsf(nA.x), fabsf(nB.x)));
-    rmax = fmaxf(rmax, fmaxf(fabsf(rA), fabsf(rB)));
+    ymax = fmaxf(ymax, fmaxf(abs_nan_inf(nA.x), abs_nan_inf(nB.x)));
+    rmax = fmaxf(rmax, fmaxf(abs_nan_inf(rA), abs_nan_inf(rB)));
   }
   rmax_o = rmax;
   ymax_o = ymax;
@@ -1179,8 +1179,8 @@ __device__ __forceinline__ void update_pass4(const RLevel& v0, int t0, int ts, c
     *reinterpret_cast<float4*>(ynext + m + 2) = make_float4(n2.x, n2.y, n3.x, n3.y);
     *reinterpret_cast<float2*>(b0 + c0 * PH0 + rowb + t) = make_float2(r0, r2);
     *reinterpret_cast<float2*>(b0 + (1 - c0) * PH0 + rowb + t) = make_float2(r1, r3);
-    ymax = fmaxf(ymax, fmaxf(fmaxf(fabsf(n0.x), fabsf(n1.x)), fmaxf(fabsf(n2.x), fabsf(n3.x))));
-    rmax = fmaxf(rmax, fmaxf(fmaxf(fabsf(r0), fabsf(r1)), fmaxf(fabsf(r2), fabsf(r3))));
+    ymax = fmaxf(ymax, fmaxf(fmaxf(abs_nan_inf(n0.x), abs_nan_inf(n1.x)), fmaxf(abs_nan_inf(n2.x), abs_nan_inf(n3.x))));
+    rmax = fmaxf(rmax, fmaxf(fmaxf(abs_nan_inf(r0), abs_nan_inf(r1)), fmaxf(abs_nan_inf(r2), abs_nan_inf(r3))));
   }
   rmax_o = rmax;
   ymax_o = ymax;
@@ -1253,7 +1253,7 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
     res = t[0];
     ymax_all = t[1];
   }
-  while (isfinite(res) && !(res < a.tol) && it < a.max_iter) {
+  while (isfinite(res) && isfinite(ymax_all) && !(res < a.tol) && it < a.max_iter) {
     // ---- FP32 V-cycle on M e = r from e = 0: the levels above the tail
     // across the sync domain, the tail in one CTA
     const int lt = R.tail;
@@ -1378,7 +1378,7 @@ __device__ void mixed_body(const MixedArgs& a, S& sync, float* dsm) {
     r->iters = it;
     r->resid = res * a.res_scale;
     r->total_iters += it;
-    if (!isfinite(res)) r->status = MAZE_ERR_NONFINITE;
+    if (!isfinite(res) || !isfinite(ymax_all)) r->status = MAZE_ERR_NONFINITE;
     else if (!(res < a.tol)) r->status = MAZE_ERR_NOT_CONVERGED;
   }
   // no block leaves (or reuses its shared memory) while another may still

@@ -165,6 +165,8 @@ def workload(name: str) -> Workload:
         return Workload("nacl1000_L31.5_N32", 10, 31.5, 32, steps=1000, seed=2000)
     if name == "nacl64000":   # 64000 ions, 128^3 grid (a profiling-size large box)
         return Workload("nacl64000_L126_N128", 40, 126.0, 128, steps=200, seed=4100)
+    if name == "nacl8000":    # 8000 ions, 64^3 grid: 1/64 of the 512000-ion box (same density, spacing, T)
+        return Workload("nacl8000_L63_N64", 20, 63.0, 64, steps=200, seed=4200)
     if name == "nacl512000":  # 512000 ions, 256^3 grid, 200 steps
         return Workload("nacl512000_L252_N256", 80, 252.0, 256, steps=200, seed=4000)
     raise KeyError(name)

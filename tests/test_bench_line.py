@@ -38,17 +38,24 @@ def test_reference_arm_line():
 
 @pytest.mark.gpu
 def test_cuda_arm_line():
+    """The default line: the 512000-ion 256^3 box in FP64 (multigrid), the
+    same box in mixed precision beside it."""
     steps = 8
-    d = _run("--steps", str(steps), "--warmup", "3")
+    d = _run("--steps", str(steps), "--warmup", "3", timeout=1200)
     _common(d, steps)
-    assert "impl" not in d
-    r = d["roofline"]
-    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] > 0 and r["achieved"] > 0
-    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
-    assert r["traffic"] is None or r["traffic"] > 0
+    assert "impl" not in d and d["dtype"] == "f64" and d["config"]["grid"] == 256
+    for r in (d["roofline"], d["roofline_other"]):
+        assert r["bound"] in ("hbm", "alu") and r["peak"] > 0 and r["achieved"] > 0
+        assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+        assert r["traffic"] is None or r["traffic"] > 0
+    assert {d["roofline"]["bound"], d["roofline_other"]["bound"]} == {"hbm", "alu"}
     e = d["e2e"]
-    assert e["h2d_bytes_per_step"] == 48000 and e["d2h_bytes_per_step"] > 48000
-    assert d["gpu_launches"] == 4 * steps          # front, pairs, solve, gather/finish per step
+    assert e["h2d_bytes_per_step"] == 48 * 512000 and e["d2h_bytes_per_step"] > 48 * 512000
+    assert d["gpu_launches"] == 7 * steps          # move, spread, 3 cell-list kernels, solve, forces
     assert d["clocks"]["sm_mhz"] > 0 and isinstance(d["clocks"]["reasons"], list)
-    assert d["force_error"] < 1e-5                 # the mixed-precision bar
+    assert d["force_error"] < 1e-7                 # FP64 at tol 1e-10 (the solver tolerance dominates)
     assert d["ms_per_step"] > 0 and d["p99_us"] >= d["p50_us"] > 0
+    m = d["mixed"]
+    assert m["steps_per_s"] > d["value"] and m["force_error"] < 1e-5
+    assert m["roofline"]["bound"] == "hbm" and m["gpu_launches"] == 7 * steps
+    assert d["cpu_baseline_all_cores"]["cores"] >= 1

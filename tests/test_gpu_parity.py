@@ -216,6 +216,22 @@ def test_not_converged_is_reported_and_stops():
     sim.close()
 
 
+@pytest.mark.parametrize("solver,precision", [("cg", M.MAZE_FP64), ("mg", M.MAZE_FP64), ("mg", M.MAZE_MIXED)])
+def test_nonfinite_warm_start_is_reported(solver, precision):
+    """A NaN in the warm start y makes the residual non-finite: the solve must
+    report MAZE_ERR_NONFINITE, not a converged result (an fmax-based norm
+    would drop the NaN and report a small residual)."""
+    sim, p, tf, _ = make("nacl1000", tol=1e-10, solver=solver, precision=precision)
+    y = sim.get(M.MAZE_Y)
+    y.ravel()[12345] = np.nan
+    sim.set(M.MAZE_Y, y)
+    sim.spread()
+    st, it, res = M.maze_solve(sim.h)
+    assert st == M.MAZE_ERR_NONFINITE, (st, it, res)
+    assert not np.isfinite(res)
+    sim.close()
+
+
 def test_zero_steps_is_noop():
     sim, p, tf, _ = make("nacl64")
     x = sim.get(M.MAZE_POS)

@@ -60,3 +60,63 @@ def test_noalloc_rejects_grids_above_its_limit():
     st, _, _ = M.maze_solve_shake_noalloc(80, d.data_ptr(), d.data_ptr(), 1e-10, 10)
     assert st == M.MAZE_ERR_INVALID
     assert "grid_N <= 64" in M.maze_last_error()
+
+
+def test_noalloc_at_its_size_limit_matches_maze_solve():
+    """grid_N = 64 fills the fixed scratch exactly (the 13824-ion box)."""
+    import torch
+    w = synth.replica(13824, 5001)
+    pos, vel, types = synth.make_state(w)
+    sim = M.MazeSim(pos, vel, types, w.L, w.N, synth.tosi_fumi_nacl(), r_cut=w.rc, dt=w.dt, tol=TOL)
+    sim.step(1)
+    sigma, y0, y_ref, it_ref = _reference_solve(sim)
+    d_sigma = torch.from_numpy(sigma.ravel().copy()).cuda()
+    d_y = torch.from_numpy(y0.ravel().copy()).cuda()
+    torch.cuda.synchronize()
+    st, it, res = M.maze_solve_shake_noalloc(64, d_sigma.data_ptr(), d_y.data_ptr(), TOL, 10000,
+                                             torch.cuda.current_stream().cuda_stream)
+    assert st == M.MAZE_OK, M.maze_last_error()
+    assert res < TOL and abs(it - it_ref) <= 2
+    y = d_y.cpu().numpy().reshape(y_ref.shape)
+    assert np.abs(y - y_ref).max() < 1e-9 * max(1.0, np.abs(y_ref).max())
+    sim.close()
+
+
+def test_noalloc_reports_not_converged_and_nonfinite():
+    import torch
+    sim, w = _context()
+    sim.step(2)
+    sigma, y0, _, _ = _reference_solve(sim)
+    sim.close()
+    stream = torch.cuda.current_stream().cuda_stream
+    d_sigma = torch.from_numpy(sigma.ravel().copy()).cuda()
+    # one CG iteration cannot reach 1e-12 from the previous step's y
+    d_y = torch.from_numpy(y0.ravel().copy()).cuda()
+    st, it, res = M.maze_solve_shake_noalloc(w.N, d_sigma.data_ptr(), d_y.data_ptr(), TOL, 1, stream)
+    assert st == M.MAZE_ERR_NOT_CONVERGED
+    assert it == 1 and np.isfinite(res) and res >= TOL
+    assert torch.isfinite(d_y).all()
+    # a NaN in sigma_p, then an infinity in the warm start
+    bad = sigma.ravel().copy()
+    bad[777] = np.nan
+    d_bad = torch.from_numpy(bad).cuda()
+    d_y = torch.from_numpy(y0.ravel().copy()).cuda()
+    st, _, res = M.maze_solve_shake_noalloc(w.N, d_bad.data_ptr(), d_y.data_ptr(), TOL, 100, stream)
+    assert st == M.MAZE_ERR_NONFINITE and not np.isfinite(res)
+    y_inf = y0.ravel().copy()
+    y_inf[5] = np.inf
+    d_y = torch.from_numpy(y_inf).cuda()
+    st, _, _ = M.maze_solve_shake_noalloc(w.N, d_sigma.data_ptr(), d_y.data_ptr(), TOL, 100, stream)
+    assert st == M.MAZE_ERR_NONFINITE
+    # and a good call afterwards still converges (no state left behind)
+    d_y = torch.from_numpy(y0.ravel().copy()).cuda()
+    st, _, res = M.maze_solve_shake_noalloc(w.N, d_sigma.data_ptr(), d_y.data_ptr(), TOL, 10000, stream)
+    assert st == M.MAZE_OK and res < TOL
+
+
+def test_noalloc_rejects_aliased_buffers():
+    import torch
+    d = torch.zeros(32 ** 3, dtype=torch.float64, device="cuda")
+    st, _, _ = M.maze_solve_shake_noalloc(32, d.data_ptr(), d.data_ptr(), 1e-10, 10)
+    assert st == M.MAZE_ERR_INVALID
+    assert "distinct" in M.maze_last_error()
