@@ -844,7 +844,9 @@ def bench_serve(args):
                                "boxes of 64-13824 ions (grids 16^3-64^3), 50-2000 steps each, mixed precision, "
                                "admission by device memory (16 GiB arena, 512 slots), continuous batching",
                    "requests": args.requests, "rate_per_s": SERVE_RATE, "cluster_ctas": info["cluster_ctas"]},
-        "p50_step_ms": out["p50_step_ms"], "p99_step_ms": out["p99_step_ms"], "served": out["served"],
+        "p50_step_ms": out["p50_step_ms"], "p99_step_ms": out["p99_step_ms"],
+        "with_arrivals": out["with_arrivals"], "without_arrivals": out["without_arrivals"],
+        "served": out["served"],
         "wall_s": out["wall_s"], "ion_steps_per_s": out["ion_steps"] / out["wall_s"],
         "roofline": None, "cpu_baseline": None,
         "e2e": {"value": out["steps_per_s"], "unit": "box-steps/s",

@@ -389,6 +389,24 @@ void maze_batch_destroy(maze_batch* b);
 /* Library version string, e.g. "maze-gb300 0.1". */
 const char* maze_version(void);
 
+/* Diagnostic: drive one of the library's bounded device-side waits to its
+ * limit and report what the kernel recorded. The paper has no counterpart;
+ * the solves and the batch step synchronise their blocks with three waits
+ * (the cooperative grid barrier, the grid reduction of doubles and the one of
+ * 64-bit integers), each of which gives up after a fixed number of polls
+ * (about a second), records MAZE_ERR_TIMEOUT and returns, so that a block
+ * that never arrives cannot hang the GPU. This call launches a small
+ * cooperative kernel whose wait can never complete - which = 0: a grid
+ * barrier waiting for one more round of arrivals than the grid makes; 1: a
+ * grid reduction of doubles in which one block publishes under another
+ * round number; 2: the same for the 64-bit integer reduction - and returns
+ * the status the kernel recorded in *status_out (MAZE_ERR_TIMEOUT when the
+ * wait gave up as designed). The call allocates and frees its own small
+ * device buffers and synchronises cuda_stream (NULL = legacy default
+ * stream). Returns MAZE_ERR_INVALID for another `which`, MAZE_ERR_CUDA when
+ * the launch or a copy fails, else MAZE_OK. */
+maze_status maze_wait_probe(int32_t which, void* cuda_stream, int32_t* status_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -783,6 +783,9 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
     size_t tot = 0;
     for (int N = c->N;; N /= 2) {
       g.Nl[g.L] = N;
+      g.lg[g.L] = -1;
+      for (int b = 1; b < 16; ++b)
+        if ((1 << b) == N) g.lg[g.L] = b;
       g.off[g.L] = tot;
       tot += (size_t)N * N * N;
       ++g.L;
@@ -797,7 +800,12 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
     }
     const int Nc = g.Nl[g.L - 1];
     gk = coarse_kernel(Nc);
-    if (!mixed) AL(c->mg_g, gk.size());
+    if (!mixed) {
+      // the FP64 V-cycle keeps its right-hand sides as -b/6: fold the -6
+      // into the coarsest solve's kernel
+      for (double& v : gk) v *= -6.0;
+      AL(c->mg_g, gk.size());
+    }
     g.x = c->mg_x;
     g.b = c->mg_b;
     g.r = c->mg_r;

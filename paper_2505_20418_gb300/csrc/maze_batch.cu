@@ -419,6 +419,11 @@ struct maze_batch {
   cudaGraphExec_t graph = nullptr;
   int graph_cluster = 0;
   cudaEvent_t ev[2] = {nullptr, nullptr};
+  // admission: a newcomer's set-up and step 0 run on their own stream, so
+  // the steps already queued on the batch stream go on meanwhile; the batch
+  // stream waits for the admission's work before its next step
+  cudaStream_t admit = nullptr;
+  cudaEvent_t admit_ev = nullptr;
 };
 
 namespace {
@@ -576,8 +581,11 @@ void destroy(maze_batch* b) {
   for (maze_ctx* c : b->box)
     if (c) free_ctx(c);
   if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->admit) cudaStreamSynchronize(b->admit);
   for (auto& e : b->ev)
     if (e) cudaEventDestroy(e);
+  if (b->admit_ev) cudaEventDestroy(b->admit_ev);
+  if (b->admit) cudaStreamDestroy(b->admit);
   cudaFree(b->d_desc);
   cudaFree(b->d_ik);
   cudaFree(b->d_order);
@@ -654,6 +662,8 @@ maze_status maze_batch_create(const maze_batch_config* cfg, maze_batch** out) {
   BK(cudaMemsetAsync(b->d_stats, 0, sizeof(maze_stats) * (size_t)S, b->stream));
   BK(cudaEventCreate(&b->ev[0]));
   BK(cudaEventCreate(&b->ev[1]));
+  BK(cudaStreamCreateWithFlags(&b->admit, cudaStreamNonBlocking));
+  BK(cudaEventCreateWithFlags(&b->admit_ev, cudaEventDisableTiming));
   BK(cudaStreamSynchronize(b->stream));
 #undef BK
   maze_status s = set_cluster(b, cta);
@@ -692,9 +702,11 @@ maze_status maze_batch_add(maze_batch* b, const maze_config* cfg, int32_t* id) {
       break;
     }
   if (slot < 0) return fail(MAZE_ERR_OOM, "every simulation slot of the batch is in use");
-  CK(cudaStreamSynchronize(b->stream));
+  // the newcomer runs its set-up and step 0 on the admission stream: steps
+  // already queued on the batch stream do not wait for it (a free slot is in
+  // no queued step's work list, and the arena's bookkeeping is on the host)
   maze_config c2 = *cfg;
-  c2.cuda_stream = b->stream;
+  c2.cuda_stream = b->admit;
   maze_ctx* c = nullptr;
   maze_status s = ctx_create(&c2, b->arena, &c);
   if (s != MAZE_OK) return s;
@@ -707,9 +719,12 @@ maze_status maze_batch_add(maze_batch* b, const maze_config* cfg, int32_t* id) {
   for (int g = 0; g < 3; ++g) d.phi[g] = reinterpret_cast<float2*>(c->phi[g]);
   const int per_cell = c->ncell > 0 ? (c->n + c->ncell - 1) / c->ncell : 0;
   d.split = std::max(1, (per_cell + kBatchWarps - 1) / kBatchWarps);
-  cudaError_t e = cudaMemcpyAsync(b->d_desc + slot, &d, sizeof d, cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_ik + slot, &c->ik, sizeof(int), cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  cudaError_t e = cudaMemcpyAsync(b->d_desc + slot, &d, sizeof d, cudaMemcpyHostToDevice, b->admit);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_ik + slot, &c->ik, sizeof(int), cudaMemcpyHostToDevice, b->admit);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->admit);
+  // later batch steps (which will include the box) start after its set-up
+  if (e == cudaSuccess) e = cudaEventRecord(b->admit_ev, b->admit);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->admit_ev, 0);
   if (e != cudaSuccess) {
     free_ctx(c);
     return fail(MAZE_ERR_CUDA, std::string("upload of the box descriptor: ") + cudaGetErrorString(e));

@@ -179,11 +179,12 @@ constexpr int kMaxLevels = 10;
 struct MgArgs {
   int L;
   int Nl[kMaxLevels];
+  int lg[kMaxLevels];      // log2(N_l) for powers of two, else -1
   size_t off[kMaxLevels];  // offsets of each level in x, b, r (level 0 at 0)
   double* x;               // corrections on levels >= 1 (level 0 uses y)
-  double* b;               // right-hand sides on levels >= 1 (level 0 uses sigma_p)
-  double* r;               // residuals, all levels
-  const double* gker;      // [Nc^3] pseudo-inverse kernel of the coarsest M
+  double* b;               // right-hand sides, stored as -b/6, all levels (level 0: -sigma_p/6)
+  double* r;               // residuals (at red points), all levels
+  const double* gker;      // [Nc^3] -6 times the pseudo-inverse kernel of the coarsest M
   int nu1, nu2;
 };
 

@@ -1,5 +1,5 @@
 // S4-S6 of the MaZe step with the multigrid constraint solver (Sec. III.A), in
-// one cooperative persistent kernel:
+// FP64, in one cooperative persistent kernel:
 //   S4  phi_p = 2 phi^k - phi^{k-1},  sigma_p = (h/4pi) M phi_p + q   (Eq. SHAKE)
 //   S5  V-cycles on M y = sigma_p from the previous y until
 //       max_n |(M y - sigma_p)_n| < tol, the residual checked after every
@@ -14,12 +14,26 @@
 // The coarsest grid (at most 8^3 points) is solved exactly: the paper runs CG
 // to convergence there; here the exact zero-mean solution is one product with
 // the pseudo-inverse of the circulant coarsest M, a periodic convolution
-// kernel g computed once on the host from M's eigenvalues.
+// kernel computed once on the host from M's eigenvalues.
 //
-// Two exact shortcuts of the same arithmetic: the first red half-sweep on a
-// coarse level starts from the zero guess, so it needs no neighbour reads;
-// the prolongation updates black points only, because the red half-sweep that
-// follows overwrites every red point without reading its old value.
+// On GB300 the FP64 pipe issues 2 operations per clock per SM (1/64 of the
+// FP32 rate), so on large grids this kernel is bound by FP64 arithmetic, not
+// by HBM. It spends as few FP64 operations per point as the method allows,
+// each an exact restatement of the same arithmetic:
+//  * every level stores its right-hand side pre-scaled, bs = -b/6, so a
+//    Gauss-Seidel update is the six-neighbour sum and one FMA,
+//    x = s/6 + bs, and a residual is 6 (x - bs) - s;
+//  * after a black half-sweep the residual at black points is zero (each was
+//    just set to make it zero), so the residual that feeds the restriction,
+//    and the convergence test after a V-cycle, are formed at red points
+//    only, and the 27-point full weighting reads only its 13 red points;
+//  * on a coarse level the first red half-sweep from the zero guess is
+//    x = bs: the restriction writes it together with the right-hand side;
+//  * the prolongation updates black points only (the next red half-sweep
+//    overwrites every red point without reading it);
+//  * maxima are integer maxima of IEEE bit patterns (no FP64 compare), and
+//    the mean of y is formed once, after the last V-cycle.
+// The grid is one 1024-thread block per SM, so every SM carries the same work.
 #include <math.h>
 
 #include "maze_internal.cuh"
@@ -28,21 +42,30 @@ namespace maze {
 
 namespace {
 
-// point of colour c (0 red, 1 black) with half-index h on an N^3 grid (N even)
-__device__ __forceinline__ int colour_point(int h, int N, int c, int& i, int& j, int& k) {
-  const int half = N >> 1;
-  const int row = h / half;
-  const int t = h - row * half;
-  k = row / N;
-  j = row - k * N;
+constexpr int kMgThreads = 1024;
+
+// Point of colour c (0 red, 1 black) with half-index h on an N^3 grid (N even):
+// h = t + (N/2)(j + N k), i = 2t + ((j + k + c) & 1). lg = log2 N for powers
+// of two (shift decode), else -1.
+__device__ __forceinline__ void colour_point(int h, int N, int lg, int c, int& i, int& j, int& k) {
+  int row, t;
+  if (lg > 0) {
+    row = h >> (lg - 1);
+    t = h & ((N >> 1) - 1);
+    k = row >> lg;
+    j = row & (N - 1);
+  } else {
+    const int half = N >> 1;
+    row = h / half;
+    t = h - row * half;
+    k = row / N;
+    j = row - k * N;
+  }
   i = 2 * t + ((j + k + c) & 1);
-  return i + N * (j + N * k);
 }
 
-__device__ __forceinline__ int wrapi(int a, int N) { return a < 0 ? a + N : (a >= N ? a - N : a); }
-
-template <typename T>
-__device__ __forceinline__ T nbr_sum(const T* x, int i, int j, int k, int N) {
+// Sum of the six periodic neighbours of (i, j, k), in a fixed order.
+__device__ __forceinline__ double nbr6(const double* __restrict__ x, int i, int j, int k, int N) {
   const int NN = N * N;
   const int n = i + N * j + NN * k;
   const int xm = i == 0 ? n + N - 1 : n - 1, xp = i == N - 1 ? n - N + 1 : n + 1;
@@ -51,20 +74,36 @@ __device__ __forceinline__ T nbr_sum(const T* x, int i, int j, int k, int N) {
   return (x[xm] + x[xp]) + (x[ym] + x[yp]) + (x[zm] + x[zp]);
 }
 
+__device__ __forceinline__ int wrapi(int a, int N) { return a < 0 ? a + N : (a >= N ? a - N : a); }
+
+// One red-black half-sweep of colour c on level (N, lg): x = s/6 + bs.
+__device__ __forceinline__ void half_sweep(double* x, const double* __restrict__ bs, int N, int lg, int c, int tid,
+                                           int stride) {
+  const int hcount = N * N * (N >> 1);
+#pragma unroll 2
+  for (int h = tid; h < hcount; h += stride) {
+    int i, j, k;
+    colour_point(h, N, lg, c, i, j, k);
+    const int m = i + N * (j + N * k);
+    x[m] = fma(nbr6(x, i, j, k, N), 1.0 / 6.0, bs[m]);
+  }
+}
+
 }  // namespace
 
-__global__ void __launch_bounds__(kSolveThreads) k_mg_solve(SolveArgs a, MgArgs g) {
+__global__ void __launch_bounds__(kMgThreads, 1) k_mg_solve(SolveArgs a, MgArgs g) {
   unsigned epoch = 0, bar_epoch = 0;
   const int n = a.n, N0 = a.N;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
   if (*a.gate != 0 || a.rec->status != MAZE_OK) return;
-  const bool m2[2] = {true, false};   // (max |r|, sum y)
-  double tot[2];
+  const bool mmax[1] = {true};
+  const bool msum[1] = {false};
+  double* sig6 = g.b;   // level 0 slot of the right-hand sides: -sigma_p / 6
 
-  // ---- S4 and the initial residual of the warm start
+  // ---- S4 and the residual of the warm start (every point)
+  double res;
   {
-    double ys = 0;
     unsigned long long rmax = 0;
     for (int m = tid; m < n; m += stride) {
       const Nbr b = neighbours(m, N0);
@@ -78,73 +117,81 @@ __global__ void __launch_bounds__(kSolveThreads) k_mg_solve(SolveArgs a, MgArgs 
         const double nk = (pk[b.xm] + pk[b.xp]) + (pk[b.ym] + pk[b.yp]) + (pk[b.zm] + pk[b.zp]);
         if (a.static_guess) {
           php = pk[m];
-          Mphp = nk - 6.0 * php;
+          Mphp = fma(-6.0, php, nk);
         } else {
-          php = 2.0 * pk[m] - pm[m];
+          php = fma(2.0, pk[m], -pm[m]);
           const double nm = (pm[b.xm] + pm[b.xp]) + (pm[b.ym] + pm[b.yp]) + (pm[b.zm] + pm[b.zp]);
-          Mphp = 2.0 * nk - nm - 6.0 * php;
+          Mphp = fma(-6.0, php, fma(2.0, nk, -nm));
         }
       }
-      const double sg = a.c_sig * Mphp + q;
+      const double sg = fma(a.c_sig, Mphp, q);
       a.phi_out[m] = php;
       a.sigma[m] = sg;
+      sig6[m] = sg * (-1.0 / 6.0);
       const double* y = a.y;
-      const double My = (y[b.xm] + y[b.xp]) + (y[b.ym] + y[b.yp]) + (y[b.zm] + y[b.zp]) - 6.0 * y[m];
+      const double My = fma(-6.0, y[m], (y[b.xm] + y[b.xp]) + (y[b.ym] + y[b.yp]) + (y[b.zm] + y[b.zp]));
       rmax = max(rmax, abs_bits(sg - My));
-      ys += y[m];
     }
-    const double v[2] = {absmax_value(rmax), ys};
-    if (!grid_reduce<2>(v, m2, a.recs, ++epoch, a.rec, tot)) return;
+    const double v[1] = {absmax_value(rmax)};
+    double t[1];
+    if (!grid_reduce<1>(v, mmax, a.recs, ++epoch, a.rec, t)) return;
+    res = t[0];
   }
-  double res = tot[0], ysum = tot[1];
   int it = 0;
-  bool finite = isfinite(res) && isfinite(ysum);
 
-  while (finite && !(res < a.tol) && it < a.max_iter) {
-    // ---- down: smooth, residual, restrict
+  while (isfinite(res) && !(res < a.tol) && it < a.max_iter) {
+    // ---- down: smooth, residual at red points, restrict
     for (int l = 0; l < g.L - 1; ++l) {
-      const int N = g.Nl[l], NN = N * N, hcount = N * NN / 2;
+      const int N = g.Nl[l], lg = g.lg[l];
       double* x = l == 0 ? a.y : g.x + g.off[l];
-      const double* b = l == 0 ? a.sigma : g.b + g.off[l];
+      const double* bs = g.b + g.off[l];
       for (int s = 0; s < g.nu1; ++s) {
-        for (int c = 0; c < 2; ++c) {
-          const bool from_zero = (l > 0 && s == 0 && c == 0);
-          for (int h = tid; h < hcount; h += stride) {
-            int i, j, k;
-            const int m = colour_point(h, N, c, i, j, k);
-            x[m] = from_zero ? -b[m] * (1.0 / 6.0) : (nbr_sum(x, i, j, k, N) - b[m]) * (1.0 / 6.0);
-          }
+        // on a coarse level the first red half-sweep (x = bs from the zero
+        // guess) was written by the restriction
+        if (!(l > 0 && s == 0)) {
+          half_sweep(x, bs, N, lg, 0, tid, stride);
           if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
         }
+        half_sweep(x, bs, N, lg, 1, tid, stride);
+        if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
       }
       double* r = g.r + g.off[l];
-      for (int m = tid; m < N * NN; m += stride) {
-        const int k = m / NN, j = (m - k * NN) / N, i = m - k * NN - j * N;
-        r[m] = b[m] - (nbr_sum(x, i, j, k, N) - 6.0 * x[m]);
+      {
+        const int hcount = N * N * (N >> 1);
+        for (int h = tid; h < hcount; h += stride) {
+          int i, j, k;
+          colour_point(h, N, lg, 0, i, j, k);
+          const int m = i + N * (j + N * k);
+          r[m] = fma(6.0, x[m] - bs[m], -nbr6(x, i, j, k, N));
+        }
       }
       if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
+      // full weighting from the 13 red points of the 3^3 neighbourhood of
+      // fine point (2I, 2J, 2K): the centre (weight 1/8) and the 12 points
+      // two of whose offsets are +-1 (weight 1/32); b_c = 4 FW(r) is stored
+      // as -b_c/6, and a red coarse point gets its first half-sweep x = bs
       const int Nc = g.Nl[l + 1], NNc = Nc * Nc;
+      const bool coarsest = (l + 1 == g.L - 1);
       double* bc = g.b + g.off[l + 1];
-      for (int m = tid; m < Nc * NNc; m += stride) {
-        const int K = m / NNc, J = (m - K * NNc) / Nc, I = m - K * NNc - J * Nc;
-        double acc = 0.0;
-#pragma unroll
-        for (int dz = -1; dz <= 1; ++dz) {
-          const int z = wrapi(2 * K + dz, N);
-          const double wz = dz == 0 ? 0.5 : 0.25;
-#pragma unroll
-          for (int dy = -1; dy <= 1; ++dy) {
-            const int yy = wrapi(2 * J + dy, N);
-            const double wzy = wz * (dy == 0 ? 0.5 : 0.25);
-            const double* row = r + (size_t)z * NN + (size_t)yy * N;
-            acc += wzy * (0.25 * row[wrapi(2 * I - 1, N)] + 0.5 * row[2 * I] + 0.25 * row[wrapi(2 * I + 1, N)]);
-          }
-        }
-        bc[m] = 4.0 * acc;
+      double* xc = g.x + g.off[l + 1];
+      const int NN = N * N;
+      for (int mc = tid; mc < Nc * NNc; mc += stride) {
+        const int K = mc / NNc, J = (mc - K * NNc) / Nc, I = mc - K * NNc - J * Nc;
+        const int i0 = 2 * I, j0 = 2 * J, k0 = 2 * K;
+        const int im = wrapi(i0 - 1, N), ip = i0 + 1;   // i0 + 1 <= N - 1
+        const int jm = wrapi(j0 - 1, N) * N, jp = (j0 + 1) * N, jc = j0 * N;
+        const int km = wrapi(k0 - 1, N) * NN, kp = (k0 + 1) * NN, kc = k0 * NN;
+        const double s12 = ((r[kc + jm + im] + r[kc + jm + ip]) + (r[kc + jp + im] + r[kc + jp + ip])) +
+                           ((r[km + jc + im] + r[km + jc + ip]) + (r[kp + jc + im] + r[kp + jc + ip])) +
+                           ((r[km + jm + i0] + r[km + jp + i0]) + (r[kp + jm + i0] + r[kp + jp + i0]));
+        const double v = fma(s12, -1.0 / 48.0, r[kc + jc + i0] * (-1.0 / 12.0));
+        bc[mc] = v;
+        if (!coarsest && ((I + J + K) & 1) == 0) xc[mc] = v;
       }
       if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
     }
-    // ---- coarsest: x = g * b (exact zero-mean solve), one warp per point
+    // ---- coarsest: x = G' * bs (exact zero-mean solve; G' = -6 times the
+    // pseudo-inverse kernel, folded on the host), one warp per point
     {
       const int Nc = g.Nl[g.L - 1], NNc = Nc * Nc, nc3 = Nc * NNc;
       const double* bc = g.b + g.off[g.L - 1];
@@ -158,7 +205,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_mg_solve(SolveArgs a, MgArgs 
         for (int q = lane; q < nc3; q += 32, ++u) {
           const int qk = q / NNc, qj = (q - qk * NNc) / Nc, qi = q - qk * NNc - qj * Nc;
           const int d = wrapi(pi - qi, Nc) + Nc * (wrapi(pj - qj, Nc) + Nc * wrapi(pk - qk, Nc));
-          acc[u & 3] += g.gker[d] * bc[q];
+          acc[u & 3] = fma(g.gker[d], bc[q], acc[u & 3]);
         }
         long long S;
         int E;
@@ -169,62 +216,79 @@ __global__ void __launch_bounds__(kSolveThreads) k_mg_solve(SolveArgs a, MgArgs 
     }
     // ---- up: prolong (black points), smooth
     for (int l = g.L - 2; l >= 0; --l) {
-      const int N = g.Nl[l], NN = N * N, hcount = N * NN / 2;
+      const int N = g.Nl[l], lg = g.lg[l], hcount = N * N * (N >> 1);
       const int Nc = g.Nl[l + 1], NNc = Nc * Nc;
       double* x = l == 0 ? a.y : g.x + g.off[l];
-      const double* b = l == 0 ? a.sigma : g.b + g.off[l];
+      const double* bs = g.b + g.off[l];
       const double* xc = g.x + g.off[l + 1];
       for (int h = tid; h < hcount; h += stride) {
         int i, j, k;
-        const int m = colour_point(h, N, 1, i, j, k);
+        colour_point(h, N, lg, 1, i, j, k);
         // trilinear: per axis the coarse index i/2 (even i) or the mean of
-        // (i-1)/2 and (i+1)/2 (odd i), periodic
-        const int i0 = i >> 1, i1 = (i & 1) ? wrapi(i0 + 1, Nc) : i0;
-        const int j0 = j >> 1, j1 = (j & 1) ? wrapi(j0 + 1, Nc) : j0;
-        const int k0 = k >> 1, k1 = (k & 1) ? wrapi(k0 + 1, Nc) : k0;
-        const double* c0 = xc + (size_t)k0 * NNc;
-        const double* c1 = xc + (size_t)k1 * NNc;
-        const double e = 0.125 * (((c0[j0 * Nc + i0] + c0[j0 * Nc + i1]) + (c0[j1 * Nc + i0] + c0[j1 * Nc + i1])) +
-                                  ((c1[j0 * Nc + i0] + c1[j0 * Nc + i1]) + (c1[j1 * Nc + i0] + c1[j1 * Nc + i1])));
+        // (i-1)/2 and (i+1)/2 (odd i), periodic; a black point has one odd
+        // coordinate (mean of 2 coarse values) or three (mean of 8)
+        const int m = i + N * (j + N * k);
+        const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
+        const int odd = (i & 1) + (j & 1) + (k & 1);
+        double e;
+        if (odd == 1) {
+          const int c0 = i0 + Nc * (j0 + Nc * k0);
+          const int c1 = (i & 1) ? wrapi(i0 + 1, Nc) + Nc * (j0 + Nc * k0)
+                       : (j & 1) ? i0 + Nc * (wrapi(j0 + 1, Nc) + Nc * k0)
+                                 : i0 + Nc * (j0 + Nc * wrapi(k0 + 1, Nc));
+          e = 0.5 * (xc[c0] + xc[c1]);
+        } else {
+          const int i1 = wrapi(i0 + 1, Nc), j1 = wrapi(j0 + 1, Nc), k1 = wrapi(k0 + 1, Nc);
+          const double* c0 = xc + (size_t)k0 * NNc;
+          const double* c1 = xc + (size_t)k1 * NNc;
+          e = 0.125 * (((c0[j0 * Nc + i0] + c0[j0 * Nc + i1]) + (c0[j1 * Nc + i0] + c0[j1 * Nc + i1])) +
+                       ((c1[j0 * Nc + i0] + c1[j0 * Nc + i1]) + (c1[j1 * Nc + i0] + c1[j1 * Nc + i1])));
+        }
         x[m] += e;
       }
       if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
       for (int s = 0; s < g.nu2; ++s) {
         for (int c = 0; c < 2; ++c) {
-          for (int h = tid; h < hcount; h += stride) {
-            int i, j, k;
-            const int m = colour_point(h, N, c, i, j, k);
-            x[m] = (nbr_sum(x, i, j, k, N) - b[m]) * (1.0 / 6.0);
-          }
+          half_sweep(x, bs, N, lg, c, tid, stride);
           if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
         }
       }
     }
     ++it;
-    // ---- residual check (Eq. res_poisson_maze) and sum y
+    // ---- convergence test (Eq. res_poisson_maze) at red points: the black
+    // residual after the last black half-sweep is zero
     {
-      double ys = 0;
       unsigned long long rmax = 0;
+      const int N = N0, lg = g.lg[0], hcount = N * N * (N >> 1);
       const double* y = a.y;
-      for (int m = tid; m < n; m += stride) {
-        const Nbr b = neighbours(m, N0);
-        const double My = (y[b.xm] + y[b.xp]) + (y[b.ym] + y[b.yp]) + (y[b.zm] + y[b.zp]) - 6.0 * y[m];
-        rmax = max(rmax, abs_bits(a.sigma[m] - My));
-        ys += y[m];
+#pragma unroll 2
+      for (int h = tid; h < hcount; h += stride) {
+        int i, j, k;
+        colour_point(h, N, lg, 0, i, j, k);
+        const int m = i + N * (j + N * k);
+        rmax = max(rmax, abs_bits(fma(6.0, y[m] - sig6[m], -nbr6(y, i, j, k, N))));
       }
-      const double v[2] = {absmax_value(rmax), ys};
-      if (!grid_reduce<2>(v, m2, a.recs, ++epoch, a.rec, tot)) return;
-      res = tot[0];
-      ysum = tot[1];
-      finite = isfinite(res) && isfinite(ysum);
+      const double v[1] = {absmax_value(rmax)};
+      double t[1];
+      if (!grid_reduce<1>(v, mmax, a.recs, ++epoch, a.rec, t)) return;
+      res = t[0];
     }
   }
-  // ---- S6
+  // ---- mean of y, then S6
+  double ysum;
+  {
+    double ys = 0.0;
+    for (int m = tid; m < n; m += stride) ys += a.y[m];
+    const double v[1] = {ys};
+    double t[1];
+    if (!grid_reduce<1>(v, msum, a.recs, ++epoch, a.rec, t)) return;
+    ysum = t[0];
+  }
   const double ybar = ysum * a.inv_n;
   for (int m = tid; m < n; m += stride) {
     const double yv = a.y[m] - ybar;
     a.y[m] = yv;
-    a.phi_out[m] = a.phi_out[m] - a.c_phi * yv;
+    a.phi_out[m] = fma(-a.c_phi, yv, a.phi_out[m]);
   }
   if (tid == 0) {
     maze_stats* r = a.rec;
@@ -240,9 +304,9 @@ int mg_blocks(int n_points) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mg_solve, kSolveThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mg_solve, kMgThreads, 0);
   if (per_sm < 1) per_sm = 1;
-  int want = (n_points + kSolveThreads - 1) / kSolveThreads;
+  int want = (n_points + kMgThreads - 1) / kMgThreads;
   int cap = sms * per_sm;
   if (cap > kMaxReduceBlocks) cap = kMaxReduceBlocks;
   return want < cap ? want : cap;
@@ -251,7 +315,7 @@ int mg_blocks(int n_points) {
 cudaError_t launch_mg_solve(const SolveArgs& a, const MgArgs& g, int blocks, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
-  cfg.blockDim = dim3(kSolveThreads);
+  cfg.blockDim = dim3(kMgThreads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];

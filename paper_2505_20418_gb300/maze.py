@@ -33,7 +33,7 @@ EXPORTS = ("maze_create", "maze_spread", "maze_solve", "maze_gather", "maze_step
            "maze_batch_remove", "maze_batch_info", "maze_batch_step", "maze_batch_step_async",
            "maze_batch_get", "maze_batch_set", "maze_batch_get_stats", "maze_batch_get_all_stats",
            "maze_batch_tune",
-           "maze_batch_destroy")
+           "maze_batch_destroy", "maze_wait_probe")
 
 _D = ctypes.c_double
 _I = ctypes.c_int32
@@ -122,6 +122,7 @@ def load(path: str = LIB_PATH):
     lib.maze_batch_tune.argtypes = [P, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]
     lib.maze_batch_destroy.argtypes = [P]
     lib.maze_batch_destroy.restype = None
+    lib.maze_wait_probe.argtypes = [_I, P, ctypes.POINTER(_I)]
     lib.maze_last_error.restype = ctypes.c_char_p
     lib.maze_version.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -237,6 +238,15 @@ def maze_solve_shake_noalloc(grid_N: int, sigma_ptr: int, y_ptr: int, tol: float
                                          float(tol), int(max_iter), ctypes.c_void_p(stream or 0),
                                          ctypes.byref(it), ctypes.byref(res))
     return st, it.value, res.value
+
+
+def maze_wait_probe(which: int, stream: int | None = None):
+    """Run one bounded device wait that cannot complete (0 grid barrier, 1 grid
+    reduction of doubles, 2 of 64-bit integers). Returns (call status,
+    status recorded by the kernel)."""
+    out = _I()
+    st = load().maze_wait_probe(int(which), ctypes.c_void_p(stream or 0), ctypes.byref(out))
+    return st, out.value
 
 
 def maze_destroy(h):

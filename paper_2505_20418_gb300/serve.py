@@ -88,11 +88,21 @@ class Server:
         """Serve ``requests`` (sorted by arrival). With ``realtime`` the loop
         admits a request only once the wall clock has passed its arrival time;
         otherwise arrivals are replayed as fast as the engine goes (every
-        request is eligible at once). Returns per-step latencies (seconds, one
-        sample per simulation per step) and aggregate throughput."""
+        request is eligible at once).
+
+        Each loop iteration queues the next k steps of every admitted
+        simulation, then admits arrived requests while those steps run on the
+        GPU (a newcomer's set-up and step 0 go to the batch's admission
+        stream), then waits for the steps and retires finished simulations;
+        newcomers join the next iteration's steps. Returns per-step latencies
+        (one sample per simulation per step: the loop iteration's time over
+        its k steps), split into iterations that admitted a request and
+        iterations that did not, and aggregate throughput."""
         pending = sorted(requests, key=lambda q: q.arrival)
         active: list[Request] = []
         lat: list[float] = []
+        lat_adm: list[float] = []
+        lat_quiet: list[float] = []
         chunk_lat: list[float] = []
         box_steps = 0
         ion_steps = 0
@@ -100,22 +110,28 @@ class Server:
         i = 0
         while (i < len(pending) or active) and time.perf_counter() - t0 < max_wall:
             t_iter = time.perf_counter()
-            now = t_iter - t0
-            # admission: arrived requests, in arrival order, while there is room
+            # queue k steps of every admitted simulation (no request overshoots)
+            k = min(self.chunk, min(q.steps - q.done for q in active)) if active else 0
+            if k:
+                self.batch.step_async(k)
+            # admission while those steps run: arrived requests, in arrival
+            # order, while there is room
+            now = time.perf_counter() - t0
+            joined = []
             while i < len(pending) and (not realtime or pending[i].arrival <= now):
                 q = pending[i]
                 if not self._try_admit(q):
                     break
                 q.admitted = time.perf_counter() - t0
-                active.append(q)
+                joined.append(q)
                 i += 1
-            if not active:
-                if i < len(pending) and realtime:
+            if not k:
+                active = joined
+                if not active and i < len(pending) and realtime:
                     time.sleep(max(0.0, min(pending[i].arrival - now, 0.01)))
                 continue
-            # advance every admitted simulation by k steps (no request overshoots)
-            k = min(self.chunk, min(q.steps - q.done for q in active))
-            st = self.batch.step_status(k)
+            # wait for the queued steps; statuses of everything stepped
+            st = self.batch.step_status(0)
             for q in active:
                 q.done += k
             box_steps += k * len(active)
@@ -134,19 +150,26 @@ class Server:
                 else:
                     keep.append(q)
             # latency of each step as its simulations saw it: the whole loop
-            # iteration (admission, the launches, retirement) over its k steps
+            # iteration (the launches, admission, retirement) over its k steps
             per = (time.perf_counter() - t_iter) / k
             chunk_lat.append(per)
-            for q in active:
-                lat.extend([per] * k)
-            active = keep
+            samples = [per] * (k * len(active))
+            lat.extend(samples)
+            (lat_adm if joined else lat_quiet).extend(samples)
+            active = keep + joined
         wall = time.perf_counter() - t0
-        lat_a = np.asarray(lat) if lat else np.zeros(1)
+
+        def pct(v, p):
+            return 1e3 * float(np.percentile(np.asarray(v), p)) if v else None
+
         return {
             "requests": len(requests), "served": sum(q.finished is not None for q in requests),
             "wall_s": wall, "box_steps": box_steps, "ion_steps": ion_steps,
             "steps_per_s": box_steps / wall if wall > 0 else 0.0,
-            "p50_step_ms": 1e3 * float(np.percentile(lat_a, 50)),
-            "p99_step_ms": 1e3 * float(np.percentile(lat_a, 99)),
+            "p50_step_ms": pct(lat, 50) or 0.0, "p99_step_ms": pct(lat, 99) or 0.0,
+            "with_arrivals": {"p50_step_ms": pct(lat_adm, 50), "p99_step_ms": pct(lat_adm, 99),
+                              "steps": len(lat_adm)},
+            "without_arrivals": {"p50_step_ms": pct(lat_quiet, 50), "p99_step_ms": pct(lat_quiet, 99),
+                                 "steps": len(lat_quiet)},
             "launches": len(chunk_lat),
         }

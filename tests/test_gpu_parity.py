@@ -278,3 +278,22 @@ def test_mg_iterations_match_the_oracle_on_a_trajectory():
         st = O.step(st, p, tf)
         sim.step(1)
         assert abs(sim.stats()["iters"] - st.iters) <= 1
+
+
+@pytest.mark.parametrize("which", [0, 1, 2])
+def test_bounded_wait_gives_up_with_timeout(which):
+    """Failure detection without a GPU fault: a grid barrier or grid reduction
+    waiting for a round no block completes gives up after its poll limit
+    (about a second), records MAZE_ERR_TIMEOUT and returns; the GPU stays
+    usable (a context built and stepped afterwards converges)."""
+    import time
+    t0 = time.perf_counter()
+    st, rec = M.maze_wait_probe(which)
+    dt = time.perf_counter() - t0
+    assert st == M.MAZE_OK, M.maze_last_error()
+    assert rec == M.MAZE_ERR_TIMEOUT
+    assert dt < 30.0
+    sim, p, tf, _ = make("nacl64", tol=1e-10)
+    sim.step(2)
+    assert sim.stats()["status"] == M.MAZE_OK
+    sim.close()

@@ -27,10 +27,14 @@ class FakeBatch:
         self.log.append(("add", i))
         return i
 
-    def step_status(self, k):
+    def step_async(self, k):
+        self.queued = dict(self.sims)     # the simulations these steps include
         for s in self.sims.values():
             s["steps"] += k
         self.log.append(("step", k, len(self.sims)))
+
+    def step_status(self, k):
+        assert k == 0                     # the server only waits for queued steps
         return M.MAZE_OK
 
     def all_stats(self):

@@ -57,7 +57,8 @@ def test_noalloc_solve_matches_maze_solve_twice():
 def test_noalloc_rejects_grids_above_its_limit():
     import torch
     d = torch.zeros(80 ** 3, dtype=torch.float64, device="cuda")
-    st, _, _ = M.maze_solve_shake_noalloc(80, d.data_ptr(), d.data_ptr(), 1e-10, 10)
+    e = torch.zeros(80 ** 3, dtype=torch.float64, device="cuda")
+    st, _, _ = M.maze_solve_shake_noalloc(80, d.data_ptr(), e.data_ptr(), 1e-10, 10)
     assert st == M.MAZE_ERR_INVALID
     assert "grid_N <= 64" in M.maze_last_error()
 
