@@ -626,6 +626,11 @@ def main():
 # Batched replicas and serving
 
 BATCH_BOXES = 128
+# FP64 tolerance at which the FP64 path's per-ion force error (~1e-6 on the
+# 1000- and 4096-ion boxes) is still at or below the mixed path's (~4e-6 at
+# any tolerance: its floor is FP32 spreading, gather and pairs); at 3e-7 it
+# is already ~1.5e-5. Equal accuracy for the FP64-vs-mixed comparison.
+FP64_EQUAL_ACCURACY_TOL = 1e-7
 
 
 def oracle_box_step_seconds(w, steps=2):
@@ -685,29 +690,38 @@ def bench_batch(args):
                for w, st in zip(ws, states))
     b = M.MazeBatch(need + (64 << 20), len(ws), cluster_ctas=args.cluster_ctas, stream=stream.cuda_stream)
     ids = [b.add(*st, w.L, w.N, tf, r_cut=w.rc, dt=w.dt, tol=w.tol, order=w.order) for w, st in zip(ws, states)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    big = need > (160 << 20)
+
+    def timed_steps(n):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        torch.cuda.synchronize()
+        for k in range(n):
+            with torch.cuda.stream(stream):
+                if not big:
+                    flush.zero_()
+                ev[k][0].record(stream)
+                b.step_async(1)
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(c) for a, c in ev]
+
+    # one cluster size for every box (the one-size tuner), then the
+    # per-size-class autotuner; the line's value is the autotuned batch
     if args.cluster_ctas == 0:
         cta, tune_ms = b.tune(3)
     else:
         cta, tune_ms = args.cluster_ctas, None
     b.step(args.warmup)
+    one_ms = timed_steps(args.steps)
+    table = b.autotune(3)
+    b.step(args.warmup)
     it0 = sum(b.stats(i)["total_iters"] for i in ids)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    big = need > (160 << 20)
     clocks = ClockSampler(0)
     clocks.start()
     time.sleep(0.3)
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            if not big:
-                flush.zero_()
-            ev[k][0].record(stream)
-            b.step_async(1)
-            ev[k][1].record(stream)
-    torch.cuda.synchronize()
+    step_ms = timed_steps(args.steps)
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(c) for a, c in ev]
     total_s = sum(step_ms) / 1e3
     st = b.step_status(0)
     stats = [b.stats(i) for i in ids]
@@ -730,15 +744,18 @@ def bench_batch(args):
         Fo = O.gather_forces(x, Q, phi_ex, w.L, w.N, w.order) + O.tf_forces(x, types, w.L, tf, w.rc)[0]
         scale = np.sqrt((np.linalg.norm(F, axis=1) ** 2).mean())
         ferr = max(ferr, float((np.linalg.norm(F - Fo, axis=1) / np.maximum(np.linalg.norm(Fo, axis=1), scale)).max()))
-    # the same boxes advanced one after another by single-box contexts:
-    # the plain FP64 path and the single-box mixed path (per size class)
-    single = {}
-    for prec in ("fp64", "mixed"):
-        per = {}
+    # the same boxes advanced one after another by single-box contexts: the
+    # plain FP64 path at the batch's tolerance, the FP64 path at the loosest
+    # tolerance whose force error stays at or below the mixed path's (equal
+    # accuracy), and the single-box mixed path (one box per size class)
+    single, single_err = {}, {}
+    for name, prec, tol in (("fp64", "fp64", None), ("fp64_equal_accuracy", "fp64", FP64_EQUAL_ACCURACY_TOL),
+                            ("mixed", "mixed", None)):
+        per, err = {}, 0.0
         for n in sorted({w.n_ions for w in ws}):
             j = next(k for k, w in enumerate(ws) if w.n_ions == n)
             w = ws[j]
-            sim = M.MazeSim(*states[j], w.L, w.N, tf, r_cut=w.rc, dt=w.dt, tol=w.tol, order=w.order,
+            sim = M.MazeSim(*states[j], w.L, w.N, tf, r_cut=w.rc, dt=w.dt, tol=tol or w.tol, order=w.order,
                             solver=M.MAZE_SOLVER_MG, precision=M.MAZE_MIXED if prec == "mixed" else M.MAZE_FP64,
                             stream=stream.cuda_stream)
             sim.step(3)
@@ -749,8 +766,10 @@ def bench_batch(args):
                 e1.record(stream)
             torch.cuda.synchronize()
             per[n] = e0.elapsed_time(e1) / 1e3 / 20
+            err = max(err, force_error_vs_oracle(M, sim, w, states[j][2], tf))
             sim.close()
-        single[prec] = mix_rate(ws, per)
+        single[name] = mix_rate(ws, per)
+        single_err[name] = err
     # end to end through the C ABI with host buffers: per step every box's
     # positions and velocities go up from pinned host memory, the step runs,
     # positions, velocities and statistics come back
@@ -783,19 +802,31 @@ def bench_batch(args):
         "metric": METRIC, "value": len(ids) * args.steps / total_s, "unit": "box-steps/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * mean_s, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f32x2", "data": "synthetic",
-        "config": batch_config(ws, {"cluster_ctas": cta, "tune_ms_per_step": tune_ms,
+        "config": batch_config(ws, {"cluster_ctas": "per size class (autotuned)", "tune_ms_per_step": tune_ms,
                                     "l2": "working set larger than L2, not flushed" if big else
                                     "flushed between timed steps (256 MiB write outside the step events)"}),
         "batch_steps_per_s": args.steps / total_s,
+        "autotune_table": table,
+        "one_size_fits_all": {"cluster_ctas": cta, "box_steps_per_s": len(ids) * len(one_ms) / (sum(one_ms) / 1e3),
+                              "ms_per_step": sum(one_ms) / len(one_ms),
+                              "how": "maze_batch_tune: one cluster size for every box, the configured V-cycle"},
         "ion_steps_per_s": sum(w.n_ions for w in ws) * args.steps / total_s,
         "p50_us": 1e3 * float(np.percentile(step_ms, 50)), "p99_us": 1e3 * float(np.percentile(step_ms, 99)),
         "iters_per_step": iters, "force_error": ferr,
-        "single_box_paths": {"fp64_box_steps_per_s": single["fp64"], "mixed_box_steps_per_s": single["mixed"],
-                             "how": "one box of each size timed alone (20 steps, CUDA events), weighted by the mix"},
+        "single_box_paths": {"fp64_box_steps_per_s": single["fp64"], "fp64_force_error": single_err["fp64"],
+                             "fp64_equal_accuracy_box_steps_per_s": single["fp64_equal_accuracy"],
+                             "fp64_equal_accuracy_tol": FP64_EQUAL_ACCURACY_TOL,
+                             "fp64_equal_accuracy_force_error": single_err["fp64_equal_accuracy"],
+                             "mixed_box_steps_per_s": single["mixed"], "mixed_force_error": single_err["mixed"],
+                             "batched_mixed_vs_fp64_equal_accuracy": len(ids) * args.steps / total_s
+                             / single["fp64_equal_accuracy"],
+                             "how": "one box of each size timed alone (20 steps, CUDA events), weighted by the mix; "
+                                    "force errors: the largest over one box of each size against the oracle's "
+                                    "exact discrete solution after the 23 steps"},
         "roofline": {"kernel": "k_batch_step", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                      "algorithmic_bytes_per_launch": bytes_launch},
-        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clk,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * (1 + len({t["cluster_ctas"] for t in table})), "clocks": clk,
     }
     print(json.dumps(line), flush=True)
 

@@ -341,8 +341,13 @@ maze_status maze_batch_box_bytes(const maze_config* cfg, size_t* bytes);
 maze_status maze_batch_free_bytes(maze_batch* b, size_t* largest_block, size_t* total_free);
 
 /* Admit one simulation: copy its state, take its buffers from the arena and
- * run its step 0 (as maze_create does) on the batch's stream, synchronously.
- * On success *id is its slot; it then advances with every maze_batch_step.
+ * queue its step 0 (as maze_create runs it) on the batch's admission stream,
+ * a stream of its own: steps already queued on the batch's stream go on
+ * meanwhile, and the call returns without waiting for step 0. On success
+ * *id is its slot; it then advances with every maze_batch_step (which first
+ * waits for pending admissions) or, once its step 0 has finished, with
+ * maze_batch_step_ready_async. A step 0 that fails shows in the
+ * simulation's statistics and stops only that simulation.
  * MAZE_ERR_OOM when no slot is free or the arena has no room (nothing is
  * changed; retry after a maze_batch_remove), MAZE_ERR_INVALID for a config
  * maze_create would reject or that the batch cannot run (see above). */
@@ -366,6 +371,20 @@ maze_status maze_batch_step(maze_batch* b, int32_t nsteps);
 /* As maze_batch_step, without waiting for the GPU or checking statuses. */
 maze_status maze_batch_step_async(maze_batch* b, int32_t nsteps);
 
+/* Continuous batching. maze_batch_refresh moves the simulations whose
+ * admission (step 0) has finished on the GPU into the work order, without
+ * waiting for the others, and lists their ids in joined[0 .. *n_joined)
+ * (joined: host array of cap >= max_sims entries). It synchronises the
+ * batch's stream. maze_batch_step_ready_async then queues nsteps steps of the
+ * simulations in the work order, without waiting for the GPU and without
+ * admitting anything new. Pair it with maze_batch_sync. */
+maze_status maze_batch_refresh(maze_batch* b, int32_t* joined, int32_t cap, int32_t* n_joined);
+maze_status maze_batch_step_ready_async(maze_batch* b, int32_t nsteps);
+
+/* Wait for the steps queued so far and return the first failing status among
+ * the simulations they advanced (named in maze_last_error), else MAZE_OK. */
+maze_status maze_batch_sync(maze_batch* b);
+
 /* maze_get / maze_set / maze_get_stats for simulation id (synchronise the
  * batch's stream first). */
 maze_status maze_batch_get(maze_batch* b, int32_t id, int32_t what, double* host_out);
@@ -382,6 +401,33 @@ maze_status maze_batch_get_all_stats(maze_batch* b, maze_stats* out, int32_t n);
  * tuning does not advance them; results do not depend on the cluster size.
  * Needs a temporary device buffer the size of the arena's used part. */
 maze_status maze_batch_tune(maze_batch* b, int32_t steps_per_trial, int32_t* chosen_ctas, double* ms_per_step);
+
+/* One row of the per-size-class autotuning table. */
+typedef struct {
+  int32_t grid_N;               /* the class: boxes of this grid edge */
+  int32_t boxes;                /* its boxes in the batch */
+  int32_t cluster_ctas;         /* CTAs per box (the tile of the grid one box gets) */
+  int32_t mg_pre, mg_post;      /* V-cycle schedule: Gauss-Seidel sweeps before / after */
+  int32_t tail_n;               /* levels of at most tail_n^3 points in one CTA (0: the default) */
+  double ms_before;             /* batch step time (ms) before this class was tuned */
+  double ms_after;              /* ... and after */
+} maze_tune_entry;
+
+/* Autotuner per size class (the project's own; the paper has none). Starting
+ * from the batch-wide cluster size, it visits the grid sizes of the batch in
+ * order of their work and for each picks in turn the CTAs per box (1-16),
+ * the size of the V-cycle's one-CTA coarse tail (8^3 or 16^3 points) and the
+ * red-black Gauss-Seidel schedule (nu1, nu2 in {(2,2), (1,2), (2,1), (1,1),
+ * (3,3)}), each trial timing whole batch steps as they run (one launch per
+ * cluster size, the launches side by side); a change must shorten the step
+ * by 3 %, so the result is never slower than the start as measured. Cluster size and tail change no result; a schedule other than the
+ * configured one changes results within the solve tolerance (every box still
+ * meets tol; the mixed-precision path is multigrid only, so there is no CG /
+ * multigrid choice to make). State is saved before and restored after every
+ * trial. table: host array of cap >= (grid sizes in the batch) entries;
+ * *n_entries rows are written. maze_batch_tune undoes these choices. */
+maze_status maze_batch_autotune(maze_batch* b, int32_t steps_per_trial, maze_tune_entry* table, int32_t cap,
+                                int32_t* n_entries);
 
 /* Free every simulation and the batch (NULL-safe). */
 void maze_batch_destroy(maze_batch* b);

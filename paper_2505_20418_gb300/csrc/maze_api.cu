@@ -899,7 +899,7 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
 
 // Full creation: setup, pinned stats buffer, upload, step 0 (spread, solve
 // from zero, phi^{-1} = phi^0, y = 0, forces F^0 and energies).
-maze_status ctx_create(const maze_config* cfg, Arena* arena, maze_ctx** out) {
+maze_status ctx_create(const maze_config* cfg, Arena* arena, maze_ctx** out, bool defer_status) {
   if (!out) return fail(MAZE_ERR_INVALID, "out is NULL");
   maze_ctx* c = nullptr;
   maze_status s = ctx_setup(cfg, arena, &c);
@@ -981,6 +981,7 @@ maze_status ctx_create(const maze_config* cfg, Arena* arena, maze_ctx** out) {
     CK(cudaMemcpyAsync(c->phi[1], c->phi[0], ng * 8, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemsetAsync(c->y, 0, ng * 8, st));
     CK(launch_forces(force_args(c, c->phi[0], 0, 0), c->fblocks, st));
+    if (defer_status) return MAZE_OK;
     r = read_stats(c);
     if (r != MAZE_OK) return r;
     return status_message(c);

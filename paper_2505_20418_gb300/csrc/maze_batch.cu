@@ -101,6 +101,8 @@ struct __align__(16) BoxDesc {
 };
 
 constexpr int kBatchThreads = 1024;
+// cluster sizes a box may be given (1, 2, 4, 8, 16 CTAs): at most one launch each
+constexpr int kMaxGroups = 5;
 constexpr int kBatchWarps = kBatchThreads / 32;
 // dynamic shared memory of the step kernel: the force staging, the sort's
 // buffers and (when a box fits) the cluster-resident V-cycle share it
@@ -407,23 +409,38 @@ struct maze_batch {
   BoxDesc* d_desc = nullptr;
   int* d_ik = nullptr;
   int* d_order = nullptr;
-  int* d_count = nullptr;
-  unsigned* d_queue = nullptr;
+  int* d_count = nullptr;         // [1 + kMaxGroups]: all active boxes, then each group's
+  unsigned* d_queue = nullptr;    // [kMaxGroups] work-queue counters
   maze_stats* d_stats = nullptr;
-  int* h_order = nullptr;         // pinned: order + count
+  int* h_order = nullptr;         // pinned: order, then the counts of d_count
   maze_stats* h_stats = nullptr;  // pinned
   int* h_ik = nullptr;            // pinned
   bool dirty = true;
   int cluster = 4;
   int nclusters = 0;
   cudaGraphExec_t graph = nullptr;
-  int graph_cluster = 0;
+  std::vector<int> graph_key;     // the launch layout the graph was captured for
+  // per-box launch choices of the autotuner (0: the batch-wide cluster size)
+  std::vector<int> box_cta;       // [slots]
+  // launch groups: boxes of one cluster size form one launch; groups run
+  // concurrently (a fork and join on auxiliary streams inside the graph)
+  int ngroups = 0;
+  int grp_cta[kMaxGroups] = {}, grp_clusters[kMaxGroups] = {}, grp_first[kMaxGroups] = {},
+      grp_count[kMaxGroups] = {};
+  cudaStream_t aux[kMaxGroups] = {};
+  int mc[17] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};  // clusters per size
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[kMaxGroups] = {};
   cudaEvent_t ev[2] = {nullptr, nullptr};
   // admission: a newcomer's set-up and step 0 run on their own stream, so
   // the steps already queued on the batch stream go on meanwhile; the batch
   // stream waits for the admission's work before its next step
   cudaStream_t admit = nullptr;
   cudaEvent_t admit_ev = nullptr;
+  // a newcomer is pending until its step 0 and descriptor upload have run
+  // (its event has completed); only then does it join the work order
+  std::vector<char> pending;           // [slots]
+  std::vector<cudaEvent_t> admit_evs;  // [slots], created on first use
 };
 
 namespace {
@@ -467,15 +484,37 @@ int max_clusters(int cta) {
   return n;
 }
 
-maze_status launch_step(maze_batch* b) {
+// Co-resident clusters of the step kernel for a cluster size (cached).
+int clusters_for(maze_batch* b, int cta) {
+  if (cta < 1 || cta > 16) return 0;
+  if (b->mc[cta] < 0) b->mc[cta] = max_clusters(cta);
+  return b->mc[cta];
+}
+
+// The descriptor of one box (its argument blocks for every phase).
+BoxDesc box_desc(maze_ctx* c) {
+  BoxDesc d;
+  memset(&d, 0, sizeof d);
+  d.ion = ion_args(c, 1, 1);
+  d.cell = cell_args(c);
+  d.force = force_args(c, nullptr, 1, 1);
+  d.mixed = mixed_args(c, 0, nullptr);
+  for (int g = 0; g < 3; ++g) d.phi[g] = reinterpret_cast<float2*>(c->phi[g]);
+  const int per_cell = c->ncell > 0 ? (c->n + c->ncell - 1) / c->ncell : 0;
+  d.split = std::max(1, (per_cell + kBatchWarps - 1) / kBatchWarps);
+  return d;
+}
+
+// One launch of the step kernel over group g's segment of the work order.
+maze_status launch_group(maze_batch* b, int g, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(b->nclusters * b->cluster);
+  cfg.gridDim = dim3(b->grp_clusters[g] * b->grp_cta[g]);
   cfg.blockDim = dim3(kBatchThreads);
   cfg.dynamicSmemBytes = kBatchSmem;
-  cfg.stream = b->stream;
+  cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = b->cluster;
+  attr[0].val.clusterDim.x = b->grp_cta[g];
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
@@ -483,25 +522,50 @@ maze_status launch_step(maze_batch* b) {
   BatchArgs a;
   a.desc = b->d_desc;
   a.ik = b->d_ik;
-  a.order = b->d_order;
-  a.count = b->d_count;
-  a.queue = b->d_queue;
-  CK(cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned), b->stream));
+  a.order = b->d_order + b->grp_first[g];
+  a.count = b->d_count + 1 + g;
+  a.queue = b->d_queue + g;
   CK(cudaLaunchKernelEx(&cfg, k_batch_step, a));
   return MAZE_OK;
 }
 
-maze_status set_cluster(maze_batch* b, int cta) {
-  const int n = max_clusters(cta);
-  if (n < 1) return fail(MAZE_ERR_INVALID, "the device cannot co-schedule a cluster of " + std::to_string(cta) + " CTAs");
-  b->cluster = cta;
-  b->nclusters = n;
+// One step of every box: reset the work queues, then one launch per group,
+// the groups side by side.
+maze_status launch_step(maze_batch* b) {
+  CK(cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned) * kMaxGroups, b->stream));
+  if (b->ngroups > 1) {
+    CK(cudaEventRecord(b->fork_ev, b->stream));
+    for (int g = 1; g < b->ngroups; ++g) CK(cudaStreamWaitEvent(b->aux[g], b->fork_ev, 0));
+  }
+  for (int g = 0; g < b->ngroups; ++g) {
+    maze_status s = launch_group(b, g, g == 0 ? b->stream : b->aux[g]);
+    if (s != MAZE_OK) return s;
+  }
+  for (int g = 1; g < b->ngroups; ++g) {
+    CK(cudaEventRecord(b->join_ev[g], b->aux[g]));
+    CK(cudaStreamWaitEvent(b->stream, b->join_ev[g], 0));
+  }
   return MAZE_OK;
 }
 
-// One graph per step: reset the work queue, launch the persistent kernel.
+maze_status set_cluster(maze_batch* b, int cta) {
+  const int n = clusters_for(b, cta);
+  if (n < 1) return fail(MAZE_ERR_INVALID, "the device cannot co-schedule a cluster of " + std::to_string(cta) + " CTAs");
+  b->cluster = cta;
+  b->nclusters = n;
+  b->dirty = true;
+  return MAZE_OK;
+}
+
+// One graph per step: reset the work queues, launch every group.
 maze_status build_graph(maze_batch* b) {
-  if (b->graph && b->graph_cluster == b->cluster) return MAZE_OK;
+  std::vector<int> key;
+  for (int g = 0; g < b->ngroups; ++g) {
+    key.push_back(b->grp_cta[g]);
+    key.push_back(b->grp_clusters[g]);
+    key.push_back(b->grp_first[g]);
+  }
+  if (b->graph && b->graph_key == key) return MAZE_OK;
   if (b->graph) {
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
@@ -518,25 +582,91 @@ maze_status build_graph(maze_batch* b) {
   e = cudaGraphInstantiate(&b->graph, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return fail(MAZE_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-  b->graph_cluster = b->cluster;
+  b->graph_key = key;
   return MAZE_OK;
 }
 
-// Upload the scheduling order (longest-processing-time first) after a
-// change of membership.
-maze_status upload_order(maze_batch* b) {
+// The cluster size box s runs with.
+int box_ctas(const maze_batch* b, int s) { return b->box_cta[s] > 0 ? b->box_cta[s] : b->cluster; }
+
+// Lay out launch groups for the boxes in ``list``: one group per cluster
+// size (ascending), boxes of a group in longest-processing-time-first order;
+// with one group the launch takes every co-resident cluster, with several
+// each takes a share of them proportional to its work (at least one cluster).
+maze_status layout_groups(maze_batch* b, std::vector<int> list) {
+  std::stable_sort(list.begin(), list.end(), [&](int x, int y) {
+    const int cx = box_ctas(b, x), cy = box_ctas(b, y);
+    if (cx != cy) return cx < cy;
+    return b->cost[x] > b->cost[y];
+  });
+  b->ngroups = 0;
+  double total = 0.0;
+  for (int s : list) total += b->cost[s];
+  const int n = (int)list.size();
+  for (int k = 0; k < n;) {
+    const int cta = box_ctas(b, list[k]);
+    int e = k;
+    double work = 0.0;
+    while (e < n && box_ctas(b, list[e]) == cta) work += b->cost[list[e++]];
+    const int g = b->ngroups++;
+    const int mc = clusters_for(b, cta);
+    if (mc < 1) return fail(MAZE_ERR_INVALID, "the device cannot co-schedule a cluster of " + std::to_string(cta) + " CTAs");
+    b->grp_cta[g] = cta;
+    b->grp_first[g] = k;
+    b->grp_count[g] = e - k;
+    int nc = mc;
+    if (total > 0.0 && e - k < n) nc = (int)(mc * work / total + 0.5);
+    b->grp_clusters[g] = std::max(1, std::min(nc, mc));
+    k = e;
+  }
+  for (int k = 0; k < n; ++k) b->h_order[k] = list[k];
+  b->h_order[slots(b)] = n;
+  for (int g = 0; g < kMaxGroups; ++g) b->h_order[slots(b) + 1 + g] = g < b->ngroups ? b->grp_count[g] : 0;
+  CK(cudaMemcpyAsync(b->d_order, b->h_order, sizeof(int) * (size_t)std::max(n, 1), cudaMemcpyHostToDevice, b->stream));
+  CK(cudaMemcpyAsync(b->d_count, b->h_order + slots(b), sizeof(int) * (1 + kMaxGroups), cudaMemcpyHostToDevice,
+                     b->stream));
+  return MAZE_OK;
+}
+
+// Upload the scheduling order after a change of membership or of the
+// per-box launch choices.
+// Pending admissions stay out of the order unless admit_ready is set, in
+// which case those whose admission has finished on the GPU join (listed in
+// ``joined`` when given).
+maze_status upload_order(maze_batch* b, bool admit_ready = true, std::vector<int>* joined = nullptr) {
   if (!b->dirty) return MAZE_OK;
   CK(cudaStreamSynchronize(b->stream));
   b->active.clear();
-  for (int s = 0; s < slots(b); ++s)
-    if (b->box[s]) b->active.push_back(s);
-  std::stable_sort(b->active.begin(), b->active.end(), [&](int x, int y) { return b->cost[x] > b->cost[y]; });
-  const int n = (int)b->active.size();
-  for (int k = 0; k < n; ++k) b->h_order[k] = b->active[k];
-  b->h_order[slots(b)] = n;
-  CK(cudaMemcpyAsync(b->d_order, b->h_order, sizeof(int) * (size_t)std::max(n, 1), cudaMemcpyHostToDevice, b->stream));
-  CK(cudaMemcpyAsync(b->d_count, b->h_order + slots(b), sizeof(int), cudaMemcpyHostToDevice, b->stream));
-  b->dirty = false;
+  bool waiting = false;
+  for (int s = 0; s < slots(b); ++s) {
+    if (!b->box[s]) continue;
+    if (b->pending[s]) {
+      const cudaError_t q = admit_ready ? cudaEventQuery(b->admit_evs[s]) : cudaErrorNotReady;
+      if (q == cudaErrorNotReady) {
+        waiting = true;
+        continue;
+      }
+      CK(q);
+      b->pending[s] = 0;
+      if (joined) joined->push_back(s);
+    }
+    b->active.push_back(s);
+  }
+  maze_status st = layout_groups(b, b->active);
+  if (st != MAZE_OK) return st;
+  // the stats and clear kernels walk the whole order
+  b->active.assign(b->h_order, b->h_order + b->active.size());
+  b->dirty = waiting;
+  return MAZE_OK;
+}
+
+// Wait for every pending admission (calls that need every box in the order).
+maze_status settle_admissions(maze_batch* b) {
+  bool any = false;
+  for (int s = 0; s < slots(b); ++s) any = any || (b->box[s] && b->pending[s]);
+  if (!any) return MAZE_OK;
+  CK(cudaStreamSynchronize(b->admit));
+  b->dirty = true;
   return MAZE_OK;
 }
 
@@ -555,6 +685,7 @@ maze_status read_all_stats(maze_batch* b) {
 
 // Bring a box's host-side rotation index up to date before a host access.
 maze_status sync_box(maze_batch* b, int id) {
+  if (b->pending[id]) CK(cudaEventSynchronize(b->admit_evs[id]));
   CK(cudaStreamSynchronize(b->stream));
   int ik = 0;
   CK(cudaMemcpy(&ik, b->d_ik + id, sizeof(int), cudaMemcpyDeviceToHost));
@@ -562,8 +693,13 @@ maze_status sync_box(maze_batch* b, int id) {
   return MAZE_OK;
 }
 
-maze_status step_async(maze_batch* b, int nsteps) {
-  maze_status s = upload_order(b);
+// Queue nsteps steps of the boxes in the work order; with wait_admissions
+// every admitted box is in it (pending admissions are waited for), else only
+// those whose admission has finished.
+maze_status step_async(maze_batch* b, int nsteps, bool wait_admissions = true) {
+  maze_status s = wait_admissions ? settle_admissions(b) : MAZE_OK;
+  if (s != MAZE_OK) return s;
+  s = upload_order(b, wait_admissions);
   if (s != MAZE_OK) return s;
   if (b->active.empty() || nsteps == 0) return MAZE_OK;
   s = build_graph(b);
@@ -586,6 +722,13 @@ void destroy(maze_batch* b) {
     if (e) cudaEventDestroy(e);
   if (b->admit_ev) cudaEventDestroy(b->admit_ev);
   if (b->admit) cudaStreamDestroy(b->admit);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  for (cudaEvent_t e : b->admit_evs)
+    if (e) cudaEventDestroy(e);
+  for (int g = 0; g < kMaxGroups; ++g) {
+    if (b->join_ev[g]) cudaEventDestroy(b->join_ev[g]);
+    if (b->aux[g]) cudaStreamDestroy(b->aux[g]);
+  }
   cudaFree(b->d_desc);
   cudaFree(b->d_ik);
   cudaFree(b->d_order);
@@ -626,6 +769,9 @@ maze_status maze_batch_create(const maze_batch_config* cfg, maze_batch** out) {
   const int S = cfg->max_sims;
   b->box.assign(S, nullptr);
   b->cost.assign(S, 0.0);
+  b->box_cta.assign(S, 0);
+  b->pending.assign(S, 0);
+  b->admit_evs.assign(S, nullptr);
   auto bad = [&](maze_status s) {
     std::string keep = maze_last_error();
     destroy(b);
@@ -651,19 +797,24 @@ maze_status maze_batch_create(const maze_batch_config* cfg, maze_batch** out) {
   BK(cudaMalloc(&b->d_desc, sizeof(BoxDesc) * (size_t)S));
   BK(cudaMalloc(&b->d_ik, sizeof(int) * (size_t)S));
   BK(cudaMalloc(&b->d_order, sizeof(int) * (size_t)S));
-  BK(cudaMalloc(&b->d_count, sizeof(int)));
-  BK(cudaMalloc(&b->d_queue, sizeof(unsigned)));
+  BK(cudaMalloc(&b->d_count, sizeof(int) * (1 + kMaxGroups)));
+  BK(cudaMalloc(&b->d_queue, sizeof(unsigned) * kMaxGroups));
   BK(cudaMalloc(&b->d_stats, sizeof(maze_stats) * (size_t)S));
-  BK(cudaMallocHost(&b->h_order, sizeof(int) * (size_t)(S + 1)));
+  BK(cudaMallocHost(&b->h_order, sizeof(int) * (size_t)(S + 1 + kMaxGroups)));
   BK(cudaMallocHost(&b->h_stats, sizeof(maze_stats) * (size_t)S));
   BK(cudaMallocHost(&b->h_ik, sizeof(int) * (size_t)S));
   BK(cudaMemsetAsync(b->d_ik, 0, sizeof(int) * (size_t)S, b->stream));
-  BK(cudaMemsetAsync(b->d_count, 0, sizeof(int), b->stream));
+  BK(cudaMemsetAsync(b->d_count, 0, sizeof(int) * (1 + kMaxGroups), b->stream));
   BK(cudaMemsetAsync(b->d_stats, 0, sizeof(maze_stats) * (size_t)S, b->stream));
   BK(cudaEventCreate(&b->ev[0]));
   BK(cudaEventCreate(&b->ev[1]));
   BK(cudaStreamCreateWithFlags(&b->admit, cudaStreamNonBlocking));
   BK(cudaEventCreateWithFlags(&b->admit_ev, cudaEventDisableTiming));
+  BK(cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming));
+  for (int g = 1; g < kMaxGroups; ++g) {
+    BK(cudaStreamCreateWithFlags(&b->aux[g], cudaStreamNonBlocking));
+    BK(cudaEventCreateWithFlags(&b->join_ev[g], cudaEventDisableTiming));
+  }
   BK(cudaStreamSynchronize(b->stream));
 #undef BK
   maze_status s = set_cluster(b, cta);
@@ -708,28 +859,23 @@ maze_status maze_batch_add(maze_batch* b, const maze_config* cfg, int32_t* id) {
   maze_config c2 = *cfg;
   c2.cuda_stream = b->admit;
   maze_ctx* c = nullptr;
-  maze_status s = ctx_create(&c2, b->arena, &c);
+  maze_status s = ctx_create(&c2, b->arena, &c, true);
   if (s != MAZE_OK) return s;
-  BoxDesc d;
-  memset(&d, 0, sizeof d);
-  d.ion = ion_args(c, 1, 1);
-  d.cell = cell_args(c);
-  d.force = force_args(c, nullptr, 1, 1);
-  d.mixed = mixed_args(c, 0, nullptr);
-  for (int g = 0; g < 3; ++g) d.phi[g] = reinterpret_cast<float2*>(c->phi[g]);
-  const int per_cell = c->ncell > 0 ? (c->n + c->ncell - 1) / c->ncell : 0;
-  d.split = std::max(1, (per_cell + kBatchWarps - 1) / kBatchWarps);
+  const BoxDesc d = box_desc(c);
+  // (pageable sources: both copies take their bytes before returning)
   cudaError_t e = cudaMemcpyAsync(b->d_desc + slot, &d, sizeof d, cudaMemcpyHostToDevice, b->admit);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_ik + slot, &c->ik, sizeof(int), cudaMemcpyHostToDevice, b->admit);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(b->admit);
-  // later batch steps (which will include the box) start after its set-up
-  if (e == cudaSuccess) e = cudaEventRecord(b->admit_ev, b->admit);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->admit_ev, 0);
+  if (e == cudaSuccess && !b->admit_evs[slot]) e = cudaEventCreateWithFlags(&b->admit_evs[slot], cudaEventDisableTiming);
+  // the box joins the work order once this event has completed (its step 0
+  // ran); a failed step 0 is in its record and stops only that box
+  if (e == cudaSuccess) e = cudaEventRecord(b->admit_evs[slot], b->admit);
+  if (e != cudaSuccess) cudaStreamSynchronize(b->admit);
   if (e != cudaSuccess) {
     free_ctx(c);
     return fail(MAZE_ERR_CUDA, std::string("upload of the box descriptor: ") + cudaGetErrorString(e));
   }
   b->box[slot] = c;
+  b->pending[slot] = 1;
   // relative cost of one step: grid points (V-cycles) and ions (pairs)
   b->cost[slot] = (double)c->ng + 24.0 * c->n;
   b->dirty = true;
@@ -740,10 +886,13 @@ maze_status maze_batch_add(maze_batch* b, const maze_config* cfg, int32_t* id) {
 maze_status maze_batch_remove(maze_batch* b, int32_t id) {
   maze_status s = check_id(b, id);
   if (s != MAZE_OK) return s;
+  if (b->pending[id]) CK(cudaEventSynchronize(b->admit_evs[id]));
   CK(cudaStreamSynchronize(b->stream));
+  b->pending[id] = 0;
   free_ctx(b->box[id]);
   b->box[id] = nullptr;
   b->cost[id] = 0.0;
+  b->box_cta[id] = 0;
   b->dirty = true;
   return MAZE_OK;
 }
@@ -764,12 +913,9 @@ maze_status maze_batch_step_async(maze_batch* b, int32_t nsteps) {
   return step_async(b, nsteps);
 }
 
-maze_status maze_batch_step(maze_batch* b, int32_t nsteps) {
-  if (!b) return fail(MAZE_ERR_INVALID, "batch is NULL");
-  if (nsteps < 0) return fail(MAZE_ERR_INVALID, "nsteps must be >= 0");
-  maze_status s = step_async(b, nsteps);
-  if (s != MAZE_OK) return s;
-  s = read_all_stats(b);
+// The first failing status among the boxes of the work order (after a sync).
+maze_status order_status(maze_batch* b) {
+  maze_status s = read_all_stats(b);
   if (s != MAZE_OK) return s;
   for (int id : b->active) {
     const int st = b->h_stats[id].status;
@@ -779,6 +925,38 @@ maze_status maze_batch_step(maze_batch* b, int32_t nsteps) {
              b->h_stats[id].resid, b->h_stats[id].iters);
     return fail((maze_status)st, buf);
   }
+  return MAZE_OK;
+}
+
+maze_status maze_batch_step(maze_batch* b, int32_t nsteps) {
+  if (!b) return fail(MAZE_ERR_INVALID, "batch is NULL");
+  if (nsteps < 0) return fail(MAZE_ERR_INVALID, "nsteps must be >= 0");
+  maze_status s = step_async(b, nsteps);
+  if (s != MAZE_OK) return s;
+  return order_status(b);
+}
+
+maze_status maze_batch_step_ready_async(maze_batch* b, int32_t nsteps) {
+  if (!b) return fail(MAZE_ERR_INVALID, "batch is NULL");
+  if (nsteps < 0) return fail(MAZE_ERR_INVALID, "nsteps must be >= 0");
+  return step_async(b, nsteps, false);
+}
+
+maze_status maze_batch_sync(maze_batch* b) {
+  if (!b) return fail(MAZE_ERR_INVALID, "batch is NULL");
+  return order_status(b);
+}
+
+maze_status maze_batch_refresh(maze_batch* b, int32_t* joined, int32_t cap, int32_t* n_joined) {
+  if (!b || !n_joined || (cap > 0 && !joined)) return fail(MAZE_ERR_INVALID, "NULL argument");
+  *n_joined = 0;
+  std::vector<int> j;
+  b->dirty = true;   // look at the pending admissions now
+  maze_status s = upload_order(b, true, &j);
+  if (s != MAZE_OK) return s;
+  if ((int)j.size() > cap) return fail(MAZE_ERR_INVALID, "joined must hold max_sims entries");
+  for (size_t k = 0; k < j.size(); ++k) joined[k] = j[k];
+  *n_joined = (int32_t)j.size();
   return MAZE_OK;
 }
 
@@ -809,7 +987,8 @@ maze_status maze_batch_get_stats(maze_batch* b, int32_t id, maze_stats* out) {
 maze_status maze_batch_get_all_stats(maze_batch* b, maze_stats* out, int32_t n) {
   if (!b || !out) return fail(MAZE_ERR_INVALID, "NULL argument");
   if (n < slots(b)) return fail(MAZE_ERR_INVALID, "out must hold max_sims entries");
-  maze_status s = upload_order(b);
+  maze_status s = settle_admissions(b);
+  if (s == MAZE_OK) s = upload_order(b);
   if (s != MAZE_OK) return s;
   s = read_all_stats(b);
   if (s != MAZE_OK) return s;
@@ -827,9 +1006,25 @@ maze_status maze_batch_get_all_stats(maze_batch* b, maze_stats* out, int32_t n) 
 maze_status maze_batch_tune(maze_batch* b, int32_t steps_per_trial, int32_t* chosen_ctas, double* ms_per_step) {
   if (!b) return fail(MAZE_ERR_INVALID, "batch is NULL");
   if (steps_per_trial < 1) return fail(MAZE_ERR_INVALID, "steps_per_trial must be >= 1");
-  maze_status s = upload_order(b);
+  maze_status s = settle_admissions(b);
+  if (s == MAZE_OK) s = upload_order(b);
   if (s != MAZE_OK) return s;
   if (b->active.empty()) return fail(MAZE_ERR_INVALID, "the batch holds no simulation");
+  // one cluster size and the configured V-cycle for every box: drop the
+  // per-class choices of maze_batch_autotune
+  CK(cudaStreamSynchronize(b->stream));
+  for (int sl : b->active) {
+    maze_ctx* c = b->box[sl];
+    b->box_cta[sl] = 0;
+    c->mx.nu1 = c->cfg.mg_pre;
+    c->mx.nu2 = c->cfg.mg_post;
+    c->mx.tail_n = 0;
+    const BoxDesc d = box_desc(c);
+    CK(cudaMemcpyAsync(b->d_desc + sl, &d, sizeof d, cudaMemcpyHostToDevice, b->stream));
+  }
+  b->dirty = true;
+  s = upload_order(b);
+  if (s != MAZE_OK) return s;
   // every trial starts from the same state: snapshot the arena (all boxes'
   // buffers and statistics) and the rotation indices, restore after each
   const size_t hw = b->arena->high_water();
@@ -854,7 +1049,7 @@ maze_status maze_batch_tune(maze_batch* b, int32_t steps_per_trial, int32_t* cho
   maze_status res = MAZE_OK;
   cudaError_t e = save();
   for (int k = 0; k < 5 && e == cudaSuccess && res == MAZE_OK; ++k) {
-    if (max_clusters(cand[k]) < 1) continue;
+    if (clusters_for(b, cand[k]) < 1) continue;
     res = set_cluster(b, cand[k]);
     if (res == MAZE_OK) res = step_async(b, 1);   // warm-up (module load, caches)
     if (res != MAZE_OK) break;
@@ -884,6 +1079,159 @@ maze_status maze_batch_tune(maze_batch* b, int32_t steps_per_trial, int32_t* cho
   if (chosen_ctas) *chosen_ctas = best;
   if (ms_per_step) *ms_per_step = best_ms;
   return MAZE_OK;
+}
+
+maze_status maze_batch_autotune(maze_batch* b, int32_t steps_per_trial, maze_tune_entry* table, int32_t cap,
+                                int32_t* n_entries) {
+  if (!b || !n_entries || (cap > 0 && !table)) return fail(MAZE_ERR_INVALID, "NULL argument");
+  if (steps_per_trial < 1) return fail(MAZE_ERR_INVALID, "steps_per_trial must be >= 1");
+  *n_entries = 0;
+  maze_status s = settle_admissions(b);
+  if (s == MAZE_OK) s = upload_order(b);
+  if (s != MAZE_OK) return s;
+  if (b->active.empty()) return fail(MAZE_ERR_INVALID, "the batch holds no simulation");
+  // size classes (boxes of one grid edge), most work first
+  std::vector<int> edges;
+  for (int sl : b->active) edges.push_back(b->box[sl]->N);
+  std::sort(edges.begin(), edges.end());
+  edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
+  if ((int)edges.size() > cap) return fail(MAZE_ERR_INVALID, "table must hold one entry per grid size in the batch");
+  std::vector<double> work(edges.size(), 0.0);
+  for (int sl : b->active)
+    work[std::lower_bound(edges.begin(), edges.end(), b->box[sl]->N) - edges.begin()] += b->cost[sl];
+  std::vector<int> cls(edges.size());
+  for (size_t q = 0; q < cls.size(); ++q) cls[q] = (int)q;
+  std::stable_sort(cls.begin(), cls.end(), [&](int x, int y) { return work[x] > work[y]; });
+  const size_t hw = b->arena->high_water();
+  const size_t ikb = sizeof(int) * (size_t)slots(b);
+  char* snap = nullptr;
+  CK(cudaStreamSynchronize(b->stream));
+  CK(cudaMalloc(&snap, hw + ikb));
+  cudaError_t e = cudaMemcpyAsync(snap, b->arena_base, hw, cudaMemcpyDeviceToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(snap + hw, b->d_ik, ikb, cudaMemcpyDeviceToDevice, b->stream);
+  auto restore = [&]() -> cudaError_t {
+    cudaError_t r = cudaMemcpyAsync(b->arena_base, snap, hw, cudaMemcpyDeviceToDevice, b->stream);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(b->d_ik, snap + hw, ikb, cudaMemcpyDeviceToDevice, b->stream);
+    return r;
+  };
+  // current choice per class: CTAs per box, V-cycle schedule, tail
+  const maze_config& cf0 = b->box[b->active[0]]->cfg;
+  std::vector<int> c_cta(edges.size(), b->cluster), c_nu1(edges.size(), cf0.mg_pre),
+      c_nu2(edges.size(), cf0.mg_post), c_tail(edges.size(), 0);
+  for (size_t q = 0; q < edges.size(); ++q)
+    for (int sl : b->active)
+      if (b->box[sl]->N == edges[q]) {
+        c_nu1[q] = b->box[sl]->cfg.mg_pre;
+        c_nu2[q] = b->box[sl]->cfg.mg_post;
+        break;
+      }
+  // install a set of choices: descriptors and the launch groups
+  auto install = [&](const std::vector<int>& cta, const std::vector<int>& n1, const std::vector<int>& n2,
+                     const std::vector<int>& tl) -> maze_status {
+    for (int sl : b->active) {
+      const size_t q = std::lower_bound(edges.begin(), edges.end(), b->box[sl]->N) - edges.begin();
+      maze_ctx* c = b->box[sl];
+      b->box_cta[sl] = cta[q];
+      c->mx.nu1 = n1[q];
+      c->mx.nu2 = n2[q];
+      c->mx.tail_n = tl[q];
+      const BoxDesc d = box_desc(c);
+      CK(cudaMemcpyAsync(b->d_desc + sl, &d, sizeof d, cudaMemcpyHostToDevice, b->stream));
+    }
+    CK(cudaStreamSynchronize(b->stream));
+    return layout_groups(b, b->active);
+  };
+  // milliseconds per step of the whole batch with these choices (every box,
+  // one launch per cluster size, the launches side by side, as the graph
+  // runs them); 1e300 when it cannot run or a box fails. State restored.
+  maze_status res = MAZE_OK;
+  auto batch_ms = [&](const std::vector<int>& cta, const std::vector<int>& n1, const std::vector<int>& n2,
+                      const std::vector<int>& tl) -> double {
+    if (e != cudaSuccess || res != MAZE_OK) return 1e300;
+    for (int x : cta)
+      if (clusters_for(b, x) < 1) return 1e300;
+    res = install(cta, n1, n2, tl);
+    if (res == MAZE_OK) res = launch_step(b);   // warm-up (module load, caches)
+    if (res == MAZE_OK) e = restore();
+    if (e == cudaSuccess && res == MAZE_OK) e = cudaEventRecord(b->ev[0], b->stream);
+    for (int t = 0; t < steps_per_trial && e == cudaSuccess && res == MAZE_OK; ++t) res = launch_step(b);
+    if (e == cudaSuccess && res == MAZE_OK) e = cudaEventRecord(b->ev[1], b->stream);
+    const int n = (int)b->active.size();
+    if (e == cudaSuccess && res == MAZE_OK) {
+      k_batch_stats<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_desc, b->d_order, b->d_count, b->d_stats);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && res == MAZE_OK)
+      e = cudaMemcpyAsync(b->h_stats, b->d_stats, sizeof(maze_stats) * (size_t)slots(b), cudaMemcpyDeviceToHost,
+                          b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    float ms = 0.f;
+    if (e == cudaSuccess && res == MAZE_OK) e = cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]);
+    if (e == cudaSuccess) e = restore();
+    if (e != cudaSuccess || res != MAZE_OK) return 1e300;
+    for (int sl : b->active)
+      if (b->h_stats[sl].status != MAZE_OK) return 1e300;
+    return (double)ms / steps_per_trial;
+  };
+  // coordinate descent on the measured batch step: classes in order of
+  // their work, for each the CTAs per box, then the tail, then the
+  // schedule; a change must shorten the step by 3 % (trial times carry
+  // noise, and the configured schedule keeps results equal to the box run
+  // alone)
+  const int ctas[5] = {1, 2, 4, 8, 16};
+  const int sched[5][2] = {{2, 2}, {1, 2}, {2, 1}, {1, 1}, {3, 3}};
+  const double margin = 0.97;
+  const double start_ms = batch_ms(c_cta, c_nu1, c_nu2, c_tail);
+  double best = start_ms;
+  std::vector<double> before(edges.size()), after(edges.size());
+  for (int q : cls) {
+    before[q] = best;
+    auto try_set = [&](int cta, int n1, int n2, int tl) {
+      std::vector<int> a = c_cta, p1 = c_nu1, p2 = c_nu2, t = c_tail;
+      a[q] = cta;
+      p1[q] = n1;
+      p2[q] = n2;
+      t[q] = tl;
+      const double ms = batch_ms(a, p1, p2, t);
+      if (ms < margin * best) {
+        best = ms;
+        c_cta = a;
+        c_nu1 = p1;
+        c_nu2 = p2;
+        c_tail = t;
+      }
+    };
+    for (int cta : ctas)
+      if (cta != c_cta[q]) try_set(cta, c_nu1[q], c_nu2[q], c_tail[q]);
+    for (int tl : {8, 16})
+      if (tl != c_tail[q]) try_set(c_cta[q], c_nu1[q], c_nu2[q], tl);
+    for (const auto& sc : sched)
+      if (sc[0] != c_nu1[q] || sc[1] != c_nu2[q]) try_set(c_cta[q], sc[0], sc[1], c_tail[q]);
+    after[q] = best;
+  }
+  if (res == MAZE_OK && e == cudaSuccess) res = install(c_cta, c_nu1, c_nu2, c_tail);
+  if (e == cudaSuccess) e = restore();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  cudaFree(snap);
+  b->dirty = true;   // regroup the launches by the chosen cluster sizes
+  if (res != MAZE_OK) return res;
+  if (e != cudaSuccess) return fail(MAZE_ERR_CUDA, std::string("autotuning: ") + cudaGetErrorString(e));
+  for (size_t q = 0; q < edges.size(); ++q) {
+    maze_tune_entry& t = table[q];
+    t.grid_N = edges[q];
+    t.boxes = 0;
+    for (int sl : b->active) t.boxes += b->box[sl]->N == edges[q] ? 1 : 0;
+    t.cluster_ctas = c_cta[q];
+    t.mg_pre = c_nu1[q];
+    t.mg_post = c_nu2[q];
+    t.tail_n = c_tail[q];
+    t.ms_before = before[q];
+    t.ms_after = after[q];
+  }
+  *n_entries = (int32_t)edges.size();
+  s = upload_order(b);
+  if (s != MAZE_OK) return s;
+  return build_graph(b);
 }
 
 }  // extern "C"

@@ -140,7 +140,10 @@ maze_status status_message(maze_ctx* c);
 void free_ctx(maze_ctx* c);
 // Validates cfg, allocates every buffer (from ``arena`` when given), uploads
 // the state and runs step 0 on ``stream`` (the config's stream when null).
-maze_status ctx_create(const maze_config* cfg, Arena* arena, maze_ctx** out);
+// Builds a context and runs step 0. With defer_status the call returns once
+// step 0 is queued on the context's stream, without waiting for it: a failure
+// of step 0 then shows only in the device record (the batch's admission).
+maze_status ctx_create(const maze_config* cfg, Arena* arena, maze_ctx** out, bool defer_status = false);
 // Device bytes a context of this configuration takes from an arena.
 maze_status ctx_bytes(const maze_config* cfg, size_t* bytes);
 

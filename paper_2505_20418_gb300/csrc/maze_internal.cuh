@@ -212,6 +212,8 @@ struct MixedArgs {
   int Nl[kMaxLevels];
   int lg[kMaxLevels];      // log2(N_l) for powers of two, else -1
   int nu1, nu2;
+  int tail_n;              // levels of at most tail_n^3 points run in one CTA (0: 8 in a cluster, 16 in
+                           // the global form); the arithmetic, hence every result, is the same either way
   float c_sig_h, c_sig_l;  // h/4pi as a double-float
   float c_phi_h, c_phi_l;  // 4pi/h as a double-float
   double tol;

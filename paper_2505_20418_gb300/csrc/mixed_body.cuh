@@ -361,9 +361,10 @@ struct Slabs {
 // levels of at most 8^3 points (a 16^3 half-sweep already costs one SM
 // ~0.8 us, as much as a cluster barrier phase; an 8^3 one ~0.2 us); in the
 // global form (one part, grid barriers of ~2 us), those of at most 16^3.
-// The global form keeps every level whole in its one part either way.
+// The global form keeps every level whole in its one part either way. A
+// box's tail_n overrides the size (the batch autotuner chooses it).
 __host__ __device__ __forceinline__ int tail_level(const MixedArgs& a, int Q) {
-  const int tn = Q == 1 ? 16 : 8;
+  const int tn = a.tail_n > 0 ? a.tail_n : (Q == 1 ? 16 : 8);
   for (int l = 0; l < a.L; ++l)
     if (a.Nl[l] <= tn) return l;
   return a.L - 1;

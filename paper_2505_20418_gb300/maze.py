@@ -33,7 +33,8 @@ EXPORTS = ("maze_create", "maze_spread", "maze_solve", "maze_gather", "maze_step
            "maze_batch_remove", "maze_batch_info", "maze_batch_step", "maze_batch_step_async",
            "maze_batch_get", "maze_batch_set", "maze_batch_get_stats", "maze_batch_get_all_stats",
            "maze_batch_tune",
-           "maze_batch_destroy", "maze_wait_probe")
+           "maze_batch_destroy", "maze_wait_probe", "maze_batch_step_ready_async", "maze_batch_sync",
+           "maze_batch_refresh", "maze_batch_autotune")
 
 _D = ctypes.c_double
 _I = ctypes.c_int32
@@ -64,6 +65,14 @@ class MazeStats(ctypes.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["momentum"] = list(self.momentum)
         return d
+
+
+class MazeTuneEntry(ctypes.Structure):
+    _fields_ = [("grid_N", _I), ("boxes", _I), ("cluster_ctas", _I), ("mg_pre", _I), ("mg_post", _I),
+                ("tail_n", _I), ("ms_before", _D), ("ms_after", _D)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class MazeBatchConfig(ctypes.Structure):
@@ -123,6 +132,10 @@ def load(path: str = LIB_PATH):
     lib.maze_batch_destroy.argtypes = [P]
     lib.maze_batch_destroy.restype = None
     lib.maze_wait_probe.argtypes = [_I, P, ctypes.POINTER(_I)]
+    lib.maze_batch_step_ready_async.argtypes = [P, _I]
+    lib.maze_batch_sync.argtypes = [P]
+    lib.maze_batch_refresh.argtypes = [P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I)]
+    lib.maze_batch_autotune.argtypes = [P, _I, ctypes.POINTER(MazeTuneEntry), _I, ctypes.POINTER(_I)]
     lib.maze_last_error.restype = ctypes.c_char_p
     lib.maze_version.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -495,6 +508,22 @@ class MazeBatch:
     def step_async(self, nsteps: int = 1):
         _check(load().maze_batch_step_async(self.h, int(nsteps)))
 
+    def step_ready_async(self, nsteps: int = 1):
+        """Queue steps of the simulations whose admission has finished."""
+        _check(load().maze_batch_step_ready_async(self.h, int(nsteps)))
+
+    def refresh(self) -> list:
+        """Ids of the simulations whose admission finished since the last call
+        (they now advance with step_ready_async)."""
+        arr = (_I * self.max_sims)()
+        n = _I()
+        _check(load().maze_batch_refresh(self.h, arr, self.max_sims, ctypes.byref(n)))
+        return [arr[k] for k in range(n.value)]
+
+    def sync_status(self) -> int:
+        """Wait for the queued steps; the first failing status among them."""
+        return load().maze_batch_sync(self.h)
+
     def get(self, i: int, what: int) -> np.ndarray:
         n, N = self.shape[int(i)]
         out = np.empty((n, 3)) if what <= MAZE_FORCE_EL else np.empty((N, N, N))
@@ -520,3 +549,11 @@ class MazeBatch:
         c, ms = _I(), _D()
         _check(load().maze_batch_tune(self.h, int(steps_per_trial), ctypes.byref(c), ctypes.byref(ms)))
         return c.value, ms.value
+
+    def autotune(self, steps_per_trial: int = 5) -> list:
+        """Per-size-class choice of CTAs per box, V-cycle schedule and coarse
+        tail; returns the table (one dict per grid size)."""
+        arr = (MazeTuneEntry * 64)()
+        n = _I()
+        _check(load().maze_batch_autotune(self.h, int(steps_per_trial), arr, 64, ctypes.byref(n)))
+        return [arr[k].as_dict() for k in range(n.value)]

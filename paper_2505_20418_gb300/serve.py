@@ -90,16 +90,18 @@ class Server:
         otherwise arrivals are replayed as fast as the engine goes (every
         request is eligible at once).
 
-        Each loop iteration queues the next k steps of every admitted
-        simulation, then admits arrived requests while those steps run on the
-        GPU (a newcomer's set-up and step 0 go to the batch's admission
-        stream), then waits for the steps and retires finished simulations;
-        newcomers join the next iteration's steps. Returns per-step latencies
-        (one sample per simulation per step: the loop iteration's time over
-        its k steps), split into iterations that admitted a request and
-        iterations that did not, and aggregate throughput."""
+        Each loop iteration lets the requests whose admission (step 0) has
+        finished on the GPU join, queues the next k steps of every joined
+        simulation, admits arrived requests while those steps run (a
+        newcomer's set-up and step 0 go to the batch's admission stream and
+        never hold up the running simulations), then waits for the steps and
+        retires finished simulations. Returns per-step latencies (one sample
+        per simulation per step: the loop iteration's time over its k steps),
+        split into iterations that admitted a request and iterations that did
+        not, and aggregate throughput."""
         pending = sorted(requests, key=lambda q: q.arrival)
         active: list[Request] = []
+        waiting: dict[int, Request] = {}        # admitted, step 0 still running
         lat: list[float] = []
         lat_adm: list[float] = []
         lat_quiet: list[float] = []
@@ -108,30 +110,35 @@ class Server:
         ion_steps = 0
         t0 = time.perf_counter()
         i = 0
-        while (i < len(pending) or active) and time.perf_counter() - t0 < max_wall:
+        while (i < len(pending) or active or waiting) and time.perf_counter() - t0 < max_wall:
             t_iter = time.perf_counter()
-            # queue k steps of every admitted simulation (no request overshoots)
+            if waiting:
+                for sid in self.batch.refresh():
+                    active.append(waiting.pop(sid))
+            # queue k steps of every joined simulation (no request overshoots)
             k = min(self.chunk, min(q.steps - q.done for q in active)) if active else 0
             if k:
-                self.batch.step_async(k)
+                self.batch.step_ready_async(k)
             # admission while those steps run: arrived requests, in arrival
             # order, while there is room
             now = time.perf_counter() - t0
-            joined = []
+            joined = 0
             while i < len(pending) and (not realtime or pending[i].arrival <= now):
                 q = pending[i]
                 if not self._try_admit(q):
                     break
                 q.admitted = time.perf_counter() - t0
-                joined.append(q)
+                waiting[q.sid] = q
+                joined += 1
                 i += 1
             if not k:
-                active = joined
-                if not active and i < len(pending) and realtime:
+                if i < len(pending) and realtime and not waiting:
                     time.sleep(max(0.0, min(pending[i].arrival - now, 0.01)))
+                elif waiting:
+                    time.sleep(0.0002)
                 continue
             # wait for the queued steps; statuses of everything stepped
-            st = self.batch.step_status(0)
+            st = self.batch.sync_status()
             for q in active:
                 q.done += k
             box_steps += k * len(active)
@@ -156,7 +163,7 @@ class Server:
             samples = [per] * (k * len(active))
             lat.extend(samples)
             (lat_adm if joined else lat_quiet).extend(samples)
-            active = keep + joined
+            active = keep
         wall = time.perf_counter() - t0
 
         def pct(v, p):

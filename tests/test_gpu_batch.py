@@ -189,3 +189,48 @@ def test_batch_rejects_what_it_cannot_run():
         b.add(pos, vel, types, L, N, TF, precision=M.MAZE_FP64, **args)
     assert e.value.status == M.MAZE_ERR_INVALID
     b.close()
+
+
+def test_autotune_per_size_class_keeps_results():
+    """maze_batch_autotune: a row per grid size; the state is restored after
+    its trials; a class that kept the configured V-cycle schedule advances bit
+    for bit as its boxes alone (cluster size and tail change no result), a
+    class given another schedule still meets the tolerance and the oracle's
+    forces within the mixed-precision bar."""
+    specs = [box(n, s) for n, s in ((216, 81), (216, 82), (512, 83), (512, 84), (1000, 85), (1000, 86))]
+    b = M.MazeBatch(GiB, 8)
+    ids = [add(b, sp, a) for sp, a in specs]
+    b.step(2)
+    before = [b.get(i, M.MAZE_POS) for i in ids]
+    table = b.autotune(2)
+    assert sorted(t["grid_N"] for t in table) == [16, 24, 32]
+    for t in table:
+        assert t["boxes"] == 2 and t["cluster_ctas"] in (1, 2, 4, 8, 16) and t["tail_n"] in (0, 8, 16)
+        assert (t["mg_pre"], t["mg_post"]) in ((2, 2), (1, 2), (2, 1), (1, 1), (3, 3))
+        assert 0 < t["ms_after"] <= t["ms_before"]
+    for i, x in zip(ids, before):
+        assert np.array_equal(b.get(i, M.MAZE_POS), x)
+    b.step(3)
+    by_n = {t["grid_N"]: t for t in table}
+    for i, (sp, a) in zip(ids, specs):
+        t = by_n[sp[4]]
+        s = b.stats(i)
+        assert s["status"] == 0 and s["step"] == 5 and s["resid"] < a["tol"]
+        if (t["mg_pre"], t["mg_post"]) == (2, 2):
+            sim, _ = alone(sp, a, 5)
+            same(b, i, sim)
+            sim.close()
+        else:
+            pos, vel, types, L, N = sp
+            p = O.Params(L=L, N=N, dt=a["dt"], tol=a["tol"], rc=a["r_cut"], P=a["order"], solver="mg")
+            st = O.init(pos, vel, types, p, TF)
+            for _ in range(5):
+                st = O.step(st, p, TF)
+            assert force_err(b.get(i, M.MAZE_FORCE), st.F) < MIXED_BAR
+    # the one-size tuner puts every box back on one cluster size and the
+    # configured schedule
+    cta, _ = b.tune(2)
+    b.step(1)
+    for i in ids:
+        assert b.stats(i)["step"] == 6
+    b.close()

@@ -101,3 +101,51 @@ def test_mixed_large_box_grid_form():
     err = np.linalg.norm(F[idx] - Fo, axis=1) / np.maximum(np.linalg.norm(Fo, axis=1), scale)
     assert err.max() < MIXED_BAR
     sim.close()
+
+
+@pytest.mark.parametrize("n_ions", [4096, 13824])
+def test_mixed_parity_on_the_largest_replica_grids(n_ions):
+    """The largest grids of the batched boxes (4096 ions, 48^3: the
+    multiply-high index decode on a non-power-of-two grid) and of the served
+    boxes (13824 ions, 64^3: the V-cycle in global scratch instead of the
+    cluster's shared memory), step 0 and one step against the oracle."""
+    w = synth.replica(n_ions, 7000 + n_ions)
+    pos, vel, types = synth.make_state(w)
+    tf = synth.tosi_fumi_nacl()
+    tol = 1e-10
+    sim = M.MazeSim(pos, vel, types, w.L, w.N, tf, r_cut=w.rc, dt=w.dt, tol=tol, order=w.order,
+                    solver=M.MAZE_SOLVER_MG, precision=M.MAZE_MIXED)
+    p = O.Params(L=w.L, N=w.N, dt=w.dt, tol=tol, rc=w.rc, P=w.order, solver="mg")
+    st = O.init(pos, vel, types, p, tf)
+    assert force_err(sim.get(M.MAZE_FORCE), st.F) < MIXED_BAR
+    st = O.step(st, p, tf)
+    sim.step(1)
+    s = sim.stats()
+    assert s["status"] == 0 and s["resid"] < tol and abs(s["iters"] - st.iters) <= 1
+    assert force_err(sim.get(M.MAZE_FORCE), st.F) < MIXED_BAR
+    x = sim.get(M.MAZE_POS)
+    Q = np.where(types == 0, 1.0, -1.0)
+    q = O.spread(x, Q, p.L, p.N, p.P)
+    sig = (p.h / (4 * np.pi)) * O.apply_M(sim.get(M.MAZE_PHI)) + q
+    assert O.inf_norm(sig) < tol + 1e-6    # FP32 spreading of q
+    sim.close()
+
+
+def test_mixed_energies_against_the_oracle():
+    """Mixed-precision energies against the FP64 oracle on the same 20-step
+    trajectory (1000 ions): kinetic, Tosi-Fumi, discrete electrostatic
+    (Eq. energy_discr), V_work (Eq. E_nostra) and their total within the
+    mixed bar of 1e-5 relative (V_work, which starts at zero, relative to the
+    kinetic plus pair energy); the constraint residual below tol on both."""
+    sim, p, tf, (pos, vel, types) = make("nacl1000")
+    st = O.init(pos, vel, types, p, tf)
+    for _ in range(20):
+        st = O.step(st, p, tf)
+        sim.step(1)
+    s = sim.stats()
+    e = O.energies(st, p)
+    for key in ("ke", "v_tf", "v_disc", "e_tot"):
+        assert abs(s[key] - e[key]) <= MIXED_BAR * abs(e[key]), (key, s[key], e[key])
+    assert abs(s["v_work"] - e["v_work"]) <= MIXED_BAR * (e["ke"] + abs(e["v_tf"]))
+    assert s["resid"] < p.tol and st.resid < p.tol
+    sim.close()

@@ -13,6 +13,7 @@ class FakeBatch:
     def __init__(self, slots, budget):
         self.slots, self.budget = slots, budget
         self.sims = {}
+        self.order = set()
         self.used = 0
         self.log = []
 
@@ -27,14 +28,18 @@ class FakeBatch:
         self.log.append(("add", i))
         return i
 
-    def step_async(self, k):
-        self.queued = dict(self.sims)     # the simulations these steps include
-        for s in self.sims.values():
-            s["steps"] += k
-        self.log.append(("step", k, len(self.sims)))
+    def refresh(self):
+        """Newcomers join the work order (every admission finishes at once here)."""
+        joined = [i for i in self.sims if i not in self.order]
+        self.order.update(joined)
+        return joined
 
-    def step_status(self, k):
-        assert k == 0                     # the server only waits for queued steps
+    def step_ready_async(self, k):
+        for i in self.order:
+            self.sims[i]["steps"] += k
+        self.log.append(("step", k, len(self.order)))
+
+    def sync_status(self):
         return M.MAZE_OK
 
     def all_stats(self):
@@ -44,6 +49,7 @@ class FakeBatch:
         return np.full((self.sims[i]["n"], 3), float(self.sims[i]["steps"]))
 
     def remove(self, i):
+        self.order.discard(i)
         self.used -= self.sims.pop(i)["need"]
         self.log.append(("remove", i))
 
