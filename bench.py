@@ -364,6 +364,7 @@ def config_dict(w, args, reference=False):
 # A kernel changed after its capture must drop its entry (traffic null).
 MEASURED_TRAFFIC = {
     ("nacl1000", "k_mixed_cluster", "mixed", "mg"): (1195520, "profiles/k_mixed_cluster_nacl1000.md"),
+    ("nacl512000", "k_mg_solve", "fp64", "mg"): (19842986000, "profiles/k_mg_solve_nacl512000_fp64.md"),
 }
 
 
