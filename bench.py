@@ -45,6 +45,7 @@ from paper_2505_20418_gb300 import synth  # noqa: E402
 
 METRIC = "MaZe steps/s, solve GB/s vs HBM peak, p50/p99 step latency at stated force error"
 KERNELS_PER_STEP_CELLS = 7    # move, spread, 3 cell-list kernels, solve, forces
+KERNELS_PER_STEP_HALF = 8     # FP64, one force block per cell: ... solve, pairs once each, gather + finish
 KERNELS_PER_STEP_NOCELLS = 4
 KERNELS_PER_STEP_FUSED = 2     # mixed precision up to 64^3, no cell list: S1-S6 in one cluster launch, the forces
 KERNELS_PER_STEP_SPLIT = 4     # mixed up to 64^3 with a cell list: S1-S3, S8 beside the solve, S7/S9
@@ -363,7 +364,6 @@ def config_dict(w, args, reference=False):
 # command and the other counters are in the named summary under profiles/.
 # A kernel changed after its capture must drop its entry (traffic null).
 MEASURED_TRAFFIC = {
-    ("nacl1000", "k_mixed_cluster", "mixed", "mg"): (1195520, "profiles/k_mixed_cluster_nacl1000.md"),
     ("nacl512000", "k_mg_solve", "fp64", "mg"): (19842986000, "profiles/k_mg_solve_nacl512000_fp64.md"),
 }
 
@@ -387,9 +387,11 @@ def solve_kernel_name(precision, solver, w):
     return "k_mg_solve" if solver == "mg" else "k_cg_solve"
 
 
-def kernels_per_step(precision, w):
+def kernels_per_step(precision, w, sms=152):
     if precision == "mixed" and w.N <= 64:
         return KERNELS_PER_STEP_SPLIT if has_cells(w) else KERNELS_PER_STEP_FUSED
+    if precision == "fp64" and has_cells(w) and int(np.floor(w.L / w.rc)) ** 3 >= 2 * sms:
+        return KERNELS_PER_STEP_HALF
     return KERNELS_PER_STEP_CELLS if has_cells(w) else KERNELS_PER_STEP_NOCELLS
 
 
@@ -606,7 +608,7 @@ def main():
             "roofline": roof, "roofline_other": other,
             "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": head["e2e"],
             "timing_error": head["timing_error"],
-            "gpu_launches": kernels_per_step(args.precision, w) * args.steps, "clocks": head["clocks"],
+            "gpu_launches": kernels_per_step(args.precision, w, sms) * args.steps, "clocks": head["clocks"],
         }
         if mixed is not None:
             mroof, _ = rooflines(w, "mixed", "mg", mixed["iters_per_step"], mixed["solve_s"], args.workload, sms)
@@ -617,7 +619,7 @@ def main():
                 "speedup_vs_fp64": mixed["steps_per_s"] / head["steps_per_s"],
                 "iters_per_step": mixed["iters_per_step"], "force_error": mixed["force_error"],
                 "phase_us": mixed["phase_us"], "solve_us": 1e6 * mixed["solve_s"], "roofline": mroof,
-                "gpu_launches": kernels_per_step("mixed", w) * args.steps, "clocks": mixed["clocks"]}
+                "gpu_launches": kernels_per_step("mixed", w, sms) * args.steps, "clocks": mixed["clocks"]}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -578,10 +578,12 @@ __device__ __forceinline__ void gather_el(const ForceArgs& a, int i, int lane, d
       gz += wt * pz;
       vd += wt * p0;
     }
-    gx = warp_sum(gx);
-    gy = warp_sum(gy);
-    gz = warp_sum(gz);
-    vd = warp_sum(vd);
+    // warp totals as exact integer sums on the integer pipe (an FP64
+    // shuffle tree would cost 20 FP64 operations per lane and ion)
+    gx = warp_dsum(gx);
+    gy = warp_dsum(gy);
+    gz = warp_dsum(gz);
+    vd = warp_dsum(vd);
   }
 }
 
@@ -1001,6 +1003,201 @@ __device__ __forceinline__ void forces_cell_slice(const ForceArgs& a, int c, int
     }
     __syncthreads();
   }
+}
+
+// S8 in FP64 with every pair evaluated once (Newton's third law), and S7 of
+// the cell's ions (to a.gath; S9 then runs one thread per ion), for boxes
+// with a cell list of reach 1: block b takes cell b. Its candidates are the
+// ions of the cell itself (a pair counted once: the candidate's slot after
+// the home ion's) and of the 13 cells of the upper half of its neighbourhood
+// (offsets (dz, dy, dx) after (0, 0, 0) in lexicographic order; with at
+// least 3 cells per edge the 27 neighbour cells are distinct, so no cell
+// pair is visited twice). Each surviving pair's force goes to both ions:
+// the home ion's share is summed over the warp in a fixed order, the
+// partner's share into a 64-bit fixed-point accumulator of the staged
+// candidate with shared-memory integer atomics; both then reach the per-ion
+// sums a.pair_fix ([n][4]: force x, y, z and pair energy, each pair's
+// energy given to both ions as the one-ion loop does) with 64-bit integer
+// atomics. Integer sums are exact, so the result does not depend on the
+// order the blocks run in. Fixed point: 2^-40 eV/A (9.1e-13) per unit, the
+// conversions done on the integer pipe (fix40), range +-8.4e6 eV/A; a pair
+// closer than 0.5 A (forces approaching that range) marks the step
+// non-finite. Staged candidates carry the periodic image of their cell
+// relative to the home cell (cells are at least r_cut wide, so for every
+// pair within r_cut that image is the minimum image, and any other pair is
+// at least r_cut apart in every image): no per-pair image arithmetic.
+constexpr double kFixFInv = 1.0 / 1099511627776.0;   // 2^-40
+
+// round(v * 2^40) as a 64-bit integer from v's bits, integer operations only
+// (the FP64 pipe's conversions are slow); |v| < 2^23, rounding half away
+// from zero, |v| < 2^-41 gives 0.
+__device__ __forceinline__ long long fix40(double v) {
+  const long long b = __double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e < 982) return 0;
+  const long long m = (b & 0xfffffffffffffLL) | (1LL << 52);
+  const int sh = 1035 - e;   // v 2^40 = m 2^(e - 1035)
+  const long long x = sh > 0 ? (m + (1LL << (sh - 1))) >> sh : m << (-sh);
+  return b < 0 ? -x : x;
+}
+constexpr int kHalfChunk = 384;
+constexpr int kHalfNbr = 14;                        // the cell itself and 13 neighbours
+template <int kW>
+struct HalfSmem {
+  float4 p[kHalfChunk];                            // FP32 positions (filter)
+  __align__(16) double xyz[3][kHalfChunk];         // FP64 positions
+  int j[kHalfChunk];                               // ion
+  int slot[kHalfChunk];                            // cell-list slot
+  unsigned long long acc[kHalfChunk][4];           // partners' shares, fixed point
+  int lo[kHalfNbr], cum[kHalfNbr + 1];
+  unsigned long long f[kCellGroup][4];             // home ions' shares, fixed point
+  int queue[kW][64];
+  int bad;
+};
+
+template <int kW>
+__device__ __forceinline__ void pairs_half_cell(const ForceArgs& a, int c, HalfSmem<kW>& sm) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int n = a.n, nc = a.nc;
+  const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+  if (threadIdx.x < kHalfNbr) {
+    // entry 0: the cell itself; then the 13 offsets after (0, 0, 0)
+    const int t = threadIdx.x == 0 ? 13 : (threadIdx.x - 1) + 14;
+    const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
+    const int cc = (cx + dx + nc) % nc + nc * ((cy + dy + nc) % nc + nc * ((cz + dz + nc) % nc));
+    sm.lo[threadIdx.x] = a.cell_start[cc];
+    sm.cum[threadIdx.x + 1] = a.cell_start[cc + 1] - a.cell_start[cc];
+  }
+  if (threadIdx.x == 0) sm.bad = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sm.cum[0] = 0;
+    for (int t = 0; t < kHalfNbr; ++t) sm.cum[t + 1] += sm.cum[t];
+  }
+  __syncthreads();
+  const int total = sm.cum[kHalfNbr];
+  const int self_end = sm.cum[1];                    // candidates [0, self_end) are the cell's own ions
+  const int c0 = a.cell_start[c], cn = a.cell_start[c + 1] - c0;
+  bool bad = false;
+  for (int g0 = c0; g0 < c0 + cn; g0 += kCellGroup) {
+    const int gn = min(kCellGroup, c0 + cn - g0);
+    for (int e = threadIdx.x; e < gn * 4; e += blockDim.x) sm.f[e >> 2][e & 3] = 0ull;
+    for (int ch0 = 0; ch0 < total; ch0 += kHalfChunk) {
+      const int len = min(kHalfChunk, total - ch0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < len; e += blockDim.x) {
+        const int tt = ch0 + e;
+        int k = 0;
+        while (k + 1 < kHalfNbr && sm.cum[k + 1] <= tt) ++k;
+        const int slot = sm.lo[k] + (tt - sm.cum[k]);
+        const int j = a.cell_ions[slot];
+        // the image of neighbour cell k next to the home cell
+        const int t = k == 0 ? 13 : (k - 1) + 14;
+        const int ox = cx + t % 3 - 1, oy = cy + (t / 3) % 3 - 1, oz = cz + t / 9 - 1;
+        const double shx = ox < 0 ? -a.L : (ox >= nc ? a.L : 0.0);
+        const double shy = oy < 0 ? -a.L : (oy >= nc ? a.L : 0.0);
+        const double shz = oz < 0 ? -a.L : (oz >= nc ? a.L : 0.0);
+        const float4 pj = a.pos_sorted[slot];
+        sm.j[e] = j;
+        sm.slot[e] = tt < self_end ? slot : 0x7fffffff;
+        sm.p[e] = make_float4(pj.x + (float)shx, pj.y + (float)shy, pj.z + (float)shz, pj.w);
+        sm.xyz[0][e] = a.pos[j] + shx;
+        sm.xyz[1][e] = a.pos[n + j] + shy;
+        sm.xyz[2][e] = a.pos[2 * n + j] + shz;
+        sm.acc[e][0] = sm.acc[e][1] = sm.acc[e][2] = sm.acc[e][3] = 0ull;
+      }
+      __syncthreads();
+      for (int gi = warp; gi < gn; gi += kW) {
+        const int islot = g0 + gi;
+        const int i = a.cell_ions[islot];
+        const double x = a.pos[i], y = a.pos[n + i], z = a.pos[2 * n + i];
+        const int ti = a.type[i];
+        const float4 pi32 = a.pos_sorted[islot];
+        int* q = sm.queue[warp];
+        int qn = 0;
+        double sfx = 0.0, sfy = 0.0, sfz = 0.0, sv = 0.0;
+        auto eval = [&](int e2) {
+          const double ddx = sm.xyz[0][e2] - x, ddy = sm.xyz[1][e2] - y, ddz = sm.xyz[2][e2] - z;
+          const double r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+          if (r2 >= a.rc2) return;
+          double fr, V;
+          tf_pair(a, ti + a.type[sm.j[e2]], r2, fr, V);
+          // force on the partner +fr d, on the home ion -fr d
+          const double fx = fr * ddx, fy = fr * ddy, fz = fr * ddz;
+          sfx -= fx;
+          sfy -= fy;
+          sfz -= fz;
+          sv += V;
+          atomicAdd(&sm.acc[e2][0], (unsigned long long)fix40(fx));
+          atomicAdd(&sm.acc[e2][1], (unsigned long long)fix40(fy));
+          atomicAdd(&sm.acc[e2][2], (unsigned long long)fix40(fz));
+          atomicAdd(&sm.acc[e2][3], (unsigned long long)fix40(V));
+        };
+        for (int e0 = 0; e0 < len; e0 += 32) {
+          const int e = e0 + lane;
+          bool pass = false;
+          // own-cell partners only after the home ion (every pair once); the
+          // other cells' candidates carry slot INT_MAX
+          if (e < len && sm.slot[e] > islot) {
+            const float4 pj = sm.p[e];
+            const float dx = pj.x - pi32.x, dy = pj.y - pi32.y, dz = pj.z - pi32.z;
+            const float r2f = dx * dx + dy * dy + dz * dz;
+            pass = r2f < a.rc2_filter;
+            bad = bad || r2f < 0.25f;
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, pass);
+          if (pass) q[qn + __popc(m & ((1u << lane) - 1u))] = e;
+          qn += __popc(m);
+          __syncwarp();
+          if (qn >= 32) {
+            eval(q[lane]);
+            __syncwarp();
+            if (lane < qn - 32) q[lane] = q[32 + lane];
+            __syncwarp();
+            qn -= 32;
+          }
+        }
+        if (lane < qn) eval(q[lane]);
+        __syncwarp();
+        // the home ion's share: each lane's sum to fixed point, an exact
+        // integer warp sum (integer pipe; no FP64 shuffle tree)
+        const long long tx = warp_isum(fix40(sfx)), ty = warp_isum(fix40(sfy)), tz = warp_isum(fix40(sfz)),
+                        tv = warp_isum(fix40(sv));
+        if (lane == 0) {
+          sm.f[gi][0] += (unsigned long long)tx;
+          sm.f[gi][1] += (unsigned long long)ty;
+          sm.f[gi][2] += (unsigned long long)tz;
+          sm.f[gi][3] += (unsigned long long)tv;
+        }
+      }
+      __syncthreads();
+      // the partners' shares of this chunk to the per-ion sums
+      for (int e = threadIdx.x; e < len * 4; e += blockDim.x) {
+        const unsigned long long v = sm.acc[e >> 2][e & 3];
+        if (v) atomicAdd(reinterpret_cast<unsigned long long*>(a.pair_fix) + (size_t)sm.j[e >> 2] * 4 + (e & 3), v);
+      }
+    }
+    // S7 for the home ions (their potential neighbourhood is the cell's)
+    for (int gi = warp; gi < gn; gi += kW) {
+      const int i = a.cell_ions[g0 + gi];
+      double gx, gy, gz, vd;
+      gather_el(a, i, lane, gx, gy, gz, vd);
+      if (lane == 0) {
+        a.gath[(size_t)i * 4] = gx;
+        a.gath[(size_t)i * 4 + 1] = gy;
+        a.gath[(size_t)i * 4 + 2] = gz;
+        a.gath[(size_t)i * 4 + 3] = vd;
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < gn * 4; e += blockDim.x)
+      atomicAdd(reinterpret_cast<unsigned long long*>(a.pair_fix) + (size_t)a.cell_ions[g0 + (e >> 2)] * 4 + (e & 3),
+                sm.f[e >> 2][e & 3]);
+  }
+  if (bad) atomicOr(&sm.bad, 1);
+  __syncthreads();
+  if (threadIdx.x == 0 && sm.bad) atomicCAS(&a.rec->status, MAZE_OK, MAZE_ERR_NONFINITE);
 }
 
 }  // namespace maze

@@ -280,6 +280,8 @@ ForceArgs force_args(maze_ctx* c, const double* phi, int do_kick, int count_step
   a.part = c->fpart;
   a.ticket = c->ticket;
   a.pair_out = c->pair_out;
+  a.pair_fix = c->pair_fix;
+  a.gath = c->gath;
   a.rec = c->rec;
   a.gate = c->gate;
   return a;
@@ -390,6 +392,18 @@ std::vector<double> coarse_kernel(int Nc) {
   return g;
 }
 
+// S7 + S8 (+ S9): one force kernel, or for FP64 boxes with pair_fix the
+// once-per-pair kernel followed by the gather and finish.
+maze_status enqueue_forces(maze_ctx* c, const ForceArgs& fa, cudaStream_t st) {
+  if (c->pair_fix) {
+    CK(launch_pairs_half(fa, st));
+    CK(launch_finish_fix(fa, st));
+  } else {
+    CK(launch_forces(fa, c->fblocks, st));
+  }
+  return MAZE_OK;
+}
+
 maze_status enqueue_cells(maze_ctx* c) {
   if (c->nc >= 3) CK(launch_cells(cell_args(c), c->stream));
   return MAZE_OK;
@@ -446,7 +460,10 @@ maze_status enqueue_step(maze_ctx* c, int timed) {
   s = enqueue_solve(c, 0, nullptr);
   if (s != MAZE_OK) return s;
   if (timed) CK(cudaEventRecordWithFlags(c->ev[3], c->stream, cudaEventRecordExternal));
-  CK(launch_forces(force_args(c, c->phi[(c->ik + 2) % 3], 1, 1), c->fblocks, c->stream));
+  {
+    const maze_status fs = enqueue_forces(c, force_args(c, c->phi[(c->ik + 2) % 3], 1, 1), c->stream);
+    if (fs != MAZE_OK) return fs;
+  }
   if (timed) CK(cudaEventRecordWithFlags(c->ev[4], c->stream, cudaEventRecordExternal));
   return MAZE_OK;
 }
@@ -880,6 +897,12 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
     AL(c->ticket, ngroups + 4);
     c->ticket_count = ngroups + 4;
   }
+  // FP64 boxes whose forces run one block per cell: the pairs once each
+  // (Newton's third law) in their own kernel, then the gather and finish
+  if (!c->mixed && c->nc >= 3 && c->reach == 1 && c->ncell >= 2 * c->num_sms) {
+    AL(c->pair_fix, 4 * (size_t)n);
+    AL(c->gath, 4 * (size_t)n);
+  }
   if (c->split_step) {
     AL(c->pair_out, 4 * (size_t)n);
     if (cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -956,6 +979,7 @@ maze_status ctx_create(const maze_config* cfg, Arena* arena, maze_ctx** out, boo
   if (!gkf.empty()) CKC(cudaMemcpyAsync(c->mx_g, gkf.data(), gkf.size() * 4, cudaMemcpyHostToDevice, st));
   CKC(cudaMemsetAsync(c->force, 0, 3 * (size_t)n * 8, st));
   CKC(cudaMemsetAsync(c->force_el, 0, 3 * (size_t)n * 8, st));
+  if (c->pair_fix) CKC(cudaMemsetAsync(c->pair_fix, 0, 4 * (size_t)n * 8, st));
   CKC(cudaMemsetAsync(c->qfix, 0, ng * 8, st));
   CKC(cudaMemsetAsync(c->y, 0, ng * 8, st));
   CKC(cudaMemsetAsync(c->phi[0], 0, ng * 8, st));
@@ -980,7 +1004,8 @@ maze_status ctx_create(const maze_config* cfg, Arena* arena, maze_ctx** out, boo
     c->ik = 0;
     CK(cudaMemcpyAsync(c->phi[1], c->phi[0], ng * 8, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemsetAsync(c->y, 0, ng * 8, st));
-    CK(launch_forces(force_args(c, c->phi[0], 0, 0), c->fblocks, st));
+    r = enqueue_forces(c, force_args(c, c->phi[0], 0, 0), st);
+    if (r != MAZE_OK) return r;
     if (defer_status) return MAZE_OK;
     r = read_stats(c);
     if (r != MAZE_OK) return r;
@@ -1160,7 +1185,8 @@ maze_status maze_gather(maze_ctx* c) {
   CK(launch_ion_update(ion_args(c, 0, 0), c->stream));
   s = enqueue_cells(c);
   if (s != MAZE_OK) return s;
-  CK(launch_forces(force_args(c, c->phi[c->ik], 0, 0), c->fblocks, c->stream));
+  s = enqueue_forces(c, force_args(c, c->phi[c->ik], 0, 0), c->stream);
+  if (s != MAZE_OK) return s;
   s = read_stats(c);
   if (s != MAZE_OK) return s;
   return status_message(c);

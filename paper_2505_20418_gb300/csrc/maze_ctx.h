@@ -97,6 +97,8 @@ struct maze_ctx {
   // the split single-box step (mixed, one cluster): S8 on side_stream beside
   // the solve, joined before S7/S9
   double* pair_out = nullptr;
+  long long* pair_fix = nullptr;   // FP64 large boxes: per-ion pair sums of the once-per-pair kernel
+  double* gath = nullptr;          // ... and their gather sums
   cudaStream_t side_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // pinned staging of the per-ion host copies (standalone contexts, made on

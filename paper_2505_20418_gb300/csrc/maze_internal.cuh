@@ -143,6 +143,9 @@ struct ForceArgs {
   double* part;          // [gridDim][8] block partials
   unsigned* ticket;      // last-block ticket (self-resetting)
   double* pair_out;      // [n][4] pair sums per ion (the split step: S8 apart from S7/S9) or nullptr
+  long long* pair_fix;   // [n][4] pair sums per ion in 2^-40 fixed point (FP64, pairs once each), zero
+                         // before the pair kernel, cleared by the kernel that reads them; or nullptr
+  double* gath;          // [n][4] gather sums per ion (with pair_fix: written by the pair kernel)
   maze_stats* rec;
   const int* gate;       // 1: this step was skipped
 };
@@ -240,6 +243,10 @@ cudaError_t launch_io_out(const double* soa, double* aos, int n, const void* rec
 cudaError_t launch_cells(const CellArgs& a, cudaStream_t s);
 cudaError_t launch_forces(const ForceArgs& a, int blocks, cudaStream_t s);
 cudaError_t launch_pairs(const ForceArgs& a, cudaStream_t s);
+// S8 once per pair and S7 (FP64, a.pair_fix, a.gath), one block per cell;
+// then S9 one thread per ion.
+cudaError_t launch_pairs_half(const ForceArgs& a, cudaStream_t s);
+cudaError_t launch_finish_fix(const ForceArgs& a, cudaStream_t s);
 cudaError_t launch_cluster_front(const IonArgs& ia, const CellArgs& ca, const MixedArgs& ma, int cluster,
                                  cudaStream_t s);
 cudaError_t launch_gather_finish(const ForceArgs& a, int blocks, cudaStream_t s);
@@ -477,6 +484,14 @@ __device__ __forceinline__ unsigned long long warp_umax64(unsigned long long u) 
 __device__ __forceinline__ void warp_dsum_fix(double v, long long& S, int& E) {
   E = (int)__reduce_max_sync(0xffffffffu, (unsigned)dbl_exp(v));
   S = warp_isum(dbl_to_fix(v, E));
+}
+
+// The same, rounded once to a double (every lane gets it).
+__device__ __forceinline__ double warp_dsum(double v) {
+  long long S;
+  int E;
+  warp_dsum_fix(v, S, E);
+  return fix_to_dbl(S, E);
 }
 
 // Grid-wide reduction of K <= 4 values (sum, or max of non-negative values

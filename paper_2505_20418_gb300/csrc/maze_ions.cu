@@ -321,6 +321,39 @@ __global__ void __launch_bounds__(kForceThreads) k_gather_finish(ForceArgs a) {
   energy_reduce(a, acc);
 }
 
+// S8 with each pair once (Newton's third law), FP64, one block per cell.
+__global__ void __launch_bounds__(kForceThreads) k_pairs_half(ForceArgs a) {
+  __shared__ HalfSmem<kForceThreads / 32> sm;
+  if (forces_live(a)) pairs_half_cell<kForceThreads / 32>(a, blockIdx.x, sm);
+}
+
+cudaError_t launch_pairs_half(const ForceArgs& a, cudaStream_t s) {
+  k_pairs_half<<<a.nc * a.nc * a.nc, kForceThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// S9 after k_pairs_half, one thread per ion: the gather sums (a.gath) and
+// the fixed-point pair sums (a.pair_fix, cleared for the next step).
+__global__ void __launch_bounds__(kForceThreads) k_finish_fix(ForceArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  if (i < a.n) {
+    long long* pf = a.pair_fix + (size_t)i * 4;
+    if (forces_live(a)) {
+      const double* g = a.gath + (size_t)i * 4;
+      finish_ion(a, i, g[0], g[1], g[2], g[3], (double)pf[0] * kFixFInv, (double)pf[1] * kFixFInv,
+                 (double)pf[2] * kFixFInv, (double)pf[3] * kFixFInv, acc);
+    }
+    pf[0] = pf[1] = pf[2] = pf[3] = 0;   // never carried over to the next step
+  }
+  energy_reduce(a, acc);
+}
+
+cudaError_t launch_finish_fix(const ForceArgs& a, cudaStream_t s) {
+  k_finish_fix<<<(a.n + kForceThreads - 1) / kForceThreads, kForceThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pairs(const ForceArgs& a, cudaStream_t s) {
   k_pairs_cells<<<a.nc * a.nc * a.nc * a.cell_split, kForceThreads, 0, s>>>(a);
   return cudaGetLastError();

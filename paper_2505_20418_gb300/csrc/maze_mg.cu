@@ -33,7 +33,10 @@
 //    overwrites every red point without reading it);
 //  * maxima are integer maxima of IEEE bit patterns (no FP64 compare), and
 //    the mean of y is formed once, after the last V-cycle.
-// The grid is one 1024-thread block per SM, so every SM carries the same work.
+// Grids of 128^3 points and more run one 1024-thread block per SM, so every
+// SM carries the same work; smaller grids, whose phases give each thread
+// only a few points, run up to 256 blocks of 256 threads (the work and its
+// memory traffic spread over more SMs).
 #include <math.h>
 
 #include "maze_internal.cuh"
@@ -43,6 +46,9 @@ namespace maze {
 namespace {
 
 constexpr int kMgThreads = 1024;
+
+// Threads per block for a grid of n points (see the note at the top).
+int mg_threads(int n) { return n >= (1 << 21) ? kMgThreads : 256; }
 
 // Point of colour c (0 red, 1 black) with half-index h on an N^3 grid (N even):
 // h = t + (N/2)(j + N k), i = 2t + ((j + k + c) & 1). lg = log2 N for powers
@@ -304,9 +310,10 @@ int mg_blocks(int n_points) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mg_solve, kMgThreads, 0);
+  const int threads = mg_threads(n_points);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mg_solve, threads, 0);
   if (per_sm < 1) per_sm = 1;
-  int want = (n_points + kMgThreads - 1) / kMgThreads;
+  int want = (n_points + threads - 1) / threads;
   int cap = sms * per_sm;
   if (cap > kMaxReduceBlocks) cap = kMaxReduceBlocks;
   return want < cap ? want : cap;
@@ -315,7 +322,7 @@ int mg_blocks(int n_points) {
 cudaError_t launch_mg_solve(const SolveArgs& a, const MgArgs& g, int blocks, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
-  cfg.blockDim = dim3(kMgThreads);
+  cfg.blockDim = dim3(mg_threads(a.n));
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];

@@ -51,7 +51,7 @@ def test_cuda_arm_line():
     assert {d["roofline"]["bound"], d["roofline_other"]["bound"]} == {"hbm", "alu"}
     e = d["e2e"]
     assert e["h2d_bytes_per_step"] == 48 * 512000 and e["d2h_bytes_per_step"] > 48 * 512000
-    assert d["gpu_launches"] == 7 * steps          # move, spread, 3 cell-list kernels, solve, forces
+    assert d["gpu_launches"] == 8 * steps          # move, spread, 3 cell-list kernels, solve, pairs, gather
     assert d["clocks"]["sm_mhz"] > 0 and isinstance(d["clocks"]["reasons"], list)
     assert d["force_error"] < 1e-7                 # FP64 at tol 1e-10 (the solver tolerance dominates)
     assert d["ms_per_step"] > 0 and d["p99_us"] >= d["p50_us"] > 0

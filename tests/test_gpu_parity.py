@@ -297,3 +297,29 @@ def test_bounded_wait_gives_up_with_timeout(which):
     sim.step(2)
     assert sim.stats()["status"] == M.MAZE_OK
     sim.close()
+
+
+def test_once_per_pair_forces_parity_and_determinism():
+    """FP64 boxes with at least 2 cells per SM evaluate each Tosi-Fumi pair
+    once (Newton's third law) with fixed-point per-ion sums; the 8000-ion /
+    64^3 box (7^3 cells) takes that path: step 0 and one step against the
+    oracle at the FP64 bar, and two runs bit for bit equal."""
+    w = synth.workload("nacl8000")
+    pos, vel, types = synth.make_state(w)
+    tf = synth.tosi_fumi_nacl()
+    sims = [M.MazeSim(pos, vel, types, w.L, w.N, tf, r_cut=w.rc, dt=w.dt, tol=TOL, solver=M.MAZE_SOLVER_MG)
+            for _ in range(2)]
+    p = O.Params(L=w.L, N=w.N, dt=w.dt, tol=TOL, rc=w.rc, P=4, solver="mg")
+    st = O.init(pos, vel, types, p, tf)
+    assert force_err(sims[0].get(M.MAZE_FORCE), st.F) < FORCE_BAR
+    st = O.step(st, p, tf)
+    for s in sims:
+        s.step(1)
+    assert force_err(sims[0].get(M.MAZE_FORCE), st.F) < FORCE_BAR
+    assert abs(sims[0].stats()["v_tf"] - st.V_tf) < 1e-9 * abs(st.V_tf)
+    for s in sims:
+        s.step(3)
+    for what in (M.MAZE_POS, M.MAZE_VEL, M.MAZE_FORCE):
+        assert np.array_equal(sims[0].get(what), sims[1].get(what))
+    for s in sims:
+        s.close()
