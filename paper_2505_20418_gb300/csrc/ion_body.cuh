@@ -244,7 +244,7 @@ __device__ __forceinline__ void spread_ion(const IonArgs& a, int i, int lane) {
       v[u] = __float2ll_rn((float)Q * w[8 + ic] * w[4 + ib] * w[ia] * (float)kQScale);
     } else {
       const double* w = a.wbuf + (size_t)i * 12;
-      v[u] = __double2ll_rn(Q * w[8 + ic] * w[4 + ib] * w[ia] * kQScale);
+      v[u] = round_scaled(Q * w[8 + ic] * w[4 + ib] * w[ia], 50);   // 2^50 = kQScale
     }
     const int ix = wrap_idx(b.x + ia, N), iy = wrap_idx(b.y + ib, N), iz = wrap_idx(b.z + ic, N);
     idx[u] = (int)(((size_t)iz * N + iy) * N + ix);
@@ -1031,15 +1031,7 @@ constexpr double kFixFInv = 1.0 / 1099511627776.0;   // 2^-40
 // round(v * 2^40) as a 64-bit integer from v's bits, integer operations only
 // (the FP64 pipe's conversions are slow); |v| < 2^23, rounding half away
 // from zero, |v| < 2^-41 gives 0.
-__device__ __forceinline__ long long fix40(double v) {
-  const long long b = __double_as_longlong(v);
-  const int e = (int)((b >> 52) & 0x7ff);
-  if (e < 982) return 0;
-  const long long m = (b & 0xfffffffffffffLL) | (1LL << 52);
-  const int sh = 1035 - e;   // v 2^40 = m 2^(e - 1035)
-  const long long x = sh > 0 ? (m + (1LL << (sh - 1))) >> sh : m << (-sh);
-  return b < 0 ? -x : x;
-}
+__device__ __forceinline__ long long fix40(double v) { return round_scaled(v, 40); }
 constexpr int kHalfChunk = 384;
 constexpr int kHalfNbr = 14;                        // the cell itself and 13 neighbours
 template <int kW>

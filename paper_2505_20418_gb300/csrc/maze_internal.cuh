@@ -368,6 +368,19 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+// round(v * 2^S) as a 64-bit integer from v's bits, integer operations only
+// (GB300's FP64-pipe conversions take several issue slots each): rounding
+// half away from zero, 0 when |v 2^S| < 1/2; requires |v 2^S| < 2^62.
+__device__ __forceinline__ long long round_scaled(double v, int S) {
+  const long long b = __double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7ff);
+  const int sh = 1075 - S - e;   // v 2^S = m 2^(e - 1075 + S)
+  if (sh > 53) return 0;
+  const long long m = (b & 0xfffffffffffffLL) | (1LL << 52);
+  const long long x = sh > 0 ? (m + (1LL << (sh - 1))) >> sh : m << (-sh);
+  return b < 0 ? -x : x;
+}
+
 // Max-norm accumulation on the integer pipe: |v| as its IEEE bit pattern. For
 // non-negative doubles the integer order is the numeric order and every NaN
 // sorts above +inf, so a NaN entry is never dropped (fmax would drop it).
