@@ -45,7 +45,7 @@ from paper_2505_20418_gb300 import synth  # noqa: E402
 
 METRIC = "MaZe steps/s, solve GB/s vs HBM peak, p50/p99 step latency at stated force error"
 KERNELS_PER_STEP_CELLS = 7    # move, spread, 3 cell-list kernels, solve, forces
-KERNELS_PER_STEP_HALF = 8     # FP64, one force block per cell: ... solve, pairs once each, gather + finish
+KERNELS_PER_STEP_HALF = 8     # one force block per cell: ... solve, pairs once each + gather, finish
 KERNELS_PER_STEP_NOCELLS = 4
 KERNELS_PER_STEP_FUSED = 2     # mixed precision up to 64^3, no cell list: S1-S6 in one cluster launch, the forces
 KERNELS_PER_STEP_SPLIT = 4     # mixed up to 64^3 with a cell list: S1-S3, S8 beside the solve, S7/S9
@@ -391,7 +391,7 @@ def solve_kernel_name(precision, solver, w):
 def kernels_per_step(precision, w, sms=152):
     if precision == "mixed" and w.N <= 64:
         return KERNELS_PER_STEP_SPLIT if has_cells(w) else KERNELS_PER_STEP_FUSED
-    if precision == "fp64" and has_cells(w) and int(np.floor(w.L / w.rc)) ** 3 >= 2 * sms:
+    if has_cells(w) and int(np.floor(w.L / w.rc)) ** 3 >= 2 * sms:   # FP64, or mixed above 64^3
         return KERNELS_PER_STEP_HALF
     return KERNELS_PER_STEP_CELLS if has_cells(w) else KERNELS_PER_STEP_NOCELLS
 

@@ -1192,4 +1192,181 @@ __device__ __forceinline__ void pairs_half_cell(const ForceArgs& a, int c, HalfS
   if (threadIdx.x == 0 && sm.bad) atomicCAS(&a.rec->status, MAZE_OK, MAZE_ERR_NONFINITE);
 }
 
+// round(v * 2^S) for an FP32 v, integer operations only (as round_scaled).
+__device__ __forceinline__ long long round_scaled_f(float v, int S) {
+  const int b = __float_as_int(v);
+  const int e = (b >> 23) & 0xff;
+  const int sh = 150 - S - e;   // v 2^S = m 2^(e - 150 + S)
+  if (sh > 24) return 0;
+  const long long m = (long long)((b & 0x7fffff) | 0x800000);
+  const long long x = sh > 0 ? (m + (1LL << (sh - 1))) >> sh : m << (-sh);
+  return b < 0 ? -x : x;
+}
+
+// The mixed-precision form of pairs_half_cell (boxes above 64^3, which run
+// one at a time): candidates staged as cell-relative hi + lo floats with the
+// neighbour cell's offset folded in by TwoSum, displacements as exact FP32
+// sums, the pair arithmetic in FP32; the same once-per-pair bookkeeping with
+// 2^-40 fixed-point sums, and the FP32 gather of the cell's ions.
+template <int kW>
+struct HalfSmemF {
+  float4 h[kHalfChunk];                            // hi parts (offset folded), type in l.w
+  float4 l[kHalfChunk];
+  int j[kHalfChunk];
+  int slot[kHalfChunk];
+  unsigned long long acc[kHalfChunk][4];
+  int lo[kHalfNbr], cum[kHalfNbr + 1];
+  unsigned long long f[kCellGroup][4];
+  int queue[kW][64];
+  int bad;
+};
+
+template <int kW>
+__device__ __forceinline__ void pairs_half_cell_mixed(const ForceArgs& a, int c, HalfSmemF<kW>& sm) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nc = a.nc;
+  const int cx = c % nc, cy = (c / nc) % nc, cz = c / (nc * nc);
+  if (threadIdx.x < kHalfNbr) {
+    const int t = threadIdx.x == 0 ? 13 : (threadIdx.x - 1) + 14;
+    const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
+    const int cc = (cx + dx + nc) % nc + nc * ((cy + dy + nc) % nc + nc * ((cz + dz + nc) % nc));
+    sm.lo[threadIdx.x] = a.cell_start[cc];
+    sm.cum[threadIdx.x + 1] = a.cell_start[cc + 1] - a.cell_start[cc];
+  }
+  if (threadIdx.x == 0) sm.bad = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sm.cum[0] = 0;
+    for (int t = 0; t < kHalfNbr; ++t) sm.cum[t + 1] += sm.cum[t];
+  }
+  __syncthreads();
+  const int total = sm.cum[kHalfNbr];
+  const int self_end = sm.cum[1];
+  const int c0 = a.cell_start[c], cn = a.cell_start[c + 1] - c0;
+  bool bad = false;
+  for (int g0 = c0; g0 < c0 + cn; g0 += kCellGroup) {
+    const int gn = min(kCellGroup, c0 + cn - g0);
+    for (int e = threadIdx.x; e < gn * 4; e += blockDim.x) sm.f[e >> 2][e & 3] = 0ull;
+    for (int ch0 = 0; ch0 < total; ch0 += kHalfChunk) {
+      const int len = min(kHalfChunk, total - ch0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < len; e += blockDim.x) {
+        const int tt = ch0 + e;
+        int k = 0;
+        while (k + 1 < kHalfNbr && sm.cum[k + 1] <= tt) ++k;
+        const int slot = sm.lo[k] + (tt - sm.cum[k]);
+        const int t = k == 0 ? 13 : (k - 1) + 14;
+        const float ox = (float)(t % 3 - 1), oy = (float)((t / 3) % 3 - 1), oz = (float)(t / 9 - 1);
+        const float4 hh = a.rel_hi_sorted[slot], ll = a.rel_lo_sorted[slot];
+        // (rel + offset * cell_len) as hi + lo: TwoSum with the offset's hi part
+        const float sx = __fadd_rn(hh.x, ox * a.cell_len_h), sy = __fadd_rn(hh.y, oy * a.cell_len_h),
+                    sz = __fadd_rn(hh.z, oz * a.cell_len_h);
+        const float bx = __fsub_rn(sx, hh.x), by = __fsub_rn(sy, hh.y), bz = __fsub_rn(sz, hh.z);
+        const float ex = __fadd_rn(__fsub_rn(hh.x, __fsub_rn(sx, bx)), __fsub_rn(ox * a.cell_len_h, bx));
+        const float ey = __fadd_rn(__fsub_rn(hh.y, __fsub_rn(sy, by)), __fsub_rn(oy * a.cell_len_h, by));
+        const float ez = __fadd_rn(__fsub_rn(hh.z, __fsub_rn(sz, bz)), __fsub_rn(oz * a.cell_len_h, bz));
+        sm.h[e] = make_float4(sx, sy, sz, hh.w);
+        sm.l[e] = make_float4(__fadd_rn(ex, __fadd_rn(ll.x, ox * a.cell_len_l)),
+                              __fadd_rn(ey, __fadd_rn(ll.y, oy * a.cell_len_l)),
+                              __fadd_rn(ez, __fadd_rn(ll.z, oz * a.cell_len_l)), ll.w);
+        sm.j[e] = a.cell_ions[slot];
+        sm.slot[e] = tt < self_end ? slot : 0x7fffffff;
+        sm.acc[e][0] = sm.acc[e][1] = sm.acc[e][2] = sm.acc[e][3] = 0ull;
+      }
+      __syncthreads();
+      for (int gi = warp; gi < gn; gi += kW) {
+        const int islot = g0 + gi;
+        const float4 ph = a.rel_hi_sorted[islot], pl = a.rel_lo_sorted[islot];
+        const int ti = (int)pl.w;
+        int* q = sm.queue[warp];
+        int qn = 0;
+        float sfx = 0.f, sfy = 0.f, sfz = 0.f, sv = 0.f;
+        auto eval = [&](int e2) {
+          const float4 h = sm.h[e2], l = sm.l[e2];
+          const float dx = disp_df(ph.x, pl.x, h.x, l.x, 0.f, 0.f);
+          const float dy = disp_df(ph.y, pl.y, h.y, l.y, 0.f, 0.f);
+          const float dz = disp_df(ph.z, pl.z, h.z, l.z, 0.f, 0.f);
+          const float r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 >= a.rc2f) return;
+          const int kind = ti + (int)l.w;
+          const float ir = rsqrtf(r2);
+          const float r = r2 * ir;
+          const float ir2 = ir * ir;
+          const float ir6 = ir2 * ir2 * ir2;
+          const float ir8 = ir6 * ir2;
+          const float exv = a.Af[kind] * expf(a.Bf * (a.sf[kind] - r));
+          const float V = exv - a.Cf[kind] * ir6 - a.Df[kind] * ir8 - a.Vcf[kind];
+          const float fr = a.Bf * exv * ir - 6.f * a.Cf[kind] * ir8 - 8.f * a.Df[kind] * ir8 * ir2;
+          const float fx = fr * dx, fy = fr * dy, fz = fr * dz;
+          sfx -= fx;
+          sfy -= fy;
+          sfz -= fz;
+          sv += V;
+          atomicAdd(&sm.acc[e2][0], (unsigned long long)round_scaled_f(fx, 40));
+          atomicAdd(&sm.acc[e2][1], (unsigned long long)round_scaled_f(fy, 40));
+          atomicAdd(&sm.acc[e2][2], (unsigned long long)round_scaled_f(fz, 40));
+          atomicAdd(&sm.acc[e2][3], (unsigned long long)round_scaled_f(V, 40));
+        };
+        for (int e0 = 0; e0 < len; e0 += 32) {
+          const int e = e0 + lane;
+          bool pass = false;
+          if (e < len && sm.slot[e] > islot) {
+            const float4 h = sm.h[e];
+            const float dx = h.x - ph.x, dy = h.y - ph.y, dz = h.z - ph.z;
+            const float r2f = dx * dx + dy * dy + dz * dz;
+            pass = r2f < a.rc2_filter;
+            bad = bad || r2f < 0.25f;
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, pass);
+          if (pass) q[qn + __popc(m & ((1u << lane) - 1u))] = e;
+          qn += __popc(m);
+          __syncwarp();
+          if (qn >= 32) {
+            eval(q[lane]);
+            __syncwarp();
+            if (lane < qn - 32) q[lane] = q[32 + lane];
+            __syncwarp();
+            qn -= 32;
+          }
+        }
+        if (lane < qn) eval(q[lane]);
+        __syncwarp();
+        // each lane's FP32 sums to fixed point, an exact integer warp sum
+        const long long tx = warp_isum(round_scaled_f(sfx, 40)), ty = warp_isum(round_scaled_f(sfy, 40)),
+                        tz = warp_isum(round_scaled_f(sfz, 40)), tv = warp_isum(round_scaled_f(sv, 40));
+        if (lane == 0) {
+          sm.f[gi][0] += (unsigned long long)tx;
+          sm.f[gi][1] += (unsigned long long)ty;
+          sm.f[gi][2] += (unsigned long long)tz;
+          sm.f[gi][3] += (unsigned long long)tv;
+        }
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < len * 4; e += blockDim.x) {
+        const unsigned long long v = sm.acc[e >> 2][e & 3];
+        if (v) atomicAdd(reinterpret_cast<unsigned long long*>(a.pair_fix) + (size_t)sm.j[e >> 2] * 4 + (e & 3), v);
+      }
+    }
+    for (int gi = warp; gi < gn; gi += kW) {
+      const int i = a.cell_ions[g0 + gi];
+      double gx, gy, gz, vd;
+      gather_el(a, i, lane, gx, gy, gz, vd);
+      if (lane == 0) {
+        a.gath[(size_t)i * 4] = gx;
+        a.gath[(size_t)i * 4 + 1] = gy;
+        a.gath[(size_t)i * 4 + 2] = gz;
+        a.gath[(size_t)i * 4 + 3] = vd;
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < gn * 4; e += blockDim.x)
+      atomicAdd(reinterpret_cast<unsigned long long*>(a.pair_fix) + (size_t)a.cell_ions[g0 + (e >> 2)] * 4 + (e & 3),
+                sm.f[e >> 2][e & 3]);
+  }
+  if (bad) atomicOr(&sm.bad, 1);
+  __syncthreads();
+  if (threadIdx.x == 0 && sm.bad) atomicCAS(&a.rec->status, MAZE_OK, MAZE_ERR_NONFINITE);
+}
+
 }  // namespace maze

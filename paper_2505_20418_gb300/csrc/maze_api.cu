@@ -897,9 +897,12 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
     AL(c->ticket, ngroups + 4);
     c->ticket_count = ngroups + 4;
   }
-  // FP64 boxes whose forces run one block per cell: the pairs once each
-  // (Newton's third law) in their own kernel, then the gather and finish
-  if (!c->mixed && c->nc >= 3 && c->reach == 1 && c->ncell >= 2 * c->num_sms) {
+  // boxes whose forces run one block per cell, FP64 or mixed above 64^3
+  // (mixed boxes up to 64^3 take the split step, and only those run in
+  // batches): the pairs once each (Newton's third law) in their own kernel
+  // with the gather, then the finish
+  if (c->nc >= 3 && c->reach == 1 && c->ncell >= 2 * c->num_sms && !arena && !c->split_step &&
+      (!c->mixed || c->N > 64)) {
     AL(c->pair_fix, 4 * (size_t)n);
     AL(c->gath, 4 * (size_t)n);
   }

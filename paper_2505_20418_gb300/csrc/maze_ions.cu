@@ -327,8 +327,17 @@ __global__ void __launch_bounds__(kForceThreads) k_pairs_half(ForceArgs a) {
   if (forces_live(a)) pairs_half_cell<kForceThreads / 32>(a, blockIdx.x, sm);
 }
 
+// The mixed-precision form (FP32 pair arithmetic on hi + lo positions).
+__global__ void __launch_bounds__(kForceThreads) k_pairs_half_mixed(ForceArgs a) {
+  __shared__ HalfSmemF<kForceThreads / 32> sm;
+  if (forces_live(a)) pairs_half_cell_mixed<kForceThreads / 32>(a, blockIdx.x, sm);
+}
+
 cudaError_t launch_pairs_half(const ForceArgs& a, cudaStream_t s) {
-  k_pairs_half<<<a.nc * a.nc * a.nc, kForceThreads, 0, s>>>(a);
+  if (a.mixed)
+    k_pairs_half_mixed<<<a.nc * a.nc * a.nc, kForceThreads, 0, s>>>(a);
+  else
+    k_pairs_half<<<a.nc * a.nc * a.nc, kForceThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 

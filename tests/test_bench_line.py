@@ -57,5 +57,5 @@ def test_cuda_arm_line():
     assert d["ms_per_step"] > 0 and d["p99_us"] >= d["p50_us"] > 0
     m = d["mixed"]
     assert m["steps_per_s"] > d["value"] and m["force_error"] < 1e-5
-    assert m["roofline"]["bound"] == "hbm" and m["gpu_launches"] == 7 * steps
+    assert m["roofline"]["bound"] == "hbm" and m["gpu_launches"] == 8 * steps
     assert d["cpu_baseline_all_cores"]["cores"] >= 1

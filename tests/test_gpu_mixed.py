@@ -149,3 +149,32 @@ def test_mixed_energies_against_the_oracle():
     assert abs(s["v_work"] - e["v_work"]) <= MIXED_BAR * (e["ke"] + abs(e["v_tf"]))
     assert s["resid"] < p.tol and st.resid < p.tol
     sim.close()
+
+
+def test_mixed_once_per_pair_forces_large_box():
+    """Mixed-precision boxes above 64^3 evaluate each Tosi-Fumi pair once
+    (FP32 arithmetic, fixed-point per-ion sums): the 64000-ion / 128^3 box,
+    sampled ions against the oracle's gather on the GPU's potential plus
+    brute-force pairs, within the mixed bar; two runs bit for bit equal."""
+    w = synth.workload("nacl64000")
+    pos, vel, types = synth.make_state(w)
+    tf = synth.tosi_fumi_nacl()
+    sims = [M.MazeSim(pos, vel, types, w.L, w.N, tf, r_cut=w.rc, dt=w.dt, tol=w.tol, solver=M.MAZE_SOLVER_MG,
+                      precision=M.MAZE_MIXED) for _ in range(2)]
+    for s in sims:
+        s.step(2)
+    st = sims[0].stats()
+    assert st["status"] == 0 and st["resid"] < w.tol
+    x = sims[0].get(M.MAZE_POS)
+    phi = sims[0].get(M.MAZE_PHI)
+    F = sims[0].get(M.MAZE_FORCE)
+    Q = np.where(types == 0, 1.0, -1.0)
+    idx = np.random.default_rng(11).choice(len(x), 48, replace=False)
+    Fo = O.gather_forces(x[idx], Q[idx], phi, w.L, w.N, 4) + O.tf_forces_on(idx, x, types, w.L, tf, w.rc)
+    scale = np.sqrt((F ** 2).sum(1).mean())
+    err = np.linalg.norm(F[idx] - Fo, axis=1) / np.maximum(np.linalg.norm(Fo, axis=1), scale)
+    assert err.max() < MIXED_BAR
+    for what in (M.MAZE_POS, M.MAZE_VEL, M.MAZE_FORCE):
+        assert np.array_equal(sims[0].get(what), sims[1].get(what))
+    for s in sims:
+        s.close()
