@@ -374,6 +374,17 @@ def measured_traffic(workload, kernel, precision, solver):
     return None if hit is None else hit[0]
 
 
+# The arithmetic each --precision computes in: FP64; FP64 state with the
+# multigrid corrections in exact 64-bit integers; FP32 grid arithmetic with
+# double-float (FP32 pair) outer vectors.
+DTYPES = {"fp64": "f64", "fp64fix": "f64+i64", "mixed": "f32+f32x2"}
+
+
+def precision_code(M, precision):
+    """The C ABI's precision constant for a --precision name."""
+    return {"fp64": M.MAZE_FP64, "mixed": M.MAZE_MIXED, "fp64fix": M.MAZE_FP64_FIXMG}[precision]
+
+
 def has_cells(w):
     """True when the box takes the cell list (at least 3 cells of r_cut a side)."""
     return int(np.floor(w.L / w.rc)) >= 3
@@ -385,6 +396,8 @@ def solve_kernel_name(precision, solver, w):
         if w.N > 64:
             return "k_mixed_grid"
         return "k_mixed_cluster" if has_cells(w) else "k_cluster_step"
+    if precision == "fp64fix":
+        return "k_mgfix_solve"
     return "k_mg_solve" if solver == "mg" else "k_cg_solve"
 
 
@@ -429,7 +442,7 @@ def time_box(args, M, w, precision, solver, stream, flush, dist=None, dev="cpu",
     tf = synth.tosi_fumi_nacl()
     sim = M.MazeSim(pos, vel, types, w.L, w.N, tf, r_cut=w.rc, dt=w.dt, tol=w.tol, order=w.order,
                     solver=M.MAZE_SOLVER_MG if solver == "mg" else M.MAZE_SOLVER_CG,
-                    precision=M.MAZE_MIXED if precision == "mixed" else M.MAZE_FP64, stream=stream.cuda_stream)
+                    precision=precision_code(M, precision), stream=stream.cuda_stream)
     sim.set_timing(True)
     for _ in range(args.warmup):
         sim.step_async(1)
@@ -541,7 +554,7 @@ def main():
     ap.add_argument("--boxes", type=int, default=128, help="batch128: number of replica boxes")
     ap.add_argument("--cluster-ctas", type=int, default=0, help="batch128: CTAs per box (0: autotune)")
     ap.add_argument("--solver", default="mg", choices=["cg", "mg"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "fp64fix"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision run beside an FP64 line")
@@ -604,7 +617,7 @@ def main():
             "metric": METRIC, "value": head["steps_per_s"], "unit": "steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f32x2",
+            "vs_baseline": None, "dtype": DTYPES[args.precision],
             "data": "synthetic", "config": config_dict(w, args),
             "p50_us": 1e3 * float(np.percentile(head["step_ms"], 50)),
             "p99_us": 1e3 * float(np.percentile(head["step_ms"], 99)),

@@ -56,7 +56,7 @@ typedef enum {
 } maze_status;
 
 enum { MAZE_SOLVER_CG = 0, MAZE_SOLVER_MG = 1 };
-enum { MAZE_FP64 = 0, MAZE_MIXED = 1 };
+enum { MAZE_FP64 = 0, MAZE_MIXED = 1, MAZE_FP64_FIXMG = 2 };
 /* How a step obtains phi^{k+1} (Sec. III.A compares the three):
  *  MAZE_SCHEME_MAZE          SHAKE: phi_p = 2 phi^k - phi^{k-1}, solve M y = sigma_p
  *                            from the previous step's y (Eqs. SHAKE-SHAKEPhiFinal)
@@ -104,7 +104,13 @@ enum { MAZE_FORCE_CD = 0, MAZE_FORCE_GRADW = 1 };
  * mg_pre/post red-black Gauss-Seidel sweeps before/after the coarse correction
  * order_P     assignment order: 2 (linear B-spline over the 8 nearest points)
  *             or 4 (cubic B-spline over 4^3 points), Sec. II.A
- * precision   MAZE_FP64, or MAZE_MIXED (FP32 grid arithmetic, FP64 reductions)
+ * precision   MAZE_FP64; MAZE_MIXED (FP32 grid arithmetic, FP64 reductions);
+ *             or MAZE_FP64_FIXMG (with MAZE_SOLVER_MG only): FP64 state and
+ *             FP64 S4/S6, each V-cycle an FP64 defect correction whose
+ *             correction is computed in exact 64-bit integers (units of a
+ *             power-of-two scale set from the residual), the residual of the
+ *             applied corrections tracked exactly; in exact arithmetic the
+ *             same iterates as MAZE_FP64
  * scheme      MAZE_SCHEME_* above (0 = MaZe)
  * force_estimator  MAZE_FORCE_* above (0 = Eq. F_nostra)
  * langevin_gamma   friction gamma (1/fs) of the OVRVO Langevin integrator
@@ -452,6 +458,19 @@ const char* maze_version(void);
  * stream). Returns MAZE_ERR_INVALID for another `which`, MAZE_ERR_CUDA when
  * the launch or a copy fails, else MAZE_OK. */
 maze_status maze_wait_probe(int32_t which, void* cuda_stream, int32_t* status_out);
+
+/* Diagnostic: the FP32/FP64 conversions that the FP64 kernels perform on the
+ * integer pipe (GB300's conversion instructions occupy the FP64 pipe), beside
+ * the conversion instructions, for n host doubles in[]: f_own/f_hw = in
+ * rounded to FP32 (nearest even); d_own/d_hw = f_hw widened back to FP64;
+ * floor_own/floor_hw = floor(in) as a 64-bit integer (0 where |in| >= 4e18);
+ * fix_own/fix_hw = the integer trunc(in 2^20) times 2^-20 as a double (0
+ * where |in| >= 4e18). Every array has n elements, host memory, owned by the
+ * caller. The call allocates, copies and synchronises on the legacy default
+ * stream. Returns MAZE_ERR_INVALID for n < 0 or a NULL array, MAZE_ERR_CUDA
+ * when a CUDA call fails, else MAZE_OK. */
+maze_status maze_convert_probe(const double* in, int32_t n, float* f_own, float* f_hw, double* d_own, double* d_hw,
+                               int64_t* floor_own, int64_t* floor_hw, double* fix_own, double* fix_hw);
 
 #ifdef __cplusplus
 }

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmaze.so")
-SOURCES = ["maze_api.cu", "maze_ions.cu", "maze_solve.cu", "maze_mg.cu", "maze_mixed.cu", "maze_noalloc.cu",
+SOURCES = ["maze_api.cu", "maze_ions.cu", "maze_solve.cu", "maze_mg.cu", "maze_mgfix.cu", "maze_mixed.cu", "maze_noalloc.cu",
            "maze_batch.cu", "maze_waits.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

@@ -15,8 +15,8 @@ namespace maze {
 // P = 4: cubic B-spline ((1-t)^3, 3t^3 - 6t^2 + 4, -3t^3 + 3t^2 + 3t + 1, t^3) / 6.
 // Split u into the first support node and the fractional offset t.
 __device__ __forceinline__ int axis_split(double u, int P, int N, double& t) {
-  const double fl = floor(u);
-  t = u - fl;
+  const long long fl = floor_ll(u);   // (integer pipe; |u| < 2N)
+  t = u - fix_to_dbl(fl, 1075);
   int first = (int)fl - (P / 2 - 1);
   if (first < 0) first += N;
   if (first >= N) first -= N;
@@ -102,7 +102,8 @@ __device__ __forceinline__ void o_step(const LangevinArgs& o, int i, int t, unsi
 }
 
 __device__ __forceinline__ double wrap_pos(double x, double L, double inv_L) {
-  x -= L * floor(x * inv_L);
+  const long long k = floor_ll(x * inv_L);   // (integer pipe; 0 for a position already in the box)
+  if (k != 0) x -= L * fix_to_dbl(k, 1075);
   if (x < 0.0) x += L;
   if (x >= L) x -= L;
   return x;
@@ -154,13 +155,13 @@ __device__ __forceinline__ void move_ion(const IonArgs& a, int i) {
       atomicCAS(&a.rec->status, MAZE_OK, MAZE_ERR_NONFINITE);
     }
     const double Q = t ? a.charge1 : a.charge0;
-    a.pos32[i] = make_float4((float)x, (float)y, (float)z, (float)Q);
+    a.pos32[i] = make_float4(dbl_to_flt(x), dbl_to_flt(y), dbl_to_flt(z), dbl_to_flt(Q));
     int cx = 0, cy = 0, cz = 0;
     if (a.nc >= 3) {
       const double cs = a.cell_scale;
-      cx = min((int)(x * cs), a.nc - 1);
-      cy = min((int)(y * cs), a.nc - 1);
-      cz = min((int)(z * cs), a.nc - 1);
+      cx = min((int)floor_ll(x * cs), a.nc - 1);   // (x >= 0: floor = truncation)
+      cy = min((int)floor_ll(y * cs), a.nc - 1);
+      cz = min((int)floor_ll(z * cs), a.nc - 1);
       const int c = cx + a.nc * (cy + a.nc * cz);
       a.cell_of[i] = c;
       atomicAdd(&a.cell_count[c], 1);
@@ -169,9 +170,10 @@ __device__ __forceinline__ void move_ion(const IonArgs& a, int i) {
       // position relative to the own cell's corner as a (hi, lo) float pair:
       // pair displacements then need no FP64 arithmetic (mixed precision)
       const double rx = x - cx * a.cell_len, ry = y - cy * a.cell_len, rz = z - cz * a.cell_len;
-      const float hx = (float)rx, hy = (float)ry, hz = (float)rz;
-      a.rel_hi[i] = make_float4(hx, hy, hz, (float)Q);
-      a.rel_lo[i] = make_float4((float)(rx - hx), (float)(ry - hy), (float)(rz - hz), (float)t);
+      const float hx = dbl_to_flt(rx), hy = dbl_to_flt(ry), hz = dbl_to_flt(rz);
+      a.rel_hi[i] = make_float4(hx, hy, hz, dbl_to_flt(Q));
+      a.rel_lo[i] = make_float4(dbl_to_flt(rx - flt_to_dbl(hx)), dbl_to_flt(ry - flt_to_dbl(hy)),
+                                dbl_to_flt(rz - flt_to_dbl(hz)), (float)t);
     }
     double tx, ty, tz;
     const int fx = axis_split(x * a.inv_h, P, N, tx);
@@ -180,17 +182,17 @@ __device__ __forceinline__ void move_ion(const IonArgs& a, int i) {
     if (a.wbuf32) {
       // mixed precision: FP32 weights from the exact fractional offsets
       float w[12];
-      bspline_weights<float>((float)tx, P, w);
-      bspline_weights<float>((float)ty, P, w + 4);
-      bspline_weights<float>((float)tz, P, w + 8);
+      bspline_weights<float>(dbl_to_flt(tx), P, w);
+      bspline_weights<float>(dbl_to_flt(ty), P, w + 4);
+      bspline_weights<float>(dbl_to_flt(tz), P, w + 8);
       float4* gw = reinterpret_cast<float4*>(a.wbuf32 + (size_t)i * 12);
       gw[0] = make_float4(w[0], w[1], w[2], w[3]);
       gw[1] = make_float4(w[4], w[5], w[6], w[7]);
       gw[2] = make_float4(w[8], w[9], w[10], w[11]);
       if (a.wdbuf32) {
-        bspline_dweights<float>((float)tx, P, w);
-        bspline_dweights<float>((float)ty, P, w + 4);
-        bspline_dweights<float>((float)tz, P, w + 8);
+        bspline_dweights<float>(dbl_to_flt(tx), P, w);
+        bspline_dweights<float>(dbl_to_flt(ty), P, w + 4);
+        bspline_dweights<float>(dbl_to_flt(tz), P, w + 8);
         float4* gd = reinterpret_cast<float4*>(a.wdbuf32 + (size_t)i * 12);
         gd[0] = make_float4(w[0], w[1], w[2], w[3]);
         gd[1] = make_float4(w[4], w[5], w[6], w[7]);
@@ -241,7 +243,7 @@ __device__ __forceinline__ void spread_ion(const IonArgs& a, int i, int lane) {
     if (a.wbuf32) {
       // mixed precision: FP32 products
       const float* w = a.wbuf32 + (size_t)i * 12;
-      v[u] = __float2ll_rn((float)Q * w[8 + ic] * w[4 + ib] * w[ia] * (float)kQScale);
+      v[u] = round_scaled_f(dbl_to_flt(Q) * w[8 + ic] * w[4 + ib] * w[ia], 50);   // 2^50 = kQScale
     } else {
       const double* w = a.wbuf + (size_t)i * 12;
       v[u] = round_scaled(Q * w[8 + ic] * w[4 + ib] * w[ia], 50);   // 2^50 = kQScale
@@ -344,7 +346,7 @@ __device__ __forceinline__ void tf_pair(const ForceArgs& a, int kind, double r2,
   // 1/r by Newton-Raphson for the reciprocal square root, y <- y (3 - r2 y^2)/2,
   // from an FP32 seed (two steps: ~2^-22 -> 2^-44 -> FP64 rounding), so no FP64
   // square root or division is needed.
-  double ir = (double)rsqrtf((float)r2);
+  double ir = flt_to_dbl(rsqrtf(dbl_to_flt(r2)));   // conversions on the integer pipe
   ir = ir * (1.5 - 0.5 * r2 * ir * ir);
   ir = ir * (1.5 - 0.5 * r2 * ir * ir);
   const double r = r2 * ir;
@@ -368,9 +370,9 @@ __device__ __forceinline__ void pair_add(const ForceArgs& a, int ti, double x, d
                                          int tj, float4 pj, double xj, double yj, double zj, PairSum& ps) {
   const float iL = a.inv_Lf;
   const float sx = rintf((pj.x - pi32.x) * iL), sy = rintf((pj.y - pi32.y) * iL), sz = rintf((pj.z - pi32.z) * iL);
-  const double ddx = (xj - x) - (double)sx * a.L;
-  const double ddy = (yj - y) - (double)sy * a.L;
-  const double ddz = (zj - z) - (double)sz * a.L;
+  const double ddx = (xj - x) - flt_to_dbl(sx) * a.L;
+  const double ddy = (yj - y) - flt_to_dbl(sy) * a.L;
+  const double ddz = (zj - z) - flt_to_dbl(sz) * a.L;
   const int kind = ti + tj;
   const double r2 = ddx * ddx + ddy * ddy + ddz * ddz;
   if (r2 >= a.rc2) return;
@@ -482,9 +484,9 @@ __device__ __forceinline__ void gather_el(const ForceArgs& a, int i, int lane, d
         sz += __shfl_xor_sync(0xffffffffu, sz, o);
         s0 += __shfl_xor_sync(0xffffffffu, s0, o);
       }
-      gx = 2.0 * (double)sx;
-      gy = 2.0 * (double)sy;
-      gz = 2.0 * (double)sz;
+      gx = 2.0 * flt_to_dbl(sx);
+      gy = 2.0 * flt_to_dbl(sy);
+      gz = 2.0 * flt_to_dbl(sz);
       vd = s0;
     } else {
       const double* w = a.wbuf + (size_t)i * 12;
@@ -496,7 +498,7 @@ __device__ __forceinline__ void gather_el(const ForceArgs& a, int i, int lane, d
         double ph;
         if (a.phi_df) {
           const float2 c0 = reinterpret_cast<const float2*>(a.phi)[at];
-          ph = (double)c0.x + (double)c0.y;
+          ph = flt_to_dbl(c0.x) + flt_to_dbl(c0.y);
         } else {
           ph = a.phi[at];
         }
@@ -562,10 +564,10 @@ __device__ __forceinline__ void gather_el(const ForceArgs& a, int i, int lane, d
         // double-float potential: differences of the (hi, lo) pairs in FP32
         const float2* f = reinterpret_cast<const float2*>(a.phi);
         const float2 xp = f[ixp], xm = f[ixm], yp = f[iyp], ym = f[iym], zp = f[izp], zm = f[izm], c0 = f[row + ix];
-        px = (double)((xp.x - xm.x) + (xp.y - xm.y));
-        py = (double)((yp.x - ym.x) + (yp.y - ym.y));
-        pz = (double)((zp.x - zm.x) + (zp.y - zm.y));
-        p0 = (double)c0.x + (double)c0.y;
+        px = flt_to_dbl((xp.x - xm.x) + (xp.y - xm.y));
+        py = flt_to_dbl((yp.x - ym.x) + (yp.y - ym.y));
+        pz = flt_to_dbl((zp.x - zm.x) + (zp.y - zm.y));
+        p0 = flt_to_dbl(c0.x) + flt_to_dbl(c0.y);
       } else {
         const double* ph = a.phi;
         px = ph[ixp] - ph[ixm];
@@ -1026,7 +1028,6 @@ __device__ __forceinline__ void forces_cell_slice(const ForceArgs& a, int c, int
 // relative to the home cell (cells are at least r_cut wide, so for every
 // pair within r_cut that image is the minimum image, and any other pair is
 // at least r_cut apart in every image): no per-pair image arithmetic.
-constexpr double kFixFInv = 1.0 / 1099511627776.0;   // 2^-40
 
 // round(v * 2^40) as a 64-bit integer from v's bits, integer operations only
 // (the FP64 pipe's conversions are slow); |v| < 2^23, rounding half away
@@ -1049,6 +1050,7 @@ struct HalfSmem {
 
 template <int kW>
 __device__ __forceinline__ void pairs_half_cell(const ForceArgs& a, int c, HalfSmem<kW>& sm) {
+  const float Lf = dbl_to_flt(a.L);   // the box edge as FP32 (image shifts of the filter copies)
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int n = a.n, nc = a.nc;
@@ -1090,10 +1092,13 @@ __device__ __forceinline__ void pairs_half_cell(const ForceArgs& a, int c, HalfS
         const double shx = ox < 0 ? -a.L : (ox >= nc ? a.L : 0.0);
         const double shy = oy < 0 ? -a.L : (oy >= nc ? a.L : 0.0);
         const double shz = oz < 0 ? -a.L : (oz >= nc ? a.L : 0.0);
+        const float fx = ox < 0 ? -Lf : (ox >= nc ? Lf : 0.f);
+        const float fy = oy < 0 ? -Lf : (oy >= nc ? Lf : 0.f);
+        const float fz = oz < 0 ? -Lf : (oz >= nc ? Lf : 0.f);
         const float4 pj = a.pos_sorted[slot];
         sm.j[e] = j;
         sm.slot[e] = tt < self_end ? slot : 0x7fffffff;
-        sm.p[e] = make_float4(pj.x + (float)shx, pj.y + (float)shy, pj.z + (float)shz, pj.w);
+        sm.p[e] = make_float4(pj.x + fx, pj.y + fy, pj.z + fz, pj.w);
         sm.xyz[0][e] = a.pos[j] + shx;
         sm.xyz[1][e] = a.pos[n + j] + shy;
         sm.xyz[2][e] = a.pos[2 * n + j] + shz;
@@ -1190,17 +1195,6 @@ __device__ __forceinline__ void pairs_half_cell(const ForceArgs& a, int c, HalfS
   if (bad) atomicOr(&sm.bad, 1);
   __syncthreads();
   if (threadIdx.x == 0 && sm.bad) atomicCAS(&a.rec->status, MAZE_OK, MAZE_ERR_NONFINITE);
-}
-
-// round(v * 2^S) for an FP32 v, integer operations only (as round_scaled).
-__device__ __forceinline__ long long round_scaled_f(float v, int S) {
-  const int b = __float_as_int(v);
-  const int e = (b >> 23) & 0xff;
-  const int sh = 150 - S - e;   // v 2^S = m 2^(e - 150 + S)
-  if (sh > 24) return 0;
-  const long long m = (long long)((b & 0x7fffff) | 0x800000);
-  const long long x = sh > 0 ? (m + (1LL << (sh - 1))) >> sh : m << (-sh);
-  return b < 0 ? -x : x;
 }
 
 // The mixed-precision form of pairs_half_cell (boxes above 64^3, which run

@@ -88,8 +88,10 @@ maze_status validate(const maze_config* c) {
       return fail(MAZE_ERR_INVALID, "multigrid needs grid_N = m * 2^k with a coarsest edge m <= 8 (e.g. 32, 48, 56)");
   }
   if (c->order_P != 2 && c->order_P != 4) return fail(MAZE_ERR_INVALID, "order_P must be 2 or 4");
-  if (c->precision != MAZE_FP64 && c->precision != MAZE_MIXED)
-    return fail(MAZE_ERR_INVALID, "precision must be MAZE_FP64 or MAZE_MIXED");
+  if (c->precision != MAZE_FP64 && c->precision != MAZE_MIXED && c->precision != MAZE_FP64_FIXMG)
+    return fail(MAZE_ERR_INVALID, "precision must be MAZE_FP64, MAZE_MIXED or MAZE_FP64_FIXMG");
+  if (c->precision == MAZE_FP64_FIXMG && c->solver != MAZE_SOLVER_MG)
+    return fail(MAZE_ERR_INVALID, "precision MAZE_FP64_FIXMG runs the multigrid solver (MAZE_SOLVER_MG)");
   if (c->precision == MAZE_MIXED && c->solver != MAZE_SOLVER_MG)
     return fail(MAZE_ERR_INVALID, "precision MAZE_MIXED runs the multigrid solver (MAZE_SOLVER_MG)");
   if (c->scheme != MAZE_SCHEME_MAZE && c->scheme != MAZE_SCHEME_MG_STATIC && c->scheme != MAZE_SCHEME_MG_TIMEPROP)
@@ -360,7 +362,8 @@ maze_status enqueue_solve(maze_ctx* c, int zero_phi, double* q_out) {
     CK(launch_mixed_solve(mixed_args(c, zero_phi, q_out), c->mx_cluster, c->mx_blocks, c->stream));
   } else if (c->cfg.solver == MAZE_SOLVER_MG) {
     CK(cudaMemsetAsync(c->bar, 0, sizeof(unsigned), c->stream));
-    CK(launch_mg_solve(solve_args(c, zero_phi, q_out), c->mg, c->sblocks, c->stream));
+    if (c->fixmg) CK(launch_mgfix_solve(solve_args(c, zero_phi, q_out), c->mg, c->sblocks, c->stream));
+    else CK(launch_mg_solve(solve_args(c, zero_phi, q_out), c->mg, c->sblocks, c->stream));
   } else {
     CK(launch_cg_solve(solve_args(c, zero_phi, q_out), c->sblocks, c->stream));
   }
@@ -740,7 +743,10 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
   c->nc = (int)floor(c->L / cfg->r_cut);
   if (c->nc < 3) c->nc = 0;
   c->ncell = c->nc * c->nc * c->nc;
-  c->sblocks = cfg->solver == MAZE_SOLVER_MG ? mg_blocks((int)ng) : solve_blocks((int)ng);
+  c->fixmg = cfg->precision == MAZE_FP64_FIXMG;
+  c->sblocks = cfg->solver != MAZE_SOLVER_MG ? solve_blocks((int)ng)
+               : c->fixmg                    ? mgfix_blocks((int)ng)
+                                             : mg_blocks((int)ng);
   c->fblocks = force_blocks(n);
   if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) c->num_sms = 1;
   if (c->ncell > 0) {

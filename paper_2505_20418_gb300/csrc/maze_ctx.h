@@ -73,6 +73,7 @@ struct maze_ctx {
   double *mg_x = nullptr, *mg_b = nullptr, *mg_r = nullptr, *mg_g = nullptr;
   // mixed precision: phi, y, sigma hold double-float pairs (float2, 8 B)
   bool mixed = false;
+  bool fixmg = false;     // MAZE_FP64_FIXMG: the integer defect-correction V-cycle
   maze::MixedArgs mx = {};
   int mx_cluster = 0, mx_blocks = 0;
   bool fused_step = false;   // S1-S6 in one cluster launch (k_cluster_step)

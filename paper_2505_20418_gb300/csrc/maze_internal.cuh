@@ -187,9 +187,18 @@ struct MgArgs {
   double* x;               // corrections on levels >= 1 (level 0 uses y)
   double* b;               // right-hand sides, stored as -b/6, all levels (level 0: -sigma_p/6)
   double* r;               // residuals (at red points), all levels
+                           // (MAZE_FP64_FIXMG: x, b, r hold int64 in units of
+                           // 2^-F, b unscaled, level 0 of x is the correction e)
   const double* gker;      // [Nc^3] -6 times the pseudo-inverse kernel of the coarsest M
   int nu1, nu2;
 };
+
+// Threads per block of the cooperative multigrid kernels for a grid of n
+// points: grids of 128^3 points and more run one 1024-thread block per SM
+// (every SM carries the same work); smaller grids, whose phases give each
+// thread only a few points, run blocks of 256 threads over more SMs.
+constexpr int kMgThreads = 1024;
+inline int mg_threads(int n) { return n >= (1 << 21) ? kMgThreads : 256; }
 
 // Mixed-precision solve (double-float outer iteration, FP32 V-cycle).
 constexpr int kMixedClusterThreads = 512;   // one cluster per box
@@ -255,6 +264,8 @@ cudaError_t launch_cg_solve(const SolveArgs& a, int blocks, cudaStream_t s);
 int solve_blocks(int n_points);
 cudaError_t launch_mg_solve(const SolveArgs& a, const MgArgs& g, int blocks, cudaStream_t s);
 int mg_blocks(int n_points);
+cudaError_t launch_mgfix_solve(const SolveArgs& a, const MgArgs& g, int blocks, cudaStream_t s);
+int mgfix_blocks(int n_points);
 cudaError_t launch_mixed_solve(const MixedArgs& a, int cluster, int blocks, cudaStream_t s);
 int mixed_cluster_size();
 int cluster_step_size();
@@ -381,6 +392,17 @@ __device__ __forceinline__ long long round_scaled(double v, int S) {
   return b < 0 ? -x : x;
 }
 
+// round(v * 2^S) for an FP32 v, integer operations only (as round_scaled).
+__device__ __forceinline__ long long round_scaled_f(float v, int S) {
+  const int b = __float_as_int(v);
+  const int e = (b >> 23) & 0xff;
+  const int sh = 150 - S - e;   // v 2^S = m 2^(e - 150 + S)
+  if (sh > 24) return 0;
+  const long long m = (long long)((b & 0x7fffff) | 0x800000);
+  const long long x = sh > 0 ? (m + (1LL << (sh - 1))) >> sh : m << (-sh);
+  return b < 0 ? -x : x;
+}
+
 // Max-norm accumulation on the integer pipe: |v| as its IEEE bit pattern. For
 // non-negative doubles the integer order is the numeric order and every NaN
 // sorts above +inf, so a NaN entry is never dropped (fmax would drop it).
@@ -405,10 +427,18 @@ struct Nbr {
 
 __device__ __forceinline__ Nbr neighbours(int n, int N) {
   const int NN = N * N;
-  const int k = n / NN;
-  const int rem = n - k * NN;
-  const int j = rem / N;
-  const int i = rem - j * N;
+  int i, j, k;
+  if ((N & (N - 1)) == 0) {   // powers of two: shifts, not divisions
+    const int lg = __ffs(N) - 1;
+    i = n & (N - 1);
+    j = (n >> lg) & (N - 1);
+    k = n >> (2 * lg);
+  } else {
+    k = n / NN;
+    const int rem = n - k * NN;
+    j = rem / N;
+    i = rem - j * N;
+  }
   Nbr b;
   b.xm = (i == 0) ? n + N - 1 : n - 1;
   b.xp = (i == N - 1) ? n - N + 1 : n + 1;
@@ -417,6 +447,26 @@ __device__ __forceinline__ Nbr neighbours(int n, int N) {
   b.zm = (k == 0) ? n + NN * (N - 1) : n - NN;
   b.zp = (k == N - 1) ? n - NN * (N - 1) : n + NN;
   return b;
+}
+
+// Point of colour c (0 red, 1 black; red = i + j + k even) with half-index h
+// on an N^3 grid (N even): h = t + (N/2)(j + N k), i = 2t + ((j + k + c) & 1).
+// lg = log2 N for powers of two (shift decode), else -1.
+__device__ __forceinline__ void colour_point(int h, int N, int lg, int c, int& i, int& j, int& k) {
+  int row, t;
+  if (lg > 0) {
+    row = h >> (lg - 1);
+    t = h & ((N >> 1) - 1);
+    k = row >> lg;
+    j = row & (N - 1);
+  } else {
+    const int half = N >> 1;
+    row = h / half;
+    t = h - row * half;
+    k = row / N;
+    j = row - k * N;
+  }
+  i = 2 * t + ((j + k + c) & 1);
 }
 
 // Identity post step of grid_reduce.
@@ -505,6 +555,92 @@ __device__ __forceinline__ double warp_dsum(double v) {
   int E;
   warp_dsum_fix(v, S, E);
   return fix_to_dbl(S, E);
+}
+
+// FP32 <-> FP64 conversions on the integer pipe. On GB300 a conversion that
+// involves FP64 (F2F, I2F, F2I) occupies the FP64 pipe for many issue slots,
+// so the FP64 hot loops build the other format's bits instead.
+
+// v to FP32, rounding to nearest even (as the conversion instruction; FP32
+// subnormal results included, overflow to infinity, NaN kept).
+__device__ __forceinline__ float dbl_to_flt(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff);
+  const unsigned long long m = b & 0xfffffffffffffULL;
+  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (m ? 0x400000u : 0u));
+  const int ef = e - 1023 + 127;
+  int sh = 29;                                   // significand bits dropped
+  unsigned long long sig = m, base = (unsigned long long)(ef > 0 ? ef : 0) << 23;
+  if (ef <= 0) {                                 // FP32 subnormal (or zero)
+    if (e == 0 || ef < -24) return __uint_as_float(sign);
+    sig = m | (1ULL << 52);
+    sh = 30 - ef;
+  }
+  unsigned long long r = base | (sig >> sh);
+  const unsigned long long rem = sig & ((1ULL << sh) - 1), halfway = 1ULL << (sh - 1);
+  if (rem > halfway || (rem == halfway && (r & 1))) ++r;   // a carry moves into the exponent
+  if (r >= 0x7f800000ULL) r = 0x7f800000ULL;
+  return __uint_as_float(sign | (unsigned)r);
+}
+
+// f to FP64 (exact).
+__device__ __forceinline__ double flt_to_dbl(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+  const int e = (int)((b >> 23) & 0xff);
+  const unsigned long long m = b & 0x7fffffu;
+  if (e == 0xff) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ULL | (m << 29)));
+  if (e == 0) {
+    if (m == 0) return __longlong_as_double((long long)sign);
+    const int p = 31 - __clz((int)m);            // value m 2^-149 = 1.f 2^(p - 149)
+    return __longlong_as_double(
+        (long long)(sign | ((unsigned long long)(p - 149 + 1023) << 52) | ((m << (52 - p)) & 0xfffffffffffffULL)));
+  }
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(e - 127 + 1023) << 52) | (m << 29)));
+}
+
+// floor(v) as an integer for finite v with |v| < 2^62.
+__device__ __forceinline__ long long floor_ll(double v) {
+  const long long b = __double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  const bool neg = b < 0;
+  if (e < 0) return (neg && (b & 0x7fffffffffffffffLL)) ? -1 : 0;   // |v| < 1
+  const long long m = (b & 0xfffffffffffffLL) | (1LL << 52);
+  if (e >= 52) return neg ? -(m << (e - 52)) : (m << (e - 52));
+  const long long ip = m >> (52 - e);
+  const bool frac = (m & ((1LL << (52 - e)) - 1)) != 0;
+  return neg ? -(ip + (frac ? 1 : 0)) : ip;
+}
+
+// S4 at grid point m with periodic neighbours b (Eq. SHAKE): the charge q
+// (read from the fixed-point grid, which is cleared; converted on the integer
+// pipe, exact for |q| < 8), phi_p = 2 phi^k -
+// phi^{k-1} (phi^k for the direct scheme from the previous potential, 0 at
+// step 0) and sigma_p = (h/4pi) M phi_p + q. phi_p goes to phi_out, sigma_p
+// to sigma and is returned.
+__device__ __forceinline__ double shake_rhs(const SolveArgs& a, int m, const Nbr& b) {
+  const double q = fix_to_dbl((long long)a.qfix[m], 1075 - 50);   // qfix 2^-50, integer ops only
+  a.qfix[m] = 0ull;
+  if (a.q_out) a.q_out[m] = q;
+  double php = 0.0, Mphp = 0.0;
+  if (!a.zero_phi) {
+    const double* pk = a.phi_k;
+    const double* pm = a.phi_km1;
+    const double nk = (pk[b.xm] + pk[b.xp]) + (pk[b.ym] + pk[b.yp]) + (pk[b.zm] + pk[b.zp]);
+    if (a.static_guess) {
+      php = pk[m];
+      Mphp = fma(-6.0, php, nk);
+    } else {
+      php = fma(2.0, pk[m], -pm[m]);
+      const double nm = (pm[b.xm] + pm[b.xp]) + (pm[b.ym] + pm[b.yp]) + (pm[b.zm] + pm[b.zp]);
+      Mphp = fma(-6.0, php, fma(2.0, nk, -nm));
+    }
+  }
+  const double sg = fma(a.c_sig, Mphp, q);
+  a.phi_out[m] = php;
+  a.sigma[m] = sg;
+  return sg;
 }
 
 // Grid-wide reduction of K <= 4 values (sum, or max of non-negative values

@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_spread(IonArgs a) {
 
 __global__ void k_q_to_double(const unsigned long long* qfix, double* q, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) q[i] = (double)(long long)qfix[i] * kQInv;
+  if (i < n) q[i] = fix_to_dbl((long long)qfix[i], 1075 - 50);   // qfix 2^-50
 }
 
 cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t s) {
@@ -350,8 +350,9 @@ __global__ void __launch_bounds__(kForceThreads) k_finish_fix(ForceArgs a) {
     long long* pf = a.pair_fix + (size_t)i * 4;
     if (forces_live(a)) {
       const double* g = a.gath + (size_t)i * 4;
-      finish_ion(a, i, g[0], g[1], g[2], g[3], (double)pf[0] * kFixFInv, (double)pf[1] * kFixFInv,
-                 (double)pf[2] * kFixFInv, (double)pf[3] * kFixFInv, acc);
+      // 2^-40 units to doubles on the integer pipe
+      finish_ion(a, i, g[0], g[1], g[2], g[3], fix_to_dbl(pf[0], 1075 - 40), fix_to_dbl(pf[1], 1075 - 40),
+                 fix_to_dbl(pf[2], 1075 - 40), fix_to_dbl(pf[3], 1075 - 40), acc);
     }
     pf[0] = pf[1] = pf[2] = pf[3] = 0;   // never carried over to the next step
   }

@@ -45,31 +45,6 @@ namespace maze {
 
 namespace {
 
-constexpr int kMgThreads = 1024;
-
-// Threads per block for a grid of n points (see the note at the top).
-int mg_threads(int n) { return n >= (1 << 21) ? kMgThreads : 256; }
-
-// Point of colour c (0 red, 1 black) with half-index h on an N^3 grid (N even):
-// h = t + (N/2)(j + N k), i = 2t + ((j + k + c) & 1). lg = log2 N for powers
-// of two (shift decode), else -1.
-__device__ __forceinline__ void colour_point(int h, int N, int lg, int c, int& i, int& j, int& k) {
-  int row, t;
-  if (lg > 0) {
-    row = h >> (lg - 1);
-    t = h & ((N >> 1) - 1);
-    k = row >> lg;
-    j = row & (N - 1);
-  } else {
-    const int half = N >> 1;
-    row = h / half;
-    t = h - row * half;
-    k = row / N;
-    j = row - k * N;
-  }
-  i = 2 * t + ((j + k + c) & 1);
-}
-
 // Sum of the six periodic neighbours of (i, j, k), in a fixed order. (No
 // pointer here is __restrict__: every vector is written in some phase of the
 // kernel, so none may be read through the non-coherent read-only path.)
@@ -116,26 +91,7 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_mg_solve(SolveArgs a, MgArgs 
     unsigned long long rmax = 0;
     for (int m = tid; m < n; m += stride) {
       const Nbr b = neighbours(m, N0);
-      const double q = (double)(long long)a.qfix[m] * kQInv;
-      a.qfix[m] = 0ull;
-      if (a.q_out) a.q_out[m] = q;
-      double php = 0.0, Mphp = 0.0;
-      if (!a.zero_phi) {
-        const double* pk = a.phi_k;
-        const double* pm = a.phi_km1;
-        const double nk = (pk[b.xm] + pk[b.xp]) + (pk[b.ym] + pk[b.yp]) + (pk[b.zm] + pk[b.zp]);
-        if (a.static_guess) {
-          php = pk[m];
-          Mphp = fma(-6.0, php, nk);
-        } else {
-          php = fma(2.0, pk[m], -pm[m]);
-          const double nm = (pm[b.xm] + pm[b.xp]) + (pm[b.ym] + pm[b.yp]) + (pm[b.zm] + pm[b.zp]);
-          Mphp = fma(-6.0, php, fma(2.0, nk, -nm));
-        }
-      }
-      const double sg = fma(a.c_sig, Mphp, q);
-      a.phi_out[m] = php;
-      a.sigma[m] = sg;
+      const double sg = shake_rhs(a, m, b);
       sig6[m] = sg * (-1.0 / 6.0);
       const double* y = a.y;
       const double My = fma(-6.0, y[m], (y[b.xm] + y[b.xp]) + (y[b.ym] + y[b.yp]) + (y[b.zm] + y[b.zp]));

@@ -1,0 +1,438 @@
+// S4-S6 of the MaZe step with the multigrid solver (Sec. III.A) at precision
+// MAZE_FP64_FIXMG: FP64 state, and V-cycles run as FP64 defect correction
+// whose corrections are computed in exact 64-bit integer arithmetic. One
+// cooperative persistent kernel.
+//
+// FP64, as in the FP64 kernel: phi, sigma_p, y; S4 (Eq. SHAKE); the residual
+// of the warm start r_0 = sigma_p - M y at every point; S6 (Eq.
+// SHAKEPhiFinal). Integer: V-cycle k solves M e = r_k for the correction of y
+// (y_{k+1} = y_k + e), every value of every level an integer multiple of
+// 2^-F_k. In exact arithmetic this is the FP64 kernel's V-cycle: red-black
+// Gauss-Seidel from y_k with right-hand side sigma_p, and from e = 0 with
+// right-hand side r_k, give the same iterate y_k + e (the update is affine),
+// and so do the restriction, the coarsest solve and the prolongation, which
+// are linear. The operators are those of the FP64 kernel: nu1 red-black
+// sweeps, 27-point full weighting of the residual (its 13 red points), the
+// exact zero-mean coarsest solve by the pseudo-inverse kernel, trilinear
+// prolongation, nu2 sweeps, the stopping test max |sigma_p - M y| < tol after
+// every V-cycle (Eqs. SHAKEy, res_poisson_maze).
+//
+// Why: GB300 issues FP64 at 2 operations per clock per SM, and a Gauss-Seidel
+// point update costs 6 of them, so the FP64 V-cycle is bound by the FP64 pipe.
+// The same update in 64-bit integers (adds, a shift, a multiply-high for the
+// division by 6) runs on the integer pipes, and the V-cycle becomes bound by
+// HBM traffic.
+//
+// Exactness and range:
+//  * the residual is tracked exactly: after the last black half-sweep of a
+//    V-cycle a black point's residual is 6 e - (s - b) (s the six-neighbour
+//    sum; at most 3 units), and the convergence pass forms b - M e at red
+//    points; both are stored as the next V-cycle's right-hand side. The
+//    stopping test therefore sees the residual of the corrections actually
+//    applied; only the FP64 additions y += e 2^-F_k round.
+//  * a Gauss-Seidel update divides by 6 rounding half away from zero; the
+//    full weighting divides by 8 and the prolongation by 2 or 8, rounding
+//    half up. Each is half a unit of the correction, 2^-(H+1) of max |r_k|.
+//  * the scale: F_k makes max |r_k| 2^F_k fall in [2^(H-1), 2^H), H = 58 -
+//    2 ceil(log2 N). The correction is bounded by |M^+|_inf max |r_k| and
+//    |M^+|_inf is about 0.048 N^2 (the h^2-scaled periodic Laplacian), so
+//    corrections stay below 2^54 and six-neighbour sums below 2^57. F never
+//    decreases, so the stored residual moves to the next scale by an exact
+//    left shift, applied where the level-0 right-hand side is read.
+//  * a coarsest correction of 2^58 units or more (a diverging solve) ends the
+//    solve with MAZE_ERR_NONFINITE instead of wrapping around.
+#include <math.h>
+
+#include "maze_internal.cuh"
+
+namespace maze {
+
+namespace {
+
+constexpr int kMaxScale = 1000;   // F stays within the range of 2^-F as a double
+
+__device__ __forceinline__ long long shl(long long v, int s) { return (long long)((unsigned long long)v << s); }
+
+__device__ __forceinline__ unsigned long long iabs(long long v) {
+  return v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+}
+
+// round(v / 6), half away from zero (|v| < 2^63 - 3).
+__device__ __forceinline__ long long div6(long long v) {
+  const long long q = (long long)((iabs(v) + 3ull) / 6ull);
+  return v < 0 ? -q : q;
+}
+
+// round(v / 2^k), half up.
+__device__ __forceinline__ long long div2k(long long v, int k) { return (v + (1LL << (k - 1))) >> k; }
+
+// Storage: every level but the coarsest keeps each vector split by colour,
+// the red points (i + j + k even) first, then the black, each in half-index
+// order h = t + (N/2)(j + N k) with i = 2t + ((j + k + c) & 1); a half-sweep
+// then reads only the other colour's array and writes its own, in unit
+// stride. The coarsest level (an edge of at most 8, possibly odd) is stored
+// in natural order i + N (j + N k).
+
+// (t, j, k) of half-index h on an edge N (lg = log2 N, or -1).
+__device__ __forceinline__ void half_decode(int h, int N, int lg, int& t, int& j, int& k) {
+  if (lg > 0) {
+    const int row = h >> (lg - 1);
+    t = h & ((N >> 1) - 1);
+    k = row >> lg;
+    j = row & (N - 1);
+  } else {
+    const int hN = N >> 1;
+    const int row = h / hN;
+    t = h - row * hN;
+    k = row / N;
+    j = row - k * N;
+  }
+}
+
+// Index of point (i, j, k) in a level's storage.
+__device__ __forceinline__ int store_index(int i, int j, int k, int N, bool split) {
+  if (!split) return i + N * (j + N * k);
+  return ((i + j + k) & 1) * ((N * N * N) >> 1) + (i >> 1) + (N >> 1) * (j + N * k);
+}
+
+// Sum of the six periodic neighbours of the point at half-index h = (t, j, k)
+// of parity p (i = 2t + p), all of the other colour, read from that colour's
+// array o: the two x-neighbours sit at h and h -+ 1 of o, the others at
+// h +- N/2 and h +- N^2/2. A fixed order.
+__device__ __forceinline__ long long nbr6s(const long long* o, int h, int t, int j, int k, int p, int N) {
+  const int hN = N >> 1, Sy = hN, Sz = hN * N;
+  const int hx = p ? (t == hN - 1 ? h - (hN - 1) : h + 1) : (t == 0 ? h + (hN - 1) : h - 1);
+  const int ym = j == 0 ? h + (N - 1) * Sy : h - Sy, yp = j == N - 1 ? h - (N - 1) * Sy : h + Sy;
+  const int zm = k == 0 ? h + (N - 1) * Sz : h - Sz, zp = k == N - 1 ? h - (N - 1) * Sz : h + Sz;
+  return (o[h] + o[hx]) + (o[ym] + o[yp]) + (o[zm] + o[zp]);
+}
+
+__device__ __forceinline__ int wrapi(int a, int N) { return a < 0 ? a + N : (a >= N ? a - N : a); }
+
+// One red-black half-sweep of colour c on a split level: x = round((s - b 2^sh) / 6).
+__device__ __forceinline__ void half_sweep_i(long long* x, const long long* b, int sh, int N, int lg, int c, int tid,
+                                             int stride) {
+  const int half = (N * N * N) >> 1;
+  long long* xc = x + c * half;
+  const long long* xo = x + (1 - c) * half;
+  const long long* bc = b + c * half;
+#pragma unroll 2
+  for (int h = tid; h < half; h += stride) {
+    int t, j, k;
+    half_decode(h, N, lg, t, j, k);
+    xc[h] = div6(nbr6s(xo, h, t, j, k, (j + k + c) & 1, N) - shl(bc[h], sh));
+  }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kMgThreads, 1) k_mgfix_solve(SolveArgs a, MgArgs g, int H) {
+  unsigned epoch = 0, bar_epoch = 0;
+  const int n = a.n, N0 = a.N, lg0 = g.lg[0], half0 = n >> 1;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = gridDim.x * blockDim.x;
+  if (*a.gate != 0 || a.rec->status != MAZE_OK) return;
+  long long* const X = reinterpret_cast<long long*>(g.x);   // corrections, level 0 included
+  long long* const B = reinterpret_cast<long long*>(g.b);   // right-hand sides
+  long long* const R = reinterpret_cast<long long*>(g.r);   // residuals at red points
+  long long* const e_red = X;
+  long long* const e_blk = X + half0;
+  long long* const b_red = B;
+  long long* const b_blk = B + half0;
+  double* const y = a.y;
+
+  // ---- S4 and the residual of the warm start (FP64, every point), kept as
+  // its bit pattern in the level-0 right-hand side until the scale is known
+  double res;
+  {
+    const bool mmax[1] = {true};
+    unsigned long long rmax = 0;
+    for (int m = tid; m < n; m += stride) {
+      const Nbr b = neighbours(m, N0);
+      const double sg = shake_rhs(a, m, b);
+      const double My = fma(-6.0, y[m], (y[b.xm] + y[b.xp]) + (y[b.ym] + y[b.yp]) + (y[b.zm] + y[b.zp]));
+      const double r0 = sg - My;
+      int i, j, k;
+      if (lg0 > 0) {
+        i = m & (N0 - 1);
+        j = (m >> lg0) & (N0 - 1);
+        k = m >> (2 * lg0);
+      } else {
+        k = m / (N0 * N0);
+        j = (m - k * N0 * N0) / N0;
+        i = m - N0 * (j + N0 * k);
+      }
+      B[store_index(i, j, k, N0, true)] = __double_as_longlong(r0);
+      rmax = max(rmax, abs_bits(r0));
+    }
+    const double v[1] = {absmax_value(rmax)};
+    double t[1];
+    if (!grid_reduce<1>(v, mmax, a.recs, ++epoch, a.rec, t)) return;
+    res = t[0];
+  }
+  // max |r_0| 2^F in [2^(H-1), 2^H)
+  int F = H - 1 - (dbl_exp(res) - 1023);
+  if (F > kMaxScale) F = kMaxScale;
+  int s = 0;   // left shift that moves the stored level-0 residual to scale F
+  int it = 0;
+  unsigned long long rmax = 0;
+  bool ovf = false;
+
+  while (isfinite(res) && !(res < a.tol) && it < a.max_iter) {
+    // ---- level 0, first red half-sweep from e = 0: e = round(-b / 6); on the
+    // first V-cycle the FP64 residual is first rounded to units of 2^-F
+    for (int h = tid; h < half0; h += stride) {
+      long long bv;
+      if (it == 0) {
+        bv = round_scaled(__longlong_as_double(b_red[h]), F);
+        b_red[h] = bv;
+        b_blk[h] = round_scaled(__longlong_as_double(b_blk[h]), F);
+      } else {
+        bv = shl(b_red[h], s);
+      }
+      e_red[h] = div6(-bv);
+    }
+    if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
+    // ---- down: smooth, residual at red points, restrict
+    for (int l = 0; l < g.L - 1; ++l) {
+      const int N = g.Nl[l], lg = g.lg[l], sh = l == 0 ? s : 0, half = (N * N * N) >> 1;
+      long long* x = X + g.off[l];
+      const long long* b = B + g.off[l];
+      for (int t = 0; t < g.nu1; ++t) {
+        // the first red half-sweep from the zero guess was written by the
+        // step above (level 0) or by the restriction (coarse levels)
+        if (t > 0) {
+          half_sweep_i(x, b, sh, N, lg, 0, tid, stride);
+          if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
+        }
+        half_sweep_i(x, b, sh, N, lg, 1, tid, stride);
+        if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
+      }
+      long long* r = R + g.off[l];   // red half-indices
+#pragma unroll 2
+      for (int h = tid; h < half; h += stride) {
+        int t, j, k;
+        half_decode(h, N, lg, t, j, k);
+        r[h] = shl(b[h], sh) - nbr6s(x + half, h, t, j, k, (j + k) & 1, N) + 6 * x[h];
+      }
+      if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
+      // b_c = 4 FW(r) = r_centre / 2 + (sum of the 12 red points two of whose
+      // offsets are +-1) / 8, over coarse points in storage order; a red
+      // coarse point gets its first half-sweep
+      const int Nc = g.Nl[l + 1], lgc = g.lg[l + 1], nc3 = Nc * Nc * Nc;
+      const bool coarsest = (l + 1 == g.L - 1);
+      long long* bc = B + g.off[l + 1];
+      long long* xc = X + g.off[l + 1];
+      const int hN = N >> 1, NhN = N * hN;
+      for (int q = tid; q < nc3; q += stride) {
+        int I, J, K;
+        if (coarsest) {
+          K = q / (Nc * Nc);
+          J = (q - K * Nc * Nc) / Nc;
+          I = q - Nc * (J + Nc * K);
+        } else {
+          const int hc = nc3 >> 1, C = q >= hc ? 1 : 0;
+          int T;
+          half_decode(q - C * hc, Nc, lgc, T, J, K);
+          I = 2 * T + ((J + K + C) & 1);
+        }
+        // fine red point (i, j, k) at half-index (i >> 1) + (N/2)(j + N k)
+        const int t0 = I, tm = wrapi(2 * I - 1, N) >> 1;   // x-offsets 0 and -1 (+1 shares t0)
+        const int j0 = 2 * J, jm = wrapi(j0 - 1, N), jp = j0 + 1;
+        const int k0 = 2 * K, km = wrapi(k0 - 1, N), kp = k0 + 1;
+        const int rj0 = hN * j0, rjm = hN * jm, rjp = hN * jp;
+        const int rk0 = NhN * k0, rkm = NhN * km, rkp = NhN * kp;
+        const long long s12 = ((r[rk0 + rjm + tm] + r[rk0 + rjm + t0]) + (r[rk0 + rjp + tm] + r[rk0 + rjp + t0])) +
+                              ((r[rkm + rj0 + tm] + r[rkm + rj0 + t0]) + (r[rkp + rj0 + tm] + r[rkp + rj0 + t0])) +
+                              ((r[rkm + rjm + t0] + r[rkm + rjp + t0]) + (r[rkp + rjm + t0] + r[rkp + rjp + t0]));
+        const long long v = div2k(4 * r[rk0 + rj0 + t0] + s12, 3);
+        bc[q] = v;
+        if (!coarsest && q < (nc3 >> 1)) xc[q] = div6(-v);
+      }
+      if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
+    }
+    // ---- coarsest (natural order): x = M^+ b, the FP64 product with the
+    // pseudo-inverse kernel (stored as -6 M^+), exact warp sums, one warp per point
+    {
+      const int Nc = g.Nl[g.L - 1], NNc = Nc * Nc, nc3 = Nc * NNc;
+      const long long* bc = B + g.off[g.L - 1];
+      long long* xc = X + g.off[g.L - 1];
+      const int lane = threadIdx.x & 31;
+      const int wid = tid >> 5, nwarps = stride >> 5;
+      for (int p = wid; p < nc3; p += nwarps) {
+        const int pk = p / NNc, pj = (p - pk * NNc) / Nc, pi = p - pk * NNc - pj * Nc;
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        int u = 0;
+        for (int q = lane; q < nc3; q += 32, ++u) {
+          const int qk = q / NNc, qj = (q - qk * NNc) / Nc, qi = q - qk * NNc - qj * Nc;
+          const int d = wrapi(pi - qi, Nc) + Nc * (wrapi(pj - qj, Nc) + Nc * wrapi(pk - qk, Nc));
+          acc[u & 3] = fma(g.gker[d], fix_to_dbl(bc[q], 1075), acc[u & 3]);
+        }
+        long long S;
+        int E;
+        warp_dsum_fix((acc[0] + acc[1]) + (acc[2] + acc[3]), S, E);
+        if (lane == 0) {
+          const double v = fix_to_dbl(S, E) * (-1.0 / 6.0);
+          const bool big = !(fabs(v) < 0x1p58);
+          ovf = ovf || big;
+          xc[p] = big ? 0 : round_scaled(v, 0);
+        }
+      }
+      if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
+    }
+    // ---- up: prolong (black points), smooth; the last black half-sweep on
+    // level 0 keeps the black residual
+    for (int l = g.L - 2; l >= 0; --l) {
+      const int N = g.Nl[l], lg = g.lg[l], sh = l == 0 ? s : 0, half = (N * N * N) >> 1;
+      const int Nc = g.Nl[l + 1];
+      const bool csplit = l + 1 < g.L - 1;
+      long long* x = X + g.off[l];
+      long long* b = B + g.off[l];
+      const long long* xc = X + g.off[l + 1];
+      for (int h = tid; h < half; h += stride) {
+        int t, j, k;
+        half_decode(h, N, lg, t, j, k);
+        const int i = 2 * t + ((j + k + 1) & 1);
+        const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
+        const int odd = (i & 1) + (j & 1) + (k & 1);
+        long long e;
+        if (odd == 1) {
+          const int c0 = store_index(i0, j0, k0, Nc, csplit);
+          const int c1 = (i & 1) ? store_index(wrapi(i0 + 1, Nc), j0, k0, Nc, csplit)
+                       : (j & 1) ? store_index(i0, wrapi(j0 + 1, Nc), k0, Nc, csplit)
+                                 : store_index(i0, j0, wrapi(k0 + 1, Nc), Nc, csplit);
+          e = div2k(xc[c0] + xc[c1], 1);
+        } else {
+          const int i1 = wrapi(i0 + 1, Nc), j1 = wrapi(j0 + 1, Nc), k1 = wrapi(k0 + 1, Nc);
+          e = div2k(((xc[store_index(i0, j0, k0, Nc, csplit)] + xc[store_index(i1, j0, k0, Nc, csplit)]) +
+                     (xc[store_index(i0, j1, k0, Nc, csplit)] + xc[store_index(i1, j1, k0, Nc, csplit)])) +
+                        ((xc[store_index(i0, j0, k1, Nc, csplit)] + xc[store_index(i1, j0, k1, Nc, csplit)]) +
+                         (xc[store_index(i0, j1, k1, Nc, csplit)] + xc[store_index(i1, j1, k1, Nc, csplit)])),
+                    3);
+        }
+        x[half + h] += e;
+      }
+      if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
+      for (int t = 0; t < g.nu2; ++t) {
+        half_sweep_i(x, b, sh, N, lg, 0, tid, stride);
+        if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
+        if (l == 0 && t == g.nu2 - 1) {
+#pragma unroll 2
+          for (int h = tid; h < half; h += stride) {
+            int tt, j, k;
+            half_decode(h, N, lg, tt, j, k);
+            const long long v = nbr6s(x, h, tt, j, k, (j + k + 1) & 1, N) - shl(b[half + h], sh);
+            const long long ev = div6(v);
+            const long long rb = 6 * ev - v;
+            x[half + h] = ev;
+            b[half + h] = rb;
+            rmax = max(rmax, iabs(rb));
+          }
+        } else {
+          half_sweep_i(x, b, sh, N, lg, 1, tid, stride);
+        }
+        if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
+      }
+    }
+    ++it;
+    // ---- level 0: r = b - M e at red points (the next right-hand side), y += e
+    // at both points of a half-index pair (i = 2t, 2t + 1: one 16-byte access),
+    // and the stopping test (Eq. res_poisson_maze) on max |r|
+    {
+#pragma unroll 2
+      for (int h = tid; h < half0; h += stride) {
+        int t, j, k;
+        half_decode(h, N0, lg0, t, j, k);
+        const int p = (j + k) & 1;
+        const long long er = e_red[h], eb = e_blk[h];
+        const long long r = shl(b_red[h], s) - nbr6s(e_blk, h, t, j, k, p, N0) + 6 * er;
+        b_red[h] = r;
+        rmax = max(rmax, iabs(r));
+        double2* yp = reinterpret_cast<double2*>(y + 2 * t + N0 * (j + N0 * k));
+        double2 yv = *yp;
+        const double dr = fix_to_dbl(er, 1075 - F), db = fix_to_dbl(eb, 1075 - F);
+        yv.x += p ? db : dr;
+        yv.y += p ? dr : db;
+        *yp = yv;
+      }
+      const double v[2] = {fix_to_dbl((long long)rmax, 1075), ovf ? 1.0 : 0.0};
+      const bool mm[2] = {true, true};
+      double t[2];
+      if (!grid_reduce<2>(v, mm, a.recs, ++epoch, a.rec, t)) return;
+      rmax = 0;
+      if (t[1] != 0.0) {
+        res = __longlong_as_double(0x7ff0000000000000LL);   // overflow: reported as non-finite
+        break;
+      }
+      res = t[0] * __longlong_as_double((long long)(1023 - F) << 52);
+      // the next scale: max |r| 2^F back to [2^(H-1), 2^H)
+      int sft = t[0] > 0.0 ? (H - 1) - (dbl_exp(t[0]) - 1023) : 0;
+      if (sft < 0) sft = 0;
+      if (F + sft > kMaxScale) sft = kMaxScale > F ? kMaxScale - F : 0;
+      s = sft;
+      F += sft;
+    }
+  }
+  if (it > 0 && !grid_barrier(a.bar, bar_epoch, a.rec)) return;
+  // ---- mean of y, then S6
+  double ysum;
+  {
+    const bool msum[1] = {false};
+    double ys = 0.0;
+    for (int m = tid; m < n; m += stride) ys += y[m];
+    const double v[1] = {ys};
+    double t[1];
+    if (!grid_reduce<1>(v, msum, a.recs, ++epoch, a.rec, t)) return;
+    ysum = t[0];
+  }
+  const double ybar = ysum * a.inv_n;
+  for (int m = tid; m < n; m += stride) {
+    const double yv = y[m] - ybar;
+    y[m] = yv;
+    a.phi_out[m] = fma(-a.c_phi, yv, a.phi_out[m]);
+  }
+  if (tid == 0) {
+    maze_stats* r = a.rec;
+    r->iters = it;
+    r->resid = res * a.res_scale;
+    r->total_iters += it;
+    if (!isfinite(res) || !isfinite(ysum)) r->status = MAZE_ERR_NONFINITE;
+    else if (!(res < a.tol)) r->status = MAZE_ERR_NOT_CONVERGED;
+  }
+}
+
+// H of the fixed-point scale for a finest edge N: 58 - 2 ceil(log2 N).
+int mgfix_headroom(int N) {
+  int c = 0;
+  while ((1 << c) < N) ++c;
+  return 58 - 2 * c;
+}
+
+int mgfix_blocks(int n_points) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int threads = mg_threads(n_points);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mgfix_solve, threads, 0);
+  if (per_sm < 1) per_sm = 1;
+  int want = (n_points + threads - 1) / threads;
+  int cap = sms * per_sm;
+  if (cap > kMaxReduceBlocks) cap = kMaxReduceBlocks;
+  return want < cap ? want : cap;
+}
+
+cudaError_t launch_mgfix_solve(const SolveArgs& a, const MgArgs& g, int blocks, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(mg_threads(a.n));
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_mgfix_solve, a, g, mgfix_headroom(a.N));
+}
+
+}  // namespace maze

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_cg_solve(SolveArgs a) {
     unsigned long long rmax = 0;
     for (int m = tid; m < n; m += stride) {
       const Nbr b = neighbours(m, N);
-      const double q = (double)(long long)a.qfix[m] * kQInv;
+      const double q = fix_to_dbl((long long)a.qfix[m], 1075 - 50);   // qfix 2^-50, integer ops only
       a.qfix[m] = 0ull;
       if (a.q_out) a.q_out[m] = q;
       double php = 0.0, Mphp = 0.0;

@@ -2,6 +2,9 @@
 // reductions) driven to its limit on purpose, so that the give-up path -
 // record MAZE_ERR_TIMEOUT, return from every block - can be observed on the
 // GPU without a fault: the wait is for a round that no block completes.
+//
+// maze_convert_probe: the integer-pipe FP32/FP64 conversions the hot kernels
+// use, computed beside the conversion instructions for a checker.
 #include <string>
 
 #include "maze_internal.cuh"
@@ -35,9 +38,73 @@ __global__ void __launch_bounds__(kProbeThreads) k_wait_probe(int which, unsigne
   }
 }
 
+// The integer-pipe conversions of maze_internal.cuh beside the conversion
+// instructions, element by element.
+__global__ void k_convert_probe(const double* in, int n, float* f_own, float* f_hw, double* d_own, double* d_hw,
+                                long long* fl_own, long long* fl_hw, double* q_own, double* q_hw) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = in[i];
+  f_own[i] = dbl_to_flt(v);
+  const float f = __double2float_rn(v);
+  f_hw[i] = f;
+  d_own[i] = flt_to_dbl(f);
+  d_hw[i] = (double)f;
+  const bool small = fabs(v) < 4.0e18;
+  fl_own[i] = small ? floor_ll(v) : 0;
+  fl_hw[i] = small ? (long long)floor(v) : 0;
+  const long long k = small ? (long long)(v * 1048576.0) : 0;   // v 2^20 as an integer
+  q_own[i] = fix_to_dbl(k, 1075 - 20);
+  q_hw[i] = (double)k * (1.0 / 1048576.0);
+}
+
 }  // namespace
 
 }  // namespace maze
+
+extern "C" maze_status maze_convert_probe(const double* in, int32_t n, float* f_own, float* f_hw, double* d_own,
+                                          double* d_hw, int64_t* floor_own, int64_t* floor_hw, double* fix_own,
+                                          double* fix_hw) {
+  using namespace maze;
+  if (n < 0 || (n > 0 && (!in || !f_own || !f_hw || !d_own || !d_hw || !floor_own || !floor_hw || !fix_own ||
+                          !fix_hw))) {
+    set_last_error("maze_convert_probe: n must be >= 0 and every array non-NULL");
+    return MAZE_ERR_INVALID;
+  }
+  if (n == 0) return MAZE_OK;
+  char* buf = nullptr;
+  const size_t N = (size_t)n;
+  const size_t bytes = N * (8 + 4 + 4 + 8 + 8 + 8 + 8 + 8 + 8);
+  cudaError_t e = cudaMalloc(&buf, bytes);
+  double* d_in = reinterpret_cast<double*>(buf);
+  double* dd_own = d_in + N;
+  double* dd_hw = dd_own + N;
+  double* dq_own = dd_hw + N;
+  double* dq_hw = dq_own + N;
+  long long* dfl_own = reinterpret_cast<long long*>(dq_hw + N);
+  long long* dfl_hw = dfl_own + N;
+  float* df_own = reinterpret_cast<float*>(dfl_hw + N);
+  float* df_hw = df_own + N;
+  if (e == cudaSuccess) e = cudaMemcpy(d_in, in, N * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_convert_probe<<<(n + 255) / 256, 256>>>(d_in, n, df_own, df_hw, dd_own, dd_hw, dfl_own, dfl_hw, dq_own, dq_hw);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(f_own, df_own, N * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(f_hw, df_hw, N * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(d_own, dd_own, N * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(d_hw, dd_hw, N * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(floor_own, dfl_own, N * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(floor_hw, dfl_hw, N * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(fix_own, dq_own, N * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(fix_hw, dq_hw, N * 8, cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess) {
+    set_last_error((std::string("maze_convert_probe: ") + cudaGetErrorString(e)).c_str());
+    return MAZE_ERR_CUDA;
+  }
+  return MAZE_OK;
+}
 
 extern "C" maze_status maze_wait_probe(int32_t which, void* cuda_stream, int32_t* status_out) {
   using namespace maze;

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libmaze.so")
 MAZE_OK, MAZE_ERR_INVALID, MAZE_ERR_OOM, MAZE_ERR_NOT_CONVERGED = 0, 1, 2, 3
 MAZE_ERR_NONFINITE, MAZE_ERR_TIMEOUT, MAZE_ERR_CUDA = 4, 5, 6
 MAZE_SOLVER_CG, MAZE_SOLVER_MG = 0, 1
-MAZE_FP64, MAZE_MIXED = 0, 1
+MAZE_FP64, MAZE_MIXED, MAZE_FP64_FIXMG = 0, 1, 2
 MAZE_SCHEME_MAZE, MAZE_SCHEME_MG_STATIC, MAZE_SCHEME_MG_TIMEPROP = 0, 1, 2
 MAZE_FORCE_CD, MAZE_FORCE_GRADW = 0, 1
 MAZE_POS, MAZE_VEL, MAZE_FORCE, MAZE_FORCE_EL = 0, 1, 2, 3
@@ -34,7 +34,7 @@ EXPORTS = ("maze_create", "maze_spread", "maze_solve", "maze_gather", "maze_step
            "maze_batch_get", "maze_batch_set", "maze_batch_get_stats", "maze_batch_get_all_stats",
            "maze_batch_tune",
            "maze_batch_destroy", "maze_wait_probe", "maze_batch_step_ready_async", "maze_batch_sync",
-           "maze_batch_refresh", "maze_batch_autotune")
+           "maze_batch_refresh", "maze_batch_autotune", "maze_convert_probe")
 
 _D = ctypes.c_double
 _I = ctypes.c_int32
@@ -132,6 +132,7 @@ def load(path: str = LIB_PATH):
     lib.maze_batch_destroy.argtypes = [P]
     lib.maze_batch_destroy.restype = None
     lib.maze_wait_probe.argtypes = [_I, P, ctypes.POINTER(_I)]
+    lib.maze_convert_probe.argtypes = [P, _I, P, P, P, P, P, P, P, P]
     lib.maze_batch_step_ready_async.argtypes = [P, _I]
     lib.maze_batch_sync.argtypes = [P]
     lib.maze_batch_refresh.argtypes = [P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I)]
@@ -260,6 +261,22 @@ def maze_wait_probe(which: int, stream: int | None = None):
     out = _I()
     st = load().maze_wait_probe(int(which), ctypes.c_void_p(stream or 0), ctypes.byref(out))
     return st, out.value
+
+
+def maze_convert_probe(x):
+    """The integer-pipe conversions of the FP64 kernels beside the conversion
+    instructions, for a float64 array x. Returns (status, dict of arrays:
+    f_own, f_hw, d_own, d_hw, floor_own, floor_hw, fix_own, fix_hw)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = x.size
+    out = {"f_own": np.zeros(n, np.float32), "f_hw": np.zeros(n, np.float32), "d_own": np.zeros(n),
+           "d_hw": np.zeros(n), "floor_own": np.zeros(n, np.int64), "floor_hw": np.zeros(n, np.int64),
+           "fix_own": np.zeros(n), "fix_hw": np.zeros(n)}
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    st = load().maze_convert_probe(ptr(x), int(n), *(ptr(out[k]) for k in ("f_own", "f_hw", "d_own", "d_hw",
+                                                                            "floor_own", "floor_hw", "fix_own",
+                                                                            "fix_hw")))
+    return st, out
 
 
 def maze_destroy(h):

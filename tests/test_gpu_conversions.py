@@ -1,0 +1,48 @@
+"""The FP32/FP64 conversions that the FP64 kernels perform with integer
+operations (dbl_to_flt, flt_to_dbl, floor_ll, fix_to_dbl) equal the GPU's
+conversion instructions bit for bit, on edge cases and on random values
+across the exponent range."""
+import numpy as np
+import pytest
+
+from paper_2505_20418_gb300 import maze as M
+
+pytestmark = pytest.mark.gpu
+
+
+def inputs():
+    f32 = np.float32
+    tiny = [0.0, -0.0, 5e-324, -5e-324, 2.0 ** -1022, 2.0 ** -126, 2.0 ** -127, 2.0 ** -149, 2.0 ** -150,
+            1.5 * 2.0 ** -150, 2.0 ** -151, 3 * 2.0 ** -151, 1.0000001 * 2.0 ** -149, -2.0 ** -149,
+            float(np.finfo(f32).tiny) * (1 - 2.0 ** -24), float(np.finfo(f32).tiny) * (1 - 2.0 ** -25)]
+    big = [float(np.finfo(f32).max), float(np.finfo(f32).max) * (1 + 2.0 ** -25),
+           float(np.finfo(f32).max) * (1 + 2.0 ** -24), 2.0 ** 128, 1e300, -1e300, np.inf, -np.inf, np.nan]
+    # ties: halfway between neighbouring floats (even and odd lower neighbours)
+    base = np.array([1.0, 1.0 + 2.0 ** -23, 3.0, 1e-3, 123.456, -7.5, 2.0 ** -140], dtype=np.float64)
+    ulp = np.abs(np.spacing(base.astype(f32)).astype(np.float64))
+    ties = np.concatenate([base + ulp / 2, base - ulp / 2, base + ulp / 2 * (1 + 2.0 ** -30)])
+    floors = [0.5, -0.5, -1e-300, 1.0, -1.0, 2.5, -2.5, 1e15 + 0.5, -1e15 - 0.5, 2.0 ** 52, 2.0 ** 53 + 2,
+              -(2.0 ** 60), 3.9e18, 0.49999999999999994, -0.9999999999999999]
+    rng = np.random.default_rng(11)
+    r = rng.standard_normal(200000) * 2.0 ** rng.integers(-160, 140, 200000)
+    r2 = rng.uniform(-1e6, 1e6, 100000)
+    return np.concatenate([np.array(tiny + big + floors), ties, r, r2])
+
+
+def test_integer_pipe_conversions_equal_the_instructions():
+    x = inputs()
+    st, o = M.maze_convert_probe(x)
+    assert st == M.MAZE_OK, M.maze_last_error()
+    nan = np.isnan(o["f_hw"])
+    assert np.array_equal(nan, np.isnan(o["f_own"]))
+    assert np.array_equal(o["f_own"][~nan].view(np.uint32), o["f_hw"][~nan].view(np.uint32))
+    ok = ~np.isnan(o["d_hw"])
+    assert np.array_equal(o["d_own"][ok].view(np.uint64), o["d_hw"][ok].view(np.uint64))
+    assert np.isnan(o["d_own"][~ok]).all()
+    assert np.array_equal(o["floor_own"], o["floor_hw"])
+    assert np.array_equal(o["fix_own"].view(np.uint64), o["fix_hw"].view(np.uint64))
+    # the hardware rounding is IEEE nearest-even: the FP32 results are numpy's
+    fin = np.isfinite(x)
+    with np.errstate(over="ignore"):
+        ref = x[fin].astype(np.float32)
+    assert np.array_equal(o["f_hw"][fin].view(np.uint32), ref.view(np.uint32))
