@@ -1,44 +1,44 @@
 // S4-S6 of the MaZe step with the multigrid solver (Sec. III.A) at precision
-// MAZE_FP64_FIXMG: FP64 state, and V-cycles run as FP64 defect correction
-// whose corrections are computed in exact 64-bit integer arithmetic. One
-// cooperative persistent kernel.
+// MAZE_FP64_FIXMG: FP64 state, and V-cycles that solve for the correction of
+// y in exact 64-bit integer arithmetic. One cooperative persistent kernel.
 //
 // FP64, as in the FP64 kernel: phi, sigma_p, y; S4 (Eq. SHAKE); the residual
 // of the warm start r_0 = sigma_p - M y at every point; S6 (Eq.
-// SHAKEPhiFinal). Integer: V-cycle k solves M e = r_k for the correction of y
-// (y_{k+1} = y_k + e), every value of every level an integer multiple of
-// 2^-F_k. In exact arithmetic this is the FP64 kernel's V-cycle: red-black
-// Gauss-Seidel from y_k with right-hand side sigma_p, and from e = 0 with
-// right-hand side r_k, give the same iterate y_k + e (the update is affine),
-// and so do the restriction, the coarsest solve and the prolongation, which
-// are linear. The operators are those of the FP64 kernel: nu1 red-black
-// sweeps, 27-point full weighting of the residual (its 13 red points), the
-// exact zero-mean coarsest solve by the pseudo-inverse kernel, trilinear
+// SHAKEPhiFinal). Integer: the V-cycles solve M E = r_0 for the correction E
+// of y (y_final = y + E 2^-F), every value of every level an integer multiple
+// of 2^-F. In exact arithmetic this is the FP64 kernel's iteration: red-black
+// Gauss-Seidel from y with right-hand side sigma_p, and from E = 0 with
+// right-hand side r_0, give the same iterates y + E (the update is affine), and
+// so do the restriction, the coarsest solve and the prolongation, which are
+// linear. The operators are those of the FP64 kernel: nu1 red-black sweeps,
+// 27-point full weighting of the residual (its 13 red points), the exact
+// zero-mean coarsest solve by the pseudo-inverse kernel, trilinear
 // prolongation, nu2 sweeps, the stopping test max |sigma_p - M y| < tol after
 // every V-cycle (Eqs. SHAKEy, res_poisson_maze).
 //
 // Why: GB300 issues FP64 at 2 operations per clock per SM, and a Gauss-Seidel
 // point update costs 6 of them, so the FP64 V-cycle is bound by the FP64 pipe.
-// The same update in 64-bit integers (adds, a shift, a multiply-high for the
+// The same update in 64-bit integers (adds and a multiply-high for the
 // division by 6) runs on the integer pipes, and the V-cycle becomes bound by
-// HBM traffic.
+// HBM traffic. y is read and written once, in S6.
 //
 // Exactness and range:
-//  * the residual is tracked exactly: after the last black half-sweep of a
-//    V-cycle a black point's residual is 6 e - (s - b) (s the six-neighbour
-//    sum; at most 3 units), and the convergence pass forms b - M e at red
-//    points; both are stored as the next V-cycle's right-hand side. The
-//    stopping test therefore sees the residual of the corrections actually
-//    applied; only the FP64 additions y += e 2^-F_k round.
+//  * the stopping test is exact: r = r_0 - M E at red points is formed in
+//    integers after each V-cycle, and after the last black half-sweep a black
+//    point's residual is the rounding of its division by 6 (at most 3 units),
+//    taken as it is made. The only roundings of the result are the FP64
+//    operations that make r_0 and y + E 2^-F.
 //  * a Gauss-Seidel update divides by 6 rounding half away from zero; the
 //    full weighting divides by 8 and the prolongation by 2 or 8, rounding
-//    half up. Each is half a unit of the correction, 2^-(H+1) of max |r_k|.
-//  * the scale: F_k makes max |r_k| 2^F_k fall in [2^(H-1), 2^H), H = 58 -
-//    2 ceil(log2 N). The correction is bounded by |M^+|_inf max |r_k| and
-//    |M^+|_inf is about 0.048 N^2 (the h^2-scaled periodic Laplacian), so
-//    corrections stay below 2^54 and six-neighbour sums below 2^57. F never
-//    decreases, so the stored residual moves to the next scale by an exact
-//    left shift, applied where the level-0 right-hand side is read.
+//    half up: half a unit, 2^-(H+1) of max |r_0|, each.
+//  * the scale: F makes max |r_0| 2^F fall in [2^(H-1), 2^H), H = 58 -
+//    2 ceil(log2 N). E approximates M^+ r_0 and |M^+|_inf is about 0.048 N^2
+//    (the h^2-scaled periodic Laplacian), so corrections stay below 2^54 and
+//    six-neighbour sums below 2^57.
+//  * once the residual has fallen 20 bits below the scale (solves from a
+//    cold start), E is applied to y, the exact residual r_0 - M E at every
+//    point becomes the right-hand side, shifted left to the finer scale, and
+//    the iteration goes on from E = 0 (a restart: the same iterates).
 //  * a coarsest correction of 2^58 units or more (a diverging solve) ends the
 //    solve with MAZE_ERR_NONFINITE instead of wrapping around.
 #include <math.h>
@@ -109,18 +109,54 @@ __device__ __forceinline__ long long nbr6s(const long long* o, int h, int t, int
 
 __device__ __forceinline__ int wrapi(int a, int N) { return a < 0 ? a + N : (a >= N ? a - N : a); }
 
-// One red-black half-sweep of colour c on a split level: x = round((s - b 2^sh) / 6).
-__device__ __forceinline__ void half_sweep_i(long long* x, const long long* b, int sh, int N, int lg, int c, int tid,
+__device__ __forceinline__ longlong2 ld2(const long long* p) { return *reinterpret_cast<const longlong2*>(p); }
+__device__ __forceinline__ void st2(long long* p, long long u, long long v) {
+  *reinterpret_cast<longlong2*>(p) = make_longlong2(u, v);
+}
+
+// Six-neighbour sums s0, s1 of the two same-row points at half-indices h0 and
+// h0 + 1 (h0 = (t0, j, k), t0 even, parity p; N a multiple of 4 so that a row
+// holds whole pairs), from the other colour's array o with 16-byte loads: the
+// pairs at h0, h0 +- N/2 and h0 +- N^2/2, and the one x-neighbour outside the
+// pair, o[t0 - 1] (p = 0) or o[t0 + 2] (p = 1), periodic in the row.
+__device__ __forceinline__ void nbr6_pair(const long long* o, int h0, int t0, int j, int k, int p, int N, long long& s0,
+                                          long long& s1) {
+  const int hN = N >> 1, Sz = hN * N;
+  const int ym = j == 0 ? h0 + (N - 1) * hN : h0 - hN, yp = j == N - 1 ? h0 - (N - 1) * hN : h0 + hN;
+  const int zm = k == 0 ? h0 + (N - 1) * Sz : h0 - Sz, zp = k == N - 1 ? h0 - (N - 1) * Sz : h0 + Sz;
+  const longlong2 c = ld2(o + h0), u = ld2(o + ym), v = ld2(o + yp), d = ld2(o + zm), e = ld2(o + zp);
+  const long long w = p ? o[t0 == hN - 2 ? h0 - t0 : h0 + 2] : o[t0 == 0 ? h0 + hN - 1 : h0 - 1];
+  s0 = (p ? c.x + c.y : w + c.x) + (u.x + v.x) + (d.x + e.x);
+  s1 = (p ? c.y + w : c.x + c.y) + (u.y + v.y) + (d.y + e.y);
+}
+
+// One red-black half-sweep of colour c on a split level: x = round((s - b) / 6);
+// two points per thread and round where the edge is a multiple of 4.
+__device__ __forceinline__ void half_sweep_i(long long* x, const long long* b, int N, int lg, int c, int tid,
                                              int stride) {
   const int half = (N * N * N) >> 1;
   long long* xc = x + c * half;
   const long long* xo = x + (1 - c) * half;
   const long long* bc = b + c * half;
+  if ((N & 3) == 0) {
+    const int npair = half >> 1;
+#pragma unroll 2
+    for (int u = tid; u < npair; u += stride) {
+      const int h0 = 2 * u;
+      int t0, j, k;
+      half_decode(h0, N, lg, t0, j, k);
+      long long s0, s1;
+      nbr6_pair(xo, h0, t0, j, k, (j + k + c) & 1, N, s0, s1);
+      const longlong2 bv = ld2(bc + h0);
+      st2(xc + h0, div6(s0 - bv.x), div6(s1 - bv.y));
+    }
+    return;
+  }
 #pragma unroll 2
   for (int h = tid; h < half; h += stride) {
     int t, j, k;
     half_decode(h, N, lg, t, j, k);
-    xc[h] = div6(nbr6s(xo, h, t, j, k, (j + k + c) & 1, N) - shl(bc[h], sh));
+    xc[h] = div6(nbr6s(xo, h, t, j, k, (j + k + c) & 1, N) - bc[h]);
   }
 }
 
@@ -143,10 +179,11 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_mgfix_solve(SolveArgs a, MgAr
 
   // ---- S4 and the residual of the warm start (FP64, every point), kept as
   // its bit pattern in the level-0 right-hand side until the scale is known
-  double res;
+  double res, ysum0;   // max |r_0|; sum of y before the correction
   {
-    const bool mmax[1] = {true};
+    const bool mm[2] = {true, false};
     unsigned long long rmax = 0;
+    double ys = 0.0;
     for (int m = tid; m < n; m += stride) {
       const Nbr b = neighbours(m, N0);
       const double sg = shake_rhs(a, m, b);
@@ -164,56 +201,72 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_mgfix_solve(SolveArgs a, MgAr
       }
       B[store_index(i, j, k, N0, true)] = __double_as_longlong(r0);
       rmax = max(rmax, abs_bits(r0));
+      ys += y[m];
     }
-    const double v[1] = {absmax_value(rmax)};
-    double t[1];
-    if (!grid_reduce<1>(v, mmax, a.recs, ++epoch, a.rec, t)) return;
+    const double v[2] = {absmax_value(rmax), ys};
+    double t[2];
+    if (!grid_reduce<2>(v, mm, a.recs, ++epoch, a.rec, t)) return;
     res = t[0];
+    ysum0 = t[1];
   }
   // max |r_0| 2^F in [2^(H-1), 2^H)
   int F = H - 1 - (dbl_exp(res) - 1023);
   if (F > kMaxScale) F = kMaxScale;
-  int s = 0;   // left shift that moves the stored level-0 residual to scale F
   int it = 0;
+  bool fresh = true;   // E = 0: level 0's first red half-sweep is E = round(-b / 6)
   unsigned long long rmax = 0;
   bool ovf = false;
+  double esum = 0.0;   // sum of E (units 2^-F) after the last V-cycle
 
   while (isfinite(res) && !(res < a.tol) && it < a.max_iter) {
-    // ---- level 0, first red half-sweep from e = 0: e = round(-b / 6); on the
-    // first V-cycle the FP64 residual is first rounded to units of 2^-F
-    for (int h = tid; h < half0; h += stride) {
-      long long bv;
-      if (it == 0) {
-        bv = round_scaled(__longlong_as_double(b_red[h]), F);
-        b_red[h] = bv;
-        b_blk[h] = round_scaled(__longlong_as_double(b_blk[h]), F);
-      } else {
-        bv = shl(b_red[h], s);
+    if (fresh) {
+      // ---- level 0, first red half-sweep from E = 0; on the first V-cycle the
+      // FP64 residual is first rounded to units of 2^-F (both colours)
+      for (int h0 = 2 * tid; h0 < half0; h0 += 2 * stride) {   // (half0 = N0^3 / 2 is a multiple of 4)
+        longlong2 bv = ld2(b_red + h0);
+        if (it == 0) {
+          bv = make_longlong2(round_scaled(__longlong_as_double(bv.x), F), round_scaled(__longlong_as_double(bv.y), F));
+          st2(b_red + h0, bv.x, bv.y);
+          const longlong2 bb = ld2(b_blk + h0);
+          st2(b_blk + h0, round_scaled(__longlong_as_double(bb.x), F), round_scaled(__longlong_as_double(bb.y), F));
+        }
+        st2(e_red + h0, div6(-bv.x), div6(-bv.y));
       }
-      e_red[h] = div6(-bv);
+      if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
     }
-    if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
     // ---- down: smooth, residual at red points, restrict
     for (int l = 0; l < g.L - 1; ++l) {
-      const int N = g.Nl[l], lg = g.lg[l], sh = l == 0 ? s : 0, half = (N * N * N) >> 1;
+      const int N = g.Nl[l], lg = g.lg[l], half = (N * N * N) >> 1;
       long long* x = X + g.off[l];
       const long long* b = B + g.off[l];
       for (int t = 0; t < g.nu1; ++t) {
-        // the first red half-sweep from the zero guess was written by the
-        // step above (level 0) or by the restriction (coarse levels)
-        if (t > 0) {
-          half_sweep_i(x, b, sh, N, lg, 0, tid, stride);
+        // a first red half-sweep from a zero guess was written by the step
+        // above (level 0, fresh) or by the restriction (coarse levels)
+        if (t > 0 || (l == 0 && !fresh)) {
+          half_sweep_i(x, b, N, lg, 0, tid, stride);
           if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
         }
-        half_sweep_i(x, b, sh, N, lg, 1, tid, stride);
+        half_sweep_i(x, b, N, lg, 1, tid, stride);
         if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
       }
       long long* r = R + g.off[l];   // red half-indices
+      if ((N & 3) == 0) {
 #pragma unroll 2
-      for (int h = tid; h < half; h += stride) {
-        int t, j, k;
-        half_decode(h, N, lg, t, j, k);
-        r[h] = shl(b[h], sh) - nbr6s(x + half, h, t, j, k, (j + k) & 1, N) + 6 * x[h];
+        for (int h0 = 2 * tid; h0 < half; h0 += 2 * stride) {
+          int t0, j, k;
+          half_decode(h0, N, lg, t0, j, k);
+          long long s0, s1;
+          nbr6_pair(x + half, h0, t0, j, k, (j + k) & 1, N, s0, s1);
+          const longlong2 xv = ld2(x + h0), bv = ld2(b + h0);
+          st2(r + h0, bv.x - s0 + 6 * xv.x, bv.y - s1 + 6 * xv.y);
+        }
+      } else {
+#pragma unroll 2
+        for (int h = tid; h < half; h += stride) {
+          int t, j, k;
+          half_decode(h, N, lg, t, j, k);
+          r[h] = b[h] - nbr6s(x + half, h, t, j, k, (j + k) & 1, N) + 6 * x[h];
+        }
       }
       if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
       // b_c = 4 FW(r) = r_centre / 2 + (sum of the 12 red points two of whose
@@ -281,13 +334,14 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_mgfix_solve(SolveArgs a, MgAr
       if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
     }
     // ---- up: prolong (black points), smooth; the last black half-sweep on
-    // level 0 keeps the black residual
+    // level 0 also takes the black points' residual (the rounding of the
+    // division, at most 3 units) into the stopping test
     for (int l = g.L - 2; l >= 0; --l) {
-      const int N = g.Nl[l], lg = g.lg[l], sh = l == 0 ? s : 0, half = (N * N * N) >> 1;
+      const int N = g.Nl[l], lg = g.lg[l], half = (N * N * N) >> 1;
       const int Nc = g.Nl[l + 1];
       const bool csplit = l + 1 < g.L - 1;
       long long* x = X + g.off[l];
-      long long* b = B + g.off[l];
+      const long long* b = B + g.off[l];
       const long long* xc = X + g.off[l + 1];
       for (int h = tid; h < half; h += stride) {
         int t, j, k;
@@ -314,82 +368,136 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_mgfix_solve(SolveArgs a, MgAr
       }
       if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
       for (int t = 0; t < g.nu2; ++t) {
-        half_sweep_i(x, b, sh, N, lg, 0, tid, stride);
+        half_sweep_i(x, b, N, lg, 0, tid, stride);
         if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
         if (l == 0 && t == g.nu2 - 1) {
+          if ((N & 3) == 0) {
 #pragma unroll 2
-          for (int h = tid; h < half; h += stride) {
-            int tt, j, k;
-            half_decode(h, N, lg, tt, j, k);
-            const long long v = nbr6s(x, h, tt, j, k, (j + k + 1) & 1, N) - shl(b[half + h], sh);
-            const long long ev = div6(v);
-            const long long rb = 6 * ev - v;
-            x[half + h] = ev;
-            b[half + h] = rb;
-            rmax = max(rmax, iabs(rb));
+            for (int h0 = 2 * tid; h0 < half; h0 += 2 * stride) {
+              int t0, j, k;
+              half_decode(h0, N, lg, t0, j, k);
+              long long s0, s1;
+              nbr6_pair(x, h0, t0, j, k, (j + k + 1) & 1, N, s0, s1);
+              const longlong2 bv = ld2(b + half + h0);
+              const long long v0 = s0 - bv.x, v1 = s1 - bv.y;
+              const long long e0 = div6(v0), e1 = div6(v1);
+              st2(x + half + h0, e0, e1);
+              rmax = max(rmax, max(iabs(6 * e0 - v0), iabs(6 * e1 - v1)));
+            }
+          } else {
+#pragma unroll 2
+            for (int h = tid; h < half; h += stride) {
+              int tt, j, k;
+              half_decode(h, N, lg, tt, j, k);
+              const long long v = nbr6s(x, h, tt, j, k, (j + k + 1) & 1, N) - b[half + h];
+              const long long ev = div6(v);
+              x[half + h] = ev;
+              rmax = max(rmax, iabs(6 * ev - v));
+            }
           }
         } else {
-          half_sweep_i(x, b, sh, N, lg, 1, tid, stride);
+          half_sweep_i(x, b, N, lg, 1, tid, stride);
         }
         if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
       }
     }
     ++it;
-    // ---- level 0: r = b - M e at red points (the next right-hand side), y += e
-    // at both points of a half-index pair (i = 2t, 2t + 1: one 16-byte access),
-    // and the stopping test (Eq. res_poisson_maze) on max |r|
+    fresh = false;
+    // ---- the stopping test (Eq. res_poisson_maze) on max |r|, r = b - M E at
+    // red points (exact)
+    // (and the sum of E, exact per thread: at most 2 half0 / threads terms below 2^54)
     {
+      long long es = 0;
+      if ((N0 & 3) == 0) {
 #pragma unroll 2
-      for (int h = tid; h < half0; h += stride) {
-        int t, j, k;
-        half_decode(h, N0, lg0, t, j, k);
-        const int p = (j + k) & 1;
-        const long long er = e_red[h], eb = e_blk[h];
-        const long long r = shl(b_red[h], s) - nbr6s(e_blk, h, t, j, k, p, N0) + 6 * er;
-        b_red[h] = r;
-        rmax = max(rmax, iabs(r));
-        double2* yp = reinterpret_cast<double2*>(y + 2 * t + N0 * (j + N0 * k));
-        double2 yv = *yp;
-        const double dr = fix_to_dbl(er, 1075 - F), db = fix_to_dbl(eb, 1075 - F);
-        yv.x += p ? db : dr;
-        yv.y += p ? dr : db;
-        *yp = yv;
+        for (int h0 = 2 * tid; h0 < half0; h0 += 2 * stride) {
+          int t0, j, k;
+          half_decode(h0, N0, lg0, t0, j, k);
+          long long s0, s1;
+          nbr6_pair(e_blk, h0, t0, j, k, (j + k) & 1, N0, s0, s1);
+          const longlong2 er = ld2(e_red + h0), eb = ld2(e_blk + h0), bv = ld2(b_red + h0);
+          rmax = max(rmax, max(iabs(bv.x - s0 + 6 * er.x), iabs(bv.y - s1 + 6 * er.y)));
+          es += (er.x + er.y) + (eb.x + eb.y);
+        }
+      } else {
+#pragma unroll 2
+        for (int h = tid; h < half0; h += stride) {
+          int t, j, k;
+          half_decode(h, N0, lg0, t, j, k);
+          rmax = max(rmax, iabs(b_red[h] - nbr6s(e_blk, h, t, j, k, (j + k) & 1, N0) + 6 * e_red[h]));
+          es += e_red[h] + e_blk[h];
+        }
       }
-      const double v[2] = {fix_to_dbl((long long)rmax, 1075), ovf ? 1.0 : 0.0};
-      const bool mm[2] = {true, true};
-      double t[2];
-      if (!grid_reduce<2>(v, mm, a.recs, ++epoch, a.rec, t)) return;
+      const double v[3] = {fix_to_dbl((long long)rmax, 1075), ovf ? 1.0 : 0.0, fix_to_dbl(es, 1075)};
+      const bool mm[3] = {true, true, false};
+      double t[3];
+      if (!grid_reduce<3>(v, mm, a.recs, ++epoch, a.rec, t)) return;
       rmax = 0;
+      esum = t[2];
       if (t[1] != 0.0) {
         res = __longlong_as_double(0x7ff0000000000000LL);   // overflow: reported as non-finite
         break;
       }
       res = t[0] * __longlong_as_double((long long)(1023 - F) << 52);
-      // the next scale: max |r| 2^F back to [2^(H-1), 2^H)
-      int sft = t[0] > 0.0 ? (H - 1) - (dbl_exp(t[0]) - 1023) : 0;
-      if (sft < 0) sft = 0;
-      if (F + sft > kMaxScale) sft = kMaxScale > F ? kMaxScale - F : 0;
-      s = sft;
-      F += sft;
+      // a residual 20 bits below the scale (a solve from a cold start): apply E
+      // to y, keep the exact residual r = b - M E at every point as the new
+      // right-hand side, rescaled, and start again from E = 0
+      const int sft = t[0] > 0.0 ? (H - 1) - (dbl_exp(t[0]) - 1023) : 0;
+      if (!(res < a.tol) && it < a.max_iter && sft >= 20 && F + sft <= kMaxScale) {
+        const int E = 1075 - F;
+        double ys = 0.0;
+        for (int h = tid; h < half0; h += stride) {
+          int t0, j, k;
+          half_decode(h, N0, lg0, t0, j, k);
+          const int p = (j + k) & 1;
+          const long long er = e_red[h], eb = e_blk[h];
+          const long long rr = b_red[h] - nbr6s(e_blk, h, t0, j, k, p, N0) + 6 * er;
+          const long long rb = b_blk[h] - nbr6s(e_red, h, t0, j, k, 1 - p, N0) + 6 * eb;
+          b_red[h] = shl(rr, sft);
+          b_blk[h] = shl(rb, sft);
+          double2* yp = reinterpret_cast<double2*>(y + 2 * t0 + N0 * (j + N0 * k));
+          double2 yv = *yp;
+          const double dr = fix_to_dbl(er, E), db = fix_to_dbl(eb, E);
+          yv.x += p ? db : dr;
+          yv.y += p ? dr : db;
+          *yp = yv;
+          ys += yv.x + yv.y;
+        }
+        const double v1[1] = {ys};
+        const bool ms[1] = {false};
+        double t1[1];
+        if (!grid_reduce<1>(v1, ms, a.recs, ++epoch, a.rec, t1)) return;   // (also the barrier before E = 0)
+        ysum0 = t1[0];
+        F += sft;
+        fresh = true;
+      }
     }
   }
-  if (it > 0 && !grid_barrier(a.bar, bar_epoch, a.rec)) return;
-  // ---- mean of y, then S6
-  double ysum;
-  {
-    const bool msum[1] = {false};
-    double ys = 0.0;
-    for (int m = tid; m < n; m += stride) ys += y[m];
-    const double v[1] = {ys};
-    double t[1];
-    if (!grid_reduce<1>(v, msum, a.recs, ++epoch, a.rec, t)) return;
-    ysum = t[0];
-  }
+  // (the last grid reduction above orders every write of E before S6's reads)
+  // ---- y + E 2^-F (after a V-cycle since the last restart) and S6; the mean
+  // of y from the sums; half-index h covers the points i = 2t, 2t + 1 of its row
+  const bool apply = it > 0 && !fresh;
+  const int Ey = 1075 - F;
+  const double ysum = apply ? ysum0 + esum * __longlong_as_double((long long)(1023 - F) << 52) : ysum0;
   const double ybar = ysum * a.inv_n;
-  for (int m = tid; m < n; m += stride) {
-    const double yv = y[m] - ybar;
-    y[m] = yv;
-    a.phi_out[m] = fma(-a.c_phi, yv, a.phi_out[m]);
+  for (int h = tid; h < half0; h += stride) {
+    int t0, j, k;
+    half_decode(h, N0, lg0, t0, j, k);
+    const int p = (j + k) & 1;
+    const int m = 2 * t0 + N0 * (j + N0 * k);
+    double2 yv = *reinterpret_cast<const double2*>(y + m);
+    if (apply) {
+      const double dr = fix_to_dbl(e_red[h], Ey), db = fix_to_dbl(e_blk[h], Ey);
+      yv.x += p ? db : dr;
+      yv.y += p ? dr : db;
+    }
+    yv.x -= ybar;
+    yv.y -= ybar;
+    *reinterpret_cast<double2*>(y + m) = yv;
+    double2 ph = *reinterpret_cast<const double2*>(a.phi_out + m);
+    ph.x = fma(-a.c_phi, yv.x, ph.x);
+    ph.y = fma(-a.c_phi, yv.y, ph.y);
+    *reinterpret_cast<double2*>(a.phi_out + m) = ph;
   }
   if (tid == 0) {
     maze_stats* r = a.rec;

@@ -23,7 +23,8 @@ def make(name, tol=TOL, precision=M.MAZE_FP64_FIXMG, **kw):
     return sim, p, tf, (pos, vel, types)
 
 
-@pytest.mark.parametrize("name", ["nacl64", "nacl64_P2", "nacl1000", "nacl216_N24", "nacl1728_N40", "tiny8_N8"])
+@pytest.mark.parametrize("name", ["nacl64", "nacl64_P2", "nacl1000", "nacl216_N24", "nacl1728_N40", "tiny8_N8",
+                                  "tiny8_N14"])
 def test_step0_and_one_step_parity(name):
     sim, p, tf, (pos, vel, types) = make(name)
     st = O.init(pos, vel, types, p, tf)

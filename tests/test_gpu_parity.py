@@ -46,6 +46,10 @@ def case(name):
         w = synth.Workload("n1728", 12, 37.8, 40, seed=32)
         pos, vel, types = synth.make_state(w)
         return pos, vel, types, w.L, w.N, w.rc, 4
+    if name == "tiny8_N14":        # an edge of 2 (mod 4): the one-point-per-thread sweeps, coarsest 7^3
+        pos, types = synth.random_neutral(8, 8.0, 5, min_dist=2.3)
+        vel = synth.maxwell(types, 1200.0, np.random.default_rng(5))
+        return pos, vel, types, 8.0, 14, 4.0, 4
     if name == "tiny8_N8":         # minimum grid, 8 ions
         pos, types = synth.random_neutral(8, 8.0, 5, min_dist=2.3)
         vel = synth.maxwell(types, 1200.0, np.random.default_rng(5))
@@ -64,7 +68,7 @@ def make(name, tol=TOL, solver="cg", **kw):
     return sim, p, tf, (pos, vel, types)
 
 
-CASES = ["nacl64", "nacl64_P2", "nacl1000", "nacl216_N24", "nacl1728_N40", "tiny8_N8"]
+CASES = ["nacl64", "nacl64_P2", "nacl1000", "nacl216_N24", "nacl1728_N40", "tiny8_N8", "tiny8_N14"]
 
 
 @pytest.mark.parametrize("name", CASES)
