@@ -3,15 +3,17 @@
 A step is one full MaZe MD step (S1-S9) of one synthetic molten-NaCl box.
 Default workload: 512000 ions (256000 Na+, 256000 Cl-), L = 252 Angstrom,
 256^3 grid, 1200 K, dt = 1 fs, constraint tolerance 1e-10, cubic B-spline
-assignment, warm-started multigrid constraint solve in FP64; the same box in
-mixed precision (FP32 V-cycle, double-float outer iteration, exact integer
-reductions) is timed after it and reported under "mixed". Inputs are
-resident in HBM when the timed region starts; L2 is flushed (256 MiB write)
-between timed steps, outside the per-step CUDA events.
+assignment, warm-started multigrid constraint solve with FP64 state whose
+V-cycle corrections are exact 64-bit integers (--precision fp64fix). The same
+box with the all-FP64 V-cycle is timed after it and reported under "fp64",
+and in mixed precision (FP32 V-cycle, double-float outer iteration, exact
+integer reductions) under "mixed". Inputs are resident in HBM when the timed
+region starts; L2 is flushed (256 MiB write) between timed steps, outside the
+per-step CUDA events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload nacl64|nacl1000|nacl8000|nacl64000|nacl512000|batch128|serve|study]
-                  [--solver cg|mg] [--precision fp64|mixed]
+                  [--solver cg|mg] [--precision fp64fix|fp64|mixed]
 
 --workload batch128 advances 128 replica boxes (216-4096 ions, 16^3-48^3
 grids) together, one persistent kernel launch per step; --workload serve runs
@@ -132,6 +134,14 @@ def solve_bytes_per_launch(N, iters, solver="cg", nu=(2, 2), precision="fp64"):
     prolongation to black points 9 B/pt; coarsest solve 16 B/pt; residual
     check on the finest level 16 B/pt.
 
+    FP64 state with the integer V-cycle (fp64fix; every level but the
+    coarsest stored split by colour, so a half-sweep reads one colour): S4
+    64 B/pt (read phi^k, phi^{k-1}, q, y; write phi_p, sigma_p, r_0, q
+    cleared), r_0 to fixed point 16 B/pt, S6 48 B/pt (read y, E, phi_p;
+    write y, phi); per V-cycle and level 24 B/pt per sweep, residual 16 B/pt,
+    full weighting 5.5 B/pt, prolongation 9 B/pt; the stopping test 12 B/pt
+    of the finest level; coarsest 16 B/pt.
+
     Mixed (double-float pairs of 8 B for phi, y, sigma_p; FP32 V-cycle):
     S4 40 B/pt (read phi^k, phi^{k-1}, q; write phi_p, sigma_p); per
     residual check 20 B/pt (read y, sigma_p; write r in FP32); per V-cycle
@@ -143,6 +153,9 @@ def solve_bytes_per_launch(N, iters, solver="cg", nu=(2, 2), precision="fp64"):
     if precision == "mixed":
         per_v = sum(n ** 3 * ((nu[0] + nu[1]) * 16 + 12 + 4.5 + 4.5) for n in lv[:-1]) + lv[-1] ** 3 * 8
         return ng * (40 + 40) + (iters + 1) * ng * 20 + iters * (per_v + ng * 20)
+    if precision == "fp64fix":
+        per_v = sum(n ** 3 * ((nu[0] + nu[1]) * 24 + 16 + 5.5 + 9) for n in lv[:-1]) + lv[-1] ** 3 * 16 + ng * 12
+        return ng * (64 + 16 + 48) + per_v * iters
     base = ng * (56 + 32)
     if solver == "cg":
         return base + ng * (64 * iters + 24)
@@ -554,10 +567,11 @@ def main():
     ap.add_argument("--boxes", type=int, default=128, help="batch128: number of replica boxes")
     ap.add_argument("--cluster-ctas", type=int, default=0, help="batch128: CTAs per box (0: autotune)")
     ap.add_argument("--solver", default="mg", choices=["cg", "mg"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "fp64fix"])
+    ap.add_argument("--precision", default="fp64fix", choices=["fp64fix", "fp64", "mixed"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision run beside an FP64 line")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the runs beside an FP64 line (the other FP64 form and mixed precision)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.workload == "batch128":
@@ -598,9 +612,12 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     head = time_box(args, M, w, args.precision, args.solver, stream, flush, dist, dev, world, rank,
                     e2e=not args.no_e2e)
-    # the same box in mixed precision beside an FP64 headline (extra keys)
-    mixed = None
-    if args.precision == "fp64" and args.solver == "mg" and not args.no_mixed:
+    # the same box beside an FP64 multigrid headline (extra keys): the other
+    # FP64 form of the solve, and mixed precision
+    mixed = other64 = None
+    if args.precision in ("fp64", "fp64fix") and args.solver == "mg" and not args.no_mixed:
+        alt = "fp64" if args.precision == "fp64fix" else "fp64fix"
+        other64 = (alt, time_box(args, M, w, alt, "mg", stream, flush, dist, dev, world, rank, e2e=False))
         mixed = time_box(args, M, w, "mixed", "mg", stream, flush, dist, dev, world, rank, e2e=False)
 
     if rank == 0:
@@ -628,13 +645,26 @@ def main():
             "timing_error": head["timing_error"],
             "gpu_launches": kernels_per_step(args.precision, w, sms) * args.steps, "clocks": head["clocks"],
         }
+        if other64 is not None:
+            alt, o = other64
+            oroof, oother = rooflines(w, alt, "mg", o["iters_per_step"], o["solve_s"], args.workload, sms)
+            line[alt] = {
+                "what": ("the same box and steps with the FP64 V-cycle (every multigrid operation in FP64 "
+                         "arithmetic)" if alt == "fp64" else
+                         "the same box and steps with the integer V-cycle (FP64 state, corrections in exact "
+                         "64-bit integers)") + ", timed the same way after the headline run",
+                "dtype": DTYPES[alt], "steps_per_s": o["steps_per_s"], "ms_per_step": o["ms_per_step"],
+                "iters_per_step": o["iters_per_step"], "force_error": o["force_error"],
+                "phase_us": o["phase_us"], "solve_us": 1e6 * o["solve_s"], "roofline": oroof,
+                "roofline_other": oother, "gpu_launches": kernels_per_step(alt, w, sms) * args.steps,
+                "clocks": o["clocks"]}
         if mixed is not None:
             mroof, _ = rooflines(w, "mixed", "mg", mixed["iters_per_step"], mixed["solve_s"], args.workload, sms)
             line["mixed"] = {
                 "what": "the same box and steps in mixed precision (FP32 V-cycle, double-float outer SHAKE "
-                        "iteration, FP64 reductions), timed the same way after the FP64 run",
+                        "iteration, FP64 reductions), timed the same way after the headline run",
                 "steps_per_s": mixed["steps_per_s"], "ms_per_step": mixed["ms_per_step"],
-                "speedup_vs_fp64": mixed["steps_per_s"] / head["steps_per_s"],
+                "speedup_vs_headline": mixed["steps_per_s"] / head["steps_per_s"],
                 "iters_per_step": mixed["iters_per_step"], "force_error": mixed["force_error"],
                 "phase_us": mixed["phase_us"], "solve_us": 1e6 * mixed["solve_s"], "roofline": mroof,
                 "gpu_launches": kernels_per_step("mixed", w, sms) * args.steps, "clocks": mixed["clocks"]}

@@ -92,7 +92,8 @@ enum { MAZE_FORCE_CD = 0, MAZE_FORCE_GRADW = 1 };
  * charge,mass per species (e, amu); the system must be neutral:
  *             |sum_a Q_a| <= 1e-9 * sum_a |Q_a|
  * tf_*        Tosi-Fumi pair energy A exp(B (s - r)) - C/r^6 - D/r^8 (Sec. III)
- *             for pair kinds 0 = (0,0), 1 = (0,1), 2 = (1,1); eV and Angstrom
+ *             for pair kinds 0 = (0,0), 1 = (0,1), 2 = (1,1); eV and Angstrom;
+ *             A >= 0
  * r_cut       pair cutoff (Angstrom), 0 < r_cut <= L/2; the pair energy is
  *             shifted to zero at r_cut, forces are truncated
  * dt          time step (fs)
@@ -471,6 +472,16 @@ maze_status maze_wait_probe(int32_t which, void* cuda_stream, int32_t* status_ou
  * when a CUDA call fails, else MAZE_OK. */
 maze_status maze_convert_probe(const double* in, int32_t n, float* f_own, float* f_hw, double* d_own, double* d_hw,
                                int64_t* floor_own, int64_t* floor_hw, double* fix_own, double* fix_hw);
+
+/* Diagnostic: the exponential the FP64 Tosi-Fumi pair forces evaluate (a
+ * table-driven method, Tang 1989: a 64-entry table of 2^(j/64), a degree-5
+ * polynomial, the power of two set in the exponent field; exp() for
+ * |x| >= 512 and non-finite x) beside the CUDA math library's exp(), for n
+ * host doubles in[]: own[i], ref[i]. Host arrays of n elements owned by the
+ * caller; the call allocates, copies and synchronises on the legacy default
+ * stream. Returns MAZE_ERR_INVALID for n < 0 or a NULL array, MAZE_ERR_CUDA
+ * when a CUDA call fails, else MAZE_OK. */
+maze_status maze_exp_probe(const double* in, int32_t n, double* own, double* ref);
 
 #ifdef __cplusplus
 }

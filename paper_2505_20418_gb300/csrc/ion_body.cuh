@@ -353,7 +353,7 @@ __device__ __forceinline__ void tf_pair(const ForceArgs& a, int kind, double r2,
   const double ir2 = ir * ir;
   const double ir6 = ir2 * ir2 * ir2;
   const double ir8 = ir6 * ir2;
-  const double ex = a.A[kind] * exp(a.B * (a.s[kind] - r));
+  const double ex = exp_tab(fma(-a.B, r, a.Ec[kind]), a.exp2tab);   // A exp(B (s - r))
   V = ex - a.C[kind] * ir6 - a.D[kind] * ir8 - a.Vc[kind];
   fr = a.B * ex * ir - 6.0 * a.C[kind] * ir8 - 8.0 * a.D[kind] * ir8 * ir2;
 }
@@ -1050,7 +1050,6 @@ struct HalfSmem {
 
 template <int kW>
 __device__ __forceinline__ void pairs_half_cell(const ForceArgs& a, int c, HalfSmem<kW>& sm) {
-  const float Lf = dbl_to_flt(a.L);   // the box edge as FP32 (image shifts of the filter copies)
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int n = a.n, nc = a.nc;
@@ -1092,9 +1091,9 @@ __device__ __forceinline__ void pairs_half_cell(const ForceArgs& a, int c, HalfS
         const double shx = ox < 0 ? -a.L : (ox >= nc ? a.L : 0.0);
         const double shy = oy < 0 ? -a.L : (oy >= nc ? a.L : 0.0);
         const double shz = oz < 0 ? -a.L : (oz >= nc ? a.L : 0.0);
-        const float fx = ox < 0 ? -Lf : (ox >= nc ? Lf : 0.f);
-        const float fy = oy < 0 ? -Lf : (oy >= nc ? Lf : 0.f);
-        const float fz = oz < 0 ? -Lf : (oz >= nc ? Lf : 0.f);
+        const float fx = ox < 0 ? -a.Lf : (ox >= nc ? a.Lf : 0.f);
+        const float fy = oy < 0 ? -a.Lf : (oy >= nc ? a.Lf : 0.f);
+        const float fz = oz < 0 ? -a.Lf : (oz >= nc ? a.Lf : 0.f);
         const float4 pj = a.pos_sorted[slot];
         sm.j[e] = j;
         sm.slot[e] = tt < self_end ? slot : 0x7fffffff;

@@ -58,6 +58,10 @@ maze_status dalloc(maze_ctx* c, T** p, size_t count) {
   return MAZE_OK;
 }
 
+void exp2_table(double* out64) {
+  for (int j = 0; j < 64; ++j) out64[j] = exp2(j / 64.0);
+}
+
 // Whether the multigrid hierarchy halves level L - 1 of edge N once more:
 // while the edge is even and above 8, and an 8^3 finest level once (so that
 // every hierarchy has at least two levels). The coarsest level, of at most
@@ -88,6 +92,9 @@ maze_status validate(const maze_config* c) {
       return fail(MAZE_ERR_INVALID, "multigrid needs grid_N = m * 2^k with a coarsest edge m <= 8 (e.g. 32, 48, 56)");
   }
   if (c->order_P != 2 && c->order_P != 4) return fail(MAZE_ERR_INVALID, "order_P must be 2 or 4");
+  for (int k = 0; k < 3; ++k)
+    if (!(c->tf_A[k] >= 0) || !isfinite(c->tf_A[k]))
+      return fail(MAZE_ERR_INVALID, "tf_A must be finite and >= 0 (a repulsive prefactor)");
   if (c->precision != MAZE_FP64 && c->precision != MAZE_MIXED && c->precision != MAZE_FP64_FIXMG)
     return fail(MAZE_ERR_INVALID, "precision must be MAZE_FP64, MAZE_MIXED or MAZE_FP64_FIXMG");
   if (c->precision == MAZE_FP64_FIXMG && c->solver != MAZE_SOLVER_MG)
@@ -260,7 +267,9 @@ ForceArgs force_args(maze_ctx* c, const double* phi, int do_kick, int count_step
     a.C[k] = g.tf_C[k];
     a.D[k] = g.tf_D[k];
     a.Vc[k] = g.tf_A[k] * exp(g.tf_B * (g.tf_s[k] - rc)) - g.tf_C[k] / pow(rc, 6) - g.tf_D[k] / pow(rc, 8);
+    a.Ec[k] = g.tf_B * g.tf_s[k] + log(g.tf_A[k]);   // (A = 0: -inf, exp gives 0)
   }
+  a.exp2tab = c->exp2tab;
   a.B = g.tf_B;
   a.rc2 = rc * rc;
   for (int k = 0; k < 3; ++k) {
@@ -784,6 +793,7 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
     if (gradw) AL(c->wdbuf, 12 * (size_t)n);
   }
   AL(c->wbase, (size_t)n);
+  AL(c->exp2tab, 64);
   AL(c->qfix, ng);
   AL(c->qd, ng);
   for (int g = 0; g < 3; ++g) AL(c->phi[g], ng);
@@ -985,6 +995,9 @@ maze_status ctx_create(const maze_config* cfg, Arena* arena, maze_ctx** out, boo
   CKC(cudaMemcpyAsync(c->vel, tmp.data(), tmp.size() * 8, cudaMemcpyHostToDevice, st));
   CKC(cudaMemcpyAsync(c->type, cfg->type, (size_t)n * 4, cudaMemcpyHostToDevice, st));
   if (!gk.empty() && c->mg_g) CKC(cudaMemcpyAsync(c->mg_g, gk.data(), gk.size() * 8, cudaMemcpyHostToDevice, st));
+  std::vector<double> e2(64);
+  exp2_table(e2.data());
+  CKC(cudaMemcpyAsync(c->exp2tab, e2.data(), 64 * 8, cudaMemcpyHostToDevice, st));
   if (!gkf.empty()) CKC(cudaMemcpyAsync(c->mx_g, gkf.data(), gkf.size() * 4, cudaMemcpyHostToDevice, st));
   CKC(cudaMemsetAsync(c->force, 0, 3 * (size_t)n * 8, st));
   CKC(cudaMemsetAsync(c->force_el, 0, 3 * (size_t)n * 8, st));

@@ -71,6 +71,7 @@ struct maze_ctx {
   // multigrid
   maze::MgArgs mg = {};
   double *mg_x = nullptr, *mg_b = nullptr, *mg_r = nullptr, *mg_g = nullptr;
+  double* exp2tab = nullptr;   // [64] 2^(j/64), the pair forces' exponential
   // mixed precision: phi, y, sigma hold double-float pairs (float2, 8 B)
   bool mixed = false;
   bool fixmg = false;     // MAZE_FP64_FIXMG: the integer defect-correction V-cycle

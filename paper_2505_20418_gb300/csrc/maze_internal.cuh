@@ -133,6 +133,8 @@ struct ForceArgs {
   double ke_coef;        // 1 / (2 acc_unit): 1/2 m v^2 in eV
   // Tosi-Fumi table by pair kind (0,0) (0,1) (1,1)
   double A[3], s[3], C[3], D[3], Vc[3];
+  double Ec[3];          // B s + ln A: the repulsion A exp(B (s - r)) = exp(Ec - B r)
+  const double* exp2tab; // [64] 2^(j/64), j = 0..63 (exp_tab)
   double B;
   double rc2;            // r_cut^2
   float rc2_filter;      // (r_cut + margin)^2 for the FP32 pre-filter
@@ -262,6 +264,8 @@ cudaError_t launch_gather_finish(const ForceArgs& a, int blocks, cudaStream_t s)
 int force_blocks(int n_ions);
 cudaError_t launch_cg_solve(const SolveArgs& a, int blocks, cudaStream_t s);
 int solve_blocks(int n_points);
+// The 64 entries 2^(j/64) of exp_tab's table (host).
+void exp2_table(double* out64);
 cudaError_t launch_mg_solve(const SolveArgs& a, const MgArgs& g, int blocks, cudaStream_t s);
 int mg_blocks(int n_points);
 cudaError_t launch_mgfix_solve(const SolveArgs& a, const MgArgs& g, int blocks, cudaStream_t s);
@@ -611,6 +615,29 @@ __device__ __forceinline__ long long floor_ll(double v) {
   const long long ip = m >> (52 - e);
   const bool frac = (m & ((1LL << (52 - e)) - 1)) != 0;
   return neg ? -(ip + (frac ? 1 : 0)) : ip;
+}
+
+// exp(x) by Tang's table-driven method (P. T. P. Tang, ACM TOMS 15, 1989):
+// x = (64 m + j) ln2/64 + r with |r| <= ln2/128, so exp(x) = 2^m 2^(j/64) e^r;
+// 2^(j/64) comes from a 64-entry table, e^r - 1 from its degree-5 Taylor
+// polynomial (the remainder r^6/720 is below 2^-54 there), the 2^m scaling is
+// an integer add to the exponent field. 10 FP64 operations and no conversion;
+// |x| >= 512, infinities and NaN take exp(). Within 2 ulp of exp() (checked
+// against it by maze_exp_probe).
+__device__ __forceinline__ double exp_tab(double x, const double* __restrict__ tab) {
+  if (((__double_as_longlong(x) >> 52) & 0x7ff) >= 1023 + 9) return exp(x);
+  const double kd = fma(x, 0x1.71547652b82fep+6, 0x1.8p52);   // 64/ln2, then round to an integer
+  const int k = (int)(unsigned)__double_as_longlong(kd);       // (the low bits of 1.5 2^52 + k)
+  const double kf = kd - 0x1.8p52;
+  double r = fma(-kf, 0x1.62e42fefa39efp-7, x);                 // ln2/64 in two parts (Cody-Waite)
+  r = fma(-kf, 0x1.abc9e3b39803fp-62, r);
+  const double c4 = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+  const double c3 = fma(r, c4, 1.0 / 6.0);
+  const double c2 = fma(r, c3, 0.5);
+  const double p = r * fma(r, c2, 1.0);                         // e^r - 1
+  const double t = __ldg(tab + (k & 63));
+  const double e = fma(t, p, t);
+  return __longlong_as_double(__double_as_longlong(e) + ((long long)(k >> 6) << 52));
 }
 
 // S4 at grid point m with periodic neighbours b (Eq. SHAKE): the charge q

@@ -4,7 +4,8 @@
 // GPU without a fault: the wait is for a round that no block completes.
 //
 // maze_convert_probe: the integer-pipe FP32/FP64 conversions the hot kernels
-// use, computed beside the conversion instructions for a checker.
+// use, computed beside the conversion instructions for a checker;
+// maze_exp_probe: the pair forces' table-driven exponential beside exp().
 #include <string>
 
 #include "maze_internal.cuh"
@@ -58,9 +59,45 @@ __global__ void k_convert_probe(const double* in, int n, float* f_own, float* f_
   q_hw[i] = (double)k * (1.0 / 1048576.0);
 }
 
+// exp_tab beside exp().
+__global__ void k_exp_probe(const double* in, int n, const double* tab, double* own, double* ref) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  own[i] = exp_tab(in[i], tab);
+  ref[i] = exp(in[i]);
+}
+
 }  // namespace
 
 }  // namespace maze
+
+extern "C" maze_status maze_exp_probe(const double* in, int32_t n, double* own, double* ref) {
+  using namespace maze;
+  if (n < 0 || (n > 0 && (!in || !own || !ref))) {
+    set_last_error("maze_exp_probe: n must be >= 0 and every array non-NULL");
+    return MAZE_ERR_INVALID;
+  }
+  if (n == 0) return MAZE_OK;
+  const size_t N = (size_t)n;
+  double tab[64];
+  exp2_table(tab);
+  double* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, (3 * N + 64) * 8);
+  if (e == cudaSuccess) e = cudaMemcpy(buf, in, N * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(buf + 3 * N, tab, 64 * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_exp_probe<<<(n + 255) / 256, 256>>>(buf, n, buf + 3 * N, buf + N, buf + 2 * N);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(own, buf + N, N * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(ref, buf + 2 * N, N * 8, cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess) {
+    set_last_error((std::string("maze_exp_probe: ") + cudaGetErrorString(e)).c_str());
+    return MAZE_ERR_CUDA;
+  }
+  return MAZE_OK;
+}
 
 extern "C" maze_status maze_convert_probe(const double* in, int32_t n, float* f_own, float* f_hw, double* d_own,
                                           double* d_hw, int64_t* floor_own, int64_t* floor_hw, double* fix_own,

@@ -34,7 +34,7 @@ EXPORTS = ("maze_create", "maze_spread", "maze_solve", "maze_gather", "maze_step
            "maze_batch_get", "maze_batch_set", "maze_batch_get_stats", "maze_batch_get_all_stats",
            "maze_batch_tune",
            "maze_batch_destroy", "maze_wait_probe", "maze_batch_step_ready_async", "maze_batch_sync",
-           "maze_batch_refresh", "maze_batch_autotune", "maze_convert_probe")
+           "maze_batch_refresh", "maze_batch_autotune", "maze_convert_probe", "maze_exp_probe")
 
 _D = ctypes.c_double
 _I = ctypes.c_int32
@@ -133,6 +133,7 @@ def load(path: str = LIB_PATH):
     lib.maze_batch_destroy.restype = None
     lib.maze_wait_probe.argtypes = [_I, P, ctypes.POINTER(_I)]
     lib.maze_convert_probe.argtypes = [P, _I, P, P, P, P, P, P, P, P]
+    lib.maze_exp_probe.argtypes = [P, _I, P, P]
     lib.maze_batch_step_ready_async.argtypes = [P, _I]
     lib.maze_batch_sync.argtypes = [P]
     lib.maze_batch_refresh.argtypes = [P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I)]
@@ -277,6 +278,16 @@ def maze_convert_probe(x):
                                                                             "floor_own", "floor_hw", "fix_own",
                                                                             "fix_hw")))
     return st, out
+
+
+def maze_exp_probe(x):
+    """The pair forces' table-driven exp beside CUDA's exp() for a float64
+    array x. Returns (status, own, ref)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    own, ref = np.zeros(x.size), np.zeros(x.size)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    st = load().maze_exp_probe(ptr(x), int(x.size), ptr(own), ptr(ref))
+    return st, own, ref
 
 
 def maze_destroy(h):

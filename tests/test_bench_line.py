@@ -38,23 +38,27 @@ def test_reference_arm_line():
 
 @pytest.mark.gpu
 def test_cuda_arm_line():
-    """The default line: the 512000-ion 256^3 box in FP64 (multigrid), the
-    same box in mixed precision beside it."""
+    """The default line: the 512000-ion 256^3 box with FP64 state and the
+    integer V-cycle (multigrid); beside it the same box with the all-FP64
+    V-cycle and in mixed precision."""
     steps = 8
     d = _run("--steps", str(steps), "--warmup", "3", timeout=1200)
     _common(d, steps)
-    assert "impl" not in d and d["dtype"] == "f64" and d["config"]["grid"] == 256
-    for r in (d["roofline"], d["roofline_other"]):
-        assert r["bound"] in ("hbm", "alu") and r["peak"] > 0 and r["achieved"] > 0
-        assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
-        assert r["traffic"] is None or r["traffic"] > 0
-    assert {d["roofline"]["bound"], d["roofline_other"]["bound"]} == {"hbm", "alu"}
+    assert "impl" not in d and d["dtype"] == "f64+i64" and d["config"]["grid"] == 256
+    r = d["roofline"]
+    assert r["bound"] == "hbm" and r["peak"] > 0 and r["achieved"] > 0
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert r["traffic"] is None or r["traffic"] > 0
     e = d["e2e"]
     assert e["h2d_bytes_per_step"] == 48 * 512000 and e["d2h_bytes_per_step"] > 48 * 512000
     assert d["gpu_launches"] == 8 * steps          # move, spread, 3 cell-list kernels, solve, pairs, gather
     assert d["clocks"]["sm_mhz"] > 0 and isinstance(d["clocks"]["reasons"], list)
     assert d["force_error"] < 1e-7                 # FP64 at tol 1e-10 (the solver tolerance dominates)
     assert d["ms_per_step"] > 0 and d["p99_us"] >= d["p50_us"] > 0
+    f = d["fp64"]
+    assert f["dtype"] == "f64" and f["iters_per_step"] == d["iters_per_step"]
+    assert abs(f["force_error"] - d["force_error"]) < 1e-9
+    assert {f["roofline"]["bound"], f["roofline_other"]["bound"]} == {"hbm", "alu"}
     m = d["mixed"]
     assert m["steps_per_s"] > d["value"] and m["force_error"] < 1e-5
     assert m["roofline"]["bound"] == "hbm" and m["gpu_launches"] == 8 * steps

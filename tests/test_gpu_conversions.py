@@ -46,3 +46,32 @@ def test_integer_pipe_conversions_equal_the_instructions():
     with np.errstate(over="ignore"):
         ref = x[fin].astype(np.float32)
     assert np.array_equal(o["f_hw"][fin].view(np.uint32), ref.view(np.uint32))
+
+
+def ulp_distance(a, b):
+    """Distance in units in the last place between doubles of the same sign."""
+    ia = a.view(np.int64).astype(object)
+    ib = b.view(np.int64).astype(object)
+    return np.array([abs(x - y) for x, y in zip(ia, ib)], dtype=np.float64)
+
+
+def test_table_exp_within_two_ulp_of_exp():
+    """The pair forces' exponential (Tang's table-driven method) against the
+    CUDA math library's exp(): within 2 ulp over the arguments of the
+    Tosi-Fumi repulsion and far beyond, at the table's breakpoints, and exp()
+    itself outside |x| < 512 and for non-finite x."""
+    rng = np.random.default_rng(3)
+    ln2_64 = np.log(2.0) / 64
+    k = np.arange(-2000, 2000)
+    edges = np.concatenate([k * ln2_64, (k + 0.5) * ln2_64, np.nextafter((k + 0.5) * ln2_64, np.inf),
+                            np.nextafter((k + 0.5) * ln2_64, -np.inf)])
+    x = np.concatenate([rng.uniform(-40, 15, 200000), rng.uniform(-511.9, 511.9, 50000), edges,
+                        [0.0, -0.0, 1e-300, -1e-300, 511.99, -511.99]])
+    st, own, ref = M.maze_exp_probe(x)
+    assert st == M.MAZE_OK, M.maze_last_error()
+    assert (own > 0).all() and (ref > 0).all()
+    assert ulp_distance(own, ref).max() <= 2
+    y = np.array([512.0, -512.0, 700.0, -745.0, 1000.0, -1000.0, np.inf, -np.inf, np.nan])
+    st, own, ref = M.maze_exp_probe(y)
+    assert st == M.MAZE_OK
+    assert np.array_equal(own[:-1], ref[:-1]) and np.isnan(own[-1]) and np.isnan(ref[-1])
