@@ -343,19 +343,22 @@ __device__ __forceinline__ void cell_sort_one(const CellArgs& a, int c, int lane
 
 __device__ __forceinline__ void tf_pair(const ForceArgs& a, int kind, double r2, double& fr, double& V) {
   // V = A exp(B (s - r)) - C r^-6 - D r^-8 - V(r_c);  fr = -(dV/dr) / r.
-  // 1/r by Newton-Raphson for the reciprocal square root, y <- y (3 - r2 y^2)/2,
-  // from an FP32 seed (two steps: ~2^-22 -> 2^-44 -> FP64 rounding), so no FP64
-  // square root or division is needed.
-  double ir = flt_to_dbl(rsqrtf(dbl_to_flt(r2)));   // conversions on the integer pipe
-  ir = ir * (1.5 - 0.5 * r2 * ir * ir);
-  ir = ir * (1.5 - 0.5 * r2 * ir * ir);
+  // 1/r from an FP32 seed y0 (relative error e0 below ~2^-22) by one step of
+  // Halley's (third-order) iteration for the reciprocal square root:
+  // e = 1 - r2 y0^2, y = y0 (1 + e/2 + 3e^2/8); the error falls to ~e0^3, below
+  // FP64 rounding. y0^2 is exact in FP64 (a 24-bit significand squared), so no
+  // FP64 square root, division or conversion is needed: 5 FP64 operations.
+  const double y0 = flt_to_dbl(rsqrtf(dbl_to_flt(r2)));   // conversions on the integer pipe
+  const double e = fma(-r2, y0 * y0, 1.0);
+  const double ir = fma(y0, e * fma(e, 0.375, 0.5), y0);
   const double r = r2 * ir;
   const double ir2 = ir * ir;
-  const double ir6 = ir2 * ir2 * ir2;
-  const double ir8 = ir6 * ir2;
+  const double ir4 = ir2 * ir2;
+  const double ir6 = ir4 * ir2;
+  const double ir8 = ir4 * ir4;
   const double ex = exp_tab(fma(-a.B, r, a.Ec[kind]), a.exp2tab);   // A exp(B (s - r))
-  V = ex - a.C[kind] * ir6 - a.D[kind] * ir8 - a.Vc[kind];
-  fr = a.B * ex * ir - 6.0 * a.C[kind] * ir8 - 8.0 * a.D[kind] * ir8 * ir2;
+  V = ex - fma(a.C[kind], ir6, fma(a.D[kind], ir8, a.Vc[kind]));
+  fr = fma(a.B * ex, ir, -ir8 * fma(a.D8[kind], ir2, a.C6[kind]));   // B ex / r - 6C r^-8 - 8D r^-10
 }
 
 // Per-lane pair sums (FP64 mode uses the doubles, mixed the floats).
@@ -1017,7 +1020,8 @@ __device__ __forceinline__ void forces_cell_slice(const ForceArgs& a, int c, int
 // pair is visited twice). Each surviving pair's force goes to both ions:
 // the home ion's share is summed over the warp in a fixed order, the
 // partner's share into a 64-bit fixed-point accumulator of the staged
-// candidate with shared-memory integer atomics; both then reach the per-ion
+// candidate with shared-memory integer atomics (the home ion's share is the
+// same rounded integer with the opposite sign); both then reach the per-ion
 // sums a.pair_fix ([n][4]: force x, y, z and pair energy, each pair's
 // energy given to both ions as the one-ion loop does) with 64-bit integer
 // atomics. Integer sums are exact, so the result does not depend on the
@@ -1112,23 +1116,25 @@ __device__ __forceinline__ void pairs_half_cell(const ForceArgs& a, int c, HalfS
         const float4 pi32 = a.pos_sorted[islot];
         int* q = sm.queue[warp];
         int qn = 0;
-        double sfx = 0.0, sfy = 0.0, sfz = 0.0, sv = 0.0;
+        long long sfx = 0, sfy = 0, sfz = 0, sv = 0;   // 2^-40 units
         auto eval = [&](int e2) {
           const double ddx = sm.xyz[0][e2] - x, ddy = sm.xyz[1][e2] - y, ddz = sm.xyz[2][e2] - z;
           const double r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-          if (r2 >= a.rc2) return;
+          // (r2 >= 0: the integer order of the bit patterns is the numeric one)
+          if (__double_as_longlong(r2) >= __double_as_longlong(a.rc2)) return;
           double fr, V;
           tf_pair(a, ti + a.type[sm.j[e2]], r2, fr, V);
-          // force on the partner +fr d, on the home ion -fr d
-          const double fx = fr * ddx, fy = fr * ddy, fz = fr * ddz;
-          sfx -= fx;
-          sfy -= fy;
-          sfz -= fz;
-          sv += V;
-          atomicAdd(&sm.acc[e2][0], (unsigned long long)fix40(fx));
-          atomicAdd(&sm.acc[e2][1], (unsigned long long)fix40(fy));
-          atomicAdd(&sm.acc[e2][2], (unsigned long long)fix40(fz));
-          atomicAdd(&sm.acc[e2][3], (unsigned long long)fix40(V));
+          // force on the partner +fr d, on the home ion -fr d: the same 2^-40
+          // integers with opposite signs (the pair's momentum balance is exact)
+          const long long qx = fix40(fr * ddx), qy = fix40(fr * ddy), qz = fix40(fr * ddz), qv = fix40(V);
+          sfx -= qx;
+          sfy -= qy;
+          sfz -= qz;
+          sv += qv;
+          atomicAdd(&sm.acc[e2][0], (unsigned long long)qx);
+          atomicAdd(&sm.acc[e2][1], (unsigned long long)qy);
+          atomicAdd(&sm.acc[e2][2], (unsigned long long)qz);
+          atomicAdd(&sm.acc[e2][3], (unsigned long long)qv);
         };
         for (int e0 = 0; e0 < len; e0 += 32) {
           const int e = e0 + lane;
@@ -1156,10 +1162,9 @@ __device__ __forceinline__ void pairs_half_cell(const ForceArgs& a, int c, HalfS
         }
         if (lane < qn) eval(q[lane]);
         __syncwarp();
-        // the home ion's share: each lane's sum to fixed point, an exact
+        // the home ion's share: each lane's 2^-40 integer sum, an exact
         // integer warp sum (integer pipe; no FP64 shuffle tree)
-        const long long tx = warp_isum(fix40(sfx)), ty = warp_isum(fix40(sfy)), tz = warp_isum(fix40(sfz)),
-                        tv = warp_isum(fix40(sv));
+        const long long tx = warp_isum(sfx), ty = warp_isum(sfy), tz = warp_isum(sfz), tv = warp_isum(sv);
         if (lane == 0) {
           sm.f[gi][0] += (unsigned long long)tx;
           sm.f[gi][1] += (unsigned long long)ty;

@@ -268,6 +268,8 @@ ForceArgs force_args(maze_ctx* c, const double* phi, int do_kick, int count_step
     a.D[k] = g.tf_D[k];
     a.Vc[k] = g.tf_A[k] * exp(g.tf_B * (g.tf_s[k] - rc)) - g.tf_C[k] / pow(rc, 6) - g.tf_D[k] / pow(rc, 8);
     a.Ec[k] = g.tf_B * g.tf_s[k] + log(g.tf_A[k]);   // (A = 0: -inf, exp gives 0)
+    a.C6[k] = 6.0 * g.tf_C[k];
+    a.D8[k] = 8.0 * g.tf_D[k];
   }
   a.exp2tab = c->exp2tab;
   a.B = g.tf_B;

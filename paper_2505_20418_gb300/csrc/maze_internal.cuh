@@ -134,6 +134,7 @@ struct ForceArgs {
   // Tosi-Fumi table by pair kind (0,0) (0,1) (1,1)
   double A[3], s[3], C[3], D[3], Vc[3];
   double Ec[3];          // B s + ln A: the repulsion A exp(B (s - r)) = exp(Ec - B r)
+  double C6[3], D8[3];   // 6 C, 8 D (the force's dispersion terms)
   const double* exp2tab; // [64] 2^(j/64), j = 0..63 (exp_tab)
   double B;
   double rc2;            // r_cut^2
