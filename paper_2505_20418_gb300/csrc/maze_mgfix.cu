@@ -4,7 +4,8 @@
 //
 // FP64, as in the FP64 kernel: phi, sigma_p, y; S4 (Eq. SHAKE); the residual
 // of the warm start r_0 = sigma_p - M y at every point; S6 (Eq.
-// SHAKEPhiFinal). Integer: the V-cycles solve M E = r_0 for the correction E
+// SHAKEPhiFinal). The Laplacian of phi_p in S4 is summed exactly in integers
+// and rounded once (exact_combination). Integer: the V-cycles solve M E = r_0 for the correction E
 // of y (y_final = y + E 2^-F), every value of every level an integer multiple
 // of 2^-F. In exact arithmetic this is the FP64 kernel's iteration: red-black
 // Gauss-Seidel from y with right-hand side sigma_p, and from E = 0 with
@@ -109,6 +110,66 @@ __device__ __forceinline__ long long nbr6s(const long long* o, int h, int t, int
 
 __device__ __forceinline__ int wrapi(int a, int N) { return a < 0 ? a + N : (a >= N ? a - N : a); }
 
+// round(v 2^(1075 - E)) for a finite v whose exponent field is at most E + 3.
+__device__ __forceinline__ long long to_units(double v, int E) {
+  const long long b = __double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7ff);
+  const long long m = e ? (b & 0xfffffffffffffLL) | (1LL << 52) : (b & 0xfffffffffffffLL);
+  const int sh = E - (e ? e : 1);
+  const long long x = sh <= 0 ? m << (-sh) : (sh >= 62 ? 0 : (m + (1LL << (sh - 1))) >> sh);
+  return b < 0 ? -x : x;
+}
+
+// sum_k c_k v_k with small integer coefficients, rounded once: every v_k
+// rounded to an eighth of an ulp of the largest |v_k| (exact for the values
+// within 3 binades of it), the integers summed exactly. A NaN or infinity
+// gives NaN.
+template <int K>
+__device__ __forceinline__ double exact_combination(const double (&v)[K], const int (&c)[K]) {
+  int emax = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) emax = max(emax, dbl_exp(v[k]));
+  if (emax == 0x7ff) return __longlong_as_double(0x7ff8000000000000LL);
+  const int E = emax - 3;
+  long long s = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) s += (long long)c[k] * to_units(v[k], E);
+  return fix_to_dbl(s, E);
+}
+
+// S4 at point m (Eq. SHAKE) as shake_rhs, with the Laplacian of phi_p summed
+// exactly on the integer pipe, M phi_p = 2 (s_k - 6 phi^k) - (s_{k-1} -
+// 6 phi^{k-1}) over the fourteen values (s the six-neighbour sums); and the
+// warm start's M y in FP64 (the two pipes share the work).
+__device__ __forceinline__ double shake_rhs_fix(const SolveArgs& a, int m, const Nbr& b, double& My) {
+  const double q = fix_to_dbl((long long)a.qfix[m], 1075 - 50);
+  a.qfix[m] = 0ull;
+  if (a.q_out) a.q_out[m] = q;
+  double php = 0.0, Mphp = 0.0;
+  if (!a.zero_phi) {
+    const double* pk = a.phi_k;
+    if (a.static_guess) {
+      php = pk[m];
+      const double v[7] = {pk[b.xm], pk[b.xp], pk[b.ym], pk[b.yp], pk[b.zm], pk[b.zp], php};
+      const int c[7] = {1, 1, 1, 1, 1, 1, -6};
+      Mphp = exact_combination(v, c);
+    } else {
+      const double* pm = a.phi_km1;
+      const double v[14] = {pk[b.xm], pk[b.xp], pk[b.ym], pk[b.yp], pk[b.zm], pk[b.zp], pk[m],
+                            pm[b.xm], pm[b.xp], pm[b.ym], pm[b.yp], pm[b.zm], pm[b.zp], pm[m]};
+      const int c[14] = {2, 2, 2, 2, 2, 2, -12, -1, -1, -1, -1, -1, -1, 6};
+      Mphp = exact_combination(v, c);
+      php = fma(2.0, v[6], -v[13]);
+    }
+  }
+  const double sg = fma(a.c_sig, Mphp, q);
+  a.phi_out[m] = php;
+  a.sigma[m] = sg;
+  const double* y = a.y;
+  My = fma(-6.0, y[m], (y[b.xm] + y[b.xp]) + (y[b.ym] + y[b.yp]) + (y[b.zm] + y[b.zp]));
+  return sg;
+}
+
 __device__ __forceinline__ longlong2 ld2(const long long* p) { return *reinterpret_cast<const longlong2*>(p); }
 __device__ __forceinline__ void st2(long long* p, long long u, long long v) {
   *reinterpret_cast<longlong2*>(p) = make_longlong2(u, v);
@@ -186,8 +247,8 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_mgfix_solve(SolveArgs a, MgAr
     double ys = 0.0;
     for (int m = tid; m < n; m += stride) {
       const Nbr b = neighbours(m, N0);
-      const double sg = shake_rhs(a, m, b);
-      const double My = fma(-6.0, y[m], (y[b.xm] + y[b.xp]) + (y[b.ym] + y[b.yp]) + (y[b.zm] + y[b.zp]));
+      double My;
+      const double sg = shake_rhs_fix(a, m, b, My);
       const double r0 = sg - My;
       int i, j, k;
       if (lg0 > 0) {

@@ -60,6 +60,11 @@ def test_solve_and_gather_from_oracle_state():
     sim.spread()
     it, res = sim.solve()
     assert res < TOL
+    # S4's Laplacian is summed exactly in integers: sigma_p at the oracle's precision
+    Q = np.where(types == 0, 1.0, -1.0)
+    q = O.spread(nxt.pos, Q, p.L, p.N, p.P)
+    _, sp = O.sigma_p(st.phi, st.phi_prev, q, p.h)
+    assert np.abs(sim.get(M.MAZE_SIGMA) - sp).max() < 1e-13 * max(1.0, np.abs(sp).max())
     assert abs(it - nxt.iters) <= 1
     assert np.abs(sim.get(M.MAZE_PHI) - nxt.phi).max() < 1e-9
     sim.gather()
