@@ -48,6 +48,8 @@ from paper_2505_20418_gb300 import synth  # noqa: E402
 METRIC = "MaZe steps/s, solve GB/s vs HBM peak, p50/p99 step latency at stated force error"
 KERNELS_PER_STEP_CELLS = 7    # move, spread, 3 cell-list kernels, solve, forces
 KERNELS_PER_STEP_HALF = 8     # one force block per cell: ... solve, pairs once each + gather, finish
+KERNELS_PER_STEP_OVERLAP = 9  # the same with the pairs beside the solve: move, 3 cell-list kernels, pairs, spread,
+#                               solve, gather, finish
 KERNELS_PER_STEP_NOCELLS = 4
 KERNELS_PER_STEP_FUSED = 2     # mixed precision up to 64^3, no cell list: S1-S6 in one cluster launch, the forces
 KERNELS_PER_STEP_SPLIT = 4     # mixed up to 64^3 with a cell list: S1-S3, S8 beside the solve, S7/S9
@@ -415,9 +417,19 @@ def solve_kernel_name(precision, solver, w):
     return "k_mg_solve" if solver == "mg" else "k_cg_solve"
 
 
+def overlapped(precision, w, sms=152):
+    """True when the step runs the pairs beside the solve (the integer
+    V-cycle on grids of 128^3 and more with at least 2 cells per SM, unless
+    MAZE_OVERLAP=0)."""
+    return (precision == "fp64fix" and w.N >= 128 and has_cells(w) and int(np.floor(w.L / w.rc)) ** 3 >= 2 * sms
+            and os.environ.get("MAZE_OVERLAP") != "0")
+
+
 def kernels_per_step(precision, w, sms=152):
     if precision == "mixed" and w.N <= 64:
         return KERNELS_PER_STEP_SPLIT if has_cells(w) else KERNELS_PER_STEP_FUSED
+    if overlapped(precision, w, sms):
+        return KERNELS_PER_STEP_OVERLAP
     if has_cells(w) and int(np.floor(w.L / w.rc)) ** 3 >= 2 * sms:   # FP64, or mixed above 64^3
         return KERNELS_PER_STEP_HALF
     return KERNELS_PER_STEP_CELLS if has_cells(w) else KERNELS_PER_STEP_NOCELLS
@@ -615,10 +627,18 @@ def main():
                     e2e=not args.no_e2e)
     # the same box beside an FP64 multigrid headline (extra keys): the other
     # FP64 form of the solve, and mixed precision
-    mixed = other64 = None
+    mixed = other64 = serial = None
     if args.precision in ("fp64", "fp64fix") and args.solver == "mg" and not args.no_mixed:
         alt = "fp64" if args.precision == "fp64fix" else "fp64fix"
         other64 = (alt, time_box(args, M, w, alt, "mg", stream, flush, dist, dev, world, rank, e2e=False))
+        if args.precision == "fp64fix" and os.environ.get("MAZE_OVERLAP") != "0":
+            # the headline runs the pairs beside the solve: the solve kernel
+            # alone, from the same box with the overlap off
+            os.environ["MAZE_OVERLAP"] = "0"
+            try:
+                serial = time_box(args, M, w, "fp64fix", "mg", stream, flush, dist, dev, world, rank, e2e=False)
+            finally:
+                del os.environ["MAZE_OVERLAP"]
         mixed = time_box(args, M, w, "mixed", "mg", stream, flush, dist, dev, world, rank, e2e=False)
 
     if rank == 0:
@@ -659,6 +679,15 @@ def main():
                 "phase_us": o["phase_us"], "solve_us": 1e6 * o["solve_s"], "roofline": oroof,
                 "roofline_other": oother, "gpu_launches": kernels_per_step(alt, w, sms) * args.steps,
                 "clocks": o["clocks"]}
+        if serial is not None:
+            sroof, _ = rooflines(w, "fp64fix", "mg", serial["iters_per_step"], serial["solve_s"], args.workload, sms)
+            line["serial"] = {
+                "what": "the same box with the pairs after the solve on one stream (MAZE_OVERLAP=0): the solve "
+                        "kernel alone on the GPU; in the headline it shares every SM with the pair kernel",
+                "steps_per_s": serial["steps_per_s"], "ms_per_step": serial["ms_per_step"],
+                "iters_per_step": serial["iters_per_step"], "force_error": serial["force_error"],
+                "phase_us": serial["phase_us"], "solve_us": 1e6 * serial["solve_s"], "roofline": sroof,
+                "gpu_launches": KERNELS_PER_STEP_HALF * args.steps, "clocks": serial["clocks"]}
         if mixed is not None:
             mroof, _ = rooflines(w, "mixed", "mg", mixed["iters_per_step"], mixed["solve_s"], args.workload, sms)
             line["mixed"] = {

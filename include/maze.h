@@ -261,7 +261,12 @@ const char* maze_last_error(void);
 /* Device timing of the phases of the most recent maze_step / maze_step_async
  * step, in milliseconds, measured with CUDA events on the context's stream:
  * out[0] half kick + drift + spread, out[1] cell list, out[2] constraint
- * solve (S4-S6), out[3] forces + second half kick. maze_set_timing(ctx, 1)
+ * solve (S4-S6), out[3] forces + second half kick. (When the pair forces
+ * run on a second stream beside the solve - MAZE_FP64_FIXMG boxes of 128^3
+ * and more with at least two cells per SM, unless the environment sets
+ * MAZE_OVERLAP=0 - out[0] is the half kick + drift, out[1] the cell list and
+ * the spread, out[3] the wait for the pairs, the gather and the second half
+ * kick.) maze_set_timing(ctx, 1)
  * makes every step record these events (a small cost); maze_get_timing
  * synchronises and fails with MAZE_ERR_INVALID while timing is off. */
 maze_status maze_set_timing(maze_ctx* ctx, int32_t on);

@@ -1052,7 +1052,9 @@ struct HalfSmem {
   int bad;
 };
 
-template <int kW>
+// kGather: also S7 of the home ions (the single-kernel form); without it the
+// pairs alone (the form that runs beside the solve, whose potential S7 needs).
+template <int kW, bool kGather = true>
 __device__ __forceinline__ void pairs_half_cell(const ForceArgs& a, int c, HalfSmem<kW>& sm) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -1180,17 +1182,18 @@ __device__ __forceinline__ void pairs_half_cell(const ForceArgs& a, int c, HalfS
       }
     }
     // S7 for the home ions (their potential neighbourhood is the cell's)
-    for (int gi = warp; gi < gn; gi += kW) {
-      const int i = a.cell_ions[g0 + gi];
-      double gx, gy, gz, vd;
-      gather_el(a, i, lane, gx, gy, gz, vd);
-      if (lane == 0) {
-        a.gath[(size_t)i * 4] = gx;
-        a.gath[(size_t)i * 4 + 1] = gy;
-        a.gath[(size_t)i * 4 + 2] = gz;
-        a.gath[(size_t)i * 4 + 3] = vd;
+    if (kGather)
+      for (int gi = warp; gi < gn; gi += kW) {
+        const int i = a.cell_ions[g0 + gi];
+        double gx, gy, gz, vd;
+        gather_el(a, i, lane, gx, gy, gz, vd);
+        if (lane == 0) {
+          a.gath[(size_t)i * 4] = gx;
+          a.gath[(size_t)i * 4 + 1] = gy;
+          a.gath[(size_t)i * 4 + 2] = gz;
+          a.gath[(size_t)i * 4 + 3] = vd;
+        }
       }
-    }
     __syncthreads();
     for (int e = threadIdx.x; e < gn * 4; e += blockDim.x)
       atomicAdd(reinterpret_cast<unsigned long long*>(a.pair_fix) + (size_t)a.cell_ions[g0 + (e >> 2)] * 4 + (e & 3),
@@ -1199,6 +1202,25 @@ __device__ __forceinline__ void pairs_half_cell(const ForceArgs& a, int c, HalfS
   if (bad) atomicOr(&sm.bad, 1);
   __syncthreads();
   if (threadIdx.x == 0 && sm.bad) atomicCAS(&a.rec->status, MAZE_OK, MAZE_ERR_NONFINITE);
+}
+
+// S7 alone for the ions of cell c (to a.gath), one warp per ion.
+template <int kW>
+__device__ __forceinline__ void gather_cell(const ForceArgs& a, int c) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int c0 = a.cell_start[c], cn = a.cell_start[c + 1] - c0;
+  for (int gi = warp; gi < cn; gi += kW) {
+    const int i = a.cell_ions[c0 + gi];
+    double gx, gy, gz, vd;
+    gather_el(a, i, lane, gx, gy, gz, vd);
+    if (lane == 0) {
+      a.gath[(size_t)i * 4] = gx;
+      a.gath[(size_t)i * 4 + 1] = gy;
+      a.gath[(size_t)i * 4 + 2] = gz;
+      a.gath[(size_t)i * 4 + 3] = vd;
+    }
+  }
 }
 
 // The mixed-precision form of pairs_half_cell (boxes above 64^3, which run

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -362,7 +363,7 @@ MixedArgs mixed_args(maze_ctx* c, int zero_phi, double* q_out) {
   return a;
 }
 
-maze_status enqueue_solve(maze_ctx* c, int zero_phi, double* q_out) {
+maze_status enqueue_solve(maze_ctx* c, int zero_phi, double* q_out, bool narrow = false) {
   // (the one-cluster mixed solve synchronises and reduces in shared memory:
   // no grid counters or reduction records to clear)
   const bool cluster = c->mixed && c->mx_cluster > 0;
@@ -373,7 +374,9 @@ maze_status enqueue_solve(maze_ctx* c, int zero_phi, double* q_out) {
     CK(launch_mixed_solve(mixed_args(c, zero_phi, q_out), c->mx_cluster, c->mx_blocks, c->stream));
   } else if (c->cfg.solver == MAZE_SOLVER_MG) {
     CK(cudaMemsetAsync(c->bar, 0, sizeof(unsigned), c->stream));
-    if (c->fixmg) CK(launch_mgfix_solve(solve_args(c, zero_phi, q_out), c->mg, c->sblocks, c->stream));
+    if (c->fixmg)
+      CK(launch_mgfix_solve(solve_args(c, zero_phi, q_out), c->mg, narrow ? c->ov_blocks : c->sblocks,
+                            narrow ? c->ov_threads : 0, c->stream));
     else CK(launch_mg_solve(solve_args(c, zero_phi, q_out), c->mg, c->sblocks, c->stream));
   } else {
     CK(launch_cg_solve(solve_args(c, zero_phi, q_out), c->sblocks, c->stream));
@@ -462,6 +465,35 @@ maze_status enqueue_step(maze_ctx* c, int timed) {
     CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     if (s != MAZE_OK) return s;
     CK(launch_gather_finish(fa, c->fblocks, c->stream));
+    if (timed) CK(cudaEventRecordWithFlags(c->ev[4], c->stream, cudaEventRecordExternal));
+    return MAZE_OK;
+  }
+  if (c->overlap) {
+    // S8 needs only the positions and the cell list: after S1 and S2 it runs
+    // on the side stream, sharing every SM with S3 and the solve (S4-S6),
+    // whose V-cycle is bound by memory latency and integer work while the
+    // pairs are bound by the FP64 pipe; then S7 (needs phi^{k+1}) and S9.
+    // (Timed phases: S1; S2 and S3; the solve S4-S6; S7-S9.)
+    if (timed) CK(cudaEventRecordWithFlags(c->ev[0], c->stream, cudaEventRecordExternal));
+    const IonArgs ia = ion_args(c, 1, 1);
+    CK(launch_ion_update(ia, c->stream, 1));
+    if (timed) CK(cudaEventRecordWithFlags(c->ev[1], c->stream, cudaEventRecordExternal));
+    maze_status s = enqueue_cells(c);
+    if (s != MAZE_OK) return s;
+    const ForceArgs fa = force_args(c, c->phi[(c->ik + 2) % 3], 1, 1);
+    CK(cudaEventRecord(c->ev_fork, c->stream));
+    CK(cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
+    CK(launch_pairs_only(fa, c->ov_pair_blocks, c->ov_pair_smem, c->side_stream));
+    CK(cudaEventRecord(c->ev_join, c->side_stream));
+    CK(launch_ion_update(ia, c->stream, 2));
+    if (timed) CK(cudaEventRecordWithFlags(c->ev[2], c->stream, cudaEventRecordExternal));
+    s = enqueue_solve(c, 0, nullptr, true);
+    if (timed && s == MAZE_OK) CK(cudaEventRecordWithFlags(c->ev[3], c->stream, cudaEventRecordExternal));
+    // join the side stream before any return (a capture must not end forked)
+    CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    if (s != MAZE_OK) return s;
+    CK(launch_gather_cells(fa, c->stream));
+    CK(launch_finish_fix(fa, c->stream));
     if (timed) CK(cudaEventRecordWithFlags(c->ev[4], c->stream, cudaEventRecordExternal));
     return MAZE_OK;
   }
@@ -923,6 +955,26 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
       (!c->mixed || c->N > 64)) {
     AL(c->pair_fix, 4 * (size_t)n);
     AL(c->gath, 4 * (size_t)n);
+    const char* ov = getenv("MAZE_OVERLAP");   // "0": off; "TxP": T solve threads, P pair blocks per SM
+    int ot = 640, op = 1;
+    if (ov && sscanf(ov, "%dx%d", &ot, &op) != 2) ot = 0;
+    if (c->fixmg && mg_threads((int)ng) == kMgThreads && ot >= 256 && ot <= kMgThreads && ot % 32 == 0 && op >= 1 &&
+        op <= 3) {
+      int smem_sm = 0;
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+      c->overlap = true;
+      c->ov_threads = ot;
+      c->ov_blocks = c->num_sms;               // one solve block per SM
+      c->ov_pair_blocks = op * c->num_sms;
+      c->ov_pair_smem = smem_sm / (op + 1) + 1024;   // no more than op pair blocks fit on an SM
+      if (cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        free_ctx(c);
+        return fail(MAZE_ERR_CUDA, "cudaStreamCreate / cudaEventCreate failed");
+      }
+    }
   }
   if (c->split_step) {
     AL(c->pair_out, 4 * (size_t)n);

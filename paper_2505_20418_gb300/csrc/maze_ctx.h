@@ -103,6 +103,12 @@ struct maze_ctx {
   double* gath = nullptr;          // ... and their gather sums
   cudaStream_t side_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // FP64 state with the integer V-cycle on a box with once-per-pair forces:
+  // the pairs (k_pairs_only, ov_pair_blocks blocks padded to ov_pair_smem
+  // bytes of shared memory) run on side_stream beside the solve (ov_blocks x
+  // ov_threads), then S7 and S9; MAZE_OVERLAP=0 turns it off
+  bool overlap = false;
+  int ov_threads = 0, ov_blocks = 0, ov_pair_blocks = 0, ov_pair_smem = 0;
   // pinned staging of the per-ion host copies (standalone contexts, made on
   // first use): [0] maze_set of positions, [1] of velocities, [2] maze_get of
   // positions, [3] of velocities (and of the forces); an uploaded stage is

@@ -245,7 +245,8 @@ struct MixedArgs {
 };
 
 // Host-side launchers (defined in the .cu files).
-cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t s);   // k_move, then k_spread if a.qfix
+// S1 and S3: part 0 both, 1 the move (S1) only, 2 the spread (S3) only.
+cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t s, int part = 0);   // k_move, then k_spread if a.qfix
 cudaError_t launch_q_to_double(const unsigned long long* qfix, double* q, int n, cudaStream_t s);
 // maze_step_io's exchange (device-accessible pinned pointers): the device's
 // [2][3][n] positions and velocities -> [2][n][3] host order, and the
@@ -258,6 +259,8 @@ cudaError_t launch_pairs(const ForceArgs& a, cudaStream_t s);
 // S8 once per pair and S7 (FP64, a.pair_fix, a.gath), one block per cell;
 // then S9 one thread per ion.
 cudaError_t launch_pairs_half(const ForceArgs& a, cudaStream_t s);
+cudaError_t launch_pairs_only(const ForceArgs& a, int blocks, int smem_bytes, cudaStream_t s);
+cudaError_t launch_gather_cells(const ForceArgs& a, cudaStream_t s);
 cudaError_t launch_finish_fix(const ForceArgs& a, cudaStream_t s);
 cudaError_t launch_cluster_front(const IonArgs& ia, const CellArgs& ca, const MixedArgs& ma, int cluster,
                                  cudaStream_t s);
@@ -269,7 +272,7 @@ int solve_blocks(int n_points);
 void exp2_table(double* out64);
 cudaError_t launch_mg_solve(const SolveArgs& a, const MgArgs& g, int blocks, cudaStream_t s);
 int mg_blocks(int n_points);
-cudaError_t launch_mgfix_solve(const SolveArgs& a, const MgArgs& g, int blocks, cudaStream_t s);
+cudaError_t launch_mgfix_solve(const SolveArgs& a, const MgArgs& g, int blocks, int threads, cudaStream_t s);
 int mgfix_blocks(int n_points);
 cudaError_t launch_mixed_solve(const MixedArgs& a, int cluster, int blocks, cudaStream_t s);
 int mixed_cluster_size();

@@ -29,9 +29,9 @@ __global__ void k_q_to_double(const unsigned long long* qfix, double* q, int n) 
   if (i < n) q[i] = fix_to_dbl((long long)qfix[i], 1075 - 50);   // qfix 2^-50
 }
 
-cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t s) {
-  k_move<<<(a.n + kIonThreads - 1) / kIonThreads, kIonThreads, 0, s>>>(a);
-  if (a.qfix) {
+cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t s, int part) {
+  if (part != 2) k_move<<<(a.n + kIonThreads - 1) / kIonThreads, kIonThreads, 0, s>>>(a);
+  if (a.qfix && part != 1) {
     const int per = kSpreadThreads / 32;
     k_spread<<<(a.n + per - 1) / per, kSpreadThreads, 0, s>>>(a);
   }
@@ -331,6 +331,40 @@ __global__ void __launch_bounds__(kForceThreads) k_pairs_half(ForceArgs a) {
 __global__ void __launch_bounds__(kForceThreads) k_pairs_half_mixed(ForceArgs a) {
   __shared__ HalfSmemF<kForceThreads / 32> sm;
   if (forces_live(a)) pairs_half_cell_mixed<kForceThreads / 32>(a, blockIdx.x, sm);
+}
+
+// S8 alone (no gather), persistent: gridDim.x blocks take the cells in turn.
+// The block's shared memory is padded (dynamic size set by the launcher) so
+// that no more of these blocks share an SM than the launcher intends: the
+// form that runs beside the solve.
+__global__ void __launch_bounds__(kForceThreads) k_pairs_only(ForceArgs a) {
+  extern __shared__ __align__(16) unsigned char pairs_smem[];
+  HalfSmem<kForceThreads / 32>& sm = *reinterpret_cast<HalfSmem<kForceThreads / 32>*>(pairs_smem);
+  if (!forces_live(a)) return;
+  const int ncell = a.nc * a.nc * a.nc;
+  for (int c = blockIdx.x; c < ncell; c += gridDim.x) {
+    pairs_half_cell<kForceThreads / 32, false>(a, c, sm);
+    __syncthreads();
+  }
+}
+
+// S7 alone, one block per cell (after the solve, beside which k_pairs_only ran).
+__global__ void __launch_bounds__(kForceThreads) k_gather_cells(ForceArgs a) {
+  if (forces_live(a)) gather_cell<kForceThreads / 32>(a, blockIdx.x);
+}
+
+cudaError_t launch_pairs_only(const ForceArgs& a, int blocks, int smem_bytes, cudaStream_t s) {
+  const int need = (int)sizeof(HalfSmem<kForceThreads / 32>);
+  if (smem_bytes < need) smem_bytes = need;
+  cudaError_t e = cudaFuncSetAttribute(k_pairs_only, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return e;
+  k_pairs_only<<<blocks, kForceThreads, smem_bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_cells(const ForceArgs& a, cudaStream_t s) {
+  k_gather_cells<<<a.nc * a.nc * a.nc, kForceThreads, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pairs_half(const ForceArgs& a, cudaStream_t s) {

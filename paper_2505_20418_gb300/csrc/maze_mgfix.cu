@@ -590,10 +590,12 @@ int mgfix_blocks(int n_points) {
   return want < cap ? want : cap;
 }
 
-cudaError_t launch_mgfix_solve(const SolveArgs& a, const MgArgs& g, int blocks, cudaStream_t s) {
+// threads = 0: mg_threads(n); otherwise that many per block (at most
+// kMgThreads; fewer leave room on each SM for a kernel that runs beside).
+cudaError_t launch_mgfix_solve(const SolveArgs& a, const MgArgs& g, int blocks, int threads, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
-  cfg.blockDim = dim3(mg_threads(a.n));
+  cfg.blockDim = dim3(threads > 0 ? threads : mg_threads(a.n));
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];

@@ -51,10 +51,13 @@ def test_cuda_arm_line():
     assert r["traffic"] is None or r["traffic"] > 0
     e = d["e2e"]
     assert e["h2d_bytes_per_step"] == 48 * 512000 and e["d2h_bytes_per_step"] > 48 * 512000
-    assert d["gpu_launches"] == 8 * steps          # move, spread, 3 cell-list kernels, solve, pairs, gather
+    assert d["gpu_launches"] == 9 * steps          # move, 3 cell-list kernels, pairs, spread, solve, gather, finish
     assert d["clocks"]["sm_mhz"] > 0 and isinstance(d["clocks"]["reasons"], list)
     assert d["force_error"] < 1e-7                 # FP64 at tol 1e-10 (the solver tolerance dominates)
     assert d["ms_per_step"] > 0 and d["p99_us"] >= d["p50_us"] > 0
+    sr = d["serial"]
+    assert sr["iters_per_step"] == d["iters_per_step"] and sr["roofline"]["bound"] == "hbm"
+    assert sr["gpu_launches"] == 8 * steps
     f = d["fp64"]
     assert f["dtype"] == "f64" and f["iters_per_step"] == d["iters_per_step"]
     assert abs(f["force_error"] - d["force_error"]) < 1e-9

@@ -186,3 +186,35 @@ def test_large_box_parity_and_agreement_with_fp64():
     assert np.abs(phi - phr).max() < 1e-7 * np.abs(phr).max()
     for s in sims:
         s.close()
+
+
+def test_overlapped_step_matches_the_serial_step(monkeypatch):
+    """On large boxes the pairs run on a second stream beside a narrower
+    solve (k_pairs_only), and S7 after it (k_gather_cells). The pair and
+    V-cycle sums are exact integers; the FP64 mean of y is summed per thread,
+    so the two launch forms agree to rounding (MAZE_OVERLAP=0 turns the
+    overlap off), and each form is bitwise reproducible."""
+    w = synth.workload("nacl64000")
+    pos, vel, types = synth.make_state(w)
+    tf = synth.tosi_fumi_nacl()
+    sims = []
+    for ov in ("0", None, None):
+        if ov is None:
+            monkeypatch.delenv("MAZE_OVERLAP", raising=False)
+        else:
+            monkeypatch.setenv("MAZE_OVERLAP", ov)
+        sims.append(M.MazeSim(pos, vel, types, w.L, w.N, tf, r_cut=w.rc, dt=w.dt, tol=w.tol,
+                              solver=M.MAZE_SOLVER_MG, precision=M.MAZE_FP64_FIXMG))
+    for s in sims:
+        s.step(1)
+    F0, F1 = sims[0].get(M.MAZE_FORCE), sims[1].get(M.MAZE_FORCE)
+    assert force_err(F1, F0) < 1e-12
+    p0, p1 = sims[0].get(M.MAZE_PHI), sims[1].get(M.MAZE_PHI)
+    assert np.abs(p1 - p0).max() < 1e-12 * np.abs(p0).max()
+    assert sims[0].stats()["iters"] == sims[1].stats()["iters"]
+    for s in sims[1:]:
+        s.step(4)
+    for what in (M.MAZE_POS, M.MAZE_VEL, M.MAZE_FORCE, M.MAZE_PHI, M.MAZE_Y):
+        assert np.array_equal(sims[1].get(what), sims[2].get(what))
+    for s in sims:
+        s.close()
