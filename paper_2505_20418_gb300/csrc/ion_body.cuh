@@ -1110,34 +1110,66 @@ __device__ __forceinline__ void pairs_half_cell(const ForceArgs& a, int c, HalfS
         sm.acc[e][0] = sm.acc[e][1] = sm.acc[e][2] = sm.acc[e][3] = 0ull;
       }
       __syncthreads();
-      for (int gi = warp; gi < gn; gi += kW) {
-        const int islot = g0 + gi;
-        const int i = a.cell_ions[islot];
-        const double x = a.pos[i], y = a.pos[n + i], z = a.pos[2 * n + i];
-        const int ti = a.type[i];
-        const float4 pi32 = a.pos_sorted[islot];
-        int* q = sm.queue[warp];
-        int qn = 0;
-        long long sfx = 0, sfy = 0, sfz = 0, sv = 0;   // 2^-40 units
-        auto eval = [&](int e2) {
-          const double ddx = sm.xyz[0][e2] - x, ddy = sm.xyz[1][e2] - y, ddz = sm.xyz[2][e2] - z;
-          const double r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-          // (r2 >= 0: the integer order of the bit patterns is the numeric one)
-          if (__double_as_longlong(r2) >= __double_as_longlong(a.rc2)) return;
-          double fr, V;
-          tf_pair(a, ti + a.type[sm.j[e2]], r2, fr, V);
-          // force on the partner +fr d, on the home ion -fr d: the same 2^-40
-          // integers with opposite signs (the pair's momentum balance is exact)
-          const long long qx = fix40(fr * ddx), qy = fix40(fr * ddy), qz = fix40(fr * ddz), qv = fix40(V);
+      // The warp's home ions share one queue of passing candidates: a batch of
+      // 32 may hold the last pairs of one ion (the "previous" one, its
+      // entries first in the queue) and the first of the next, so the FP64
+      // arithmetic runs on full warps (the FP64 pipe issues a warp
+      // instruction at the same cost however many lanes are active).
+      int* q = sm.queue[warp];
+      int qn = 0;           // queued entries
+      int qc = 0;           // of which the first qc belong to the previous ion
+      int pgi = -1, pion = 0, pti = 0;
+      long long px = 0, py = 0, pz = 0, pv = 0;   // the previous ion's per-lane sums, 2^-40 units
+      auto flush_prev = [&]() {
+        const long long tx = warp_isum(px), ty = warp_isum(py), tz = warp_isum(pz), tv = warp_isum(pv);
+        if (lane == 0) {
+          sm.f[pgi][0] += (unsigned long long)tx;
+          sm.f[pgi][1] += (unsigned long long)ty;
+          sm.f[pgi][2] += (unsigned long long)tz;
+          sm.f[pgi][3] += (unsigned long long)tv;
+        }
+        px = py = pz = pv = 0;
+      };
+      double x = 0, y = 0, z = 0;   // the current home ion
+      int ti = 0;
+      long long sfx = 0, sfy = 0, sfz = 0, sv = 0;   // its per-lane sums, 2^-40 units
+      // pair (home, candidate e2); prv: the home ion is the previous one
+      auto eval = [&](int e2, bool prv) {
+        const double hx = prv ? a.pos[pion] : x, hy = prv ? a.pos[n + pion] : y, hz = prv ? a.pos[2 * n + pion] : z;
+        const double ddx = sm.xyz[0][e2] - hx, ddy = sm.xyz[1][e2] - hy, ddz = sm.xyz[2][e2] - hz;
+        const double r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+        // (r2 >= 0: the integer order of the bit patterns is the numeric one)
+        if (__double_as_longlong(r2) >= __double_as_longlong(a.rc2)) return;
+        double fr, V;
+        tf_pair(a, (prv ? pti : ti) + a.type[sm.j[e2]], r2, fr, V);
+        // force on the partner +fr d, on the home ion -fr d: the same 2^-40
+        // integers with opposite signs (the pair's momentum balance is exact)
+        const long long qx = fix40(fr * ddx), qy = fix40(fr * ddy), qz = fix40(fr * ddz), qv = fix40(V);
+        if (prv) {
+          px -= qx;
+          py -= qy;
+          pz -= qz;
+          pv += qv;
+        } else {
           sfx -= qx;
           sfy -= qy;
           sfz -= qz;
           sv += qv;
-          atomicAdd(&sm.acc[e2][0], (unsigned long long)qx);
-          atomicAdd(&sm.acc[e2][1], (unsigned long long)qy);
-          atomicAdd(&sm.acc[e2][2], (unsigned long long)qz);
-          atomicAdd(&sm.acc[e2][3], (unsigned long long)qv);
-        };
+        }
+        atomicAdd(&sm.acc[e2][0], (unsigned long long)qx);
+        atomicAdd(&sm.acc[e2][1], (unsigned long long)qy);
+        atomicAdd(&sm.acc[e2][2], (unsigned long long)qz);
+        atomicAdd(&sm.acc[e2][3], (unsigned long long)qv);
+      };
+      for (int gi = warp; gi < gn; gi += kW) {
+        const int islot = g0 + gi;
+        const int i = a.cell_ions[islot];
+        x = a.pos[i];
+        y = a.pos[n + i];
+        z = a.pos[2 * n + i];
+        ti = a.type[i];
+        const float4 pi32 = a.pos_sorted[islot];
+        sfx = sfy = sfz = sv = 0;
         for (int e0 = 0; e0 < len; e0 += 32) {
           const int e = e0 + lane;
           bool pass = false;
@@ -1155,25 +1187,50 @@ __device__ __forceinline__ void pairs_half_cell(const ForceArgs& a, int c, HalfS
           qn += __popc(m);
           __syncwarp();
           if (qn >= 32) {
-            eval(q[lane]);
+            eval(q[lane], lane < qc);
             __syncwarp();
+            if (qc > 0) {   // the previous ion's last entries are done
+              flush_prev();
+              qc = 0;
+            }
             if (lane < qn - 32) q[lane] = q[32 + lane];
             __syncwarp();
             qn -= 32;
           }
         }
-        if (lane < qn) eval(q[lane]);
-        __syncwarp();
-        // the home ion's share: each lane's 2^-40 integer sum, an exact
-        // integer warp sum (integer pipe; no FP64 shuffle tree)
-        const long long tx = warp_isum(sfx), ty = warp_isum(sfy), tz = warp_isum(sfz), tv = warp_isum(sv);
-        if (lane == 0) {
-          sm.f[gi][0] += (unsigned long long)tx;
-          sm.f[gi][1] += (unsigned long long)ty;
-          sm.f[gi][2] += (unsigned long long)tz;
-          sm.f[gi][3] += (unsigned long long)tv;
+        if (qc > 0) {
+          // the previous ion is still queued (this one passed too few
+          // candidates to fill a batch): finish both now
+          if (lane < qn) eval(q[lane], lane < qc);
+          __syncwarp();
+          flush_prev();
+          qc = 0;
+          qn = 0;
+          px = sfx;
+          py = sfy;
+          pz = sfz;
+          pv = sv;
+          pgi = gi;
+          flush_prev();
+        } else {
+          // this ion's remaining entries wait for the next ion's (none left:
+          // its sums are complete)
+          qc = qn;
+          pgi = gi;
+          pion = i;
+          pti = ti;
+          px = sfx;
+          py = sfy;
+          pz = sfz;
+          pv = sv;
+          if (qc == 0) flush_prev();
         }
       }
+      if (qn > 0) {
+        if (lane < qn) eval(q[lane], true);
+        __syncwarp();
+      }
+      if (pgi >= 0) flush_prev();
       __syncthreads();
       // the partners' shares of this chunk to the per-ion sums
       for (int e = threadIdx.x; e < len * 4; e += blockDim.x) {

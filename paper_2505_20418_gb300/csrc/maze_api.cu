@@ -955,11 +955,25 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
       (!c->mixed || c->N > 64)) {
     AL(c->pair_fix, 4 * (size_t)n);
     AL(c->gath, 4 * (size_t)n);
-    const char* ov = getenv("MAZE_OVERLAP");   // "0": off; "TxP": T solve threads, P pair blocks per SM
-    int ot = 640, op = 1;
-    if (ov && sscanf(ov, "%dx%d", &ot, &op) != 2) ot = 0;
-    if (c->fixmg && mg_threads((int)ng) == kMgThreads && ot >= 256 && ot <= kMgThreads && ot % 32 == 0 && op >= 1 &&
-        op <= 3) {
+    // the split of each SM: P pair blocks of kForceThreads and one solve
+    // block of T threads, T the largest whose registers fit beside them. The
+    // register file is split over the SM's 4 sub-partitions, warps are
+    // dealt to them in turn, and a warp takes 32 x (registers per thread,
+    // rounded up to 8): so per sub-partition ceil(pair warps / 4) pair warps
+    // and T / 128 solve warps must fit in a quarter of the file.
+    // MAZE_OVERLAP: "0" off, "TxP" (T 0: the largest that fits)
+    const char* ov = getenv("MAZE_OVERLAP");
+    int ot = 0, op = 1;
+    if (ov && sscanf(ov, "%dx%d", &ot, &op) != 2) ot = -1;
+    int regs_sm = 0;
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    const int rp = (pairs_only_regs() + 7) / 8 * 8, rs = (mgfix_regs() + 7) / 8 * 8;
+    const int pair_warps = op * kForceThreads / 32;
+    const int per_part = regs_sm / 4 - (pair_warps + 3) / 4 * 32 * rp;
+    int tmax = per_part > 0 ? per_part / (32 * rs) * 4 * 32 : 0;
+    if (tmax > kMgThreads) tmax = kMgThreads;
+    if (ot == 0 || ot > tmax) ot = tmax;
+    if (c->fixmg && mg_threads((int)ng) == kMgThreads && ot >= 256 && ot % 32 == 0 && op >= 1 && op <= 3) {
       int smem_sm = 0;
       cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
       c->overlap = true;

@@ -260,6 +260,8 @@ cudaError_t launch_pairs(const ForceArgs& a, cudaStream_t s);
 // then S9 one thread per ion.
 cudaError_t launch_pairs_half(const ForceArgs& a, cudaStream_t s);
 cudaError_t launch_pairs_only(const ForceArgs& a, int blocks, int smem_bytes, cudaStream_t s);
+int pairs_only_regs();   // registers per thread of k_pairs_only
+int mgfix_regs();        // and of k_mgfix_solve
 cudaError_t launch_gather_cells(const ForceArgs& a, cudaStream_t s);
 cudaError_t launch_finish_fix(const ForceArgs& a, cudaStream_t s);
 cudaError_t launch_cluster_front(const IonArgs& ia, const CellArgs& ca, const MixedArgs& ma, int cluster,

@@ -362,6 +362,12 @@ cudaError_t launch_pairs_only(const ForceArgs& a, int blocks, int smem_bytes, cu
   return cudaGetLastError();
 }
 
+int pairs_only_regs() {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, k_pairs_only) != cudaSuccess) return 255;
+  return fa.numRegs;
+}
+
 cudaError_t launch_gather_cells(const ForceArgs& a, cudaStream_t s) {
   k_gather_cells<<<a.nc * a.nc * a.nc, kForceThreads, 0, s>>>(a);
   return cudaGetLastError();

@@ -570,6 +570,13 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_mgfix_solve(SolveArgs a, MgAr
   }
 }
 
+// Registers per thread of the solve kernel (for sharing SMs with another kernel).
+int mgfix_regs() {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, k_mgfix_solve) != cudaSuccess) return 64;
+  return fa.numRegs;
+}
+
 // H of the fixed-point scale for a finest edge N: 58 - 2 ceil(log2 N).
 int mgfix_headroom(int N) {
   int c = 0;
