@@ -101,6 +101,16 @@ __device__ __forceinline__ void o_step(const LangevinArgs& o, int i, int t, unsi
   vz = o.a * vz + sd * (r23 * c3);
 }
 
+// A position wrapped into [0, L) exactly as maze_set wraps it on the host
+// (the same operations: an in-box value unchanged, else x - L floor(x / L)).
+__device__ __forceinline__ double wrap_set(double x, double L) {
+  if (x >= 0.0 && x < L) return x;
+  x -= L * floor(x / L);
+  if (x < 0.0) x += L;
+  if (x >= L) x = 0.0;
+  return x;
+}
+
 __device__ __forceinline__ double wrap_pos(double x, double L, double inv_L) {
   const long long k = floor_ll(x * inv_L);   // (integer pipe; 0 for a position already in the box)
   if (k != 0) x -= L * fix_to_dbl(k, 1075);
@@ -116,10 +126,12 @@ __device__ __forceinline__ void move_ion(const IonArgs& a, int i) {
   const int N = a.N, P = a.P;
   {
     // (maze_step_io's exchange: this step's positions and velocities straight
-    // from the caller's pinned [n][3] copy)
-    const double* pin = a.io_in ? a.io_in + 3 * (size_t)i : nullptr;
-    const double* vin = a.io_in ? a.io_in + 3 * ((size_t)a.n + i) : nullptr;
-    double x = pin ? pin[0] : a.pos[i], y = pin ? pin[1] : a.pos[a.n + i], z = pin ? pin[2] : a.pos[2 * a.n + i];
+    // from the caller's pinned [n][3] arrays, or the context's stage; the
+    // positions wrapped as maze_set wraps them)
+    const double* pin = a.io ? a.io->pos_in + 3 * (size_t)i : nullptr;
+    const double* vin = a.io ? a.io->vel_in + 3 * (size_t)i : nullptr;
+    double x = pin ? wrap_set(pin[0], a.L) : a.pos[i], y = pin ? wrap_set(pin[1], a.L) : a.pos[a.n + i],
+           z = pin ? wrap_set(pin[2], a.L) : a.pos[2 * a.n + i];
     const int t = a.type[i];
     if (pin && !a.do_move) {
       a.pos[i] = x;

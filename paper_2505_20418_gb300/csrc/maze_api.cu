@@ -8,6 +8,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
+#include <functional>
+#include <condition_variable>
 #include <atomic>
 #include <string>
 #include <thread>
@@ -179,7 +182,7 @@ IonArgs ion_args(maze_ctx* c, int do_move, int do_spread) {
   a.wbuf = c->wbuf;
   a.wbuf32 = c->mixed ? c->wbuf32 : nullptr;
   a.wbase = c->wbase;
-  a.io_in = do_move ? c->io_in_dev : nullptr;
+  a.io = (do_move && c->io_capture) ? c->io_desc : nullptr;
   a.rel_hi = c->mixed ? c->rel_hi : nullptr;
   a.rel_lo = c->mixed ? c->rel_lo : nullptr;
   a.cell_len = c->nc >= 3 ? c->L / c->nc : c->L;
@@ -611,6 +614,8 @@ void free_ctx(maze_ctx* c) {
   for (int g = 0; g < 3; ++g)
     if (c->io_graph[g]) cudaGraphExecDestroy(c->io_graph[g]);
   if (c->io_stage) cudaFreeHost(c->io_stage);
+  if (c->io_desc_host) cudaFreeHost(c->io_desc_host);
+  if (c->io_desc) cudaFree(c->io_desc);
   for (int k = 0; k < 5; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   for (void* p : c->allocs) {
@@ -629,6 +634,66 @@ void free_ctx(maze_ctx* c) {
   delete c;
 }
 
+// Host threads for the exchange's copies: created once per process and
+// kept (a thread started and joined per call costs more than a share of the
+// copies on the GPU machine's Arm cores), woken per job; the caller runs task 0,
+// the workers the rest. Jobs from several host threads run one at a time.
+class HostPool {
+ public:
+  explicit HostPool(int workers) {
+    for (int w = 0; w < workers; ++w) std::thread([this] { loop(); }).detach();
+  }
+  void run(int tasks, const std::function<void(int)>& job) {
+    std::lock_guard<std::mutex> one(run_mutex_);
+    {
+      std::lock_guard<std::mutex> g(m_);
+      job_ = &job;
+      tasks_ = tasks;
+      next_.store(1);
+      left_.store(tasks - 1);
+      ++gen_;
+    }
+    cv_.notify_all();
+    job(0);
+    work();
+    std::unique_lock<std::mutex> lk(m_);
+    done_.wait(lk, [&] { return left_.load() == 0; });
+  }
+
+ private:
+  void loop() {
+    unsigned seen = 0;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> lk(m_);
+        cv_.wait(lk, [&] { return gen_ != seen; });
+        seen = gen_;
+      }
+      work();
+    }
+  }
+  void work() {
+    for (int t; (t = next_.fetch_add(1)) < tasks_;) {
+      (*job_)(t);
+      if (left_.fetch_sub(1) == 1) {
+        std::lock_guard<std::mutex> g(m_);
+        done_.notify_all();
+      }
+    }
+  }
+  std::mutex run_mutex_, m_;
+  std::condition_variable cv_, done_;
+  unsigned gen_ = 0;
+  int tasks_ = 0;
+  std::atomic<int> next_{0}, left_{0};
+  const std::function<void(int)>* job_ = nullptr;
+};
+
+HostPool& host_pool() {
+  static HostPool* pool = new HostPool(15);   // never destroyed: its threads wait until the process ends
+  return *pool;
+}
+
 // fn(lo, hi) over [0, n) in chunks on host threads for large n (the per-ion
 // host loops of big boxes), else in the calling thread.
 template <class F>
@@ -640,12 +705,9 @@ void host_ranges(int n, F fn) {
     fn(0, n);
     return;
   }
-  std::vector<std::thread> th;
-  th.reserve(T - 1);
   const int chunk = (n + T - 1) / T;
-  for (int t = 1; t < T; ++t) th.emplace_back(fn, std::min(n, t * chunk), std::min(n, (t + 1) * chunk));
-  fn(0, std::min(n, chunk));
-  for (auto& x : th) x.join();
+  const std::function<void(int)> job = [&](int t) { fn(std::min(n, t * chunk), std::min(n, (t + 1) * chunk)); };
+  host_pool().run(T, job);
 }
 
 bool ion_finite(const maze_ctx* c, const double* in) {
@@ -1143,13 +1205,17 @@ maze_status build_io_graphs(maze_ctx* c) {
     cudaGetLastError();
     return MAZE_OK;   // (no device addresses: the separate form)
   }
-  const double* st_in = static_cast<const double*>(st);
-  double* st_out = static_cast<double*>(st) + n6;
+  c->io_stage_dev = static_cast<const double*>(st);
+  if (cudaMallocHost(&c->io_desc_host, sizeof(IoDesc)) != cudaSuccess ||
+      cudaMalloc(&c->io_desc, sizeof(IoDesc)) != cudaSuccess) {
+    cudaGetLastError();
+    return MAZE_OK;
+  }
   // read by the captured step's S1, and only there: cleared on every way out
-  c->io_in_dev = st_in;
+  c->io_capture = true;
   struct Clear {
     maze_ctx* c;
-    ~Clear() { c->io_in_dev = nullptr; }
+    ~Clear() { c->io_capture = false; }
   } clear{c};
   const int ik0 = c->ik;
   for (int g = 0; g < 3; ++g) {
@@ -1162,9 +1228,13 @@ maze_status build_io_graphs(maze_ctx* c) {
     }
     // the pinned stages and record are read and written by the SMs
     // directly (device addresses of the host allocations)
-    bool ok = cudaMemsetAsync(&c->rec->status, 0, sizeof(int32_t), c->stream) == cudaSuccess;
+    // (this exchange's buffer addresses, written by the host before each launch)
+    bool ok = cudaMemcpyAsync(c->io_desc, c->io_desc_host, sizeof(IoDesc), cudaMemcpyHostToDevice, c->stream) ==
+              cudaSuccess;
+    ok = ok && cudaMemsetAsync(&c->rec->status, 0, sizeof(int32_t), c->stream) == cudaSuccess;
     ok = ok && enqueue_step(c, 0) == MAZE_OK;
-    ok = ok && launch_io_out(c->pos, st_out, c->n, c->rec, rec_out, sizeof(maze_stats), c->stream) == cudaSuccess;
+    ok = ok && launch_io_out(c->pos, c->io_desc, c->n, c->rec, rec_out, sizeof(maze_stats), c->stream) ==
+                   cudaSuccess;
     const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
     if (!ok || e != cudaSuccess || !graph ||
         cudaGraphInstantiate(&c->io_graph[g], graph, 0) != cudaSuccess) {
@@ -1195,24 +1265,53 @@ maze_status step_io_graph(maze_ctx* c, const double* pos_in, const double* vel_i
   }
   const int64_t before = c->rec_host->step;
   const int ik0 = c->ik;
-  // inputs into the exchange stage in the caller's order (positions wrapped
-  // into [0, L) as maze_set does); the graph reorders them on the device
+  // Pinned caller arrays are read and written by the device directly (their
+  // device addresses go to the graph through the descriptor); other arrays
+  // pass through the context's pinned stage. Either way the inputs are
+  // checked on the host first (a non-finite value: nothing runs), and S1
+  // wraps the positions into [0, L) as maze_set does.
   const size_t n3 = 3 * (size_t)c->n;
   double* in = c->io_stage;
   const double* out = c->io_stage + 2 * n3;
-  const double L = c->L;
-  std::atomic<bool> bad{false};
-  host_ranges(c->n, [&, in, L](int lo, int hi) {
-    bool b = false;
-    for (size_t e = 3 * (size_t)lo; e < 3 * (size_t)hi; ++e) {
-      const double x = pos_in[e], v = vel_in[e];
-      b |= !isfinite(x) || !isfinite(v);
-      in[e] = wrap_host(x, L);
-      in[n3 + e] = v;
+  auto pinned = [](const void* p) -> void* {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
     }
-    if (b) bad.store(true, std::memory_order_relaxed);
-  });
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+  };
+  const void* dpi = pinned(pos_in);
+  const void* dvi = pinned(vel_in);
+  void* dpo = pinned(pos_out);
+  void* dvo = pinned(vel_out);
+  const bool direct_in = dpi && dvi, direct_out = dpo && dvo;
+  std::atomic<bool> bad{false};
+  if (direct_in) {
+    host_ranges(c->n, [&](int lo, int hi) {
+      bool b = false;
+      for (size_t e = 3 * (size_t)lo; e < 3 * (size_t)hi; ++e) b |= !isfinite(pos_in[e]) || !isfinite(vel_in[e]);
+      if (b) bad.store(true, std::memory_order_relaxed);
+    });
+  } else {
+    const double L = c->L;
+    host_ranges(c->n, [&, in, L](int lo, int hi) {
+      bool b = false;
+      for (size_t e = 3 * (size_t)lo; e < 3 * (size_t)hi; ++e) {
+        const double x = pos_in[e], v = vel_in[e];
+        b |= !isfinite(x) || !isfinite(v);
+        in[e] = wrap_host(x, L);
+        in[n3 + e] = v;
+      }
+      if (b) bad.store(true, std::memory_order_relaxed);
+    });
+  }
   if (bad.load()) return fail(MAZE_ERR_INVALID, "non-finite input");   // (nothing uploaded or run)
+  IoDesc& d = *c->io_desc_host;
+  d.pos_in = direct_in ? static_cast<const double*>(dpi) : c->io_stage_dev;
+  d.vel_in = direct_in ? static_cast<const double*>(dvi) : c->io_stage_dev + n3;
+  d.pos_out = direct_out ? static_cast<double*>(dpo) : const_cast<double*>(c->io_stage_dev) + 2 * n3;
+  d.vel_out = direct_out ? static_cast<double*>(dvo) : const_cast<double*>(c->io_stage_dev) + 3 * n3;
   c->rec_dirty = true;
   c->staged_fresh[0] = c->staged_fresh[1] = false;
   c->want_ion[0] = c->want_ion[1] = false;
@@ -1225,10 +1324,11 @@ maze_status step_io_graph(maze_ctx* c, const double* pos_in, const double* vel_i
     const int64_t done = c->rec_host->step - before;
     c->ik = (int)((ik0 + 2 * (done % 3)) % 3);
   }
-  host_ranges(c->n, [=](int lo, int hi) {
-    memcpy(pos_out + 3 * (size_t)lo, out + 3 * (size_t)lo, 3 * (size_t)(hi - lo) * sizeof(double));
-    memcpy(vel_out + 3 * (size_t)lo, out + n3 + 3 * (size_t)lo, 3 * (size_t)(hi - lo) * sizeof(double));
-  });
+  if (!direct_out)
+    host_ranges(c->n, [=](int lo, int hi) {
+      memcpy(pos_out + 3 * (size_t)lo, out + 3 * (size_t)lo, 3 * (size_t)(hi - lo) * sizeof(double));
+      memcpy(vel_out + 3 * (size_t)lo, out + n3 + 3 * (size_t)lo, 3 * (size_t)(hi - lo) * sizeof(double));
+    });
   if (stats_out) *stats_out = *c->rec_host;
   return status_message(c);
 }

@@ -127,7 +127,10 @@ struct maze_ctx {
   cudaGraphExec_t io_graph[3] = {nullptr, nullptr, nullptr};
   bool io_tried = false, io_ok = false;
   double* io_stage = nullptr;   // pinned [2][2][n][3]: positions, velocities in; then out
-  const double* io_in_dev = nullptr;   // device address of its input half, while the graphs are captured
+  const double* io_stage_dev = nullptr;   // its device address
+  maze::IoDesc* io_desc_host = nullptr;   // pinned: this exchange's buffers (device addresses)
+  maze::IoDesc* io_desc = nullptr;        // device copy, filled by the graph's first node
+  bool io_capture = false;                // S1 reads the exchange's inputs (while the graphs are captured)
   int timing = 0;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   int max_iter_init = 20000;

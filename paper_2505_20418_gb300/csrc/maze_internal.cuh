@@ -42,6 +42,15 @@ struct LangevinArgs {
   unsigned key0, key1;   // generator key (seed)
 };
 
+// maze_step_io's exchange buffers as device addresses of pinned host memory:
+// the caller's own arrays when they are pinned, else the context's stage.
+struct IoDesc {
+  const double* pos_in;   // [n][3]
+  const double* vel_in;   // [n][3]
+  double* pos_out;        // [n][3]
+  double* vel_out;        // [n][3]
+};
+
 struct IonArgs {
   int n;                 // ions
   double L, h;           // box edge, grid spacing
@@ -72,8 +81,9 @@ struct IonArgs {
   double* wdbuf;         // [n][3][4] weight derivatives dW/dt (Eq. F_Benoit, FP64) or nullptr
   float* wdbuf32;        // the same in FP32 (mixed precision) or nullptr
   LangevinArgs ou;       // OVRVO O steps (off when ou.on == 0)
-  const double* io_in;   // [2][n][3] positions, velocities in the caller's order (pinned, device
-                         // address: maze_step_io's exchange), read instead of pos / vel, or nullptr
+  const IoDesc* io;      // maze_step_io's exchange (device memory): this step's positions and
+                         // velocities in the caller's [n][3] order, read instead of pos / vel
+                         // (positions wrapped as maze_set wraps them), or nullptr
 };
 
 struct CellArgs {
@@ -251,7 +261,7 @@ cudaError_t launch_q_to_double(const unsigned long long* qfix, double* q, int n,
 // maze_step_io's exchange (device-accessible pinned pointers): the device's
 // [2][3][n] positions and velocities -> [2][n][3] host order, and the
 // record (rec_bytes a multiple of 8)
-cudaError_t launch_io_out(const double* soa, double* aos, int n, const void* rec, void* rec_out, size_t rec_bytes,
+cudaError_t launch_io_out(const double* soa, const IoDesc* io, int n, const void* rec, void* rec_out, size_t rec_bytes,
                           cudaStream_t s);
 cudaError_t launch_cells(const CellArgs& a, cudaStream_t s);
 cudaError_t launch_forces(const ForceArgs& a, int blocks, cudaStream_t s);

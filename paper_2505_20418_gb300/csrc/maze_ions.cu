@@ -41,17 +41,20 @@ cudaError_t launch_ion_update(const IonArgs& a, cudaStream_t s, int part) {
 // The read-back of maze_step_io's exchange, by the SMs on pinned host
 // memory (device addresses of the host allocations; no copy engine between
 // the step's kernels and the host): the device's [3][n] positions and
-// velocities (velocities after positions) -> [n][3] order, and the record's
-// words. (The inputs are read by the step's S1 itself: IonArgs::io_in.)
+// velocities (velocities after positions) -> [n][3] order into the arrays
+// the exchange descriptor names, and the record's words. (The inputs are
+// read by the step's S1 itself: IonArgs::io.)
 
-__global__ void k_io_out(const double* __restrict__ soa, double* __restrict__ aos, int n,
+__global__ void k_io_out(const double* __restrict__ soa, const IoDesc* __restrict__ io, int n,
                          const unsigned long long* __restrict__ rec, unsigned long long* __restrict__ rec_out,
                          int rec_words) {
   const int n3 = 3 * n;
+  double* const po = io->pos_out;
+  double* const vo = io->vel_out;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 2 * n3 + rec_words; e += gridDim.x * blockDim.x) {
     if (e < 2 * n3) {
       const int a = e >= n3 ? 1 : 0, r = e - a * n3, i = r / 3, d = r - 3 * i;
-      aos[e] = soa[a * n3 + d * n + i];
+      (a ? vo : po)[r] = soa[a * n3 + d * n + i];
     } else {
       rec_out[e - 2 * n3] = rec[e - 2 * n3];
     }
@@ -60,10 +63,10 @@ __global__ void k_io_out(const double* __restrict__ soa, double* __restrict__ ao
 
 static int io_blocks(int items) { return std::max(1, std::min(1216, (items + 255) / 256)); }
 
-cudaError_t launch_io_out(const double* soa, double* aos, int n, const void* rec, void* rec_out, size_t rec_bytes,
+cudaError_t launch_io_out(const double* soa, const IoDesc* io, int n, const void* rec, void* rec_out, size_t rec_bytes,
                           cudaStream_t s) {
   const int words = (int)(rec_bytes / 8);
-  k_io_out<<<io_blocks(6 * n + words), 256, 0, s>>>(soa, aos, n, static_cast<const unsigned long long*>(rec),
+  k_io_out<<<io_blocks(6 * n + words), 256, 0, s>>>(soa, io, n, static_cast<const unsigned long long*>(rec),
                                                     static_cast<unsigned long long*>(rec_out), words);
   return cudaGetLastError();
 }
