@@ -245,26 +245,33 @@ __device__ __forceinline__ void spread_ion(const IonArgs& a, int i, int lane) {
   const double Q = a.type[i] ? a.charge1 : a.charge0;
   long long v[2] = {0, 0};
   int idx[2] = {-1, -1};
+  // P is 2 or 4: support index sidx = ia + P (ib + P ic) by shifts; a lane's
+  // two points (sidx = lane, lane + 32) share ia and ib, so the FP64 product
+  // Q w_a w_b is formed once per lane
+  const int lp = P == 4 ? 2 : 1;
+  const int ia = lane & (P - 1), ib = (lane >> lp) & (P - 1);
+  double qab = 0.0;
+  if (!a.wbuf32) {
+    const double* w = a.wbuf + (size_t)i * 12;
+    qab = Q * w[ia] * w[4 + ib];
+  }
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
     const int sidx = lane + 32 * u;
     if (sidx >= P3) continue;
-    // P is 2 or 4: sidx = ia + P (ib + P ic) by shifts
-    const int lp = P == 4 ? 2 : 1;
-    const int ia = sidx & (P - 1), ib = (sidx >> lp) & (P - 1), ic = sidx >> (2 * lp);
+    const int ic = sidx >> (2 * lp);
     if (a.wbuf32) {
       // mixed precision: FP32 products
       const float* w = a.wbuf32 + (size_t)i * 12;
       v[u] = round_scaled_f(dbl_to_flt(Q) * w[8 + ic] * w[4 + ib] * w[ia], 50);   // 2^50 = kQScale
     } else {
-      const double* w = a.wbuf + (size_t)i * 12;
-      v[u] = round_scaled(Q * w[8 + ic] * w[4 + ib] * w[ia], 50);   // 2^50 = kQScale
+      v[u] = round_scaled(qab * a.wbuf[(size_t)i * 12 + 8 + ic], 50);   // 2^50 = kQScale
     }
     const int ix = wrap_idx(b.x + ia, N), iy = wrap_idx(b.y + ib, N), iz = wrap_idx(b.z + ic, N);
     idx[u] = (int)(((size_t)iz * N + iy) * N + ix);
   }
   const long long total = warp_isum(v[0] + v[1]);
-  if (lane == 0) v[0] += __double2ll_rn(Q * kQScale) - total;
+  if (lane == 0) v[0] += round_scaled(Q, 50) - total;   // (Q 2^50 exactly, on the integer pipe)
 #pragma unroll
   for (int u = 0; u < 2; ++u)
     if (idx[u] >= 0) atomicAdd(&a.qfix[idx[u]], (unsigned long long)v[u]);
@@ -1057,7 +1064,8 @@ struct HalfSmem {
   __align__(16) double xyz[3][kHalfChunk];         // FP64 positions
   int j[kHalfChunk];                               // ion
   int slot[kHalfChunk];                            // cell-list slot
-  unsigned long long acc[kHalfChunk][4];           // partners' shares, fixed point
+  unsigned long long acc[4][kHalfChunk];           // partners' shares, fixed point (component-major:
+                                                   // a warp's atomics on 32 candidates hit distinct banks)
   int lo[kHalfNbr], cum[kHalfNbr + 1];
   unsigned long long f[kCellGroup][4];             // home ions' shares, fixed point
   int queue[kW][64];
@@ -1119,7 +1127,7 @@ __device__ __forceinline__ void pairs_half_cell(const ForceArgs& a, int c, HalfS
         sm.xyz[0][e] = a.pos[j] + shx;
         sm.xyz[1][e] = a.pos[n + j] + shy;
         sm.xyz[2][e] = a.pos[2 * n + j] + shz;
-        sm.acc[e][0] = sm.acc[e][1] = sm.acc[e][2] = sm.acc[e][3] = 0ull;
+        sm.acc[0][e] = sm.acc[1][e] = sm.acc[2][e] = sm.acc[3][e] = 0ull;
       }
       __syncthreads();
       // The warp's home ions share one queue of passing candidates: a batch of
@@ -1168,10 +1176,10 @@ __device__ __forceinline__ void pairs_half_cell(const ForceArgs& a, int c, HalfS
           sfz -= qz;
           sv += qv;
         }
-        atomicAdd(&sm.acc[e2][0], (unsigned long long)qx);
-        atomicAdd(&sm.acc[e2][1], (unsigned long long)qy);
-        atomicAdd(&sm.acc[e2][2], (unsigned long long)qz);
-        atomicAdd(&sm.acc[e2][3], (unsigned long long)qv);
+        atomicAdd(&sm.acc[0][e2], (unsigned long long)qx);
+        atomicAdd(&sm.acc[1][e2], (unsigned long long)qy);
+        atomicAdd(&sm.acc[2][e2], (unsigned long long)qz);
+        atomicAdd(&sm.acc[3][e2], (unsigned long long)qv);
       };
       for (int gi = warp; gi < gn; gi += kW) {
         const int islot = g0 + gi;
@@ -1246,7 +1254,7 @@ __device__ __forceinline__ void pairs_half_cell(const ForceArgs& a, int c, HalfS
       __syncthreads();
       // the partners' shares of this chunk to the per-ion sums
       for (int e = threadIdx.x; e < len * 4; e += blockDim.x) {
-        const unsigned long long v = sm.acc[e >> 2][e & 3];
+        const unsigned long long v = sm.acc[e & 3][e >> 2];
         if (v) atomicAdd(reinterpret_cast<unsigned long long*>(a.pair_fix) + (size_t)sm.j[e >> 2] * 4 + (e & 3), v);
       }
     }
