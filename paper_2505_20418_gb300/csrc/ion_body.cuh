@@ -1311,7 +1311,7 @@ struct HalfSmemF {
   float4 l[kHalfChunk];
   int j[kHalfChunk];
   int slot[kHalfChunk];
-  unsigned long long acc[kHalfChunk][4];
+  unsigned long long acc[4][kHalfChunk];   // component-major
   int lo[kHalfNbr], cum[kHalfNbr + 1];
   unsigned long long f[kCellGroup][4];
   int queue[kW][64];
@@ -1369,42 +1369,70 @@ __device__ __forceinline__ void pairs_half_cell_mixed(const ForceArgs& a, int c,
                               __fadd_rn(ez, __fadd_rn(ll.z, oz * a.cell_len_l)), ll.w);
         sm.j[e] = a.cell_ions[slot];
         sm.slot[e] = tt < self_end ? slot : 0x7fffffff;
-        sm.acc[e][0] = sm.acc[e][1] = sm.acc[e][2] = sm.acc[e][3] = 0ull;
+        sm.acc[0][e] = sm.acc[1][e] = sm.acc[2][e] = sm.acc[3][e] = 0ull;
       }
       __syncthreads();
-      for (int gi = warp; gi < gn; gi += kW) {
-        const int islot = g0 + gi;
-        const float4 ph = a.rel_hi_sorted[islot], pl = a.rel_lo_sorted[islot];
+      // one queue of passing candidates for the warp's home ions, as in the
+      // FP64 kernel: batches of 32 on full warps, a batch's first entries
+      // possibly the previous ion's
+      int* q = sm.queue[warp];
+      int qn = 0, qc = 0;
+      int pgi = -1, pslot = 0;
+      long long px = 0, py = 0, pz = 0, pv = 0;   // the previous ion's per-lane sums, 2^-40 units
+      auto flush_prev = [&]() {
+        const long long tx = warp_isum(px), ty = warp_isum(py), tz = warp_isum(pz), tv = warp_isum(pv);
+        if (lane == 0) {
+          sm.f[pgi][0] += (unsigned long long)tx;
+          sm.f[pgi][1] += (unsigned long long)ty;
+          sm.f[pgi][2] += (unsigned long long)tz;
+          sm.f[pgi][3] += (unsigned long long)tv;
+        }
+        px = py = pz = pv = 0;
+      };
+      int islot = 0;
+      long long sfx = 0, sfy = 0, sfz = 0, sv = 0;   // the current ion's per-lane sums, 2^-40 units
+      auto eval = [&](int e2, bool prv) {
+        const int hs = prv ? pslot : islot;
+        const float4 ph = a.rel_hi_sorted[hs], pl = a.rel_lo_sorted[hs];
         const int ti = (int)pl.w;
-        int* q = sm.queue[warp];
-        int qn = 0;
-        float sfx = 0.f, sfy = 0.f, sfz = 0.f, sv = 0.f;
-        auto eval = [&](int e2) {
-          const float4 h = sm.h[e2], l = sm.l[e2];
-          const float dx = disp_df(ph.x, pl.x, h.x, l.x, 0.f, 0.f);
-          const float dy = disp_df(ph.y, pl.y, h.y, l.y, 0.f, 0.f);
-          const float dz = disp_df(ph.z, pl.z, h.z, l.z, 0.f, 0.f);
-          const float r2 = dx * dx + dy * dy + dz * dz;
-          if (r2 >= a.rc2f) return;
-          const int kind = ti + (int)l.w;
-          const float ir = rsqrtf(r2);
-          const float r = r2 * ir;
-          const float ir2 = ir * ir;
-          const float ir6 = ir2 * ir2 * ir2;
-          const float ir8 = ir6 * ir2;
-          const float exv = a.Af[kind] * expf(a.Bf * (a.sf[kind] - r));
-          const float V = exv - a.Cf[kind] * ir6 - a.Df[kind] * ir8 - a.Vcf[kind];
-          const float fr = a.Bf * exv * ir - 6.f * a.Cf[kind] * ir8 - 8.f * a.Df[kind] * ir8 * ir2;
-          const float fx = fr * dx, fy = fr * dy, fz = fr * dz;
-          sfx -= fx;
-          sfy -= fy;
-          sfz -= fz;
-          sv += V;
-          atomicAdd(&sm.acc[e2][0], (unsigned long long)round_scaled_f(fx, 40));
-          atomicAdd(&sm.acc[e2][1], (unsigned long long)round_scaled_f(fy, 40));
-          atomicAdd(&sm.acc[e2][2], (unsigned long long)round_scaled_f(fz, 40));
-          atomicAdd(&sm.acc[e2][3], (unsigned long long)round_scaled_f(V, 40));
-        };
+        const float4 h = sm.h[e2], l = sm.l[e2];
+        const float dx = disp_df(ph.x, pl.x, h.x, l.x, 0.f, 0.f);
+        const float dy = disp_df(ph.y, pl.y, h.y, l.y, 0.f, 0.f);
+        const float dz = disp_df(ph.z, pl.z, h.z, l.z, 0.f, 0.f);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 >= a.rc2f) return;
+        const int kind = ti + (int)l.w;
+        const float ir = rsqrtf(r2);
+        const float r = r2 * ir;
+        const float ir2 = ir * ir;
+        const float ir6 = ir2 * ir2 * ir2;
+        const float ir8 = ir6 * ir2;
+        const float exv = a.Af[kind] * expf(a.Bf * (a.sf[kind] - r));
+        const float V = exv - a.Cf[kind] * ir6 - a.Df[kind] * ir8 - a.Vcf[kind];
+        const float fr = a.Bf * exv * ir - 6.f * a.Cf[kind] * ir8 - 8.f * a.Df[kind] * ir8 * ir2;
+        // the partner +f, the home ion -f: the same 2^-40 integers
+        const long long qx = round_scaled_f(fr * dx, 40), qy = round_scaled_f(fr * dy, 40),
+                        qz = round_scaled_f(fr * dz, 40), qv = round_scaled_f(V, 40);
+        if (prv) {
+          px -= qx;
+          py -= qy;
+          pz -= qz;
+          pv += qv;
+        } else {
+          sfx -= qx;
+          sfy -= qy;
+          sfz -= qz;
+          sv += qv;
+        }
+        atomicAdd(&sm.acc[0][e2], (unsigned long long)qx);
+        atomicAdd(&sm.acc[1][e2], (unsigned long long)qy);
+        atomicAdd(&sm.acc[2][e2], (unsigned long long)qz);
+        atomicAdd(&sm.acc[3][e2], (unsigned long long)qv);
+      };
+      for (int gi = warp; gi < gn; gi += kW) {
+        islot = g0 + gi;
+        const float4 ph = a.rel_hi_sorted[islot];
+        sfx = sfy = sfz = sv = 0;
         for (int e0 = 0; e0 < len; e0 += 32) {
           const int e = e0 + lane;
           bool pass = false;
@@ -1420,28 +1448,49 @@ __device__ __forceinline__ void pairs_half_cell_mixed(const ForceArgs& a, int c,
           qn += __popc(m);
           __syncwarp();
           if (qn >= 32) {
-            eval(q[lane]);
+            eval(q[lane], lane < qc);
             __syncwarp();
+            if (qc > 0) {
+              flush_prev();
+              qc = 0;
+            }
             if (lane < qn - 32) q[lane] = q[32 + lane];
             __syncwarp();
             qn -= 32;
           }
         }
-        if (lane < qn) eval(q[lane]);
-        __syncwarp();
-        // each lane's FP32 sums to fixed point, an exact integer warp sum
-        const long long tx = warp_isum(round_scaled_f(sfx, 40)), ty = warp_isum(round_scaled_f(sfy, 40)),
-                        tz = warp_isum(round_scaled_f(sfz, 40)), tv = warp_isum(round_scaled_f(sv, 40));
-        if (lane == 0) {
-          sm.f[gi][0] += (unsigned long long)tx;
-          sm.f[gi][1] += (unsigned long long)ty;
-          sm.f[gi][2] += (unsigned long long)tz;
-          sm.f[gi][3] += (unsigned long long)tv;
+        if (qc > 0) {
+          // the previous ion is still queued: finish both now
+          if (lane < qn) eval(q[lane], lane < qc);
+          __syncwarp();
+          flush_prev();
+          qc = 0;
+          qn = 0;
+          px = sfx;
+          py = sfy;
+          pz = sfz;
+          pv = sv;
+          pgi = gi;
+          flush_prev();
+        } else {
+          qc = qn;
+          pgi = gi;
+          pslot = islot;
+          px = sfx;
+          py = sfy;
+          pz = sfz;
+          pv = sv;
+          if (qc == 0) flush_prev();
         }
       }
+      if (qn > 0) {
+        if (lane < qn) eval(q[lane], true);
+        __syncwarp();
+      }
+      if (pgi >= 0) flush_prev();
       __syncthreads();
       for (int e = threadIdx.x; e < len * 4; e += blockDim.x) {
-        const unsigned long long v = sm.acc[e >> 2][e & 3];
+        const unsigned long long v = sm.acc[e & 3][e >> 2];
         if (v) atomicAdd(reinterpret_cast<unsigned long long*>(a.pair_fix) + (size_t)sm.j[e >> 2] * 4 + (e & 3), v);
       }
     }
