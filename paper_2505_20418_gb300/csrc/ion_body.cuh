@@ -1318,7 +1318,7 @@ struct HalfSmemF {
   int bad;
 };
 
-template <int kW>
+template <int kW, bool kGather = true>
 __device__ __forceinline__ void pairs_half_cell_mixed(const ForceArgs& a, int c, HalfSmemF<kW>& sm) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -1494,17 +1494,18 @@ __device__ __forceinline__ void pairs_half_cell_mixed(const ForceArgs& a, int c,
         if (v) atomicAdd(reinterpret_cast<unsigned long long*>(a.pair_fix) + (size_t)sm.j[e >> 2] * 4 + (e & 3), v);
       }
     }
-    for (int gi = warp; gi < gn; gi += kW) {
-      const int i = a.cell_ions[g0 + gi];
-      double gx, gy, gz, vd;
-      gather_el(a, i, lane, gx, gy, gz, vd);
-      if (lane == 0) {
-        a.gath[(size_t)i * 4] = gx;
-        a.gath[(size_t)i * 4 + 1] = gy;
-        a.gath[(size_t)i * 4 + 2] = gz;
-        a.gath[(size_t)i * 4 + 3] = vd;
+    if (kGather)
+      for (int gi = warp; gi < gn; gi += kW) {
+        const int i = a.cell_ions[g0 + gi];
+        double gx, gy, gz, vd;
+        gather_el(a, i, lane, gx, gy, gz, vd);
+        if (lane == 0) {
+          a.gath[(size_t)i * 4] = gx;
+          a.gath[(size_t)i * 4 + 1] = gy;
+          a.gath[(size_t)i * 4 + 2] = gz;
+          a.gath[(size_t)i * 4 + 3] = vd;
+        }
       }
-    }
     __syncthreads();
     for (int e = threadIdx.x; e < gn * 4; e += blockDim.x)
       atomicAdd(reinterpret_cast<unsigned long long*>(a.pair_fix) + (size_t)a.cell_ions[g0 + (e >> 2)] * 4 + (e & 3),

@@ -374,7 +374,8 @@ maze_status enqueue_solve(maze_ctx* c, int zero_phi, double* q_out, bool narrow 
   if (!zero_phi && c->cfg.scheme != MAZE_SCHEME_MAZE) CK(cudaMemsetAsync(c->y, 0, c->ng * 8, c->stream));
   if (c->mixed) {
     if (!cluster) CK(cudaMemsetAsync(c->bar, 0, sizeof(unsigned), c->stream));
-    CK(launch_mixed_solve(mixed_args(c, zero_phi, q_out), c->mx_cluster, c->mx_blocks, c->stream));
+    CK(launch_mixed_solve(mixed_args(c, zero_phi, q_out), c->mx_cluster, narrow ? c->ov_blocks : c->mx_blocks,
+                          c->stream, narrow ? c->ov_threads : 0));
   } else if (c->cfg.solver == MAZE_SOLVER_MG) {
     CK(cudaMemsetAsync(c->bar, 0, sizeof(unsigned), c->stream));
     if (c->fixmg)
@@ -1029,13 +1030,18 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
     if (ov && sscanf(ov, "%dx%d", &ot, &op) != 2) ot = -1;
     int regs_sm = 0;
     cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-    const int rp = (pairs_only_regs() + 7) / 8 * 8, rs = (mgfix_regs() + 7) / 8 * 8;
+    const int rp = (pairs_only_regs(c->mixed) + 7) / 8 * 8;
+    const int rs = ((c->mixed ? mixed_grid_regs() : mgfix_regs()) + 7) / 8 * 8;
     const int pair_warps = op * kForceThreads / 32;
     const int per_part = regs_sm / 4 - (pair_warps + 3) / 4 * 32 * rp;
     int tmax = per_part > 0 ? per_part / (32 * rs) * 4 * 32 : 0;
     if (tmax > kMgThreads) tmax = kMgThreads;
     if (ot == 0 || ot > tmax) ot = tmax;
-    if (c->fixmg && mg_threads((int)ng) == kMgThreads && ot >= 256 && ot % 32 == 0 && op >= 1 && op <= 3) {
+    // (the integer V-cycle on grids of 128^3 and more; the mixed solve in its
+    // cooperative grid form, which needs at least 512 threads per block)
+    const bool form = (c->fixmg && mg_threads((int)ng) == kMgThreads) ||
+                      (c->mixed && c->mx_cluster == 0 && c->N >= 128 && ot >= 512);
+    if (form && ot >= 256 && ot % 32 == 0 && op >= 1 && op <= 3) {
       int smem_sm = 0;
       cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
       c->overlap = true;

@@ -270,8 +270,9 @@ cudaError_t launch_pairs(const ForceArgs& a, cudaStream_t s);
 // then S9 one thread per ion.
 cudaError_t launch_pairs_half(const ForceArgs& a, cudaStream_t s);
 cudaError_t launch_pairs_only(const ForceArgs& a, int blocks, int smem_bytes, cudaStream_t s);
-int pairs_only_regs();   // registers per thread of k_pairs_only
-int mgfix_regs();        // and of k_mgfix_solve
+int pairs_only_regs(bool mixed);   // registers per thread of k_pairs_only(_mixed)
+int mgfix_regs();                  // and of k_mgfix_solve
+int mixed_grid_regs();             // and of k_mixed_grid
 cudaError_t launch_gather_cells(const ForceArgs& a, cudaStream_t s);
 cudaError_t launch_finish_fix(const ForceArgs& a, cudaStream_t s);
 cudaError_t launch_cluster_front(const IonArgs& ia, const CellArgs& ca, const MixedArgs& ma, int cluster,
@@ -286,7 +287,9 @@ cudaError_t launch_mg_solve(const SolveArgs& a, const MgArgs& g, int blocks, cud
 int mg_blocks(int n_points);
 cudaError_t launch_mgfix_solve(const SolveArgs& a, const MgArgs& g, int blocks, int threads, cudaStream_t s);
 int mgfix_blocks(int n_points);
-cudaError_t launch_mixed_solve(const MixedArgs& a, int cluster, int blocks, cudaStream_t s);
+// threads > 0: the cooperative grid form with that many threads per block
+// (at least 512; fewer than kMixedGridThreads leave room beside it)
+cudaError_t launch_mixed_solve(const MixedArgs& a, int cluster, int blocks, cudaStream_t s, int threads = 0);
 int mixed_cluster_size();
 int cluster_step_size();
 // S1-S6 of one mixed-precision step of a box up to 64^3 in one cluster launch.

@@ -336,7 +336,8 @@ __global__ void __launch_bounds__(kForceThreads) k_pairs_half_mixed(ForceArgs a)
   if (forces_live(a)) pairs_half_cell_mixed<kForceThreads / 32>(a, blockIdx.x, sm);
 }
 
-// S8 alone (no gather), persistent: gridDim.x blocks take the cells in turn.
+// S8 alone (no gather), persistent: gridDim.x blocks take the cells in turn
+// (FP64, or the FP32 pair arithmetic of mixed precision).
 // The block's shared memory is padded (dynamic size set by the launcher) so
 // that no more of these blocks share an SM than the launcher intends: the
 // form that runs beside the solve.
@@ -351,23 +352,41 @@ __global__ void __launch_bounds__(kForceThreads) k_pairs_only(ForceArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(kForceThreads) k_pairs_only_mixed(ForceArgs a) {
+  extern __shared__ __align__(16) unsigned char pairs_smem[];
+  HalfSmemF<kForceThreads / 32>& sm = *reinterpret_cast<HalfSmemF<kForceThreads / 32>*>(pairs_smem);
+  if (!forces_live(a)) return;
+  const int ncell = a.nc * a.nc * a.nc;
+  for (int c = blockIdx.x; c < ncell; c += gridDim.x) {
+    pairs_half_cell_mixed<kForceThreads / 32, false>(a, c, sm);
+    __syncthreads();
+  }
+}
+
 // S7 alone, one block per cell (after the solve, beside which k_pairs_only ran).
 __global__ void __launch_bounds__(kForceThreads) k_gather_cells(ForceArgs a) {
   if (forces_live(a)) gather_cell<kForceThreads / 32>(a, blockIdx.x);
 }
 
 cudaError_t launch_pairs_only(const ForceArgs& a, int blocks, int smem_bytes, cudaStream_t s) {
-  const int need = (int)sizeof(HalfSmem<kForceThreads / 32>);
+  const int need = a.mixed ? (int)sizeof(HalfSmemF<kForceThreads / 32>) : (int)sizeof(HalfSmem<kForceThreads / 32>);
   if (smem_bytes < need) smem_bytes = need;
-  cudaError_t e = cudaFuncSetAttribute(k_pairs_only, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-  if (e != cudaSuccess) return e;
-  k_pairs_only<<<blocks, kForceThreads, smem_bytes, s>>>(a);
+  if (a.mixed) {
+    cudaError_t e = cudaFuncSetAttribute(k_pairs_only_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e != cudaSuccess) return e;
+    k_pairs_only_mixed<<<blocks, kForceThreads, smem_bytes, s>>>(a);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_pairs_only, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e != cudaSuccess) return e;
+    k_pairs_only<<<blocks, kForceThreads, smem_bytes, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
-int pairs_only_regs() {
+int pairs_only_regs(bool mixed) {
   cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, k_pairs_only) != cudaSuccess) return 255;
+  if (cudaFuncGetAttributes(&fa, mixed ? (const void*)k_pairs_only_mixed : (const void*)k_pairs_only) != cudaSuccess)
+    return 255;
   return fa.numRegs;
 }
 

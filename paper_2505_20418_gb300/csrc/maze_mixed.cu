@@ -62,7 +62,13 @@ int mixed_grid_blocks(int n_points) {
   return want < cap ? want : cap;
 }
 
-cudaError_t launch_mixed_solve(const MixedArgs& a, int cluster, int blocks, cudaStream_t s) {
+int mixed_grid_regs() {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, k_mixed_grid) != cudaSuccess) return 64;
+  return fa.numRegs;
+}
+
+cudaError_t launch_mixed_solve(const MixedArgs& a, int cluster, int blocks, cudaStream_t s, int threads) {
   cudaLaunchConfig_t cfg = {};
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -78,7 +84,7 @@ cudaError_t launch_mixed_solve(const MixedArgs& a, int cluster, int blocks, cuda
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_mixed_cluster, a);
   }
-  cfg.blockDim = dim3(kMixedGridThreads);
+  cfg.blockDim = dim3(threads > 0 ? threads : kMixedGridThreads);
   cfg.gridDim = dim3(blocks);
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
