@@ -488,6 +488,24 @@ maze_status maze_convert_probe(const double* in, int32_t n, float* f_own, float*
  * when a CUDA call fails, else MAZE_OK. */
 maze_status maze_exp_probe(const double* in, int32_t n, double* own, double* ref);
 
+/* Diagnostic: the double-float arithmetic that the FP64 boxes' once-per-pair
+ * kernel runs on the FP32 pipe (Sec. III's Tosi-Fumi pair, evaluated as an
+ * unevaluated sum of two floats to ~1e-14 relative), for n host doubles in[],
+ * each split into (hi, lo) floats first (hi = in rounded to FP32, lo = the
+ * rest rounded to FP32). what = 0: out0[i] = exp(in[i]) by the double-float
+ * table method (out1 and cfg unused, may be NULL). what = 1: in[i] is a
+ * squared distance r^2 (A^2) of a pair of kind kind[i] (0 Na-Na, 1 Na-Cl,
+ * 2 Cl-Cl) with the Tosi-Fumi table and r_cut of *cfg; out0[i] = -(dV/dr)/r
+ * (eV/A^2), out1[i] = V(r) - V(r_cut) (eV), as hi + lo. what = 2: the same
+ * pair in FP64 arithmetic (the form of the other force kernels). Only the
+ * Tosi-Fumi fields and r_cut of cfg are read. Host arrays of n elements owned
+ * by the caller; the call allocates, copies and synchronises on the legacy
+ * default stream. Returns MAZE_ERR_INVALID for another what, n < 0, a NULL
+ * array that the mode reads or writes, or a kind outside 0..2;
+ * MAZE_ERR_CUDA when a CUDA call fails; else MAZE_OK. */
+maze_status maze_df_probe(const maze_config* cfg, int32_t what, const double* in, const int32_t* kind, int32_t n,
+                          double* out0, double* out1);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,6 +6,7 @@
 #include <math.h>
 
 #include "maze_internal.cuh"
+#include "df_arith.cuh"
 
 namespace maze {
 
@@ -378,6 +379,38 @@ __device__ __forceinline__ void tf_pair(const ForceArgs& a, int kind, double r2,
   const double ex = exp_tab(fma(-a.B, r, a.Ec[kind]), a.exp2tab);   // A exp(B (s - r))
   V = ex - fma(a.C[kind], ir6, fma(a.D[kind], ir8, a.Vc[kind]));
   fr = fma(a.B * ex, ir, -ir8 * fma(a.D8[kind], ir2, a.C6[kind]));   // B ex / r - 6C r^-8 - 8D r^-10
+}
+
+__device__ __forceinline__ dfl f2df(float2 v) { return {v.x, v.y}; }
+
+// tf_pair in double-float arithmetic on the FP32 pipe (FP64 boxes of the
+// once-per-pair kernel): the same quantities from the squared distance r2 as
+// a (hi, lo) pair, to ~1e-13 of the terms' magnitudes. 1/r from the FP32
+// reciprocal square root of r2's hi part, one FP32 Newton step (y0 within an
+// ulp or two, so that the correction below is small and its roundings
+// negligible), then one Halley step with e = 1 - r2 y0^2 formed exactly (y0^2
+// and r2.h y0^2 as exact products; 1 - r2.h y0^2 is exact, the two lie
+// within a factor of 2): y = y0 + y0 e (1/2 + 3e/8); the repulsion
+// exp(Ec - B r) by df_exp; V and fr as in tf_pair.
+__device__ __forceinline__ void tf_pair_df(const ForceArgs& a, int kind, dfl r2, dfl& fr, dfl& V) {
+  const PairDf& k = a.pdf;
+  float y0 = rsqrtf(r2.h);
+  y0 = __fmul_rn(y0, __fmaf_rn(-0.5f, __fmul_rn(__fmul_rn(r2.h, y0), y0), 1.5f));
+  const dfl y2 = df_two_prod(y0, y0);
+  const dfl b = df_two_prod(r2.h, y2.h);
+  const float bl = __fmaf_rn(r2.l, y2.h, __fmaf_rn(r2.h, y2.l, b.l));
+  const float e = __fsub_rn(__fsub_rn(1.f, b.h), bl);
+  const dfl ir = df_fast_sum(y0, __fmul_rn(y0, __fmul_rn(e, __fmaf_rn(e, 0.375f, 0.5f))));
+  const dfl r = df_mul(r2, ir);
+  const dfl ir2 = df_sqr(ir);
+  const dfl ir4 = df_sqr(ir2);
+  const dfl ir6 = df_mul(ir4, ir2);
+  const dfl ir8 = df_sqr(ir4);
+  const dfl ex = df_exp(df_add(f2df(k.Ec[kind]), df_neg(df_mul(f2df(k.B), r))), a.exp2tab_f);   // A exp(B (s - r))
+  V = df_add(ex, df_neg(df_add(df_mul(f2df(k.C[kind]), ir6), df_add(df_mul(f2df(k.D[kind]), ir8), f2df(k.Vc[kind])))));
+  // B ex / r - r^-8 (6C + 8D r^-2)
+  fr = df_add(df_mul(df_mul(f2df(k.B), ex), ir),
+              df_neg(df_mul(ir8, df_add(df_mul(f2df(k.D8[kind]), ir2), f2df(k.C6[kind])))));
 }
 
 // Per-lane pair sums (FP64 mode uses the doubles, mixed the floats).
@@ -1305,6 +1338,12 @@ __device__ __forceinline__ void gather_cell(const ForceArgs& a, int c) {
 // neighbour cell's offset folded in by TwoSum, displacements as exact FP32
 // sums, the pair arithmetic in FP32; the same once-per-pair bookkeeping with
 // 2^-40 fixed-point sums, and the FP32 gather of the cell's ions.
+// kDF: the FP64 boxes' form, the same staging with the displacement kept as
+// a double-float pair (the hi parts' difference exact by TwoSum, the lo
+// parts' difference added), r^2 from exact squares, the pair by tf_pair_df
+// and the 2^-40 integers from both halves of each product; the gather in
+// FP64. Every quantity reaches ~1e-13 relative (the cell-relative hi + lo
+// coordinates hold a position to ~2^-44 A), the FP64 force bar is 1e-10.
 template <int kW>
 struct HalfSmemF {
   float4 h[kHalfChunk];                            // hi parts (offset folded), type in l.w
@@ -1318,7 +1357,7 @@ struct HalfSmemF {
   int bad;
 };
 
-template <int kW, bool kGather = true>
+template <int kW, bool kGather = true, bool kDF = false>
 __device__ __forceinline__ void pairs_half_cell_mixed(const ForceArgs& a, int c, HalfSmemF<kW>& sm) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -1396,23 +1435,52 @@ __device__ __forceinline__ void pairs_half_cell_mixed(const ForceArgs& a, int c,
         const float4 ph = a.rel_hi_sorted[hs], pl = a.rel_lo_sorted[hs];
         const int ti = (int)pl.w;
         const float4 h = sm.h[e2], l = sm.l[e2];
-        const float dx = disp_df(ph.x, pl.x, h.x, l.x, 0.f, 0.f);
-        const float dy = disp_df(ph.y, pl.y, h.y, l.y, 0.f, 0.f);
-        const float dz = disp_df(ph.z, pl.z, h.z, l.z, 0.f, 0.f);
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 >= a.rc2f) return;
         const int kind = ti + (int)l.w;
-        const float ir = rsqrtf(r2);
-        const float r = r2 * ir;
-        const float ir2 = ir * ir;
-        const float ir6 = ir2 * ir2 * ir2;
-        const float ir8 = ir6 * ir2;
-        const float exv = a.Af[kind] * expf(a.Bf * (a.sf[kind] - r));
-        const float V = exv - a.Cf[kind] * ir6 - a.Df[kind] * ir8 - a.Vcf[kind];
-        const float fr = a.Bf * exv * ir - 6.f * a.Cf[kind] * ir8 - 8.f * a.Df[kind] * ir8 * ir2;
+        long long qx, qy, qz, qv;
+        if constexpr (kDF) {
+          const dfl sx = df_two_sum(h.x, -ph.x), sy = df_two_sum(h.y, -ph.y), sz = df_two_sum(h.z, -ph.z);
+          // (Fast2Sum: the lo parts' difference is below 2^-18 A, so it can
+          // exceed the hi difference only for a component of that size,
+          // whose rounding then stays below 2^-42 A)
+          const dfl dx = df_fast_sum(sx.h, __fadd_rn(sx.l, __fsub_rn(l.x, pl.x)));
+          const dfl dy = df_fast_sum(sy.h, __fadd_rn(sy.l, __fsub_rn(l.y, pl.y)));
+          const dfl dz = df_fast_sum(sz.h, __fadd_rn(sz.l, __fsub_rn(l.z, pl.z)));
+          const dfl px = df_two_prod(dx.h, dx.h), py = df_two_prod(dy.h, dy.h), pz = df_two_prod(dz.h, dz.h);
+          const dfl s1 = df_two_sum(px.h, py.h);
+          const dfl s2 = df_two_sum(s1.h, pz.h);
+          float lo = __fadd_rn(s1.l, s2.l);
+          lo = __fadd_rn(lo, __fmaf_rn(__fadd_rn(dx.h, dx.h), dx.l, px.l));
+          lo = __fadd_rn(lo, __fmaf_rn(__fadd_rn(dy.h, dy.h), dy.l, py.l));
+          lo = __fadd_rn(lo, __fmaf_rn(__fadd_rn(dz.h, dz.h), dz.l, pz.l));
+          const dfl r2 = df_fast_sum(s2.h, lo);
+          if (!df_less(r2, f2df(a.pdf.rc2))) return;
+          dfl fr, V;
+          tf_pair_df(a, kind, r2, fr, V);
+          const dfl fx = df_mul(fr, dx), fy = df_mul(fr, dy), fz = df_mul(fr, dz);
+          qx = round_scaled_f(fx.h, 40) + round_scaled_f(fx.l, 40);
+          qy = round_scaled_f(fy.h, 40) + round_scaled_f(fy.l, 40);
+          qz = round_scaled_f(fz.h, 40) + round_scaled_f(fz.l, 40);
+          qv = round_scaled_f(V.h, 40) + round_scaled_f(V.l, 40);
+        } else {
+          const float dx = disp_df(ph.x, pl.x, h.x, l.x, 0.f, 0.f);
+          const float dy = disp_df(ph.y, pl.y, h.y, l.y, 0.f, 0.f);
+          const float dz = disp_df(ph.z, pl.z, h.z, l.z, 0.f, 0.f);
+          const float r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 >= a.rc2f) return;
+          const float ir = rsqrtf(r2);
+          const float r = r2 * ir;
+          const float ir2 = ir * ir;
+          const float ir6 = ir2 * ir2 * ir2;
+          const float ir8 = ir6 * ir2;
+          const float exv = a.Af[kind] * expf(a.Bf * (a.sf[kind] - r));
+          const float V = exv - a.Cf[kind] * ir6 - a.Df[kind] * ir8 - a.Vcf[kind];
+          const float fr = a.Bf * exv * ir - 6.f * a.Cf[kind] * ir8 - 8.f * a.Df[kind] * ir8 * ir2;
+          qx = round_scaled_f(fr * dx, 40);
+          qy = round_scaled_f(fr * dy, 40);
+          qz = round_scaled_f(fr * dz, 40);
+          qv = round_scaled_f(V, 40);
+        }
         // the partner +f, the home ion -f: the same 2^-40 integers
-        const long long qx = round_scaled_f(fr * dx, 40), qy = round_scaled_f(fr * dy, 40),
-                        qz = round_scaled_f(fr * dz, 40), qv = round_scaled_f(V, 40);
         if (prv) {
           px -= qx;
           py -= qy;

@@ -3,6 +3,7 @@
 // checkpoints. See include/maze.h for the contract of each entry point.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <cmath>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -183,8 +184,8 @@ IonArgs ion_args(maze_ctx* c, int do_move, int do_spread) {
   a.wbuf32 = c->mixed ? c->wbuf32 : nullptr;
   a.wbase = c->wbase;
   a.io = (do_move && c->io_capture) ? c->io_desc : nullptr;
-  a.rel_hi = c->mixed ? c->rel_hi : nullptr;
-  a.rel_lo = c->mixed ? c->rel_lo : nullptr;
+  a.rel_hi = (c->mixed || c->pair_df) ? c->rel_hi : nullptr;
+  a.rel_lo = (c->mixed || c->pair_df) ? c->rel_lo : nullptr;
   a.cell_len = c->nc >= 3 ? c->L / c->nc : c->L;
   a.wdbuf = c->wdbuf;
   a.wdbuf32 = c->wdbuf32;
@@ -203,12 +204,46 @@ CellArgs cell_args(maze_ctx* c) {
   a.cell_ions = c->cell_ions;
   a.pos32 = c->pos32;
   a.pos_sorted = c->pos_sorted;
-  a.rel_hi = c->mixed ? c->rel_hi : nullptr;
+  a.rel_hi = (c->mixed || c->pair_df) ? c->rel_hi : nullptr;
   a.rel_lo = c->rel_lo;
   a.rel_hi_sorted = c->rel_hi_s;
   a.rel_lo_sorted = c->rel_lo_s;
   a.rec = c->rec;
   return a;
+}
+
+// The Tosi-Fumi table of the pair kernels from the configuration, V(r) =
+// A exp(B (s - r)) - C r^-6 - D r^-8 - V(r_cut) per pair kind, in FP64 and as
+// (hi, lo) float pairs for the double-float form.
+void fill_pair_consts(const maze_config& g, ForceArgs& a) {
+  const double rc = g.r_cut;
+  for (int k = 0; k < 3; ++k) {
+    a.A[k] = g.tf_A[k];
+    a.s[k] = g.tf_s[k];
+    a.C[k] = g.tf_C[k];
+    a.D[k] = g.tf_D[k];
+    a.Vc[k] = g.tf_A[k] * exp(g.tf_B * (g.tf_s[k] - rc)) - g.tf_C[k] / pow(rc, 6) - g.tf_D[k] / pow(rc, 8);
+    a.Ec[k] = g.tf_B * g.tf_s[k] + log(g.tf_A[k]);   // (A = 0: -inf, exp gives 0)
+    a.C6[k] = 6.0 * g.tf_C[k];
+    a.D8[k] = 8.0 * g.tf_D[k];
+  }
+  a.B = g.tf_B;
+  a.rc2 = rc * rc;
+  auto split = [](double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+  };
+  a.pdf.B = split(g.tf_B);
+  a.pdf.rc2 = split(a.rc2);
+  for (int k = 0; k < 3; ++k) {
+    // (A = 0 makes Ec -inf: a large negative finite value gives the same 0)
+    a.pdf.Ec[k] = split(std::isfinite(a.Ec[k]) ? a.Ec[k] : -1e4);
+    a.pdf.C[k] = split(a.C[k]);
+    a.pdf.D[k] = split(a.D[k]);
+    a.pdf.Vc[k] = split(a.Vc[k]);
+    a.pdf.C6[k] = split(a.C6[k]);
+    a.pdf.D8[k] = split(a.D8[k]);
+  }
 }
 
 ForceArgs force_args(maze_ctx* c, const double* phi, int do_kick, int count_step) {
@@ -265,19 +300,10 @@ ForceArgs force_args(maze_ctx* c, const double* phi, int do_kick, int count_step
   a.dt = g.dt;
   a.ke_coef = 0.5 / MAZE_ACC_UNIT;
   const double rc = g.r_cut;
-  for (int k = 0; k < 3; ++k) {
-    a.A[k] = g.tf_A[k];
-    a.s[k] = g.tf_s[k];
-    a.C[k] = g.tf_C[k];
-    a.D[k] = g.tf_D[k];
-    a.Vc[k] = g.tf_A[k] * exp(g.tf_B * (g.tf_s[k] - rc)) - g.tf_C[k] / pow(rc, 6) - g.tf_D[k] / pow(rc, 8);
-    a.Ec[k] = g.tf_B * g.tf_s[k] + log(g.tf_A[k]);   // (A = 0: -inf, exp gives 0)
-    a.C6[k] = 6.0 * g.tf_C[k];
-    a.D8[k] = 8.0 * g.tf_D[k];
-  }
+  fill_pair_consts(g, a);
   a.exp2tab = c->exp2tab;
-  a.B = g.tf_B;
-  a.rc2 = rc * rc;
+  a.pair_df = c->pair_df ? 1 : 0;
+  a.exp2tab_f = c->exp2tab_f;
   for (int k = 0; k < 3; ++k) {
     a.Af[k] = (float)a.A[k];
     a.sf[k] = (float)a.s[k];
@@ -1018,6 +1044,17 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
       (!c->mixed || c->N > 64)) {
     AL(c->pair_fix, 4 * (size_t)n);
     AL(c->gath, 4 * (size_t)n);
+    // FP64 boxes: the pair arithmetic in double-float on the FP32 pipe, from
+    // cell-relative hi + lo positions (MAZE_PAIRS_FP64=1: in FP64 arithmetic)
+    const char* pf = getenv("MAZE_PAIRS_FP64");
+    if (!c->mixed && !(pf && pf[0] == '1')) {
+      c->pair_df = true;
+      AL(c->rel_hi, (size_t)n);
+      AL(c->rel_lo, (size_t)n);
+      AL(c->rel_hi_s, (size_t)n);
+      AL(c->rel_lo_s, (size_t)n);
+      AL(c->exp2tab_f, 64);
+    }
     // the split of each SM: P pair blocks of kForceThreads and one solve
     // block of T threads, T the largest whose registers fit beside them. The
     // register file is split over the SM's 4 sub-partitions, warps are
@@ -1030,7 +1067,7 @@ maze_status ctx_setup(const maze_config* cfg, Arena* arena, maze_ctx** out) {
     if (ov && sscanf(ov, "%dx%d", &ot, &op) != 2) ot = -1;
     int regs_sm = 0;
     cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-    const int rp = (pairs_only_regs(c->mixed) + 7) / 8 * 8;
+    const int rp = (pairs_only_regs(c->mixed, c->pair_df) + 7) / 8 * 8;
     const int rs = ((c->mixed ? mixed_grid_regs() : mgfix_regs()) + 7) / 8 * 8;
     const int pair_warps = op * kForceThreads / 32;
     const int per_part = regs_sm / 4 - (pair_warps + 3) / 4 * 32 * rp;
@@ -1134,6 +1171,9 @@ maze_status ctx_create(const maze_config* cfg, Arena* arena, maze_ctx** out, boo
   std::vector<double> e2(64);
   exp2_table(e2.data());
   CKC(cudaMemcpyAsync(c->exp2tab, e2.data(), 64 * 8, cudaMemcpyHostToDevice, st));
+  std::vector<float2> e2f(64);
+  for (int j = 0; j < 64; ++j) e2f[j] = make_float2((float)e2[j], (float)(e2[j] - (double)(float)e2[j]));
+  if (c->exp2tab_f) CKC(cudaMemcpyAsync(c->exp2tab_f, e2f.data(), 64 * sizeof(float2), cudaMemcpyHostToDevice, st));
   if (!gkf.empty()) CKC(cudaMemcpyAsync(c->mx_g, gkf.data(), gkf.size() * 4, cudaMemcpyHostToDevice, st));
   CKC(cudaMemsetAsync(c->force, 0, 3 * (size_t)n * 8, st));
   CKC(cudaMemsetAsync(c->force_el, 0, 3 * (size_t)n * 8, st));

@@ -72,6 +72,8 @@ struct maze_ctx {
   maze::MgArgs mg = {};
   double *mg_x = nullptr, *mg_b = nullptr, *mg_r = nullptr, *mg_g = nullptr;
   double* exp2tab = nullptr;   // [64] 2^(j/64), the pair forces' exponential
+  float2* exp2tab_f = nullptr;  // [64] the same as (hi, lo) floats (double-float pairs)
+  bool pair_df = false;         // FP64 once-per-pair kernel with double-float pair arithmetic
   // mixed precision: phi, y, sigma hold double-float pairs (float2, 8 B)
   bool mixed = false;
   bool fixmg = false;     // MAZE_FP64_FIXMG: the integer defect-correction V-cycle

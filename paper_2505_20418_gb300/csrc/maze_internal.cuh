@@ -102,6 +102,13 @@ struct CellArgs {
   maze_stats* rec;
 };
 
+// Tosi-Fumi constants as (hi, lo) float pairs for the double-float pair
+// arithmetic of FP64 boxes (each pair the double's value to ~2^-48).
+struct PairDf {
+  float2 B, rc2;
+  float2 Ec[3], C[3], D[3], Vc[3], C6[3], D8[3];
+};
+
 struct ForceArgs {
   int n;
   double L, h;
@@ -146,6 +153,9 @@ struct ForceArgs {
   double Ec[3];          // B s + ln A: the repulsion A exp(B (s - r)) = exp(Ec - B r)
   double C6[3], D8[3];   // 6 C, 8 D (the force's dispersion terms)
   const double* exp2tab; // [64] 2^(j/64), j = 0..63 (exp_tab)
+  int pair_df;           // 1: FP64 box whose pair arithmetic runs in double-float on the FP32 pipe
+  PairDf pdf;            // the Tosi-Fumi table for it
+  const float2* exp2tab_f;  // [64] 2^(j/64) as (hi, lo) floats (df_exp)
   double B;
   double rc2;            // r_cut^2
   float rc2_filter;      // (r_cut + margin)^2 for the FP32 pre-filter
@@ -270,7 +280,8 @@ cudaError_t launch_pairs(const ForceArgs& a, cudaStream_t s);
 // then S9 one thread per ion.
 cudaError_t launch_pairs_half(const ForceArgs& a, cudaStream_t s);
 cudaError_t launch_pairs_only(const ForceArgs& a, int blocks, int smem_bytes, cudaStream_t s);
-int pairs_only_regs(bool mixed);   // registers per thread of k_pairs_only(_mixed)
+int pairs_only_regs(bool mixed, bool df);   // registers per thread of k_pairs_only(_mixed, _df)
+void fill_pair_consts(const maze_config& g, ForceArgs& a);   // Tosi-Fumi table (host)
 int mgfix_regs();                  // and of k_mgfix_solve
 int mixed_grid_regs();             // and of k_mixed_grid
 cudaError_t launch_gather_cells(const ForceArgs& a, cudaStream_t s);

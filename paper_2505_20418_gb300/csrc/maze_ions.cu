@@ -336,6 +336,13 @@ __global__ void __launch_bounds__(kForceThreads) k_pairs_half_mixed(ForceArgs a)
   if (forces_live(a)) pairs_half_cell_mixed<kForceThreads / 32>(a, blockIdx.x, sm);
 }
 
+// The FP64 boxes' form with the pair arithmetic in double-float on the FP32
+// pipe (the gather in FP64).
+__global__ void __launch_bounds__(kForceThreads) k_pairs_half_df(ForceArgs a) {
+  __shared__ HalfSmemF<kForceThreads / 32> sm;
+  if (forces_live(a)) pairs_half_cell_mixed<kForceThreads / 32, true, true>(a, blockIdx.x, sm);
+}
+
 // S8 alone (no gather), persistent: gridDim.x blocks take the cells in turn
 // (FP64, or the FP32 pair arithmetic of mixed precision).
 // The block's shared memory is padded (dynamic size set by the launcher) so
@@ -363,15 +370,31 @@ __global__ void __launch_bounds__(kForceThreads) k_pairs_only_mixed(ForceArgs a)
   }
 }
 
+__global__ void __launch_bounds__(kForceThreads) k_pairs_only_df(ForceArgs a) {
+  extern __shared__ __align__(16) unsigned char pairs_smem[];
+  HalfSmemF<kForceThreads / 32>& sm = *reinterpret_cast<HalfSmemF<kForceThreads / 32>*>(pairs_smem);
+  if (!forces_live(a)) return;
+  const int ncell = a.nc * a.nc * a.nc;
+  for (int c = blockIdx.x; c < ncell; c += gridDim.x) {
+    pairs_half_cell_mixed<kForceThreads / 32, false, true>(a, c, sm);
+    __syncthreads();
+  }
+}
+
 // S7 alone, one block per cell (after the solve, beside which k_pairs_only ran).
 __global__ void __launch_bounds__(kForceThreads) k_gather_cells(ForceArgs a) {
   if (forces_live(a)) gather_cell<kForceThreads / 32>(a, blockIdx.x);
 }
 
 cudaError_t launch_pairs_only(const ForceArgs& a, int blocks, int smem_bytes, cudaStream_t s) {
-  const int need = a.mixed ? (int)sizeof(HalfSmemF<kForceThreads / 32>) : (int)sizeof(HalfSmem<kForceThreads / 32>);
+  const int need = (a.mixed || a.pair_df) ? (int)sizeof(HalfSmemF<kForceThreads / 32>)
+                                          : (int)sizeof(HalfSmem<kForceThreads / 32>);
   if (smem_bytes < need) smem_bytes = need;
-  if (a.mixed) {
+  if (a.pair_df) {
+    cudaError_t e = cudaFuncSetAttribute(k_pairs_only_df, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e != cudaSuccess) return e;
+    k_pairs_only_df<<<blocks, kForceThreads, smem_bytes, s>>>(a);
+  } else if (a.mixed) {
     cudaError_t e = cudaFuncSetAttribute(k_pairs_only_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e != cudaSuccess) return e;
     k_pairs_only_mixed<<<blocks, kForceThreads, smem_bytes, s>>>(a);
@@ -383,10 +406,10 @@ cudaError_t launch_pairs_only(const ForceArgs& a, int blocks, int smem_bytes, cu
   return cudaGetLastError();
 }
 
-int pairs_only_regs(bool mixed) {
+int pairs_only_regs(bool mixed, bool df) {
   cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, mixed ? (const void*)k_pairs_only_mixed : (const void*)k_pairs_only) != cudaSuccess)
-    return 255;
+  const void* k = df ? (const void*)k_pairs_only_df : mixed ? (const void*)k_pairs_only_mixed : (const void*)k_pairs_only;
+  if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) return 255;
   return fa.numRegs;
 }
 
@@ -398,6 +421,8 @@ cudaError_t launch_gather_cells(const ForceArgs& a, cudaStream_t s) {
 cudaError_t launch_pairs_half(const ForceArgs& a, cudaStream_t s) {
   if (a.mixed)
     k_pairs_half_mixed<<<a.nc * a.nc * a.nc, kForceThreads, 0, s>>>(a);
+  else if (a.pair_df)
+    k_pairs_half_df<<<a.nc * a.nc * a.nc, kForceThreads, 0, s>>>(a);
   else
     k_pairs_half<<<a.nc * a.nc * a.nc, kForceThreads, 0, s>>>(a);
   return cudaGetLastError();

@@ -5,10 +5,13 @@
 //
 // maze_convert_probe: the integer-pipe FP32/FP64 conversions the hot kernels
 // use, computed beside the conversion instructions for a checker;
-// maze_exp_probe: the pair forces' table-driven exponential beside exp().
+// maze_exp_probe: the pair forces' table-driven exponential beside exp();
+// maze_df_probe: the double-float exponential and Tosi-Fumi pair of the FP64
+// boxes' pair kernel, and the FP64 pair beside them.
 #include <string>
+#include <vector>
 
-#include "maze_internal.cuh"
+#include "ion_body.cuh"
 
 namespace maze {
 
@@ -65,6 +68,29 @@ __global__ void k_exp_probe(const double* in, int n, const double* tab, double* 
   if (i >= n) return;
   own[i] = exp_tab(in[i], tab);
   ref[i] = exp(in[i]);
+}
+
+// df_exp, tf_pair_df or tf_pair on host doubles split into (hi, lo) floats.
+__global__ void k_df_probe(ForceArgs a, int what, const double* in, const int* kind, int n, double* o0, double* o1) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double x = in[i];
+  const float xh = dbl_to_flt(x);
+  const dfl xd = {xh, dbl_to_flt(x - flt_to_dbl(xh))};
+  if (what == 0) {
+    const dfl e = df_exp(xd, a.exp2tab_f);
+    o0[i] = flt_to_dbl(e.h) + flt_to_dbl(e.l);
+  } else if (what == 1) {
+    dfl fr, V;
+    tf_pair_df(a, kind[i], xd, fr, V);
+    o0[i] = flt_to_dbl(fr.h) + flt_to_dbl(fr.l);
+    o1[i] = flt_to_dbl(V.h) + flt_to_dbl(V.l);
+  } else {
+    double fr, V;
+    tf_pair(a, kind[i], x, fr, V);
+    o0[i] = fr;
+    o1[i] = V;
+  }
 }
 
 }  // namespace
@@ -183,5 +209,55 @@ extern "C" maze_status maze_wait_probe(int32_t which, void* cuda_stream, int32_t
     return MAZE_ERR_CUDA;
   }
   *status_out = host.status;
+  return MAZE_OK;
+}
+
+extern "C" maze_status maze_df_probe(const maze_config* cfg, int32_t what, const double* in, const int32_t* kind,
+                                     int32_t n, double* out0, double* out1) {
+  using namespace maze;
+  if (what < 0 || what > 2 || n < 0 || (n > 0 && (!in || !out0 || (what > 0 && (!cfg || !kind || !out1))))) {
+    set_last_error("maze_df_probe: what must be 0, 1 or 2, n >= 0, and the arrays (and cfg for a pair) non-NULL");
+    return MAZE_ERR_INVALID;
+  }
+  if (what > 0)
+    for (int32_t i = 0; i < n; ++i)
+      if (kind[i] < 0 || kind[i] > 2) {
+        set_last_error("maze_df_probe: kind must be 0, 1 or 2");
+        return MAZE_ERR_INVALID;
+      }
+  if (n == 0) return MAZE_OK;
+  ForceArgs a = {};
+  if (what > 0) fill_pair_consts(*cfg, a);
+  std::vector<double> e2(64);
+  exp2_table(e2.data());
+  std::vector<float2> tab(64);
+  for (int j = 0; j < 64; ++j) tab[j] = make_float2((float)e2[j], (float)(e2[j] - (double)(float)e2[j]));
+  const size_t N = (size_t)n;
+  char* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, 64 * 8 + 64 * sizeof(float2) + N * (8 + 4 + 8 + 8));
+  double* d_tab = reinterpret_cast<double*>(buf);
+  float2* d_tabf = reinterpret_cast<float2*>(d_tab + 64);
+  double* d_in = reinterpret_cast<double*>(d_tabf + 64);
+  double* d_o0 = d_in + N;
+  double* d_o1 = d_o0 + N;
+  int* d_kind = reinterpret_cast<int*>(d_o1 + N);
+  if (e == cudaSuccess) e = cudaMemcpy(d_tab, e2.data(), 64 * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_tabf, tab.data(), 64 * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_in, in, N * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(d_kind, 0, N * 4);
+  if (e == cudaSuccess && what > 0) e = cudaMemcpy(d_kind, kind, N * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    a.exp2tab = d_tab;
+    a.exp2tab_f = d_tabf;
+    k_df_probe<<<(n + 255) / 256, 256>>>(a, what, d_in, d_kind, n, d_o0, d_o1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out0, d_o0, N * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && what > 0) e = cudaMemcpy(out1, d_o1, N * 8, cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess) {
+    set_last_error((std::string("maze_df_probe: ") + cudaGetErrorString(e)).c_str());
+    return MAZE_ERR_CUDA;
+  }
   return MAZE_OK;
 }

@@ -34,7 +34,8 @@ EXPORTS = ("maze_create", "maze_spread", "maze_solve", "maze_gather", "maze_step
            "maze_batch_get", "maze_batch_set", "maze_batch_get_stats", "maze_batch_get_all_stats",
            "maze_batch_tune",
            "maze_batch_destroy", "maze_wait_probe", "maze_batch_step_ready_async", "maze_batch_sync",
-           "maze_batch_refresh", "maze_batch_autotune", "maze_convert_probe", "maze_exp_probe")
+           "maze_batch_refresh", "maze_batch_autotune", "maze_convert_probe", "maze_exp_probe",
+           "maze_df_probe")
 
 _D = ctypes.c_double
 _I = ctypes.c_int32
@@ -134,6 +135,7 @@ def load(path: str = LIB_PATH):
     lib.maze_wait_probe.argtypes = [_I, P, ctypes.POINTER(_I)]
     lib.maze_convert_probe.argtypes = [P, _I, P, P, P, P, P, P, P, P]
     lib.maze_exp_probe.argtypes = [P, _I, P, P]
+    lib.maze_df_probe.argtypes = [ctypes.POINTER(MazeConfig), _I, P, P, _I, P, P]
     lib.maze_batch_step_ready_async.argtypes = [P, _I]
     lib.maze_batch_sync.argtypes = [P]
     lib.maze_batch_refresh.argtypes = [P, ctypes.POINTER(_I), _I, ctypes.POINTER(_I)]
@@ -288,6 +290,30 @@ def maze_exp_probe(x):
     ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     st = load().maze_exp_probe(ptr(x), int(x.size), ptr(own), ptr(ref))
     return st, own, ref
+
+
+def maze_df_probe(what, x, kind=None, tf=None, r_cut=9.0):
+    """The double-float exponential (what 0) or Tosi-Fumi pair (what 1; FP64
+    form: what 2) of the FP64 boxes' pair kernel on the float64 array x, each
+    value split into (hi, lo) floats first; kind and the table tf (with
+    r_cut) for the pair. Returns (status, out0, out1)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = x.size
+    o0, o1 = np.zeros(n), np.zeros(n)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    cfg = None
+    k = np.zeros(n, np.int32) if kind is None else np.ascontiguousarray(kind, dtype=np.int32)
+    if tf is not None:
+        cfg = MazeConfig()
+        cfg.tf_A[:] = list(tf.A)
+        cfg.tf_B = tf.B
+        cfg.tf_s[:] = list(tf.s)
+        cfg.tf_C[:] = list(tf.C)
+        cfg.tf_D[:] = list(tf.D)
+        cfg.r_cut = float(r_cut)
+    st = load().maze_df_probe(ctypes.byref(cfg) if cfg is not None else None, int(what), ptr(x), ptr(k), int(n),
+                              ptr(o0), ptr(o1))
+    return st, o0, o1
 
 
 def maze_destroy(h):

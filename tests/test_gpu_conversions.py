@@ -75,3 +75,62 @@ def test_table_exp_within_two_ulp_of_exp():
     st, own, ref = M.maze_exp_probe(y)
     assert st == M.MAZE_OK
     assert np.array_equal(own[:-1], ref[:-1]) and np.isnan(own[-1]) and np.isnan(ref[-1])
+
+
+def split_df(x):
+    """x as the (hi, lo) float pair the GPU forms, and their exact sum."""
+    h = x.astype(np.float32).astype(np.float64)
+    l = (x - h).astype(np.float32).astype(np.float64)
+    return h + l
+
+
+def test_double_float_exp_against_numpy():
+    """The double-float exponential of the FP64 boxes' pair kernel (Tang's
+    table method with a 2^(j/64) table held as float pairs) against numpy's
+    FP64 exp of the same (hi, lo) input: within 3e-14 relative across the
+    pair repulsion's arguments, the table breakpoints and -70 <= x < 87 (below
+    -70 the lo float turns subnormal); 0 and infinity beyond |x| = 87."""
+    rng = np.random.default_rng(5)
+    ln2_64 = np.log(2.0) / 64
+    k = np.arange(-5000, 5000)
+    x = np.concatenate([rng.uniform(-30, 12, 200000), rng.uniform(-70, 86.9, 50000), k * ln2_64,
+                        (k + 0.5) * ln2_64, [0.0, -0.0, 1e-30, -1e-30, 86.9, -70.0]])
+    st, own, _ = M.maze_df_probe(0, x)
+    assert st == M.MAZE_OK, M.maze_last_error()
+    ref = np.exp(split_df(x))
+    rel = np.abs(own - ref) / ref
+    assert rel.max() < 3e-14, rel.max()
+    st, own, _ = M.maze_df_probe(0, np.array([88.0, 100.0, -88.0, -100.0]))
+    assert st == M.MAZE_OK
+    assert np.isinf(own[0]) and np.isinf(own[1]) and own[2] == 0 and own[3] == 0
+
+
+def test_double_float_tosi_fumi_pair_against_oracle():
+    """The Tosi-Fumi pair in double-float arithmetic (and in FP64, the other
+    kernels' form) against the oracle's pair formula in FP64 on the same
+    squared distance, every pair kind, 0.6 A to r_cut: -(dV/dr)/r and the
+    shifted energy within 5e-13 of the sum of their terms' magnitudes (the
+    double-float products keep ~2^-47; the FP64 force bar is 1e-10)."""
+    from oracle import maze_oracle as O
+    from paper_2505_20418_gb300 import synth
+    tf = synth.tosi_fumi_nacl()
+    rc = 9.0
+    rng = np.random.default_rng(8)
+    r = np.concatenate([rng.uniform(0.6, rc, 60000), np.linspace(1.5, rc * (1 - 1e-12), 3000)])
+    r2 = r * r
+    kind = rng.integers(0, 3, r.size).astype(np.int32)
+    rr = np.sqrt(split_df(r2))
+    V, f = O._tf_pair(rr, kind, tf)
+    Vc, _ = O._tf_pair(np.full(r.size, rc), kind, tf)
+    A, s, C, D = (np.asarray(v)[kind] for v in (tf.A, tf.s, tf.C, tf.D))
+    ex = A * np.exp(tf.B * (s - rr))
+    f_scale = (tf.B * ex + 6 * C / rr ** 7 + 8 * D / rr ** 9) / rr
+    v_scale = ex + C / rr ** 6 + D / rr ** 8 + np.abs(Vc)
+    for what in (1, 2):
+        st, fr, vv = M.maze_df_probe(what, r2, kind, tf, rc)
+        assert st == M.MAZE_OK, M.maze_last_error()
+        ef = np.abs(fr - f / rr) / f_scale
+        ev = np.abs(vv - (V - Vc)) / v_scale
+        assert ef.max() < 5e-13 and ev.max() < 5e-13, (what, ef.max(), ev.max())
+    st, _, _ = M.maze_df_probe(1, r2[:4], np.array([0, 1, 2, 3], np.int32), tf, rc)
+    assert st == M.MAZE_ERR_INVALID
