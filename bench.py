@@ -392,8 +392,17 @@ def measured_traffic(workload, kernel, precision, solver):
 
 # The arithmetic each --precision computes in: FP64; FP64 state with the
 # multigrid corrections in exact 64-bit integers; FP32 grid arithmetic with
-# double-float (FP32 pair) outer vectors.
+# double-float (FP32 pair) outer vectors. FP64 boxes with at least two cells
+# per SM evaluate the Tosi-Fumi pairs in double-float on the FP32 pipe (~1e-13
+# relative): "+f32x2" (dtype()).
 DTYPES = {"fp64": "f64", "fp64fix": "f64+i64", "mixed": "f32+f32x2"}
+
+
+def dtype(precision, w, sms=152):
+    """DTYPES, with the double-float pair arithmetic of large FP64 boxes."""
+    if precision != "mixed" and has_cells(w) and int(np.floor(w.L / w.rc)) ** 3 >= 2 * sms:
+        return DTYPES[precision] + "+f32x2"
+    return DTYPES[precision]
 
 
 def precision_code(M, precision):
@@ -655,7 +664,7 @@ def main():
             "metric": METRIC, "value": head["steps_per_s"], "unit": "steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": DTYPES[args.precision],
+            "vs_baseline": None, "dtype": dtype(args.precision, w, sms),
             "data": "synthetic", "config": config_dict(w, args),
             "p50_us": 1e3 * float(np.percentile(head["step_ms"], 50)),
             "p99_us": 1e3 * float(np.percentile(head["step_ms"], 99)),
@@ -674,7 +683,7 @@ def main():
                          "arithmetic)" if alt == "fp64" else
                          "the same box and steps with the integer V-cycle (FP64 state, corrections in exact "
                          "64-bit integers)") + ", timed the same way after the headline run",
-                "dtype": DTYPES[alt], "steps_per_s": o["steps_per_s"], "ms_per_step": o["ms_per_step"],
+                "dtype": dtype(alt, w, sms), "steps_per_s": o["steps_per_s"], "ms_per_step": o["ms_per_step"],
                 "iters_per_step": o["iters_per_step"], "force_error": o["force_error"],
                 "phase_us": o["phase_us"], "solve_us": 1e6 * o["solve_s"], "roofline": oroof,
                 "roofline_other": oother, "gpu_launches": kernels_per_step(alt, w, sms) * args.steps,

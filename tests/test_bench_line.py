@@ -44,7 +44,7 @@ def test_cuda_arm_line():
     steps = 8
     d = _run("--steps", str(steps), "--warmup", "3", timeout=1200)
     _common(d, steps)
-    assert "impl" not in d and d["dtype"] == "f64+i64" and d["config"]["grid"] == 256
+    assert "impl" not in d and d["dtype"] == "f64+i64+f32x2" and d["config"]["grid"] == 256
     r = d["roofline"]
     assert r["bound"] == "hbm" and r["peak"] > 0 and r["achieved"] > 0
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
@@ -59,7 +59,7 @@ def test_cuda_arm_line():
     assert sr["iters_per_step"] == d["iters_per_step"] and sr["roofline"]["bound"] == "hbm"
     assert sr["gpu_launches"] == 8 * steps
     f = d["fp64"]
-    assert f["dtype"] == "f64" and f["iters_per_step"] == d["iters_per_step"]
+    assert f["dtype"] == "f64+f32x2" and f["iters_per_step"] == d["iters_per_step"]
     assert abs(f["force_error"] - d["force_error"]) < 1e-9
     assert {f["roofline"]["bound"], f["roofline_other"]["bound"]} == {"hbm", "alu"}
     m = d["mixed"]
