@@ -57,7 +57,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=max(1, len(jobs))) as ex:
         list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
-        run([nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"])
+        run([nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart", "-ldl"])
     return LIB
 
 

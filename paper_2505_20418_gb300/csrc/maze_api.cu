@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "maze_ctx.h"
+#include "maze_trace.h"
 
 using namespace maze;
 
@@ -1383,12 +1384,16 @@ maze_status step_io_graph(maze_ctx* c, const double* pos_in, const double* vel_i
 
 extern "C" {
 
-maze_status maze_create(const maze_config* cfg, maze_ctx** out) { return ctx_create(cfg, nullptr, out); }
+maze_status maze_create(const maze_config* cfg, maze_ctx** out) {
+  maze::TraceRange tr("maze_create");
+  return ctx_create(cfg, nullptr, out);
+}
 
 
 void maze_destroy(maze_ctx* ctx) { free_ctx(ctx); }
 
 maze_status maze_spread(maze_ctx* c) {
+  maze::TraceRange tr("maze_spread");
   if (!c) return fail(MAZE_ERR_INVALID, "ctx is NULL");
   maze_status s = clear_status(c);
   if (s != MAZE_OK) return s;
@@ -1401,6 +1406,7 @@ maze_status maze_spread(maze_ctx* c) {
 }
 
 maze_status maze_solve(maze_ctx* c, int32_t* iters, double* resid) {
+  maze::TraceRange tr("maze_solve");
   if (!c) return fail(MAZE_ERR_INVALID, "ctx is NULL");
   maze_status s = clear_status(c);
   if (s != MAZE_OK) return s;
@@ -1415,6 +1421,7 @@ maze_status maze_solve(maze_ctx* c, int32_t* iters, double* resid) {
 }
 
 maze_status maze_gather(maze_ctx* c) {
+  maze::TraceRange tr("maze_gather");
   if (!c) return fail(MAZE_ERR_INVALID, "ctx is NULL");
   maze_status s = clear_status(c);
   if (s != MAZE_OK) return s;
@@ -1429,6 +1436,7 @@ maze_status maze_gather(maze_ctx* c) {
 }
 
 maze_status maze_step_async(maze_ctx* c, int32_t nsteps) {
+  maze::TraceRange tr("maze_step_async");
   if (!c) return fail(MAZE_ERR_INVALID, "ctx is NULL");
   if (nsteps < 0) return fail(MAZE_ERR_INVALID, "nsteps must be >= 0");
   c->rec_dirty = true;
@@ -1451,6 +1459,7 @@ maze_status maze_step_async(maze_ctx* c, int32_t nsteps) {
 }
 
 maze_status maze_step(maze_ctx* c, int32_t nsteps) {
+  maze::TraceRange tr("maze_step");
   if (!c) return fail(MAZE_ERR_INVALID, "ctx is NULL");
   maze_status s = MAZE_OK;
   if (c->rec_dirty) {   // (the record a synchronising call left is current)
@@ -1619,6 +1628,7 @@ maze_status maze_set(maze_ctx* c, int32_t what, const double* in) {
 
 maze_status maze_step_io(maze_ctx* c, const double* pos_in, const double* vel_in, int32_t nsteps, double* pos_out,
                          double* vel_out, maze_stats* stats_out) {
+  maze::TraceRange tr("maze_step_io");
   if (!c) return fail(MAZE_ERR_INVALID, "ctx is NULL");
   if (nsteps < 0) return fail(MAZE_ERR_INVALID, "nsteps must be >= 0");
   maze_status s;

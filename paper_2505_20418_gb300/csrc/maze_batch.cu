@@ -25,6 +25,7 @@
 
 #include "ion_body.cuh"
 #include "maze_ctx.h"
+#include "maze_trace.h"
 #include "mixed_body.cuh"
 
 namespace maze {
@@ -908,6 +909,7 @@ maze_status maze_batch_info(maze_batch* b, int32_t* count, int32_t* cluster_ctas
 }
 
 maze_status maze_batch_step_async(maze_batch* b, int32_t nsteps) {
+  maze::TraceRange tr("maze_batch_step_async");
   if (!b) return fail(MAZE_ERR_INVALID, "batch is NULL");
   if (nsteps < 0) return fail(MAZE_ERR_INVALID, "nsteps must be >= 0");
   return step_async(b, nsteps);
@@ -929,6 +931,7 @@ maze_status order_status(maze_batch* b) {
 }
 
 maze_status maze_batch_step(maze_batch* b, int32_t nsteps) {
+  maze::TraceRange tr("maze_batch_step");
   if (!b) return fail(MAZE_ERR_INVALID, "batch is NULL");
   if (nsteps < 0) return fail(MAZE_ERR_INVALID, "nsteps must be >= 0");
   maze_status s = step_async(b, nsteps);
@@ -937,6 +940,7 @@ maze_status maze_batch_step(maze_batch* b, int32_t nsteps) {
 }
 
 maze_status maze_batch_step_ready_async(maze_batch* b, int32_t nsteps) {
+  maze::TraceRange tr("maze_batch_step_ready_async");
   if (!b) return fail(MAZE_ERR_INVALID, "batch is NULL");
   if (nsteps < 0) return fail(MAZE_ERR_INVALID, "nsteps must be >= 0");
   return step_async(b, nsteps, false);
