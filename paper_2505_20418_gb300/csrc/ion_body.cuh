@@ -616,10 +616,14 @@ __device__ __forceinline__ void gather_el(const ForceArgs& a, int i, int lane, d
     vd = s0;
   } else {
     const double* w = a.wbuf + (size_t)i * 12;
+    // a lane's support points (sidx = lane, lane + 32) share ia and ib: the
+    // FP64 product w_a w_b once per lane (the same association as before)
+    const int ia = lane & (P - 1), ib = (lane >> lp) & (P - 1);
+    const double wab = w[ia] * w[4 + ib];
     for (int sidx = lane; sidx < P3; sidx += 32) {
-      const int ia = sidx & (P - 1), ib = (sidx >> lp) & (P - 1), ic = sidx >> (2 * lp);
+      const int ic = sidx >> (2 * lp);
       const int ix = wrap_idx(first.x + ia, N), iy = wrap_idx(first.y + ib, N), iz = wrap_idx(first.z + ic, N);
-      const double wt = w[ia] * w[4 + ib] * w[8 + ic];
+      const double wt = wab * w[8 + ic];
       const int row = iz * NN + iy * N;
       const int ixp = row + (ix == N - 1 ? 0 : ix + 1), ixm = row + (ix == 0 ? N - 1 : ix - 1);
       const int iyp = iz * NN + (iy == N - 1 ? 0 : iy + 1) * N + ix;

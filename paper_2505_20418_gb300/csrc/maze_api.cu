@@ -503,8 +503,10 @@ maze_status enqueue_step(maze_ctx* c, int timed) {
     // S8 needs only the positions and the cell list: after S1 and S2 it runs
     // on the side stream, sharing every SM with S3 and the solve (S4-S6),
     // whose V-cycle is bound by memory latency and integer work while the
-    // pairs are bound by the FP64 pipe; then S7 (needs phi^{k+1}) and S9.
-    // (Timed phases: S1; S2 and S3; the solve S4-S6; S7-S9.)
+    // pairs are bound by instruction issue; then S7 (needs phi^{k+1}) and S9.
+    // (Timed phases: S1; S2 and S3; the solve S4-S6; S7-S9.) The cell list
+    // on the side stream too (beside S3) made the step slower: the pairs
+    // then started late and ended after the solve.
     if (timed) CK(cudaEventRecordWithFlags(c->ev[0], c->stream, cudaEventRecordExternal));
     const IonArgs ia = ion_args(c, 1, 1);
     CK(launch_ion_update(ia, c->stream, 1));
