@@ -548,6 +548,47 @@ def time_box(args, M, w, precision, solver, stream, flush, dist=None, dev="cpu",
     return out
 
 
+def full_run(M, w, precision, solver, stream, flush):
+    """The configuration's whole run: a fresh box advanced its w.steps steps
+    from its initial state, every step timed with CUDA events (L2 flushed
+    between steps, outside the events), as a user runs it (no phase events in
+    the graphs). The V-cycle count per step grows as the lattice start melts
+    (steps 3 to ~35 need 4 at 512000 ions, later ones 5), so the K timed steps
+    after W warm-up steps of the line are an early window of this run; this
+    key gives the whole run beside them."""
+    import torch
+    pos, vel, types = synth.make_state(w)
+    tf = synth.tosi_fumi_nacl()
+    sim = M.MazeSim(pos, vel, types, w.L, w.N, tf, r_cut=w.rc, dt=w.dt, tol=w.tol, order=w.order,
+                    solver=M.MAZE_SOLVER_MG if solver == "mg" else M.MAZE_SOLVER_CG,
+                    precision=precision_code(M, precision), stream=stream.cuda_stream)
+    sim.set_timing(False)
+    ms, its = [], []
+    prev = sim.stats()["total_iters"]
+    for _ in range(w.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0.record(stream)
+            sim.step_async(1)
+            e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        t = sim.stats()["total_iters"]
+        its.append(t - prev)
+        prev = t
+    st = sim.stats()
+    sim.close()
+    if st["status"] != 0:
+        raise RuntimeError(f"full run failed: {st}")
+    q = max(1, len(ms) // 4)
+    return {"what": f"the configuration's {w.steps} steps from its initial state on a fresh box, each timed "
+                    "(untimed graphs, L2 flushed between steps)",
+            "steps": w.steps, "steps_per_s": 1e3 * len(ms) / sum(ms), "ms_per_step": sum(ms) / len(ms),
+            "iters_per_step": sum(its) / len(its),
+            "last_quarter": {"ms_per_step": sum(ms[-q:]) / q, "iters_per_step": sum(its[-q:]) / q}}
+
+
 def rooflines(w, precision, solver, iters, solve_s, workload, sms):
     """The solve kernel against its roofs: HBM (measured copy peak) always;
     for FP64 multigrid also the FP64 pipe. ``roofline`` is the binding one
@@ -592,6 +633,7 @@ def main():
     ap.add_argument("--precision", default="fp64fix", choices=["fp64fix", "fp64", "mixed"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-full", action="store_true", help="skip the configuration's whole run beside the line")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the runs beside an FP64 line (the other FP64 form and mixed precision)")
     args = ap.parse_args()
@@ -650,6 +692,10 @@ def main():
                 del os.environ["MAZE_OVERLAP"]
         mixed = time_box(args, M, w, "mixed", "mg", stream, flush, dist, dev, world, rank, e2e=False)
 
+    whole = None
+    if rank == 0 and not args.no_full:
+        whole = full_run(M, w, args.precision, args.solver, stream, flush)
+
     if rank == 0:
         roof, other = rooflines(w, args.precision, args.solver, head["iters_per_step"], head["solve_s"],
                                 args.workload, sms)
@@ -674,6 +720,7 @@ def main():
             "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": head["e2e"],
             "timing_error": head["timing_error"],
             "gpu_launches": kernels_per_step(args.precision, w, sms) * args.steps, "clocks": head["clocks"],
+            "full_run": whole,
         }
         if other64 is not None:
             alt, o = other64

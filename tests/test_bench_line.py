@@ -55,6 +55,8 @@ def test_cuda_arm_line():
     assert d["clocks"]["sm_mhz"] > 0 and isinstance(d["clocks"]["reasons"], list)
     assert d["force_error"] < 1e-7                 # FP64 at tol 1e-10 (the solver tolerance dominates)
     assert d["ms_per_step"] > 0 and d["p99_us"] >= d["p50_us"] > 0
+    fr = d["full_run"]                             # the configuration's 200 steps from the start
+    assert fr["steps"] == 200 and fr["steps_per_s"] > 0 and fr["iters_per_step"] >= 4.0
     sr = d["serial"]
     assert sr["iters_per_step"] == d["iters_per_step"] and sr["roofline"]["bound"] == "hbm"
     assert sr["gpu_launches"] == 8 * steps
