@@ -191,13 +191,14 @@ __device__ __forceinline__ void nbr6_pair(const long long* o, int h0, int t0, in
   s1 = (p ? c.y + w : c.x + c.y) + (u.y + v.y) + (d.y + e.y);
 }
 
-// One red-black half-sweep of colour c on a split level: x = round((s - b) / 6);
-// two points per thread and round where the edge is a multiple of 4.
-__device__ __forceinline__ void half_sweep_i(long long* x, const long long* b, int N, int lg, int c, int tid,
-                                             int stride) {
+// One red-black half-sweep of colour c on a split level with its red and
+// black halves at xr and xb: x = round((s - b) / 6); two points per thread
+// and round where the edge is a multiple of 4.
+__device__ __forceinline__ void half_sweep_i(long long* xr, long long* xb, const long long* b, int N, int lg, int c,
+                                             int tid, int stride) {
   const int half = (N * N * N) >> 1;
-  long long* xc = x + c * half;
-  const long long* xo = x + (1 - c) * half;
+  long long* xc = c ? xb : xr;
+  const long long* xo = c ? xr : xb;
   const long long* bc = b + c * half;
   if ((N & 3) == 0) {
     const int npair = half >> 1;
@@ -232,7 +233,11 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_mgfix_solve(SolveArgs a, MgAr
   long long* const X = reinterpret_cast<long long*>(g.x);   // corrections, level 0 included
   long long* const B = reinterpret_cast<long long*>(g.b);   // right-hand sides
   long long* const R = reinterpret_cast<long long*>(g.r);   // residuals at red points
-  long long* const e_red = X;
+  // level 0's red corrections and its red residuals (for the restriction)
+  // live in two arrays whose roles swap when the stopping test has already
+  // made the next V-cycle's first red half-sweep (below)
+  long long* e_red = X;
+  long long* r_red0 = R;
   long long* const e_blk = X + half0;
   long long* const b_red = B;
   long long* const b_blk = B + half0;
@@ -275,6 +280,8 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_mgfix_solve(SolveArgs a, MgAr
   if (F > kMaxScale) F = kMaxScale;
   int it = 0;
   bool fresh = true;   // E = 0: level 0's first red half-sweep is E = round(-b / 6)
+  bool red_done = false;   // the stopping test made the next V-cycle's first red half-sweep
+  const bool spec = g.nu1 > 0;   // (the V-cycle starts with a red half-sweep on level 0)
   unsigned long long rmax = 0;
   bool ovf = false;
   double esum = 0.0;   // sum of E (units 2^-F) after the last V-cycle
@@ -298,27 +305,29 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_mgfix_solve(SolveArgs a, MgAr
     // ---- down: smooth, residual at red points, restrict
     for (int l = 0; l < g.L - 1; ++l) {
       const int N = g.Nl[l], lg = g.lg[l], half = (N * N * N) >> 1;
-      long long* x = X + g.off[l];
+      long long* xr = l ? X + g.off[l] : e_red;
+      long long* xb = l ? xr + half : e_blk;
       const long long* b = B + g.off[l];
       for (int t = 0; t < g.nu1; ++t) {
         // a first red half-sweep from a zero guess was written by the step
-        // above (level 0, fresh) or by the restriction (coarse levels)
-        if (t > 0 || (l == 0 && !fresh)) {
-          half_sweep_i(x, b, N, lg, 0, tid, stride);
+        // above (level 0, fresh) or by the restriction (coarse levels); on
+        // level 0 the previous stopping test may have made it (red_done)
+        if (t > 0 || (l == 0 && !fresh && !red_done)) {
+          half_sweep_i(xr, xb, b, N, lg, 0, tid, stride);
           if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
         }
-        half_sweep_i(x, b, N, lg, 1, tid, stride);
+        half_sweep_i(xr, xb, b, N, lg, 1, tid, stride);
         if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
       }
-      long long* r = R + g.off[l];   // red half-indices
+      long long* r = l ? R + g.off[l] : r_red0;   // red half-indices
       if ((N & 3) == 0) {
 #pragma unroll 2
         for (int h0 = 2 * tid; h0 < half; h0 += 2 * stride) {
           int t0, j, k;
           half_decode(h0, N, lg, t0, j, k);
           long long s0, s1;
-          nbr6_pair(x + half, h0, t0, j, k, (j + k) & 1, N, s0, s1);
-          const longlong2 xv = ld2(x + h0), bv = ld2(b + h0);
+          nbr6_pair(xb, h0, t0, j, k, (j + k) & 1, N, s0, s1);
+          const longlong2 xv = ld2(xr + h0), bv = ld2(b + h0);
           st2(r + h0, bv.x - s0 + 6 * xv.x, bv.y - s1 + 6 * xv.y);
         }
       } else {
@@ -326,7 +335,7 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_mgfix_solve(SolveArgs a, MgAr
         for (int h = tid; h < half; h += stride) {
           int t, j, k;
           half_decode(h, N, lg, t, j, k);
-          r[h] = b[h] - nbr6s(x + half, h, t, j, k, (j + k) & 1, N) + 6 * x[h];
+          r[h] = b[h] - nbr6s(xb, h, t, j, k, (j + k) & 1, N) + 6 * xr[h];
         }
       }
       if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
@@ -401,7 +410,8 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_mgfix_solve(SolveArgs a, MgAr
       const int N = g.Nl[l], lg = g.lg[l], half = (N * N * N) >> 1;
       const int Nc = g.Nl[l + 1];
       const bool csplit = l + 1 < g.L - 1;
-      long long* x = X + g.off[l];
+      long long* xr = l ? X + g.off[l] : e_red;
+      long long* xb = l ? xr + half : e_blk;
       const long long* b = B + g.off[l];
       const long long* xc = X + g.off[l + 1];
       for (int h = tid; h < half; h += stride) {
@@ -425,11 +435,11 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_mgfix_solve(SolveArgs a, MgAr
                          (xc[store_index(i0, j1, k1, Nc, csplit)] + xc[store_index(i1, j1, k1, Nc, csplit)])),
                     3);
         }
-        x[half + h] += e;
+        xb[h] += e;
       }
       if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
       for (int t = 0; t < g.nu2; ++t) {
-        half_sweep_i(x, b, N, lg, 0, tid, stride);
+        half_sweep_i(xr, xb, b, N, lg, 0, tid, stride);
         if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
         if (l == 0 && t == g.nu2 - 1) {
           if ((N & 3) == 0) {
@@ -438,11 +448,11 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_mgfix_solve(SolveArgs a, MgAr
               int t0, j, k;
               half_decode(h0, N, lg, t0, j, k);
               long long s0, s1;
-              nbr6_pair(x, h0, t0, j, k, (j + k + 1) & 1, N, s0, s1);
+              nbr6_pair(xr, h0, t0, j, k, (j + k + 1) & 1, N, s0, s1);
               const longlong2 bv = ld2(b + half + h0);
               const long long v0 = s0 - bv.x, v1 = s1 - bv.y;
               const long long e0 = div6(v0), e1 = div6(v1);
-              st2(x + half + h0, e0, e1);
+              st2(xb + h0, e0, e1);
               rmax = max(rmax, max(iabs(6 * e0 - v0), iabs(6 * e1 - v1)));
             }
           } else {
@@ -450,14 +460,14 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_mgfix_solve(SolveArgs a, MgAr
             for (int h = tid; h < half; h += stride) {
               int tt, j, k;
               half_decode(h, N, lg, tt, j, k);
-              const long long v = nbr6s(x, h, tt, j, k, (j + k + 1) & 1, N) - b[half + h];
+              const long long v = nbr6s(xr, h, tt, j, k, (j + k + 1) & 1, N) - b[half + h];
               const long long ev = div6(v);
-              x[half + h] = ev;
+              xb[h] = ev;
               rmax = max(rmax, iabs(6 * ev - v));
             }
           }
         } else {
-          half_sweep_i(x, b, N, lg, 1, tid, stride);
+          half_sweep_i(xr, xb, b, N, lg, 1, tid, stride);
         }
         if (!grid_barrier(a.bar, bar_epoch, a.rec)) return;
       }
@@ -467,6 +477,11 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_mgfix_solve(SolveArgs a, MgAr
     // ---- the stopping test (Eq. res_poisson_maze) on max |r|, r = b - M E at
     // red points (exact)
     // (and the sum of E, exact per thread: at most 2 half0 / threads terms below 2^54)
+    // The same pass also makes the red half-sweep that the next V-cycle
+    // would start with (it reads the same black neighbours and right-hand
+    // side) into the spare red array; if the solve goes on, the two red
+    // arrays swap roles and the next V-cycle skips that half-sweep. The
+    // iterates are unchanged; a pass and a grid barrier per V-cycle go.
     {
       long long es = 0;
       if ((N0 & 3) == 0) {
@@ -479,14 +494,17 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_mgfix_solve(SolveArgs a, MgAr
           const longlong2 er = ld2(e_red + h0), eb = ld2(e_blk + h0), bv = ld2(b_red + h0);
           rmax = max(rmax, max(iabs(bv.x - s0 + 6 * er.x), iabs(bv.y - s1 + 6 * er.y)));
           es += (er.x + er.y) + (eb.x + eb.y);
+          if (spec) st2(r_red0 + h0, div6(s0 - bv.x), div6(s1 - bv.y));
         }
       } else {
 #pragma unroll 2
         for (int h = tid; h < half0; h += stride) {
           int t, j, k;
           half_decode(h, N0, lg0, t, j, k);
-          rmax = max(rmax, iabs(b_red[h] - nbr6s(e_blk, h, t, j, k, (j + k) & 1, N0) + 6 * e_red[h]));
+          const long long s0 = nbr6s(e_blk, h, t, j, k, (j + k) & 1, N0);
+          rmax = max(rmax, iabs(b_red[h] - s0 + 6 * e_red[h]));
           es += e_red[h] + e_blk[h];
+          if (spec) r_red0[h] = div6(s0 - b_red[h]);
         }
       }
       const double v[3] = {fix_to_dbl((long long)rmax, 1075), ovf ? 1.0 : 0.0, fix_to_dbl(es, 1075)};
@@ -504,6 +522,15 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_mgfix_solve(SolveArgs a, MgAr
       // to y, keep the exact residual r = b - M E at every point as the new
       // right-hand side, rescaled, and start again from E = 0
       const int sft = t[0] > 0.0 ? (H - 1) - (dbl_exp(t[0]) - 1023) : 0;
+      red_done = false;
+      if (!(res < a.tol) && it < a.max_iter && !(sft >= 20 && F + sft <= kMaxScale) && spec) {
+        // the solve goes on without a restart: the red half-sweep above is
+        // the next V-cycle's first (all threads take the same decision)
+        long long* const tmp = e_red;
+        e_red = r_red0;
+        r_red0 = tmp;
+        red_done = true;
+      }
       if (!(res < a.tol) && it < a.max_iter && sft >= 20 && F + sft <= kMaxScale) {
         const int E = 1075 - F;
         double ys = 0.0;
