@@ -379,6 +379,7 @@ def config_dict(w, args, reference=False):
 # command and the other counters are in the named summary under profiles/.
 # A kernel changed after its capture must drop its entry (traffic null).
 MEASURED_TRAFFIC = {
+    ("nacl512000", "k_mgfix_solve", "fp64fix", "mg"): (10833341000, "profiles/k_mgfix_solve_nacl512000.md"),
     ("nacl512000", "k_mg_solve", "fp64", "mg"): (19889471000, "profiles/k_mg_solve_nacl512000_fp64.md"),
     ("nacl512000", "k_mixed_grid", "mixed", "mg"): (6902114000, "profiles/k_mixed_grid_nacl512000.md"),
 }
