@@ -79,6 +79,46 @@ cudaError_t launch_q_to_double(const unsigned long long* qfix, double* q, int n,
 // S2: one block scans, one thread per ion claims a slot, one warp per cell sorts.
 __global__ void k_cell_scan(CellArgs a) { cell_scan_block(a); }
 
+// The same scan with the counts staged in shared memory (boxes whose counts
+// fit): coalesced loads and stores instead of each thread walking its own
+// run of cells in global memory; each thread then scans a contiguous run of
+// the staged counts, and one block scan joins the runs.
+__global__ void __launch_bounds__(1024) k_cell_scan_smem(CellArgs a) {
+  extern __shared__ int s_cnt[];             // [ncell]
+  __shared__ int s_part[1024];
+  const int T = blockDim.x, nc = a.ncell;
+  for (int c = threadIdx.x; c < nc; c += T) {
+    s_cnt[c] = a.cell_count[c];
+    a.cell_count[c] = 0;                     // cleared for the next step
+  }
+  __syncthreads();
+  const int chunk = (nc + T - 1) / T;
+  const int lo = min(threadIdx.x * chunk, nc), hi = min(lo + chunk, nc);
+  int sum = 0;
+  for (int c = lo; c < hi; ++c) sum += s_cnt[c];
+  s_part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < T; o <<= 1) {          // Hillis-Steele inclusive scan of the runs' sums
+    const int v = threadIdx.x >= o ? s_part[threadIdx.x - o] : 0;
+    __syncthreads();
+    s_part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = s_part[threadIdx.x] - sum;
+  for (int c = lo; c < hi; ++c) {            // exclusive prefix sums, in place
+    const int v = s_cnt[c];
+    s_cnt[c] = run;
+    run += v;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < nc; c += T) {
+    const int v = s_cnt[c];
+    a.cell_start[c] = v;
+    a.cursor[c] = v;
+  }
+  if (threadIdx.x == T - 1) a.cell_start[nc] = s_part[T - 1];
+}
+
 __global__ void k_cell_fill(CellArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < a.n) cell_fill_ion(a, i);
@@ -93,7 +133,20 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_cell_sort(CellArgs a) {
 }
 
 cudaError_t launch_cells(const CellArgs& a, cudaStream_t s) {
-  k_cell_scan<<<1, 1024, 0, s>>>(a);
+  int dev = 0, smem_max = 0;                 // opt-in shared memory per block of this device
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    smem_max = 0;
+  }
+  const int need = a.ncell * (int)sizeof(int);
+  if (need + 8192 <= smem_max) {             // (the static 4 KB of partial sums beside it)
+    cudaError_t e = cudaFuncSetAttribute(k_cell_scan_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+    if (e != cudaSuccess) return e;
+    k_cell_scan_smem<<<1, 1024, need, s>>>(a);
+  } else {
+    k_cell_scan<<<1, 1024, 0, s>>>(a);
+  }
   k_cell_fill<<<(a.n + 255) / 256, 256, 0, s>>>(a);
   k_cell_sort<<<(a.ncell + kSortWarps - 1) / kSortWarps, kSortWarps * 32, 0, s>>>(a);
   return cudaGetLastError();
